@@ -1,0 +1,266 @@
+/*
+ * nb_oracle.c -- the oracle for the short-range non-bonded forces.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load or call this file.  It shares no
+ * code, header, table or constant with the CUDA library, and the library
+ * never calls it.
+ *
+ * What it computes is the plain definition of the quantity that the paper's
+ * cluster-pair method evaluates (Introduction: each particle's electrostatic
+ * and van der Waals forces from all other particles inside a spherical
+ * cut-off; Section 3.2: the cluster-pair list only adds interactions that are
+ * known to be zero, so the method reaches the same sum):
+ *
+ *   for every unordered atom pair (i, j), i < j, that is not excluded:
+ *     d   = x_i - x_j, reduced to the minimum image of the rectangular box
+ *     r^2 = |d|^2;  the pair contributes only if r^2 < rc^2 (strict)
+ *     Lennard-Jones  V = c12 / r^12 - c6 / r^6
+ *                    F/r = (12 c12 / r^12 - 6 c6 / r^6) / r^2
+ *     reaction field V = f qi qj / eps_r (1/r + k_rf r^2 - c_rf)
+ *                    F/r = f qi qj / eps_r (1/r^3 - 2 k_rf)
+ *                    k_rf = (eps_rf - eps_r) / ((2 eps_rf + eps_r) rc^3),
+ *                    c_rf = 1/rc + k_rf rc^2  (eps_rf = 0 means infinity:
+ *                    k_rf = 1 / (2 rc^3))
+ *     Ewald real     V = f qi qj / eps_r erfc(beta r) / r
+ *                    F/r = f qi qj / eps_r (erfc(beta r)/r
+ *                          + 2 beta/sqrt(pi) exp(-beta^2 r^2)) / r^2
+ *     force on i = (F/r) d, force on j = -(F/r) d
+ *     virial Xi -= 1/2 (F/r) d (x) d
+ *
+ * Everything is double precision.  Inputs are the same float32 values the
+ * CUDA path receives, promoted exactly by the caller.  Exclusions are a CSR
+ * list over atoms; a pair is excluded if either atom lists the other.
+ *
+ * The interaction forms, the strict cut-off test, the virial convention and
+ * the treatment of excluded pairs (they contribute nothing) are readings of
+ * a paper that states none of them; each one is pinned by the oracle tests.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_RF 0
+#define OR_EWALD 1
+
+static double min_image(double d, double L) { return d - L * round(d / L); }
+
+static int excluded(int i, int j, const int *ei, const int *ea) {
+    if (!ei) return 0;
+    for (int k = ei[i]; k < ei[i + 1]; ++k)
+        if (ea[k] == j) return 1;
+    for (int k = ei[j]; k < ei[j + 1]; ++k)
+        if (ea[k] == i) return 1;
+    return 0;
+}
+
+typedef struct {
+    double rc2, krf, crf, beta, fpre;
+    int coul, ntypes;
+    const double *c6, *c12;
+} setup_t;
+
+static setup_t make_setup(double rc, int coul, double eps_r, double eps_rf, double beta,
+                          double fcoul, int ntypes, const double *c6, const double *c12) {
+    setup_t s;
+    s.rc2 = rc * rc;
+    if (eps_rf == 0.0)
+        s.krf = 1.0 / (2.0 * rc * rc * rc);
+    else
+        s.krf = (eps_rf - eps_r) / ((2.0 * eps_rf + eps_r) * rc * rc * rc);
+    s.crf = 1.0 / rc + s.krf * rc * rc;
+    s.beta = beta;
+    s.fpre = fcoul / eps_r;
+    s.coul = coul;
+    s.ntypes = ntypes;
+    s.c6 = c6;
+    s.c12 = c12;
+    return s;
+}
+
+/* One pair at squared distance r2 (already known to be inside the cut-off).
+ * Returns F/r; writes the energy parts. */
+static double pair_terms(const setup_t *s, double r2, double qq, int ti, int tj, double *v_lj,
+                         double *v_c, double *e12, double *e6, double *fr_lj, double *fr_c) {
+    double r = sqrt(r2);
+    double c6 = s->c6[ti * s->ntypes + tj];
+    double c12 = s->c12[ti * s->ntypes + tj];
+    double ir2 = 1.0 / r2;
+    double ir6 = ir2 * ir2 * ir2;
+    double t12 = c12 * ir6 * ir6;
+    double t6 = c6 * ir6;
+    *e12 = t12;
+    *e6 = t6;
+    *v_lj = t12 - t6;
+    double flj = (12.0 * t12 - 6.0 * t6) * ir2;
+    double fc, vc;
+    double fq = s->fpre * qq;
+    if (s->coul == OR_RF) {
+        vc = fq * (1.0 / r + s->krf * r2 - s->crf);
+        fc = fq * (1.0 / (r2 * r) - 2.0 * s->krf);
+    } else {
+        double br = s->beta * r;
+        double ec = erfc(br);
+        vc = fq * ec / r;
+        fc = fq * (ec / r + 2.0 * s->beta / sqrt(M_PI) * exp(-br * br)) * ir2;
+    }
+    *v_c = vc;
+    *fr_lj = flj;
+    *fr_c = fc;
+    return flj + fc;
+}
+
+/*
+ * Energies and virial over all unordered pairs.
+ * out[0] = E_LJ, out[1] = E_Coulomb, out[2..10] = virial (row-major 3x3),
+ * out[11] = sum c12/r^12, out[12] = sum c6/r^6,
+ * out[13] = sum over pairs of d.F (LJ part), out[14] = the same for Coulomb.
+ * npairs[0] = number of interacting pairs.
+ */
+int or_energy_virial(int n, const double *x, const double *q, const int *type, const double *box,
+                     double rc, int coul, double eps_r, double eps_rf, double beta, double fcoul,
+                     int ntypes, const double *c6, const double *c12, const int *excl_index,
+                     const int *excl_atoms, double *out, long long *npairs) {
+    if (n < 0 || !out) return 1;
+    setup_t s = make_setup(rc, coul, eps_r, eps_rf, beta, fcoul, ntypes, c6, c12);
+    double elj = 0, ec = 0, e12 = 0, e6 = 0, rf_lj = 0, rf_c = 0;
+    double vxx = 0, vxy = 0, vxz = 0, vyy = 0, vyz = 0, vzz = 0;
+    long long np = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : elj, ec, e12, e6, rf_lj, rf_c, vxx, vxy, vxz, vyy, vyz, vzz, np)
+    for (int i = 0; i < n; ++i) {
+        for (int j = i + 1; j < n; ++j) {
+            double dx = min_image(x[3 * i + 0] - x[3 * j + 0], box[0]);
+            double dy = min_image(x[3 * i + 1] - x[3 * j + 1], box[1]);
+            double dz = min_image(x[3 * i + 2] - x[3 * j + 2], box[2]);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (!(r2 < s.rc2)) continue;
+            if (excluded(i, j, excl_index, excl_atoms)) continue;
+            double vl, vc, a12, a6, fl, fc;
+            double fr = pair_terms(&s, r2, q[i] * q[j], type[i], type[j], &vl, &vc, &a12, &a6, &fl, &fc);
+            elj += vl;
+            ec += vc;
+            e12 += a12;
+            e6 += a6;
+            rf_lj += fl * r2;
+            rf_c += fc * r2;
+            vxx -= 0.5 * fr * dx * dx;
+            vxy -= 0.5 * fr * dx * dy;
+            vxz -= 0.5 * fr * dx * dz;
+            vyy -= 0.5 * fr * dy * dy;
+            vyz -= 0.5 * fr * dy * dz;
+            vzz -= 0.5 * fr * dz * dz;
+            np += 1;
+        }
+    }
+    out[0] = elj;
+    out[1] = ec;
+    out[2] = vxx; out[3] = vxy; out[4] = vxz;
+    out[5] = vxy; out[6] = vyy; out[7] = vyz;
+    out[8] = vxz; out[9] = vyz; out[10] = vzz;
+    out[11] = e12;
+    out[12] = e6;
+    out[13] = rf_lj;
+    out[14] = rf_c;
+    if (npairs) npairs[0] = np;
+    return 0;
+}
+
+/*
+ * Total force on each selected atom: sum over every other atom j of the pair
+ * force (no use of Newton's third law, so every row is independent).
+ * sel == NULL selects all atoms (nsel must then equal n).  f: nsel*3.
+ */
+int or_forces(int n, const double *x, const double *q, const int *type, const double *box,
+              double rc, int coul, double eps_r, double eps_rf, double beta, double fcoul,
+              int ntypes, const double *c6, const double *c12, const int *excl_index,
+              const int *excl_atoms, int nsel, const int *sel, double *f) {
+    if (n < 0 || nsel < 0 || !f) return 1;
+    if (!sel && nsel != n) return 1;
+    setup_t s = make_setup(rc, coul, eps_r, eps_rf, beta, fcoul, ntypes, c6, c12);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int k = 0; k < nsel; ++k) {
+        int i = sel ? sel[k] : k;
+        double fx = 0, fy = 0, fz = 0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = min_image(x[3 * i + 0] - x[3 * j + 0], box[0]);
+            double dy = min_image(x[3 * i + 1] - x[3 * j + 1], box[1]);
+            double dz = min_image(x[3 * i + 2] - x[3 * j + 2], box[2]);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (!(r2 < s.rc2)) continue;
+            if (excluded(i, j, excl_index, excl_atoms)) continue;
+            double vl, vc, a12, a6, fl, fc;
+            double fr = pair_terms(&s, r2, q[i] * q[j], type[i], type[j], &vl, &vc, &a12, &a6, &fl, &fc);
+            fx += fr * dx;
+            fy += fr * dy;
+            fz += fr * dz;
+        }
+        f[3 * k + 0] = fx;
+        f[3 * k + 1] = fy;
+        f[3 * k + 2] = fz;
+    }
+    return 0;
+}
+
+/*
+ * The set of interacting pairs: every unordered pair i < j, not excluded,
+ * with minimum-image r^2 < r_cut^2 (evaluated in double precision).
+ * counts: n entries (pairs whose lower index is i).  If pairs != NULL it
+ * receives 2 ints per pair (i, j), ordered by i then j, and must hold the
+ * total given by a previous count-only call.  Returns the total, or -1.
+ */
+long long or_pairs(int n, const double *x, const double *box, double r_cut, const int *excl_index,
+                   const int *excl_atoms, long long *counts, int *pairs) {
+    if (n < 0 || !counts) return -1;
+    double rc2 = r_cut * r_cut;
+    if (!pairs) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int i = 0; i < n; ++i) {
+            long long c = 0;
+            for (int j = i + 1; j < n; ++j) {
+                double dx = min_image(x[3 * i + 0] - x[3 * j + 0], box[0]);
+                double dy = min_image(x[3 * i + 1] - x[3 * j + 1], box[1]);
+                double dz = min_image(x[3 * i + 2] - x[3 * j + 2], box[2]);
+                if (!(dx * dx + dy * dy + dz * dz < rc2)) continue;
+                if (excluded(i, j, excl_index, excl_atoms)) continue;
+                ++c;
+            }
+            counts[i] = c;
+        }
+    }
+    long long total = 0;
+    for (int i = 0; i < n; ++i) total += counts[i];
+    if (!pairs) return total;
+    long long *start = (long long *)malloc(sizeof(long long) * (size_t)(n + 1));
+    if (!start) return -1;
+    start[0] = 0;
+    for (int i = 0; i < n; ++i) start[i + 1] = start[i] + counts[i];
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < n; ++i) {
+        long long w = start[i];
+        for (int j = i + 1; j < n; ++j) {
+            double dx = min_image(x[3 * i + 0] - x[3 * j + 0], box[0]);
+            double dy = min_image(x[3 * i + 1] - x[3 * j + 1], box[1]);
+            double dz = min_image(x[3 * i + 2] - x[3 * j + 2], box[2]);
+            if (!(dx * dx + dy * dy + dz * dz < rc2)) continue;
+            if (excluded(i, j, excl_index, excl_atoms)) continue;
+            pairs[2 * w + 0] = i;
+            pairs[2 * w + 1] = j;
+            ++w;
+        }
+    }
+    free(start);
+    return total;
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
