@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark of the short-range non-bonded hot path on GB300.
+
+Default workload (one step = one pass of the whole hot path):
+  24,000-atom water box (8,000 three-site waters, L = 6.21 nm), Lennard-Jones
+  + reaction-field, rc = 1.0 nm, rlist = 1.1 nm.  A step is grid put + pair
+  search + masks + prune, then 10 force evaluations on the same list, the
+  last 9 after Gaussian moves (sigma = 0.005 nm per coordinate per
+  evaluation, cumulative); the 10th also computes energies and the virial.
+Metric: useful non-bonded pair interactions per second (atom pairs inside
+rc, not excluded, counted by the kernel) over the whole step.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                    [--workload mid|large]
+
+--impl reference times the FP64 oracle (the CPU baseline) on the same
+workload.  Under torchrun (N > 1) every rank evaluates an independent replica
+on its own GPU ("replicas only": the path has no cross-GPU exchange); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1506_00716_gb300 import waterbox as wb  # noqa: E402
+
+METRIC = "nonbonded pair interactions/s"
+UNIT = "pairs/s"
+EVALS_PER_STEP = 10
+SIGMA = 0.005
+# FP32 flops per evaluated atom-pair slot in the force kernel's pair code
+# (FADD/FMUL = 1, FFMA = 2), by (coulomb, virial); see the design doc.
+FLOPS_PER_SLOT = {("rf", False): 30, ("rf", True): 42, ("ewald", False): 56, ("ewald", True): 68}
+# kernels launched per timed stage (nb_ctx_timing)
+KERNELS_PER_STAGE = {"grid": 6, "search": 1, "prune": 1, "coord": 1, "zero": 1, "forces": 1, "final": 2,
+                     "energy": 1}
+FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self) -> dict:
+        rows = [r for r in csv.reader(io.StringIO(getattr(self, "out", ""))) if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]
+                          and "Not" not in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- ours
+
+class MidWorkload:
+    """24,000-atom box; step = rebuild + 10 evaluations with Gaussian moves."""
+
+    name = "mid"
+
+    def __init__(self, torch, dev, seed: int = 2):
+        self.torch = torch
+        self.sys = wb.mid_box(seed=seed)
+        self.params = wb.params_rf()
+        self.coul = "rf"
+        s = self.sys
+        rng = np.random.default_rng(1000 + seed)
+        frames = [s.x.astype(np.float64)]
+        for _ in range(EVALS_PER_STEP - 1):
+            frames.append(frames[-1] + rng.normal(0.0, SIGMA, size=s.x.shape))
+        self.frames_host = [np.ascontiguousarray(f.astype(np.float32)) for f in frames]
+        self.xq_host = np.ascontiguousarray(s.xq())
+        self.type_host = np.ascontiguousarray(s.type)
+        self.xq = torch.from_numpy(self.xq_host).to(dev)
+        self.type = torch.from_numpy(self.type_host).to(dev)
+        self.frames = [torch.from_numpy(f).to(dev) for f in self.frames_host]
+        self.config = {
+            "workload": "water box, 24,000 atoms (8,000 rigid 3-site waters), L=6.21 nm, LJ + "
+                        "reaction-field (eps_rf=78), rc=1.0 nm, rlist=1.1 nm; step = grid put + "
+                        "pair search + prune + 10 force evaluations (energies and virial on the "
+                        "10th), Gaussian moves (sigma 0.005 nm) between evaluations",
+            "atoms": s.n, "evals_per_step": EVALS_PER_STEP, "coulomb": "reaction-field",
+            "l2": "flushed before every timed step (512 MB write)",
+        }
+
+
+def run_ours(args) -> dict:
+    import torch
+
+    from paper_1506_00716_gb300 import build as nbbuild
+    from paper_1506_00716_gb300 import nb
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nbbuild.build()
+    stream = torch.cuda.Stream(device=dev)
+    flush_buf = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    wl = MidWorkload(torch, dev)
+    s = wl.sys
+    all_flags = nb.NB_F_ENERGY | nb.NB_F_VIRIAL
+    flags_of = [0] * (EVALS_PER_STEP - 1) + [all_flags]
+    ctx = nb.nb_ctx_create(local, stream.cuda_stream, 0)
+    h = nb.nb_sys_create(ctx, wl.params, s.n, s.box)
+    nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
+    f_dev = torch.empty((s.n, 3), dtype=torch.float32, device=dev)
+    e_dev = torch.empty(2, dtype=torch.float64, device=dev)
+    v_dev = torch.empty(9, dtype=torch.float64, device=dev)
+
+    def step(xq, ty, frames, f, e, v):
+        nb.nb_grid_put(h, xq, ty)
+        nb.nb_pairlist_build(h)
+        for k in range(EVALS_PER_STEP):
+            nb.nb_forces(h, None if k == 0 else frames[k], f, e, v, flags_of[k])
+
+    # interacting pairs of every evaluation of one step, counted by the energy
+    # kernel in an untimed pass over the same inputs (the counts are exact)
+    with torch.cuda.stream(stream):
+        nb.nb_grid_put(h, wl.xq, wl.type)
+        nb.nb_pairlist_build(h)
+        pairs_per_step = 0
+        for k in range(EVALS_PER_STEP):
+            nb.nb_forces(h, None if k == 0 else wl.frames[k], f_dev, e_dev, v_dev, all_flags)
+            pairs_per_step += nb.nb_eval_info(h)["n_pairs"]
+        info = nb.nb_pairlist_info(h)
+
+    def flush():
+        with torch.cuda.stream(stream):
+            flush_buf.fill_(1.0)
+
+    # warm-up
+    for _ in range(args.warmup):
+        flush()
+        with torch.cuda.stream(stream):
+            step(wl.xq, wl.type, wl.frames, f_dev, e_dev, v_dev)
+    stream.synchronize()
+    nb.nb_ctx_timing(ctx, reset=True)
+    nb.nb_ctx_set_timing(ctx, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush()
+            with torch.cuda.stream(stream):
+                ev[k][0].record(stream)
+                step(wl.xq, wl.type, wl.frames, f_dev, e_dev, v_dev)
+                ev[k][1].record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall
+    nb.nb_ctx_set_timing(ctx, False)
+    stage = nb.nb_ctx_timing(ctx, reset=True)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([dev_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = float(t.item())
+    total_pairs = pairs_per_step * args.steps * world
+    value = total_pairs / (dev_ms * 1e-3)
+
+    # roofline of the force kernel (9 launches without and 1 with virial per step)
+    f_ms, f_n = stage["forces"]
+    avg_ms = f_ms / max(f_n, 1)
+    slots = info["n_slots"]
+    fps = ((EVALS_PER_STEP - 1) * FLOPS_PER_SLOT[(wl.coul, False)] + FLOPS_PER_SLOT[(wl.coul, True)]) \
+        / EVALS_PER_STEP
+    flops = fps * slots
+    props = torch.cuda.get_device_properties(dev)
+    peaks, peak_kind = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops / (avg_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
+                "traffic": _traffic_per_launch("forces_rf_mid"),
+                "kernel": "k_forces<RF> (9 of 10 launches without, 1 with virial)",
+                "peak_kind": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({peak_kind} clock)",
+                "avg_launch_ms": round(avg_ms, 5), "slots_per_launch": slots,
+                "flops_per_slot": fps}
+    launches = sum(n * KERNELS_PER_STAGE[name] for name, (_, n) in stage.items())
+
+    # end to end through the C ABI with host buffers
+    e2e = _e2e(torch, nb, h, wl, stream, flags_of, pairs_per_step, args, flush)
+
+    nb.nb_sys_destroy(h)
+    nb.nb_ctx_destroy(ctx)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {**wl.config, "parallelism": f"replicas{world}",
+                   "pairs_per_step": pairs_per_step, "list_entries": info["n_entries"],
+                   "list_entries_raw": info["n_entries_raw"], "wall_s": round(t_wall, 4)},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
+        "stages_ms_per_step": {k: round(v[0] / args.steps, 5) for k, v in stage.items()},
+        "clocks": clk.summary(),
+    }
+    if world > 1:
+        dist.barrier()
+    return out
+
+
+def _traffic_per_launch(key: str):
+    """DRAM bytes per launch from the committed ncu summary, if its kernel source still matches."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh).get(key)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1506_00716_gb300", "csrc", "nb_kernel.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec.get("bytes") if rec.get("source_sha") == sha else None
+
+
+def _e2e(torch, nb, h, wl, stream, flags_of, pairs_per_step, args, flush):
+    s = wl.sys
+    xq = torch.from_numpy(wl.xq_host).pin_memory()
+    ty = torch.from_numpy(wl.type_host).pin_memory()
+    frames = [torch.from_numpy(f).pin_memory() for f in wl.frames_host]
+    f = torch.empty((s.n, 3), dtype=torch.float32).pin_memory()
+    e = torch.empty(2, dtype=torch.float64).pin_memory()
+    v = torch.empty(9, dtype=torch.float64).pin_memory()
+
+    def step():
+        nb.nb_grid_put(h, xq, ty)
+        nb.nb_pairlist_build(h)
+        for k in range(EVALS_PER_STEP):
+            nb.nb_forces(h, None if k == 0 else frames[k], f, e, v, flags_of[k])
+        stream.synchronize()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush()
+            step()
+        tot = 0.0
+        for _ in range(args.steps):
+            flush()
+            stream.synchronize()
+            t0 = time.perf_counter()
+            step()
+            tot += time.perf_counter() - t0
+    n = s.n
+    h2d = 16 * n + 4 * n + (EVALS_PER_STEP - 1) * 12 * n
+    d2h = EVALS_PER_STEP * (12 * n + 16 + 72)
+    return {"value": pairs_per_step * args.steps / tot, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * tot / args.steps}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def _oracle_eval(oracle, s, p):
+    ev = oracle.energy_virial(s, p)
+    oracle.forces(s, p)
+    return ev["npairs"]
+
+
+def cpu_baseline(min_seconds: float = 10.0) -> dict:
+    """The FP64 oracle as it stands, on this host's cores, over whole evaluations of the box."""
+    import oracle
+
+    s = wb.mid_box(seed=2)
+    p = wb.params_rf()
+    oracle.build()
+    n_eval, pairs, t0 = 0, 0, time.perf_counter()
+    while True:
+        pairs += _oracle_eval(oracle, s, p)
+        n_eval += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    return {"value": pairs / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n_eval} full O(N^2) evaluations (energy/virial pass + per-atom force pass) "
+                      f"of the 24,000-atom box, {el:.1f} s"}
+
+
+def run_reference(args) -> dict | None:
+    world, rank, _ = _dist()
+    if rank != 0:
+        return None
+    import oracle
+
+    oracle.build()
+    s = wb.mid_box(seed=2)
+    p = wb.params_rf()
+    for _ in range(args.warmup):
+        _oracle_eval(oracle, s, p)
+    pairs, t0 = 0, time.perf_counter()
+    for _ in range(args.steps):
+        pairs += _oracle_eval(oracle, s, p)
+    el = time.perf_counter() - t0
+    value = pairs / el
+    cores = oracle.num_threads()
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": "water box, 24,000 atoms, LJ + reaction-field, rc=1.0 nm; one step = "
+                               "one full FP64 oracle evaluation", "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full evaluations of the 24,000-atom box"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        out = run_reference(args)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    out = run_ours(args)
+    world, rank, _ = _dist()
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

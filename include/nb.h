@@ -1,0 +1,277 @@
+/*
+ * nb.h -- C ABI of the GB300 short-range non-bonded library.
+ *
+ * The library evaluates the short-range non-bonded forces, energies and
+ * virial of periodic particle systems with the cluster-pair scheme of
+ * Pall et al. (arXiv:1506.00716, Section 3.2 "SIMD parallelism"):
+ *   - particles are put on a grid of x-y columns and sorted along z inside
+ *     each column, and every column is cut into clusters of exactly M = 8
+ *     particles (nb_grid_put);
+ *   - a buffered list of cluster pairs (bounding-box distance < rlist, with
+ *     rlist > rc) is built once and reused over many force evaluations, with
+ *     per-pair interaction masks, then pruned to the pairs that have at least
+ *     one particle pair inside rlist (nb_pairlist_build; Section 3.2 and the
+ *     "Heterogeneous parallelization" part of Section 3.2.1, where the list
+ *     is pruned on the GPU and reused for many steps);
+ *   - a cluster-pair kernel computes M x N interactions per list entry
+ *     (nb_forces; Section 3.2).
+ * All work runs on one CUDA device; there is no CPU fallback.
+ *
+ * Units: nm, kJ/mol, elementary charge.  Boxes are rectangular (periodic in
+ * x, y and z) and every edge must be at least 2 * rlist.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an nb_status; none aborts.  NB_OK is 0.  A failing
+ *     call leaves a message for nb_last_error() in thread-local storage.
+ *   - Buffers are owned by the caller.  A pointer argument described as
+ *     "host or device" is read or written through cudaMemcpyAsync on the
+ *     context's stream, so both kinds work; calls that return results into
+ *     host memory synchronise the stream before returning.  Device pointers
+ *     must stay valid until the stream has passed the call.
+ *   - All device work of a context is ordered on the CUDA stream given to
+ *     nb_ctx_create (NULL = the legacy default stream).
+ *   - Handles are not thread-safe: one host thread at a time per context.
+ */
+#ifndef NB_H
+#define NB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nb_ctx nb_ctx;
+typedef struct nb_sys nb_sys;
+typedef struct nb_batch nb_batch;
+
+typedef enum {
+    NB_OK = 0,
+    NB_ERR_ARG = 1,      /* invalid argument (NULL handle, bad size or flag) */
+    NB_ERR_BOX = 2,      /* a box edge is shorter than 2 * rlist */
+    NB_ERR_OOM = 3,      /* a device allocation failed */
+    NB_ERR_BUDGET = 4,   /* the context's HBM budget would be exceeded */
+    NB_ERR_CUDA = 5,     /* a CUDA runtime call or kernel launch failed */
+    NB_ERR_NOT_READY = 6,/* the batch ticket has not completed yet */
+    NB_ERR_TIMEOUT = 7,  /* a bounded wait ran out */
+    NB_ERR_STATE = 8,    /* call out of order, e.g. nb_forces before a list exists */
+    NB_ERR_CAPACITY = 9  /* a fixed device capacity was exceeded (reported, no overrun) */
+} nb_status;
+
+enum { NB_COUL_RF = 0, NB_COUL_EWALD = 1 };
+
+/* Flags of nb_forces, nb_batch_submit. */
+enum {
+    NB_F_ENERGY = 1u,  /* compute E_LJ and E_Coulomb */
+    NB_F_VIRIAL = 2u   /* compute the 3x3 virial */
+};
+
+/*
+ * Interaction parameters (Section 3.2: van der Waals and electrostatics
+ * inside a spherical cut-off, with a list buffer rlist > rc).
+ *   rc          interaction cut-off (nm); a pair interacts iff r^2 < rc^2
+ *   rlist       list radius (nm), rlist >= rc
+ *   coul        NB_COUL_RF: reaction field, V = f qi qj / eps_r
+ *                 (1/r + k_rf r^2 - c_rf), k_rf = (eps_rf - eps_r) /
+ *                 ((2 eps_rf + eps_r) rc^3), c_rf = 1/rc + k_rf rc^2
+ *                 (eps_rf = 0 means infinity: k_rf = 1/(2 rc^3));
+ *               NB_COUL_EWALD: Ewald real space, V = f qi qj / eps_r
+ *                 erfc(beta r) / r
+ *   fcoul       electric conversion factor f = 1/(4 pi eps_0), 138.935458
+ *   ntypes      number of Lennard-Jones types, 1..64
+ *   c6, c12     host arrays of ntypes*ntypes floats, row-major [ti*ntypes+tj],
+ *               V_LJ = c12/r^12 - c6/r^6; copied during nb_sys_create
+ * Excluded pairs contribute nothing; neither the reaction-field nor the
+ * Ewald exclusion correction is applied.
+ */
+typedef struct {
+    double rc, rlist;
+    int coul;
+    double eps_r, eps_rf, ewald_beta, fcoul;
+    int ntypes;
+    const float *c6, *c12;
+} nb_params;
+
+/* Counts of the current pair list (nb_pairlist_info). */
+typedef struct {
+    long long n_clusters;    /* clusters of M = 8 slots, fillers included */
+    long long n_items;       /* (i-cluster, periodic shift) work items */
+    long long n_entries;     /* cluster-pair entries after pruning */
+    long long n_entries_raw; /* entries that passed the bounding-box test */
+    long long n_slots;       /* M*N atom-pair slots the kernel evaluates */
+} nb_list_info;
+
+/* Result counts of the last evaluation (nb_eval_info). */
+typedef struct {
+    long long n_pairs;  /* atom pairs inside rc, not excluded, counted by the kernel
+                           (float32 distance test); set by evaluations with NB_F_ENERGY */
+} nb_eval_stats;
+
+/* Stages timed by nb_ctx_timing. */
+enum {
+    NB_STAGE_GRID = 0,    /* nb_grid_put kernels */
+    NB_STAGE_SEARCH = 1,  /* cluster-pair search */
+    NB_STAGE_PRUNE = 2,   /* list prune */
+    NB_STAGE_COORD = 3,   /* coordinate update of nb_forces(x_new) */
+    NB_STAGE_ZERO = 4,    /* force-buffer clear */
+    NB_STAGE_FORCES = 5,  /* the cluster-pair force kernel */
+    NB_STAGE_FINAL = 6,   /* unsort + FP64 energy/virial finalisation */
+    NB_STAGE_ENERGY = 7,  /* the double-float energy kernel (NB_F_ENERGY) */
+    NB_NSTAGE = 8
+};
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *nb_last_error(void);
+
+/*
+ * Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (NULL = legacy default stream).  `hbm_budget_bytes` caps the device memory
+ * the context's systems and batches may hold (0 = no cap); requests over the
+ * cap fail with NB_ERR_BUDGET and allocate nothing.
+ */
+nb_status nb_ctx_create(int device, void *cuda_stream, size_t hbm_budget_bytes, nb_ctx **out);
+nb_status nb_ctx_destroy(nb_ctx *ctx);
+/*
+ * Per-stage device timing: when enabled, every stage launched by the context
+ * is bracketed by CUDA events on the context's stream.  nb_ctx_timing
+ * synchronises the stream and returns, per NB_STAGE_*, the summed elapsed
+ * milliseconds and the number of timed launches since the last reset
+ * (ms and launches: NB_NSTAGE entries, either may be NULL); reset != 0
+ * clears the totals.
+ */
+nb_status nb_ctx_set_timing(nb_ctx *ctx, int enable);
+nb_status nb_ctx_timing(nb_ctx *ctx, double *ms, long long *launches, int reset);
+/* Device bytes currently held by the context's systems and batches. */
+nb_status nb_ctx_memory(nb_ctx *ctx, size_t *bytes_in_use, size_t *budget);
+/* Device bytes nb_sys_create would reserve for a system of natoms atoms. */
+nb_status nb_sys_footprint(const nb_params *params, int natoms, const double box[3], size_t *bytes);
+
+/*
+ * Create a system of `natoms` atoms in a rectangular box box[0..2] (nm).
+ * The device uses float(box[k]); pass float-representable values to make
+ * host and device see the same box.  Fails with NB_ERR_BOX if any edge is
+ * below 2 * rlist, NB_ERR_BUDGET / NB_ERR_OOM if the memory is not there.
+ */
+nb_status nb_sys_create(nb_ctx *ctx, const nb_params *params, int natoms, const double box[3],
+                        nb_sys **out);
+nb_status nb_sys_destroy(nb_sys *sys);
+
+/*
+ * Exclusions as a CSR over atoms in the caller's order: the partners of
+ * atom a are excl_atoms[excl_index[a] .. excl_index[a+1]-1].  A pair is
+ * excluded if either atom lists the other (the list is symmetrised here).
+ * Host pointers.  Excluded pairs do not interact.  Takes effect at the next
+ * nb_pairlist_build.
+ */
+nb_status nb_set_exclusions(nb_sys *sys, const int *excl_index, const int *excl_atoms);
+
+/*
+ * Grid put (Section 3.2): take coordinates and charges xq (natoms * 4 floats,
+ * x y z q, caller's order; host or device) and Lennard-Jones types (natoms
+ * ints in [0, ntypes); host or device), wrap the coordinates into the box,
+ * bin atoms into x-y columns, sort each column along z (ties by atom index)
+ * and cut it into clusters of 8, padding with non-interacting fillers, and
+ * compute each cluster's bounding box.  Invalidates the pair list.
+ */
+nb_status nb_grid_put(nb_sys *sys, const float *xq, const int *type);
+
+/*
+ * Build the buffered cluster-pair list (Section 3.2): every pair of
+ * clusters whose bounding boxes come closer than rlist under some periodic
+ * image, kept once per unordered pair (half list), with an 8x8 interaction
+ * mask that removes excluded pairs, fillers and the lower triangle of
+ * self-pairs; then prune entries with no atom pair inside rlist.  Needs a
+ * preceding nb_grid_put.  Synchronises the stream to check the list
+ * capacity, and grows it and rebuilds if needed.
+ */
+nb_status nb_pairlist_build(nb_sys *sys);
+nb_status nb_pairlist_info(nb_sys *sys, nb_list_info *info);
+
+/*
+ * Evaluate forces (and, per flags, energies and virial) with the current
+ * list (Section 3.2 cluster-pair kernel).
+ *   x_new   NULL: use the coordinates of the last nb_grid_put; otherwise
+ *           natoms * 3 floats (host or device), the new positions in the
+ *           caller's order.  They must be continuous with those of the last
+ *           nb_grid_put (no re-wrapping into the box between list builds),
+ *           and the list stays valid while every atom has moved less than
+ *           (rlist - rc) / 2.
+ *   f       natoms * 3 floats (host or device), the force on each atom in the
+ *           caller's order (overwritten); NULL skips the copy-out.
+ *   energy  2 doubles (host or device): E_LJ, E_Coulomb; NULL allowed.
+ *   virial  9 doubles (host or device): Xi = -1/2 sum_pairs d (x) F,
+ *           row-major; NULL allowed.
+ *   flags   NB_F_ENERGY | NB_F_VIRIAL; energy / virial must be non-NULL when
+ *           their flag is set.
+ * Forces and virial: float32 pair arithmetic and per-atom accumulation, the
+ * virial summed over the system in float64.  Energies (NB_F_ENERGY, an extra
+ * kernel): double-float pair arithmetic on the float32 pipes, summed in
+ * float64.  Cut-off decisions are exact for the float32 inputs.
+ */
+nb_status nb_forces(nb_sys *sys, const float *x_new, float *f, double *energy, double *virial,
+                    unsigned flags);
+
+/* Counts of the last evaluation of this system (synchronises the stream). */
+nb_status nb_eval_info(nb_sys *sys, nb_eval_stats *stats);
+
+/*
+ * Test hook: copy the current list to host memory.  Any output pointer may
+ * be NULL.  Sizes come from nb_pairlist_info.
+ *   perm        n_clusters * 8 ints: original atom index of each sorted slot,
+ *               -1 for fillers
+ *   items       n_items * 4 ints: (i-cluster, first entry, end entry, shift)
+ *               where shift = (sx+1)*9 + (sy+1)*3 + (sz+1), the i-cluster
+ *               being displaced by (sx Lx, sy Ly, sz Lz)
+ *   cj          n_entries_total ints, j-cluster of each entry (indices up to
+ *               the largest item end)
+ *   mask        n_entries_total unsigned long long: bit 8*i + t set means the
+ *               pair (i-slot i, j-slot t XOR i) may interact
+ *   n_entries_total  receives the size of the entry arrays
+ */
+nb_status nb_pairlist_export(nb_sys *sys, int *perm, int *items, int *cj,
+                             unsigned long long *mask, long long *n_entries_total);
+
+/*
+ * Batched evaluation of many independent systems (the paper's ensemble
+ * simulations, Section 3.3): one launch per stage covers every system, the
+ * force stage is one persistent kernel over a flattened worklist of all
+ * systems' cluster pairs, and the whole sequence is captured once in a CUDA
+ * graph and replayed.
+ *
+ * nb_batch_create: the systems must share one context and equal parameters;
+ * each needs a preceding nb_sys_set_coords (or nb_grid_put).  The batch
+ * holds its own list buffers (counted against the budget).
+ */
+nb_status nb_batch_create(nb_ctx *ctx, nb_sys *const *systems, int n, nb_batch **out);
+nb_status nb_batch_destroy(nb_batch *batch);
+/*
+ * Stage new coordinates for one system without running anything: xq is
+ * natoms * 4 floats and type natoms ints (host or device).  The next batch
+ * submission grids, lists and evaluates from them.
+ */
+nb_status nb_sys_set_coords(nb_sys *sys, const float *xq, const int *type);
+/*
+ * Launch grid put, list build, prune and force evaluation for every system
+ * of the batch (flags as nb_forces).  Returns at once; *ticket identifies
+ * the submission.
+ */
+nb_status nb_batch_submit(nb_batch *batch, unsigned flags, unsigned long long *ticket);
+/*
+ * Wait up to timeout_us microseconds (0 = just test) for a submission.
+ * *done = 1 once it has finished.  Returns NB_ERR_TIMEOUT if it has not
+ * finished in time, NB_ERR_CAPACITY if a list outgrew its buffer (the batch
+ * then grows its buffers; submit again).
+ */
+nb_status nb_batch_poll(nb_batch *batch, unsigned long long ticket, long long timeout_us, int *done);
+/*
+ * Copy one system's results of the last completed submission: f (natoms*3
+ * floats), energy (2 doubles), virial (9 doubles); host or device; NULL
+ * skips.
+ */
+nb_status nb_sys_results(nb_sys *sys, float *f, double *energy, double *virial);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NB_H */

@@ -1,0 +1,965 @@
+// nb_api.cu -- the C ABI (include/nb.h): contexts, systems, plans and the
+// batch engine.  Host code only; every arithmetic step of the method runs in
+// the kernels of nb_grid.cu, nb_search.cu and nb_kernel.cu.
+//
+// A "plan" is a set of systems evaluated by one sequence of launches: a
+// standalone system owns a plan of one, a batch owns a plan over all of its
+// systems.  Each system owns its per-atom, per-slot and per-cluster device
+// buffers; a plan owns the cluster-pair list (work items, entries, masks)
+// and the device descriptor array the kernels index by system.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "nb_internal.cuh"
+
+using namespace nbgb;
+
+namespace {
+
+thread_local std::string g_err;
+
+nb_status fail(nb_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+nb_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(NB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define NB_CK(call)                                        \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Geometry {
+    int ncx, ncy, ncol, clcap;
+    float cw[2], icw[2];
+};
+
+Geometry make_geometry(int natoms, const double box[3]) {
+    Geometry g;
+    double vol = box[0] * box[1] * box[2];
+    double rho = natoms / vol;
+    double side = std::cbrt((double)CL / rho);
+    g.ncx = std::max(1, (int)std::floor(box[0] / side));
+    g.ncy = std::max(1, (int)std::floor(box[1] / side));
+    g.ncol = g.ncx * g.ncy;
+    g.clcap = (natoms + CL - 1) / CL + g.ncol;
+    g.cw[0] = (float)(box[0] / g.ncx);
+    g.cw[1] = (float)(box[1] / g.ncy);
+    g.icw[0] = (float)(g.ncx / box[0]);
+    g.icw[1] = (float)(g.ncy / box[1]);
+    return g;
+}
+
+// Expected list sizes (half list, before pruning) for capacity planning.
+void list_estimate(const nb_params& p, int natoms, const double box[3], int clcap, long long* items,
+                   long long* entries) {
+    double vol = box[0] * box[1] * box[2];
+    double rho = natoms / vol;
+    double ext = std::cbrt((double)CL / rho);
+    double s = 2.0 * ext, r = p.rlist;
+    double steiner = s * s * s + 6.0 * s * s * r + 3.0 * M_PI * s * r * r + 4.0 / 3.0 * M_PI * r * r * r;
+    double per_cl = steiner * rho / CL / 2.0;
+    double shift = 1.0;
+    for (int d = 0; d < 3; ++d) shift *= 1.0 + 2.0 * std::min(1.0, (r + ext) / box[d]);
+    *items = (long long)(clcap * std::min(27.0, shift * 1.25)) + 256;
+    *entries = (long long)(clcap * (per_cl * 1.35 + 8.0) * std::max(1.0, shift / 4.0)) + 4096;
+}
+
+}  // namespace
+
+struct Plan;
+
+struct TimedLaunch {
+    int stage;
+    cudaEvent_t a, b;
+};
+
+struct nb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;
+    size_t in_use = 0;
+    int num_sms = 0;
+    bool timing = false;
+    bool capturing = false;
+    std::vector<TimedLaunch> pending;
+    std::vector<cudaEvent_t> pool;
+    double tot_ms[NB_NSTAGE] = {0};
+    long long launches[NB_NSTAGE] = {0};
+};
+
+struct nb_sys {
+    nb_ctx* ctx = nullptr;
+    nb_params p{};
+    std::vector<float> c6, c12;
+    int natoms = 0;
+    double box[3] = {0, 0, 0};
+    Geometry geo{};
+    SysDev h{};              // descriptor (device pointers)
+    void* block = nullptr;   // one allocation holding all per-system buffers
+    size_t bytes = 0;
+    int* d_excl = nullptr;   // exclusion CSR (index then atoms)
+    size_t excl_bytes = 0;
+    float2* d_lj = nullptr;
+    Plan* plan = nullptr;    // standalone plan (lazy)
+    bool has_coords = false;
+    bool gridded = false;
+    bool listed = false;
+};
+
+struct Plan {
+    nb_ctx* ctx = nullptr;
+    std::vector<nb_sys*> systems;
+    SysDev* d_sys = nullptr;
+    int* d_off = nullptr;     // atom, col, cl prefix arrays (3 * (nsys + 1))
+    ListDev list{};
+    void* list_block = nullptr;
+    size_t list_bytes = 0;
+    size_t fixed_bytes = 0;
+    int tot_atoms = 0, tot_cols = 0, tot_clcap = 0;
+    long long item_cap = 0, entry_cap = 0;
+    int* h_counters = nullptr;  // pinned readback
+    KParams kp{};
+    // graph state (batches)
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t done_ev = nullptr;
+    unsigned long long ticket = 0;
+    unsigned long long done_ticket = 0;
+};
+
+struct nb_batch {
+    nb_ctx* ctx = nullptr;
+    Plan* plan = nullptr;
+};
+
+namespace {
+
+cudaEvent_t pool_event(nb_ctx* c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one stage with CUDA events on the context's stream when timing is on.
+struct StageScope {
+    nb_ctx* c;
+    int stage;
+    cudaEvent_t a = nullptr;
+    StageScope(nb_ctx* ctx, int st) : c(ctx), stage(st) {
+        if (c->timing && !c->capturing) {
+            a = pool_event(c);
+            if (a) cudaEventRecord(a, c->stream);
+        }
+    }
+    ~StageScope() {
+        if (!a) return;
+        cudaEvent_t b = pool_event(c);
+        if (!b) return;
+        cudaEventRecord(b, c->stream);
+        c->pending.push_back({stage, a, b});
+    }
+};
+
+nb_status ctx_reserve(nb_ctx* ctx, size_t bytes) {
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+        return fail(NB_ERR_BUDGET, "HBM budget exceeded: " + std::to_string(ctx->in_use) + " + " +
+                                       std::to_string(bytes) + " > " + std::to_string(ctx->budget));
+    return NB_OK;
+}
+
+nb_status dev_alloc(nb_ctx* ctx, void** ptr, size_t bytes) {
+    nb_status s = ctx_reserve(ctx, bytes);
+    if (s != NB_OK) return s;
+    cudaError_t e = cudaMallocAsync(ptr, bytes, ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NB_ERR_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+    }
+    ctx->in_use += bytes;
+    return NB_OK;
+}
+
+void dev_free(nb_ctx* ctx, void* ptr, size_t bytes) {
+    if (!ptr) return;
+    cudaFreeAsync(ptr, ctx->stream);
+    ctx->in_use -= std::min(ctx->in_use, bytes);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Per-system buffer layout inside one allocation.
+size_t sys_layout(int natoms, const Geometry& g, int ntypes, SysDev* h, char* base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* p = base ? base + off : nullptr;
+        off += align256(bytes);
+        return p;
+    };
+    size_t n = (size_t)natoms, S = (size_t)g.clcap * CL;
+    char* xq_in = take(16 * n);
+    char* type_in = take(4 * n);
+    char* x_new = take(12 * n);
+    char* atom_col = take(4 * n);
+    char* atom_slot = take(4 * n);
+    char* iperm = take(4 * n);
+    char* f_out = take(12 * n);
+    char* keys = take(8 * S);
+    char* xq_s = take(16 * S);
+    char* type_s = take(4 * S);
+    char* perm = take(4 * S);
+    char* wrapk = take(4 * S);
+    char* f_s = take(16 * S);
+    char* bb = take(32 * (size_t)g.clcap);
+    char* col_count = take(4 * (size_t)g.ncol);
+    char* col_cl0 = take(4 * ((size_t)g.ncol + 1));
+    char* acc = take(8 * NACC);
+    char* res = take(8 * NRES);
+    char* lj = take(8 * (size_t)ntypes * ntypes);
+    (void)lj;
+    if (h) {
+        h->xq_in = (float4*)xq_in;
+        h->type_in = (int*)type_in;
+        h->x_new = (float*)x_new;
+        h->atom_col = (int*)atom_col;
+        h->atom_slot = (int*)atom_slot;
+        h->iperm = (int*)iperm;
+        h->f_out = (float*)f_out;
+        h->keys = (unsigned long long*)keys;
+        h->xq_s = (float4*)xq_s;
+        h->type_s = (int*)type_s;
+        h->perm = (int*)perm;
+        h->wrapk = (int*)wrapk;
+        h->f_s = (float4*)f_s;
+        h->bb = (float4*)bb;
+        h->col_count = (int*)col_count;
+        h->col_cl0 = (int*)col_cl0;
+        h->acc = (double*)acc;
+        h->res = (double*)res;
+    }
+    return off;
+}
+
+float2* sys_lj_ptr(nb_sys* s) {
+    size_t total = sys_layout(s->natoms, s->geo, s->p.ntypes, nullptr, nullptr);
+    size_t lj = align256(8 * (size_t)s->p.ntypes * s->p.ntypes);
+    return (float2*)((char*)s->block + total - lj);
+}
+
+KParams make_kparams(const nb_sys* s) {
+    KParams k{};
+    const nb_params& p = s->p;
+    double maxL = std::max(s->box[0], std::max(s->box[1], s->box[2]));
+    double pad = 1e-5 * (1.0 + maxL);
+    k.rc2_d = p.rc * p.rc;
+    k.rc2 = (float)(p.rc * p.rc);
+    k.rc2_lo = (float)(p.rc * p.rc * (1.0 - 2e-5));
+    k.rc2_hi = (float)(p.rc * p.rc * (1.0 + 2e-5));
+    k.rl_search = (float)(p.rlist + pad);
+    k.rl2_prune = (float)((p.rlist + pad) * (p.rlist + pad));
+    k.fq = (float)(p.fcoul / p.eps_r);
+    double krf = p.eps_rf == 0.0 ? 1.0 / (2.0 * p.rc * p.rc * p.rc)
+                                 : (p.eps_rf - p.eps_r) / ((2.0 * p.eps_rf + p.eps_r) * p.rc * p.rc * p.rc);
+    k.krf = (float)krf;
+    k.two_krf = (float)(2.0 * krf);
+    k.crf = (float)(1.0 / p.rc + krf * p.rc * p.rc);
+    k.beta = (float)p.ewald_beta;
+    double crf = 1.0 / p.rc + krf * p.rc * p.rc;
+    double fq = p.fcoul / p.eps_r;
+    double mb = -p.ewald_beta * p.ewald_beta * 1.4426950408889634;
+    k.krf_h = (float)krf;
+    k.krf_l = (float)(krf - (double)k.krf_h);
+    k.crf_h = (float)crf;
+    k.crf_l = (float)(crf - (double)k.crf_h);
+    k.fq_h = (float)fq;
+    k.fq_l = (float)(fq - (double)k.fq_h);
+    k.mb2l2e_h = (float)mb;
+    k.mb2l2e_l = (float)(mb - (double)k.mb2l2e_h);
+    k.max_entries = 32;
+    k.coul = p.coul;
+    k.ntypes = p.ntypes;
+    k.lj = s->d_lj;
+    return k;
+}
+
+bool same_params(const nb_sys* a, const nb_sys* b) {
+    const nb_params &p = a->p, &q = b->p;
+    return p.rc == q.rc && p.rlist == q.rlist && p.coul == q.coul && p.eps_r == q.eps_r &&
+           p.eps_rf == q.eps_rf && p.ewald_beta == q.ewald_beta && p.fcoul == q.fcoul &&
+           p.ntypes == q.ntypes && a->c6 == b->c6 && a->c12 == b->c12;
+}
+
+void plan_free_list(Plan* pl) {
+    if (pl->list_block) dev_free(pl->ctx, pl->list_block, pl->list_bytes);
+    pl->list_block = nullptr;
+    pl->list_bytes = 0;
+}
+
+void plan_drop_graphs(Plan* pl) {
+    for (auto& g : pl->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+nb_status plan_alloc_list(Plan* pl, long long items, long long entries) {
+    plan_free_list(pl);
+    items = std::min<long long>(items, (1ll << 31) - 1);
+    entries = std::min<long long>(entries, (1ll << 31) - 1);
+    size_t bytes = align256(16 * (size_t)items) + align256(4 * (size_t)entries) +
+                   align256(8 * (size_t)entries) + align256(4 * CNT_N);
+    void* blk = nullptr;
+    nb_status s = dev_alloc(pl->ctx, &blk, bytes);
+    if (s != NB_OK) return s;
+    char* b = (char*)blk;
+    pl->list.items = (int4*)b;
+    b += align256(16 * (size_t)items);
+    pl->list.cj = (int*)b;
+    b += align256(4 * (size_t)entries);
+    pl->list.mask = (unsigned long long*)b;
+    b += align256(8 * (size_t)entries);
+    pl->list.counters = (int*)b;
+    pl->list.item_cap = (int)items;
+    pl->list.entry_cap = (int)entries;
+    pl->item_cap = items;
+    pl->entry_cap = entries;
+    pl->list_block = blk;
+    pl->list_bytes = bytes;
+    NB_CK(cudaMemsetAsync(pl->list.counters, 0, 4 * CNT_N, pl->ctx->stream));
+    plan_drop_graphs(pl);
+    return NB_OK;
+}
+
+void plan_destroy(Plan* pl) {
+    if (!pl) return;
+    plan_drop_graphs(pl);
+    plan_free_list(pl);
+    if (pl->d_sys) dev_free(pl->ctx, pl->d_sys, pl->fixed_bytes);
+    if (pl->h_counters) cudaFreeHost(pl->h_counters);
+    if (pl->done_ev) cudaEventDestroy(pl->done_ev);
+    delete pl;
+}
+
+nb_status plan_create(nb_ctx* ctx, nb_sys* const* systems, int n, Plan** out) {
+    Plan* pl = new Plan();
+    pl->ctx = ctx;
+    pl->systems.assign(systems, systems + n);
+    std::vector<SysDev> hs(n);
+    std::vector<int> off(3 * (n + 1), 0);
+    long long items = 0, entries = 0;
+    for (int k = 0; k < n; ++k) {
+        nb_sys* s = systems[k];
+        hs[k] = s->h;
+        off[k + 1] = off[k] + s->natoms;
+        off[(n + 1) + k + 1] = off[(n + 1) + k] + s->geo.ncol;
+        off[2 * (n + 1) + k + 1] = off[2 * (n + 1) + k] + s->geo.clcap;
+        long long it, en;
+        list_estimate(s->p, s->natoms, s->box, s->geo.clcap, &it, &en);
+        items += it;
+        entries += en;
+    }
+    pl->tot_atoms = off[n];
+    pl->tot_cols = off[(n + 1) + n];
+    pl->tot_clcap = off[2 * (n + 1) + n];
+    size_t fixed = align256(sizeof(SysDev) * n) + align256(4 * off.size());
+    void* blk = nullptr;
+    nb_status st = dev_alloc(ctx, &blk, fixed);
+    if (st != NB_OK) { delete pl; return st; }
+    pl->fixed_bytes = fixed;
+    pl->d_sys = (SysDev*)blk;
+    pl->d_off = (int*)((char*)blk + align256(sizeof(SysDev) * n));
+    cudaError_t e = cudaMemcpyAsync(pl->d_sys, hs.data(), sizeof(SysDev) * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pl->d_off, off.data(), 4 * off.size(), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMallocHost(&pl->h_counters, 4 * CNT_N);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->done_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        plan_destroy(pl);
+        return cuda_fail(e, "plan_create");
+    }
+    // the memcpys above read host vectors that go out of scope
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) { plan_destroy(pl); return cuda_fail(e, "plan_create sync"); }
+    st = plan_alloc_list(pl, items, entries);
+    if (st != NB_OK) { plan_destroy(pl); return st; }
+    pl->kp = make_kparams(systems[0]);
+    *out = pl;
+    return NB_OK;
+}
+
+PlanLaunch launch_of(const Plan* pl) {
+    PlanLaunch p{};
+    int n = (int)pl->systems.size();
+    p.nsys = n;
+    p.d_sys = pl->d_sys;
+    p.d_atom_off = pl->d_off;
+    p.d_col_off = pl->d_off + (n + 1);
+    p.d_cl_off = pl->d_off + 2 * (n + 1);
+    p.tot_atoms = pl->tot_atoms;
+    p.tot_cols = pl->tot_cols;
+    p.tot_clcap = pl->tot_clcap;
+    p.list = pl->list;
+    p.kp = pl->kp;
+    p.num_sms = pl->ctx->num_sms;
+    return p;
+}
+
+// Copy one system's inputs into its device buffers.
+nb_status stage_coords(nb_sys* s, const float* xq, const int* type) {
+    if (!xq || !type) return fail(NB_ERR_ARG, "xq and type must be non-NULL");
+    cudaStream_t st = s->ctx->stream;
+    NB_CK(cudaMemcpyAsync(s->h.xq_in, xq, 16 * (size_t)s->natoms, cudaMemcpyDefault, st));
+    NB_CK(cudaMemcpyAsync(s->h.type_in, type, 4 * (size_t)s->natoms, cudaMemcpyDefault, st));
+    s->has_coords = true;
+    return NB_OK;
+}
+
+// Search + prune with capacity growth.  Synchronises the stream.
+nb_status plan_build_list(Plan* pl) {
+    cudaStream_t st = pl->ctx->stream;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        NB_CK(cudaMemsetAsync(pl->list.counters + CNT_ITEMS, 0, 4 * 2, st));
+        NB_CK(cudaMemsetAsync(pl->list.counters + CNT_PRUNED, 0, 4, st));
+        PlanLaunch p = launch_of(pl);
+        {
+            StageScope sc(pl->ctx, NB_STAGE_SEARCH);
+            NB_CK(launch_search(p, st));
+        }
+        NB_CK(cudaMemcpyAsync(pl->h_counters, pl->list.counters, 4 * CNT_N, cudaMemcpyDeviceToHost, st));
+        NB_CK(cudaStreamSynchronize(st));
+        int ov = pl->h_counters[CNT_OVERFLOW];
+        if (ov & 3) {
+            long long ni = std::max<long long>(pl->h_counters[CNT_ITEMS], pl->item_cap);
+            long long ne = std::max<long long>(pl->h_counters[CNT_ENTRIES], pl->entry_cap);
+            NB_CK(cudaMemsetAsync(pl->list.counters + CNT_OVERFLOW, 0, 4, st));
+            nb_status s = plan_alloc_list(pl, ni + ni / 4 + 256, ne + ne / 4 + 4096);
+            if (s != NB_OK) return s;
+            continue;
+        }
+        {
+            StageScope sc(pl->ctx, NB_STAGE_PRUNE);
+            NB_CK(launch_prune(p, st));
+        }
+        return NB_OK;
+    }
+    return fail(NB_ERR_CAPACITY, "pair list did not fit after growing its buffers");
+}
+
+nb_status plan_eval(Plan* pl, unsigned flags) {
+    cudaStream_t st = pl->ctx->stream;
+    PlanLaunch p = launch_of(pl);
+    {
+        StageScope sc(pl->ctx, NB_STAGE_ZERO);
+        NB_CK(launch_zero_forces(p, st));
+    }
+    {
+        StageScope sc(pl->ctx, NB_STAGE_FORCES);
+        NB_CK(launch_forces(p, flags, st));
+    }
+    if (flags & NB_F_ENERGY) {
+        StageScope sc(pl->ctx, NB_STAGE_ENERGY);
+        NB_CK(launch_energy(p, st));
+    }
+    {
+        StageScope sc(pl->ctx, NB_STAGE_FINAL);
+        NB_CK(launch_finalize(p, flags, st));
+    }
+    return NB_OK;
+}
+
+nb_status copy_out(nb_sys* s, float* f, double* energy, double* virial, unsigned flags, bool* need_sync) {
+    cudaStream_t st = s->ctx->stream;
+    bool host = false;
+    if (f) {
+        NB_CK(cudaMemcpyAsync(f, s->h.f_out, 12 * (size_t)s->natoms, cudaMemcpyDefault, st));
+        host = host || !is_device_ptr(f);
+    }
+    if (energy && (flags & NB_F_ENERGY)) {
+        NB_CK(cudaMemcpyAsync(energy, s->h.res, 16, cudaMemcpyDefault, st));
+        host = host || !is_device_ptr(energy);
+    }
+    if (virial && (flags & NB_F_VIRIAL)) {
+        NB_CK(cudaMemcpyAsync(virial, s->h.res + 2, 72, cudaMemcpyDefault, st));
+        host = host || !is_device_ptr(virial);
+    }
+    *need_sync = host;
+    return NB_OK;
+}
+
+nb_status check_params(const nb_params* p) {
+    if (!p) return fail(NB_ERR_ARG, "params is NULL");
+    if (!(p->rc > 0) || !(p->rlist >= p->rc)) return fail(NB_ERR_ARG, "need 0 < rc <= rlist");
+    if (p->coul != NB_COUL_RF && p->coul != NB_COUL_EWALD) return fail(NB_ERR_ARG, "unknown coul");
+    if (!(p->eps_r > 0)) return fail(NB_ERR_ARG, "eps_r must be > 0");
+    if (p->coul == NB_COUL_EWALD && !(p->ewald_beta > 0)) return fail(NB_ERR_ARG, "ewald_beta must be > 0");
+    if (p->ntypes < 1 || p->ntypes > MAX_TYPES) return fail(NB_ERR_ARG, "ntypes must be in 1..64");
+    if (!p->c6 || !p->c12) return fail(NB_ERR_ARG, "c6 / c12 are NULL");
+    return NB_OK;
+}
+
+nb_status check_box(const nb_params* p, const double box[3]) {
+    if (!box) return fail(NB_ERR_ARG, "box is NULL");
+    for (int d = 0; d < 3; ++d) {
+        if (!(box[d] > 0) || !std::isfinite(box[d])) return fail(NB_ERR_ARG, "box edges must be positive");
+        if ((float)box[d] < (float)(2.0 * p->rlist))
+            return fail(NB_ERR_BOX, "box edge shorter than 2 * rlist");
+    }
+    return NB_OK;
+}
+
+size_t plan_bytes_estimate(const nb_params* p, int natoms, const double box[3], const Geometry& g) {
+    long long it, en;
+    list_estimate(*p, natoms, box, g.clcap, &it, &en);
+    return align256(16 * (size_t)it) + align256(12 * (size_t)en) + 4096;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nb_last_error(void) { return g_err.c_str(); }
+
+nb_status nb_ctx_create(int device, void* cuda_stream, size_t hbm_budget_bytes, nb_ctx** out) {
+    if (!out) return fail(NB_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(NB_ERR_ARG, "no such CUDA device");
+    NB_CK(cudaSetDevice(device));
+    nb_ctx* c = new nb_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->budget = hbm_budget_bytes;
+    e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaDeviceGetAttribute"); }
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        unsigned long long thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = c;
+    return NB_OK;
+}
+
+nb_status nb_ctx_destroy(nb_ctx* ctx) {
+    if (!ctx) return fail(NB_ERR_ARG, "ctx is NULL");
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& t : ctx->pending) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (auto e : ctx->pool) cudaEventDestroy(e);
+    delete ctx;
+    return NB_OK;
+}
+
+nb_status nb_ctx_set_timing(nb_ctx* ctx, int enable) {
+    if (!ctx) return fail(NB_ERR_ARG, "ctx is NULL");
+    ctx->timing = enable != 0;
+    return NB_OK;
+}
+
+nb_status nb_ctx_timing(nb_ctx* ctx, double* ms, long long* launches, int reset) {
+    if (!ctx) return fail(NB_ERR_ARG, "ctx is NULL");
+    NB_CK(cudaStreamSynchronize(ctx->stream));
+    for (auto& t : ctx->pending) {
+        float el = 0.f;
+        NB_CK(cudaEventElapsedTime(&el, t.a, t.b));
+        ctx->tot_ms[t.stage] += el;
+        ctx->launches[t.stage] += 1;
+        ctx->pool.push_back(t.a);
+        ctx->pool.push_back(t.b);
+    }
+    ctx->pending.clear();
+    for (int k = 0; k < NB_NSTAGE; ++k) {
+        if (ms) ms[k] = ctx->tot_ms[k];
+        if (launches) launches[k] = ctx->launches[k];
+        if (reset) {
+            ctx->tot_ms[k] = 0;
+            ctx->launches[k] = 0;
+        }
+    }
+    return NB_OK;
+}
+
+nb_status nb_ctx_memory(nb_ctx* ctx, size_t* bytes_in_use, size_t* budget) {
+    if (!ctx) return fail(NB_ERR_ARG, "ctx is NULL");
+    if (bytes_in_use) *bytes_in_use = ctx->in_use;
+    if (budget) *budget = ctx->budget;
+    return NB_OK;
+}
+
+nb_status nb_sys_footprint(const nb_params* params, int natoms, const double box[3], size_t* bytes) {
+    nb_status s = check_params(params);
+    if (s != NB_OK) return s;
+    if (natoms <= 0) return fail(NB_ERR_ARG, "natoms must be > 0");
+    s = check_box(params, box);
+    if (s != NB_OK) return s;
+    if (!bytes) return fail(NB_ERR_ARG, "bytes is NULL");
+    Geometry g = make_geometry(natoms, box);
+    *bytes = sys_layout(natoms, g, params->ntypes, nullptr, nullptr) + plan_bytes_estimate(params, natoms, box, g);
+    return NB_OK;
+}
+
+nb_status nb_sys_create(nb_ctx* ctx, const nb_params* params, int natoms, const double box[3], nb_sys** out) {
+    if (!ctx || !out) return fail(NB_ERR_ARG, "ctx / out is NULL");
+    *out = nullptr;
+    nb_status s = check_params(params);
+    if (s != NB_OK) return s;
+    if (natoms <= 0) return fail(NB_ERR_ARG, "natoms must be > 0");
+    s = check_box(params, box);
+    if (s != NB_OK) return s;
+    nb_sys* y = new nb_sys();
+    y->ctx = ctx;
+    y->p = *params;
+    int nt = params->ntypes;
+    y->c6.assign(params->c6, params->c6 + nt * nt);
+    y->c12.assign(params->c12, params->c12 + nt * nt);
+    y->p.c6 = y->c6.data();
+    y->p.c12 = y->c12.data();
+    y->natoms = natoms;
+    for (int d = 0; d < 3; ++d) y->box[d] = box[d];
+    y->geo = make_geometry(natoms, box);
+    size_t bytes = sys_layout(natoms, y->geo, nt, nullptr, nullptr);
+    s = dev_alloc(ctx, &y->block, bytes);
+    if (s != NB_OK) { delete y; return s; }
+    y->bytes = bytes;
+    sys_layout(natoms, y->geo, nt, &y->h, (char*)y->block);
+    y->d_lj = sys_lj_ptr(y);
+    SysDev& h = y->h;
+    for (int d = 0; d < 3; ++d) h.L[d] = (float)box[d];
+    h.cw[0] = y->geo.cw[0];
+    h.cw[1] = y->geo.cw[1];
+    h.icw[0] = y->geo.icw[0];
+    h.icw[1] = y->geo.icw[1];
+    h.ncx = y->geo.ncx;
+    h.ncy = y->geo.ncy;
+    h.ncol = y->geo.ncol;
+    h.natoms = natoms;
+    h.clcap = y->geo.clcap;
+    h.excl_index = nullptr;
+    h.excl_atoms = nullptr;
+    std::vector<float2> lj(nt * nt);
+    for (int k = 0; k < nt * nt; ++k) lj[k] = make_float2(6.0f * y->c6[k], 12.0f * y->c12[k]);
+    cudaError_t e = cudaMemcpyAsync(y->d_lj, lj.data(), 8 * lj.size(), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h.acc, 0, 8 * NACC, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h.res, 0, 8 * NRES, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        dev_free(ctx, y->block, y->bytes);
+        delete y;
+        return cuda_fail(e, "nb_sys_create");
+    }
+    *out = y;
+    return NB_OK;
+}
+
+nb_status nb_sys_destroy(nb_sys* sys) {
+    if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
+    nb_ctx* ctx = sys->ctx;
+    plan_destroy(sys->plan);
+    if (sys->d_excl) dev_free(ctx, sys->d_excl, sys->excl_bytes);
+    dev_free(ctx, sys->block, sys->bytes);
+    delete sys;
+    return NB_OK;
+}
+
+nb_status nb_set_exclusions(nb_sys* sys, const int* excl_index, const int* excl_atoms) {
+    if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
+    if (!excl_index) return fail(NB_ERR_ARG, "excl_index is NULL");
+    int n = sys->natoms;
+    if (excl_index[0] != 0) return fail(NB_ERR_ARG, "excl_index[0] must be 0");
+    std::vector<std::vector<int>> adj(n);
+    for (int a = 0; a < n; ++a) {
+        if (excl_index[a + 1] < excl_index[a]) return fail(NB_ERR_ARG, "excl_index must be non-decreasing");
+        for (int k = excl_index[a]; k < excl_index[a + 1]; ++k) {
+            int b = excl_atoms[k];
+            if (b < 0 || b >= n) return fail(NB_ERR_ARG, "exclusion partner out of range");
+            if (b == a) continue;
+            adj[a].push_back(b);
+            adj[b].push_back(a);
+        }
+    }
+    std::vector<int> idx(n + 1, 0), at;
+    for (int a = 0; a < n; ++a) {
+        auto& v = adj[a];
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        idx[a + 1] = idx[a] + (int)v.size();
+        at.insert(at.end(), v.begin(), v.end());
+    }
+    if (sys->d_excl) dev_free(sys->ctx, sys->d_excl, sys->excl_bytes);
+    sys->d_excl = nullptr;
+    size_t bytes = 4 * (idx.size() + std::max<size_t>(1, at.size()));
+    void* p = nullptr;
+    nb_status s = dev_alloc(sys->ctx, &p, bytes);
+    if (s != NB_OK) return s;
+    sys->d_excl = (int*)p;
+    sys->excl_bytes = bytes;
+    NB_CK(cudaMemcpyAsync(sys->d_excl, idx.data(), 4 * idx.size(), cudaMemcpyHostToDevice, sys->ctx->stream));
+    if (!at.empty())
+        NB_CK(cudaMemcpyAsync(sys->d_excl + idx.size(), at.data(), 4 * at.size(), cudaMemcpyHostToDevice,
+                              sys->ctx->stream));
+    NB_CK(cudaStreamSynchronize(sys->ctx->stream));
+    sys->h.excl_index = sys->d_excl;
+    sys->h.excl_atoms = sys->d_excl + idx.size();
+    // descriptors held by plans are stale now
+    if (sys->plan) { plan_destroy(sys->plan); sys->plan = nullptr; }
+    sys->listed = false;
+    return NB_OK;
+}
+
+static nb_status ensure_plan(nb_sys* sys) {
+    if (sys->plan) return NB_OK;
+    nb_sys* one[1] = {sys};
+    return plan_create(sys->ctx, one, 1, &sys->plan);
+}
+
+nb_status nb_grid_put(nb_sys* sys, const float* xq, const int* type) {
+    if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
+    nb_status s = stage_coords(sys, xq, type);
+    if (s != NB_OK) return s;
+    s = ensure_plan(sys);
+    if (s != NB_OK) return s;
+    cudaStream_t st = sys->ctx->stream;
+    NB_CK(cudaMemsetAsync(sys->plan->list.counters + CNT_OVERFLOW, 0, 4, st));
+    {
+        StageScope sc(sys->ctx, NB_STAGE_GRID);
+        NB_CK(launch_grid_put(launch_of(sys->plan), st));
+    }
+    sys->gridded = true;
+    sys->listed = false;
+    return NB_OK;
+}
+
+nb_status nb_pairlist_build(nb_sys* sys) {
+    if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
+    if (!sys->gridded) return fail(NB_ERR_STATE, "nb_pairlist_build needs a preceding nb_grid_put");
+    nb_status s = plan_build_list(sys->plan);
+    if (s != NB_OK) return s;
+    sys->listed = true;
+    return NB_OK;
+}
+
+nb_status nb_pairlist_info(nb_sys* sys, nb_list_info* info) {
+    if (!sys || !info) return fail(NB_ERR_ARG, "sys / info is NULL");
+    if (!sys->listed) return fail(NB_ERR_STATE, "no pair list");
+    Plan* pl = sys->plan;
+    cudaStream_t st = sys->ctx->stream;
+    int ncl = 0;
+    NB_CK(cudaMemcpyAsync(pl->h_counters, pl->list.counters, 4 * CNT_N, cudaMemcpyDeviceToHost, st));
+    NB_CK(cudaMemcpyAsync(&ncl, sys->h.col_cl0 + sys->geo.ncol, 4, cudaMemcpyDeviceToHost, st));
+    NB_CK(cudaStreamSynchronize(st));
+    info->n_clusters = ncl;
+    info->n_items = pl->h_counters[CNT_ITEMS];
+    info->n_entries_raw = pl->h_counters[CNT_ENTRIES];
+    info->n_entries = pl->h_counters[CNT_PRUNED];
+    info->n_slots = (long long)pl->h_counters[CNT_PRUNED] * CL * CL;
+    return NB_OK;
+}
+
+nb_status nb_eval_info(nb_sys* sys, nb_eval_stats* stats) {
+    if (!sys || !stats) return fail(NB_ERR_ARG, "sys / stats is NULL");
+    double np = 0;
+    NB_CK(cudaMemcpyAsync(&np, sys->h.res + 11, 8, cudaMemcpyDeviceToHost, sys->ctx->stream));
+    NB_CK(cudaStreamSynchronize(sys->ctx->stream));
+    stats->n_pairs = (long long)np;
+    return NB_OK;
+}
+
+nb_status nb_pairlist_export(nb_sys* sys, int* perm, int* items, int* cj, unsigned long long* mask,
+                             long long* n_entries_total) {
+    if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
+    if (!sys->listed) return fail(NB_ERR_STATE, "no pair list");
+    nb_list_info info;
+    nb_status s = nb_pairlist_info(sys, &info);
+    if (s != NB_OK) return s;
+    Plan* pl = sys->plan;
+    cudaStream_t st = sys->ctx->stream;
+    long long ne = std::min<long long>(info.n_entries_raw, pl->entry_cap);
+    if (n_entries_total) *n_entries_total = ne;
+    if (perm) NB_CK(cudaMemcpyAsync(perm, sys->h.perm, 4 * (size_t)info.n_clusters * CL, cudaMemcpyDefault, st));
+    if (items) NB_CK(cudaMemcpyAsync(items, pl->list.items, 16 * (size_t)info.n_items, cudaMemcpyDefault, st));
+    if (cj) NB_CK(cudaMemcpyAsync(cj, pl->list.cj, 4 * (size_t)ne, cudaMemcpyDefault, st));
+    if (mask) NB_CK(cudaMemcpyAsync(mask, pl->list.mask, 8 * (size_t)ne, cudaMemcpyDefault, st));
+    NB_CK(cudaStreamSynchronize(st));
+    return NB_OK;
+}
+
+nb_status nb_forces(nb_sys* sys, const float* x_new, float* f, double* energy, double* virial, unsigned flags) {
+    if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
+    if (flags & ~(unsigned)(NB_F_ENERGY | NB_F_VIRIAL)) return fail(NB_ERR_ARG, "unknown flag bits");
+    if ((flags & NB_F_ENERGY) && !energy) return fail(NB_ERR_ARG, "NB_F_ENERGY needs energy");
+    if ((flags & NB_F_VIRIAL) && !virial) return fail(NB_ERR_ARG, "NB_F_VIRIAL needs virial");
+    if (!sys->listed) return fail(NB_ERR_STATE, "nb_forces needs a pair list (nb_pairlist_build)");
+    Plan* pl = sys->plan;
+    cudaStream_t st = sys->ctx->stream;
+    if (x_new) {
+        NB_CK(cudaMemcpyAsync(sys->h.x_new, x_new, 12 * (size_t)sys->natoms, cudaMemcpyDefault, st));
+        StageScope sc(sys->ctx, NB_STAGE_COORD);
+        NB_CK(launch_coord_update(launch_of(pl), st));
+    }
+    nb_status s = plan_eval(pl, flags);
+    if (s != NB_OK) return s;
+    bool need_sync = false;
+    s = copy_out(sys, f, energy, virial, flags, &need_sync);
+    if (s != NB_OK) return s;
+    if (need_sync) NB_CK(cudaStreamSynchronize(st));
+    return NB_OK;
+}
+
+// ------------------------------------------------------------------ batches
+
+nb_status nb_sys_set_coords(nb_sys* sys, const float* xq, const int* type) {
+    if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
+    nb_status s = stage_coords(sys, xq, type);
+    if (s != NB_OK) return s;
+    sys->gridded = false;
+    sys->listed = false;
+    return NB_OK;
+}
+
+nb_status nb_batch_create(nb_ctx* ctx, nb_sys* const* systems, int n, nb_batch** out) {
+    if (!ctx || !systems || !out || n <= 0) return fail(NB_ERR_ARG, "bad batch arguments");
+    *out = nullptr;
+    for (int k = 0; k < n; ++k) {
+        if (!systems[k] || systems[k]->ctx != ctx) return fail(NB_ERR_ARG, "system from another context");
+        if (!same_params(systems[0], systems[k])) return fail(NB_ERR_ARG, "systems differ in parameters");
+    }
+    nb_batch* b = new nb_batch();
+    b->ctx = ctx;
+    nb_status s = plan_create(ctx, systems, n, &b->plan);
+    if (s != NB_OK) { delete b; return s; }
+    *out = b;
+    return NB_OK;
+}
+
+nb_status nb_batch_destroy(nb_batch* batch) {
+    if (!batch) return fail(NB_ERR_ARG, "batch is NULL");
+    cudaStreamSynchronize(batch->ctx->stream);
+    plan_destroy(batch->plan);
+    delete batch;
+    return NB_OK;
+}
+
+static nb_status batch_record(Plan* pl, unsigned flags) {
+    cudaStream_t st = pl->ctx->stream;
+    PlanLaunch p = launch_of(pl);
+    NB_CK(cudaMemsetAsync(pl->list.counters, 0, 4 * CNT_N, st));
+    NB_CK(launch_grid_put(p, st));
+    NB_CK(launch_search(p, st));
+    NB_CK(launch_prune(p, st));
+    NB_CK(launch_zero_forces(p, st));
+    NB_CK(launch_forces(p, flags, st));
+    if (flags & NB_F_ENERGY) NB_CK(launch_energy(p, st));
+    NB_CK(launch_finalize(p, flags, st));
+    NB_CK(cudaMemcpyAsync(pl->h_counters, pl->list.counters, 4 * CNT_N, cudaMemcpyDeviceToHost, st));
+    return NB_OK;
+}
+
+nb_status nb_batch_submit(nb_batch* batch, unsigned flags, unsigned long long* ticket) {
+    if (!batch || !ticket) return fail(NB_ERR_ARG, "batch / ticket is NULL");
+    if (flags & ~(unsigned)(NB_F_ENERGY | NB_F_VIRIAL)) return fail(NB_ERR_ARG, "unknown flag bits");
+    Plan* pl = batch->plan;
+    for (nb_sys* s : pl->systems)
+        if (!s->has_coords) return fail(NB_ERR_STATE, "a batch system has no coordinates");
+    cudaStream_t st = batch->ctx->stream;
+    cudaGraphExec_t& ge = pl->graph[flags & 3];
+    if (!ge) {
+        if (st == nullptr) {
+            // the legacy default stream cannot be captured: run the launches directly
+            nb_status s = batch_record(pl, flags);
+            if (s != NB_OK) return s;
+        } else {
+            cudaGraph_t g = nullptr;
+            NB_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            batch->ctx->capturing = true;
+            nb_status s = batch_record(pl, flags);
+            batch->ctx->capturing = false;
+            cudaError_t e = cudaStreamEndCapture(st, &g);
+            if (s != NB_OK) { if (g) cudaGraphDestroy(g); return s; }
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { ge = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+        }
+    }
+    if (ge) NB_CK(cudaGraphLaunch(ge, st));
+    NB_CK(cudaEventRecord(pl->done_ev, st));
+    *ticket = ++pl->ticket;
+    for (nb_sys* s : pl->systems) {
+        s->gridded = false;
+        s->listed = false;
+    }
+    return NB_OK;
+}
+
+nb_status nb_batch_poll(nb_batch* batch, unsigned long long ticket, long long timeout_us, int* done) {
+    if (!batch || !done) return fail(NB_ERR_ARG, "batch / done is NULL");
+    Plan* pl = batch->plan;
+    *done = 0;
+    if (ticket == 0 || ticket > pl->ticket) return fail(NB_ERR_ARG, "unknown ticket");
+    if (ticket < pl->ticket || ticket <= pl->done_ticket) {
+        *done = 1;
+        return NB_OK;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(pl->done_ev);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "cudaEventQuery");
+        long long el = std::chrono::duration_cast<std::chrono::microseconds>(
+                           std::chrono::steady_clock::now() - t0).count();
+        if (el >= timeout_us) return fail(NB_ERR_TIMEOUT, "batch not finished within the timeout");
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    pl->done_ticket = ticket;
+    *done = 1;
+    int ov = pl->h_counters[CNT_OVERFLOW];
+    if (ov & 3) {
+        long long ni = std::max<long long>(pl->h_counters[CNT_ITEMS], pl->item_cap);
+        long long ne = std::max<long long>(pl->h_counters[CNT_ENTRIES], pl->entry_cap);
+        nb_status s = plan_alloc_list(pl, ni + ni / 4 + 256, ne + ne / 4 + 4096);
+        if (s != NB_OK) return s;
+        NB_CK(cudaStreamSynchronize(batch->ctx->stream));
+        return fail(NB_ERR_CAPACITY, "batch pair list outgrew its buffer; buffers grown, submit again");
+    }
+    return NB_OK;
+}
+
+nb_status nb_sys_results(nb_sys* sys, float* f, double* energy, double* virial) {
+    if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
+    bool need_sync = false;
+    nb_status s = copy_out(sys, f, energy, virial, (energy ? NB_F_ENERGY : 0) | (virial ? NB_F_VIRIAL : 0),
+                           &need_sync);
+    if (s != NB_OK) return s;
+    if (need_sync) NB_CK(cudaStreamSynchronize(sys->ctx->stream));
+    return NB_OK;
+}
+
+}  // extern "C"

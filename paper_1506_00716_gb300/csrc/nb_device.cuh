@@ -1,0 +1,80 @@
+// nb_device.cuh -- device helpers shared by the force and energy kernels:
+// SFU approximations issued as single PTX instructions, error-free float32
+// transformations (two-sum, two-product) for the compensated ("double-float")
+// energy arithmetic, and the exact cut-off decision.
+#pragma once
+
+#include "nb_internal.cuh"
+
+namespace nbgb {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+__device__ __forceinline__ int find_sys_dev(const int* __restrict__ off, int nsys, int idx) {
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= idx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float rsqrt_sfu(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_sfu(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_sfu(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// s + e = a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// s + e = a + b exactly, valid when |a| >= |b| (Dekker's fast two-sum).
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    e = b - (s - a);
+}
+// p + e = a * b exactly (fused multiply-add residual).
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+// i-atom position displaced by the item's periodic shift, kept as an
+// unevaluated sum hi + lo that equals x_i + S exactly.
+struct ShiftedI {
+    float xh, yh, zh, xl, yl, zl;
+};
+
+__device__ __forceinline__ ShiftedI shift_i(float4 xi, int sh, float Lx, float Ly, float Lz) {
+    ShiftedI s;
+    two_sum(xi.x, (float)(sh / 9 - 1) * Lx, s.xh, s.xl);
+    two_sum(xi.y, (float)((sh / 3) % 3 - 1) * Ly, s.yh, s.yl);
+    two_sum(xi.z, (float)(sh % 3 - 1) * Lz, s.zh, s.zl);
+    return s;
+}
+
+// Exact cut-off decision for a pair near rc: the float64 squared distance of
+// the float32 inputs, summed in the oracle's operation order (no fused
+// multiply-add), so that both sides decide every borderline pair alike.
+__device__ __forceinline__ bool exact_inside(const ShiftedI& xs, float4 xj, double rc2) {
+    const double dx = __dadd_rn(__dadd_rn((double)xs.xh, (double)xs.xl), -(double)xj.x);
+    const double dy = __dadd_rn(__dadd_rn((double)xs.yh, (double)xs.yl), -(double)xj.y);
+    const double dz = __dadd_rn(__dadd_rn((double)xs.zh, (double)xs.zl), -(double)xj.z);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return r2 < rc2;
+}
+
+}  // namespace nbgb

@@ -1,0 +1,264 @@
+// nb_energy.cu -- the energy kernel: Lennard-Jones and Coulomb energies of
+// the cluster-pair list, and the count of interacting pairs.
+//
+// The system energy of a box of neutral molecules is a sum of pair terms that
+// cancel to a few parts in 10^3 - 10^4 (Coulomb), so float32 pair terms
+// (relative error ~1e-7 each) cannot give the energy to 1e-6.  This kernel
+// therefore evaluates each pair in double-float arithmetic on the float32
+// pipes (values carried as unevaluated sums hi + lo of two floats, built
+// from error-free two-sum / two-product steps):
+//   d = x_i + S - x_j and r^2 in double-float, 1/r = y (1 + h/2) with
+//   y = rsqrt(r^2_hi) and the residual h = 1 - r^2 y^2 computed with fused
+//   multiply-adds, and then
+//   RF:    V = f qi qj (1/r + k_rf r^2 - c_rf) fully in double-float;
+//   Ewald: V = f qi qj erfc(b r)/r with erfc(x) = exp(-x^2) R(u) from the
+//          degree-12 fit (head + tail coefficients), exp(-x^2) from the SFU
+//          base-2 exponential of the double-float argument's head times the
+//          first-order factor of its tail;
+//   LJ:    c12 r^-12, c6 r^-6 in float32 from the accurate 1/r.
+// Coulomb energies accumulate in double-float per lane and work item, and in
+// float64 across items and warps.  Cut-off decisions are exact (the float64
+// distance of the float32 inputs decides pairs near rc), so the counted pair
+// set is the oracle's.  The work distribution is the force kernel's: a
+// persistent grid over the (i-cluster, shift) items, four entries in flight
+// per warp, j-clusters staged in shared memory.
+#include "erfc_fit.cuh"
+#include "nb_device.cuh"
+
+namespace nbgb {
+
+namespace {
+
+constexpr unsigned FULL = FULL_MASK;
+constexpr int EW = 8;  // warps per block
+
+__device__ __forceinline__ float erfcx_energy(float x) {
+    x = fminf(x, EF_XMAX);
+    const float d = fmaf(EF_P, x, 1.f);
+    float t = rcp_sfu(d);
+    t = t * fmaf(-d, t, 2.f);  // one Newton step
+    const float u = fmaf(EF_UA, t, EF_UB);
+    float rh = EF_EN_HI[EF_NE - 1], rl = EF_EN_LO[EF_NE - 1];
+#pragma unroll
+    for (int k = EF_NE - 2; k >= 0; --k) {
+        rh = fmaf(rh, u, EF_EN_HI[k]);
+        rl = fmaf(rl, u, EF_EN_LO[k]);
+    }
+    return rh + rl;
+}
+
+template <int COUL>
+__device__ __forceinline__ void pair_energy(const float4 xj, int tj, const ShiftedI& xs, float qih,
+                                            float qil, int tirow, const float2* __restrict__ s_lj,
+                                            bool bit, const KParams& kp, float& ch, float& cl,
+                                            float& e12, float& e6, int& npair) {
+    float dxh, dxe, dyh, dye, dzh, dze;
+    two_sum(xs.xh, -xj.x, dxh, dxe);
+    two_sum(xs.yh, -xj.y, dyh, dye);
+    two_sum(xs.zh, -xj.z, dzh, dze);
+    const float dxl = dxe + xs.xl, dyl = dye + xs.yl, dzl = dze + xs.zl;
+    float px, ex, py, ey, pz, ez;
+    two_prod(dxh, dxh, px, ex);
+    two_prod(dyh, dyh, py, ey);
+    two_prod(dzh, dzh, pz, ez);
+    ex = fmaf(2.f * dxh, dxl, ex);
+    ey = fmaf(2.f * dyh, dyl, ey);
+    ez = fmaf(2.f * dzh, dzl, ez);
+    float s1, e1, r2h, e2;
+    two_sum(px, py, s1, e1);
+    two_sum(s1, pz, r2h, e2);
+    const float r2l = (e1 + e2) + (ex + (ey + ez));
+
+    bool in = bit && r2h < kp.rc2_lo;
+    const bool maybe = bit && !in && r2h < kp.rc2_hi;
+    if (maybe) in = exact_inside(xs, xj, kp.rc2_d);
+    npair += __popc(__ballot_sync(FULL, in));
+
+    // 1/r = y (1 + h/2), h = 1 - r^2 y^2
+    const float y = rsqrt_sfu(r2h);
+    float y2, y2e;
+    two_prod(y, y, y2, y2e);
+    float h = fmaf(-r2h, y2, 1.f);
+    h = fmaf(-r2h, y2e, h);
+    h = fmaf(-r2l, y2, h);
+    const float ril = 0.5f * y * h;
+    const float rif = y + ril;
+
+    const float2 c = s_lj[tirow + tj];
+    const float ri2 = rif * rif;
+    const float ri6 = ri2 * ri2 * ri2;
+    const float t6 = c.x * ri6;
+    const float t12 = c.y * ri6 * ri6;
+    e12 += in ? t12 : 0.f;
+    e6 += in ? t6 : 0.f;
+
+    float qh, qe;
+    two_prod(qih, xj.w, qh, qe);
+    const float ql = fmaf(qil, xj.w, qe);
+    float vh, vl;
+    if (COUL == NB_COUL_RF) {
+        float kh, ke;
+        two_prod(kp.krf_h, r2h, kh, ke);
+        const float kl = fmaf(kp.krf_h, r2l, fmaf(kp.krf_l, r2h, ke));
+        float sh, es, gh, eg;
+        two_sum(y, kh, sh, es);
+        two_sum(sh, -kp.crf_h, gh, eg);
+        const float gl = ((es + eg) + (ril + kl)) - kp.crf_l;
+        float ve;
+        two_prod(qh, gh, vh, ve);
+        vl = fmaf(qh, gl, fmaf(ql, gh, ve));
+    } else {
+        const float r = r2h * rif;
+        const float R = erfcx_energy(kp.beta * r);
+        float ah, ae;
+        two_prod(kp.mb2l2e_h, r2h, ah, ae);
+        const float al = fmaf(kp.mb2l2e_h, r2l, fmaf(kp.mb2l2e_l, r2h, ae));
+        float e = ex2_sfu(ah);
+        e = fmaf(e * 0.69314718055994531f, al, e);
+        const float w = (R * e) * rif;
+        float ve;
+        two_prod(qh, w, vh, ve);
+        vl = fmaf(ql, w, ve);
+    }
+    if (!in) {
+        vh = 0.f;
+        vl = 0.f;
+    }
+    float th, te;
+    two_sum(ch, vh, th, te);
+    ch = th;
+    cl += te + vl;
+}
+
+__device__ __forceinline__ void flush_energy(const SysDev* __restrict__ sys, int s, double& dec,
+                                             double& d12, double& d6, long long& np, int lane) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        dec += __shfl_xor_sync(FULL, dec, off);
+        d12 += __shfl_xor_sync(FULL, d12, off);
+        d6 += __shfl_xor_sync(FULL, d6, off);
+    }
+    if (lane == 0) {
+        atomicAdd(sys[s].acc + ACC_EC, dec);
+        atomicAdd(sys[s].acc + ACC_E12, d12);
+        atomicAdd(sys[s].acc + ACC_E6, d6);
+        atomicAdd(sys[s].acc + ACC_NPAIR, (double)np);
+    }
+    dec = d12 = d6 = 0.0;
+    np = 0;
+}
+
+template <int COUL>
+__global__ void __launch_bounds__(EW * 32)
+k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
+    extern __shared__ float2 s_lj[];
+    __shared__ __align__(16) float4 s_j[EW][4][2 * CL];
+
+    const int lane = threadIdx.x & 31;
+    const int i = lane & 7;
+    const int g = lane >> 3;
+    const int w = threadIdx.x >> 5;
+    const int nt = kp.ntypes;
+    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) s_lj[k] = kp.lj[k];
+    __syncthreads();
+
+    float4* sjg = &s_j[w][g][0];
+    const int nitems = min(list.counters[CNT_ITEMS], list.item_cap);
+    int cur_sys = -1;
+    const float4* xq_s = nullptr;
+    const int* type_s = nullptr;
+    float Lx = 0.f, Ly = 0.f, Lz = 0.f;
+    double dec = 0.0, d12 = 0.0, d6 = 0.0;
+    long long np = 0;
+
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(list.counters + CNT_EWORK, 1);
+        it = __shfl_sync(FULL, it, 0);
+        if (it >= nitems) break;
+        const int4 item = list.items[it];
+        const int sid = item.w >> 5;
+        const int sh = item.w & 31;
+        if (sid != cur_sys) {
+            if (cur_sys >= 0) flush_energy(sys, cur_sys, dec, d12, d6, np, lane);
+            cur_sys = sid;
+            xq_s = sys[sid].xq_s;
+            type_s = sys[sid].type_s;
+            Lx = sys[sid].L[0];
+            Ly = sys[sid].L[1];
+            Lz = sys[sid].L[2];
+        }
+        const int ci = item.x, jb = item.y, je = item.z;
+        if (jb >= je) continue;
+        const float4 xi4 = xq_s[ci * CL + i];
+        const ShiftedI xs = shift_i(xi4, sh, Lx, Ly, Lz);
+        float qih, qie;
+        two_prod(kp.fq_h, xi4.w, qih, qie);
+        const float qil = fmaf(kp.fq_l, xi4.w, qie);
+        const int tirow = type_s[ci * CL + i] * nt;
+
+        float ch = 0.f, cl = 0.f, e12 = 0.f, e6 = 0.f;
+        int npair = 0;
+
+        int e = jb + g;
+        bool act = e < je;
+        unsigned long long pm = 0ull;
+        float4 pxq = make_float4(0.f, 0.f, 0.f, 0.f);
+        int pty = 0;
+        if (act) {
+            const int cjn = list.cj[e];
+            pm = list.mask[e];
+            pxq = xq_s[cjn * CL + i];
+            pty = type_s[cjn * CL + i];
+        }
+        for (int base = jb; base < je; base += 4) {
+            __syncwarp();
+            sjg[i] = pxq;
+            sjg[CL + i] = make_float4(__int_as_float(pty), 0.f, 0.f, 0.f);
+            const unsigned long long cm = pm;
+            e = base + 4 + g;
+            act = e < je;
+            pm = 0ull;
+            if (act) {
+                const int cjn = list.cj[e];
+                pm = list.mask[e];
+                pxq = xq_s[cjn * CL + i];
+                pty = type_s[cjn * CL + i];
+            }
+            __syncwarp();
+            const unsigned row = (unsigned)(cm >> (8 * i)) & 0xffu;
+#pragma unroll
+            for (int t = 0; t < CL; ++t) {
+                const int js = t ^ i;
+                pair_energy<COUL>(sjg[js], __float_as_int(sjg[CL + js].x), xs, qih, qil, tirow, s_lj,
+                                  (row >> t) & 1u, kp, ch, cl, e12, e6, npair);
+            }
+        }
+        dec += (double)ch + (double)cl;
+        d12 += (double)e12;
+        d6 += (double)e6;
+        if (lane == 0) np += npair;
+    }
+    if (cur_sys >= 0) flush_energy(sys, cur_sys, dec, d12, d6, np, lane);
+}
+
+template <int COUL>
+cudaError_t launch_energy_t(const PlanLaunch& p, cudaStream_t st) {
+    size_t smem = (size_t)p.kp.ntypes * p.kp.ntypes * sizeof(float2);
+    auto kern = k_energy<COUL>;
+    int per_sm = 0;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, EW * 32, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) per_sm = 1;
+    kern<<<p.num_sms * per_sm, EW * 32, smem, st>>>(p.d_sys, p.list, p.kp);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_energy(const PlanLaunch& p, cudaStream_t st) {
+    if (p.kp.coul == NB_COUL_RF) return launch_energy_t<NB_COUL_RF>(p, st);
+    return launch_energy_t<NB_COUL_EWALD>(p, st);
+}
+
+}  // namespace nbgb

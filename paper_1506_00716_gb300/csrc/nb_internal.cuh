@@ -1,0 +1,132 @@
+// nb_internal.cuh -- device data layout and kernel launch interfaces shared by
+// the library's translation units.  Not part of the public ABI (include/nb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nb.h"
+
+namespace nbgb {
+
+// Cluster size: every i- and j-cluster holds exactly CL atom slots
+// (Section 3.2: "clusters, each containing exactly M particles"; here
+// M = N = 8 so that one 8-lane group of a warp covers one cluster).
+constexpr int CL = 8;
+constexpr int MAX_TYPES = 64;
+constexpr int COL_MAX = 4096;      // atoms per column sorted in shared memory
+constexpr int NSHIFT = 27;         // periodic images (sx, sy, sz) in {-1,0,1}^3
+constexpr int SHIFT_ZERO = 13;     // index of the zero shift
+constexpr int SEARCH_BUF = 384;    // entries a search warp buffers before flushing
+constexpr int EXCL_BUF = 128;      // exclusion partners a search warp caches
+
+// Counter slots of a list (ListDev::counters).
+enum {
+    CNT_ITEMS = 0,      // work items written (may exceed capacity: then overflow)
+    CNT_ENTRIES = 1,    // raw entries written by the search
+    CNT_OVERFLOW = 2,   // bit 0: items, bit 1: entries
+    CNT_WORK = 3,       // persistent-kernel work counter
+    CNT_PRUNED = 4,     // entries kept by the prune
+    CNT_EWORK = 5,      // energy-kernel work counter
+    CNT_N = 8
+};
+
+// Per-system device descriptor.  Every pointer is a device pointer owned by
+// the system (nb_sys).  "slot" arrays have clcap * CL elements in the sorted
+// (grid) order; "atom" arrays have natoms elements in the caller's order.
+struct SysDev {
+    float L[3];          // box edges
+    float cw[2];         // column widths in x, y
+    float icw[2];        // 1 / column width
+    int ncx, ncy, ncol;  // grid columns
+    int natoms;
+    int clcap;           // cluster capacity = ceil(natoms / CL) + ncol
+    // inputs, caller's order
+    float4* xq_in;       // [natoms] x y z q
+    int* type_in;        // [natoms]
+    float* x_new;        // [natoms * 3] staged coordinates for nb_forces(x_new)
+    // grid
+    int* col_count;      // [ncol] atoms per column
+    int* col_cl0;        // [ncol + 1] first cluster of each column; [ncol] = #clusters
+    int* atom_col;       // [natoms]
+    int* atom_slot;      // [natoms] arrival slot inside the column (pre-sort)
+    unsigned long long* keys;  // [slots] (z key << 32 | atom) in column order
+    float4* xq_s;        // [slots] sorted x y z q (fillers: far away, q = 0)
+    int* type_s;         // [slots]
+    int* perm;           // [slots] original atom of each slot, -1 = filler
+    int* iperm;          // [natoms] slot of each atom
+    int* wrapk;          // [slots] box multiples added by wrapping (3 x int8 packed)
+    float4* bb;          // [clcap * 2] cluster bounding boxes: lo (w = #real), hi
+    // exclusions: symmetric CSR in the caller's order (may be empty)
+    const int* excl_index;  // [natoms + 1] or nullptr
+    const int* excl_atoms;
+    // outputs
+    float4* f_s;         // [slots] forces in sorted order (w unused)
+    float* f_out;        // [natoms * 3] forces in the caller's order
+    double* acc;         // [NACC] FP64 energy/virial accumulators
+    double* res;         // [NRES] E_LJ, E_C, virial row-major, pair count
+};
+
+// Accumulator layout of SysDev::acc.
+enum { ACC_E12 = 0, ACC_E6 = 1, ACC_EC = 2, ACC_VXX = 3, ACC_VYY = 4, ACC_VZZ = 5,
+       ACC_VXY = 6, ACC_VXZ = 7, ACC_VYZ = 8, ACC_NPAIR = 9, ACC_ECLO = 10, NACC = 11 };
+constexpr int NRES = 12;  // SysDev::res: E_LJ, E_C, virial[9], interacting pairs
+
+// Per-plan (one system, or one batch of systems) cluster-pair list.
+struct ListDev {
+    int4* items;         // (ci, first entry, end entry, sys << 5 | shift)
+    int* cj;             // j-cluster per entry
+    unsigned long long* mask;  // 8x8 interaction bits per entry (rotated layout)
+    int* counters;       // [CNT_N]
+    int item_cap;
+    int entry_cap;
+};
+
+// Interaction constants (identical for all systems of a plan).
+struct KParams {
+    double rc2_d;        // cut-off^2 in float64 (exact decisions near rc)
+    float rc2;           // cut-off^2
+    float rc2_lo, rc2_hi;  // band around rc^2 decided exactly
+    float rl_search;     // list radius used by the bounding-box test (padded)
+    float rl2_prune;     // list radius^2 used by the prune (padded)
+    float fq;            // fcoul / eps_r
+    float krf, two_krf, crf;
+    float beta;          // Ewald splitting parameter
+    // double-float (hi + lo) constants of the energy kernel
+    float krf_h, krf_l, crf_h, crf_l, fq_h, fq_l;
+    float mb2l2e_h, mb2l2e_l;  // -beta^2 log2(e)
+    int coul;
+    int ntypes;
+    int max_entries;     // list entries per work item (items are split beyond)
+    const float2* lj;    // [ntypes^2] (6 c6, 12 c12)
+};
+
+// Host-side view of a plan, used to size launches.
+struct PlanLaunch {
+    int nsys;
+    const SysDev* d_sys;     // [nsys]
+    const int* d_atom_off;   // [nsys + 1] prefix of natoms
+    const int* d_col_off;    // [nsys + 1] prefix of ncol
+    const int* d_cl_off;     // [nsys + 1] prefix of clcap
+    int tot_atoms, tot_cols, tot_clcap;
+    ListDev list;
+    KParams kp;
+    int num_sms;
+};
+
+// Shift index <-> vector.
+__host__ __device__ inline int shift_index(int sx, int sy, int sz) {
+    return (sx + 1) * 9 + (sy + 1) * 3 + (sz + 1);
+}
+
+// Kernel launchers (each returns the launch status).
+cudaError_t launch_grid_put(const PlanLaunch& p, cudaStream_t st);
+cudaError_t launch_search(const PlanLaunch& p, cudaStream_t st);
+cudaError_t launch_prune(const PlanLaunch& p, cudaStream_t st);
+cudaError_t launch_zero_forces(const PlanLaunch& p, cudaStream_t st);
+cudaError_t launch_coord_update(const PlanLaunch& p, cudaStream_t st);
+cudaError_t launch_forces(const PlanLaunch& p, unsigned flags, cudaStream_t st);
+cudaError_t launch_energy(const PlanLaunch& p, cudaStream_t st);
+cudaError_t launch_finalize(const PlanLaunch& p, unsigned flags, cudaStream_t st);
+
+}  // namespace nbgb

@@ -1,0 +1,426 @@
+// nb_kernel.cu -- the cluster-pair force kernel and the per-evaluation
+// stages around it (clear, coordinate update, unsort, finalisation).
+//
+// Cluster-pair kernel (Section 3.2): the M = 8 atoms of the i-cluster stay
+// in registers while the list entries stream past; every entry's j-cluster
+// (N = 8 atoms) is staged in shared memory and its M x N pairs are computed
+// without further global loads.  Warp mapping on sm_103a: lane = 8 g + i,
+// i = i-slot, g = one of four entries in flight.  Lane i visits the j-slots
+// in the order t XOR i (t = 0..7), so the eight j-force partial sums it
+// keeps are already arranged for a three-step transposed butterfly that
+// leaves the full force of j-slot i in lane i (21 shuffles per 64 pairs, no
+// selects).  j-forces then go to memory with one float4 atomic per atom and
+// entry; i-forces are reduced over the four groups at the end of the item.
+// A persistent grid pulls (i-cluster, shift) work items from a global
+// counter, so one launch covers every system of a batch.
+//
+// Per pair (float32): d = x_i + S - x_j with x_i + S carried error-free as
+// hi + lo, r^2, interaction iff mask bit and r^2 < rc^2, 1/r by the SFU
+// reciprocal square root,
+//   LJ:    F/r = (12 c12 r^-12 - 6 c6 r^-6) / r^2
+//   RF:    F/r = f qi qj (r^-3 - 2 k_rf)
+//   Ewald: F/r = f qi qj (erfc(b r)/r + 2b/sqrt(pi) exp(-b^2 r^2)) / r^2
+// with erfc(x) = exp(-x^2) R(u) from the degree-8 least-squares fit of
+// erfc_fit.cuh (relative error 2e-8).  Optional virial
+// Xi = -1/2 sum_pairs (F/r) d (x) d, summed per pair in float32 and across
+// items in float64.
+//
+// Cut-off decisions are exact: with reaction field (whose force steps at
+// rc), pairs whose float32 r^2 lies within a relative 2e-5 of rc^2 are left
+// out of the main pass and decided on a rare path from the float64 distance
+// of the float32 inputs, the same decision the float64 oracle takes.
+#include "erfc_fit.cuh"
+#include "nb_device.cuh"
+
+namespace nbgb {
+
+namespace {
+
+constexpr unsigned FULL = FULL_MASK;
+constexpr int FW = 8;  // warps per block of the force kernel
+
+struct EwaldC {
+    float beta, mb2_log2e, c2;  // beta, -beta^2 log2(e), 2 beta / sqrt(pi)
+};
+
+// erfc(x) exp(x^2) from the force fit.
+__device__ __forceinline__ float erfcx_force(float x) {
+    x = fminf(x, EF_XMAX);
+    const float t = rcp_sfu(fmaf(EF_P, x, 1.f));
+    const float u = fmaf(EF_UA, t, EF_UB);
+    float r = EF_FORCE[EF_NF - 1];
+#pragma unroll
+    for (int k = EF_NF - 2; k >= 0; --k) r = fmaf(r, u, EF_FORCE[k]);
+    return r;
+}
+
+// Force of one pair slot: d, r^2 and the decision `in` are given.
+template <int COUL, bool VIR>
+__device__ __forceinline__ void pair_force(float dx, float dy, float dz, float r2, bool in, float qi,
+                                           float qj, float2 c, const KParams& kp, const EwaldC& ew,
+                                           float& fix, float& fiy, float& fiz, float& fjx,
+                                           float& fjy, float& fjz, float (&v)[6]) {
+    float rinv = rsqrt_sfu(r2);
+    rinv = in ? rinv : 0.f;
+    const float qq = in ? qi * qj : 0.f;
+    const float rinv2 = rinv * rinv;
+    const float rinv6 = rinv2 * rinv2 * rinv2;
+    const float t6 = c.x * rinv6;
+    const float t12 = c.y * rinv6 * rinv6;
+    float fr;  // F/r
+    if (COUL == NB_COUL_RF) {
+        const float fc = qq * fmaf(rinv, rinv2, -kp.two_krf);
+        fr = fmaf(t12 - t6, rinv2, fc);
+    } else {
+        const float r = r2 * rinv;
+        const float ex = ex2_sfu(r2 * ew.mb2_log2e);
+        const float erfcv = erfcx_force(ew.beta * r) * ex;
+        fr = (fmaf(qq * ew.c2, ex, qq * erfcv * rinv) + t12 - t6) * rinv2;
+    }
+    const float fx = fr * dx, fy = fr * dy, fz = fr * dz;
+    fix += fx; fiy += fy; fiz += fz;
+    fjx -= fx; fjy -= fy; fjz -= fz;
+    if (VIR) {
+        v[0] = fmaf(fx, dx, v[0]);
+        v[1] = fmaf(fy, dy, v[1]);
+        v[2] = fmaf(fz, dz, v[2]);
+        v[3] = fmaf(fx, dy, v[3]);
+        v[4] = fmaf(fx, dz, v[4]);
+        v[5] = fmaf(fy, dz, v[5]);
+    }
+}
+
+// The M x N = 8 x 8 pairs of one entry for one lane (i-slot i): slot t pairs
+// i with j-slot t XOR i.  With EXACT, pairs within the band around rc^2 are
+// left out and reported in `band` (bit t).
+template <int COUL, bool VIR, bool MASKED, bool SHIFTED, bool EXACT>
+__device__ __forceinline__ void pair_block(const float4* __restrict__ sj, int i, const ShiftedI& xs,
+                                           float qi, int tirow, const float2* __restrict__ s_lj,
+                                           unsigned row, const KParams& kp, const EwaldC& ew,
+                                           float& fix, float& fiy, float& fiz, float (&fj)[CL][3],
+                                           float (&v)[6], unsigned& band) {
+#pragma unroll
+    for (int t = 0; t < CL; ++t) {
+        const int js = t ^ i;
+        const float4 xj = sj[js];
+        const int tj = __float_as_int(sj[CL + js].x);
+        float dx = xs.xh - xj.x;
+        float dy = xs.yh - xj.y;
+        float dz = xs.zh - xj.z;
+        if (SHIFTED) {
+            dx += xs.xl;
+            dy += xs.yl;
+            dz += xs.zl;
+        }
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        bool in = r2 < (EXACT ? kp.rc2_lo : kp.rc2);
+        bool maybe = false;
+        if (EXACT) maybe = !in && r2 < kp.rc2_hi;
+        if (MASKED) {
+            const bool bit = (row >> t) & 1u;
+            in = in && bit;
+            maybe = maybe && bit;
+        }
+        if (EXACT && maybe) band |= 1u << t;
+        pair_force<COUL, VIR>(dx, dy, dz, r2, in, qi, xj.w, s_lj[tirow + tj], kp, ew, fix, fiy, fiz,
+                              fj[t][0], fj[t][1], fj[t][2], v);
+    }
+}
+
+template <int COUL, bool VIR>
+__global__ void __launch_bounds__(FW * 32)
+k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
+    constexpr bool EXACT = COUL == NB_COUL_RF;
+    extern __shared__ float2 s_lj[];
+    __shared__ __align__(16) float4 s_j[FW][4][2 * CL];
+    __shared__ double s_acc[FW][6];
+    __shared__ float s_fix[FW][4][CL][3];
+
+    const int lane = threadIdx.x & 31;
+    const int i = lane & 7;
+    const int g = lane >> 3;
+    const int w = threadIdx.x >> 5;
+    const int nt = kp.ntypes;
+    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) s_lj[k] = kp.lj[k];
+    if (lane < 6) s_acc[w][lane] = 0.0;
+    __syncthreads();
+
+    EwaldC ew;
+    ew.beta = kp.beta;
+    ew.mb2_log2e = -kp.beta * kp.beta * 1.4426950408889634f;
+    ew.c2 = 2.0f * kp.beta * 0.5641895835477563f;
+
+    float4* sjg = &s_j[w][g][0];
+    const int nitems = min(list.counters[CNT_ITEMS], list.item_cap);
+    int cur_sys = -1;
+    const float4* xq_s = nullptr;
+    const int* type_s = nullptr;
+    float4* f_s = nullptr;
+    float Lx = 0.f, Ly = 0.f, Lz = 0.f;
+
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(list.counters + CNT_WORK, 1);
+        it = __shfl_sync(FULL, it, 0);
+        if (it >= nitems) break;
+        const int4 item = list.items[it];
+        const int sid = item.w >> 5;
+        const int sh = item.w & 31;
+        if (sid != cur_sys) {
+            if (VIR && cur_sys >= 0) {
+                __syncwarp();
+                if (lane < 6 && s_acc[w][lane] != 0.0) atomicAdd(sys[cur_sys].acc + ACC_VXX + lane, s_acc[w][lane]);
+                __syncwarp();
+                if (lane < 6) s_acc[w][lane] = 0.0;
+                __syncwarp();
+            }
+            cur_sys = sid;
+            xq_s = sys[sid].xq_s;
+            type_s = sys[sid].type_s;
+            f_s = sys[sid].f_s;
+            Lx = sys[sid].L[0];
+            Ly = sys[sid].L[1];
+            Lz = sys[sid].L[2];
+        }
+        const int ci = item.x, jb = item.y, je = item.z;
+        if (jb >= je) continue;
+        const bool shifted = sh != SHIFT_ZERO;
+        const float4 xi4 = xq_s[ci * CL + i];
+        const ShiftedI xs = shift_i(xi4, sh, Lx, Ly, Lz);
+        const float qi = xi4.w * kp.fq;
+        const int tirow = type_s[ci * CL + i] * nt;
+
+        float fix = 0.f, fiy = 0.f, fiz = 0.f;
+        float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+
+        int e = jb + g;
+        bool act = e < je;
+        int cjn = 0;
+        unsigned long long pm = 0ull;
+        float4 pxq = make_float4(0.f, 0.f, 0.f, 0.f);
+        int pty = 0;
+        if (act) {
+            cjn = list.cj[e];
+            pm = list.mask[e];
+            pxq = xq_s[cjn * CL + i];
+            pty = type_s[cjn * CL + i];
+        }
+        for (int base = jb; base < je; base += 4) {
+            __syncwarp();
+            sjg[i] = pxq;
+            sjg[CL + i] = make_float4(__int_as_float(pty), 0.f, 0.f, 0.f);
+            const int ccj = cjn;
+            const bool cact = act;
+            const unsigned long long cm = pm;
+            e = base + 4 + g;
+            act = e < je;
+            pm = 0ull;
+            if (act) {
+                cjn = list.cj[e];
+                pm = list.mask[e];
+                pxq = xq_s[cjn * CL + i];
+                pty = type_s[cjn * CL + i];
+            }
+            __syncwarp();
+            const unsigned row = (unsigned)(cm >> (8 * i)) & 0xffu;
+            float fj[CL][3];
+#pragma unroll
+            for (int t = 0; t < CL; ++t) fj[t][0] = fj[t][1] = fj[t][2] = 0.f;
+            unsigned band = 0;
+            const bool full = __all_sync(FULL, row == 0xffu);
+            if (full && !shifted)
+                pair_block<COUL, VIR, false, false, EXACT>(sjg, i, xs, qi, tirow, s_lj, row, kp, ew,
+                                                          fix, fiy, fiz, fj, v, band);
+            else if (full)
+                pair_block<COUL, VIR, false, true, EXACT>(sjg, i, xs, qi, tirow, s_lj, row, kp, ew,
+                                                         fix, fiy, fiz, fj, v, band);
+            else
+                pair_block<COUL, VIR, true, true, EXACT>(sjg, i, xs, qi, tirow, s_lj, row, kp, ew,
+                                                        fix, fiy, fiz, fj, v, band);
+            // transposed butterfly over the 8 lanes of the group
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) fj[t][c] += __shfl_xor_sync(FULL, fj[t + 4][c], 4);
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) fj[t][c] += __shfl_xor_sync(FULL, fj[t + 2][c], 2);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) fj[0][c] += __shfl_xor_sync(FULL, fj[1][c], 1);
+            if (EXACT && __any_sync(FULL, band != 0u)) {
+                // rare path: pairs within the band around rc, decided exactly
+                s_fix[w][g][i][0] = s_fix[w][g][i][1] = s_fix[w][g][i][2] = 0.f;
+                __syncwarp();
+                while (band) {
+                    const int t = __ffs(band) - 1;
+                    band &= band - 1;
+                    const int js = t ^ i;
+                    const float4 xj = sjg[js];
+                    if (!exact_inside(xs, xj, kp.rc2_d)) continue;
+                    const int tj = __float_as_int(sjg[CL + js].x);
+                    const float dx = (xs.xh - xj.x) + xs.xl;
+                    const float dy = (xs.yh - xj.y) + xs.yl;
+                    const float dz = (xs.zh - xj.z) + xs.zl;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    float gx = 0.f, gy = 0.f, gz = 0.f;
+                    pair_force<COUL, VIR>(dx, dy, dz, r2, true, qi, xj.w, s_lj[tirow + tj], kp, ew, fix,
+                                          fiy, fiz, gx, gy, gz, v);
+                    atomicAdd(&s_fix[w][g][js][0], gx);
+                    atomicAdd(&s_fix[w][g][js][1], gy);
+                    atomicAdd(&s_fix[w][g][js][2], gz);
+                }
+                __syncwarp();
+                fj[0][0] += s_fix[w][g][i][0];
+                fj[0][1] += s_fix[w][g][i][1];
+                fj[0][2] += s_fix[w][g][i][2];
+            }
+            if (cact) atomicAdd(f_s + ccj * CL + i, make_float4(fj[0][0], fj[0][1], fj[0][2], 0.f));
+        }
+        fix += __shfl_xor_sync(FULL, fix, 8);
+        fiy += __shfl_xor_sync(FULL, fiy, 8);
+        fiz += __shfl_xor_sync(FULL, fiz, 8);
+        fix += __shfl_xor_sync(FULL, fix, 16);
+        fiy += __shfl_xor_sync(FULL, fiy, 16);
+        fiz += __shfl_xor_sync(FULL, fiz, 16);
+        if (g == 0) atomicAdd(f_s + ci * CL + i, make_float4(fix, fiy, fiz, 0.f));
+        if (VIR) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], off);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) s_acc[w][k] += (double)v[k];
+            }
+        }
+    }
+    if (VIR && cur_sys >= 0) {
+        __syncwarp();
+        if (lane < 6 && s_acc[w][lane] != 0.0) atomicAdd(sys[cur_sys].acc + ACC_VXX + lane, s_acc[w][lane]);
+    }
+}
+
+// Zero the sorted force buffers, the accumulators of every system and the
+// work counters.
+__global__ void k_zero(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys,
+                       int tot_slots, int* __restrict__ counters) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        counters[CNT_WORK] = 0;
+        counters[CNT_EWORK] = 0;
+    }
+    if (t >= tot_slots) return;
+    int c = t / CL;
+    int s = find_sys_dev(cl_off, nsys, c);
+    const SysDev& d = sys[s];
+    int slot = t - cl_off[s] * CL;
+    d.f_s[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (slot < NACC) d.acc[slot] = 0.0;
+}
+
+// Stale-list evaluation: copy new coordinates into the sorted slots without
+// re-sorting, applying the box multiples recorded by the last grid put.
+__global__ void k_coord_update(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys,
+                               int tot_slots) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tot_slots) return;
+    int s = find_sys_dev(cl_off, nsys, t / CL);
+    const SysDev& d = sys[s];
+    int slot = t - cl_off[s] * CL;
+    if (slot >= d.col_cl0[d.ncol] * CL) return;
+    int a = d.perm[slot];
+    if (a < 0) return;
+    int wk = d.wrapk[slot];
+    int kx = (int)(signed char)(wk & 0xff);
+    int ky = (int)(signed char)((wk >> 8) & 0xff);
+    int kz = (int)(signed char)((wk >> 16) & 0xff);
+    float4 v = d.xq_s[slot];
+    v.x = d.x_new[3 * a + 0] - (float)kx * d.L[0];
+    v.y = d.x_new[3 * a + 1] - (float)ky * d.L[1];
+    v.z = d.x_new[3 * a + 2] - (float)kz * d.L[2];
+    d.xq_s[slot] = v;
+}
+
+// Forces back to the caller's atom order.
+__global__ void k_unsort(const SysDev* __restrict__ sys, const int* __restrict__ atom_off, int nsys,
+                         int tot_atoms) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tot_atoms) return;
+    int s = find_sys_dev(atom_off, nsys, t);
+    const SysDev& d = sys[s];
+    int a = t - atom_off[s];
+    float4 f = d.f_s[d.iperm[a]];
+    d.f_out[3 * a + 0] = f.x;
+    d.f_out[3 * a + 1] = f.y;
+    d.f_out[3 * a + 2] = f.z;
+}
+
+// Final FP64 combination of the accumulators of each system.
+__global__ void k_energy_final(const SysDev* __restrict__ sys, int nsys) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    const SysDev& d = sys[s];
+    const double* a = d.acc;
+    double* r = d.res;
+    r[0] = a[ACC_E12] / 12.0 - a[ACC_E6] / 6.0;
+    r[1] = a[ACC_EC] + a[ACC_ECLO];
+    r[2] = -0.5 * a[ACC_VXX];
+    r[3] = -0.5 * a[ACC_VXY];
+    r[4] = -0.5 * a[ACC_VXZ];
+    r[5] = -0.5 * a[ACC_VXY];
+    r[6] = -0.5 * a[ACC_VYY];
+    r[7] = -0.5 * a[ACC_VYZ];
+    r[8] = -0.5 * a[ACC_VXZ];
+    r[9] = -0.5 * a[ACC_VYZ];
+    r[10] = -0.5 * a[ACC_VZZ];
+    r[11] = a[ACC_NPAIR];
+}
+
+template <int COUL, bool VIR>
+cudaError_t launch_forces_t(const PlanLaunch& p, cudaStream_t st) {
+    size_t smem = (size_t)p.kp.ntypes * p.kp.ntypes * sizeof(float2);
+    auto kern = k_forces<COUL, VIR>;
+    int per_sm = 0;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FW * 32, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) per_sm = 1;
+    kern<<<p.num_sms * per_sm, FW * 32, smem, st>>>(p.d_sys, p.list, p.kp);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_zero_forces(const PlanLaunch& p, cudaStream_t st) {
+    int tot = p.tot_clcap * CL;
+    int bs = 256;
+    k_zero<<<(tot + bs - 1) / bs + 1, bs, 0, st>>>(p.d_sys, p.d_cl_off, p.nsys, tot, p.list.counters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coord_update(const PlanLaunch& p, cudaStream_t st) {
+    int tot = p.tot_clcap * CL;
+    if (tot <= 0) return cudaSuccess;
+    int bs = 256;
+    k_coord_update<<<(tot + bs - 1) / bs, bs, 0, st>>>(p.d_sys, p.d_cl_off, p.nsys, tot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces(const PlanLaunch& p, unsigned flags, cudaStream_t st) {
+    bool vi = flags & NB_F_VIRIAL;
+    if (p.kp.coul == NB_COUL_RF)
+        return vi ? launch_forces_t<NB_COUL_RF, true>(p, st) : launch_forces_t<NB_COUL_RF, false>(p, st);
+    return vi ? launch_forces_t<NB_COUL_EWALD, true>(p, st) : launch_forces_t<NB_COUL_EWALD, false>(p, st);
+}
+
+cudaError_t launch_finalize(const PlanLaunch& p, unsigned flags, cudaStream_t st) {
+    int bs = 256;
+    if (p.tot_atoms > 0)
+        k_unsort<<<(p.tot_atoms + bs - 1) / bs, bs, 0, st>>>(p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms);
+    if (flags & (NB_F_ENERGY | NB_F_VIRIAL))
+        k_energy_final<<<(p.nsys + 127) / 128, 128, 0, st>>>(p.d_sys, p.nsys);
+    return cudaGetLastError();
+}
+
+}  // namespace nbgb

@@ -1,0 +1,269 @@
+"""Thin ctypes binding of the C ABI in include/nb.h.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library libnbgb.so.  There is no fallback; if the library is missing or no
+GPU is present the calls raise.
+
+Buffers may be numpy arrays (host memory) or torch tensors (host or CUDA);
+the library moves data with cudaMemcpyAsync on the context's stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+NB_OK = 0
+NB_COUL_RF = 0
+NB_COUL_EWALD = 1
+NB_F_ENERGY = 1
+NB_F_VIRIAL = 2
+
+STATUS = {0: "NB_OK", 1: "NB_ERR_ARG", 2: "NB_ERR_BOX", 3: "NB_ERR_OOM", 4: "NB_ERR_BUDGET",
+          5: "NB_ERR_CUDA", 6: "NB_ERR_NOT_READY", 7: "NB_ERR_TIMEOUT", 8: "NB_ERR_STATE",
+          9: "NB_ERR_CAPACITY"}
+
+# the exported functions declared in include/nb.h
+EXPORTS = ["nb_last_error", "nb_ctx_create", "nb_ctx_destroy", "nb_ctx_memory", "nb_sys_footprint",
+           "nb_sys_create", "nb_sys_destroy", "nb_set_exclusions", "nb_grid_put", "nb_pairlist_build",
+           "nb_pairlist_info", "nb_forces", "nb_pairlist_export", "nb_batch_create",
+           "nb_batch_destroy", "nb_sys_set_coords", "nb_batch_submit", "nb_batch_poll",
+           "nb_sys_results", "nb_ctx_set_timing", "nb_ctx_timing", "nb_eval_info"]
+NB_NSTAGE = 8
+STAGES = ["grid", "search", "prune", "coord", "zero", "forces", "final", "energy"]
+
+
+class NbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class nb_params(ctypes.Structure):
+    _fields_ = [("rc", ctypes.c_double), ("rlist", ctypes.c_double), ("coul", ctypes.c_int),
+                ("eps_r", ctypes.c_double), ("eps_rf", ctypes.c_double),
+                ("ewald_beta", ctypes.c_double), ("fcoul", ctypes.c_double),
+                ("ntypes", ctypes.c_int), ("c6", ctypes.POINTER(ctypes.c_float)),
+                ("c12", ctypes.POINTER(ctypes.c_float))]
+
+
+class nb_list_info(ctypes.Structure):
+    _fields_ = [("n_clusters", ctypes.c_longlong), ("n_items", ctypes.c_longlong),
+                ("n_entries", ctypes.c_longlong), ("n_entries_raw", ctypes.c_longlong),
+                ("n_slots", ctypes.c_longlong)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_st = ctypes.c_int
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libnbgb.so (raise if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise NbError(5, f"{path} not found: build it with paper_1506_00716_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "nb_last_error": ([], ctypes.c_char_p),
+        "nb_ctx_create": ([ctypes.c_int, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)], _st),
+        "nb_ctx_destroy": ([_vp], _st),
+        "nb_ctx_memory": ([_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)], _st),
+        "nb_sys_footprint": ([ctypes.POINTER(nb_params), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_size_t)], _st),
+        "nb_sys_create": ([_vp, ctypes.POINTER(nb_params), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(_vp)], _st),
+        "nb_sys_destroy": ([_vp], _st),
+        "nb_set_exclusions": ([_vp, _vp, _vp], _st),
+        "nb_grid_put": ([_vp, _vp, _vp], _st),
+        "nb_pairlist_build": ([_vp], _st),
+        "nb_pairlist_info": ([_vp, ctypes.POINTER(nb_list_info)], _st),
+        "nb_forces": ([_vp, _vp, _vp, _vp, _vp, ctypes.c_uint], _st),
+        "nb_pairlist_export": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong)], _st),
+        "nb_batch_create": ([_vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp)], _st),
+        "nb_batch_destroy": ([_vp], _st),
+        "nb_sys_set_coords": ([_vp, _vp, _vp], _st),
+        "nb_batch_submit": ([_vp, ctypes.c_uint, ctypes.POINTER(ctypes.c_ulonglong)], _st),
+        "nb_batch_poll": ([_vp, ctypes.c_ulonglong, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)], _st),
+        "nb_sys_results": ([_vp, _vp, _vp, _vp], _st),
+        "nb_ctx_set_timing": ([_vp, ctypes.c_int], _st),
+        "nb_ctx_timing": ([_vp, _vp, _vp, ctypes.c_int], _st),
+        "nb_eval_info": ([_vp, ctypes.POINTER(ctypes.c_longlong)], _st),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().nb_last_error().decode()
+
+
+def check(status: int) -> int:
+    if status != NB_OK:
+        raise NbError(status, last_error())
+    return status
+
+
+def ptr(x):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    if hasattr(x, "ctypes"):
+        return ctypes.c_void_p(x.ctypes.data)
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def make_params(p) -> tuple[nb_params, tuple]:
+    """nb_params from an object with rc, rlist, coul, eps_r, eps_rf, beta, fcoul, ntypes, c6, c12."""
+    import numpy as np
+
+    c6 = np.ascontiguousarray(p.c6, dtype=np.float32)
+    c12 = np.ascontiguousarray(p.c12, dtype=np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    s = nb_params(float(p.rc), float(p.rlist), int(p.coul), float(p.eps_r), float(p.eps_rf),
+                  float(p.beta), float(p.fcoul), int(p.ntypes), c6.ctypes.data_as(fp),
+                  c12.ctypes.data_as(fp))
+    return s, (c6, c12)
+
+
+# ----------------------------------------------------------------- wrappers
+
+def nb_ctx_create(device: int = 0, stream=None, budget: int = 0) -> int:
+    out = _vp()
+    st = None
+    if stream is not None:
+        st = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    check(load().nb_ctx_create(device, st, budget, ctypes.byref(out)))
+    return out.value
+
+
+def nb_ctx_destroy(ctx) -> None:
+    check(load().nb_ctx_destroy(ctx))
+
+
+def nb_ctx_memory(ctx) -> tuple[int, int]:
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    check(load().nb_ctx_memory(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def nb_sys_footprint(params, natoms: int, box) -> int:
+    ps, keep = make_params(params)
+    b = (ctypes.c_double * 3)(*[float(v) for v in box])
+    out = ctypes.c_size_t()
+    check(load().nb_sys_footprint(ctypes.byref(ps), natoms, b, ctypes.byref(out)))
+    del keep
+    return out.value
+
+
+def nb_sys_create(ctx, params, natoms: int, box) -> int:
+    ps, keep = make_params(params)
+    b = (ctypes.c_double * 3)(*[float(v) for v in box])
+    out = _vp()
+    check(load().nb_sys_create(ctx, ctypes.byref(ps), natoms, b, ctypes.byref(out)))
+    del keep
+    return out.value
+
+
+def nb_sys_destroy(sys) -> None:
+    check(load().nb_sys_destroy(sys))
+
+
+def nb_set_exclusions(sys, excl_index, excl_atoms) -> None:
+    import numpy as np
+
+    ei = np.ascontiguousarray(excl_index, dtype=np.int32)
+    ea = np.ascontiguousarray(excl_atoms, dtype=np.int32)
+    if ea.size == 0:
+        ea = np.zeros(1, dtype=np.int32)
+    check(load().nb_set_exclusions(sys, ptr(ei), ptr(ea)))
+
+
+def nb_grid_put(sys, xq, type_) -> None:
+    check(load().nb_grid_put(sys, ptr(xq), ptr(type_)))
+
+
+def nb_pairlist_build(sys) -> None:
+    check(load().nb_pairlist_build(sys))
+
+
+def nb_pairlist_info(sys) -> dict:
+    info = nb_list_info()
+    check(load().nb_pairlist_info(sys, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in nb_list_info._fields_}
+
+
+def nb_forces(sys, x_new=None, f=None, energy=None, virial=None, flags: int = 0) -> None:
+    check(load().nb_forces(sys, ptr(x_new), ptr(f), ptr(energy), ptr(virial), flags))
+
+
+def nb_pairlist_export(sys, perm=None, items=None, cj=None, mask=None) -> int:
+    n = ctypes.c_longlong()
+    check(load().nb_pairlist_export(sys, ptr(perm), ptr(items), ptr(cj), ptr(mask), ctypes.byref(n)))
+    return n.value
+
+
+def nb_batch_create(ctx, systems) -> int:
+    arr = (_vp * len(systems))(*systems)
+    out = _vp()
+    check(load().nb_batch_create(ctx, arr, len(systems), ctypes.byref(out)))
+    return out.value
+
+
+def nb_batch_destroy(batch) -> None:
+    check(load().nb_batch_destroy(batch))
+
+
+def nb_sys_set_coords(sys, xq, type_) -> None:
+    check(load().nb_sys_set_coords(sys, ptr(xq), ptr(type_)))
+
+
+def nb_batch_submit(batch, flags: int = 0) -> int:
+    t = ctypes.c_ulonglong()
+    check(load().nb_batch_submit(batch, flags, ctypes.byref(t)))
+    return t.value
+
+
+def nb_batch_poll(batch, ticket: int, timeout_us: int = 0) -> bool:
+    """True once the submission finished; raises NbError on NB_ERR_TIMEOUT and other failures."""
+    done = ctypes.c_int()
+    check(load().nb_batch_poll(batch, ticket, timeout_us, ctypes.byref(done)))
+    return bool(done.value)
+
+
+def nb_sys_results(sys, f=None, energy=None, virial=None) -> None:
+    check(load().nb_sys_results(sys, ptr(f), ptr(energy), ptr(virial)))
+
+
+def nb_ctx_set_timing(ctx, enable: bool) -> None:
+    check(load().nb_ctx_set_timing(ctx, 1 if enable else 0))
+
+
+def nb_ctx_timing(ctx, reset: bool = False) -> dict:
+    """{stage: (total ms, launches)} of the stages timed since the last reset."""
+    ms = (ctypes.c_double * NB_NSTAGE)()
+    n = (ctypes.c_longlong * NB_NSTAGE)()
+    check(load().nb_ctx_timing(ctx, ctypes.cast(ms, _vp), ctypes.cast(n, _vp), 1 if reset else 0))
+    return {name: (ms[k], n[k]) for k, name in enumerate(STAGES)}
+
+
+def nb_eval_info(sys) -> dict:
+    n = ctypes.c_longlong()
+    check(load().nb_eval_info(sys, ctypes.byref(n)))
+    return {"n_pairs": n.value}

@@ -1,0 +1,199 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: the pair list covers the oracle's interacting pairs exactly
+(integer set equality) and every pair inside rlist; forces within
+RMS(dF)/RMS(F) <= 1e-5; E_LJ, E_C within 1e-6 relative; every virial
+component within 1e-6 of the virial's Frobenius norm.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1506_00716_gb300 import nb
+from paper_1506_00716_gb300 import waterbox as wb
+from _support import expand_pairs, export_list, gpu_eval, rel_rms
+
+pytestmark = pytest.mark.gpu
+
+F_TOL = 1e-5
+E_TOL = 1e-6
+V_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1506_00716_gb300 import build as nbbuild
+
+    nbbuild.build()
+    c = nb.nb_ctx_create(0, None, 0)
+    yield c
+    nb.nb_ctx_destroy(c)
+
+
+BOXES = {
+    "small": lambda: wb.small_box(seed=1),
+    "mid": lambda: wb.mid_box(seed=2),
+}
+
+
+@pytest.mark.parametrize("name", ["small", "mid"])
+def test_pairlist_covers_oracle_pairs_exactly(ctx, name):
+    s = BOXES[name]()
+    p = wb.params_rf()
+    _, _, _, h = gpu_eval(ctx, s, p, flags=0, keep=True)
+    try:
+        info, perm, items, cj, mask = export_list(h)
+    finally:
+        nb.nb_sys_destroy(h)
+    assert sorted(perm[perm >= 0].tolist()) == list(range(s.n))
+    got, occurrences = expand_pairs(s, perm, items, cj, mask, p.rc)
+    ref = oracle.pairs(s, p.rc)
+    assert occurrences == got.shape[0], "a pair appears twice inside rc (double counting)"
+    assert np.array_equal(got, ref)
+    got_l, _ = expand_pairs(s, perm, items, cj, mask, p.rlist)
+    ref_l = oracle.pairs(s, p.rlist)
+    assert np.isin(ref_l, got_l).all(), "a pair inside rlist is missing from the list"
+    assert info["n_entries"] <= info["n_entries_raw"]
+
+
+def _check(s, p, f, e, v, f_tol=F_TOL, e_tol=E_TOL, v_tol=V_TOL):
+    ref_f = oracle.forces(s, p)
+    ref = oracle.energy_virial(s, p)
+    errs = {
+        "f": rel_rms(f, ref_f),
+        "e_lj": abs(e[0] - ref["e_lj"]) / abs(ref["e_lj"]),
+        "e_coul": abs(e[1] - ref["e_coul"]) / abs(ref["e_coul"]),
+        "virial": float(np.abs(v - ref["virial"].reshape(-1)).max() / np.linalg.norm(ref["virial"])),
+    }
+    print(errs)
+    assert errs["f"] <= f_tol, errs
+    assert errs["e_lj"] <= e_tol, errs
+    assert errs["e_coul"] <= e_tol, errs
+    assert errs["virial"] <= v_tol, errs
+    return errs
+
+
+@pytest.mark.parametrize("name", ["small", "mid"])
+@pytest.mark.parametrize("coul", [wb.COUL_RF, wb.COUL_EWALD])
+def test_forces_energies_virial(ctx, name, coul):
+    s = BOXES[name]()
+    p = wb.Params(coul=coul)
+    f, e, v, _ = gpu_eval(ctx, s, p)
+    _check(s, p, f, e, v)
+
+
+@pytest.mark.parametrize("flags", [0, nb.NB_F_ENERGY, nb.NB_F_VIRIAL])
+def test_flag_variants_give_the_same_forces(ctx, flags):
+    s = BOXES["small"]()
+    p = wb.params_rf()
+    f_all, e_all, v_all, _ = gpu_eval(ctx, s, p)
+    f, e, v, _ = gpu_eval(ctx, s, p, flags=flags)
+    assert rel_rms(f, f_all) < 1e-6
+    if flags & nb.NB_F_ENERGY:
+        assert np.allclose(e, e_all, rtol=1e-9, atol=0)
+    if flags & nb.NB_F_VIRIAL:
+        assert np.allclose(v, v_all, rtol=1e-9, atol=1e-9)
+
+
+def test_stale_list_evaluations(ctx):
+    """24,000-atom box: list rebuilt every 10 evaluations, Gaussian moves between."""
+    s = wb.mid_box(seed=2)
+    p = wb.params_rf()
+    h = nb.nb_sys_create(ctx, p, s.n, s.box)
+    nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
+    rng = np.random.default_rng(99)
+    try:
+        for ev in range(12):
+            if ev % 10 == 0:
+                nb.nb_grid_put(h, s.xq(), s.type)
+                nb.nb_pairlist_build(h)
+                x_new = None
+            else:
+                s.x = (s.x.astype(np.float64) + rng.normal(0.0, 0.005, size=s.x.shape)).astype(np.float32)
+                x_new = np.ascontiguousarray(s.x)
+            if ev in (0, 5, 9, 11):
+                f = np.zeros((s.n, 3), dtype=np.float32)
+                e = np.zeros(2)
+                v = np.zeros(9)
+                nb.nb_forces(h, x_new, f, e, v, nb.NB_F_ENERGY | nb.NB_F_VIRIAL)
+                _check(s, p, f, e, v)
+            else:
+                nb.nb_forces(h, x_new, None, None, None, 0)
+    finally:
+        nb.nb_sys_destroy(h)
+
+
+def test_single_molecule_has_no_interactions(ctx):
+    s = wb.water_box(1, 3.0, seed=5)
+    f, e, v, _ = gpu_eval(ctx, s, wb.params_rf())
+    assert np.all(f == 0) and np.all(e == 0) and np.all(v == 0)
+
+
+def test_two_atoms_across_the_boundary(ctx):
+    L = wb.f32(2.5)
+    s = wb.System(x=np.array([[0.05, 1.0, 1.0], [L - 0.25, 1.0, 1.0]], dtype=np.float32),
+                  q=np.array([1.0, -1.0], dtype=np.float32), type=np.array([0, 0], dtype=np.int32),
+                  box=np.array([L, L, L]), excl_index=np.zeros(3, dtype=np.int32),
+                  excl_atoms=np.zeros(0, dtype=np.int32), n_mol=0, seed=0)
+    p = wb.params_rf()
+    f, e, v, _ = gpu_eval(ctx, s, p)
+    _check(s, p, f, e, v, f_tol=1e-6, e_tol=1e-6, v_tol=1e-6)
+
+
+def test_coordinates_outside_the_box_are_wrapped(ctx):
+    s = BOXES["small"]()
+    p = wb.params_rf()
+    f0, e0, v0, _ = gpu_eval(ctx, s, p)
+    L = np.float32(s.box[0])
+    moved = wb.System(**{**s.__dict__})
+    k = np.random.default_rng(3).integers(-2, 3, size=s.x.shape).astype(np.float32)
+    moved.x = (s.x + k * L).astype(np.float32)
+    f1, e1, v1, _ = gpu_eval(ctx, moved, p)
+    # the library wraps x - L floor(x / L) in float32; for |k| <= 2 that is the
+    # same rounding as numpy's, so the oracle sees exactly the wrapped inputs
+    wrapped = wb.System(**{**moved.__dict__})
+    w = (moved.x - L * np.floor(moved.x / L)).astype(np.float32)
+    w[w >= L] = 0.0
+    wrapped.x = w
+    _check(wrapped, p, f1, e1, v1)
+
+
+def test_box_of_exactly_two_list_radii(ctx):
+    s = wb.water_box(300, 2.2, seed=8)
+    p = wb.params_rf()
+    f, e, v, _ = gpu_eval(ctx, s, p)
+    _check(s, p, f, e, v)
+
+
+def test_error_paths(ctx):
+    p = wb.params_rf()
+    with pytest.raises(nb.NbError) as ei:
+        nb.nb_sys_create(ctx, p, 100, [1.5, 3.0, 3.0])
+    assert ei.value.status == 2
+    h = nb.nb_sys_create(ctx, p, 3, [3.0, 3.0, 3.0])
+    try:
+        with pytest.raises(nb.NbError) as ei:
+            nb.nb_pairlist_build(h)
+        assert ei.value.status == 8
+        with pytest.raises(nb.NbError) as ei:
+            nb.nb_forces(h, None, None, None, None, 0)
+        assert ei.value.status == 8
+        with pytest.raises(nb.NbError) as ei:
+            nb.nb_forces(h, None, None, None, None, 1)  # energy flag without a buffer
+        assert ei.value.status == 1
+    finally:
+        nb.nb_sys_destroy(h)
+
+
+def test_budget_refuses_without_allocating(ctx):
+    c = nb.nb_ctx_create(0, None, 1 << 20)
+    try:
+        with pytest.raises(nb.NbError) as ei:
+            nb.nb_sys_create(c, wb.params_rf(), 24000, [6.21] * 3)
+        assert ei.value.status == 4
+        assert nb.nb_ctx_memory(c)[0] == 0
+    finally:
+        nb.nb_ctx_destroy(c)
