@@ -14,7 +14,9 @@ roundings.
 Two fits: degree 8 for the force kernel (max relative error ~2e-8) and
 degree 12 for the energy kernel (~4e-11), the latter with every
 coefficient split into a float32 head and a float32 tail so that the
-rounding of the coefficients does not bias the energy.
+rounding of the coefficients does not bias the energy.  A third fit, of
+2^f on [-0.5, 0.5] (degree 10, head + tail), gives the energy kernel an
+exponential free of the SFU's approximation error.
 
 Run: python fit_erfc.py  (needs numpy and scipy; the output is committed)
 """
@@ -44,6 +46,14 @@ def fit(deg: int) -> np.ndarray:
     return series.convert(kind=np.polynomial.Polynomial).coef
 
 
+def fit_exp2(deg: int) -> np.ndarray:
+    """2^f on f in [-0.5, 0.5] by least squares at Chebyshev nodes (power basis in f)."""
+    v = np.cos(np.pi * (np.arange(M) + 0.5) / M)
+    f = 0.5 * v
+    series = np.polynomial.Chebyshev.fit(f, np.exp2(f), deg, domain=[-0.5, 0.5])
+    return series.convert(kind=np.polynomial.Polynomial).coef
+
+
 def max_rel_error(a: np.ndarray) -> float:
     x = np.linspace(0.0, XMAX, 400001)
     t = 1.0 / (1.0 + P * x)
@@ -61,6 +71,11 @@ def main():
     ae = fit(12)
     ae_hi = ae.astype(np.float32)
     ae_lo = (ae - ae_hi.astype(np.float64)).astype(np.float32)
+    a2 = fit_exp2(10)
+    ff = np.linspace(-0.5, 0.5, 200001)
+    e2 = float(np.abs(np.polynomial.polynomial.polyval(ff, a2) / np.exp2(ff) - 1.0).max())
+    a2_hi = a2.astype(np.float32)
+    a2_lo = (a2 - a2_hi.astype(np.float64)).astype(np.float32)
     lines = [
         "// erfc_fit.cuh -- generated by fit_erfc.py; do not edit.",
         "// erfc(x) = exp(-x^2) R(u), t = 1/(1 + EF_P x), u = EF_UA t + EF_UB, x in [0, EF_XMAX].",
@@ -77,6 +92,10 @@ def main():
         f"constexpr int EF_NE = {len(ae)};",
         "__device__ constexpr float EF_EN_HI[EF_NE] = {" + ", ".join(fmt(v) for v in ae_hi) + "};",
         "__device__ constexpr float EF_EN_LO[EF_NE] = {" + ", ".join(fmt(v) for v in ae_lo) + "};",
+        f"// 2^f on [-0.5, 0.5]: degree {len(a2) - 1}, max relative error {e2:.2e}",
+        f"constexpr int EX2_N = {len(a2)};",
+        "__device__ constexpr float EX2_HI[EX2_N] = {" + ", ".join(fmt(v) for v in a2_hi) + "};",
+        "__device__ constexpr float EX2_LO[EX2_N] = {" + ", ".join(fmt(v) for v in a2_lo) + "};",
         "}  // namespace nbgb",
         "",
     ]

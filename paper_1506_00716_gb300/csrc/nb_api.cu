@@ -239,7 +239,7 @@ size_t sys_layout(int natoms, const Geometry& g, int ntypes, SysDev* h, char* ba
     char* col_cl0 = take(4 * ((size_t)g.ncol + 1));
     char* acc = take(8 * NACC);
     char* res = take(8 * NRES);
-    char* lj = take(8 * (size_t)ntypes * ntypes);
+    char* lj = take(16 * (size_t)ntypes * ntypes);  // (6 c6, 12 c12) then (c6, c12)
     (void)lj;
     if (h) {
         h->xq_in = (float4*)xq_in;
@@ -266,7 +266,7 @@ size_t sys_layout(int natoms, const Geometry& g, int ntypes, SysDev* h, char* ba
 
 float2* sys_lj_ptr(nb_sys* s) {
     size_t total = sys_layout(s->natoms, s->geo, s->p.ntypes, nullptr, nullptr);
-    size_t lj = align256(8 * (size_t)s->p.ntypes * s->p.ntypes);
+    size_t lj = align256(16 * (size_t)s->p.ntypes * s->p.ntypes);
     return (float2*)((char*)s->block + total - lj);
 }
 
@@ -303,6 +303,7 @@ KParams make_kparams(const nb_sys* s) {
     k.coul = p.coul;
     k.ntypes = p.ntypes;
     k.lj = s->d_lj;
+    k.lje = s->d_lj + (size_t)p.ntypes * p.ntypes;
     return k;
 }
 
@@ -664,8 +665,11 @@ nb_status nb_sys_create(nb_ctx* ctx, const nb_params* params, int natoms, const 
     h.clcap = y->geo.clcap;
     h.excl_index = nullptr;
     h.excl_atoms = nullptr;
-    std::vector<float2> lj(nt * nt);
-    for (int k = 0; k < nt * nt; ++k) lj[k] = make_float2(6.0f * y->c6[k], 12.0f * y->c12[k]);
+    std::vector<float2> lj(2 * nt * nt);
+    for (int k = 0; k < nt * nt; ++k) {
+        lj[k] = make_float2(6.0f * y->c6[k], 12.0f * y->c12[k]);
+        lj[nt * nt + k] = make_float2(y->c6[k], y->c12[k]);
+    }
     cudaError_t e = cudaMemcpyAsync(y->d_lj, lj.data(), 8 * lj.size(), cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h.acc, 0, 8 * NACC, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h.res, 0, 8 * NRES, ctx->stream);

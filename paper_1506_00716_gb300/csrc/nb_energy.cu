@@ -12,10 +12,11 @@
 //   multiply-adds, and then
 //   RF:    V = f qi qj (1/r + k_rf r^2 - c_rf) fully in double-float;
 //   Ewald: V = f qi qj erfc(b r)/r with erfc(x) = exp(-x^2) R(u) from the
-//          degree-12 fit (head + tail coefficients), exp(-x^2) from the SFU
-//          base-2 exponential of the double-float argument's head times the
-//          first-order factor of its tail;
-//   LJ:    c12 r^-12, c6 r^-6 in float32 from the accurate 1/r.
+//          degree-12 fit (head + tail coefficients) and exp(-x^2) = 2^a
+//          from the double-float argument a by exact range reduction and a
+//          fitted polynomial (no SFU approximation);
+//   LJ:    c12 r^-12, c6 r^-6 in float32 from the accurate 1/r and the
+//          unscaled c6, c12 (pre-scaled 6 c6, 12 c12 would round).
 // Coulomb energies accumulate in double-float per lane and work item, and in
 // float64 across items and warps.  Cut-off decisions are exact (the float64
 // distance of the float32 inputs decides pairs near rc), so the counted pair
@@ -45,6 +46,22 @@ __device__ __forceinline__ float erfcx_energy(float x) {
         rl = fmaf(rl, u, EF_EN_LO[k]);
     }
     return rh + rl;
+}
+
+// 2^a for a = ah + al <= 0 without the SFU: a = n + f with n = rint(ah) and
+// f = (ah - n) + al in [-0.5, 0.5] (ah - n is exact), 2^f from the degree-10
+// fit (head + tail coefficients), times 2^n built in the exponent field.
+__device__ __forceinline__ float exp2_dd(float ah, float al) {
+    ah = fmaxf(ah, -120.f);
+    const float n = rintf(ah);
+    const float f = (ah - n) + al;
+    float ph = EX2_HI[EX2_N - 1], pl = EX2_LO[EX2_N - 1];
+#pragma unroll
+    for (int k = EX2_N - 2; k >= 0; --k) {
+        ph = fmaf(ph, f, EX2_HI[k]);
+        pl = fmaf(pl, f, EX2_LO[k]);
+    }
+    return (ph + pl) * __int_as_float(((int)n + 127) << 23);
 }
 
 template <int COUL>
@@ -113,9 +130,7 @@ __device__ __forceinline__ void pair_energy(const float4 xj, int tj, const Shift
         float ah, ae;
         two_prod(kp.mb2l2e_h, r2h, ah, ae);
         const float al = fmaf(kp.mb2l2e_h, r2l, fmaf(kp.mb2l2e_l, r2h, ae));
-        float e = ex2_sfu(ah);
-        e = fmaf(e * 0.69314718055994531f, al, e);
-        const float w = (R * e) * rif;
+        const float w = (R * exp2_dd(ah, al)) * rif;
         float ve;
         two_prod(qh, w, vh, ve);
         vl = fmaf(ql, w, ve);
@@ -159,7 +174,7 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     const int g = lane >> 3;
     const int w = threadIdx.x >> 5;
     const int nt = kp.ntypes;
-    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) s_lj[k] = kp.lj[k];
+    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) s_lj[k] = kp.lje[k];
     __syncthreads();
 
     float4* sjg = &s_j[w][g][0];

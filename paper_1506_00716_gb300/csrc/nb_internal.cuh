@@ -98,7 +98,8 @@ struct KParams {
     int coul;
     int ntypes;
     int max_entries;     // list entries per work item (items are split beyond)
-    const float2* lj;    // [ntypes^2] (6 c6, 12 c12)
+    const float2* lj;    // [ntypes^2] (6 c6, 12 c12), force kernel
+    const float2* lje;   // [ntypes^2] (c6, c12), energy kernel
 };
 
 // Host-side view of a plan, used to size launches.

@@ -364,7 +364,7 @@ __global__ void k_energy_final(const SysDev* __restrict__ sys, int nsys) {
     const SysDev& d = sys[s];
     const double* a = d.acc;
     double* r = d.res;
-    r[0] = a[ACC_E12] / 12.0 - a[ACC_E6] / 6.0;
+    r[0] = a[ACC_E12] - a[ACC_E6];
     r[1] = a[ACC_EC] + a[ACC_ECLO];
     r[2] = -0.5 * a[ACC_VXX];
     r[3] = -0.5 * a[ACC_VXY];

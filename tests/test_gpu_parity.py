@@ -85,6 +85,18 @@ def test_forces_energies_virial(ctx, name, coul):
     _check(s, p, f, e, v)
 
 
+@pytest.mark.parametrize("coul", [wb.COUL_RF, wb.COUL_EWALD])
+def test_interacting_pair_count_is_exact(ctx, coul):
+    s = BOXES["mid"]()
+    p = wb.Params(coul=coul)
+    _, _, _, h = gpu_eval(ctx, s, p, keep=True)
+    try:
+        n = nb.nb_eval_info(h)["n_pairs"]
+    finally:
+        nb.nb_sys_destroy(h)
+    assert n == oracle.energy_virial(s, p)["npairs"]
+
+
 @pytest.mark.parametrize("flags", [0, nb.NB_F_ENERGY, nb.NB_F_VIRIAL])
 def test_flag_variants_give_the_same_forces(ctx, flags):
     s = BOXES["small"]()
