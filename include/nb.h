@@ -270,6 +270,43 @@ nb_status nb_batch_poll(nb_batch *batch, unsigned long long ticket, long long ti
  */
 nb_status nb_sys_results(nb_sys *sys, float *f, double *energy, double *virial);
 
+/*
+ * Allocation-free evaluation, for callers that cannot allocate device
+ * memory: code that runs where cudaMalloc is unavailable or not allowed
+ * (inside another framework's memory manager, a latency-critical loop that
+ * must not hit the allocator, a plug-in that only receives a stream).  The
+ * paper has no counterpart; this is an interface of this library.
+ *
+ * One call runs grid put, pair search, prune, forces and (per flags)
+ * energies and virial for one system of at most NB_NOALLOC_MAX_ATOMS atoms,
+ * using as scratch a fixed device array of NB_NOALLOC_SCRATCH_BYTES that is
+ * part of the library (every GPU that loads the library holds it until the
+ * process exits).  It calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *   params, natoms, box  as nb_sys_create
+ *   excl_index,          host CSR of exclusions (may both be NULL); unlike
+ *   excl_atoms           nb_set_exclusions, every excluded pair must be
+ *                        listed under both of its atoms
+ *   xq, type             as nb_grid_put (host or device)
+ *   f, energy, virial,   as nb_forces (host or device; f may be NULL)
+ *   flags
+ *   cuda_stream          the stream to run on (NULL = legacy default stream);
+ *                        the calling thread's current CUDA device is used
+ * Returns NB_ERR_CAPACITY if natoms exceeds the maximum or the pair list
+ * does not fit the scratch array.  Synchronises the stream before returning.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress), so make the first call before any stream capture.
+ * All calls share the scratch array: calls whose GPU work overlaps (other
+ * streams or host threads on the same device) race and must be serialised
+ * by the caller.
+ */
+#define NB_NOALLOC_MAX_ATOMS 32768
+#define NB_NOALLOC_SCRATCH_BYTES (32u << 20)
+nb_status nb_eval_noalloc(const nb_params *params, int natoms, const double box[3],
+                          const int *excl_index, const int *excl_atoms, const float *xq,
+                          const int *type, float *f, double *energy, double *virial,
+                          unsigned flags, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -540,6 +540,52 @@ size_t plan_bytes_estimate(const nb_params* p, int natoms, const double box[3], 
 
 }  // namespace
 
+// Helpers shared with the allocation-free entry point (nb_static.cu).
+namespace nbgb {
+
+nb_status api_fail(nb_status s, const char* msg) { return fail(s, msg); }
+
+nb_status api_check_system(const nb_params* params, int natoms, const double box[3]) {
+    nb_status s = check_params(params);
+    if (s != NB_OK) return s;
+    if (natoms <= 0) return fail(NB_ERR_ARG, "natoms must be > 0");
+    return check_box(params, box);
+}
+
+size_t api_sys_layout(int natoms, const double box[3], int ntypes, SysDev* h, char* base) {
+    Geometry g = make_geometry(natoms, box);
+    if (h) {
+        for (int d = 0; d < 3; ++d) h->L[d] = (float)box[d];
+        h->cw[0] = g.cw[0];
+        h->cw[1] = g.cw[1];
+        h->icw[0] = g.icw[0];
+        h->icw[1] = g.icw[1];
+        h->ncx = g.ncx;
+        h->ncy = g.ncy;
+        h->ncol = g.ncol;
+        h->natoms = natoms;
+        h->clcap = g.clcap;
+        h->excl_index = nullptr;
+        h->excl_atoms = nullptr;
+    }
+    return sys_layout(natoms, g, ntypes, h, base);
+}
+
+KParams api_kparams(const nb_params& p, const double box[3], float2* lj) {
+    nb_sys tmp;
+    tmp.p = p;
+    for (int d = 0; d < 3; ++d) tmp.box[d] = box[d];
+    tmp.d_lj = lj;
+    return make_kparams(&tmp);
+}
+
+void api_list_estimate(const nb_params& p, int natoms, const double box[3], int clcap, long long* items,
+                       long long* entries) {
+    list_estimate(p, natoms, box, clcap, items, entries);
+}
+
+}  // namespace nbgb
+
 extern "C" {
 
 const char* nb_last_error(void) { return g_err.c_str(); }

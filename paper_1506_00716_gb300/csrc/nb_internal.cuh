@@ -120,6 +120,16 @@ __host__ __device__ inline int shift_index(int sx, int sy, int sz) {
     return (sx + 1) * 9 + (sy + 1) * 3 + (sz + 1);
 }
 
+// Host helpers of nb_api.cu shared with the allocation-free entry point.
+nb_status api_fail(nb_status s, const char* msg);
+nb_status api_check_system(const nb_params* params, int natoms, const double box[3]);
+// Geometry and buffer layout of one system inside `base` (nullptr: size only);
+// returns the bytes used, the LJ tables occupying the last 16 * ntypes^2.
+size_t api_sys_layout(int natoms, const double box[3], int ntypes, SysDev* h, char* base);
+KParams api_kparams(const nb_params& p, const double box[3], float2* lj);
+void api_list_estimate(const nb_params& p, int natoms, const double box[3], int clcap, long long* items,
+                       long long* entries);
+
 // Kernel launchers (each returns the launch status).
 cudaError_t launch_grid_put(const PlanLaunch& p, cudaStream_t st);
 cudaError_t launch_search(const PlanLaunch& p, cudaStream_t st);

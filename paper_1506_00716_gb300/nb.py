@@ -29,7 +29,8 @@ EXPORTS = ["nb_last_error", "nb_ctx_create", "nb_ctx_destroy", "nb_ctx_memory", 
            "nb_sys_create", "nb_sys_destroy", "nb_set_exclusions", "nb_grid_put", "nb_pairlist_build",
            "nb_pairlist_info", "nb_forces", "nb_pairlist_export", "nb_batch_create",
            "nb_batch_destroy", "nb_sys_set_coords", "nb_batch_submit", "nb_batch_poll",
-           "nb_sys_results", "nb_ctx_set_timing", "nb_ctx_timing", "nb_eval_info"]
+           "nb_sys_results", "nb_ctx_set_timing", "nb_ctx_timing", "nb_eval_info",
+           "nb_eval_noalloc"]
 NB_NSTAGE = 8
 STAGES = ["grid", "search", "prune", "coord", "zero", "forces", "final", "energy"]
 
@@ -97,6 +98,8 @@ def load(path: str | None = None):
         "nb_ctx_set_timing": ([_vp, ctypes.c_int], _st),
         "nb_ctx_timing": ([_vp, _vp, _vp, ctypes.c_int], _st),
         "nb_eval_info": ([_vp, ctypes.POINTER(ctypes.c_longlong)], _st),
+        "nb_eval_noalloc": ([ctypes.POINTER(nb_params), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                             _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_uint, _vp], _st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -267,3 +270,24 @@ def nb_eval_info(sys) -> dict:
     n = ctypes.c_longlong()
     check(load().nb_eval_info(sys, ctypes.byref(n)))
     return {"n_pairs": n.value}
+
+
+def nb_eval_noalloc(params, natoms: int, box, excl_index, excl_atoms, xq, type_, f=None, energy=None,
+                    virial=None, flags: int = 0, stream=None) -> None:
+    """Allocation-free evaluation through a fixed scratch array (see include/nb.h)."""
+    import numpy as np
+
+    ps, keep = make_params(params)
+    b = (ctypes.c_double * 3)(*[float(v) for v in box])
+    ei = ea = None
+    if excl_index is not None:
+        ei = np.ascontiguousarray(excl_index, dtype=np.int32)
+        ea = np.ascontiguousarray(excl_atoms, dtype=np.int32)
+        if ea.size == 0:
+            ea = np.zeros(1, dtype=np.int32)
+    st = None
+    if stream is not None:
+        st = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    check(load().nb_eval_noalloc(ctypes.byref(ps), natoms, b, ptr(ei), ptr(ea), ptr(xq), ptr(type_),
+                                 ptr(f), ptr(energy), ptr(virial), flags, st))
+    del keep
