@@ -299,6 +299,8 @@ KParams make_kparams(const nb_sys* s) {
     k.fq_l = (float)(fq - (double)k.fq_h);
     k.mb2l2e_h = (float)mb;
     k.mb2l2e_l = (float)(mb - (double)k.mb2l2e_h);
+    k.beta_h = (float)p.ewald_beta;
+    k.beta_l = (float)(p.ewald_beta - (double)k.beta_h);
     k.max_entries = 32;
     k.coul = p.coul;
     k.ntypes = p.ntypes;

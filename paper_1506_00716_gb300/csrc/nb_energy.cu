@@ -12,9 +12,10 @@
 //   multiply-adds, and then
 //   RF:    V = f qi qj (1/r + k_rf r^2 - c_rf) fully in double-float;
 //   Ewald: V = f qi qj erfc(b r)/r with erfc(x) = exp(-x^2) R(u) from the
-//          degree-12 fit (head + tail coefficients) and exp(-x^2) = 2^a
-//          from the double-float argument a by exact range reduction and a
-//          fitted polynomial (no SFU approximation);
+//          degree-12 fit and exp(-x^2) = 2^a by exact range reduction and
+//          the degree-10 fit of 2^f (no SFU approximation); x = b r, t, u
+//          and the large head terms of both polynomials in double-float
+//          (compensated Horner), their small tails in float32;
 //   LJ:    c12 r^-12, c6 r^-6 in float32 from the accurate 1/r and the
 //          unscaled c6, c12 (pre-scaled 6 c6, 12 c12 would round).
 // Coulomb energies accumulate in double-float per lane and work item, and in
@@ -33,35 +34,71 @@ namespace {
 constexpr unsigned FULL = FULL_MASK;
 constexpr int EW = 8;  // warps per block
 
-__device__ __forceinline__ float erfcx_energy(float x) {
-    x = fminf(x, EF_XMAX);
-    const float d = fmaf(EF_P, x, 1.f);
-    float t = rcp_sfu(d);
-    t = t * fmaf(-d, t, 2.f);  // one Newton step
-    const float u = fmaf(EF_UA, t, EF_UB);
-    float rh = EF_EN_HI[EF_NE - 1], rl = EF_EN_LO[EF_NE - 1];
+// Horner steps over coefficients hi[k] + lo[k], k = k1 .. 0, in compensated
+// (double-float) arithmetic: p = p * u + c with p, u, c all hi + lo.
+template <int K1>
+__device__ __forceinline__ void horner_dd(const float* hi, const float* lo, float uh, float ul, float& ph,
+                                          float& pl) {
 #pragma unroll
-    for (int k = EF_NE - 2; k >= 0; --k) {
-        rh = fmaf(rh, u, EF_EN_HI[k]);
-        rl = fmaf(rl, u, EF_EN_LO[k]);
+    for (int k = K1; k >= 0; --k) {
+        float m, me, sum, se;
+        two_prod(ph, uh, m, me);
+        const float cross = fmaf(ph, ul, pl * uh);
+        two_sum(m, hi[k], sum, se);
+        ph = sum;
+        pl = ((me + se) + cross) + lo[k];
     }
-    return rh + rl;
 }
 
-// 2^a for a = ah + al <= 0 without the SFU: a = n + f with n = rint(ah) and
-// f = (ah - n) + al in [-0.5, 0.5] (ah - n is exact), 2^f from the degree-10
-// fit (head + tail coefficients), times 2^n built in the exponent field.
-__device__ __forceinline__ float exp2_dd(float ah, float al) {
+// Number of head coefficients evaluated in double-float; the tail terms are
+// small enough (|a_k u^k| <= 5e-4) for plain float32.
+constexpr int EF_HEAD = 5;   // erfc fit: k = 0..4
+constexpr int EX2_HEAD = 4;  // 2^f fit: k = 0..3
+
+// erfc(x) in double-float for x = xh + xl >= 0, from the degree-12 fit and
+// the double-float exponential 2^a, a = ah + al = -x^2 log2(e) (given).
+__device__ __forceinline__ void erfc_dd(float xh, float xl, float ah, float al, float& eh, float& el) {
+    if (xh > EF_XMAX) {
+        xh = EF_XMAX;
+        xl = 0.f;
+    }
+    // d = 1 + P x
+    float m, me, dh, de;
+    two_prod(EF_P, xh, m, me);
+    two_sum(1.f, m, dh, de);
+    const float dl = de + fmaf(EF_P, xl, me);
+    // t = 1 / d
+    float th = rcp_sfu(dh);
+    th = th * fmaf(-dh, th, 2.f);
+    float r = fmaf(-dh, th, 1.f);
+    r = fmaf(-dl, th, r);
+    const float tl = th * r;
+    // u = UA t + UB
+    float uh, ue, sh, se;
+    two_prod(EF_UA, th, uh, ue);
+    two_sum(uh, EF_UB, sh, se);
+    const float ul = se + fmaf(EF_UA, tl, ue);
+    uh = sh;
+    // R(u): float32 tail, double-float head
+    float ph = EF_EN_HI[EF_NE - 1], pl = 0.f;
+#pragma unroll
+    for (int k = EF_NE - 2; k >= EF_HEAD; --k) ph = fmaf(ph, uh, EF_EN_HI[k]);
+    horner_dd<EF_HEAD - 1>(EF_EN_HI, EF_EN_LO, uh, ul, ph, pl);
+    // 2^a = 2^n 2^f, f = (ah - n) + al in [-0.5, 0.5], ah - n exact
     ah = fmaxf(ah, -120.f);
     const float n = rintf(ah);
-    const float f = (ah - n) + al;
-    float ph = EX2_HI[EX2_N - 1], pl = EX2_LO[EX2_N - 1];
+    const float fh = ah - n;
+    float qh = EX2_HI[EX2_N - 1], ql = 0.f;
 #pragma unroll
-    for (int k = EX2_N - 2; k >= 0; --k) {
-        ph = fmaf(ph, f, EX2_HI[k]);
-        pl = fmaf(pl, f, EX2_LO[k]);
-    }
-    return (ph + pl) * __int_as_float(((int)n + 127) << 23);
+    for (int k = EX2_N - 2; k >= EX2_HEAD; --k) qh = fmaf(qh, fh, EX2_HI[k]);
+    horner_dd<EX2_HEAD - 1>(EX2_HI, EX2_LO, fh, al, qh, ql);
+    const float scale = __int_as_float(((int)n + 127) << 23);
+    // erfc = R 2^a
+    float ch, ce;
+    two_prod(ph, qh, ch, ce);
+    const float cl = ce + fmaf(ph, ql, pl * qh);
+    eh = ch * scale;
+    el = cl * scale;
 }
 
 template <int COUL>
@@ -125,15 +162,25 @@ __device__ __forceinline__ void pair_energy(const float4 xj, int tj, const Shift
         two_prod(qh, gh, vh, ve);
         vl = fmaf(qh, gl, fmaf(ql, gh, ve));
     } else {
-        const float r = r2h * rif;
-        const float R = erfcx_energy(kp.beta * r);
+        // r = r^2 (1/r), x = beta r, all double-float
+        float rh, re;
+        two_prod(r2h, y, rh, re);
+        const float rl = re + fmaf(r2h, ril, r2l * y);
+        float xh, xe;
+        two_prod(kp.beta_h, rh, xh, xe);
+        const float xl = xe + fmaf(kp.beta_h, rl, kp.beta_l * rh);
         float ah, ae;
         two_prod(kp.mb2l2e_h, r2h, ah, ae);
         const float al = fmaf(kp.mb2l2e_h, r2l, fmaf(kp.mb2l2e_l, r2h, ae));
-        const float w = (R * exp2_dd(ah, al)) * rif;
+        float eh, el;
+        erfc_dd(xh, xl, ah, al, eh, el);
+        // w = erfc / r, V = q q w
+        float wh, we;
+        two_prod(eh, y, wh, we);
+        const float wl = we + fmaf(eh, ril, el * y);
         float ve;
-        two_prod(qh, w, vh, ve);
-        vl = fmaf(ql, w, ve);
+        two_prod(qh, wh, vh, ve);
+        vl = ve + fmaf(qh, wl, ql * wh);
     }
     if (!in) {
         vh = 0.f;

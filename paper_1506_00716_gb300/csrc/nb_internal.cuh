@@ -95,6 +95,7 @@ struct KParams {
     // double-float (hi + lo) constants of the energy kernel
     float krf_h, krf_l, crf_h, crf_l, fq_h, fq_l;
     float mb2l2e_h, mb2l2e_l;  // -beta^2 log2(e)
+    float beta_h, beta_l;
     int coul;
     int ntypes;
     int max_entries;     // list entries per work item (items are split beyond)
