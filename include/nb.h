@@ -112,13 +112,30 @@ enum {
     NB_STAGE_GRID = 0,    /* nb_grid_put kernels */
     NB_STAGE_SEARCH = 1,  /* cluster-pair search */
     NB_STAGE_PRUNE = 2,   /* list prune */
-    NB_STAGE_COORD = 3,   /* coordinate update of nb_forces(x_new) */
-    NB_STAGE_ZERO = 4,    /* force-buffer clear */
+    NB_STAGE_COORD = 3,   /* staging copy of nb_forces(x_new) */
+    NB_STAGE_ZERO = 4,    /* force-buffer clear + coordinate update */
     NB_STAGE_FORCES = 5,  /* the cluster-pair force kernel */
     NB_STAGE_FINAL = 6,   /* unsort + FP64 energy/virial finalisation */
     NB_STAGE_ENERGY = 7,  /* the double-float energy kernel (NB_F_ENERGY) */
     NB_NSTAGE = 8
 };
+
+/*
+ * Launch tuning of a context (chosen per system size by the project's
+ * autotuner, paper_1506_00716_gb300/autotune.py).  Takes effect at the next
+ * list build or batch submission.
+ *   max_entries       list entries per work item: (i-cluster, shift) runs
+ *                     longer than this are split into several items, which
+ *                     balances the persistent force kernel on small systems;
+ *                     4..4096 (default 32)
+ *   force_min_blocks  register budget of the force kernel, as the number of
+ *                     256-thread blocks guaranteed resident per SM: 1 (up to
+ *                     255 registers per thread), 2 (128) or 3 (85, default)
+ */
+typedef struct {
+    int max_entries;
+    int force_min_blocks;
+} nb_tuning;
 
 /* Message of the calling thread's last failure ("" if none). */
 const char *nb_last_error(void);
@@ -139,6 +156,8 @@ nb_status nb_ctx_destroy(nb_ctx *ctx);
  * (ms and launches: NB_NSTAGE entries, either may be NULL); reset != 0
  * clears the totals.
  */
+nb_status nb_ctx_set_tuning(nb_ctx *ctx, const nb_tuning *tuning);
+nb_status nb_ctx_get_tuning(nb_ctx *ctx, nb_tuning *tuning);
 nb_status nb_ctx_set_timing(nb_ctx *ctx, int enable);
 nb_status nb_ctx_timing(nb_ctx *ctx, double *ms, long long *launches, int reset);
 /* Device bytes currently held by the context's systems and batches. */

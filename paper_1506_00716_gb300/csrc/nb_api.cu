@@ -102,6 +102,8 @@ struct nb_ctx {
     int num_sms = 0;
     bool timing = false;
     bool capturing = false;
+    nb_tuning tuning{32, 3};
+    unsigned tuning_gen = 0;
     std::vector<TimedLaunch> pending;
     std::vector<cudaEvent_t> pool;
     double tot_ms[NB_NSTAGE] = {0};
@@ -142,6 +144,7 @@ struct Plan {
     KParams kp{};
     // graph state (batches)
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    unsigned graph_tuning_gen = 0;
     cudaEvent_t done_ev = nullptr;
     unsigned long long ticket = 0;
     unsigned long long done_ticket = 0;
@@ -302,6 +305,7 @@ KParams make_kparams(const nb_sys* s) {
     k.beta_h = (float)p.ewald_beta;
     k.beta_l = (float)(p.ewald_beta - (double)k.beta_h);
     k.max_entries = 32;
+    k.force_min_blocks = 3;
     k.coul = p.coul;
     k.ntypes = p.ntypes;
     k.lj = s->d_lj;
@@ -416,6 +420,8 @@ nb_status plan_create(nb_ctx* ctx, nb_sys* const* systems, int n, Plan** out) {
 
 PlanLaunch launch_of(const Plan* pl) {
     PlanLaunch p{};
+    const_cast<Plan*>(pl)->kp.max_entries = pl->ctx->tuning.max_entries;
+    const_cast<Plan*>(pl)->kp.force_min_blocks = pl->ctx->tuning.force_min_blocks;
     int n = (int)pl->systems.size();
     p.nsys = n;
     p.d_sys = pl->d_sys;
@@ -472,12 +478,12 @@ nb_status plan_build_list(Plan* pl) {
     return fail(NB_ERR_CAPACITY, "pair list did not fit after growing its buffers");
 }
 
-nb_status plan_eval(Plan* pl, unsigned flags) {
+nb_status plan_eval(Plan* pl, unsigned flags, bool coords) {
     cudaStream_t st = pl->ctx->stream;
     PlanLaunch p = launch_of(pl);
     {
         StageScope sc(pl->ctx, NB_STAGE_ZERO);
-        NB_CK(launch_zero_forces(p, st));
+        NB_CK(launch_prepare(p, coords, st));
     }
     {
         StageScope sc(pl->ctx, NB_STAGE_FORCES);
@@ -624,6 +630,21 @@ nb_status nb_ctx_destroy(nb_ctx* ctx) {
     }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     delete ctx;
+    return NB_OK;
+}
+
+nb_status nb_ctx_set_tuning(nb_ctx* ctx, const nb_tuning* t) {
+    if (!ctx || !t) return fail(NB_ERR_ARG, "ctx / tuning is NULL");
+    if (t->max_entries < 4 || t->max_entries > 4096) return fail(NB_ERR_ARG, "max_entries must be in 4..4096");
+    if (t->force_min_blocks < 1 || t->force_min_blocks > 3) return fail(NB_ERR_ARG, "force_min_blocks must be 1, 2 or 3");
+    ctx->tuning = *t;
+    ctx->tuning_gen += 1;
+    return NB_OK;
+}
+
+nb_status nb_ctx_get_tuning(nb_ctx* ctx, nb_tuning* t) {
+    if (!ctx || !t) return fail(NB_ERR_ARG, "ctx / tuning is NULL");
+    *t = ctx->tuning;
     return NB_OK;
 }
 
@@ -872,11 +893,10 @@ nb_status nb_forces(nb_sys* sys, const float* x_new, float* f, double* energy, d
     Plan* pl = sys->plan;
     cudaStream_t st = sys->ctx->stream;
     if (x_new) {
-        NB_CK(cudaMemcpyAsync(sys->h.x_new, x_new, 12 * (size_t)sys->natoms, cudaMemcpyDefault, st));
         StageScope sc(sys->ctx, NB_STAGE_COORD);
-        NB_CK(launch_coord_update(launch_of(pl), st));
+        NB_CK(cudaMemcpyAsync(sys->h.x_new, x_new, 12 * (size_t)sys->natoms, cudaMemcpyDefault, st));
     }
-    nb_status s = plan_eval(pl, flags);
+    nb_status s = plan_eval(pl, flags, x_new != nullptr);
     if (s != NB_OK) return s;
     bool need_sync = false;
     s = copy_out(sys, f, energy, virial, flags, &need_sync);
@@ -926,7 +946,7 @@ static nb_status batch_record(Plan* pl, unsigned flags) {
     NB_CK(launch_grid_put(p, st));
     NB_CK(launch_search(p, st));
     NB_CK(launch_prune(p, st));
-    NB_CK(launch_zero_forces(p, st));
+    NB_CK(launch_prepare(p, false, st));
     NB_CK(launch_forces(p, flags, st));
     if (flags & NB_F_ENERGY) NB_CK(launch_energy(p, st));
     NB_CK(launch_finalize(p, flags, st));
@@ -941,6 +961,10 @@ nb_status nb_batch_submit(nb_batch* batch, unsigned flags, unsigned long long* t
     for (nb_sys* s : pl->systems)
         if (!s->has_coords) return fail(NB_ERR_STATE, "a batch system has no coordinates");
     cudaStream_t st = batch->ctx->stream;
+    if (pl->graph_tuning_gen != batch->ctx->tuning_gen) {
+        plan_drop_graphs(pl);
+        pl->graph_tuning_gen = batch->ctx->tuning_gen;
+    }
     cudaGraphExec_t& ge = pl->graph[flags & 3];
     if (!ge) {
         if (st == nullptr) {

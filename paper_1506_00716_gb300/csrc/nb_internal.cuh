@@ -99,6 +99,7 @@ struct KParams {
     int coul;
     int ntypes;
     int max_entries;     // list entries per work item (items are split beyond)
+    int force_min_blocks;  // force-kernel launch-bounds variant: 1, 2 or 3
     const float2* lj;    // [ntypes^2] (6 c6, 12 c12), force kernel
     const float2* lje;   // [ntypes^2] (c6, c12), energy kernel
 };
@@ -135,8 +136,9 @@ void api_list_estimate(const nb_params& p, int natoms, const double box[3], int 
 cudaError_t launch_grid_put(const PlanLaunch& p, cudaStream_t st);
 cudaError_t launch_search(const PlanLaunch& p, cudaStream_t st);
 cudaError_t launch_prune(const PlanLaunch& p, cudaStream_t st);
-cudaError_t launch_zero_forces(const PlanLaunch& p, cudaStream_t st);
-cudaError_t launch_coord_update(const PlanLaunch& p, cudaStream_t st);
+// Start of an evaluation: clear forces, accumulators and work counters; with
+// coords, also move the staged x_new into the sorted slots.
+cudaError_t launch_prepare(const PlanLaunch& p, bool coords, cudaStream_t st);
 cudaError_t launch_forces(const PlanLaunch& p, unsigned flags, cudaStream_t st);
 cudaError_t launch_energy(const PlanLaunch& p, cudaStream_t st);
 cudaError_t launch_finalize(const PlanLaunch& p, unsigned flags, cudaStream_t st);

@@ -1,5 +1,6 @@
 // nb_kernel.cu -- the cluster-pair force kernel and the per-evaluation
-// stages around it (clear, coordinate update, unsort, finalisation).
+// stages around it (k_prepare: clear + coordinate update; k_finish: unsort +
+// finalisation).
 //
 // Cluster-pair kernel (Section 3.2): the M = 8 atoms of the i-cluster stay
 // in registers while the list entries stream past; every entry's j-cluster
@@ -127,8 +128,8 @@ __device__ __forceinline__ void pair_block(const float4* __restrict__ sj, int i,
     }
 }
 
-template <int COUL, bool VIR>
-__global__ void __launch_bounds__(FW * 32)
+template <int COUL, bool VIR, int MINB>
+__global__ void __launch_bounds__(FW * 32, MINB)
 k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     constexpr bool EXACT = COUL == NB_COUL_RF;
     extern __shared__ float2 s_lj[];
@@ -302,33 +303,25 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     }
 }
 
-// Zero the sorted force buffers, the accumulators of every system and the
-// work counters.
-__global__ void k_zero(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys,
-                       int tot_slots, int* __restrict__ counters) {
+// Start of an evaluation: zero the sorted force buffers, the accumulators of
+// every system and the work counters; with COORD, also copy new coordinates
+// into the sorted slots without re-sorting, applying the box multiples
+// recorded by the last grid put (stale-list evaluations).
+template <bool COORD>
+__global__ void k_prepare(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys,
+                          int tot_slots, int* __restrict__ counters) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {
         counters[CNT_WORK] = 0;
         counters[CNT_EWORK] = 0;
     }
     if (t >= tot_slots) return;
-    int c = t / CL;
-    int s = find_sys_dev(cl_off, nsys, c);
+    int s = find_sys_dev(cl_off, nsys, t / CL);
     const SysDev& d = sys[s];
     int slot = t - cl_off[s] * CL;
     d.f_s[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (slot < NACC) d.acc[slot] = 0.0;
-}
-
-// Stale-list evaluation: copy new coordinates into the sorted slots without
-// re-sorting, applying the box multiples recorded by the last grid put.
-__global__ void k_coord_update(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys,
-                               int tot_slots) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tot_slots) return;
-    int s = find_sys_dev(cl_off, nsys, t / CL);
-    const SysDev& d = sys[s];
-    int slot = t - cl_off[s] * CL;
+    if (!COORD) return;
     if (slot >= d.col_cl0[d.ncol] * CL) return;
     int a = d.perm[slot];
     if (a < 0) return;
@@ -343,10 +336,29 @@ __global__ void k_coord_update(const SysDev* __restrict__ sys, const int* __rest
     d.xq_s[slot] = v;
 }
 
-// Forces back to the caller's atom order.
-__global__ void k_unsort(const SysDev* __restrict__ sys, const int* __restrict__ atom_off, int nsys,
+// End of an evaluation: forces back to the caller's atom order and, with
+// ENER_VIR, the final FP64 combination of each system's accumulators.
+template <bool ENER_VIR>
+__global__ void k_finish(const SysDev* __restrict__ sys, const int* __restrict__ atom_off, int nsys,
                          int tot_atoms) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ENER_VIR && t < nsys) {
+        const SysDev& d = sys[t];
+        const double* a = d.acc;
+        double* r = d.res;
+        r[0] = a[ACC_E12] - a[ACC_E6];
+        r[1] = a[ACC_EC] + a[ACC_ECLO];
+        r[2] = -0.5 * a[ACC_VXX];
+        r[3] = -0.5 * a[ACC_VXY];
+        r[4] = -0.5 * a[ACC_VXZ];
+        r[5] = -0.5 * a[ACC_VXY];
+        r[6] = -0.5 * a[ACC_VYY];
+        r[7] = -0.5 * a[ACC_VYZ];
+        r[8] = -0.5 * a[ACC_VXZ];
+        r[9] = -0.5 * a[ACC_VYZ];
+        r[10] = -0.5 * a[ACC_VZZ];
+        r[11] = a[ACC_NPAIR];
+    }
     if (t >= tot_atoms) return;
     int s = find_sys_dev(atom_off, nsys, t);
     const SysDev& d = sys[s];
@@ -357,31 +369,10 @@ __global__ void k_unsort(const SysDev* __restrict__ sys, const int* __restrict__
     d.f_out[3 * a + 2] = f.z;
 }
 
-// Final FP64 combination of the accumulators of each system.
-__global__ void k_energy_final(const SysDev* __restrict__ sys, int nsys) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nsys) return;
-    const SysDev& d = sys[s];
-    const double* a = d.acc;
-    double* r = d.res;
-    r[0] = a[ACC_E12] - a[ACC_E6];
-    r[1] = a[ACC_EC] + a[ACC_ECLO];
-    r[2] = -0.5 * a[ACC_VXX];
-    r[3] = -0.5 * a[ACC_VXY];
-    r[4] = -0.5 * a[ACC_VXZ];
-    r[5] = -0.5 * a[ACC_VXY];
-    r[6] = -0.5 * a[ACC_VYY];
-    r[7] = -0.5 * a[ACC_VYZ];
-    r[8] = -0.5 * a[ACC_VXZ];
-    r[9] = -0.5 * a[ACC_VYZ];
-    r[10] = -0.5 * a[ACC_VZZ];
-    r[11] = a[ACC_NPAIR];
-}
-
-template <int COUL, bool VIR>
+template <int COUL, bool VIR, int MINB>
 cudaError_t launch_forces_t(const PlanLaunch& p, cudaStream_t st) {
     size_t smem = (size_t)p.kp.ntypes * p.kp.ntypes * sizeof(float2);
-    auto kern = k_forces<COUL, VIR>;
+    auto kern = k_forces<COUL, VIR, MINB>;
     int per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FW * 32, smem);
     if (err != cudaSuccess) return err;
@@ -392,34 +383,41 @@ cudaError_t launch_forces_t(const PlanLaunch& p, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t launch_zero_forces(const PlanLaunch& p, cudaStream_t st) {
+cudaError_t launch_prepare(const PlanLaunch& p, bool coords, cudaStream_t st) {
     int tot = p.tot_clcap * CL;
     int bs = 256;
-    k_zero<<<(tot + bs - 1) / bs + 1, bs, 0, st>>>(p.d_sys, p.d_cl_off, p.nsys, tot, p.list.counters);
+    unsigned blocks = (unsigned)((tot + bs - 1) / bs + 1);
+    if (coords)
+        k_prepare<true><<<blocks, bs, 0, st>>>(p.d_sys, p.d_cl_off, p.nsys, tot, p.list.counters);
+    else
+        k_prepare<false><<<blocks, bs, 0, st>>>(p.d_sys, p.d_cl_off, p.nsys, tot, p.list.counters);
     return cudaGetLastError();
 }
 
-cudaError_t launch_coord_update(const PlanLaunch& p, cudaStream_t st) {
-    int tot = p.tot_clcap * CL;
-    if (tot <= 0) return cudaSuccess;
-    int bs = 256;
-    k_coord_update<<<(tot + bs - 1) / bs, bs, 0, st>>>(p.d_sys, p.d_cl_off, p.nsys, tot);
-    return cudaGetLastError();
+template <int COUL, bool VIR>
+cudaError_t launch_forces_v(const PlanLaunch& p, cudaStream_t st) {
+    switch (p.kp.force_min_blocks) {
+        case 1: return launch_forces_t<COUL, VIR, 1>(p, st);
+        case 2: return launch_forces_t<COUL, VIR, 2>(p, st);
+        default: return launch_forces_t<COUL, VIR, 3>(p, st);
+    }
 }
 
 cudaError_t launch_forces(const PlanLaunch& p, unsigned flags, cudaStream_t st) {
     bool vi = flags & NB_F_VIRIAL;
     if (p.kp.coul == NB_COUL_RF)
-        return vi ? launch_forces_t<NB_COUL_RF, true>(p, st) : launch_forces_t<NB_COUL_RF, false>(p, st);
-    return vi ? launch_forces_t<NB_COUL_EWALD, true>(p, st) : launch_forces_t<NB_COUL_EWALD, false>(p, st);
+        return vi ? launch_forces_v<NB_COUL_RF, true>(p, st) : launch_forces_v<NB_COUL_RF, false>(p, st);
+    return vi ? launch_forces_v<NB_COUL_EWALD, true>(p, st) : launch_forces_v<NB_COUL_EWALD, false>(p, st);
 }
 
 cudaError_t launch_finalize(const PlanLaunch& p, unsigned flags, cudaStream_t st) {
     int bs = 256;
-    if (p.tot_atoms > 0)
-        k_unsort<<<(p.tot_atoms + bs - 1) / bs, bs, 0, st>>>(p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms);
+    int n = p.tot_atoms > p.nsys ? p.tot_atoms : p.nsys;
+    unsigned blocks = (unsigned)((n + bs - 1) / bs);
     if (flags & (NB_F_ENERGY | NB_F_VIRIAL))
-        k_energy_final<<<(p.nsys + 127) / 128, 128, 0, st>>>(p.d_sys, p.nsys);
+        k_finish<true><<<blocks, bs, 0, st>>>(p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms);
+    else
+        k_finish<false><<<blocks, bs, 0, st>>>(p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms);
     return cudaGetLastError();
 }
 

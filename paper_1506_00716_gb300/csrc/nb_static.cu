@@ -193,7 +193,7 @@ extern "C" nb_status nb_eval_noalloc(const nb_params* params, int natoms, const 
     NA_CK(launch_grid_put(p, st));
     NA_CK(launch_search(p, st));
     NA_CK(launch_prune(p, st));
-    NA_CK(launch_zero_forces(p, st));
+    NA_CK(launch_prepare(p, false, st));
     NA_CK(launch_forces(p, flags, st));
     if (flags & NB_F_ENERGY) NA_CK(launch_energy(p, st));
     NA_CK(launch_finalize(p, flags, st));

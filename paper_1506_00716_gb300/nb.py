@@ -30,7 +30,7 @@ EXPORTS = ["nb_last_error", "nb_ctx_create", "nb_ctx_destroy", "nb_ctx_memory", 
            "nb_pairlist_info", "nb_forces", "nb_pairlist_export", "nb_batch_create",
            "nb_batch_destroy", "nb_sys_set_coords", "nb_batch_submit", "nb_batch_poll",
            "nb_sys_results", "nb_ctx_set_timing", "nb_ctx_timing", "nb_eval_info",
-           "nb_eval_noalloc"]
+           "nb_eval_noalloc", "nb_ctx_set_tuning", "nb_ctx_get_tuning"]
 NB_NSTAGE = 8
 STAGES = ["grid", "search", "prune", "coord", "zero", "forces", "final", "energy"]
 
@@ -47,6 +47,10 @@ class nb_params(ctypes.Structure):
                 ("ewald_beta", ctypes.c_double), ("fcoul", ctypes.c_double),
                 ("ntypes", ctypes.c_int), ("c6", ctypes.POINTER(ctypes.c_float)),
                 ("c12", ctypes.POINTER(ctypes.c_float))]
+
+
+class nb_tuning(ctypes.Structure):
+    _fields_ = [("max_entries", ctypes.c_int), ("force_min_blocks", ctypes.c_int)]
 
 
 class nb_list_info(ctypes.Structure):
@@ -96,6 +100,8 @@ def load(path: str | None = None):
         "nb_batch_poll": ([_vp, ctypes.c_ulonglong, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)], _st),
         "nb_sys_results": ([_vp, _vp, _vp, _vp], _st),
         "nb_ctx_set_timing": ([_vp, ctypes.c_int], _st),
+        "nb_ctx_set_tuning": ([_vp, ctypes.POINTER(nb_tuning)], _st),
+        "nb_ctx_get_tuning": ([_vp, ctypes.POINTER(nb_tuning)], _st),
         "nb_ctx_timing": ([_vp, _vp, _vp, ctypes.c_int], _st),
         "nb_eval_info": ([_vp, ctypes.POINTER(ctypes.c_longlong)], _st),
         "nb_eval_noalloc": ([ctypes.POINTER(nb_params), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -291,3 +297,14 @@ def nb_eval_noalloc(params, natoms: int, box, excl_index, excl_atoms, xq, type_,
     check(load().nb_eval_noalloc(ctypes.byref(ps), natoms, b, ptr(ei), ptr(ea), ptr(xq), ptr(type_),
                                  ptr(f), ptr(energy), ptr(virial), flags, st))
     del keep
+
+
+def nb_ctx_set_tuning(ctx, max_entries: int = 32, force_min_blocks: int = 3) -> None:
+    t = nb_tuning(int(max_entries), int(force_min_blocks))
+    check(load().nb_ctx_set_tuning(ctx, ctypes.byref(t)))
+
+
+def nb_ctx_get_tuning(ctx) -> dict:
+    t = nb_tuning()
+    check(load().nb_ctx_get_tuning(ctx, ctypes.byref(t)))
+    return {"max_entries": t.max_entries, "force_min_blocks": t.force_min_blocks}

@@ -32,7 +32,8 @@ def torch_cuda():
 
 
 def _systems():
-    return [wb.water_box(m, None, seed=40 + k) for k, m in enumerate([300, 1000, 650, 2400, 120])]
+    # uneven sizes, every box edge >= 2 rlist (>= 400 molecules at 33.4 / nm^3)
+    return [wb.water_box(m, None, seed=40 + k) for k, m in enumerate([400, 1000, 650, 2400, 520])]
 
 
 def _run_batch(ctx, systems, params, submits=2):
