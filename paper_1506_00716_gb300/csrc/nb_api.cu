@@ -16,11 +16,11 @@
 #include <thread>
 #include <vector>
 
-#include "nb_internal.cuh"
+#include "nb_host.h"
 
 using namespace nbgb;
 
-namespace {
+namespace nbgb {
 
 thread_local std::string g_err;
 
@@ -49,10 +49,7 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-struct Geometry {
-    int ncx, ncy, ncol, clcap;
-    float cw[2], icw[2];
-};
+
 
 Geometry make_geometry(int natoms, const double box[3]) {
     Geometry g;
@@ -85,77 +82,9 @@ void list_estimate(const nb_params& p, int natoms, const double box[3], int clca
     *entries = (long long)(clcap * (per_cl * 1.35 + 8.0) * std::max(1.0, shift / 4.0)) + 4096;
 }
 
-}  // namespace
+}  // namespace nbgb
 
-struct Plan;
-
-struct TimedLaunch {
-    int stage;
-    cudaEvent_t a, b;
-};
-
-struct nb_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    size_t budget = 0;
-    size_t in_use = 0;
-    int num_sms = 0;
-    bool timing = false;
-    bool capturing = false;
-    nb_tuning tuning{32, 3};
-    unsigned tuning_gen = 0;
-    std::vector<TimedLaunch> pending;
-    std::vector<cudaEvent_t> pool;
-    double tot_ms[NB_NSTAGE] = {0};
-    long long launches[NB_NSTAGE] = {0};
-};
-
-struct nb_sys {
-    nb_ctx* ctx = nullptr;
-    nb_params p{};
-    std::vector<float> c6, c12;
-    int natoms = 0;
-    double box[3] = {0, 0, 0};
-    Geometry geo{};
-    SysDev h{};              // descriptor (device pointers)
-    void* block = nullptr;   // one allocation holding all per-system buffers
-    size_t bytes = 0;
-    int* d_excl = nullptr;   // exclusion CSR (index then atoms)
-    size_t excl_bytes = 0;
-    float2* d_lj = nullptr;
-    Plan* plan = nullptr;    // standalone plan (lazy)
-    bool has_coords = false;
-    bool gridded = false;
-    bool listed = false;
-};
-
-struct Plan {
-    nb_ctx* ctx = nullptr;
-    std::vector<nb_sys*> systems;
-    SysDev* d_sys = nullptr;
-    int* d_off = nullptr;     // atom, col, cl prefix arrays (3 * (nsys + 1))
-    ListDev list{};
-    void* list_block = nullptr;
-    size_t list_bytes = 0;
-    size_t fixed_bytes = 0;
-    int tot_atoms = 0, tot_cols = 0, tot_clcap = 0;
-    long long item_cap = 0, entry_cap = 0;
-    int* h_counters = nullptr;  // pinned readback
-    KParams kp{};
-    // graph state (batches)
-    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
-    unsigned graph_tuning_gen = 0;
-    cudaEvent_t done_ev = nullptr;
-    unsigned long long ticket = 0;
-    unsigned long long done_ticket = 0;
-};
-
-struct nb_batch {
-    nb_ctx* ctx = nullptr;
-    Plan* plan = nullptr;
-};
-
-namespace {
+namespace nbgb {
 
 cudaEvent_t pool_event(nb_ctx* c) {
     if (!c->pool.empty()) {
@@ -546,7 +475,7 @@ size_t plan_bytes_estimate(const nb_params* p, int natoms, const double box[3], 
     return align256(16 * (size_t)it) + align256(12 * (size_t)en) + 4096;
 }
 
-}  // namespace
+}  // namespace nbgb
 
 // Helpers shared with the allocation-free entry point (nb_static.cu).
 namespace nbgb {
@@ -767,24 +696,37 @@ nb_status nb_set_exclusions(nb_sys* sys, const int* excl_index, const int* excl_
     if (!excl_index) return fail(NB_ERR_ARG, "excl_index is NULL");
     int n = sys->natoms;
     if (excl_index[0] != 0) return fail(NB_ERR_ARG, "excl_index[0] must be 0");
-    std::vector<std::vector<int>> adj(n);
+    // symmetrise with flat arrays: degree count, prefix, fill, then sort and
+    // de-duplicate each atom's (short) partner list
+    std::vector<int> deg(n + 1, 0);
     for (int a = 0; a < n; ++a) {
         if (excl_index[a + 1] < excl_index[a]) return fail(NB_ERR_ARG, "excl_index must be non-decreasing");
         for (int k = excl_index[a]; k < excl_index[a + 1]; ++k) {
             int b = excl_atoms[k];
             if (b < 0 || b >= n) return fail(NB_ERR_ARG, "exclusion partner out of range");
             if (b == a) continue;
-            adj[a].push_back(b);
-            adj[b].push_back(a);
+            ++deg[a + 1];
+            ++deg[b + 1];
         }
     }
+    for (int a = 0; a < n; ++a) deg[a + 1] += deg[a];
+    std::vector<int> fillp(deg.begin(), deg.end() - 1), flat(deg[n]);
+    for (int a = 0; a < n; ++a)
+        for (int k = excl_index[a]; k < excl_index[a + 1]; ++k) {
+            int b = excl_atoms[k];
+            if (b == a) continue;
+            flat[fillp[a]++] = b;
+            flat[fillp[b]++] = a;
+        }
     std::vector<int> idx(n + 1, 0), at;
+    at.reserve(flat.size());
     for (int a = 0; a < n; ++a) {
-        auto& v = adj[a];
-        std::sort(v.begin(), v.end());
-        v.erase(std::unique(v.begin(), v.end()), v.end());
-        idx[a + 1] = idx[a] + (int)v.size();
-        at.insert(at.end(), v.begin(), v.end());
+        int* first = flat.data() + deg[a];
+        int* last = flat.data() + deg[a + 1];
+        std::sort(first, last);
+        int* end_u = std::unique(first, last);
+        at.insert(at.end(), first, end_u);
+        idx[a + 1] = (int)at.size();
     }
     if (sys->d_excl) dev_free(sys->ctx, sys->d_excl, sys->excl_bytes);
     sys->d_excl = nullptr;

@@ -23,7 +23,12 @@
 // distance of the float32 inputs decides pairs near rc), so the counted pair
 // set is the oracle's.  The work distribution is the force kernel's: a
 // persistent grid over the (i-cluster, shift) items, four entries in flight
-// per warp, j-clusters staged in shared memory.
+// per warp, j-clusters staged in shared memory.  Only about a third of the
+// 8 x 8 pair slots lie inside rc, so each warp first screens its slots in
+// float32 and pushes the pairs inside rc (or within the band around it,
+// decided exactly later) into a ring queue in shared memory as (j slot,
+// i-slot) records; the double-float evaluation then takes 32 queued pairs
+// at a time, one per lane, with no idle lanes.
 #include "erfc_fit.cuh"
 #include "nb_device.cuh"
 
@@ -101,11 +106,14 @@ __device__ __forceinline__ void erfc_dd(float xh, float xl, float ah, float al, 
     el = cl * scale;
 }
 
+// Energy of one queued pair.  `valid`: the lane holds a pair; `maybe`: its
+// float32 r^2 fell in the band around rc^2 and the decision is taken here,
+// exactly; otherwise the pair is inside rc.
 template <int COUL>
 __device__ __forceinline__ void pair_energy(const float4 xj, int tj, const ShiftedI& xs, float qih,
                                             float qil, int tirow, const float2* __restrict__ s_lj,
-                                            bool bit, const KParams& kp, float& ch, float& cl,
-                                            float& e12, float& e6, int& npair) {
+                                            bool valid, bool maybe, const KParams& kp, float& ch,
+                                            float& cl, float& e12, float& e6, int& npair) {
     float dxh, dxe, dyh, dye, dzh, dze;
     two_sum(xs.xh, -xj.x, dxh, dxe);
     two_sum(xs.yh, -xj.y, dyh, dye);
@@ -123,9 +131,8 @@ __device__ __forceinline__ void pair_energy(const float4 xj, int tj, const Shift
     two_sum(s1, pz, r2h, e2);
     const float r2l = (e1 + e2) + (ex + (ey + ez));
 
-    bool in = bit && r2h < kp.rc2_lo;
-    const bool maybe = bit && !in && r2h < kp.rc2_hi;
-    if (maybe) in = exact_inside(xs, xj, kp.rc2_d);
+    bool in = valid;
+    if (valid && maybe) in = exact_inside(xs, xj, kp.rc2_d);
     npair += __popc(__ballot_sync(FULL, in));
 
     // 1/r = y (1 + h/2), h = 1 - r^2 y^2
@@ -210,11 +217,38 @@ __device__ __forceinline__ void flush_energy(const SysDev* __restrict__ sys, int
     np = 0;
 }
 
+constexpr int QCAP = 512;  // per-warp ring queue of candidate pairs (>= 31 + 8 * 32)
+
+// i-atom data of the current item, one record per i-slot (shared by the
+// lanes that evaluate queued pairs).
+struct IRec {
+    ShiftedI xs;
+    float qih, qil;
+    int tirow;
+};
+
+// Queue entry: j slot index << 4 | i-slot << 1 | band flag.
+template <int COUL>
+__device__ __forceinline__ void drain(int k, const int* __restrict__ qm, const IRec* __restrict__ irec,
+                                      const float4* __restrict__ xq_s, const int* __restrict__ type_s,
+                                      const float2* __restrict__ s_lj, const KParams& kp, float& ch,
+                                      float& cl, float& e12, float& e6, int& npair, bool valid) {
+    const int m = valid ? qm[k & (QCAP - 1)] : 0;
+    const int js = m >> 4;
+    const float4 xj = valid ? xq_s[js] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int tj = valid ? type_s[js] : 0;
+    const IRec& ir = irec[(m >> 1) & 7];
+    pair_energy<COUL>(xj, tj, ir.xs, ir.qih, ir.qil, ir.tirow, s_lj, valid, m & 1, kp, ch, cl, e12, e6,
+                      npair);
+}
+
 template <int COUL>
 __global__ void __launch_bounds__(EW * 32)
 k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     extern __shared__ float2 s_lj[];
     __shared__ __align__(16) float4 s_j[EW][4][2 * CL];
+    __shared__ int s_qm[EW][QCAP];
+    __shared__ IRec s_irec[EW][CL];
 
     const int lane = threadIdx.x & 31;
     const int i = lane & 7;
@@ -225,6 +259,8 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     __syncthreads();
 
     float4* sjg = &s_j[w][g][0];
+    int* qm = s_qm[w];
+    IRec* irec = s_irec[w];
     const int nitems = min(list.counters[CNT_ITEMS], list.item_cap);
     int cur_sys = -1;
     const float4* xq_s = nullptr;
@@ -254,48 +290,71 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         if (jb >= je) continue;
         const float4 xi4 = xq_s[ci * CL + i];
         const ShiftedI xs = shift_i(xi4, sh, Lx, Ly, Lz);
-        float qih, qie;
-        two_prod(kp.fq_h, xi4.w, qih, qie);
-        const float qil = fmaf(kp.fq_l, xi4.w, qie);
-        const int tirow = type_s[ci * CL + i] * nt;
+        __syncwarp();
+        if (g == 0) {
+            IRec r;
+            r.xs = xs;
+            two_prod(kp.fq_h, xi4.w, r.qih, r.qil);
+            r.qil = fmaf(kp.fq_l, xi4.w, r.qil);
+            r.tirow = type_s[ci * CL + i] * nt;
+            irec[i] = r;
+        }
 
         float ch = 0.f, cl = 0.f, e12 = 0.f, e6 = 0.f;
         int npair = 0;
+        int head = 0, tail = 0;  // ring positions, identical in every lane
 
         int e = jb + g;
         bool act = e < je;
         unsigned long long pm = 0ull;
+        int pj = 0;
         float4 pxq = make_float4(0.f, 0.f, 0.f, 0.f);
-        int pty = 0;
         if (act) {
-            const int cjn = list.cj[e];
+            pj = list.cj[e] * CL;
             pm = list.mask[e];
-            pxq = xq_s[cjn * CL + i];
-            pty = type_s[cjn * CL + i];
+            pxq = xq_s[pj + i];
         }
         for (int base = jb; base < je; base += 4) {
             __syncwarp();
             sjg[i] = pxq;
-            sjg[CL + i] = make_float4(__int_as_float(pty), 0.f, 0.f, 0.f);
+            const int cj0 = pj;
             const unsigned long long cm = pm;
             e = base + 4 + g;
             act = e < je;
             pm = 0ull;
             if (act) {
-                const int cjn = list.cj[e];
+                pj = list.cj[e] * CL;
                 pm = list.mask[e];
-                pxq = xq_s[cjn * CL + i];
-                pty = type_s[cjn * CL + i];
+                pxq = xq_s[pj + i];
             }
             __syncwarp();
             const unsigned row = (unsigned)(cm >> (8 * i)) & 0xffu;
 #pragma unroll
             for (int t = 0; t < CL; ++t) {
                 const int js = t ^ i;
-                pair_energy<COUL>(sjg[js], __float_as_int(sjg[CL + js].x), xs, qih, qil, tirow, s_lj,
-                                  (row >> t) & 1u, kp, ch, cl, e12, e6, npair);
+                const float4 xj = sjg[js];
+                const float dx = xs.xh - xj.x, dy = xs.yh - xj.y, dz = xs.zh - xj.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const bool bit = (row >> t) & 1u;
+                const bool in = bit && r2 < kp.rc2_lo;
+                const bool maybe = bit && !in && r2 < kp.rc2_hi;
+                const bool q = in || maybe;
+                const unsigned bal = __ballot_sync(FULL, q);
+                if (q) {
+                    const int pos = (tail + __popc(bal & ((1u << lane) - 1u))) & (QCAP - 1);
+                    qm[pos] = ((cj0 + js) << 4) | (i << 1) | (int)maybe;
+                }
+                tail += __popc(bal);
+            }
+            __syncwarp();
+            while (tail - head >= 32) {
+                drain<COUL>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e6, npair, true);
+                head += 32;
             }
         }
+        if (tail > head)
+            drain<COUL>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e6, npair,
+                        lane < tail - head);
         dec += (double)ch + (double)cl;
         d12 += (double)e12;
         d6 += (double)e6;

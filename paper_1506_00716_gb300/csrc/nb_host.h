@@ -1,0 +1,104 @@
+// nb_host.h -- host-side state of the library (contexts, systems, plans)
+// and the helpers of nb_api.cu that other translation units use (the
+// serving engine).  Not part of the public ABI.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "nb_internal.cuh"
+
+namespace nbgb {
+
+struct Geometry {
+    int ncx, ncy, ncol, clcap;
+    float cw[2], icw[2];
+};
+
+}  // namespace nbgb
+
+struct Plan;
+using nbgb::Geometry;
+
+struct TimedLaunch {
+    int stage;
+    cudaEvent_t a, b;
+};
+
+struct nb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;
+    size_t in_use = 0;
+    int num_sms = 0;
+    bool timing = false;
+    bool capturing = false;
+    nb_tuning tuning{32, 3};
+    unsigned tuning_gen = 0;
+    std::vector<TimedLaunch> pending;
+    std::vector<cudaEvent_t> pool;
+    double tot_ms[NB_NSTAGE] = {0};
+    long long launches[NB_NSTAGE] = {0};
+};
+
+struct nb_sys {
+    nb_ctx* ctx = nullptr;
+    nb_params p{};
+    std::vector<float> c6, c12;
+    int natoms = 0;
+    double box[3] = {0, 0, 0};
+    nbgb::Geometry geo{};
+    nbgb::SysDev h{};              // descriptor (device pointers)
+    void* block = nullptr;   // one allocation holding all per-system buffers
+    size_t bytes = 0;
+    int* d_excl = nullptr;   // exclusion CSR (index then atoms)
+    size_t excl_bytes = 0;
+    float2* d_lj = nullptr;
+    Plan* plan = nullptr;    // standalone plan (lazy)
+    bool has_coords = false;
+    bool gridded = false;
+    bool listed = false;
+};
+
+struct Plan {
+    nb_ctx* ctx = nullptr;
+    std::vector<nb_sys*> systems;
+    nbgb::SysDev* d_sys = nullptr;
+    int* d_off = nullptr;     // atom, col, cl prefix arrays (3 * (nsys + 1))
+    nbgb::ListDev list{};
+    void* list_block = nullptr;
+    size_t list_bytes = 0;
+    size_t fixed_bytes = 0;
+    int tot_atoms = 0, tot_cols = 0, tot_clcap = 0;
+    long long item_cap = 0, entry_cap = 0;
+    int* h_counters = nullptr;  // pinned readback
+    nbgb::KParams kp{};
+    // graph state (batches)
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    unsigned graph_tuning_gen = 0;
+    cudaEvent_t done_ev = nullptr;
+    unsigned long long ticket = 0;
+    unsigned long long done_ticket = 0;
+};
+
+struct nb_batch {
+    nb_ctx* ctx = nullptr;
+    Plan* plan = nullptr;
+};
+
+namespace nbgb {
+
+nb_status fail(nb_status s, const std::string& msg);
+nb_status cuda_fail(cudaError_t e, const char* what);
+bool is_device_ptr(const void* p);
+Geometry make_geometry(int natoms, const double box[3]);
+void list_estimate(const nb_params& p, int natoms, const double box[3], int clcap, long long* items,
+                   long long* entries);
+nb_status dev_alloc(nb_ctx* ctx, void** ptr, size_t bytes);
+void dev_free(nb_ctx* ctx, void* ptr, size_t bytes);
+nb_status plan_create(nb_ctx* ctx, nb_sys* const* systems, int n, Plan** out);
+void plan_destroy(Plan* pl);
+PlanLaunch launch_of(const Plan* pl);
+nb_status stage_coords(nb_sys* s, const float* xq, const int* type);
+
+}  // namespace nbgb

@@ -47,18 +47,24 @@ __device__ unsigned long long diag_mask() {
     return m;
 }
 
-// bits of pairs with i < ni and j < nj
-__device__ unsigned long long real_mask(int ni, int nj) {
+// bits of pairs with j < nj (all i), and with i < ni (all j)
+__device__ unsigned long long col_mask(int nj) {
     unsigned long long m = 0;
-    for (int i = 0; i < ni; ++i)
+    for (int i = 0; i < CL; ++i)
         for (int j = 0; j < nj; ++j) m |= 1ull << rot_bit(i, j);
     return m;
 }
+__device__ __forceinline__ unsigned long long row_mask(int ni) {
+    return ni >= CL ? ~0ull : ((1ull << (8 * ni)) - 1ull);
+}
+
+constexpr int MAX_RUNS = 32;
 
 struct SearchWarpSmem {
     int cj[SEARCH_BUF];
     unsigned long long mask[SEARCH_BUF];
-    unsigned char sh[SEARCH_BUF];
+    int run_start[MAX_RUNS];
+    int run_shift[MAX_RUNS];
     int ex_slot[EXCL_BUF];
     unsigned char ex_i[EXCL_BUF];
     int n_ex;
@@ -68,24 +74,25 @@ __device__ __forceinline__ float gap(float alo, float ahi, float blo, float bhi)
     return fmaxf(0.f, fmaxf(blo - ahi, alo - bhi));
 }
 
-// Write the buffered entries as work items: one per run of equal shift,
-// split into pieces of at most max_entries entries.
-__device__ void flush(SearchWarpSmem& sm, int nbuf, int ci, int sid, const ListDev& list, int lane,
-                      int max_entries) {
+// Write the buffered entries as work items: one per run of equal shift
+// (runs are recorded while appending), split into pieces of at most
+// max_entries entries.
+__device__ void flush(SearchWarpSmem& sm, int nbuf, int nruns, int ci, int sid, const ListDev& list,
+                      int lane, int max_entries) {
     if (nbuf == 0) return;
-    // items per run start, and their total
-    int nitems = 0;
-    for (int base = 0; base < nbuf; base += 32) {
-        int k = base + lane;
-        int nch = 0;
-        if (k < nbuf && (k == 0 || sm.sh[k] != sm.sh[k - 1])) {
-            int e = k + 1;
-            while (e < nbuf && sm.sh[e] == sm.sh[k]) ++e;
-            nch = (e - k + max_entries - 1) / max_entries;
-        }
-        for (int off = 16; off > 0; off >>= 1) nch += __shfl_xor_sync(FULL, nch, off);
-        nitems += nch;
+    int nch = 0, rs = 0, re = 0;
+    if (lane < nruns) {
+        rs = sm.run_start[lane];
+        re = lane + 1 < nruns ? sm.run_start[lane + 1] : nbuf;
+        nch = (re - rs + max_entries - 1) / max_entries;
     }
+    int incl = nch;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int v = __shfl_up_sync(FULL, incl, off);
+        if (lane >= off) incl += v;
+    }
+    const int nitems = __shfl_sync(FULL, incl, 31);
     int ibase = 0, ebase = 0;
     if (lane == 0) {
         ibase = atomicAdd(list.counters + CNT_ITEMS, nitems);
@@ -93,8 +100,8 @@ __device__ void flush(SearchWarpSmem& sm, int nbuf, int ci, int sid, const ListD
     }
     ibase = __shfl_sync(FULL, ibase, 0);
     ebase = __shfl_sync(FULL, ebase, 0);
-    bool ok_e = (long long)ebase + nbuf <= list.entry_cap;
-    bool ok_i = (long long)ibase + nitems <= list.item_cap;
+    const bool ok_e = (long long)ebase + nbuf <= list.entry_cap;
+    const bool ok_i = (long long)ibase + nitems <= list.item_cap;
     if (lane == 0 && !ok_e) atomicOr(list.counters + CNT_OVERFLOW, 2);
     if (lane == 0 && !ok_i) atomicOr(list.counters + CNT_OVERFLOW, 1);
     if (ok_e) {
@@ -103,31 +110,14 @@ __device__ void flush(SearchWarpSmem& sm, int nbuf, int ci, int sid, const ListD
             list.mask[ebase + k] = sm.mask[k];
         }
     }
-    if (ok_i) {
+    if (ok_i && lane < nruns) {
         // on entry overflow the items are still written, empty, so that the
         // counted item range never holds stale data
-        int ord = 0;
-        for (int base = 0; base < nbuf; base += 32) {
-            int k = base + lane;
-            int e = k, nch = 0;
-            if (k < nbuf && (k == 0 || sm.sh[k] != sm.sh[k - 1])) {
-                e = k + 1;
-                while (e < nbuf && sm.sh[e] == sm.sh[k]) ++e;
-                nch = (e - k + max_entries - 1) / max_entries;
-            }
-            int incl = nch;
-            for (int off = 1; off < 32; off <<= 1) {
-                int v = __shfl_up_sync(FULL, incl, off);
-                if (lane >= off) incl += v;
-            }
-            int idx = ibase + ord + incl - nch;
-            for (int q = 0; q < nch; ++q) {
-                int a = k + q * max_entries;
-                int b = min(e, a + max_entries);
-                list.items[idx + q] = ok_e ? make_int4(ci, ebase + a, ebase + b, (sid << 5) | sm.sh[k])
-                                           : make_int4(ci, 0, 0, (sid << 5) | sm.sh[k]);
-            }
-            ord += __shfl_sync(FULL, incl, 31);
+        const int w = (sid << 5) | sm.run_shift[lane];
+        int idx = ibase + incl - nch;
+        for (int a = rs; a < re; a += max_entries, ++idx) {
+            const int b = min(re, a + max_entries);
+            list.items[idx] = ok_e ? make_int4(ci, ebase + a, ebase + b, w) : make_int4(ci, 0, 0, w);
         }
     }
     __syncwarp();
@@ -137,6 +127,11 @@ __global__ void __launch_bounds__(SEARCH_WARPS * 32)
 k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys, int tot_clcap,
          ListDev list, KParams kp) {
     __shared__ SearchWarpSmem s_w[SEARCH_WARPS];
+    __shared__ unsigned long long s_colmask[CL + 1];
+    __shared__ unsigned long long s_diag;
+    if (threadIdx.x <= CL) s_colmask[threadIdx.x] = col_mask(threadIdx.x);
+    if (threadIdx.x == 32) s_diag = diag_mask();
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int gw = blockIdx.x * SEARCH_WARPS + w;
@@ -151,18 +146,21 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
     const float4 lo_i = d.bb[2 * ci];
     const float4 hi_i = d.bb[2 * ci + 1];
     const int nri = (int)lo_i.w;
+    const unsigned long long rmask_i = row_mask(nri);
     const float rl = kp.rl_search;
     const float rl2 = rl * rl;
     const float eps = 1e-5f * fmaxf(1.f, fmaxf(d.L[0], fmaxf(d.L[1], d.L[2])));
 
-    // cache the exclusion partners (as sorted slots) of this cluster's atoms
+    // exclusion partners (sorted slots) of this cluster's atoms, and a
+    // 64-bit filter of their clusters for a quick test of each candidate
     if (lane == 0) sm.n_ex = 0;
     __syncwarp();
-    bool ex_overflow = false;
+    unsigned long long xfilter = 0;
     if (d.excl_index != nullptr && lane < nri) {
         int a = d.perm[ci * CL + lane];
         for (int e = d.excl_index[a]; e < d.excl_index[a + 1]; ++e) {
             int p = d.iperm[d.excl_atoms[e]];
+            xfilter |= 1ull << ((p >> 3) & 63);
             int k = atomicAdd(&sm.n_ex, 1);
             if (k < EXCL_BUF) {
                 sm.ex_slot[k] = p;
@@ -170,12 +168,13 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
             }
         }
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) xfilter |= __shfl_xor_sync(FULL, xfilter, off);
     __syncwarp();
     const int n_ex = min(sm.n_ex, EXCL_BUF);
-    ex_overflow = sm.n_ex > EXCL_BUF;
-    const unsigned long long dmask = diag_mask();
+    const bool ex_overflow = sm.n_ex > EXCL_BUF;
 
-    int nbuf = 0;
+    int nbuf = 0, nruns = 0;
     for (int sx = -1; sx <= 1; ++sx) {
         if (sx == 1 && !(lo_i.x < rl)) continue;
         if (sx == -1 && !(hi_i.x > d.L[0] - rl)) continue;
@@ -189,93 +188,123 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
                 const float Sx = sx * d.L[0], Sy = sy * d.L[1], Sz = sz * d.L[2];
                 const float lx = lo_i.x + Sx, ly = lo_i.y + Sy, lz = lo_i.z + Sz;
                 const float hx = hi_i.x + Sx, hy = hi_i.y + Sy, hz = hi_i.z + Sz;
-                int cx0 = max(0, (int)floorf((lx - rl) * d.icw[0]) - 1);
-                int cx1 = min(d.ncx - 1, (int)floorf((hx + rl) * d.icw[0]) + 1);
-                int cy0 = max(0, (int)floorf((ly - rl) * d.icw[1]) - 1);
-                int cy1 = min(d.ncy - 1, (int)floorf((hy + rl) * d.icw[1]) + 1);
+                const int cx0 = max(0, (int)floorf((lx - rl) * d.icw[0]) - 1);
+                const int cx1 = min(d.ncx - 1, (int)floorf((hx + rl) * d.icw[0]) + 1);
+                const int cy0 = max(0, (int)floorf((ly - rl) * d.icw[1]) - 1);
+                const int cy1 = min(d.ncy - 1, (int)floorf((hy + rl) * d.icw[1]) + 1);
                 if (cx0 > cx1 || cy0 > cy1) continue;
                 const int nyc = cy1 - cy0 + 1;
                 const int ncand = (cx1 - cx0 + 1) * nyc;
                 const float zmin = lz - rl, zmax = hz + rl;
+                bool run_open = false;
                 for (int cbase = 0; cbase < ncand; cbase += 32) {
-                    int k = cbase + lane;
-                    bool has = k < ncand;
-                    int cur = 0, cend = 0;
-                    if (has) {
-                        int cx = cx0 + k / nyc, cy = cy0 + k % nyc;
-                        float fx0 = cx * d.cw[0] - eps, fx1 = (cx + 1) * d.cw[0] + eps;
-                        float fy0 = cy * d.cw[1] - eps, fy1 = (cy + 1) * d.cw[1] + eps;
-                        float gx = gap(lx, hx, fx0, fx1), gy = gap(ly, hy, fy0, fy1);
-                        if (gx * gx + gy * gy >= rl2) has = false;
-                        if (has) {
-                            int col = cx * d.ncy + cy;
-                            int c0 = d.col_cl0[col], c1 = d.col_cl0[col + 1];
-                            // first cluster whose top is at or above zmin
-                            int a = c0, b = c1;
+                    // each lane: one candidate column, its z-window of clusters
+                    const int k = cbase + lane;
+                    int c0 = 0, cnt = 0;
+                    if (k < ncand) {
+                        const int cx = cx0 + k / nyc, cy = cy0 + k % nyc;
+                        const float fx0 = cx * d.cw[0] - eps, fx1 = (cx + 1) * d.cw[0] + eps;
+                        const float fy0 = cy * d.cw[1] - eps, fy1 = (cy + 1) * d.cw[1] + eps;
+                        const float gx = gap(lx, hx, fx0, fx1), gy = gap(ly, hy, fy0, fy1);
+                        if (gx * gx + gy * gy < rl2) {
+                            const int col = cx * d.ncy + cy;
+                            const int a0 = d.col_cl0[col], b0 = d.col_cl0[col + 1];
+                            int a = a0, b = b0;  // first cluster with top >= zmin
                             while (a < b) {
-                                int m = (a + b) >> 1;
+                                const int m = (a + b) >> 1;
                                 if (d.bb[2 * m + 1].z < zmin) a = m + 1; else b = m;
                             }
-                            cur = a;
-                            cend = c1;
+                            int u = a, v = b0;  // first cluster with bottom > zmax
+                            while (u < v) {
+                                const int m = (u + v) >> 1;
+                                if (d.bb[2 * m].z <= zmax) u = m + 1; else v = m;
+                            }
+                            c0 = a;
+                            cnt = u - a;
                         }
                     }
-                    for (;;) {
-                        bool cand = has && cur < cend;
-                        float4 lj = make_float4(0.f, 0.f, 0.f, 0.f), hj;
-                        if (cand) {
-                            lj = d.bb[2 * cur];
-                            if (lj.z > zmax) { cand = false; has = false; }
+                    int incl = cnt;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int vv = __shfl_up_sync(FULL, incl, off);
+                        if (lane >= off) incl += vv;
+                    }
+                    const int total = __shfl_sync(FULL, incl, 31);
+                    // lanes stride over the flattened candidates of the 32 columns
+                    for (int t0 = 0; t0 < total; t0 += 32) {
+                        const int t = t0 + lane;
+                        // owner lane: first lane whose inclusive count exceeds t
+                        int lo = 0;
+#pragma unroll
+                        for (int step = 16; step > 0; step >>= 1) {
+                            const int probe = __shfl_sync(FULL, incl, lo + step - 1);
+                            if (probe <= t) lo += step;
                         }
-                        if (!__any_sync(FULL, cand)) break;
+                        const int own_incl = __shfl_sync(FULL, incl, lo);
+                        const int own_cnt = __shfl_sync(FULL, cnt, lo);
+                        const int own_c0 = __shfl_sync(FULL, c0, lo);
+                        const int cur = own_c0 + t - (own_incl - own_cnt);
                         bool pass = false;
-                        if (cand) {
-                            hj = d.bb[2 * cur + 1];
-                            float gx = gap(lx, hx, lj.x, hj.x);
-                            float gy = gap(ly, hy, lj.y, hj.y);
-                            float gz = gap(lz, hz, lj.z, hj.z);
+                        float4 lj = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (t < total) {
+                            lj = d.bb[2 * cur];
+                            const float4 hj = d.bb[2 * cur + 1];
+                            const float gx = gap(lx, hx, lj.x, hj.x);
+                            const float gy = gap(ly, hy, lj.y, hj.y);
+                            const float gz = gap(lz, hz, lj.z, hj.z);
                             pass = gx * gx + gy * gy + gz * gz < rl2 &&
                                    (cur > ci || (cur == ci && shift >= SHIFT_ZERO));
                         }
-                        unsigned bal = __ballot_sync(FULL, pass);
-                        int np = __popc(bal);
-                        if (nbuf + np > SEARCH_BUF) {
-                            flush(sm, nbuf, ci, sid, list, lane, kp.max_entries);
+                        const unsigned bal = __ballot_sync(FULL, pass);
+                        const int np = __popc(bal);
+                        if (np == 0) continue;
+                        if (nbuf + np > SEARCH_BUF || (!run_open && nruns == MAX_RUNS)) {
+                            flush(sm, nbuf, nruns, ci, sid, list, lane, kp.max_entries);
                             nbuf = 0;
+                            nruns = 0;
+                            run_open = false;
+                        }
+                        if (!run_open) {
+                            if (lane == 0) {
+                                sm.run_start[nruns] = nbuf;
+                                sm.run_shift[nruns] = shift;
+                            }
+                            ++nruns;
+                            run_open = true;
                         }
                         if (pass) {
                             unsigned long long m = ~0ull;
-                            if (cur == ci && shift == SHIFT_ZERO) m = dmask;
-                            int nrj = (int)lj.w;
-                            if (nri < CL || nrj < CL) m &= real_mask(nri, nrj);
-                            if (!ex_overflow) {
-                                for (int q = 0; q < n_ex; ++q) {
-                                    int p = sm.ex_slot[q];
-                                    if ((p >> 3) == cur) m &= ~(1ull << rot_bit(sm.ex_i[q], p & 7));
-                                }
-                            } else {
-                                for (int ii = 0; ii < nri; ++ii) {
-                                    int a = d.perm[ci * CL + ii];
-                                    for (int e = d.excl_index[a]; e < d.excl_index[a + 1]; ++e) {
-                                        int p = d.iperm[d.excl_atoms[e]];
-                                        if ((p >> 3) == cur) m &= ~(1ull << rot_bit(ii, p & 7));
+                            if (cur == ci && shift == SHIFT_ZERO) m = s_diag;
+                            const int nrj = (int)lj.w;
+                            m &= rmask_i & s_colmask[nrj];
+                            if ((xfilter >> (cur & 63)) & 1ull) {
+                                if (!ex_overflow) {
+                                    for (int q = 0; q < n_ex; ++q) {
+                                        const int p = sm.ex_slot[q];
+                                        if ((p >> 3) == cur) m &= ~(1ull << rot_bit(sm.ex_i[q], p & 7));
+                                    }
+                                } else {
+                                    for (int ii = 0; ii < nri; ++ii) {
+                                        const int a = d.perm[ci * CL + ii];
+                                        for (int e = d.excl_index[a]; e < d.excl_index[a + 1]; ++e) {
+                                            const int p = d.iperm[d.excl_atoms[e]];
+                                            if ((p >> 3) == cur) m &= ~(1ull << rot_bit(ii, p & 7));
+                                        }
                                     }
                                 }
                             }
-                            int idx = nbuf + __popc(bal & ((1u << lane) - 1u));
+                            const int idx = nbuf + __popc(bal & ((1u << lane) - 1u));
                             sm.cj[idx] = cur;
                             sm.mask[idx] = m;
-                            sm.sh[idx] = (unsigned char)shift;
                         }
                         nbuf += np;
                         __syncwarp();
-                        if (cand) ++cur;
                     }
                 }
             }
         }
     }
-    flush(sm, nbuf, ci, sid, list, lane, kp.max_entries);
+    flush(sm, nbuf, nruns, ci, sid, list, lane, kp.max_entries);
 }
 
 constexpr int PRUNE_WARPS = 8;
