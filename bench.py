@@ -463,6 +463,166 @@ def run_large(args) -> dict:
     }
 
 
+def _batch_eval(nb, b, flags, timeout_us=60_000_000):
+    """Submit a batch and wait; a list that outgrew its buffer (the library
+    grows it and says so) is submitted once more."""
+    for attempt in range(3):
+        try:
+            return nb.nb_batch_poll(b, nb.nb_batch_submit(b, flags), timeout_us)
+        except nb.NbError as exc:
+            if exc.status != 9 or attempt == 2:  # NB_ERR_CAPACITY
+                raise
+    return False
+
+
+def run_ensemble(args) -> dict:
+    """64 independent boxes (1,000-32,000 waters, log-uniform), LJ + RF: one
+    batched submission (one launch per stage, CUDA graph) against 64 plain
+    per-system evaluations, both with energies and virial."""
+    import torch
+
+    from paper_1506_00716_gb300 import autotune, nb
+    from paper_1506_00716_gb300 import build as nbbuild
+
+    torch.cuda.set_device(0)
+    nbbuild.build()
+    stream = torch.cuda.Stream()
+    systems = wb.ensemble(64, 1000, 32000, seed=4)
+    p = wb.params_rf()
+    flags = nb.NB_F_ENERGY | nb.NB_F_VIRIAL
+    ctx = nb.nb_ctx_create(0, stream.cuda_stream, 0)
+    tot_atoms = sum(x.n for x in systems)
+    tuning = autotune.apply(ctx, "rf", tot_atoms // len(systems), gpu=torch.cuda.get_device_name(0))
+    hs = []
+    for x in systems:
+        h = nb.nb_sys_create(ctx, p, x.n, x.box)
+        nb.nb_set_exclusions(h, x.excl_index, x.excl_atoms)
+        nb.nb_sys_set_coords(h, x.xq(), x.type)
+        hs.append(h)
+    dev_in = [(torch.from_numpy(x.xq()).cuda(), torch.from_numpy(x.type).cuda()) for x in systems]
+    b = nb.nb_batch_create(ctx, hs)
+    # batched
+    for _ in range(args.warmup):
+        assert _batch_eval(nb, b, flags)
+    stream.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for h, (xq, ty) in zip(hs, dev_in):
+            nb.nb_sys_set_coords(h, xq, ty)
+        assert _batch_eval(nb, b, flags)
+    t_batch = (time.perf_counter() - t0) / args.steps
+    e = np.zeros(2)
+    pairs = 0
+    for h in hs:  # per-system interacting pairs of the last batched evaluation
+        nb.nb_sys_results(h, None, e, None)
+    nb.nb_batch_destroy(b)
+    # plain: one system after another through the single-system entry points
+    f = torch.empty((max(x.n for x in systems), 3), dtype=torch.float32, device="cuda")
+    ed = torch.empty(2, dtype=torch.float64, device="cuda")
+    vd = torch.empty(9, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            for h, (xq, ty) in zip(hs, dev_in):
+                nb.nb_grid_put(h, xq, ty)
+                nb.nb_pairlist_build(h)
+                nb.nb_forces(h, None, f, ed, vd, flags)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for h, (xq, ty) in zip(hs, dev_in):
+                nb.nb_grid_put(h, xq, ty)
+                nb.nb_pairlist_build(h)
+                nb.nb_forces(h, None, f, ed, vd, flags)
+            stream.synchronize()
+        t_plain = (time.perf_counter() - t0) / args.steps
+        for h in hs:
+            pairs += nb.nb_eval_info(h)["n_pairs"]
+    for h in hs:
+        nb.nb_sys_destroy(h)
+    nb.nb_ctx_destroy(ctx)
+    return {"workload": "64 water boxes, 1,000-32,000 waters (log-uniform, seed 4), "
+                        f"{tot_atoms} atoms in total, LJ + RF, energies and virial",
+            "batched_systems_per_s": len(systems) / t_batch, "plain_systems_per_s": len(systems) / t_plain,
+            "batched_over_plain": t_plain / t_batch, "batched_pairs_per_s": pairs / t_batch,
+            "batched_ms": 1e3 * t_batch, "plain_ms": 1e3 * t_plain, "tuning": tuning,
+            "timing": "host wall clock per evaluation of all 64 systems (submit to completion)"}
+
+
+def run_serve(args, n_req: int = 256) -> dict:
+    """Poisson stream (2000 req/s, seed 5) of single-point Ewald evaluations of
+    boxes of 1,000-100,000 waters (log-uniform), fresh coordinates each, served
+    by the continuous-batching server under a 120 GB budget; compared with the
+    same requests as serial plain calls."""
+    import threading
+
+    import torch
+
+    from paper_1506_00716_gb300 import autotune, nb
+    from paper_1506_00716_gb300 import build as nbbuild
+
+    torch.cuda.set_device(0)
+    nbbuild.build()
+    arrivals, sizes = wb.request_stream(n_req, 2000.0, 1000, 100000, seed=5)
+    reqs = [wb.water_box(m, None, seed=5000 + k) for k, m in enumerate(sizes)]
+    p = wb.params_ewald()
+    flags = nb.NB_F_ENERGY | nb.NB_F_VIRIAL
+    ctx = nb.nb_ctx_create(0, None, 0)
+    tuning = autotune.apply(ctx, "ewald", int(np.median([r.n for r in reqs])),
+                            gpu=torch.cuda.get_device_name(0))
+    srv = nb.nb_server_create(ctx, p, 120 << 30, 64)
+    # warm-up: a few requests through the server
+    for r in reqs[:4]:
+        nb.nb_server_wait(srv, nb.nb_server_submit(srv, r.n, r.box, r.xq(), r.type, r.excl_index,
+                                                   r.excl_atoms, flags))
+    inputs = [(r.xq(), r.type) for r in reqs]
+    tickets = [0] * n_req
+    t_start = time.perf_counter()
+
+    def submitter():
+        for k, r in enumerate(reqs):
+            delay = t_start + arrivals[k] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = nb.nb_server_submit(srv, r.n, r.box, inputs[k][0], inputs[k][1], r.excl_index,
+                                             r.excl_atoms, flags)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    lat, waves, pairs = [], [], 0
+    for k, r in enumerate(reqs):
+        st = nb.nb_server_wait(srv, tickets[k])
+        lat.append(st["latency_s"])
+        waves.append(st["wave_size"])
+        pairs += st["n_pairs"]
+    t_served = time.perf_counter() - t_start
+    nb.nb_server_destroy(srv)
+    # serial plain calls, one request after another
+    e = np.zeros(2)
+    v = np.zeros(9)
+    t0 = time.perf_counter()
+    for r, (xq, ty) in zip(reqs, inputs):
+        h = nb.nb_sys_create(ctx, p, r.n, r.box)
+        nb.nb_set_exclusions(h, r.excl_index, r.excl_atoms)
+        nb.nb_grid_put(h, xq, ty)
+        nb.nb_pairlist_build(h)
+        f = np.empty((r.n, 3), dtype=np.float32)
+        nb.nb_forces(h, None, f, e, v, flags)
+        nb.nb_sys_destroy(h)
+    t_serial = time.perf_counter() - t0
+    nb.nb_ctx_destroy(ctx)
+    lat_ms = np.array(lat) * 1e3
+    return {"workload": f"{n_req} requests, Poisson 2000 req/s (seed 5), 1,000-100,000 waters "
+                        "(log-uniform), LJ + Ewald real space, energies and virial, fresh lists",
+            "served_systems_per_s": n_req / t_served, "serial_systems_per_s": n_req / t_serial,
+            "served_over_serial": t_serial / t_served, "p50_ms": float(np.percentile(lat_ms, 50)),
+            "p99_ms": float(np.percentile(lat_ms, 99)), "mean_wave": float(np.mean(waves)),
+            "served_pairs_per_s": pairs / t_served, "offered_req_per_s": n_req / float(arrivals[-1]),
+            "budget_gb": 120, "tuning": tuning,
+            "timing": "host wall clock from the first arrival to the last result; latency per request "
+                      "from submission to results"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -471,11 +631,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 3M-atom summary object")
-    ap.add_argument("--workload", default="mid", choices=["mid", "large"])
+    ap.add_argument("--workload", default="mid", choices=["mid", "large", "ensemble", "serve"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and serving summaries")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "large" and args.impl == "ours":
         print(json.dumps(run_large(args)))
+        return
+    if args.workload == "ensemble" and args.impl == "ours":
+        print(json.dumps(run_ensemble(args)))
+        return
+    if args.workload == "serve" and args.impl == "ours":
+        print(json.dumps(run_serve(args)))
         return
     if args.impl == "reference":
         out = run_reference(args)
@@ -492,6 +659,9 @@ def main():
                                 "computed_pairs_per_s": lg["config"]["computed_pairs_per_s"],
                                 "roofline": lg["roofline"], "build_ms": lg["build_ms"],
                                 "energy_eval_ms": lg["energy_eval_ms"], "tuning": lg["config"]["tuning"]}
+        if world == 1 and not args.no_extra:
+            out["ensemble"] = run_ensemble(argparse.Namespace(steps=5, warmup=3))
+            out["serving"] = run_serve(argparse.Namespace(steps=1, warmup=1))
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out))

@@ -290,6 +290,57 @@ nb_status nb_batch_poll(nb_batch *batch, unsigned long long ticket, long long ti
 nb_status nb_sys_results(nb_sys *sys, float *f, double *energy, double *virial);
 
 /*
+ * Serving (continuous batching of independent single-point evaluations, the
+ * serving form of the paper's ensemble workloads, Section 3.3).  A server
+ * owns a scheduler thread and two CUDA streams.  Requests are queued by
+ * nb_server_submit; whenever a stream is free, the scheduler admits the
+ * oldest pending requests that fit the server's HBM budget (at most max_wave
+ * of them) as one wave: their grid put, list build, prune, forces and
+ * energies run as one launch per stage over all of them.  Two waves are in
+ * flight at a time, so the upload, grid and search of one wave overlap the
+ * force kernel of the other, and requests that arrive meanwhile join the
+ * next wave as memory frees up.  Device state of a request exists only while
+ * its wave runs.
+ */
+typedef struct nb_server nb_server;
+
+/* Timings of one request (seconds, steady clock). */
+typedef struct {
+    double latency_s;  /* submission to results available */
+    double queue_s;    /* submission to admission into a wave */
+    long long n_pairs; /* interacting pairs (requests with NB_F_ENERGY) */
+    int wave_size;     /* requests in the wave that served it */
+} nb_request_stats;
+
+/*
+ * Create a server on ctx's device with the given parameters (copied).
+ * hbm_budget_bytes caps the device memory of the waves in flight (0 = no
+ * cap); max_wave caps the requests per wave (1..4096).
+ */
+nb_status nb_server_create(nb_ctx *ctx, const nb_params *params, size_t hbm_budget_bytes, int max_wave,
+                           nb_server **out);
+/* Stop accepting requests, finish all pending and in-flight work, free. */
+nb_status nb_server_destroy(nb_server *srv);
+/*
+ * Queue one evaluation.  natoms, box as nb_sys_create; xq, type as
+ * nb_grid_put but host memory only (copied before returning); exclusions
+ * as nb_set_exclusions (host, may be NULL); flags as nb_forces.  Returns a
+ * ticket.  A request larger than the whole budget fails at nb_server_wait
+ * with NB_ERR_BUDGET.
+ */
+nb_status nb_server_submit(nb_server *srv, int natoms, const double box[3], const float *xq,
+                           const int *type, const int *excl_index, const int *excl_atoms, unsigned flags,
+                           unsigned long long *ticket);
+/*
+ * Wait up to timeout_us (< 0: no limit) for a ticket and copy its results
+ * to host memory: f (natoms*3 floats), energy (2), virial (9), stats; any
+ * may be NULL.  NB_ERR_TIMEOUT if not finished in time (the ticket stays
+ * valid); each ticket's results can be collected once.
+ */
+nb_status nb_server_wait(nb_server *srv, unsigned long long ticket, long long timeout_us, float *f,
+                         double *energy, double *virial, nb_request_stats *stats);
+
+/*
  * Allocation-free evaluation, for callers that cannot allocate device
  * memory: code that runs where cudaMalloc is unavailable or not allowed
  * (inside another framework's memory manager, a latency-critical loop that

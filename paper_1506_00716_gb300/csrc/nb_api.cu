@@ -68,8 +68,8 @@ Geometry make_geometry(int natoms, const double box[3]) {
 }
 
 // Expected list sizes (half list, before pruning) for capacity planning.
-void list_estimate(const nb_params& p, int natoms, const double box[3], int clcap, long long* items,
-                   long long* entries) {
+void list_estimate(const nb_params& p, int natoms, const double box[3], int clcap, int max_entries,
+                   long long* items, long long* entries) {
     double vol = box[0] * box[1] * box[2];
     double rho = natoms / vol;
     double ext = std::cbrt((double)CL / rho);
@@ -78,8 +78,10 @@ void list_estimate(const nb_params& p, int natoms, const double box[3], int clca
     double per_cl = steiner * rho / CL / 2.0;
     double shift = 1.0;
     for (int d = 0; d < 3; ++d) shift *= 1.0 + 2.0 * std::min(1.0, (r + ext) / box[d]);
-    *items = (long long)(clcap * std::min(27.0, shift * 1.25)) + 256;
     *entries = (long long)(clcap * (per_cl * 1.35 + 8.0) * std::max(1.0, shift / 4.0)) + 4096;
+    // one item per (cluster, shift) run, plus the splits of runs longer than
+    // max_entries
+    *items = (long long)(clcap * std::min(27.0, shift * 1.25)) + *entries / std::max(1, max_entries) + 256;
 }
 
 }  // namespace nbgb
@@ -202,17 +204,23 @@ float2* sys_lj_ptr(nb_sys* s) {
     return (float2*)((char*)s->block + total - lj);
 }
 
+// The list radius is padded by 1e-5 (1 + the longest box edge): float32
+// coordinates of that magnitude carry rounding errors far below the pad, so
+// no pair inside rlist can be lost to them.
+void list_radii(double rlist, const double box[3], SysDev* h) {
+    double maxL = std::max(box[0], std::max(box[1], box[2]));
+    double rl = rlist + 1e-5 * (1.0 + maxL);
+    h->rl_search = (float)rl;
+    h->rl2_prune = (float)(rl * rl);
+}
+
 KParams make_kparams(const nb_sys* s) {
     KParams k{};
     const nb_params& p = s->p;
-    double maxL = std::max(s->box[0], std::max(s->box[1], s->box[2]));
-    double pad = 1e-5 * (1.0 + maxL);
     k.rc2_d = p.rc * p.rc;
     k.rc2 = (float)(p.rc * p.rc);
     k.rc2_lo = (float)(p.rc * p.rc * (1.0 - 2e-5));
     k.rc2_hi = (float)(p.rc * p.rc * (1.0 + 2e-5));
-    k.rl_search = (float)(p.rlist + pad);
-    k.rl2_prune = (float)((p.rlist + pad) * (p.rlist + pad));
     k.fq = (float)(p.fcoul / p.eps_r);
     double krf = p.eps_rf == 0.0 ? 1.0 / (2.0 * p.rc * p.rc * p.rc)
                                  : (p.eps_rf - p.eps_r) / ((2.0 * p.eps_rf + p.eps_r) * p.rc * p.rc * p.rc);
@@ -300,7 +308,7 @@ void plan_destroy(Plan* pl) {
     delete pl;
 }
 
-nb_status plan_create(nb_ctx* ctx, nb_sys* const* systems, int n, Plan** out) {
+nb_status plan_create(nb_ctx* ctx, nb_sys* const* systems, int n, Plan** out, double boost) {
     Plan* pl = new Plan();
     pl->ctx = ctx;
     pl->systems.assign(systems, systems + n);
@@ -314,9 +322,9 @@ nb_status plan_create(nb_ctx* ctx, nb_sys* const* systems, int n, Plan** out) {
         off[(n + 1) + k + 1] = off[(n + 1) + k] + s->geo.ncol;
         off[2 * (n + 1) + k + 1] = off[2 * (n + 1) + k] + s->geo.clcap;
         long long it, en;
-        list_estimate(s->p, s->natoms, s->box, s->geo.clcap, &it, &en);
-        items += it;
-        entries += en;
+        list_estimate(s->p, s->natoms, s->box, s->geo.clcap, ctx->tuning.max_entries, &it, &en);
+        items += (long long)(it * boost);
+        entries += (long long)(en * boost);
     }
     pl->tot_atoms = off[n];
     pl->tot_cols = off[(n + 1) + n];
@@ -471,7 +479,7 @@ nb_status check_box(const nb_params* p, const double box[3]) {
 
 size_t plan_bytes_estimate(const nb_params* p, int natoms, const double box[3], const Geometry& g) {
     long long it, en;
-    list_estimate(*p, natoms, box, g.clcap, &it, &en);
+    list_estimate(*p, natoms, box, g.clcap, 8, &it, &en);
     return align256(16 * (size_t)it) + align256(12 * (size_t)en) + 4096;
 }
 
@@ -508,6 +516,8 @@ size_t api_sys_layout(int natoms, const double box[3], int ntypes, SysDev* h, ch
     return sys_layout(natoms, g, ntypes, h, base);
 }
 
+void api_list_radii(double rlist, const double box[3], SysDev* h) { list_radii(rlist, box, h); }
+
 KParams api_kparams(const nb_params& p, const double box[3], float2* lj) {
     nb_sys tmp;
     tmp.p = p;
@@ -518,7 +528,7 @@ KParams api_kparams(const nb_params& p, const double box[3], float2* lj) {
 
 void api_list_estimate(const nb_params& p, int natoms, const double box[3], int clcap, long long* items,
                        long long* entries) {
-    list_estimate(p, natoms, box, clcap, items, entries);
+    list_estimate(p, natoms, box, clcap, 32, items, entries);
 }
 
 }  // namespace nbgb
@@ -652,6 +662,7 @@ nb_status nb_sys_create(nb_ctx* ctx, const nb_params* params, int natoms, const 
     y->d_lj = sys_lj_ptr(y);
     SysDev& h = y->h;
     for (int d = 0; d < 3; ++d) h.L[d] = (float)box[d];
+    list_radii(params->rlist, box, &h);
     h.cw[0] = y->geo.cw[0];
     h.cw[1] = y->geo.cw[1];
     h.icw[0] = y->geo.icw[0];
@@ -884,14 +895,36 @@ nb_status nb_batch_destroy(nb_batch* batch) {
 static nb_status batch_record(Plan* pl, unsigned flags) {
     cudaStream_t st = pl->ctx->stream;
     PlanLaunch p = launch_of(pl);
+    // per-stage timing applies when the sequence runs directly (not captured)
     NB_CK(cudaMemsetAsync(pl->list.counters, 0, 4 * CNT_N, st));
-    NB_CK(launch_grid_put(p, st));
-    NB_CK(launch_search(p, st));
-    NB_CK(launch_prune(p, st));
-    NB_CK(launch_prepare(p, false, st));
-    NB_CK(launch_forces(p, flags, st));
-    if (flags & NB_F_ENERGY) NB_CK(launch_energy(p, st));
-    NB_CK(launch_finalize(p, flags, st));
+    {
+        StageScope sc(pl->ctx, NB_STAGE_GRID);
+        NB_CK(launch_grid_put(p, st));
+    }
+    {
+        StageScope sc(pl->ctx, NB_STAGE_SEARCH);
+        NB_CK(launch_search(p, st));
+    }
+    {
+        StageScope sc(pl->ctx, NB_STAGE_PRUNE);
+        NB_CK(launch_prune(p, st));
+    }
+    {
+        StageScope sc(pl->ctx, NB_STAGE_ZERO);
+        NB_CK(launch_prepare(p, false, st));
+    }
+    {
+        StageScope sc(pl->ctx, NB_STAGE_FORCES);
+        NB_CK(launch_forces(p, flags, st));
+    }
+    if (flags & NB_F_ENERGY) {
+        StageScope sc(pl->ctx, NB_STAGE_ENERGY);
+        NB_CK(launch_energy(p, st));
+    }
+    {
+        StageScope sc(pl->ctx, NB_STAGE_FINAL);
+        NB_CK(launch_finalize(p, flags, st));
+    }
     NB_CK(cudaMemcpyAsync(pl->h_counters, pl->list.counters, 4 * CNT_N, cudaMemcpyDeviceToHost, st));
     return NB_OK;
 }

@@ -92,11 +92,12 @@ nb_status fail(nb_status s, const std::string& msg);
 nb_status cuda_fail(cudaError_t e, const char* what);
 bool is_device_ptr(const void* p);
 Geometry make_geometry(int natoms, const double box[3]);
-void list_estimate(const nb_params& p, int natoms, const double box[3], int clcap, long long* items,
-                   long long* entries);
+void list_estimate(const nb_params& p, int natoms, const double box[3], int clcap, int max_entries,
+                   long long* items, long long* entries);
 nb_status dev_alloc(nb_ctx* ctx, void** ptr, size_t bytes);
 void dev_free(nb_ctx* ctx, void* ptr, size_t bytes);
-nb_status plan_create(nb_ctx* ctx, nb_sys* const* systems, int n, Plan** out);
+// boost scales the estimated list capacity (retries after an overflow)
+nb_status plan_create(nb_ctx* ctx, nb_sys* const* systems, int n, Plan** out, double boost = 1.0);
 void plan_destroy(Plan* pl);
 PlanLaunch launch_of(const Plan* pl);
 nb_status stage_coords(nb_sys* s, const float* xq, const int* type);

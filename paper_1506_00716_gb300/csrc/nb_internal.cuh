@@ -65,6 +65,11 @@ struct SysDev {
     float* f_out;        // [natoms * 3] forces in the caller's order
     double* acc;         // [NACC] FP64 energy/virial accumulators
     double* res;         // [NRES] E_LJ, E_C, virial row-major, pair count
+    // list radius of this system, padded for the float32 rounding of
+    // coordinates of this box's magnitude; per system, so that a system's
+    // list does not depend on the other systems of a batch
+    float rl_search;     // used by the bounding-box test
+    float rl2_prune;     // its square, used by the prune
 };
 
 // Accumulator layout of SysDev::acc.
@@ -87,8 +92,6 @@ struct KParams {
     double rc2_d;        // cut-off^2 in float64 (exact decisions near rc)
     float rc2;           // cut-off^2
     float rc2_lo, rc2_hi;  // band around rc^2 decided exactly
-    float rl_search;     // list radius used by the bounding-box test (padded)
-    float rl2_prune;     // list radius^2 used by the prune (padded)
     float fq;            // fcoul / eps_r
     float krf, two_krf, crf;
     float beta;          // Ewald splitting parameter
@@ -129,6 +132,8 @@ nb_status api_check_system(const nb_params* params, int natoms, const double box
 // returns the bytes used, the LJ tables occupying the last 16 * ntypes^2.
 size_t api_sys_layout(int natoms, const double box[3], int ntypes, SysDev* h, char* base);
 KParams api_kparams(const nb_params& p, const double box[3], float2* lj);
+// Padded list radius of a system (SysDev::rl_search, rl2_prune).
+void api_list_radii(double rlist, const double box[3], SysDev* h);
 void api_list_estimate(const nb_params& p, int natoms, const double box[3], int clcap, long long* items,
                        long long* entries);
 

@@ -101,7 +101,7 @@ __device__ void flush(SearchWarpSmem& sm, int nbuf, int nruns, int ci, int sid, 
     ibase = __shfl_sync(FULL, ibase, 0);
     ebase = __shfl_sync(FULL, ebase, 0);
     const bool ok_e = (long long)ebase + nbuf <= list.entry_cap;
-    const bool ok_i = (long long)ibase + nitems <= list.item_cap;
+    const bool ok_i = (long long)ibase + nitems <= list.item_cap;  // only reported
     if (lane == 0 && !ok_e) atomicOr(list.counters + CNT_OVERFLOW, 2);
     if (lane == 0 && !ok_i) atomicOr(list.counters + CNT_OVERFLOW, 1);
     if (ok_e) {
@@ -110,12 +110,15 @@ __device__ void flush(SearchWarpSmem& sm, int nbuf, int nruns, int ci, int sid, 
             list.mask[ebase + k] = sm.mask[k];
         }
     }
-    if (ok_i && lane < nruns) {
-        // on entry overflow the items are still written, empty, so that the
-        // counted item range never holds stale data
+    if (lane < nruns) {
+        // Every reserved item slot below the capacity is written, so that the
+        // item range the kernels read (up to min(count, capacity)) never holds
+        // stale data: a real item if this flush's entries fit, otherwise an
+        // empty one.  Slots at or beyond the capacity are not written.
         const int w = (sid << 5) | sm.run_shift[lane];
         int idx = ibase + incl - nch;
         for (int a = rs; a < re; a += max_entries, ++idx) {
+            if (idx >= list.item_cap) break;
             const int b = min(re, a + max_entries);
             list.items[idx] = ok_e ? make_int4(ci, ebase + a, ebase + b, w) : make_int4(ci, 0, 0, w);
         }
@@ -147,7 +150,7 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
     const float4 hi_i = d.bb[2 * ci + 1];
     const int nri = (int)lo_i.w;
     const unsigned long long rmask_i = row_mask(nri);
-    const float rl = kp.rl_search;
+    const float rl = d.rl_search;
     const float rl2 = rl * rl;
     const float eps = 1e-5f * fmaxf(1.f, fmaxf(d.L[0], fmaxf(d.L[1], d.L[2])));
 
@@ -313,11 +316,11 @@ __global__ void __launch_bounds__(PRUNE_WARPS * 32)
 k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     const int lane = threadIdx.x & 31;
     const int nitems = min(list.counters[CNT_ITEMS], list.item_cap);
-    const float rl2 = kp.rl2_prune;
     for (int it = blockIdx.x * PRUNE_WARPS + (threadIdx.x >> 5); it < nitems;
          it += gridDim.x * PRUNE_WARPS) {
         int4 item = list.items[it];
         const SysDev& d = sys[item.w >> 5];
+        const float rl2 = d.rl2_prune;
         int sh = item.w & 31;
         float Sx = (sh / 9 - 1) * d.L[0], Sy = ((sh / 3) % 3 - 1) * d.L[1], Sz = (sh % 3 - 1) * d.L[2];
         float3 xi[CL];

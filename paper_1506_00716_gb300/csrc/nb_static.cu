@@ -113,6 +113,7 @@ extern "C" nb_status nb_eval_noalloc(const nb_params* params, int natoms, const 
         return api_fail(NB_ERR_CAPACITY, "nb_eval_noalloc: the box needs too many grid columns");
     char* sys_base = base + off;
     api_sys_layout(natoms, box, nt, &h, sys_base);
+    api_list_radii(params->rlist, box, &h);
     off += up256(sys_bytes);
     float2* d_lj = (float2*)(sys_base + sys_bytes - up256(16 * (size_t)nt * nt));
     float2* d_lje = d_lj + (size_t)nt * nt;

@@ -30,7 +30,8 @@ EXPORTS = ["nb_last_error", "nb_ctx_create", "nb_ctx_destroy", "nb_ctx_memory", 
            "nb_pairlist_info", "nb_forces", "nb_pairlist_export", "nb_batch_create",
            "nb_batch_destroy", "nb_sys_set_coords", "nb_batch_submit", "nb_batch_poll",
            "nb_sys_results", "nb_ctx_set_timing", "nb_ctx_timing", "nb_eval_info",
-           "nb_eval_noalloc", "nb_ctx_set_tuning", "nb_ctx_get_tuning"]
+           "nb_eval_noalloc", "nb_ctx_set_tuning", "nb_ctx_get_tuning", "nb_server_create",
+           "nb_server_destroy", "nb_server_submit", "nb_server_wait"]
 NB_NSTAGE = 8
 STAGES = ["grid", "search", "prune", "coord", "zero", "forces", "final", "energy"]
 
@@ -51,6 +52,11 @@ class nb_params(ctypes.Structure):
 
 class nb_tuning(ctypes.Structure):
     _fields_ = [("max_entries", ctypes.c_int), ("force_min_blocks", ctypes.c_int)]
+
+
+class nb_request_stats(ctypes.Structure):
+    _fields_ = [("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double),
+                ("n_pairs", ctypes.c_longlong), ("wave_size", ctypes.c_int)]
 
 
 class nb_list_info(ctypes.Structure):
@@ -102,6 +108,13 @@ def load(path: str | None = None):
         "nb_ctx_set_timing": ([_vp, ctypes.c_int], _st),
         "nb_ctx_set_tuning": ([_vp, ctypes.POINTER(nb_tuning)], _st),
         "nb_ctx_get_tuning": ([_vp, ctypes.POINTER(nb_tuning)], _st),
+        "nb_server_create": ([_vp, ctypes.POINTER(nb_params), ctypes.c_size_t, ctypes.c_int,
+                              ctypes.POINTER(_vp)], _st),
+        "nb_server_destroy": ([_vp], _st),
+        "nb_server_submit": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp, _vp, _vp, _vp,
+                              ctypes.c_uint, ctypes.POINTER(ctypes.c_ulonglong)], _st),
+        "nb_server_wait": ([_vp, ctypes.c_ulonglong, ctypes.c_longlong, _vp, _vp, _vp,
+                            ctypes.POINTER(nb_request_stats)], _st),
         "nb_ctx_timing": ([_vp, _vp, _vp, ctypes.c_int], _st),
         "nb_eval_info": ([_vp, ctypes.POINTER(ctypes.c_longlong)], _st),
         "nb_eval_noalloc": ([ctypes.POINTER(nb_params), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -308,3 +321,37 @@ def nb_ctx_get_tuning(ctx) -> dict:
     t = nb_tuning()
     check(load().nb_ctx_get_tuning(ctx, ctypes.byref(t)))
     return {"max_entries": t.max_entries, "force_min_blocks": t.force_min_blocks}
+
+
+def nb_server_create(ctx, params, budget: int = 0, max_wave: int = 64) -> int:
+    ps, keep = make_params(params)
+    out = _vp()
+    check(load().nb_server_create(ctx, ctypes.byref(ps), budget, max_wave, ctypes.byref(out)))
+    del keep
+    return out.value
+
+
+def nb_server_destroy(srv) -> None:
+    check(load().nb_server_destroy(srv))
+
+
+def nb_server_submit(srv, natoms: int, box, xq, type_, excl_index=None, excl_atoms=None, flags: int = 0) -> int:
+    import numpy as np
+
+    b = (ctypes.c_double * 3)(*[float(v) for v in box])
+    ei = ea = None
+    if excl_index is not None:
+        ei = np.ascontiguousarray(excl_index, dtype=np.int32)
+        ea = np.ascontiguousarray(excl_atoms, dtype=np.int32)
+        if ea.size == 0:
+            ea = np.zeros(1, dtype=np.int32)
+    t = ctypes.c_ulonglong()
+    check(load().nb_server_submit(srv, natoms, b, ptr(xq), ptr(type_), ptr(ei), ptr(ea), flags,
+                                  ctypes.byref(t)))
+    return t.value
+
+
+def nb_server_wait(srv, ticket: int, timeout_us: int = -1, f=None, energy=None, virial=None) -> dict:
+    st = nb_request_stats()
+    check(load().nb_server_wait(srv, ticket, timeout_us, ptr(f), ptr(energy), ptr(virial), ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in nb_request_stats._fields_}

@@ -121,3 +121,50 @@ def test_batch_poll_times_out_while_the_stream_is_busy(torch_cuda):
         for h in handles:
             nb.nb_sys_destroy(h)
         nb.nb_ctx_destroy(ctx)
+
+
+def test_batch_recovers_from_a_list_overflow(torch_cuda):
+    """A list that outgrows its capacity reports NB_ERR_CAPACITY, leaves the
+    device state sound, and the resubmitted batch is correct.
+
+    The batch's list capacity is sized for the tuning in force when it is
+    created (max_entries 4096: about one item per (cluster, shift) run).
+    Switching to max_entries 4 afterwards splits every run into items of four
+    entries, several times more items than that capacity holds."""
+    torch = torch_cuda
+    stream = torch.cuda.Stream()
+    ctx = nb.nb_ctx_create(0, stream, 0)
+    systems = _systems()[:3]
+    p = wb.params_rf()
+    handles = []
+    try:
+        nb.nb_ctx_set_tuning(ctx, 4096, 3)
+        for s in systems:
+            h = nb.nb_sys_create(ctx, p, s.n, s.box)
+            nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
+            nb.nb_sys_set_coords(h, s.xq(), s.type)
+            handles.append(h)
+        b = nb.nb_batch_create(ctx, handles)
+        try:
+            nb.nb_ctx_set_tuning(ctx, 4, 3)
+            t = nb.nb_batch_submit(b, FLAGS)
+            with pytest.raises(nb.NbError) as ei:
+                nb.nb_batch_poll(b, t, 10_000_000)
+            assert ei.value.status == 9  # NB_ERR_CAPACITY, buffers grown
+            t = nb.nb_batch_submit(b, FLAGS)
+            assert nb.nb_batch_poll(b, t, 10_000_000)
+            for h, s in zip(handles, systems):
+                f = np.zeros((s.n, 3), dtype=np.float32)
+                e = np.zeros(2)
+                v = np.zeros(9)
+                nb.nb_sys_results(h, f, e, v)
+                ref = oracle.energy_virial(s, p)
+                assert rel_rms(f, oracle.forces(s, p)) < 1e-5
+                assert abs(e[0] - ref["e_lj"]) <= 1e-6 * abs(ref["e_lj"])
+                assert abs(e[1] - ref["e_coul"]) <= 1e-6 * abs(ref["e_coul"])
+        finally:
+            nb.nb_batch_destroy(b)
+    finally:
+        for h in handles:
+            nb.nb_sys_destroy(h)
+        nb.nb_ctx_destroy(ctx)
