@@ -42,8 +42,11 @@ METRIC = "nonbonded pair interactions/s"
 UNIT = "pairs/s"
 EVALS_PER_STEP = 10
 SIGMA = 0.005
-# FP32 flops per evaluated atom-pair slot in the force kernel's pair code
-# (FADD/FMUL = 1, FFMA = 2), by (coulomb, virial); see the design doc.
+# FP32-pipe instructions (FADD, FMUL, FFMA: one each) per evaluated atom-pair
+# slot in the force kernel's pair code, by (coulomb, virial), counted from the
+# source; and the same code's flops (FFMA = 2).  The FP32-pipe fraction is the
+# instruction rate over SMs x 128 FP32 lanes x SM clock.
+INST_PER_SLOT = {("rf", False): 26, ("rf", True): 32, ("ewald", False): 43, ("ewald", True): 49}
 FLOPS_PER_SLOT = {("rf", False): 30, ("rf", True): 42, ("ewald", False): 56, ("ewald", True): 68}
 # kernels launched per timed stage (nb_ctx_timing)
 KERNELS_PER_STAGE = {"grid": 6, "search": 1, "prune": 1, "coord": 0, "zero": 1, "forces": 1, "final": 1,
@@ -234,21 +237,9 @@ def run_ours(args) -> dict:
     f_ms, f_n = stage["forces"]
     avg_ms = f_ms / max(f_n, 1)
     slots = info["n_slots"]
-    fps = ((EVALS_PER_STEP - 1) * FLOPS_PER_SLOT[(wl.coul, False)] + FLOPS_PER_SLOT[(wl.coul, True)]) \
-        / EVALS_PER_STEP
-    flops = fps * slots
-    props = torch.cuda.get_device_properties(dev)
-    peaks, peak_kind = _peaks()
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
-    achieved = flops / (avg_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
-                "traffic": _traffic_per_launch("forces_rf_mid"),
-                "kernel": "k_forces<RF> (9 of 10 launches without, 1 with virial)",
-                "peak_kind": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({peak_kind} clock)",
-                "avg_launch_ms": round(avg_ms, 5), "slots_per_launch": slots,
-                "flops_per_slot": fps}
+    roofline = _fp32_roofline(torch, dev, wl.coul, EVALS_PER_STEP - 1, 1, slots, avg_ms,
+                              "k_forces<RF> (9 of 10 launches without, 1 with virial)",
+                              _traffic_per_launch("forces_rf_mid"))
     launches = sum(n * KERNELS_PER_STAGE[name] for name, (_, n) in stage.items())
 
     # end to end through the C ABI with host buffers
@@ -271,6 +262,27 @@ def run_ours(args) -> dict:
     if world > 1:
         dist.barrier()
     return out
+
+
+def _fp32_roofline(torch, dev, coul, n_plain, n_vir, slots, avg_ms, kernel, traffic) -> dict:
+    """FP32-pipe roofline of the force kernel: FP32 instructions per slot x
+    slots per launch / launch time, against SMs x 128 lanes x SM clock."""
+    n = n_plain + n_vir
+    ips = (n_plain * INST_PER_SLOT[(coul, False)] + n_vir * INST_PER_SLOT[(coul, True)]) / n
+    fps = (n_plain * FLOPS_PER_SLOT[(coul, False)] + n_vir * FLOPS_PER_SLOT[(coul, True)]) / n
+    props = torch.cuda.get_device_properties(dev)
+    peaks, peak_kind = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e12
+    achieved = ips * slots / (avg_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+            "unit": "T FP32 inst/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "kernel": kernel,
+            "peak_kind": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz "
+                         f"({peak_kind} max SM clock)",
+            "avg_launch_ms": round(avg_ms, 5), "slots_per_launch": slots,
+            "inst_per_slot": round(ips, 2), "flops_per_slot": round(fps, 2),
+            "achieved_tflops": round(fps * slots / (avg_ms * 1e-3) / 1e12, 3)}
 
 
 def _traffic_per_launch(key: str):
@@ -434,13 +446,9 @@ def run_large(args) -> dict:
     nb.nb_ctx_destroy(ctx)
     f_ms, f_n = stage["forces"]
     avg = f_ms / f_n
-    # 9 + 1: the last launch carried the virial
-    fps = ((f_n - 1) * FLOPS_PER_SLOT[("ewald", False)] + FLOPS_PER_SLOT[("ewald", True)]) / f_n
-    peaks, peak_kind = _peaks()
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    props = torch.cuda.get_device_properties(dev)
-    peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
-    achieved = fps * info["n_slots"] / (avg * 1e-3) / 1e12
+    # the last launch carried the virial
+    roofline = _fp32_roofline(torch, dev, "ewald", f_n - 1, 1, info["n_slots"], avg, "k_forces<Ewald>",
+                              _traffic_per_launch("forces_ewald_large"))
     grid_bytes = s.n * (20 + 24 + 8 + 8) + info["n_clusters"] * 32
     return {
         "metric": METRIC, "value": n_pairs / (avg * 1e-3), "unit": UNIT, "n_gpus": 1,
@@ -452,10 +460,7 @@ def run_large(args) -> dict:
                    "computed_slots": info["n_slots"], "computed_pairs_per_s": info["n_slots"] / (avg * 1e-3),
                    "list_entries": info["n_entries"], "list_entries_raw": info["n_entries_raw"],
                    "generate_s": round(t_gen, 2), "tuning": tuning},
-        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
-                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": "k_forces<Ewald>", "flops_per_slot": fps,
-                     "peak_kind": f"derived ({peak_kind} clock)"},
+        "roofline": roofline,
         "build_ms": {"grid": stage["grid"][0], "search": stage["search"][0], "prune": stage["prune"][0]},
         "grid_put_gbs": grid_bytes / (stage["grid"][0] * 1e-3) / 1e9,
         "energy_eval_ms": stage["energy"][0] / max(stage["energy"][1], 1),

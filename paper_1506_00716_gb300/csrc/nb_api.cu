@@ -88,6 +88,84 @@ void list_estimate(const nb_params& p, int natoms, const double box[3], int clca
 
 namespace nbgb {
 
+nb_status excl_symmetrise(int n, const int* excl_index, const int* excl_atoms, std::vector<int>& idx,
+                          std::vector<int>& at) {
+    if (!excl_index) return fail(NB_ERR_ARG, "excl_index is NULL");
+    if (excl_index[0] != 0) return fail(NB_ERR_ARG, "excl_index[0] must be 0");
+    for (int a = 0; a < n; ++a)
+        if (excl_index[a + 1] < excl_index[a]) return fail(NB_ERR_ARG, "excl_index must be non-decreasing");
+    const int nnz = excl_index[n];
+    if (nnz > 0 && !excl_atoms) return fail(NB_ERR_ARG, "excl_atoms is NULL");
+    for (int k = 0; k < nnz; ++k)
+        if (excl_atoms[k] < 0 || excl_atoms[k] >= n) return fail(NB_ERR_ARG, "exclusion partner out of range");
+    // already symmetric, strictly ascending per atom and free of self pairs?
+    bool canon = true;
+    for (int a = 0; a < n && canon; ++a)
+        for (int k = excl_index[a]; k < excl_index[a + 1] && canon; ++k) {
+            const int b = excl_atoms[k];
+            if (b == a || (k > excl_index[a] && excl_atoms[k - 1] >= b)) canon = false;
+            else canon = std::binary_search(excl_atoms + excl_index[b], excl_atoms + excl_index[b + 1], a);
+        }
+    if (canon) {
+        idx.assign(excl_index, excl_index + n + 1);
+        at.assign(excl_atoms, excl_atoms + nnz);
+        return NB_OK;
+    }
+    // symmetrise with flat arrays: degree count, prefix, fill, then sort and
+    // de-duplicate each atom's (short) partner list
+    std::vector<int> deg(n + 1, 0);
+    for (int a = 0; a < n; ++a)
+        for (int k = excl_index[a]; k < excl_index[a + 1]; ++k) {
+            const int b = excl_atoms[k];
+            if (b == a) continue;
+            ++deg[a + 1];
+            ++deg[b + 1];
+        }
+    for (int a = 0; a < n; ++a) deg[a + 1] += deg[a];
+    std::vector<int> fillp(deg.begin(), deg.end() - 1), flat(deg[n]);
+    for (int a = 0; a < n; ++a)
+        for (int k = excl_index[a]; k < excl_index[a + 1]; ++k) {
+            const int b = excl_atoms[k];
+            if (b == a) continue;
+            flat[fillp[a]++] = b;
+            flat[fillp[b]++] = a;
+        }
+    idx.assign(n + 1, 0);
+    at.clear();
+    at.reserve(flat.size());
+    for (int a = 0; a < n; ++a) {
+        int* first = flat.data() + deg[a];
+        int* last = flat.data() + deg[a + 1];
+        std::sort(first, last);
+        int* end_u = std::unique(first, last);
+        at.insert(at.end(), first, end_u);
+        idx[a + 1] = (int)at.size();
+    }
+    return NB_OK;
+}
+
+nb_status sys_upload_exclusions(nb_sys* sys, const std::vector<int>& idx, const std::vector<int>& at) {
+    if (sys->d_excl) dev_free(sys->ctx, sys->d_excl, sys->excl_bytes);
+    sys->d_excl = nullptr;
+    size_t bytes = 4 * (idx.size() + std::max<size_t>(1, at.size()));
+    void* p = nullptr;
+    nb_status s = dev_alloc(sys->ctx, &p, bytes);
+    if (s != NB_OK) return s;
+    sys->d_excl = (int*)p;
+    sys->excl_bytes = bytes;
+    // pageable sources: each copy returns once it has consumed its source
+    NB_CK(cudaMemcpyAsync(sys->d_excl, idx.data(), 4 * idx.size(), cudaMemcpyHostToDevice, sys->ctx->stream));
+    if (!at.empty())
+        NB_CK(cudaMemcpyAsync(sys->d_excl + idx.size(), at.data(), 4 * at.size(), cudaMemcpyHostToDevice,
+                              sys->ctx->stream));
+    sys->h.excl_index = sys->d_excl;
+    sys->h.excl_atoms = sys->d_excl + idx.size();
+    // descriptors held by plans are stale now
+    if (sys->plan) { plan_destroy(sys->plan); sys->plan = nullptr; }
+    sys->listed = false;
+    return NB_OK;
+}
+
 cudaEvent_t pool_event(nb_ctx* c) {
     if (!c->pool.empty()) {
         cudaEvent_t e = c->pool.back();
@@ -298,12 +376,31 @@ nb_status plan_alloc_list(Plan* pl, long long items, long long entries) {
     return NB_OK;
 }
 
+constexpr int CNT_BLOCK_INTS = 16;  // >= CNT_N, 64 bytes
+static_assert(CNT_BLOCK_INTS >= CNT_N, "counter block too small");
+
+int* ctx_counters_get(nb_ctx* c) {
+    if (c->cnt_free.empty()) {
+        const int per_slab = 256;
+        void* slab = nullptr;
+        if (cudaMallocHost(&slab, sizeof(int) * CNT_BLOCK_INTS * per_slab) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        c->cnt_slabs.push_back(slab);
+        for (int k = per_slab - 1; k >= 0; --k) c->cnt_free.push_back((int*)slab + CNT_BLOCK_INTS * k);
+    }
+    int* p = c->cnt_free.back();
+    c->cnt_free.pop_back();
+    return p;
+}
+
 void plan_destroy(Plan* pl) {
     if (!pl) return;
     plan_drop_graphs(pl);
     plan_free_list(pl);
     if (pl->d_sys) dev_free(pl->ctx, pl->d_sys, pl->fixed_bytes);
-    if (pl->h_counters) cudaFreeHost(pl->h_counters);
+    if (pl->h_counters) pl->ctx->cnt_free.push_back(pl->h_counters);
     if (pl->done_ev) cudaEventDestroy(pl->done_ev);
     delete pl;
 }
@@ -339,15 +436,17 @@ nb_status plan_create(nb_ctx* ctx, nb_sys* const* systems, int n, Plan** out, do
     cudaError_t e = cudaMemcpyAsync(pl->d_sys, hs.data(), sizeof(SysDev) * n, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(pl->d_off, off.data(), 4 * off.size(), cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) e = cudaMallocHost(&pl->h_counters, 4 * CNT_N);
+    // (copies from pageable host memory return once the source is consumed,
+    // so the host vectors may go out of scope)
+    if (e == cudaSuccess) {
+        pl->h_counters = ctx_counters_get(ctx);
+        if (!pl->h_counters) e = cudaErrorMemoryAllocation;
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->done_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         plan_destroy(pl);
         return cuda_fail(e, "plan_create");
     }
-    // the memcpys above read host vectors that go out of scope
-    e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) { plan_destroy(pl); return cuda_fail(e, "plan_create sync"); }
     st = plan_alloc_list(pl, items, entries);
     if (st != NB_OK) { plan_destroy(pl); return st; }
     pl->kp = make_kparams(systems[0]);
@@ -568,6 +667,7 @@ nb_status nb_ctx_destroy(nb_ctx* ctx) {
         cudaEventDestroy(t.b);
     }
     for (auto e : ctx->pool) cudaEventDestroy(e);
+    for (void* slab : ctx->cnt_slabs) cudaFreeHost(slab);
     delete ctx;
     return NB_OK;
 }
@@ -682,7 +782,6 @@ nb_status nb_sys_create(nb_ctx* ctx, const nb_params* params, int natoms, const 
     cudaError_t e = cudaMemcpyAsync(y->d_lj, lj.data(), 8 * lj.size(), cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h.acc, 0, 8 * NACC, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h.res, 0, 8 * NRES, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         dev_free(ctx, y->block, y->bytes);
         delete y;
@@ -704,60 +803,10 @@ nb_status nb_sys_destroy(nb_sys* sys) {
 
 nb_status nb_set_exclusions(nb_sys* sys, const int* excl_index, const int* excl_atoms) {
     if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
-    if (!excl_index) return fail(NB_ERR_ARG, "excl_index is NULL");
-    int n = sys->natoms;
-    if (excl_index[0] != 0) return fail(NB_ERR_ARG, "excl_index[0] must be 0");
-    // symmetrise with flat arrays: degree count, prefix, fill, then sort and
-    // de-duplicate each atom's (short) partner list
-    std::vector<int> deg(n + 1, 0);
-    for (int a = 0; a < n; ++a) {
-        if (excl_index[a + 1] < excl_index[a]) return fail(NB_ERR_ARG, "excl_index must be non-decreasing");
-        for (int k = excl_index[a]; k < excl_index[a + 1]; ++k) {
-            int b = excl_atoms[k];
-            if (b < 0 || b >= n) return fail(NB_ERR_ARG, "exclusion partner out of range");
-            if (b == a) continue;
-            ++deg[a + 1];
-            ++deg[b + 1];
-        }
-    }
-    for (int a = 0; a < n; ++a) deg[a + 1] += deg[a];
-    std::vector<int> fillp(deg.begin(), deg.end() - 1), flat(deg[n]);
-    for (int a = 0; a < n; ++a)
-        for (int k = excl_index[a]; k < excl_index[a + 1]; ++k) {
-            int b = excl_atoms[k];
-            if (b == a) continue;
-            flat[fillp[a]++] = b;
-            flat[fillp[b]++] = a;
-        }
-    std::vector<int> idx(n + 1, 0), at;
-    at.reserve(flat.size());
-    for (int a = 0; a < n; ++a) {
-        int* first = flat.data() + deg[a];
-        int* last = flat.data() + deg[a + 1];
-        std::sort(first, last);
-        int* end_u = std::unique(first, last);
-        at.insert(at.end(), first, end_u);
-        idx[a + 1] = (int)at.size();
-    }
-    if (sys->d_excl) dev_free(sys->ctx, sys->d_excl, sys->excl_bytes);
-    sys->d_excl = nullptr;
-    size_t bytes = 4 * (idx.size() + std::max<size_t>(1, at.size()));
-    void* p = nullptr;
-    nb_status s = dev_alloc(sys->ctx, &p, bytes);
+    std::vector<int> idx, at;
+    nb_status s = excl_symmetrise(sys->natoms, excl_index, excl_atoms, idx, at);
     if (s != NB_OK) return s;
-    sys->d_excl = (int*)p;
-    sys->excl_bytes = bytes;
-    NB_CK(cudaMemcpyAsync(sys->d_excl, idx.data(), 4 * idx.size(), cudaMemcpyHostToDevice, sys->ctx->stream));
-    if (!at.empty())
-        NB_CK(cudaMemcpyAsync(sys->d_excl + idx.size(), at.data(), 4 * at.size(), cudaMemcpyHostToDevice,
-                              sys->ctx->stream));
-    NB_CK(cudaStreamSynchronize(sys->ctx->stream));
-    sys->h.excl_index = sys->d_excl;
-    sys->h.excl_atoms = sys->d_excl + idx.size();
-    // descriptors held by plans are stale now
-    if (sys->plan) { plan_destroy(sys->plan); sys->plan = nullptr; }
-    sys->listed = false;
-    return NB_OK;
+    return sys_upload_exclusions(sys, idx, at);
 }
 
 static nb_status ensure_plan(nb_sys* sys) {

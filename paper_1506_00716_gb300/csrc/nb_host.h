@@ -37,6 +37,10 @@ struct nb_ctx {
     unsigned tuning_gen = 0;
     std::vector<TimedLaunch> pending;
     std::vector<cudaEvent_t> pool;
+    // pinned counter read-back blocks of plans, carved from slabs so that
+    // creating and destroying a plan allocates and frees no pinned memory
+    std::vector<int*> cnt_free;
+    std::vector<void*> cnt_slabs;
     double tot_ms[NB_NSTAGE] = {0};
     long long launches[NB_NSTAGE] = {0};
 };
@@ -101,5 +105,11 @@ nb_status plan_create(nb_ctx* ctx, nb_sys* const* systems, int n, Plan** out, do
 void plan_destroy(Plan* pl);
 PlanLaunch launch_of(const Plan* pl);
 nb_status stage_coords(nb_sys* s, const float* xq, const int* type);
+// Symmetric, sorted, duplicate-free exclusion CSR from the caller's CSR
+// (validated; a list that already has that form is copied as it is).
+nb_status excl_symmetrise(int n, const int* excl_index, const int* excl_atoms, std::vector<int>& idx,
+                          std::vector<int>& at);
+// Upload a CSR made by excl_symmetrise to the system's device buffers.
+nb_status sys_upload_exclusions(nb_sys* sys, const std::vector<int>& idx, const std::vector<int>& at);
 
 }  // namespace nbgb

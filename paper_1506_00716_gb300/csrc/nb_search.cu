@@ -312,50 +312,76 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
 
 constexpr int PRUNE_WARPS = 8;
 
+// Prune (Section 3.3): drop the entries of which no atom pair whose mask bit
+// is set lies within the list radius.  A warp takes one work item at a time.
+// Per chunk of 32 entries, lane k loads entry k's j-cluster index and mask
+// (coalesced); the chunk is then tested in steps of 16 entries, lane = 8 g +
+// j holding j-atom j of four entries g, g + 4, g + 8, g + 12 (four
+// independent coalesced loads in flight) against the eight i-atoms of the
+// item, which every lane keeps in registers.  Kept entries are compacted in
+// place, in order; a write never passes the entries still to be read.
 __global__ void __launch_bounds__(PRUNE_WARPS * 32)
 k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     const int lane = threadIdx.x & 31;
+    const int jj = lane & 7;
+    const int g = lane >> 3;
     const int nitems = min(list.counters[CNT_ITEMS], list.item_cap);
     for (int it = blockIdx.x * PRUNE_WARPS + (threadIdx.x >> 5); it < nitems;
          it += gridDim.x * PRUNE_WARPS) {
-        int4 item = list.items[it];
+        const int4 item = list.items[it];
+        if (item.y >= item.z) continue;
         const SysDev& d = sys[item.w >> 5];
         const float rl2 = d.rl2_prune;
-        int sh = item.w & 31;
-        float Sx = (sh / 9 - 1) * d.L[0], Sy = ((sh / 3) % 3 - 1) * d.L[1], Sz = (sh % 3 - 1) * d.L[2];
+        const int sh = item.w & 31;
+        const float Sx = (sh / 9 - 1) * d.L[0], Sy = ((sh / 3) % 3 - 1) * d.L[1], Sz = (sh % 3 - 1) * d.L[2];
         float3 xi[CL];
 #pragma unroll
         for (int k = 0; k < CL; ++k) {
-            float4 v = d.xq_s[item.x * CL + k];
+            const float4 v = d.xq_s[item.x * CL + k];
             xi[k] = make_float3(v.x + Sx, v.y + Sy, v.z + Sz);
         }
         int write = item.y;
         for (int base = item.y; base < item.z; base += 32) {
-            int e = base + lane;
-            bool keep = false;
+            const int n = min(32, item.z - base);
             int cjv = 0;
-            unsigned long long m = 0;
-            if (e < item.z) {
-                cjv = list.cj[e];
-                m = list.mask[e];
-                for (int jj = 0; jj < CL && !keep; ++jj) {
-                    float4 xj = d.xq_s[cjv * CL + jj];
+            unsigned long long m = 0ull;
+            if (lane < n) {
+                cjv = list.cj[base + lane];
+                m = list.mask[base + lane];
+            }
+            unsigned keep = 0;  // bit k: entry base + k is kept
+            for (int q0 = 0; q0 < n; q0 += 16) {
+                float4 xj[4];
+                unsigned long long mq[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = q0 + 4 * u + g;
+                    const int cjk = __shfl_sync(FULL, cjv, k & 31);
+                    mq[u] = __shfl_sync(FULL, m, k & 31);
+                    xj[u] = k < n ? d.xq_s[cjk * CL + jj] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    bool near = false;
 #pragma unroll
                     for (int ii = 0; ii < CL; ++ii) {
-                        float dx = xi[ii].x - xj.x, dy = xi[ii].y - xj.y, dz = xi[ii].z - xj.z;
-                        float r2 = dx * dx + dy * dy + dz * dz;
-                        bool bit = (m >> rot_bit(ii, jj)) & 1ull;
-                        keep = keep || (bit && r2 < rl2);
+                        const float dx = xi[ii].x - xj[u].x, dy = xi[ii].y - xj[u].y, dz = xi[ii].z - xj[u].z;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const bool bit = (mq[u] >> rot_bit(ii, jj)) & 1ull;
+                        near = near || (bit && r2 < rl2);
                     }
+                    const unsigned bal = __ballot_sync(FULL, near);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        keep |= (((bal >> (8 * q)) & 0xffu) != 0u ? 1u : 0u) << (q0 + 4 * u + q);
                 }
             }
-            unsigned bal = __ballot_sync(FULL, keep);
-            if (keep) {
-                int idx = write + __popc(bal & ((1u << lane) - 1u));
+            if (lane < n && ((keep >> lane) & 1u)) {
+                const int idx = write + __popc(keep & ((1u << lane) - 1u));
                 list.cj[idx] = cjv;
                 list.mask[idx] = m;
             }
-            write += __popc(bal);
+            write += __popc(keep);
         }
         if (lane == 0) {
             list.items[it].z = write;

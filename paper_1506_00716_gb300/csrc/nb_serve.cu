@@ -143,7 +143,7 @@ void launch_wave(nb_server* s, int k, std::vector<Request*> reqs) {
     for (Request* r : reqs) {
         nb_sys* y = nullptr;
         nb_status stt = nb_sys_create(ctx, &s->p, r->natoms, r->box, &y);
-        if (stt == NB_OK && r->has_excl) stt = nb_set_exclusions(y, r->ei.data(), r->ea.data());
+        if (stt == NB_OK && r->has_excl) stt = sys_upload_exclusions(y, r->ei, r->ea);
         if (stt == NB_OK) stt = stage_coords(y, r->xq.data(), r->type.data());
         if (stt != NB_OK) {
             if (y) nb_sys_destroy(y);
@@ -389,12 +389,15 @@ nb_status nb_server_submit(nb_server* s, int natoms, const double box[3], const 
     r->xq.assign(xq, xq + 4 * (size_t)natoms);
     r->type.assign(type, type + natoms);
     if (excl_index) {
+        // validated and symmetrised here, on the caller's thread
+        st = excl_symmetrise(natoms, excl_index, excl_atoms, r->ei, r->ea);
+        if (st != NB_OK) {
+            delete r;
+            return st;
+        }
         r->has_excl = true;
-        r->ei.assign(excl_index, excl_index + natoms + 1);
-        r->ea.assign(excl_atoms, excl_atoms + excl_index[natoms]);
-        if (r->ea.empty()) r->ea.push_back(0);
     }
-    r->est_bytes = est + 4 * (size_t)(natoms + 1 + (r->has_excl ? excl_index[natoms] : 0)) + 4096;
+    r->est_bytes = est + 4 * (r->ei.size() + r->ea.size() + 1) + 4096;
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lock(s->mu);
