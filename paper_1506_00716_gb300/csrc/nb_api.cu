@@ -514,9 +514,15 @@ nb_status plan_build_list(Plan* pl) {
     return fail(NB_ERR_CAPACITY, "pair list did not fit after growing its buffers");
 }
 
-nb_status plan_eval(Plan* pl, unsigned flags, bool coords) {
+nb_status plan_eval(Plan* pl, unsigned flags, bool coords, const PlanLaunch* ext) {
     cudaStream_t st = pl->ctx->stream;
     PlanLaunch p = launch_of(pl);
+    if (ext) {
+        p.x_ext = ext->x_ext;
+        p.f_ext = ext->f_ext;
+        p.e_ext = ext->e_ext;
+        p.v_ext = ext->v_ext;
+    }
     {
         StageScope sc(pl->ctx, NB_STAGE_ZERO);
         NB_CK(launch_prepare(p, coords, st));
@@ -894,14 +900,22 @@ nb_status nb_forces(nb_sys* sys, const float* x_new, float* f, double* energy, d
     if (!sys->listed) return fail(NB_ERR_STATE, "nb_forces needs a pair list (nb_pairlist_build)");
     Plan* pl = sys->plan;
     cudaStream_t st = sys->ctx->stream;
-    if (x_new) {
+    // device arrays of the caller are read and written by the kernels
+    // themselves; host arrays go through the system's staging buffers
+    PlanLaunch ext{};
+    if (x_new && is_device_ptr(x_new)) ext.x_ext = x_new;
+    if (f && is_device_ptr(f)) ext.f_ext = f;
+    if (energy && is_device_ptr(energy)) ext.e_ext = energy;
+    if (virial && is_device_ptr(virial)) ext.v_ext = virial;
+    if (x_new && !ext.x_ext) {
         StageScope sc(sys->ctx, NB_STAGE_COORD);
-        NB_CK(cudaMemcpyAsync(sys->h.x_new, x_new, 12 * (size_t)sys->natoms, cudaMemcpyDefault, st));
+        NB_CK(cudaMemcpyAsync(sys->h.x_new, x_new, 12 * (size_t)sys->natoms, cudaMemcpyHostToDevice, st));
     }
-    nb_status s = plan_eval(pl, flags, x_new != nullptr);
+    nb_status s = plan_eval(pl, flags, x_new != nullptr, &ext);
     if (s != NB_OK) return s;
     bool need_sync = false;
-    s = copy_out(sys, f, energy, virial, flags, &need_sync);
+    s = copy_out(sys, ext.f_ext ? nullptr : f, ext.e_ext ? nullptr : energy, ext.v_ext ? nullptr : virial,
+                 flags, &need_sync);
     if (s != NB_OK) return s;
     if (need_sync) NB_CK(cudaStreamSynchronize(st));
     return NB_OK;

@@ -118,6 +118,13 @@ struct PlanLaunch {
     ListDev list;
     KParams kp;
     int num_sms;
+    // single-system evaluations only (nsys == 1), each may be null: the
+    // caller's device arrays read or written directly instead of through a
+    // staging copy
+    const float* x_ext;      // [natoms * 3] new coordinates (k_prepare)
+    float* f_ext;            // [natoms * 3] forces (k_finish)
+    double* e_ext;           // [2] E_LJ, E_C (k_finish)
+    double* v_ext;           // [9] virial (k_finish)
 };
 
 // Shift index <-> vector.

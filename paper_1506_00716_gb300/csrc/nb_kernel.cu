@@ -309,7 +309,7 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
 // recorded by the last grid put (stale-list evaluations).
 template <bool COORD>
 __global__ void k_prepare(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys,
-                          int tot_slots, int* __restrict__ counters) {
+                          int tot_slots, int* __restrict__ counters, const float* __restrict__ x_ext) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {
         counters[CNT_WORK] = 0;
@@ -329,10 +329,11 @@ __global__ void k_prepare(const SysDev* __restrict__ sys, const int* __restrict_
     int kx = (int)(signed char)(wk & 0xff);
     int ky = (int)(signed char)((wk >> 8) & 0xff);
     int kz = (int)(signed char)((wk >> 16) & 0xff);
+    const float* xn = x_ext ? x_ext : d.x_new;
     float4 v = d.xq_s[slot];
-    v.x = d.x_new[3 * a + 0] - (float)kx * d.L[0];
-    v.y = d.x_new[3 * a + 1] - (float)ky * d.L[1];
-    v.z = d.x_new[3 * a + 2] - (float)kz * d.L[2];
+    v.x = xn[3 * a + 0] - (float)kx * d.L[0];
+    v.y = xn[3 * a + 1] - (float)ky * d.L[1];
+    v.z = xn[3 * a + 2] - (float)kz * d.L[2];
     d.xq_s[slot] = v;
 }
 
@@ -340,7 +341,8 @@ __global__ void k_prepare(const SysDev* __restrict__ sys, const int* __restrict_
 // ENER_VIR, the final FP64 combination of each system's accumulators.
 template <bool ENER_VIR>
 __global__ void k_finish(const SysDev* __restrict__ sys, const int* __restrict__ atom_off, int nsys,
-                         int tot_atoms) {
+                         int tot_atoms, float* __restrict__ f_ext, double* __restrict__ e_ext,
+                         double* __restrict__ v_ext) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (ENER_VIR && t < nsys) {
         const SysDev& d = sys[t];
@@ -358,6 +360,12 @@ __global__ void k_finish(const SysDev* __restrict__ sys, const int* __restrict__
         r[9] = -0.5 * a[ACC_VYZ];
         r[10] = -0.5 * a[ACC_VZZ];
         r[11] = a[ACC_NPAIR];
+        if (e_ext) {
+            e_ext[0] = r[0];
+            e_ext[1] = r[1];
+        }
+        if (v_ext)
+            for (int k = 0; k < 9; ++k) v_ext[k] = r[2 + k];
     }
     if (t >= tot_atoms) return;
     int s = find_sys_dev(atom_off, nsys, t);
@@ -367,6 +375,11 @@ __global__ void k_finish(const SysDev* __restrict__ sys, const int* __restrict__
     d.f_out[3 * a + 0] = f.x;
     d.f_out[3 * a + 1] = f.y;
     d.f_out[3 * a + 2] = f.z;
+    if (f_ext) {
+        f_ext[3 * a + 0] = f.x;
+        f_ext[3 * a + 1] = f.y;
+        f_ext[3 * a + 2] = f.z;
+    }
 }
 
 template <int COUL, bool VIR, int MINB>
@@ -387,10 +400,11 @@ cudaError_t launch_prepare(const PlanLaunch& p, bool coords, cudaStream_t st) {
     int tot = p.tot_clcap * CL;
     int bs = 256;
     unsigned blocks = (unsigned)((tot + bs - 1) / bs + 1);
+    const float* x_ext = p.nsys == 1 ? p.x_ext : nullptr;
     if (coords)
-        k_prepare<true><<<blocks, bs, 0, st>>>(p.d_sys, p.d_cl_off, p.nsys, tot, p.list.counters);
+        k_prepare<true><<<blocks, bs, 0, st>>>(p.d_sys, p.d_cl_off, p.nsys, tot, p.list.counters, x_ext);
     else
-        k_prepare<false><<<blocks, bs, 0, st>>>(p.d_sys, p.d_cl_off, p.nsys, tot, p.list.counters);
+        k_prepare<false><<<blocks, bs, 0, st>>>(p.d_sys, p.d_cl_off, p.nsys, tot, p.list.counters, nullptr);
     return cudaGetLastError();
 }
 
@@ -414,10 +428,15 @@ cudaError_t launch_finalize(const PlanLaunch& p, unsigned flags, cudaStream_t st
     int bs = 256;
     int n = p.tot_atoms > p.nsys ? p.tot_atoms : p.nsys;
     unsigned blocks = (unsigned)((n + bs - 1) / bs);
+    const bool one = p.nsys == 1;
+    float* f_ext = one ? p.f_ext : nullptr;
+    double* e_ext = one && (flags & NB_F_ENERGY) ? p.e_ext : nullptr;
+    double* v_ext = one && (flags & NB_F_VIRIAL) ? p.v_ext : nullptr;
     if (flags & (NB_F_ENERGY | NB_F_VIRIAL))
-        k_finish<true><<<blocks, bs, 0, st>>>(p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms);
+        k_finish<true><<<blocks, bs, 0, st>>>(p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms, f_ext, e_ext, v_ext);
     else
-        k_finish<false><<<blocks, bs, 0, st>>>(p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms);
+        k_finish<false><<<blocks, bs, 0, st>>>(p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms, f_ext, nullptr,
+                                               nullptr);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,137 @@
+"""Parity at the full sizes of the timed workloads.
+
+3,000,000-atom Ewald box, in the launch configuration the benchmark uses
+(its tuning table entry): the oracle's O(N) per-atom force loop on sampled
+atoms against the GPU forces of those atoms, plus properties that hold at any
+size (net force ~ 0, invariance under a permutation of the axes).
+
+64-box ensemble, through the batched path (one launch per stage over every
+system): sampled forces of every system against the oracle, and the full
+energies and virial of the systems small enough for the O(N^2) oracle.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1506_00716_gb300 import autotune, nb
+from paper_1506_00716_gb300 import waterbox as wb
+from _support import rel_rms
+
+pytestmark = pytest.mark.gpu
+
+F_TOL = 1e-5
+E_TOL = 1e-6
+V_TOL = 1e-6
+FLAGS = nb.NB_F_ENERGY | nb.NB_F_VIRIAL
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1506_00716_gb300 import build as nbbuild
+
+    nbbuild.build()
+    torch.cuda.set_device(0)
+    return torch
+
+
+def _eval(ctx, s, p):
+    h = nb.nb_sys_create(ctx, p, s.n, s.box)
+    try:
+        nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
+        nb.nb_grid_put(h, s.xq(), s.type)
+        nb.nb_pairlist_build(h)
+        f = np.zeros((s.n, 3), dtype=np.float32)
+        e = np.zeros(2)
+        v = np.zeros(9)
+        nb.nb_forces(h, None, f, e, v, FLAGS)
+        npairs = nb.nb_eval_info(h)["n_pairs"]
+    finally:
+        nb.nb_sys_destroy(h)
+    return f, e, v, npairs
+
+
+def test_large_box_sampled_forces_and_invariants(torch_cuda):
+    torch = torch_cuda
+    s = wb.large_box(seed=3)
+    p = wb.params_ewald()
+    ctx = nb.nb_ctx_create(0, None, 0)
+    try:
+        autotune.apply(ctx, "ewald", s.n, gpu=torch.cuda.get_device_name(0))
+        f, e, v, npairs = _eval(ctx, s, p)
+        rng = np.random.default_rng(31)
+        sel = np.sort(rng.choice(s.n, size=192, replace=False)).astype(np.int32)
+        ref = oracle.forces(s, p, sel)
+        assert rel_rms(f[sel], ref) <= F_TOL
+        # net force: the j-force of every pair is the negated i-force
+        rms = np.sqrt((f.astype(np.float64) ** 2).mean())
+        assert np.linalg.norm(f.astype(np.float64).sum(0)) <= 1e-4 * np.sqrt(s.n) * rms
+        assert np.isfinite(e).all() and np.isfinite(v).all()
+        # about 6.33e8 interacting pairs at 100.2 atoms/nm^3 and rc = 1 nm
+        assert 6.0e8 < npairs < 6.7e8
+
+        # permute the axes (cubic box): another grid, cluster assignment and
+        # summation order, the same physics.  Forces and virial permute; the
+        # pair count (exact cut-off decisions) and the double-float energies
+        # are unchanged
+        perm = [1, 2, 0]
+        t = dataclasses.replace(s, x=np.ascontiguousarray(s.x[:, perm]))
+        f2, e2, v2, npairs2 = _eval(ctx, t, p)
+        assert npairs2 == npairs
+        assert rel_rms(f2, f[:, perm]) <= 1e-6
+        assert np.abs(e2 - e).max() <= 1e-9 * np.abs(e).max()
+        v3 = v.reshape(3, 3)[np.ix_(perm, perm)].reshape(-1)
+        assert np.abs(v2 - v3).max() <= 1e-6 * np.linalg.norm(v)
+    finally:
+        nb.nb_ctx_destroy(ctx)
+
+
+def test_ensemble_batched_against_oracle(torch_cuda):
+    torch = torch_cuda
+    systems = wb.ensemble(64, 1000, 32000, seed=4)
+    p = wb.params_rf()
+    stream = torch.cuda.Stream()
+    ctx = nb.nb_ctx_create(0, stream, 0)
+    hs = []
+    try:
+        tot = sum(x.n for x in systems)
+        autotune.apply(ctx, "rf", tot // len(systems), gpu=torch.cuda.get_device_name(0))
+        for x in systems:
+            h = nb.nb_sys_create(ctx, p, x.n, x.box)
+            nb.nb_set_exclusions(h, x.excl_index, x.excl_atoms)
+            nb.nb_sys_set_coords(h, x.xq(), x.type)
+            hs.append(h)
+        b = nb.nb_batch_create(ctx, hs)
+        try:
+            for attempt in range(3):
+                try:
+                    assert nb.nb_batch_poll(b, nb.nb_batch_submit(b, FLAGS), 60_000_000)
+                    break
+                except nb.NbError as exc:  # list outgrew its estimate: grown, submit again
+                    assert exc.status == 9 and attempt < 2
+            rng = np.random.default_rng(32)
+            order = np.argsort([x.n for x in systems])
+            full = set(order[:12].tolist())  # the smallest systems: full O(N^2) oracle
+            for k, (h, x) in enumerate(zip(hs, systems)):
+                f = np.zeros((x.n, 3), dtype=np.float32)
+                e = np.zeros(2)
+                v = np.zeros(9)
+                nb.nb_sys_results(h, f, e, v)
+                sel = np.sort(rng.choice(x.n, size=48, replace=False)).astype(np.int32)
+                assert rel_rms(f[sel], oracle.forces(x, p, sel)) <= F_TOL, k
+                if k in full:
+                    ref = oracle.energy_virial(x, p)
+                    assert abs(e[0] - ref["e_lj"]) <= E_TOL * abs(ref["e_lj"]), k
+                    assert abs(e[1] - ref["e_coul"]) <= E_TOL * abs(ref["e_coul"]), k
+                    vr = ref["virial"].reshape(-1)
+                    assert np.abs(v - vr).max() <= V_TOL * np.linalg.norm(vr), k
+        finally:
+            nb.nb_batch_destroy(b)
+    finally:
+        for h in hs:
+            nb.nb_sys_destroy(h)
+        nb.nb_ctx_destroy(ctx)
