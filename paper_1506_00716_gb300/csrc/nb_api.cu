@@ -144,22 +144,22 @@ nb_status excl_symmetrise(int n, const int* excl_index, const int* excl_atoms, s
     return NB_OK;
 }
 
-nb_status sys_upload_exclusions(nb_sys* sys, const std::vector<int>& idx, const std::vector<int>& at) {
+nb_status sys_upload_exclusions(nb_sys* sys, const int* idx, const int* at) {
     if (sys->d_excl) dev_free(sys->ctx, sys->d_excl, sys->excl_bytes);
     sys->d_excl = nullptr;
-    size_t bytes = 4 * (idx.size() + std::max<size_t>(1, at.size()));
+    const size_t nidx = (size_t)sys->natoms + 1;
+    const size_t nat = (size_t)idx[sys->natoms];
+    size_t bytes = 4 * (nidx + std::max<size_t>(1, nat));
     void* p = nullptr;
     nb_status s = dev_alloc(sys->ctx, &p, bytes);
     if (s != NB_OK) return s;
     sys->d_excl = (int*)p;
     sys->excl_bytes = bytes;
-    // pageable sources: each copy returns once it has consumed its source
-    NB_CK(cudaMemcpyAsync(sys->d_excl, idx.data(), 4 * idx.size(), cudaMemcpyHostToDevice, sys->ctx->stream));
-    if (!at.empty())
-        NB_CK(cudaMemcpyAsync(sys->d_excl + idx.size(), at.data(), 4 * at.size(), cudaMemcpyHostToDevice,
-                              sys->ctx->stream));
+    NB_CK(cudaMemcpyAsync(sys->d_excl, idx, 4 * nidx, cudaMemcpyHostToDevice, sys->ctx->stream));
+    if (nat > 0)
+        NB_CK(cudaMemcpyAsync(sys->d_excl + nidx, at, 4 * nat, cudaMemcpyHostToDevice, sys->ctx->stream));
     sys->h.excl_index = sys->d_excl;
-    sys->h.excl_atoms = sys->d_excl + idx.size();
+    sys->h.excl_atoms = sys->d_excl + nidx;
     // descriptors held by plans are stale now
     if (sys->plan) { plan_destroy(sys->plan); sys->plan = nullptr; }
     sys->listed = false;
@@ -812,7 +812,8 @@ nb_status nb_set_exclusions(nb_sys* sys, const int* excl_index, const int* excl_
     std::vector<int> idx, at;
     nb_status s = excl_symmetrise(sys->natoms, excl_index, excl_atoms, idx, at);
     if (s != NB_OK) return s;
-    return sys_upload_exclusions(sys, idx, at);
+    // pageable vectors: each copy has consumed its source when it returns
+    return sys_upload_exclusions(sys, idx.data(), at.data());
 }
 
 static nb_status ensure_plan(nb_sys* sys) {

@@ -109,7 +109,9 @@ nb_status stage_coords(nb_sys* s, const float* xq, const int* type);
 // (validated; a list that already has that form is copied as it is).
 nb_status excl_symmetrise(int n, const int* excl_index, const int* excl_atoms, std::vector<int>& idx,
                           std::vector<int>& at);
-// Upload a CSR made by excl_symmetrise to the system's device buffers.
-nb_status sys_upload_exclusions(nb_sys* sys, const std::vector<int>& idx, const std::vector<int>& at);
+// Upload a CSR made by excl_symmetrise (idx: natoms + 1 entries, at: idx[natoms])
+// to the system's device buffers.  Pageable sources are consumed when the call
+// returns; pinned sources must stay valid until the stream has passed the copies.
+nb_status sys_upload_exclusions(nb_sys* sys, const int* idx, const int* at);
 
 }  // namespace nbgb

@@ -60,6 +60,15 @@ __device__ __forceinline__ unsigned long long row_mask(int ni) {
 
 constexpr int MAX_RUNS = 32;
 
+// Entries of cluster pairs whose bounding boxes lie closer than the list
+// radius minus this margin (nm) are kept without testing their atom pairs:
+// with clusters about 0.4 nm across, such a pair practically always has an
+// atom pair inside the radius, and an entry kept without one only adds
+// masked-out work.  The others carry PRUNE_CHECK in their cluster index
+// until the prune has tested them.
+constexpr float PRUNE_SURE_MARGIN = 0.3f;
+constexpr int PRUNE_CHECK = 1 << 30;
+
 struct SearchWarpSmem {
     int cj[SEARCH_BUF];
     unsigned long long mask[SEARCH_BUF];
@@ -152,6 +161,8 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
     const unsigned long long rmask_i = row_mask(nri);
     const float rl = d.rl_search;
     const float rl2 = rl * rl;
+    const float rbb = fmaxf(0.f, rl - PRUNE_SURE_MARGIN);
+    const float rbb2 = rbb * rbb;
     const float eps = 1e-5f * fmaxf(1.f, fmaxf(d.L[0], fmaxf(d.L[1], d.L[2])));
 
     // exclusion partners (sorted slots) of this cluster's atoms, and a
@@ -248,6 +259,7 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
                         const int own_c0 = __shfl_sync(FULL, c0, lo);
                         const int cur = own_c0 + t - (own_incl - own_cnt);
                         bool pass = false;
+                        float g2 = 0.f;
                         float4 lj = make_float4(0.f, 0.f, 0.f, 0.f);
                         if (t < total) {
                             lj = d.bb[2 * cur];
@@ -255,8 +267,8 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
                             const float gx = gap(lx, hx, lj.x, hj.x);
                             const float gy = gap(ly, hy, lj.y, hj.y);
                             const float gz = gap(lz, hz, lj.z, hj.z);
-                            pass = gx * gx + gy * gy + gz * gz < rl2 &&
-                                   (cur > ci || (cur == ci && shift >= SHIFT_ZERO));
+                            g2 = gx * gx + gy * gy + gz * gz;
+                            pass = g2 < rl2 && (cur > ci || (cur == ci && shift >= SHIFT_ZERO));
                         }
                         const unsigned bal = __ballot_sync(FULL, pass);
                         const int np = __popc(bal);
@@ -297,7 +309,9 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
                                 }
                             }
                             const int idx = nbuf + __popc(bal & ((1u << lane) - 1u));
-                            sm.cj[idx] = cur;
+                            // entries whose boxes are not clearly inside the
+                            // list radius get their atom pairs tested by the prune
+                            sm.cj[idx] = g2 < rbb2 ? cur : (cur | PRUNE_CHECK);
                             sm.mask[idx] = m;
                         }
                         nbuf += np;
@@ -315,19 +329,21 @@ constexpr int PRUNE_WARPS = 8;
 // Prune (Section 3.3): drop the entries of which no atom pair whose mask bit
 // is set lies within the list radius.  A warp takes one work item at a time.
 // Per chunk of 32 entries, lane k loads entry k's j-cluster index and mask
-// (coalesced); the chunk is then tested in steps of 16 entries, lane = 8 g +
-// j holding j-atom j of four entries g, g + 4, g + 8, g + 12 (four
-// independent coalesced loads in flight) against the eight i-atoms of the
-// item, which every lane keeps in registers.  Kept entries are compacted in
-// place, in order; a write never passes the entries still to be read.
+// (coalesced).  Entries the search marked as certain are kept as they are;
+// the others are tested 16 at a time, lane = 8 g + j holding j-atom j of four
+// of them (four independent coalesced loads in flight) against the eight
+// i-atoms of the item, which every lane keeps in registers.  Kept entries are
+// compacted in place, in order, without the mark; a write never passes the
+// entries still to be read.
 __global__ void __launch_bounds__(PRUNE_WARPS * 32)
 k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
+    __shared__ unsigned char s_rank[PRUNE_WARPS][32];
     const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
     const int jj = lane & 7;
     const int g = lane >> 3;
     const int nitems = min(list.counters[CNT_ITEMS], list.item_cap);
-    for (int it = blockIdx.x * PRUNE_WARPS + (threadIdx.x >> 5); it < nitems;
-         it += gridDim.x * PRUNE_WARPS) {
+    for (int it = blockIdx.x * PRUNE_WARPS + w; it < nitems; it += gridDim.x * PRUNE_WARPS) {
         const int4 item = list.items[it];
         if (item.y >= item.z) continue;
         const SysDev& d = sys[item.w >> 5];
@@ -345,20 +361,28 @@ k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             const int n = min(32, item.z - base);
             int cjv = 0;
             unsigned long long m = 0ull;
+            bool chk = false;
             if (lane < n) {
-                cjv = list.cj[base + lane];
+                const int c = list.cj[base + lane];
+                chk = (c & PRUNE_CHECK) != 0;
+                cjv = c & ~PRUNE_CHECK;
                 m = list.mask[base + lane];
             }
-            unsigned keep = 0;  // bit k: entry base + k is kept
-            for (int q0 = 0; q0 < n; q0 += 16) {
+            const unsigned chk_bal = __ballot_sync(FULL, chk);
+            unsigned keep = __ballot_sync(FULL, lane < n && !chk);  // bit k: entry base + k is kept
+            const int nchk = __popc(chk_bal);
+            if (chk) s_rank[w][__popc(chk_bal & ((1u << lane) - 1u))] = (unsigned char)lane;
+            __syncwarp();
+            for (int q0 = 0; q0 < nchk; q0 += 16) {
                 float4 xj[4];
                 unsigned long long mq[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int k = q0 + 4 * u + g;
-                    const int cjk = __shfl_sync(FULL, cjv, k & 31);
-                    mq[u] = __shfl_sync(FULL, m, k & 31);
-                    xj[u] = k < n ? d.xq_s[cjk * CL + jj] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+                    const int src = k < nchk ? s_rank[w][k] : 0;
+                    const int cjk = __shfl_sync(FULL, cjv, src);
+                    mq[u] = __shfl_sync(FULL, m, src);
+                    xj[u] = k < nchk ? d.xq_s[cjk * CL + jj] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -372,10 +396,13 @@ k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
                     }
                     const unsigned bal = __ballot_sync(FULL, near);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        keep |= (((bal >> (8 * q)) & 0xffu) != 0u ? 1u : 0u) << (q0 + 4 * u + q);
+                    for (int q = 0; q < 4; ++q) {
+                        const int k = q0 + 4 * u + q;
+                        if (k < nchk && ((bal >> (8 * q)) & 0xffu) != 0u) keep |= 1u << s_rank[w][k];
+                    }
                 }
             }
+            __syncwarp();
             if (lane < n && ((keep >> lane) & 1u)) {
                 const int idx = write + __popc(keep & ((1u << lane) - 1u));
                 list.cj[idx] = cjv;

@@ -13,6 +13,7 @@
 // one wave's force kernel runs, the next wave's upload, grid and search run
 // on the other stream.
 #include <algorithm>
+#include <cstring>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -34,8 +35,14 @@ struct Request {
     int natoms = 0;
     double box[3] = {0, 0, 0};
     unsigned flags = 0;
-    std::vector<float> xq;
-    std::vector<int> type, ei, ea;
+    // inputs, copied at submission into one pinned block (the uploads are
+    // then plain DMA): x y z q, types, and the symmetric exclusion CSR
+    void* pin = nullptr;
+    size_t pin_class = 0;
+    const float* xq = nullptr;
+    const int* type = nullptr;
+    const int* ei = nullptr;
+    const int* ea = nullptr;
     bool has_excl = false;
     size_t est_bytes = 0;
     // results
@@ -84,6 +91,44 @@ struct Wave {
     bool busy = false;
 };
 
+// Pinned host blocks in power-of-two size classes, reused across requests so
+// that steady-state serving allocates no pinned memory.
+struct PinnedPool {
+    std::mutex mu;
+    std::unordered_map<size_t, std::vector<void*>> free_blocks;
+    std::vector<void*> all;
+    void* get(size_t bytes, size_t* cls) {
+        size_t c = (size_t)1 << 16;
+        while (c < bytes) c <<= 1;
+        *cls = c;
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            auto& v = free_blocks[c];
+            if (!v.empty()) {
+                void* p = v.back();
+                v.pop_back();
+                return p;
+            }
+        }
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, c, cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        std::lock_guard<std::mutex> lock(mu);
+        all.push_back(p);
+        return p;
+    }
+    void put(void* p, size_t cls) {
+        if (!p) return;
+        std::lock_guard<std::mutex> lock(mu);
+        free_blocks[cls].push_back(p);
+    }
+    ~PinnedPool() {
+        for (void* p : all) cudaFreeHost(p);
+    }
+};
+
 }  // namespace
 
 struct nb_server {
@@ -103,6 +148,7 @@ struct nb_server {
     std::condition_variable cv_sched, cv_done;
     std::deque<Request*> pending;
     std::unordered_map<unsigned long long, Request*> reqs;
+    PinnedPool pinned;
     bool stop = false;
     unsigned long long next_id = 1;
     std::thread thread;
@@ -110,7 +156,10 @@ struct nb_server {
 
 namespace {
 
+// Called once the device no longer reads the request's pinned inputs.
 void finish(nb_server* s, Request* r, nb_status st, const std::string& msg) {
+    s->pinned.put(r->pin, r->pin_class);
+    r->pin = nullptr;
     r->status = st;
     r->err = msg;
     r->t_done = Clock::now();
@@ -125,6 +174,8 @@ void launch_wave(nb_server* s, int k, std::vector<Request*> reqs) {
     w = Wave();
     nb_ctx* ctx = s->ctxs[k];
     auto fail_all = [&](nb_status code, const std::string& msg) {
+        // uploads already enqueued still read the requests' pinned inputs
+        cudaStreamSynchronize(s->streams[k]);
         for (nb_sys* y : w.systems) nb_sys_destroy(y);
         w.systems.clear();
         std::lock_guard<std::mutex> lock(s->mu);
@@ -144,7 +195,7 @@ void launch_wave(nb_server* s, int k, std::vector<Request*> reqs) {
         nb_sys* y = nullptr;
         nb_status stt = nb_sys_create(ctx, &s->p, r->natoms, r->box, &y);
         if (stt == NB_OK && r->has_excl) stt = sys_upload_exclusions(y, r->ei, r->ea);
-        if (stt == NB_OK) stt = stage_coords(y, r->xq.data(), r->type.data());
+        if (stt == NB_OK) stt = stage_coords(y, r->xq, r->type);
         if (stt != NB_OK) {
             if (y) nb_sys_destroy(y);
             fail_all(stt, nb_last_error());
@@ -382,26 +433,42 @@ nb_status nb_server_submit(nb_server* s, int natoms, const double box[3], const 
     size_t est = 0;
     nb_status st = nb_sys_footprint(&s->p, natoms, box, &est);
     if (st != NB_OK) return st;
+    // exclusions validated and symmetrised here, on the caller's thread
+    std::vector<int> ei, ea;
+    if (excl_index) {
+        st = excl_symmetrise(natoms, excl_index, excl_atoms, ei, ea);
+        if (st != NB_OK) return st;
+    }
     Request* r = new Request();
     r->natoms = natoms;
     for (int d = 0; d < 3; ++d) r->box[d] = box[d];
     r->flags = flags;
-    r->xq.assign(xq, xq + 4 * (size_t)natoms);
-    r->type.assign(type, type + natoms);
+    const size_t n = (size_t)natoms;
+    const size_t bytes = 16 * n + 4 * n + 4 * (ei.size() + ea.size());
+    char* b = (char*)s->pinned.get(bytes, &r->pin_class);
+    if (!b) {
+        delete r;
+        return fail(NB_ERR_OOM, "pinned staging allocation failed");
+    }
+    r->pin = b;
+    std::memcpy(b, xq, 16 * n);
+    std::memcpy(b + 16 * n, type, 4 * n);
+    r->xq = (const float*)b;
+    r->type = (const int*)(b + 16 * n);
     if (excl_index) {
-        // validated and symmetrised here, on the caller's thread
-        st = excl_symmetrise(natoms, excl_index, excl_atoms, r->ei, r->ea);
-        if (st != NB_OK) {
-            delete r;
-            return st;
-        }
+        int* e = (int*)(b + 20 * n);
+        std::memcpy(e, ei.data(), 4 * ei.size());
+        if (!ea.empty()) std::memcpy(e + ei.size(), ea.data(), 4 * ea.size());
+        r->ei = e;
+        r->ea = e + ei.size();
         r->has_excl = true;
     }
-    r->est_bytes = est + 4 * (r->ei.size() + r->ea.size() + 1) + 4096;
+    r->est_bytes = est + 4 * (ei.size() + ea.size() + 1) + 4096;
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lock(s->mu);
         if (s->stop) {
+            s->pinned.put(r->pin, r->pin_class);
             delete r;
             return fail(NB_ERR_STATE, "server is shutting down");
         }

@@ -1,0 +1,133 @@
+"""Error of every result against the FP64 oracle, as a markdown table.
+
+Not a test: a report, run on a GPU machine after `__graft_entry__.build()`:
+
+    python tests/report_errors.py
+
+Per workload it evaluates through the C ABI and prints RMS(dF)/RMS(F), the
+relative errors of E_LJ and E_C, the largest virial component error relative to
+the virial's Frobenius norm, and whether the interacting-pair count equals the
+oracle's.  The 3M-atom box gets forces of 192 sampled atoms (the oracle's
+per-atom loop); the ensemble goes through the batched path.
+"""
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+sys.path.insert(0, HERE)
+
+import oracle  # noqa: E402
+from paper_1506_00716_gb300 import autotune, nb  # noqa: E402
+from paper_1506_00716_gb300 import waterbox as wb  # noqa: E402
+from _support import rel_rms  # noqa: E402
+
+FLAGS = nb.NB_F_ENERGY | nb.NB_F_VIRIAL
+
+
+def _eval(ctx, s, p):
+    h = nb.nb_sys_create(ctx, p, s.n, s.box)
+    try:
+        nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
+        nb.nb_grid_put(h, s.xq(), s.type)
+        nb.nb_pairlist_build(h)
+        f = np.zeros((s.n, 3), dtype=np.float32)
+        e = np.zeros(2)
+        v = np.zeros(9)
+        nb.nb_forces(h, None, f, e, v, FLAGS)
+        npairs = nb.nb_eval_info(h)["n_pairs"]
+    finally:
+        nb.nb_sys_destroy(h)
+    return f, e, v, npairs
+
+
+def _row(name, f_err, e, v, npairs, ref):
+    if ref is None:
+        return f"| {name} | {f_err:.2e} | — | — | — | — |"
+    vr = ref["virial"].reshape(-1)
+    ref_pairs = ref["npairs"]
+    count = "equal" if npairs == ref_pairs else f"{npairs} vs {ref_pairs}"
+    return (f"| {name} | {f_err:.2e} | {abs(e[0] - ref['e_lj']) / abs(ref['e_lj']):.2e} | "
+            f"{abs(e[1] - ref['e_coul']) / abs(ref['e_coul']):.2e} | "
+            f"{np.abs(v - vr).max() / np.linalg.norm(vr):.2e} | {count} |")
+
+
+def main():
+    import torch
+
+    from paper_1506_00716_gb300 import build as nbbuild
+
+    nbbuild.build()
+    torch.cuda.set_device(0)
+    gpu = torch.cuda.get_device_name(0)
+    ctx = nb.nb_ctx_create(0, None, 0)
+    rows = ["| workload | RMS(dF)/RMS(F) | E_LJ rel | E_C rel | virial / norm | pair count |",
+            "|---|---:|---:|---:|---:|---|"]
+    for name, s in (("small (1,944 atoms)", wb.small_box(seed=1)), ("mid (24,000 atoms)", wb.mid_box(seed=2))):
+        for cname, p in (("RF", wb.params_rf()), ("Ewald", wb.params_ewald())):
+            autotune.apply(ctx, "rf" if cname == "RF" else "ewald", s.n, gpu=gpu)
+            f, e, v, npairs = _eval(ctx, s, p)
+            ref = oracle.energy_virial(s, p)
+            rows.append(_row(f"{name}, {cname}", rel_rms(f, oracle.forces(s, p)), e, v, npairs, ref))
+            print(rows[-1], flush=True)
+    s = wb.large_box(seed=3)
+    p = wb.params_ewald()
+    autotune.apply(ctx, "ewald", s.n, gpu=gpu)
+    f, e, v, npairs = _eval(ctx, s, p)
+    sel = np.sort(np.random.default_rng(31).choice(s.n, size=192, replace=False)).astype(np.int32)
+    rows.append(_row("large (3,000,000 atoms), Ewald, 192 sampled atoms", rel_rms(f[sel], oracle.forces(s, p, sel)),
+                     e, v, npairs, None))
+    print(rows[-1], flush=True)
+    nb.nb_ctx_destroy(ctx)
+
+    # ensemble through the batched path: worst case over the systems
+    systems = wb.ensemble(64, 1000, 32000, seed=4)
+    p = wb.params_rf()
+    stream = torch.cuda.Stream()
+    ctx = nb.nb_ctx_create(0, stream, 0)
+    autotune.apply(ctx, "rf", sum(x.n for x in systems) // len(systems), gpu=gpu)
+    hs = []
+    for x in systems:
+        h = nb.nb_sys_create(ctx, p, x.n, x.box)
+        nb.nb_set_exclusions(h, x.excl_index, x.excl_atoms)
+        nb.nb_sys_set_coords(h, x.xq(), x.type)
+        hs.append(h)
+    b = nb.nb_batch_create(ctx, hs)
+    for attempt in range(3):
+        try:
+            nb.nb_batch_poll(b, nb.nb_batch_submit(b, FLAGS), 60_000_000)
+            break
+        except nb.NbError as exc:
+            if exc.status != 9:
+                raise
+    rng = np.random.default_rng(32)
+    order = np.argsort([x.n for x in systems])
+    worst = np.zeros(4)
+    for k in range(len(systems)):
+        x, h = systems[k], hs[k]
+        f = np.zeros((x.n, 3), dtype=np.float32)
+        e = np.zeros(2)
+        v = np.zeros(9)
+        nb.nb_sys_results(h, f, e, v)
+        sel = np.sort(rng.choice(x.n, size=48, replace=False)).astype(np.int32)
+        worst[0] = max(worst[0], rel_rms(f[sel], oracle.forces(x, p, sel)))
+        if k in set(order[:12].tolist()):
+            ref = oracle.energy_virial(x, p)
+            vr = ref["virial"].reshape(-1)
+            worst[1] = max(worst[1], abs(e[0] - ref["e_lj"]) / abs(ref["e_lj"]))
+            worst[2] = max(worst[2], abs(e[1] - ref["e_coul"]) / abs(ref["e_coul"]))
+            worst[3] = max(worst[3], np.abs(v - vr).max() / np.linalg.norm(vr))
+    rows.append(f"| ensemble (64 boxes, batched), RF: worst system; energies of the 12 smallest | "
+                f"{worst[0]:.2e} | {worst[1]:.2e} | {worst[2]:.2e} | {worst[3]:.2e} | — |")
+    print(rows[-1], flush=True)
+    nb.nb_batch_destroy(b)
+    for h in hs:
+        nb.nb_sys_destroy(h)
+    nb.nb_ctx_destroy(ctx)
+    print("\n".join(rows))
+
+
+if __name__ == "__main__":
+    main()

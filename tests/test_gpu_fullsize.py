@@ -76,14 +76,15 @@ def test_large_box_sampled_forces_and_invariants(torch_cuda):
 
         # permute the axes (cubic box): another grid, cluster assignment and
         # summation order, the same physics.  Forces and virial permute; the
-        # pair count (exact cut-off decisions) and the double-float energies
-        # are unchanged
+        # pair count (exact cut-off decisions) is identical; the energies
+        # agree to the float rounding of their per-item LJ partial sums
+        # (~1e-9 relative) and the float64 sums across items
         perm = [1, 2, 0]
         t = dataclasses.replace(s, x=np.ascontiguousarray(s.x[:, perm]))
         f2, e2, v2, npairs2 = _eval(ctx, t, p)
         assert npairs2 == npairs
         assert rel_rms(f2, f[:, perm]) <= 1e-6
-        assert np.abs(e2 - e).max() <= 1e-9 * np.abs(e).max()
+        assert (np.abs(e2 - e) <= 1e-8 * np.abs(e)).all()
         v3 = v.reshape(3, 3)[np.ix_(perm, perm)].reshape(-1)
         assert np.abs(v2 - v3).max() <= 1e-6 * np.linalg.norm(v)
     finally:
