@@ -352,7 +352,7 @@ nb_status plan_alloc_list(Plan* pl, long long items, long long entries) {
     plan_free_list(pl);
     items = std::min<long long>(items, (1ll << 31) - 1);
     entries = std::min<long long>(entries, (1ll << 31) - 1);
-    size_t bytes = align256(16 * (size_t)items) + align256(4 * (size_t)entries) +
+    size_t bytes = align256(16 * (size_t)items) + align256(4 * (size_t)items) + align256(4 * (size_t)entries) +
                    align256(8 * (size_t)entries) + align256(4 * CNT_N);
     void* blk = nullptr;
     nb_status s = dev_alloc(pl->ctx, &blk, bytes);
@@ -360,6 +360,8 @@ nb_status plan_alloc_list(Plan* pl, long long items, long long entries) {
     char* b = (char*)blk;
     pl->list.items = (int4*)b;
     b += align256(16 * (size_t)items);
+    pl->list.order = (int*)b;
+    b += align256(4 * (size_t)items);
     pl->list.cj = (int*)b;
     b += align256(4 * (size_t)entries);
     pl->list.mask = (unsigned long long*)b;
@@ -458,6 +460,7 @@ PlanLaunch launch_of(const Plan* pl) {
     PlanLaunch p{};
     const_cast<Plan*>(pl)->kp.max_entries = pl->ctx->tuning.max_entries;
     const_cast<Plan*>(pl)->kp.force_min_blocks = pl->ctx->tuning.force_min_blocks;
+    const_cast<Plan*>(pl)->kp.lpt_max_items = LPT_ITEMS_PER_WARP * LPT_WARPS_PER_SM * pl->ctx->num_sms;
     int n = (int)pl->systems.size();
     p.nsys = n;
     p.d_sys = pl->d_sys;
@@ -488,7 +491,7 @@ nb_status plan_build_list(Plan* pl) {
     cudaStream_t st = pl->ctx->stream;
     for (int attempt = 0; attempt < 4; ++attempt) {
         NB_CK(cudaMemsetAsync(pl->list.counters + CNT_ITEMS, 0, 4 * 2, st));
-        NB_CK(cudaMemsetAsync(pl->list.counters + CNT_PRUNED, 0, 4, st));
+        NB_CK(cudaMemsetAsync(pl->list.counters + CNT_PRUNED, 0, 4 * (CNT_N - CNT_PRUNED), st));
         PlanLaunch p = launch_of(pl);
         {
             StageScope sc(pl->ctx, NB_STAGE_SEARCH);
@@ -585,7 +588,7 @@ nb_status check_box(const nb_params* p, const double box[3]) {
 size_t plan_bytes_estimate(const nb_params* p, int natoms, const double box[3], const Geometry& g) {
     long long it, en;
     list_estimate(*p, natoms, box, g.clcap, 8, &it, &en);
-    return align256(16 * (size_t)it) + align256(12 * (size_t)en) + 4096;
+    return align256(20 * (size_t)it) + align256(12 * (size_t)en) + 4096;
 }
 
 }  // namespace nbgb

@@ -28,6 +28,8 @@ enum {
     CNT_WORK = 3,       // persistent-kernel work counter
     CNT_PRUNED = 4,     // entries kept by the prune
     CNT_EWORK = 5,      // energy-kernel work counter
+    CNT_ORD_LONG = 6,   // non-empty items the prune ordered first (long ones)
+    CNT_ORD_SHORT = 7,  // non-empty items the prune ordered last (short ones)
     CNT_N = 8
 };
 
@@ -83,9 +85,25 @@ struct ListDev {
     int* cj;             // j-cluster per entry
     unsigned long long* mask;  // 8x8 interaction bits per entry (rotated layout)
     int* counters;       // [CNT_N]
+    // evaluation order of the non-empty items, written by the prune: the
+    // long items (more than max_entries / 2 entries) from the front, the
+    // short ones from the back, so that the persistent kernels take the
+    // longest work first and end on short items
+    int* order;          // [item_cap]
     int item_cap;
     int entry_cap;
 };
+
+// The prune writes that order, and the persistent kernels follow it, when the
+// list has at most this many items per warp the force kernel can keep
+// resident (KParams::lpt_max_items); longer lists are taken in cluster order.
+constexpr int LPT_ITEMS_PER_WARP = 4;
+constexpr int LPT_WARPS_PER_SM = 24;
+
+// Item index of the k-th item in evaluation order (k < n_long + n_short).
+__device__ __forceinline__ int ordered_item(const ListDev& list, int k, int n_long) {
+    return k < n_long ? list.order[k] : list.order[list.item_cap - 1 - (k - n_long)];
+}
 
 // Interaction constants (identical for all systems of a plan).
 struct KParams {
@@ -102,6 +120,7 @@ struct KParams {
     int coul;
     int ntypes;
     int max_entries;     // list entries per work item (items are split beyond)
+    int lpt_max_items;   // item count up to which items run longest first
     int force_min_blocks;  // force-kernel launch-bounds variant: 1, 2 or 3
     const float2* lj;    // [ntypes^2] (6 c6, 12 c12), force kernel
     const float2* lje;   // [ntypes^2] (c6, c12), energy kernel

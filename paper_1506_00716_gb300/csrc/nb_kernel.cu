@@ -152,7 +152,13 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     ew.c2 = 2.0f * kp.beta * 0.5641895835477563f;
 
     float4* sjg = &s_j[w][g][0];
-    const int nitems = min(list.counters[CNT_ITEMS], list.item_cap);
+    // longest-first order for short lists, where the last items decide the
+    // launch's length; cluster order otherwise (neighbouring items share
+    // j-clusters in L1 and L2)
+    const int n_raw = min(list.counters[CNT_ITEMS], list.item_cap);
+    const bool ordered = n_raw <= kp.lpt_max_items;
+    const int n_long = ordered ? list.counters[CNT_ORD_LONG] : 0;
+    const int nitems = ordered ? n_long + list.counters[CNT_ORD_SHORT] : n_raw;
     int cur_sys = -1;
     const float4* xq_s = nullptr;
     const int* type_s = nullptr;
@@ -164,7 +170,7 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         if (lane == 0) it = atomicAdd(list.counters + CNT_WORK, 1);
         it = __shfl_sync(FULL, it, 0);
         if (it >= nitems) break;
-        const int4 item = list.items[it];
+        const int4 item = list.items[ordered ? ordered_item(list, it, n_long) : it];
         const int sid = item.w >> 5;
         const int sh = item.w & 31;
         if (sid != cur_sys) {

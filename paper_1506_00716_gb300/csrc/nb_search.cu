@@ -343,6 +343,7 @@ k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     const int jj = lane & 7;
     const int g = lane >> 3;
     const int nitems = min(list.counters[CNT_ITEMS], list.item_cap);
+    const bool ordered = nitems <= kp.lpt_max_items;
     for (int it = blockIdx.x * PRUNE_WARPS + w; it < nitems; it += gridDim.x * PRUNE_WARPS) {
         const int4 item = list.items[it];
         if (item.y >= item.z) continue;
@@ -411,8 +412,13 @@ k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             write += __popc(keep);
         }
         if (lane == 0) {
+            const int len = write - item.y;
             list.items[it].z = write;
-            atomicAdd(list.counters + CNT_PRUNED, write - item.y);
+            atomicAdd(list.counters + CNT_PRUNED, len);
+            if (ordered && len > kp.max_entries / 2)
+                list.order[atomicAdd(list.counters + CNT_ORD_LONG, 1)] = it;
+            else if (ordered && len > 0)
+                list.order[list.item_cap - 1 - atomicAdd(list.counters + CNT_ORD_SHORT, 1)] = it;
         }
     }
 }

@@ -130,9 +130,11 @@ extern "C" nb_status nb_eval_noalloc(const nb_params* params, int natoms, const 
     if (off >= NB_NOALLOC_SCRATCH_BYTES)
         return api_fail(NB_ERR_CAPACITY, "nb_eval_noalloc: system does not fit the scratch array");
     size_t rest = NB_NOALLOC_SCRATCH_BYTES - off;
-    long long items = std::min<long long>(est_items + est_entries / 8, (long long)(rest / 8 / 16));
+    long long items = std::min<long long>(est_items + est_entries / 8, (long long)(rest / 8 / 20));
     int4* d_items = (int4*)(base + off);
     off += up256(16 * (size_t)items);
+    int* d_order = (int*)(base + off);
+    off += up256(4 * (size_t)items);
     rest = NB_NOALLOC_SCRATCH_BYTES > off ? NB_NOALLOC_SCRATCH_BYTES - off : 0;
     long long entries = (long long)(rest / 12) - 64;
     if (entries < est_entries / 2)
@@ -163,12 +165,14 @@ extern "C" nb_status nb_eval_noalloc(const nb_params* params, int natoms, const 
     p.list.cj = d_cj;
     p.list.mask = d_mask;
     p.list.counters = d_counters;
+    p.list.order = d_order;
     p.list.item_cap = (int)items;
     p.list.entry_cap = (int)entries;
     p.kp = api_kparams(*params, box, d_lj);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaError_t e = cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    p.kp.lpt_max_items = LPT_ITEMS_PER_WARP * LPT_WARPS_PER_SM * p.num_sms;
 
 #define NA_CK(call)                                                  \
     do {                                                             \
