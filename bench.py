@@ -601,6 +601,19 @@ def run_serve(args, n_req: int = 256) -> dict:
         waves.append(st["wave_size"])
         pairs += st["n_pairs"]
     t_served = time.perf_counter() - t_start
+    # capacity: the same requests all queued at once (the Poisson stream above
+    # offers ~2000 req/s, which the server keeps up with, so its throughput
+    # there is the arrival rate)
+    def burst():
+        t0 = time.perf_counter()
+        tk = [nb.nb_server_submit(srv, r.n, r.box, inputs[k][0], inputs[k][1], r.excl_index, r.excl_atoms,
+                                  flags) for k, r in enumerate(reqs)]
+        t_sub = time.perf_counter() - t0
+        w = [nb.nb_server_wait(srv, t)["wave_size"] for t in tk]
+        return time.perf_counter() - t0, t_sub, w
+
+    burst()  # untimed: fills the server's pinned staging pool to steady state
+    t_sat, t_sat_submit, sat_waves = burst()
     nb.nb_server_destroy(srv)
     # serial plain calls, one request after another
     e = np.zeros(2)
@@ -623,9 +636,12 @@ def run_serve(args, n_req: int = 256) -> dict:
             "served_over_serial": t_serial / t_served, "p50_ms": float(np.percentile(lat_ms, 50)),
             "p99_ms": float(np.percentile(lat_ms, 99)), "mean_wave": float(np.mean(waves)),
             "served_pairs_per_s": pairs / t_served, "offered_req_per_s": n_req / float(arrivals[-1]),
+            "saturated_systems_per_s": n_req / t_sat, "saturated_over_serial": t_serial / t_sat,
+            "saturated_mean_wave": float(np.mean(sat_waves)), "saturated_submit_ms": 1e3 * t_sat_submit,
             "budget_gb": 120, "tuning": tuning,
             "timing": "host wall clock from the first arrival to the last result; latency per request "
-                      "from submission to results"}
+                      "from submission to results; saturated = all requests queued at once, first "
+                      "submission to last result"}
 
 
 def main():

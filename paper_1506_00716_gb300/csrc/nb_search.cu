@@ -335,7 +335,7 @@ constexpr int PRUNE_WARPS = 8;
 // i-atoms of the item, which every lane keeps in registers.  Kept entries are
 // compacted in place, in order, without the mark; a write never passes the
 // entries still to be read.
-__global__ void __launch_bounds__(PRUNE_WARPS * 32)
+__global__ void __launch_bounds__(PRUNE_WARPS * 32, 3)
 k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     __shared__ unsigned char s_rank[PRUNE_WARPS][32];
     const int lane = threadIdx.x & 31;
@@ -387,15 +387,25 @@ k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    bool near = false;
+                    // bit ii: i-atom ii lies within the list radius of this j-atom
+                    unsigned nb8 = 0;
 #pragma unroll
                     for (int ii = 0; ii < CL; ++ii) {
                         const float dx = xi[ii].x - xj[u].x, dy = xi[ii].y - xj[u].y, dz = xi[ii].z - xj[u].z;
                         const float r2 = dx * dx + dy * dy + dz * dz;
-                        const bool bit = (mq[u] >> rot_bit(ii, jj)) & 1ull;
-                        near = near || (bit && r2 < rl2);
+                        nb8 |= (r2 < rl2 ? 1u : 0u) << ii;
                     }
-                    const unsigned bal = __ballot_sync(FULL, near);
+                    // the mask column of j-slot jj (bit ii = pair (ii, jj)), only
+                    // when one of the four entries has a partial mask
+                    if (__any_sync(FULL, mq[u] != ~0ull)) {
+                        const unsigned lo = (unsigned)mq[u], hi = (unsigned)(mq[u] >> 32);
+                        unsigned col = 0;
+#pragma unroll
+                        for (int ii = 0; ii < CL; ++ii)
+                            col |= (((ii < 4 ? lo : hi) >> (8 * (ii & 3) + (ii ^ jj))) & 1u) << ii;
+                        nb8 &= col;
+                    }
+                    const unsigned bal = __ballot_sync(FULL, nb8 != 0u);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int k = q0 + 4 * u + q;
