@@ -39,6 +39,16 @@ nb_status cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
     } while (0)
 
+bool is_pinned_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 bool is_device_ptr(const void* p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -89,26 +99,37 @@ void list_estimate(const nb_params& p, int natoms, const double box[3], int clca
 namespace nbgb {
 
 nb_status excl_symmetrise(int n, const int* excl_index, const int* excl_atoms, std::vector<int>& idx,
-                          std::vector<int>& at) {
+                          std::vector<int>& at, const int** out_idx, const int** out_at) {
     if (!excl_index) return fail(NB_ERR_ARG, "excl_index is NULL");
     if (excl_index[0] != 0) return fail(NB_ERR_ARG, "excl_index[0] must be 0");
-    for (int a = 0; a < n; ++a)
-        if (excl_index[a + 1] < excl_index[a]) return fail(NB_ERR_ARG, "excl_index must be non-decreasing");
-    const int nnz = excl_index[n];
-    if (nnz > 0 && !excl_atoms) return fail(NB_ERR_ARG, "excl_atoms is NULL");
-    for (int k = 0; k < nnz; ++k)
-        if (excl_atoms[k] < 0 || excl_atoms[k] >= n) return fail(NB_ERR_ARG, "exclusion partner out of range");
-    // already symmetric, strictly ascending per atom and free of self pairs?
+    // one pass: validate, and see whether the list is already symmetric,
+    // strictly ascending per atom and free of self pairs (then it is used
+    // as it is)
     bool canon = true;
-    for (int a = 0; a < n && canon; ++a)
-        for (int k = excl_index[a]; k < excl_index[a + 1] && canon; ++k) {
+    for (int a = 0; a < n; ++a) {
+        const int k0 = excl_index[a], k1 = excl_index[a + 1];
+        if (k1 < k0) return fail(NB_ERR_ARG, "excl_index must be non-decreasing");
+        if (k1 > k0 && !excl_atoms) return fail(NB_ERR_ARG, "excl_atoms is NULL");
+        int prev = -1;
+        for (int k = k0; k < k1; ++k) {
             const int b = excl_atoms[k];
-            if (b == a || (k > excl_index[a] && excl_atoms[k - 1] >= b)) canon = false;
-            else canon = std::binary_search(excl_atoms + excl_index[b], excl_atoms + excl_index[b + 1], a);
+            if ((unsigned)b >= (unsigned)n) return fail(NB_ERR_ARG, "exclusion partner out of range");
+            if (!canon) continue;
+            if (b == a || b <= prev) {
+                canon = false;
+                continue;
+            }
+            prev = b;
+            // b must list a (rows are short: a linear scan; a malformed row
+            // of b is reported when b is visited)
+            bool found = false;
+            for (int q = excl_index[b]; q < excl_index[b + 1]; ++q) found = found || excl_atoms[q] == a;
+            canon = found;
         }
+    }
     if (canon) {
-        idx.assign(excl_index, excl_index + n + 1);
-        at.assign(excl_atoms, excl_atoms + nnz);
+        *out_idx = excl_index;
+        *out_at = excl_atoms;
         return NB_OK;
     }
     // symmetrise with flat arrays: degree count, prefix, fill, then sort and
@@ -141,6 +162,8 @@ nb_status excl_symmetrise(int n, const int* excl_index, const int* excl_atoms, s
         at.insert(at.end(), first, end_u);
         idx[a + 1] = (int)at.size();
     }
+    *out_idx = idx.data();
+    *out_at = at.data();
     return NB_OK;
 }
 
@@ -813,10 +836,19 @@ nb_status nb_sys_destroy(nb_sys* sys) {
 nb_status nb_set_exclusions(nb_sys* sys, const int* excl_index, const int* excl_atoms) {
     if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
     std::vector<int> idx, at;
-    nb_status s = excl_symmetrise(sys->natoms, excl_index, excl_atoms, idx, at);
+    const int *pi = nullptr, *pa = nullptr;
+    nb_status s = excl_symmetrise(sys->natoms, excl_index, excl_atoms, idx, at, &pi, &pa);
     if (s != NB_OK) return s;
-    // pageable vectors: each copy has consumed its source when it returns
-    return sys_upload_exclusions(sys, idx.data(), at.data());
+    // copies from pageable memory have consumed their source when they
+    // return; a pinned caller array would be read later, so it is copied
+    // to pageable memory first (the call copies its inputs)
+    if (pi == excl_index && (is_pinned_ptr(excl_index) || is_pinned_ptr(excl_atoms))) {
+        idx.assign(excl_index, excl_index + sys->natoms + 1);
+        at.assign(excl_atoms, excl_atoms + excl_index[sys->natoms]);
+        pi = idx.data();
+        pa = at.data();
+    }
+    return sys_upload_exclusions(sys, pi, pa);
 }
 
 static nb_status ensure_plan(nb_sys* sys) {

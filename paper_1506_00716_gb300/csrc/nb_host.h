@@ -95,6 +95,7 @@ namespace nbgb {
 nb_status fail(nb_status s, const std::string& msg);
 nb_status cuda_fail(cudaError_t e, const char* what);
 bool is_device_ptr(const void* p);
+bool is_pinned_ptr(const void* p);
 Geometry make_geometry(int natoms, const double box[3]);
 void list_estimate(const nb_params& p, int natoms, const double box[3], int clcap, int max_entries,
                    long long* items, long long* entries);
@@ -106,9 +107,10 @@ void plan_destroy(Plan* pl);
 PlanLaunch launch_of(const Plan* pl);
 nb_status stage_coords(nb_sys* s, const float* xq, const int* type);
 // Symmetric, sorted, duplicate-free exclusion CSR from the caller's CSR
-// (validated; a list that already has that form is copied as it is).
+// (validated).  *out_idx / *out_at point at the caller's arrays when they
+// already have that form, else at idx / at, which receive the symmetrised CSR.
 nb_status excl_symmetrise(int n, const int* excl_index, const int* excl_atoms, std::vector<int>& idx,
-                          std::vector<int>& at);
+                          std::vector<int>& at, const int** out_idx, const int** out_at);
 // Upload a CSR made by excl_symmetrise (idx: natoms + 1 entries, at: idx[natoms])
 // to the system's device buffers.  Pageable sources are consumed when the call
 // returns; pinned sources must stay valid until the stream has passed the copies.

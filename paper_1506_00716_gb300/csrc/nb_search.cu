@@ -83,6 +83,47 @@ __device__ __forceinline__ float gap(float alo, float ahi, float blo, float bhi)
     return fmaxf(0.f, fmaxf(blo - ahi, alo - bhi));
 }
 
+// Partition point of a column's clusters [lo, hi): with TOP, the first
+// cluster whose top z is >= z; otherwise the first whose bottom z is > z.
+// The clusters of a column are z-sorted, so both keys ascend.  The search
+// starts at a guess (the column's atoms spread evenly over the box height,
+// which puts it within a cluster or two) and walks at most WALK steps; if the
+// answer is farther, it bisects the remaining range.
+constexpr int WALK = 3;
+
+template <bool TOP>
+__device__ __forceinline__ int window_bound(const float4* __restrict__ bb, int lo, int hi, float z, int guess) {
+    auto before = [&](int m) {  // cluster m lies before the partition point
+        return TOP ? bb[2 * m + 1].z < z : bb[2 * m].z <= z;
+    };
+    int g = min(max(guess, lo), hi);
+    int steps = 0;
+    while (g > lo && !before(g - 1)) {
+        if (++steps > WALK) {
+            hi = g - 1;  // the answer is <= g - 1
+            g = -1;
+            break;
+        }
+        --g;
+    }
+    if (g >= 0) {
+        while (g < hi && before(g)) {
+            if (++steps > WALK) {
+                lo = g + 1;  // the answer is >= g + 1
+                g = -1;
+                break;
+            }
+            ++g;
+        }
+    }
+    if (g >= 0) return g;
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (before(m)) lo = m + 1; else hi = m;
+    }
+    return lo;
+}
+
 // Write the buffered entries as work items: one per run of equal shift
 // (runs are recorded while appending), split into pieces of at most
 // max_entries entries.
@@ -161,6 +202,7 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
     const unsigned long long rmask_i = row_mask(nri);
     const float rl = d.rl_search;
     const float rl2 = rl * rl;
+    const float izl = 1.f / d.L[2];
     const float rbb = fmaxf(0.f, rl - PRUNE_SURE_MARGIN);
     const float rbb2 = rbb * rbb;
     const float eps = 1e-5f * fmaxf(1.f, fmaxf(d.L[0], fmaxf(d.L[1], d.L[2])));
@@ -223,16 +265,12 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
                         if (gx * gx + gy * gy < rl2) {
                             const int col = cx * d.ncy + cy;
                             const int a0 = d.col_cl0[col], b0 = d.col_cl0[col + 1];
-                            int a = a0, b = b0;  // first cluster with top >= zmin
-                            while (a < b) {
-                                const int m = (a + b) >> 1;
-                                if (d.bb[2 * m + 1].z < zmin) a = m + 1; else b = m;
-                            }
-                            int u = a, v = b0;  // first cluster with bottom > zmax
-                            while (u < v) {
-                                const int m = (u + v) >> 1;
-                                if (d.bb[2 * m].z <= zmax) u = m + 1; else v = m;
-                            }
+                            const float cl_per_z = (float)(b0 - a0) * izl;
+                            // first cluster with top >= zmin, and first with
+                            // bottom > zmax (tops and bottoms ascend along the
+                            // column)
+                            const int a = window_bound<true>(d.bb, a0, b0, zmin, a0 + (int)(zmin * cl_per_z));
+                            const int u = window_bound<false>(d.bb, a, b0, zmax, a + (int)((zmax - zmin) * cl_per_z));
                             c0 = a;
                             cnt = u - a;
                         }

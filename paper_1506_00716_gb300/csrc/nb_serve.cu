@@ -434,17 +434,21 @@ nb_status nb_server_submit(nb_server* s, int natoms, const double box[3], const 
     nb_status st = nb_sys_footprint(&s->p, natoms, box, &est);
     if (st != NB_OK) return st;
     // exclusions validated and symmetrised here, on the caller's thread
-    std::vector<int> ei, ea;
+    std::vector<int> ei_v, ea_v;
+    const int *pei = nullptr, *pea = nullptr;
+    size_t n_ei = 0, n_ea = 0;
     if (excl_index) {
-        st = excl_symmetrise(natoms, excl_index, excl_atoms, ei, ea);
+        st = excl_symmetrise(natoms, excl_index, excl_atoms, ei_v, ea_v, &pei, &pea);
         if (st != NB_OK) return st;
+        n_ei = (size_t)natoms + 1;
+        n_ea = (size_t)pei[natoms];
     }
     Request* r = new Request();
     r->natoms = natoms;
     for (int d = 0; d < 3; ++d) r->box[d] = box[d];
     r->flags = flags;
     const size_t n = (size_t)natoms;
-    const size_t bytes = 16 * n + 4 * n + 4 * (ei.size() + ea.size());
+    const size_t bytes = 16 * n + 4 * n + 4 * (n_ei + n_ea);
     char* b = (char*)s->pinned.get(bytes, &r->pin_class);
     if (!b) {
         delete r;
@@ -457,13 +461,13 @@ nb_status nb_server_submit(nb_server* s, int natoms, const double box[3], const 
     r->type = (const int*)(b + 16 * n);
     if (excl_index) {
         int* e = (int*)(b + 20 * n);
-        std::memcpy(e, ei.data(), 4 * ei.size());
-        if (!ea.empty()) std::memcpy(e + ei.size(), ea.data(), 4 * ea.size());
+        std::memcpy(e, pei, 4 * n_ei);
+        if (n_ea) std::memcpy(e + n_ei, pea, 4 * n_ea);
         r->ei = e;
-        r->ea = e + ei.size();
+        r->ea = e + n_ei;
         r->has_excl = true;
     }
-    r->est_bytes = est + 4 * (ei.size() + ea.size() + 1) + 4096;
+    r->est_bytes = est + 4 * (n_ei + n_ea + 1) + 4096;
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lock(s->mu);
