@@ -604,10 +604,19 @@ def run_serve(args, n_req: int = 256) -> dict:
     # capacity: the same requests all queued at once (the Poisson stream above
     # offers ~2000 req/s, which the server keeps up with, so its throughput
     # there is the arrival rate)
+    from concurrent.futures import ThreadPoolExecutor
+
+    def submit_one(k):
+        r = reqs[k]
+        return nb.nb_server_submit(srv, r.n, r.box, inputs[k][0], inputs[k][1], r.excl_index, r.excl_atoms,
+                                   flags)
+
     def burst():
+        # eight client threads submit concurrently (each submission copies its
+        # inputs and checks its exclusions on the submitting thread)
         t0 = time.perf_counter()
-        tk = [nb.nb_server_submit(srv, r.n, r.box, inputs[k][0], inputs[k][1], r.excl_index, r.excl_atoms,
-                                  flags) for k, r in enumerate(reqs)]
+        with ThreadPoolExecutor(max_workers=8) as ex:
+            tk = list(ex.map(submit_one, range(n_req)))
         t_sub = time.perf_counter() - t0
         w = [nb.nb_server_wait(srv, t)["wave_size"] for t in tk]
         return time.perf_counter() - t0, t_sub, w
@@ -640,8 +649,8 @@ def run_serve(args, n_req: int = 256) -> dict:
             "saturated_mean_wave": float(np.mean(sat_waves)), "saturated_submit_ms": 1e3 * t_sat_submit,
             "budget_gb": 120, "tuning": tuning,
             "timing": "host wall clock from the first arrival to the last result; latency per request "
-                      "from submission to results; saturated = all requests queued at once, first "
-                      "submission to last result"}
+                      "from submission to results; saturated = all requests queued at once by 8 client "
+                      "threads, first submission to last result"}
 
 
 def main():
