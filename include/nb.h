@@ -154,11 +154,16 @@ nb_status nb_ctx_destroy(nb_ctx *ctx);
  * synchronises the stream and returns, per NB_STAGE_*, the summed elapsed
  * milliseconds and the number of timed launches since the last reset
  * (ms and launches: NB_NSTAGE entries, either may be NULL); reset != 0
- * clears the totals.
+ * clears the totals.  nb_ctx_set_timing(ctx, enable) times every stage
+ * (enable != 0) or none; nb_ctx_set_timing_stages times only the stages whose
+ * bit (1 << NB_STAGE_*) is set in stage_mask.  Each timed stage adds two
+ * event records to the stream, which separate the stage's kernels from
+ * their neighbours on the device: time only what is needed.
  */
 nb_status nb_ctx_set_tuning(nb_ctx *ctx, const nb_tuning *tuning);
 nb_status nb_ctx_get_tuning(nb_ctx *ctx, nb_tuning *tuning);
 nb_status nb_ctx_set_timing(nb_ctx *ctx, int enable);
+nb_status nb_ctx_set_timing_stages(nb_ctx *ctx, unsigned stage_mask);
 nb_status nb_ctx_timing(nb_ctx *ctx, double *ms, long long *launches, int reset);
 /* Device bytes currently held by the context's systems and batches. */
 nb_status nb_ctx_memory(nb_ctx *ctx, size_t *bytes_in_use, size_t *budget);

@@ -206,7 +206,7 @@ struct StageScope {
     int stage;
     cudaEvent_t a = nullptr;
     StageScope(nb_ctx* ctx, int st) : c(ctx), stage(st) {
-        if (c->timing && !c->capturing) {
+        if (((c->timing >> st) & 1u) && !c->capturing) {
             a = pool_event(c);
             if (a) cudaEventRecord(a, c->stream);
         }
@@ -721,7 +721,14 @@ nb_status nb_ctx_get_tuning(nb_ctx* ctx, nb_tuning* t) {
 
 nb_status nb_ctx_set_timing(nb_ctx* ctx, int enable) {
     if (!ctx) return fail(NB_ERR_ARG, "ctx is NULL");
-    ctx->timing = enable != 0;
+    ctx->timing = enable != 0 ? (1u << NB_NSTAGE) - 1u : 0u;
+    return NB_OK;
+}
+
+nb_status nb_ctx_set_timing_stages(nb_ctx* ctx, unsigned stage_mask) {
+    if (!ctx) return fail(NB_ERR_ARG, "ctx is NULL");
+    if (stage_mask >> NB_NSTAGE) return fail(NB_ERR_ARG, "stage_mask has bits beyond NB_NSTAGE");
+    ctx->timing = stage_mask;
     return NB_OK;
 }
 

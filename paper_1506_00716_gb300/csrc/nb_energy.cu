@@ -245,6 +245,8 @@ __device__ __forceinline__ void drain(int k, const int* __restrict__ qm, const I
 template <int COUL>
 __global__ void __launch_bounds__(EW * 32)
 k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ float2 s_lj[];
     __shared__ __align__(16) float4 s_j[EW][4][2 * CL];
     __shared__ int s_qm[EW][QCAP];
@@ -377,8 +379,7 @@ cudaError_t launch_energy_t(const PlanLaunch& p, cudaStream_t st) {
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, EW * 32, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) per_sm = 1;
-    kern<<<p.num_sms * per_sm, EW * 32, smem, st>>>(p.d_sys, p.list, p.kp);
-    return cudaGetLastError();
+    return launch_pdl(kern, (unsigned)(p.num_sms * per_sm), EW * 32, smem, st, p.d_sys, p.list, p.kp);
 }
 
 }  // namespace

@@ -47,6 +47,8 @@ __device__ __forceinline__ int pack_wrap(int kx, int ky, int kz) {
 
 __global__ void k_zero_cols(const SysDev* __restrict__ sys, const int* __restrict__ col_off,
                             int nsys, int tot_cols) {
+    pdl_wait();
+    pdl_trigger();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= tot_cols) return;
     int s = find_sys(col_off, nsys, t);
@@ -55,6 +57,8 @@ __global__ void k_zero_cols(const SysDev* __restrict__ sys, const int* __restric
 
 __global__ void k_bin(const SysDev* __restrict__ sys, const int* __restrict__ atom_off, int nsys,
                       int tot_atoms) {
+    pdl_wait();
+    pdl_trigger();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= tot_atoms) return;
     int s = find_sys(atom_off, nsys, t);
@@ -74,6 +78,8 @@ __global__ void k_bin(const SysDev* __restrict__ sys, const int* __restrict__ at
 
 // One block per system: exclusive prefix over clusters per column.
 __global__ void k_col_scan(const SysDev* __restrict__ sys) {
+    pdl_wait();
+    pdl_trigger();
     const SysDev& d = sys[blockIdx.x];
     __shared__ int s_part[1024];
     __shared__ int s_carry;
@@ -101,6 +107,8 @@ __global__ void k_col_scan(const SysDev* __restrict__ sys) {
 
 __global__ void k_scatter(const SysDev* __restrict__ sys, const int* __restrict__ atom_off, int nsys,
                           int tot_atoms) {
+    pdl_wait();
+    pdl_trigger();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= tot_atoms) return;
     int s = find_sys(atom_off, nsys, t);
@@ -152,6 +160,8 @@ __device__ void block_sort(K* a, int n) {
 // sorted arrays.  Columns longer than COL_MAX are sorted in global memory.
 __global__ void __launch_bounds__(256) k_col_sort(const SysDev* __restrict__ sys,
                                                   const int* __restrict__ col_off, int nsys) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ unsigned long long s_key[COL_MAX];
     int s = find_sys(col_off, nsys, blockIdx.x);
     const SysDev& d = sys[s];
@@ -196,6 +206,8 @@ __global__ void __launch_bounds__(256) k_col_sort(const SysDev* __restrict__ sys
 
 __global__ void k_bbox(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys,
                        int tot_clcap) {
+    pdl_wait();
+    pdl_trigger();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= tot_clcap) return;
     int s = find_sys(cl_off, nsys, t);
@@ -222,18 +234,19 @@ static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + 
 
 cudaError_t launch_grid_put(const PlanLaunch& p, cudaStream_t st) {
     const int bs = 256;
+    cudaError_t e = cudaSuccess;
     if (p.tot_cols > 0)
-        k_zero_cols<<<blocks_for(p.tot_cols, bs), bs, 0, st>>>(p.d_sys, p.d_col_off, p.nsys, p.tot_cols);
-    if (p.tot_atoms > 0)
-        k_bin<<<blocks_for(p.tot_atoms, bs), bs, 0, st>>>(p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms);
-    k_col_scan<<<p.nsys, 1024, 0, st>>>(p.d_sys);
-    if (p.tot_atoms > 0)
-        k_scatter<<<blocks_for(p.tot_atoms, bs), bs, 0, st>>>(p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms);
-    if (p.tot_cols > 0)
-        k_col_sort<<<p.tot_cols, 256, 0, st>>>(p.d_sys, p.d_col_off, p.nsys);
-    if (p.tot_clcap > 0)
-        k_bbox<<<blocks_for(p.tot_clcap, bs), bs, 0, st>>>(p.d_sys, p.d_cl_off, p.nsys, p.tot_clcap);
-    return cudaGetLastError();
+        e = launch_pdl(k_zero_cols, blocks_for(p.tot_cols, bs), bs, 0, st, p.d_sys, p.d_col_off, p.nsys, p.tot_cols);
+    if (e == cudaSuccess && p.tot_atoms > 0)
+        e = launch_pdl(k_bin, blocks_for(p.tot_atoms, bs), bs, 0, st, p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms);
+    if (e == cudaSuccess) e = launch_pdl(k_col_scan, (unsigned)p.nsys, 1024, 0, st, p.d_sys);
+    if (e == cudaSuccess && p.tot_atoms > 0)
+        e = launch_pdl(k_scatter, blocks_for(p.tot_atoms, bs), bs, 0, st, p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms);
+    if (e == cudaSuccess && p.tot_cols > 0)
+        e = launch_pdl(k_col_sort, (unsigned)p.tot_cols, 256, 0, st, p.d_sys, p.d_col_off, p.nsys);
+    if (e == cudaSuccess && p.tot_clcap > 0)
+        e = launch_pdl(k_bbox, blocks_for(p.tot_clcap, bs), bs, 0, st, p.d_sys, p.d_cl_off, p.nsys, p.tot_clcap);
+    return e;
 }
 
 }  // namespace nbgb

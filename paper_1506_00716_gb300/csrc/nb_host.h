@@ -31,7 +31,7 @@ struct nb_ctx {
     size_t budget = 0;
     size_t in_use = 0;
     int num_sms = 0;
-    bool timing = false;
+    unsigned timing = 0;  // mask of timed stages (1 << NB_STAGE_*)
     bool capturing = false;
     nb_tuning tuning{32, 3};
     unsigned tuning_gen = 0;

@@ -146,6 +146,33 @@ struct PlanLaunch {
     double* v_ext;           // [9] virial (k_finish)
 };
 
+// Programmatic dependent launch.  The path's kernels are launched with
+// programmatic stream serialization: a kernel may be scheduled onto the SMs
+// while the previous kernel of the stream finishes, which hides the launch
+// latency between the many short stages.  Every such kernel calls pdl_wait()
+// as its first statement, which returns once the previous grid has completed
+// and its memory operations are visible, so no kernel reads anything early;
+// pdl_trigger() lets the next kernel be scheduled once every block of this
+// one has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Shift index <-> vector.
 __host__ __device__ inline int shift_index(int sx, int sy, int sz) {
     return (sx + 1) * 9 + (sy + 1) * 3 + (sz + 1);

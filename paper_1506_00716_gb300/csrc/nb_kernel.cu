@@ -131,6 +131,8 @@ __device__ __forceinline__ void pair_block(const float4* __restrict__ sj, int i,
 template <int COUL, bool VIR, int MINB>
 __global__ void __launch_bounds__(FW * 32, MINB)
 k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
+    pdl_wait();
+    pdl_trigger();
     constexpr bool EXACT = COUL == NB_COUL_RF;
     extern __shared__ float2 s_lj[];
     __shared__ __align__(16) float4 s_j[FW][4][2 * CL];
@@ -316,6 +318,8 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
 template <bool COORD>
 __global__ void k_prepare(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys,
                           int tot_slots, int* __restrict__ counters, const float* __restrict__ x_ext) {
+    pdl_wait();
+    pdl_trigger();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {
         counters[CNT_WORK] = 0;
@@ -349,6 +353,8 @@ template <bool ENER_VIR>
 __global__ void k_finish(const SysDev* __restrict__ sys, const int* __restrict__ atom_off, int nsys,
                          int tot_atoms, float* __restrict__ f_ext, double* __restrict__ e_ext,
                          double* __restrict__ v_ext) {
+    pdl_wait();
+    pdl_trigger();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (ENER_VIR && t < nsys) {
         const SysDev& d = sys[t];
@@ -396,8 +402,7 @@ cudaError_t launch_forces_t(const PlanLaunch& p, cudaStream_t st) {
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FW * 32, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) per_sm = 1;
-    kern<<<p.num_sms * per_sm, FW * 32, smem, st>>>(p.d_sys, p.list, p.kp);
-    return cudaGetLastError();
+    return launch_pdl(kern, (unsigned)(p.num_sms * per_sm), FW * 32, smem, st, p.d_sys, p.list, p.kp);
 }
 
 }  // namespace
@@ -408,10 +413,9 @@ cudaError_t launch_prepare(const PlanLaunch& p, bool coords, cudaStream_t st) {
     unsigned blocks = (unsigned)((tot + bs - 1) / bs + 1);
     const float* x_ext = p.nsys == 1 ? p.x_ext : nullptr;
     if (coords)
-        k_prepare<true><<<blocks, bs, 0, st>>>(p.d_sys, p.d_cl_off, p.nsys, tot, p.list.counters, x_ext);
-    else
-        k_prepare<false><<<blocks, bs, 0, st>>>(p.d_sys, p.d_cl_off, p.nsys, tot, p.list.counters, nullptr);
-    return cudaGetLastError();
+        return launch_pdl(k_prepare<true>, blocks, bs, 0, st, p.d_sys, p.d_cl_off, p.nsys, tot, p.list.counters, x_ext);
+    return launch_pdl(k_prepare<false>, blocks, bs, 0, st, p.d_sys, p.d_cl_off, p.nsys, tot, p.list.counters,
+                      (const float*)nullptr);
 }
 
 template <int COUL, bool VIR>
@@ -439,11 +443,10 @@ cudaError_t launch_finalize(const PlanLaunch& p, unsigned flags, cudaStream_t st
     double* e_ext = one && (flags & NB_F_ENERGY) ? p.e_ext : nullptr;
     double* v_ext = one && (flags & NB_F_VIRIAL) ? p.v_ext : nullptr;
     if (flags & (NB_F_ENERGY | NB_F_VIRIAL))
-        k_finish<true><<<blocks, bs, 0, st>>>(p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms, f_ext, e_ext, v_ext);
-    else
-        k_finish<false><<<blocks, bs, 0, st>>>(p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms, f_ext, nullptr,
-                                               nullptr);
-    return cudaGetLastError();
+        return launch_pdl(k_finish<true>, blocks, bs, 0, st, p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms, f_ext, e_ext,
+                          v_ext);
+    return launch_pdl(k_finish<false>, blocks, bs, 0, st, p.d_sys, p.d_atom_off, p.nsys, p.tot_atoms, f_ext,
+                      (double*)nullptr, (double*)nullptr);
 }
 
 }  // namespace nbgb

@@ -179,6 +179,8 @@ __device__ void flush(SearchWarpSmem& sm, int nbuf, int nruns, int ci, int sid, 
 __global__ void __launch_bounds__(SEARCH_WARPS * 32)
 k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys, int tot_clcap,
          ListDev list, KParams kp) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ SearchWarpSmem s_w[SEARCH_WARPS];
     __shared__ unsigned long long s_colmask[CL + 1];
     __shared__ unsigned long long s_diag;
@@ -375,6 +377,8 @@ constexpr int PRUNE_WARPS = 8;
 // entries still to be read.
 __global__ void __launch_bounds__(PRUNE_WARPS * 32, 3)
 k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ unsigned char s_rank[PRUNE_WARPS][32];
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
@@ -476,14 +480,13 @@ k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
 cudaError_t launch_search(const PlanLaunch& p, cudaStream_t st) {
     if (p.tot_clcap <= 0) return cudaSuccess;
     unsigned blocks = (unsigned)((p.tot_clcap + SEARCH_WARPS - 1) / SEARCH_WARPS);
-    k_search<<<blocks, SEARCH_WARPS * 32, 0, st>>>(p.d_sys, p.d_cl_off, p.nsys, p.tot_clcap, p.list, p.kp);
-    return cudaGetLastError();
+    return launch_pdl(k_search, blocks, SEARCH_WARPS * 32, 0, st, p.d_sys, p.d_cl_off, p.nsys, p.tot_clcap, p.list,
+                      p.kp);
 }
 
 cudaError_t launch_prune(const PlanLaunch& p, cudaStream_t st) {
     unsigned blocks = (unsigned)(p.num_sms * 8);
-    k_prune<<<blocks, PRUNE_WARPS * 32, 0, st>>>(p.d_sys, p.list, p.kp);
-    return cudaGetLastError();
+    return launch_pdl(k_prune, blocks, PRUNE_WARPS * 32, 0, st, p.d_sys, p.list, p.kp);
 }
 
 }  // namespace nbgb

@@ -29,7 +29,7 @@ EXPORTS = ["nb_last_error", "nb_ctx_create", "nb_ctx_destroy", "nb_ctx_memory", 
            "nb_sys_create", "nb_sys_destroy", "nb_set_exclusions", "nb_grid_put", "nb_pairlist_build",
            "nb_pairlist_info", "nb_forces", "nb_pairlist_export", "nb_batch_create",
            "nb_batch_destroy", "nb_sys_set_coords", "nb_batch_submit", "nb_batch_poll",
-           "nb_sys_results", "nb_ctx_set_timing", "nb_ctx_timing", "nb_eval_info",
+           "nb_sys_results", "nb_ctx_set_timing", "nb_ctx_set_timing_stages", "nb_ctx_timing", "nb_eval_info",
            "nb_eval_noalloc", "nb_ctx_set_tuning", "nb_ctx_get_tuning", "nb_server_create",
            "nb_server_destroy", "nb_server_submit", "nb_server_wait"]
 NB_NSTAGE = 8
@@ -106,6 +106,7 @@ def load(path: str | None = None):
         "nb_batch_poll": ([_vp, ctypes.c_ulonglong, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)], _st),
         "nb_sys_results": ([_vp, _vp, _vp, _vp], _st),
         "nb_ctx_set_timing": ([_vp, ctypes.c_int], _st),
+        "nb_ctx_set_timing_stages": ([_vp, ctypes.c_uint], _st),
         "nb_ctx_set_tuning": ([_vp, ctypes.POINTER(nb_tuning)], _st),
         "nb_ctx_get_tuning": ([_vp, ctypes.POINTER(nb_tuning)], _st),
         "nb_server_create": ([_vp, ctypes.POINTER(nb_params), ctypes.c_size_t, ctypes.c_int,
@@ -275,6 +276,14 @@ def nb_sys_results(sys, f=None, energy=None, virial=None) -> None:
 
 def nb_ctx_set_timing(ctx, enable: bool) -> None:
     check(load().nb_ctx_set_timing(ctx, 1 if enable else 0))
+
+
+def nb_ctx_set_timing_stages(ctx, stages) -> None:
+    """Time only the named stages (names from STAGES)."""
+    mask = 0
+    for name in stages:
+        mask |= 1 << STAGES.index(name)
+    check(load().nb_ctx_set_timing_stages(ctx, mask))
 
 
 def nb_ctx_timing(ctx, reset: bool = False) -> dict:

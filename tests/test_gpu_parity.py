@@ -5,6 +5,8 @@ Tolerances: the pair list covers the oracle's interacting pairs exactly
 RMS(dF)/RMS(F) <= 1e-5; E_LJ, E_C within 1e-6 relative; every virial
 component within 1e-6 of the virial's Frobenius norm.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -178,6 +180,33 @@ def test_box_of_exactly_two_list_radii(ctx):
     p = wb.params_rf()
     f, e, v, _ = gpu_eval(ctx, s, p)
     _check(s, p, f, e, v)
+
+
+def test_one_sided_exclusions_are_symmetrised(ctx):
+    """Exclusions listed in one direction only, unsorted, with a self pair and
+    a duplicate, give the same result as the canonical symmetric list: the
+    library symmetrises what is not canonical and uses a canonical list as it
+    is."""
+    s = BOXES["small"]()
+    p = wb.params_rf()
+    n = s.n
+    rows = []
+    for a in range(n):
+        m0 = 3 * (a // 3)
+        partners = [b for b in range(m0, m0 + 3) if b > a][::-1]  # one direction, descending
+        if a % 3 == 0:
+            partners += [a, partners[0]]  # a self pair and a duplicate
+        rows.append(partners)
+    idx = np.zeros(n + 1, dtype=np.int32)
+    idx[1:] = np.cumsum([len(r) for r in rows])
+    atoms = np.array([b for r in rows for b in r], dtype=np.int32)
+    one_sided = dataclasses.replace(s, excl_index=idx, excl_atoms=atoms)
+    f0, e0, v0, _ = gpu_eval(ctx, s, p)
+    f1, e1, v1, _ = gpu_eval(ctx, one_sided, p)
+    assert rel_rms(f1, f0) < 1e-6
+    assert np.allclose(e1, e0, rtol=1e-12, atol=0)
+    assert np.abs(v1 - v0).max() <= 1e-7 * np.linalg.norm(v0)
+    _check(s, p, f1, e1, v1)
 
 
 def test_error_paths(ctx):
