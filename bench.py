@@ -378,6 +378,10 @@ def cpu_baseline(min_seconds: float = 10.0) -> dict:
 
 
 def run_reference(args) -> dict | None:
+    """The FP64 oracle, as it stands, on the host cores: each step computes the
+    forces of one of D disjoint atom subsets (round robin) of the 24,000-atom
+    box and is credited with 1/D of the box's interacting pairs, D chosen so
+    that the whole run stays within about two minutes."""
     world, rank, _ = _dist()
     if rank != 0:
         return None
@@ -386,23 +390,34 @@ def run_reference(args) -> dict | None:
     oracle.build()
     s = wb.mid_box(seed=2)
     p = wb.params_rf()
-    for _ in range(args.warmup):
-        _oracle_eval(oracle, s, p)
-    pairs, t0 = 0, time.perf_counter()
-    for _ in range(args.steps):
-        pairs += _oracle_eval(oracle, s, p)
+    n_pairs = oracle.energy_virial(s, p)["npairs"]  # untimed: the credit per full force pass
+    probe = np.arange(0, s.n, 64, dtype=np.int32)
+    t0 = time.perf_counter()
+    oracle.forces(s, p, probe)
+    t_full = 64.0 * (time.perf_counter() - t0)
+    n_sub = 1
+    while n_sub < 64 and (args.steps + args.warmup) * t_full / n_sub > 120.0:
+        n_sub *= 2
+    subsets = [np.arange(k, s.n, n_sub, dtype=np.int32) for k in range(n_sub)]
+    for k in range(args.warmup):
+        oracle.forces(s, p, subsets[k % n_sub])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.forces(s, p, subsets[k % n_sub])
     el = time.perf_counter() - t0
-    value = pairs / el
+    value = n_pairs * args.steps / n_sub / el
     cores = oracle.num_threads()
+    wl = {"workload": "water box, 24,000 atoms (8,000 rigid 3-site waters), L=6.21 nm, LJ + reaction-field "
+                      "(eps_rf=78), rc=1.0 nm, rlist=1.1 nm", "atoms": s.n, "coulomb": "reaction-field",
+          "parallelism": "host cores"}
+    sample = (f"each step: FP64 oracle forces of 1/{n_sub} of the atoms (round robin), credited with "
+              f"1/{n_sub} of the box's {n_pairs} interacting pairs")
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "impl": "reference",
-        "config": {"workload": "water box, 24,000 atoms, LJ + reaction-field, rc=1.0 nm; one step = "
-                               "one full FP64 oracle evaluation", "parallelism": "host cores"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} full evaluations of the 24,000-atom box"},
+        "impl": "reference", "config": wl,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
