@@ -240,12 +240,8 @@ def run_ours(args) -> dict:
     nb.nb_ctx_set_timing(ctx, False)
     stage = nb.nb_ctx_timing(ctx, reset=True)
     dev_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([dev_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = float(t.item())
-    total_pairs = pairs_per_step * args.steps * world
-    value = total_pairs / (dev_ms * 1e-3)
+    dev_ms = max_over_ranks(dev_ms, dev)
+    value = job_throughput(pairs_per_step, args.steps, world, dev_ms)
 
     # roofline of the force kernel (9 launches without and 1 with virial per
     # step), from its events inside the timed region
@@ -299,6 +295,27 @@ def _fp32_roofline(torch, dev, coul, n_plain, n_vir, slots, avg_ms, kernel, traf
             "avg_launch_ms": round(avg_ms, 5), "slots_per_launch": slots,
             "inst_per_slot": round(ips, 2), "flops_per_slot": round(fps, 2),
             "achieved_tflops": round(fps * slots / (avg_ms * 1e-3) / 1e12, 3)}
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest of every rank's x (x itself outside a process group).  The
+    tensor lives where the group's backend wants it: CUDA for NCCL, host
+    memory otherwise."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(pairs_per_step: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job pairs/s: every rank evaluates its own replica of the workload
+    (weak scaling), so the job does world x the pairs in the slowest rank's time."""
+    return pairs_per_step * steps * world / (max_ms * 1e-3)
 
 
 def _traffic_per_launch(key: str):
