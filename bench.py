@@ -260,7 +260,9 @@ def run_ours(args) -> dict:
     nb.nb_ctx_destroy(ctx)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
+        "ms_per_step_p10_p50_p90": [round(float(np.percentile(step_ms, q)), 5) for q in (10, 50, 90)],
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {**wl.config, "parallelism": f"replicas{world}",
                    "pairs_per_step": pairs_per_step, "list_entries": info["n_entries"],

@@ -30,6 +30,10 @@ _lib = None
 
 RF = 0
 EWALD = 1
+# potential modifiers (bits of Params.modifiers; nb_oracle.c documents them)
+MOD_LJ_SHIFT = 1
+MOD_EWALD_SHIFT = 2
+MOD_RF_EXCL = 4
 
 
 def build(force: bool = False) -> str:
@@ -56,7 +60,7 @@ def _load():
     ip = ctypes.POINTER(ctypes.c_int)
     lp = ctypes.POINTER(ctypes.c_longlong)
     common = [ctypes.c_int, dp, dp, ip, dp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
-              ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, ip, ip]
+              ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, ip, ip, ctypes.c_int]
     lib.or_energy_virial.argtypes = common + [dp, lp]
     lib.or_energy_virial.restype = ctypes.c_int
     lib.or_forces.argtypes = common + [ctypes.c_int, ip, dp]
@@ -93,7 +97,7 @@ def _common(sys, params):
     keep = (x, q, t, b, c6, c12, ei, ea)
     args = [sys.n, xp, qp, tp, bp, float(params.rc), int(params.coul), float(params.eps_r),
             float(params.eps_rf), float(params.beta), float(params.fcoul), int(params.ntypes),
-            c6p, c12p, eip, eap]
+            c6p, c12p, eip, eap, int(getattr(params, "modifiers", 0))]
     return keep, args
 
 

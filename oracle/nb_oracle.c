@@ -28,6 +28,19 @@
  *     force on i = (F/r) d, force on j = -(F/r) d
  *     virial Xi -= 1/2 (F/r) d (x) d
  *
+ * Optional potential modifiers (bits of `mods`; all off by default):
+ *   OR_MOD_LJ_SHIFT     every interacting pair's Lennard-Jones energy is taken
+ *                       relative to its value at the cut-off:
+ *                       V = c12 (1/r^12 - 1/rc^12) - c6 (1/r^6 - 1/rc^6);
+ *                       forces unchanged
+ *   OR_MOD_EWALD_SHIFT  likewise for the Ewald real-space term:
+ *                       V = f qi qj / eps_r (erfc(beta r)/r - erfc(beta rc)/rc)
+ *   OR_MOD_RF_EXCL      reaction-field correction of excluded pairs: every
+ *                       excluded pair (i, j) with r^2 < rc^2 contributes
+ *                       V = f qi qj / eps_r (k_rf r^2 - c_rf) and the force
+ *                       of that potential, F/r = -2 f qi qj / eps_r k_rf
+ *                       (no self term)
+ *
  * Everything is double precision.  Inputs are the same float32 values the
  * CUDA path receives, promoted exactly by the caller.  Exclusions are a CSR
  * list over atoms; a pair is excluded if either atom lists the other.
@@ -46,6 +59,9 @@
 
 #define OR_RF 0
 #define OR_EWALD 1
+#define OR_MOD_LJ_SHIFT 1
+#define OR_MOD_EWALD_SHIFT 2
+#define OR_MOD_RF_EXCL 4
 
 static double min_image(double d, double L) { return d - L * round(d / L); }
 
@@ -59,15 +75,17 @@ static int excluded(int i, int j, const int *ei, const int *ea) {
 }
 
 typedef struct {
-    double rc2, krf, crf, beta, fpre;
-    int coul, ntypes;
+    double rc, rc2, krf, crf, beta, fpre;
+    int coul, ntypes, mods;
     const double *c6, *c12;
 } setup_t;
 
 static setup_t make_setup(double rc, int coul, double eps_r, double eps_rf, double beta,
-                          double fcoul, int ntypes, const double *c6, const double *c12) {
+                          double fcoul, int ntypes, const double *c6, const double *c12, int mods) {
     setup_t s;
+    s.rc = rc;
     s.rc2 = rc * rc;
+    s.mods = mods;
     if (eps_rf == 0.0)
         s.krf = 1.0 / (2.0 * rc * rc * rc);
     else
@@ -96,6 +114,10 @@ static double pair_terms(const setup_t *s, double r2, double qq, int ti, int tj,
     *e12 = t12;
     *e6 = t6;
     *v_lj = t12 - t6;
+    if (s->mods & OR_MOD_LJ_SHIFT) {
+        double irc6 = 1.0 / (s->rc2 * s->rc2 * s->rc2);
+        *v_lj -= c12 * irc6 * irc6 - c6 * irc6;
+    }
     double flj = (12.0 * t12 - 6.0 * t6) * ir2;
     double fc, vc;
     double fq = s->fpre * qq;
@@ -106,12 +128,21 @@ static double pair_terms(const setup_t *s, double r2, double qq, int ti, int tj,
         double br = s->beta * r;
         double ec = erfc(br);
         vc = fq * ec / r;
+        if (s->mods & OR_MOD_EWALD_SHIFT) vc -= fq * erfc(s->beta * s->rc) / s->rc;
         fc = fq * (ec / r + 2.0 * s->beta / sqrt(M_PI) * exp(-br * br)) * ir2;
     }
     *v_c = vc;
     *fr_lj = flj;
     *fr_c = fc;
     return flj + fc;
+}
+
+/* Reaction-field correction of one excluded pair inside the cut-off:
+ * returns F/r and writes the energy. */
+static double excl_rf_terms(const setup_t *s, double r2, double qq, double *v_c) {
+    double fq = s->fpre * qq;
+    *v_c = fq * (s->krf * r2 - s->crf);
+    return -2.0 * fq * s->krf;
 }
 
 /*
@@ -124,9 +155,9 @@ static double pair_terms(const setup_t *s, double r2, double qq, int ti, int tj,
 int or_energy_virial(int n, const double *x, const double *q, const int *type, const double *box,
                      double rc, int coul, double eps_r, double eps_rf, double beta, double fcoul,
                      int ntypes, const double *c6, const double *c12, const int *excl_index,
-                     const int *excl_atoms, double *out, long long *npairs) {
+                     const int *excl_atoms, int mods, double *out, long long *npairs) {
     if (n < 0 || !out) return 1;
-    setup_t s = make_setup(rc, coul, eps_r, eps_rf, beta, fcoul, ntypes, c6, c12);
+    setup_t s = make_setup(rc, coul, eps_r, eps_rf, beta, fcoul, ntypes, c6, c12, mods);
     double elj = 0, ec = 0, e12 = 0, e6 = 0, rf_lj = 0, rf_c = 0;
     double vxx = 0, vxy = 0, vxz = 0, vyy = 0, vyz = 0, vzz = 0;
     long long np = 0;
@@ -138,22 +169,30 @@ int or_energy_virial(int n, const double *x, const double *q, const int *type, c
             double dz = min_image(x[3 * i + 2] - x[3 * j + 2], box[2]);
             double r2 = dx * dx + dy * dy + dz * dz;
             if (!(r2 < s.rc2)) continue;
-            if (excluded(i, j, excl_index, excl_atoms)) continue;
-            double vl, vc, a12, a6, fl, fc;
-            double fr = pair_terms(&s, r2, q[i] * q[j], type[i], type[j], &vl, &vc, &a12, &a6, &fl, &fc);
-            elj += vl;
-            ec += vc;
-            e12 += a12;
-            e6 += a6;
-            rf_lj += fl * r2;
-            rf_c += fc * r2;
+            double fr;
+            if (excluded(i, j, excl_index, excl_atoms)) {
+                if (!(s.mods & OR_MOD_RF_EXCL) || s.coul != OR_RF) continue;
+                double vc;
+                fr = excl_rf_terms(&s, r2, q[i] * q[j], &vc);
+                ec += vc;
+                rf_c += fr * r2;
+            } else {
+                double vl, vc, a12, a6, fl, fc;
+                fr = pair_terms(&s, r2, q[i] * q[j], type[i], type[j], &vl, &vc, &a12, &a6, &fl, &fc);
+                elj += vl;
+                ec += vc;
+                e12 += a12;
+                e6 += a6;
+                rf_lj += fl * r2;
+                rf_c += fc * r2;
+                np += 1;
+            }
             vxx -= 0.5 * fr * dx * dx;
             vxy -= 0.5 * fr * dx * dy;
             vxz -= 0.5 * fr * dx * dz;
             vyy -= 0.5 * fr * dy * dy;
             vyz -= 0.5 * fr * dy * dz;
             vzz -= 0.5 * fr * dz * dz;
-            np += 1;
         }
     }
     out[0] = elj;
@@ -177,10 +216,10 @@ int or_energy_virial(int n, const double *x, const double *q, const int *type, c
 int or_forces(int n, const double *x, const double *q, const int *type, const double *box,
               double rc, int coul, double eps_r, double eps_rf, double beta, double fcoul,
               int ntypes, const double *c6, const double *c12, const int *excl_index,
-              const int *excl_atoms, int nsel, const int *sel, double *f) {
+              const int *excl_atoms, int mods, int nsel, const int *sel, double *f) {
     if (n < 0 || nsel < 0 || !f) return 1;
     if (!sel && nsel != n) return 1;
-    setup_t s = make_setup(rc, coul, eps_r, eps_rf, beta, fcoul, ntypes, c6, c12);
+    setup_t s = make_setup(rc, coul, eps_r, eps_rf, beta, fcoul, ntypes, c6, c12, mods);
 #pragma omp parallel for schedule(dynamic, 4)
     for (int k = 0; k < nsel; ++k) {
         int i = sel ? sel[k] : k;
@@ -192,9 +231,15 @@ int or_forces(int n, const double *x, const double *q, const int *type, const do
             double dz = min_image(x[3 * i + 2] - x[3 * j + 2], box[2]);
             double r2 = dx * dx + dy * dy + dz * dz;
             if (!(r2 < s.rc2)) continue;
-            if (excluded(i, j, excl_index, excl_atoms)) continue;
-            double vl, vc, a12, a6, fl, fc;
-            double fr = pair_terms(&s, r2, q[i] * q[j], type[i], type[j], &vl, &vc, &a12, &a6, &fl, &fc);
+            double fr;
+            if (excluded(i, j, excl_index, excl_atoms)) {
+                if (!(s.mods & OR_MOD_RF_EXCL) || s.coul != OR_RF) continue;
+                double vc;
+                fr = excl_rf_terms(&s, r2, q[i] * q[j], &vc);
+            } else {
+                double vl, vc, a12, a6, fl, fc;
+                fr = pair_terms(&s, r2, q[i] * q[j], type[i], type[j], &vl, &vc, &a12, &a6, &fl, &fc);
+            }
             fx += fr * dx;
             fy += fr * dy;
             fz += fr * dz;

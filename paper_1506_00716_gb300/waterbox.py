@@ -59,6 +59,7 @@ class Params:
     ntypes: int = 2
     c6: np.ndarray = dataclasses.field(default_factory=lambda: lj_table()[0])
     c12: np.ndarray = dataclasses.field(default_factory=lambda: lj_table()[1])
+    modifiers: int = 0  # potential-modifier bits (library: NB_MOD_*, oracle: MOD_*)
 
 
 @dataclasses.dataclass

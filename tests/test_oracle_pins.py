@@ -138,6 +138,95 @@ def test_excluded_pairs_contribute_nothing():
         assert np.all(oracle.forces(box, p) == 0.0)
 
 
+# --------------------------------------------------- potential modifiers
+
+def test_lj_potential_shift():
+    p0 = _lj_params()
+    p1 = _lj_params(modifiers=oracle.MOD_LJ_SHIFT)
+    c6, c12, rc = p0.c6[0], p0.c12[0], p0.rc
+    v_rc = c12 / rc**12 - c6 / rc**6  # the unshifted pair energy at the cut-off
+    for r in (0.3, 0.5, 0.9):
+        s = _two(r)
+        e0, e1 = oracle.energy_virial(s, p0), oracle.energy_virial(s, p1)
+        assert e1["e_lj"] == pytest.approx(e0["e_lj"] - v_rc, rel=1e-12, abs=1e-15)
+        assert np.array_equal(oracle.forces(s, p0), oracle.forces(s, p1))
+        assert np.array_equal(e0["virial"], e1["virial"])
+    # the shifted potential is continuous at the cut-off
+    assert abs(oracle.energy_virial(_two(rc - 1e-7), p1)["e_lj"]) < 1e-8
+    assert oracle.energy_virial(_two(rc + 1e-7), p1)["e_lj"] == 0.0
+
+
+def test_ewald_potential_shift():
+    zero = np.zeros(4)
+    p0 = wb.Params(coul=wb.COUL_EWALD, c6=zero, c12=zero)
+    p1 = wb.Params(coul=wb.COUL_EWALD, c6=zero, c12=zero, modifiers=oracle.MOD_EWALD_SHIFT)
+    q1, q2 = 0.6, -0.9
+    shift = p0.fcoul * q1 * q2 * math.erfc(p0.beta * p0.rc) / p0.rc
+    for r in (0.2, 0.6, 0.95):
+        s = _two(r, q1, q2)
+        e0, e1 = oracle.energy_virial(s, p0), oracle.energy_virial(s, p1)
+        assert e1["e_coul"] == pytest.approx(e0["e_coul"] - shift, rel=1e-12, abs=1e-15)
+        assert np.array_equal(oracle.forces(s, p0), oracle.forces(s, p1))
+    assert abs(oracle.energy_virial(_two(p0.rc - 1e-7, q1, q2), p1)["e_coul"]) < 1e-7
+    # the modifier leaves reaction field alone
+    prf = wb.Params(c6=zero, c12=zero, modifiers=oracle.MOD_EWALD_SHIFT)
+    s = _two(0.4, q1, q2)
+    assert oracle.energy_virial(s, prf)["e_coul"] == oracle.energy_virial(s, wb.Params(c6=zero, c12=zero))["e_coul"]
+
+
+def test_rf_exclusion_correction():
+    zero = np.zeros(4)
+    p = wb.Params(c6=zero, c12=zero, modifiers=oracle.MOD_RF_EXCL)
+    q1, q2 = 0.6, -0.9
+    rc, er, erf = p.rc, p.eps_r, p.eps_rf
+    krf = (erf - er) / ((2 * erf + er) * rc**3)
+    crf = 1 / rc + krf * rc**2
+    excl = (np.array([0, 1, 2], dtype=np.int32), np.array([1, 0], dtype=np.int32))
+    for r, inside in ((0.1, True), (0.97, True), (1.2, False)):
+        s = _system([[1.0, 1.0, 1.0], [1.0 + r, 1.0, 1.0]], [q1, q2], [0, 0], 5.0, excl)
+        ev = oracle.energy_virial(s, p)
+        f = oracle.forces(s, p)
+        if inside:
+            assert ev["e_coul"] == pytest.approx(p.fcoul * q1 * q2 * (krf * r * r - crf), rel=1e-13)
+            # F_i = -dV/dx_i with V = f q1 q2 (k_rf r^2 - c_rf): -2 f q1 q2 k_rf (x_i - x_j)
+            assert f[0, 0] == pytest.approx(2 * p.fcoul * q1 * q2 * krf * r, rel=1e-13)
+            assert f[1, 0] == pytest.approx(-f[0, 0], rel=1e-15)
+            # virial -1/2 d (x) F: xx = -1/2 (-r) (2 f qq k_rf r)
+            assert ev["virial"][0, 0] == pytest.approx(p.fcoul * q1 * q2 * krf * r * r, rel=1e-13)
+        else:
+            assert ev["e_coul"] == 0.0 and np.all(f == 0.0)
+        assert ev["npairs"] == 0  # excluded pairs are not interacting pairs
+        # without the modifier the excluded pair contributes nothing
+        s0 = oracle.energy_virial(s, wb.Params(c6=zero, c12=zero))
+        assert s0["e_coul"] == 0.0
+
+
+@pytest.mark.parametrize("mods,coul", [(1 | 4, wb.COUL_RF), (1 | 2, wb.COUL_EWALD)])
+def test_modified_forces_are_minus_energy_gradient(mods, coul):
+    sys = wb.small_box(seed=15)
+    sys.x = sys.x.astype(np.float64)
+    p = wb.Params(coul=coul, modifiers=mods)
+    f = oracle.forces(sys, p)
+    assert np.abs(f.sum(0)).max() <= 1e-9 * np.abs(f).sum()
+    rng = np.random.default_rng(1)
+    h = 1e-6
+    checked = 0
+    for a in rng.choice(sys.n, size=6, replace=False):
+        for d in range(3):
+            xp, xm = sys.x.copy(), sys.x.copy()
+            xp[a, d] += h
+            xm[a, d] -= h
+            sp = wb.System(**{**sys.__dict__}); sp.x = xp
+            sm = wb.System(**{**sys.__dict__}); sm.x = xm
+            ep, npp = _etot(sp, p)
+            em, nm = _etot(sm, p)
+            if npp != nm:
+                continue
+            assert -(ep - em) / (2 * h) == pytest.approx(f[a, d], rel=2e-6, abs=2e-4)
+            checked += 1
+    assert checked >= 12
+
+
 # ------------------------------------------------------ laws and symmetries
 
 @pytest.mark.parametrize("coul", [wb.COUL_RF, wb.COUL_EWALD])
