@@ -81,15 +81,32 @@ enum {
  *   ntypes      number of Lennard-Jones types, 1..64
  *   c6, c12     host arrays of ntypes*ntypes floats, row-major [ti*ntypes+tj],
  *               V_LJ = c12/r^12 - c6/r^6; copied during nb_sys_create
- * Excluded pairs contribute nothing; neither the reaction-field nor the
- * Ewald exclusion correction is applied.
+ *   modifiers   bits of NB_MOD_* (0: none).  Without modifiers, excluded
+ *               pairs contribute nothing and the potentials are cut plainly
+ *               at rc (the reaction-field one is zero there by its c_rf).
+ *               The paper states no cut-off treatment; these are the
+ *               common alternatives:
+ *     NB_MOD_LJ_SHIFT     every interacting pair's Lennard-Jones energy is
+ *                         taken relative to its value at rc (forces unchanged)
+ *     NB_MOD_EWALD_SHIFT  likewise for the Ewald real-space energy,
+ *                         f qi qj / eps_r (erfc(beta r)/r - erfc(beta rc)/rc);
+ *                         NB_COUL_EWALD only
+ *     NB_MOD_RF_EXCL      every excluded pair with r^2 < rc^2 contributes
+ *                         f qi qj / eps_r (k_rf r^2 - c_rf) to E_Coulomb, with
+ *                         its force and virial (no self term); NB_COUL_RF only.
+ *                         Evaluated in float64 over the exclusion list.
+ *               Other bits, or a modifier with the other electrostatics,
+ *               fail with NB_ERR_ARG.
  */
+enum { NB_MOD_LJ_SHIFT = 1u, NB_MOD_EWALD_SHIFT = 2u, NB_MOD_RF_EXCL = 4u };
+
 typedef struct {
     double rc, rlist;
     int coul;
     double eps_r, eps_rf, ewald_beta, fcoul;
     int ntypes;
     const float *c6, *c12;
+    unsigned modifiers;
 } nb_params;
 
 /* Counts of the current pair list (nb_pairlist_info). */

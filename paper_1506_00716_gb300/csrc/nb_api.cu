@@ -342,6 +342,18 @@ KParams make_kparams(const nb_sys* s) {
     k.mb2l2e_l = (float)(mb - (double)k.mb2l2e_h);
     k.beta_h = (float)p.ewald_beta;
     k.beta_l = (float)(p.ewald_beta - (double)k.beta_h);
+    k.mods = p.modifiers;
+    const double irc6 = 1.0 / (p.rc * p.rc * p.rc * p.rc * p.rc * p.rc);
+    k.irc6_h = (float)irc6;
+    k.irc6_l = (float)(irc6 - (double)k.irc6_h);
+    k.irc12_h = (float)(irc6 * irc6);
+    k.irc12_l = (float)(irc6 * irc6 - (double)k.irc12_h);
+    const double ewc = p.coul == NB_COUL_EWALD ? std::erfc(p.ewald_beta * p.rc) / p.rc : 0.0;
+    k.ewc_h = (float)ewc;
+    k.ewc_l = (float)(ewc - (double)k.ewc_h);
+    k.fq_d = fq;
+    k.krf_d = krf;
+    k.crf_d = crf;
     k.max_entries = 32;
     k.force_min_blocks = 3;
     k.coul = p.coul;
@@ -355,7 +367,7 @@ bool same_params(const nb_sys* a, const nb_sys* b) {
     const nb_params &p = a->p, &q = b->p;
     return p.rc == q.rc && p.rlist == q.rlist && p.coul == q.coul && p.eps_r == q.eps_r &&
            p.eps_rf == q.eps_rf && p.ewald_beta == q.ewald_beta && p.fcoul == q.fcoul &&
-           p.ntypes == q.ntypes && a->c6 == b->c6 && a->c12 == b->c12;
+           p.ntypes == q.ntypes && p.modifiers == q.modifiers && a->c6 == b->c6 && a->c12 == b->c12;
 }
 
 void plan_free_list(Plan* pl) {
@@ -563,6 +575,7 @@ nb_status plan_eval(Plan* pl, unsigned flags, bool coords, const PlanLaunch* ext
     }
     {
         StageScope sc(pl->ctx, NB_STAGE_FINAL);
+        NB_CK(launch_excl_corr(p, flags, st));
         NB_CK(launch_finalize(p, flags, st));
     }
     return NB_OK;
@@ -595,6 +608,12 @@ nb_status check_params(const nb_params* p) {
     if (p->coul == NB_COUL_EWALD && !(p->ewald_beta > 0)) return fail(NB_ERR_ARG, "ewald_beta must be > 0");
     if (p->ntypes < 1 || p->ntypes > MAX_TYPES) return fail(NB_ERR_ARG, "ntypes must be in 1..64");
     if (!p->c6 || !p->c12) return fail(NB_ERR_ARG, "c6 / c12 are NULL");
+    if (p->modifiers & ~(unsigned)(NB_MOD_LJ_SHIFT | NB_MOD_EWALD_SHIFT | NB_MOD_RF_EXCL))
+        return fail(NB_ERR_ARG, "unknown modifier bits");
+    if ((p->modifiers & NB_MOD_EWALD_SHIFT) && p->coul != NB_COUL_EWALD)
+        return fail(NB_ERR_ARG, "NB_MOD_EWALD_SHIFT needs NB_COUL_EWALD");
+    if ((p->modifiers & NB_MOD_RF_EXCL) && p->coul != NB_COUL_RF)
+        return fail(NB_ERR_ARG, "NB_MOD_RF_EXCL needs NB_COUL_RF");
     return NB_OK;
 }
 
@@ -1029,6 +1048,7 @@ static nb_status batch_record(Plan* pl, unsigned flags) {
     }
     {
         StageScope sc(pl->ctx, NB_STAGE_FINAL);
+        NB_CK(launch_excl_corr(p, flags, st));
         NB_CK(launch_finalize(p, flags, st));
     }
     NB_CK(cudaMemcpyAsync(pl->h_counters, pl->list.counters, 4 * CNT_N, cudaMemcpyDeviceToHost, st));

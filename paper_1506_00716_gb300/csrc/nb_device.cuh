@@ -46,6 +46,15 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
     s = a + b;
     e = b - (s - a);
 }
+// (ph + pl) = (ah + al) (bh + bl) to about 2^-46 relative (double-float
+// product; the al bl term is below that and dropped).
+__device__ __forceinline__ void dd_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, fmaf(al, bh, e));
+    ph = p + e;
+    pl = e - (ph - p);
+}
 // p + e = a * b exactly (fused multiply-add residual).
 __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
     p = a * b;

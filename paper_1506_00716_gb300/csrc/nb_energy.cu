@@ -18,6 +18,9 @@
 //          (compensated Horner), their small tails in float32;
 //   LJ:    c12 r^-12, c6 r^-6 in float32 from the accurate 1/r and the
 //          unscaled c6, c12 (pre-scaled 6 c6, 12 c12 would round).
+// With the potential-shift modifiers the LJ terms become c12 (r^-12 -
+// rc^-12) and c6 (r^-6 - rc^-6), and erfc(beta r)/r becomes erfc(beta r)/r -
+// erfc(beta rc)/rc (the constant as hi + lo).
 // Coulomb energies accumulate in double-float per lane and work item, and in
 // float64 across items and warps.  Cut-off decisions are exact (the float64
 // distance of the float32 inputs decides pairs near rc), so the counted pair
@@ -113,7 +116,8 @@ template <int COUL>
 __device__ __forceinline__ void pair_energy(const float4 xj, int tj, const ShiftedI& xs, float qih,
                                             float qil, int tirow, const float2* __restrict__ s_lj,
                                             bool valid, bool maybe, const KParams& kp, float& ch,
-                                            float& cl, float& e12, float& e6, int& npair) {
+                                            float& cl, float& e12, float& e12l, float& e6, float& e6l,
+                                            int& npair) {
     float dxh, dxe, dyh, dye, dzh, dze;
     two_sum(xs.xh, -xj.x, dxh, dxe);
     two_sum(xs.yh, -xj.y, dyh, dye);
@@ -146,12 +150,43 @@ __device__ __forceinline__ void pair_energy(const float4 xj, int tj, const Shift
     const float rif = y + ril;
 
     const float2 c = s_lj[tirow + tj];
-    const float ri2 = rif * rif;
-    const float ri6 = ri2 * ri2 * ri2;
-    const float t6 = c.x * ri6;
-    const float t12 = c.y * ri6 * ri6;
-    e12 += in ? t12 : 0.f;
-    e6 += in ? t6 : 0.f;
+    if (kp.mods & NB_MOD_LJ_SHIFT) {
+        // Shifted LJ energies, c12 (r^-12 - rc^-12) and c6 (r^-6 - rc^-6),
+        // in double-float: the shift takes away most of E_LJ, so the float32
+        // terms' rounding would no longer be small next to what is left.
+        float ah, al;
+        fast_two_sum(y, ril, ah, al);  // 1/r
+        float p2h, p2l, p4h, p4l, p6h, p6l, p12h, p12l;
+        dd_mul(ah, al, ah, al, p2h, p2l);
+        dd_mul(p2h, p2l, p2h, p2l, p4h, p4l);
+        dd_mul(p4h, p4l, p2h, p2l, p6h, p6l);
+        dd_mul(p6h, p6l, p6h, p6l, p12h, p12l);
+        float dh, dl, t6, t6l, t12, t12l;
+        two_sum(p6h, -kp.irc6_h, dh, dl);
+        dl += p6l - kp.irc6_l;
+        two_prod(c.x, dh, t6, t6l);
+        t6l = fmaf(c.x, dl, t6l);
+        two_sum(p12h, -kp.irc12_h, dh, dl);
+        dl += p12l - kp.irc12_l;
+        two_prod(c.y, dh, t12, t12l);
+        t12l = fmaf(c.y, dl, t12l);
+        if (in) {
+            float sh, se;
+            two_sum(e12, t12, sh, se);
+            e12 = sh;
+            e12l += se + t12l;
+            two_sum(e6, t6, sh, se);
+            e6 = sh;
+            e6l += se + t6l;
+        }
+    } else {
+        const float ri2 = rif * rif;
+        const float ri6 = ri2 * ri2 * ri2;
+        const float t6 = c.x * ri6;
+        const float t12 = c.y * ri6 * ri6;
+        e12 += in ? t12 : 0.f;
+        e6 += in ? t6 : 0.f;
+    }
 
     float qh, qe;
     two_prod(qih, xj.w, qh, qe);
@@ -184,7 +219,14 @@ __device__ __forceinline__ void pair_energy(const float4 xj, int tj, const Shift
         // w = erfc / r, V = q q w
         float wh, we;
         two_prod(eh, y, wh, we);
-        const float wl = we + fmaf(eh, ril, el * y);
+        float wl = we + fmaf(eh, ril, el * y);
+        if (kp.mods & NB_MOD_EWALD_SHIFT) {
+            // w - erfc(beta rc)/rc, in double-float
+            float dh, de;
+            two_sum(wh, -kp.ewc_h, dh, de);
+            wl = de + (wl - kp.ewc_l);
+            wh = dh;
+        }
         float ve;
         two_prod(qh, wh, vh, ve);
         vl = ve + fmaf(qh, wl, ql * wh);
@@ -232,14 +274,15 @@ template <int COUL>
 __device__ __forceinline__ void drain(int k, const int* __restrict__ qm, const IRec* __restrict__ irec,
                                       const float4* __restrict__ xq_s, const int* __restrict__ type_s,
                                       const float2* __restrict__ s_lj, const KParams& kp, float& ch,
-                                      float& cl, float& e12, float& e6, int& npair, bool valid) {
+                                      float& cl, float& e12, float& e12l, float& e6, float& e6l, int& npair,
+                                      bool valid) {
     const int m = valid ? qm[k & (QCAP - 1)] : 0;
     const int js = m >> 4;
     const float4 xj = valid ? xq_s[js] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int tj = valid ? type_s[js] : 0;
     const IRec& ir = irec[(m >> 1) & 7];
-    pair_energy<COUL>(xj, tj, ir.xs, ir.qih, ir.qil, ir.tirow, s_lj, valid, m & 1, kp, ch, cl, e12, e6,
-                      npair);
+    pair_energy<COUL>(xj, tj, ir.xs, ir.qih, ir.qil, ir.tirow, s_lj, valid, m & 1, kp, ch, cl, e12, e12l, e6,
+                      e6l, npair);
 }
 
 template <int COUL>
@@ -308,7 +351,7 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             irec[i] = r;
         }
 
-        float ch = 0.f, cl = 0.f, e12 = 0.f, e6 = 0.f;
+        float ch = 0.f, cl = 0.f, e12 = 0.f, e12l = 0.f, e6 = 0.f, e6l = 0.f;
         int npair = 0;
         int head = 0, tail = 0;  // ring positions, identical in every lane
 
@@ -356,16 +399,17 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             }
             __syncwarp();
             while (tail - head >= 32) {
-                drain<COUL>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e6, npair, true);
+                drain<COUL>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e12l, e6, e6l, npair,
+                            true);
                 head += 32;
             }
         }
         if (tail > head)
-            drain<COUL>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e6, npair,
+            drain<COUL>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e12l, e6, e6l, npair,
                         lane < tail - head);
         dec += (double)ch + (double)cl;
-        d12 += (double)e12;
-        d6 += (double)e6;
+        d12 += (double)e12 + (double)e12l;
+        d6 += (double)e6 + (double)e6l;
         if (lane == 0) np += npair;
     }
     if (cur_sys >= 0) flush_energy(sys, cur_sys, dec, d12, d6, np, lane);

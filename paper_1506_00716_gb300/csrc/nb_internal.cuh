@@ -119,6 +119,10 @@ struct KParams {
     float beta_h, beta_l;
     int coul;
     int ntypes;
+    unsigned mods;       // NB_MOD_* potential modifiers
+    float irc6_h, irc6_l, irc12_h, irc12_l;  // rc^-6, rc^-12 as hi + lo (NB_MOD_LJ_SHIFT)
+    float ewc_h, ewc_l;  // erfc(beta rc) / rc as hi + lo (NB_MOD_EWALD_SHIFT)
+    double fq_d, krf_d, crf_d;  // f / eps_r, k_rf, c_rf in float64 (NB_MOD_RF_EXCL)
     int max_entries;     // list entries per work item (items are split beyond)
     int lpt_max_items;   // item count up to which items run longest first
     int force_min_blocks;  // force-kernel launch-bounds variant: 1, 2 or 3
@@ -200,5 +204,8 @@ cudaError_t launch_prepare(const PlanLaunch& p, bool coords, cudaStream_t st);
 cudaError_t launch_forces(const PlanLaunch& p, unsigned flags, cudaStream_t st);
 cudaError_t launch_energy(const PlanLaunch& p, cudaStream_t st);
 cudaError_t launch_finalize(const PlanLaunch& p, unsigned flags, cudaStream_t st);
+// Reaction-field correction of excluded pairs (NB_MOD_RF_EXCL; nothing
+// otherwise): after the force and energy kernels, before the finalisation.
+cudaError_t launch_excl_corr(const PlanLaunch& p, unsigned flags, cudaStream_t st);
 
 }  // namespace nbgb

@@ -245,6 +245,7 @@ nb_status run_wave(nb_server* s, int k, double boost) {
     if (e == cudaSuccess) e = launch_prepare(pl, false, st);
     if (e == cudaSuccess) e = launch_forces(pl, flags, st);
     if (e == cudaSuccess && (flags & NB_F_ENERGY)) e = launch_energy(pl, st);
+    if (e == cudaSuccess) e = launch_excl_corr(pl, flags, st);
     if (e == cudaSuccess) e = launch_finalize(pl, flags, st);
     float* hf = (float*)s->f_stage[k].p;
     double* hres = (double*)s->res_stage[k].p;

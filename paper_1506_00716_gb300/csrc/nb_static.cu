@@ -201,6 +201,7 @@ extern "C" nb_status nb_eval_noalloc(const nb_params* params, int natoms, const 
     NA_CK(launch_prepare(p, false, st));
     NA_CK(launch_forces(p, flags, st));
     if (flags & NB_F_ENERGY) NA_CK(launch_energy(p, st));
+    NA_CK(launch_excl_corr(p, flags, st));
     NA_CK(launch_finalize(p, flags, st));
     if (f) NA_CK(cudaMemcpyAsync(f, h.f_out, 12 * (size_t)natoms, cudaMemcpyDefault, st));
     if (flags & NB_F_ENERGY) NA_CK(cudaMemcpyAsync(energy, h.res, 16, cudaMemcpyDefault, st));

@@ -33,6 +33,9 @@ EXPORTS = ["nb_last_error", "nb_ctx_create", "nb_ctx_destroy", "nb_ctx_memory", 
            "nb_eval_noalloc", "nb_ctx_set_tuning", "nb_ctx_get_tuning", "nb_server_create",
            "nb_server_destroy", "nb_server_submit", "nb_server_wait"]
 NB_NSTAGE = 8
+NB_MOD_LJ_SHIFT = 1
+NB_MOD_EWALD_SHIFT = 2
+NB_MOD_RF_EXCL = 4
 STAGES = ["grid", "search", "prune", "coord", "zero", "forces", "final", "energy"]
 
 
@@ -47,7 +50,7 @@ class nb_params(ctypes.Structure):
                 ("eps_r", ctypes.c_double), ("eps_rf", ctypes.c_double),
                 ("ewald_beta", ctypes.c_double), ("fcoul", ctypes.c_double),
                 ("ntypes", ctypes.c_int), ("c6", ctypes.POINTER(ctypes.c_float)),
-                ("c12", ctypes.POINTER(ctypes.c_float))]
+                ("c12", ctypes.POINTER(ctypes.c_float)), ("modifiers", ctypes.c_uint)]
 
 
 class nb_tuning(ctypes.Structure):
@@ -161,7 +164,7 @@ def make_params(p) -> tuple[nb_params, tuple]:
     fp = ctypes.POINTER(ctypes.c_float)
     s = nb_params(float(p.rc), float(p.rlist), int(p.coul), float(p.eps_r), float(p.eps_rf),
                   float(p.beta), float(p.fcoul), int(p.ntypes), c6.ctypes.data_as(fp),
-                  c12.ctypes.data_as(fp))
+                  c12.ctypes.data_as(fp), int(getattr(p, "modifiers", 0)))
     return s, (c6, c12)
 
 

@@ -72,6 +72,16 @@ def main():
             ref = oracle.energy_virial(s, p)
             rows.append(_row(f"{name}, {cname}", rel_rms(f, oracle.forces(s, p)), e, v, npairs, ref))
             print(rows[-1], flush=True)
+    for name, s in (("small (1,944 atoms)", wb.small_box(seed=1)), ("mid (24,000 atoms)", wb.mid_box(seed=2))):
+        for cname, coul, mods, label in (
+                ("RF", wb.COUL_RF, nb.NB_MOD_LJ_SHIFT | nb.NB_MOD_RF_EXCL, "LJ shift + RF exclusion correction"),
+                ("Ewald", wb.COUL_EWALD, nb.NB_MOD_LJ_SHIFT | nb.NB_MOD_EWALD_SHIFT, "LJ + Ewald shifts")):
+            p = wb.Params(coul=coul, modifiers=mods)
+            autotune.apply(ctx, "rf" if cname == "RF" else "ewald", s.n, gpu=gpu)
+            f, e, v, npairs = _eval(ctx, s, p)
+            ref = oracle.energy_virial(s, p)
+            rows.append(_row(f"{name}, {cname}, {label}", rel_rms(f, oracle.forces(s, p)), e, v, npairs, ref))
+            print(rows[-1], flush=True)
     s = wb.large_box(seed=3)
     p = wb.params_ewald()
     autotune.apply(ctx, "ewald", s.n, gpu=gpu)

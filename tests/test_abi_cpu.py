@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 import shutil
+import subprocess
 
 import pytest
 
@@ -38,10 +39,44 @@ def test_exports_every_declared_function(lib):
         assert getattr(lib, name) is not None
 
 
-def test_params_struct_layout_matches_header():
-    # double rc, rlist; int coul; double eps_r, eps_rf, ewald_beta, fcoul; int ntypes; 2 pointers
-    assert ctypes.sizeof(nb.nb_params) == 8 * 2 + 8 + 8 * 4 + 8 + 8 * 2
-    assert ctypes.sizeof(nb.nb_list_info) == 5 * 8
+def test_params_struct_layout_matches_header(tmp_path):
+    """The binding's structs have the C compiler's layout of include/nb.h."""
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "nb.h"\n'
+        "#define F(s, m) printf(#s \" \" #m \" %zu\\n\", offsetof(s, m))\n"
+        "int main(void) {\n"
+        '  printf("nb_params size %zu\\n", sizeof(nb_params));\n'
+        "  F(nb_params, rc); F(nb_params, rlist); F(nb_params, coul); F(nb_params, eps_r);\n"
+        "  F(nb_params, eps_rf); F(nb_params, ewald_beta); F(nb_params, fcoul); F(nb_params, ntypes);\n"
+        "  F(nb_params, c6); F(nb_params, c12); F(nb_params, modifiers);\n"
+        '  printf("nb_tuning size %zu\\n", sizeof(nb_tuning));\n'
+        '  printf("nb_request_stats size %zu\\n", sizeof(nb_request_stats));\n'
+        '  printf("nb_list_info size %zu\\n", sizeof(nb_list_info));\n'
+        "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {" ".join(line.split()[:2]): int(line.split()[2]) for line in out if line.strip()}
+    assert got["nb_params size"] == ctypes.sizeof(nb.nb_params)
+    for name, _ in nb.nb_params._fields_:
+        assert got[f"nb_params {name}"] == getattr(nb.nb_params, name).offset, name
+    assert got["nb_tuning size"] == ctypes.sizeof(nb.nb_tuning)
+    assert got["nb_request_stats size"] == ctypes.sizeof(nb.nb_request_stats)
+    assert got["nb_list_info size"] == ctypes.sizeof(nb.nb_list_info)
+
+
+def test_modifiers_are_validated(lib):
+    box = [3.0, 3.0, 3.0]
+    ok = [(wb.COUL_RF, nb.NB_MOD_LJ_SHIFT | nb.NB_MOD_RF_EXCL),
+          (wb.COUL_EWALD, nb.NB_MOD_LJ_SHIFT | nb.NB_MOD_EWALD_SHIFT)]
+    for coul, mods in ok:
+        assert nb.nb_sys_footprint(wb.Params(coul=coul, modifiers=mods), 1944, box) > 0
+    bad = [(wb.COUL_RF, nb.NB_MOD_EWALD_SHIFT), (wb.COUL_EWALD, nb.NB_MOD_RF_EXCL), (wb.COUL_RF, 8)]
+    for coul, mods in bad:
+        with pytest.raises(nb.NbError) as e:
+            nb.nb_sys_footprint(wb.Params(coul=coul, modifiers=mods), 1944, box)
+        assert e.value.status == 1  # NB_ERR_ARG
 
 
 def test_footprint_validates_arguments(lib):

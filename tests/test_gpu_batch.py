@@ -168,3 +168,25 @@ def test_batch_recovers_from_a_list_overflow(torch_cuda):
         for h in handles:
             nb.nb_sys_destroy(h)
         nb.nb_ctx_destroy(ctx)
+
+
+def test_batch_with_reaction_field_exclusion_correction(torch_cuda):
+    """The modifiers go through the batched path too (one launch per stage
+    for all systems, the excluded-pair correction included)."""
+    torch = torch_cuda
+    stream = torch.cuda.Stream()
+    ctx = nb.nb_ctx_create(0, stream, 0)
+    try:
+        systems = _systems()[:3]
+        p = wb.Params(coul=wb.COUL_RF, modifiers=nb.NB_MOD_LJ_SHIFT | nb.NB_MOD_RF_EXCL)
+        runs = _run_batch(ctx, systems, p, submits=1)
+        for k, s in enumerate(systems):
+            f, e, v = runs[0][k]
+            ref = oracle.energy_virial(s, p)
+            assert rel_rms(f, oracle.forces(s, p)) < 1e-5
+            assert abs(e[0] - ref["e_lj"]) <= 1e-6 * abs(ref["e_lj"])
+            assert abs(e[1] - ref["e_coul"]) <= 1e-6 * abs(ref["e_coul"])
+            vr = ref["virial"].reshape(-1)
+            assert np.abs(v - vr).max() <= 1e-6 * np.linalg.norm(vr)
+    finally:
+        nb.nb_ctx_destroy(ctx)

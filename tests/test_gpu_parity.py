@@ -182,6 +182,26 @@ def test_box_of_exactly_two_list_radii(ctx):
     _check(s, p, f, e, v)
 
 
+MODIFIER_CASES = [
+    (wb.COUL_RF, nb.NB_MOD_LJ_SHIFT),
+    (wb.COUL_RF, nb.NB_MOD_RF_EXCL),
+    (wb.COUL_RF, nb.NB_MOD_LJ_SHIFT | nb.NB_MOD_RF_EXCL),
+    (wb.COUL_EWALD, nb.NB_MOD_EWALD_SHIFT),
+    (wb.COUL_EWALD, nb.NB_MOD_LJ_SHIFT | nb.NB_MOD_EWALD_SHIFT),
+]
+
+
+@pytest.mark.parametrize("coul,mods", MODIFIER_CASES)
+@pytest.mark.parametrize("name", ["small", "mid"])
+def test_potential_modifiers(ctx, name, coul, mods):
+    """Potential-shift and excluded-pair reaction-field variants against the
+    oracle with the same modifiers, at the standard tolerances."""
+    s = BOXES[name]()
+    p = wb.Params(coul=coul, modifiers=mods)
+    f, e, v, _ = gpu_eval(ctx, s, p)
+    _check(s, p, f, e, v)
+
+
 def test_one_sided_exclusions_are_symmetrised(ctx):
     """Exclusions listed in one direction only, unsorted, with a self pair and
     a duplicate, give the same result as the canonical symmetric list: the
