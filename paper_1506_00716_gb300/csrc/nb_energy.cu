@@ -112,7 +112,7 @@ __device__ __forceinline__ void erfc_dd(float xh, float xl, float ah, float al, 
 // Energy of one queued pair.  `valid`: the lane holds a pair; `maybe`: its
 // float32 r^2 fell in the band around rc^2 and the decision is taken here,
 // exactly; otherwise the pair is inside rc.
-template <int COUL>
+template <int COUL, bool LJSH>
 __device__ __forceinline__ void pair_energy(const float4 xj, int tj, const ShiftedI& xs, float qih,
                                             float qil, int tirow, const float2* __restrict__ s_lj,
                                             bool valid, bool maybe, const KParams& kp, float& ch,
@@ -150,7 +150,7 @@ __device__ __forceinline__ void pair_energy(const float4 xj, int tj, const Shift
     const float rif = y + ril;
 
     const float2 c = s_lj[tirow + tj];
-    if (kp.mods & NB_MOD_LJ_SHIFT) {
+    if (LJSH) {
         // Shifted LJ energies, c12 (r^-12 - rc^-12) and c6 (r^-6 - rc^-6),
         // in double-float: the shift takes away most of E_LJ, so the float32
         // terms' rounding would no longer be small next to what is left.
@@ -270,7 +270,7 @@ struct IRec {
 };
 
 // Queue entry: j slot index << 4 | i-slot << 1 | band flag.
-template <int COUL>
+template <int COUL, bool LJSH>
 __device__ __forceinline__ void drain(int k, const int* __restrict__ qm, const IRec* __restrict__ irec,
                                       const float4* __restrict__ xq_s, const int* __restrict__ type_s,
                                       const float2* __restrict__ s_lj, const KParams& kp, float& ch,
@@ -281,11 +281,11 @@ __device__ __forceinline__ void drain(int k, const int* __restrict__ qm, const I
     const float4 xj = valid ? xq_s[js] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int tj = valid ? type_s[js] : 0;
     const IRec& ir = irec[(m >> 1) & 7];
-    pair_energy<COUL>(xj, tj, ir.xs, ir.qih, ir.qil, ir.tirow, s_lj, valid, m & 1, kp, ch, cl, e12, e12l, e6,
+    pair_energy<COUL, LJSH>(xj, tj, ir.xs, ir.qih, ir.qil, ir.tirow, s_lj, valid, m & 1, kp, ch, cl, e12, e12l, e6,
                       e6l, npair);
 }
 
-template <int COUL>
+template <int COUL, bool LJSH>
 __global__ void __launch_bounds__(EW * 32)
 k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     pdl_wait();
@@ -399,13 +399,13 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             }
             __syncwarp();
             while (tail - head >= 32) {
-                drain<COUL>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e12l, e6, e6l, npair,
+                drain<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e12l, e6, e6l, npair,
                             true);
                 head += 32;
             }
         }
         if (tail > head)
-            drain<COUL>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e12l, e6, e6l, npair,
+            drain<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e12l, e6, e6l, npair,
                         lane < tail - head);
         dec += (double)ch + (double)cl;
         d12 += (double)e12 + (double)e12l;
@@ -415,10 +415,10 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     if (cur_sys >= 0) flush_energy(sys, cur_sys, dec, d12, d6, np, lane);
 }
 
-template <int COUL>
+template <int COUL, bool LJSH>
 cudaError_t launch_energy_t(const PlanLaunch& p, cudaStream_t st) {
     size_t smem = (size_t)p.kp.ntypes * p.kp.ntypes * sizeof(float2);
-    auto kern = k_energy<COUL>;
+    auto kern = k_energy<COUL, LJSH>;
     int per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, EW * 32, smem);
     if (err != cudaSuccess) return err;
@@ -429,8 +429,12 @@ cudaError_t launch_energy_t(const PlanLaunch& p, cudaStream_t st) {
 }  // namespace
 
 cudaError_t launch_energy(const PlanLaunch& p, cudaStream_t st) {
-    if (p.kp.coul == NB_COUL_RF) return launch_energy_t<NB_COUL_RF>(p, st);
-    return launch_energy_t<NB_COUL_EWALD>(p, st);
+    // the shifted LJ terms are a separate instantiation (double-float LJ),
+    // so the default kernel keeps its register budget
+    const bool ljsh = p.kp.mods & NB_MOD_LJ_SHIFT;
+    if (p.kp.coul == NB_COUL_RF)
+        return ljsh ? launch_energy_t<NB_COUL_RF, true>(p, st) : launch_energy_t<NB_COUL_RF, false>(p, st);
+    return ljsh ? launch_energy_t<NB_COUL_EWALD, true>(p, st) : launch_energy_t<NB_COUL_EWALD, false>(p, st);
 }
 
 }  // namespace nbgb
