@@ -116,6 +116,8 @@ typedef struct {
     long long n_entries;     /* cluster-pair entries after pruning */
     long long n_entries_raw; /* entries that passed the bounding-box test */
     long long n_slots;       /* M*N atom-pair slots the kernel evaluates */
+    long long n_entries_inner; /* entries of the inner list (nb_pairlist_prune),
+                                  n_entries when there is none */
 } nb_list_info;
 
 /* Result counts of the last evaluation (nb_eval_info). */
@@ -227,6 +229,18 @@ nb_status nb_grid_put(nb_sys *sys, const float *xq, const int *type);
  */
 nb_status nb_pairlist_build(nb_sys *sys);
 nb_status nb_pairlist_info(nb_sys *sys, nb_list_info *info);
+/*
+ * Dynamic pruning (Section 3.2.1: the list is built with a buffer, pruned on
+ * the GPU and reused): prune the list of the last nb_pairlist_build, out of
+ * place, to the radius r_inner (rc <= r_inner <= rlist) using the current
+ * coordinates (those of the last nb_grid_put or nb_forces).  Until the next
+ * nb_pairlist_build, evaluations use this inner list; the outer one is kept,
+ * so the call can be repeated as the atoms move.  The caller keeps every
+ * displacement since the call small enough for r_inner - rc to cover it, as
+ * rlist - rc must cover those since the build.  NB_ERR_STATE without a list,
+ * NB_ERR_ARG for r_inner outside [rc, rlist].
+ */
+nb_status nb_pairlist_prune(nb_sys *sys, double r_inner);
 
 /*
  * Evaluate forces (and, per flags, energies and virial) with the current

@@ -370,10 +370,47 @@ bool same_params(const nb_sys* a, const nb_sys* b) {
            p.ntypes == q.ntypes && p.modifiers == q.modifiers && a->c6 == b->c6 && a->c12 == b->c12;
 }
 
+void plan_free_inner(Plan* pl) {
+    if (pl->inner_block) dev_free(pl->ctx, pl->inner_block, pl->inner_bytes);
+    pl->inner_block = nullptr;
+    pl->inner_bytes = 0;
+    pl->inner = ListDev{};
+    pl->use_inner = false;
+}
+
 void plan_free_list(Plan* pl) {
+    plan_free_inner(pl);
     if (pl->list_block) dev_free(pl->ctx, pl->list_block, pl->list_bytes);
     pl->list_block = nullptr;
     pl->list_bytes = 0;
+}
+
+// Buffers of the inner list, with the outer list's capacities.
+nb_status plan_alloc_inner(Plan* pl) {
+    if (pl->inner_block && pl->inner.item_cap == pl->list.item_cap && pl->inner.entry_cap == pl->list.entry_cap)
+        return NB_OK;
+    plan_free_inner(pl);
+    const size_t items = (size_t)pl->list.item_cap, entries = (size_t)pl->list.entry_cap;
+    size_t bytes = align256(16 * items) + align256(4 * items) + align256(4 * entries) + align256(8 * entries) +
+                   align256(4 * CNT_N);
+    void* blk = nullptr;
+    nb_status s = dev_alloc(pl->ctx, &blk, bytes);
+    if (s != NB_OK) return s;
+    char* b = (char*)blk;
+    pl->inner.items = (int4*)b;
+    b += align256(16 * items);
+    pl->inner.order = (int*)b;
+    b += align256(4 * items);
+    pl->inner.cj = (int*)b;
+    b += align256(4 * entries);
+    pl->inner.mask = (unsigned long long*)b;
+    b += align256(8 * entries);
+    pl->inner.counters = (int*)b;
+    pl->inner.item_cap = pl->list.item_cap;
+    pl->inner.entry_cap = pl->list.entry_cap;
+    pl->inner_block = blk;
+    pl->inner_bytes = bytes;
+    return NB_OK;
 }
 
 void plan_drop_graphs(Plan* pl) {
@@ -505,7 +542,7 @@ PlanLaunch launch_of(const Plan* pl) {
     p.tot_atoms = pl->tot_atoms;
     p.tot_cols = pl->tot_cols;
     p.tot_clcap = pl->tot_clcap;
-    p.list = pl->list;
+    p.list = pl->use_inner ? pl->inner : pl->list;
     p.kp = pl->kp;
     p.num_sms = pl->ctx->num_sms;
     return p;
@@ -524,6 +561,7 @@ nb_status stage_coords(nb_sys* s, const float* xq, const int* type) {
 // Search + prune with capacity growth.  Synchronises the stream.
 nb_status plan_build_list(Plan* pl) {
     cudaStream_t st = pl->ctx->stream;
+    pl->use_inner = false;  // a new outer list supersedes any inner one
     for (int attempt = 0; attempt < 4; ++attempt) {
         NB_CK(cudaMemsetAsync(pl->list.counters + CNT_ITEMS, 0, 4 * 2, st));
         NB_CK(cudaMemsetAsync(pl->list.counters + CNT_PRUNED, 0, 4 * (CNT_N - CNT_PRUNED), st));
@@ -909,6 +947,29 @@ nb_status nb_pairlist_build(nb_sys* sys) {
     return NB_OK;
 }
 
+nb_status nb_pairlist_prune(nb_sys* sys, double r_inner) {
+    if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
+    if (!sys->listed) return fail(NB_ERR_STATE, "nb_pairlist_prune needs a pair list (nb_pairlist_build)");
+    if (!(r_inner >= sys->p.rc) || !(r_inner <= sys->p.rlist))
+        return fail(NB_ERR_ARG, "r_inner must lie in [rc, rlist]");
+    Plan* pl = sys->plan;
+    cudaStream_t st = sys->ctx->stream;
+    nb_status s = plan_alloc_inner(pl);
+    if (s != NB_OK) return s;
+    NB_CK(cudaMemsetAsync(pl->inner.counters, 0, 4 * CNT_N, st));
+    // padded like the outer radius, for the float32 rounding of coordinates
+    double maxL = std::max(sys->box[0], std::max(sys->box[1], sys->box[2]));
+    double r = r_inner + 1e-5 * (1.0 + maxL);
+    pl->use_inner = false;
+    PlanLaunch p = launch_of(pl);
+    {
+        StageScope sc(sys->ctx, NB_STAGE_PRUNE);
+        NB_CK(launch_prune_into(p, pl->list, pl->inner, (float)(r * r), st));
+    }
+    pl->use_inner = true;
+    return NB_OK;
+}
+
 nb_status nb_pairlist_info(nb_sys* sys, nb_list_info* info) {
     if (!sys || !info) return fail(NB_ERR_ARG, "sys / info is NULL");
     if (!sys->listed) return fail(NB_ERR_STATE, "no pair list");
@@ -922,7 +983,13 @@ nb_status nb_pairlist_info(nb_sys* sys, nb_list_info* info) {
     info->n_items = pl->h_counters[CNT_ITEMS];
     info->n_entries_raw = pl->h_counters[CNT_ENTRIES];
     info->n_entries = pl->h_counters[CNT_PRUNED];
-    info->n_slots = (long long)pl->h_counters[CNT_PRUNED] * CL * CL;
+    info->n_entries_inner = info->n_entries;
+    if (pl->use_inner) {
+        NB_CK(cudaMemcpyAsync(pl->h_counters, pl->inner.counters, 4 * CNT_N, cudaMemcpyDeviceToHost, st));
+        NB_CK(cudaStreamSynchronize(st));
+        info->n_entries_inner = pl->h_counters[CNT_PRUNED];
+    }
+    info->n_slots = info->n_entries_inner * CL * CL;
     return NB_OK;
 }
 

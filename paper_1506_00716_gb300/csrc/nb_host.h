@@ -72,6 +72,12 @@ struct Plan {
     nbgb::ListDev list{};
     void* list_block = nullptr;
     size_t list_bytes = 0;
+    // inner list (nb_pairlist_prune): the outer list pruned, out of place, to
+    // a smaller radius; the evaluations use it while use_inner is set
+    nbgb::ListDev inner{};
+    void* inner_block = nullptr;
+    size_t inner_bytes = 0;
+    bool use_inner = false;
     size_t fixed_bytes = 0;
     int tot_atoms = 0, tot_cols = 0, tot_clcap = 0;
     long long item_cap = 0, entry_cap = 0;

@@ -198,6 +198,10 @@ void api_list_estimate(const nb_params& p, int natoms, const double box[3], int 
 cudaError_t launch_grid_put(const PlanLaunch& p, cudaStream_t st);
 cudaError_t launch_search(const PlanLaunch& p, cudaStream_t st);
 cudaError_t launch_prune(const PlanLaunch& p, cudaStream_t st);
+// Prune src out of place into dst (same capacities) at radius^2 rl2_inner;
+// dst's counters must be zero.
+cudaError_t launch_prune_into(const PlanLaunch& p, const ListDev& src, const ListDev& dst, float rl2_inner,
+                              cudaStream_t st);
 // Start of an evaluation: clear forces, accumulators and work counters; with
 // coords, also move the staged x_new into the sorted slots.
 cudaError_t launch_prepare(const PlanLaunch& p, bool coords, cudaStream_t st);

@@ -375,8 +375,13 @@ constexpr int PRUNE_WARPS = 8;
 // i-atoms of the item, which every lane keeps in registers.  Kept entries are
 // compacted in place, in order, without the mark; a write never passes the
 // entries still to be read.
+//
+// The same kernel prunes out of place (dst != src, the inner list of
+// nb_pairlist_prune): it then tests every entry against the radius rl2_inner
+// and writes the kept entries to the same positions of dst, with dst's items,
+// counters and order.
 __global__ void __launch_bounds__(PRUNE_WARPS * 32, 3)
-k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
+k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, float rl2_inner) {
     pdl_wait();
     pdl_trigger();
     __shared__ unsigned char s_rank[PRUNE_WARPS][32];
@@ -384,13 +389,18 @@ k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     const int w = threadIdx.x >> 5;
     const int jj = lane & 7;
     const int g = lane >> 3;
-    const int nitems = min(list.counters[CNT_ITEMS], list.item_cap);
+    const bool inner = rl2_inner > 0.f;
+    const int nitems = min(src.counters[CNT_ITEMS], src.item_cap);
     const bool ordered = nitems <= kp.lpt_max_items;
+    if (inner && blockIdx.x == 0 && threadIdx.x == 0) dst.counters[CNT_ITEMS] = nitems;
     for (int it = blockIdx.x * PRUNE_WARPS + w; it < nitems; it += gridDim.x * PRUNE_WARPS) {
-        const int4 item = list.items[it];
-        if (item.y >= item.z) continue;
+        const int4 item = src.items[it];
+        if (item.y >= item.z) {
+            if (inner && (threadIdx.x & 31) == 0) dst.items[it] = item;
+            continue;
+        }
         const SysDev& d = sys[item.w >> 5];
-        const float rl2 = d.rl2_prune;
+        const float rl2 = inner ? rl2_inner : d.rl2_prune;
         const int sh = item.w & 31;
         const float Sx = (sh / 9 - 1) * d.L[0], Sy = ((sh / 3) % 3 - 1) * d.L[1], Sz = (sh % 3 - 1) * d.L[2];
         float3 xi[CL];
@@ -406,10 +416,10 @@ k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             unsigned long long m = 0ull;
             bool chk = false;
             if (lane < n) {
-                const int c = list.cj[base + lane];
-                chk = (c & PRUNE_CHECK) != 0;
+                const int c = src.cj[base + lane];
+                chk = inner || (c & PRUNE_CHECK) != 0;
                 cjv = c & ~PRUNE_CHECK;
-                m = list.mask[base + lane];
+                m = src.mask[base + lane];
             }
             const unsigned chk_bal = __ballot_sync(FULL, chk);
             unsigned keep = __ballot_sync(FULL, lane < n && !chk);  // bit k: entry base + k is kept
@@ -458,19 +468,19 @@ k_prune(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             __syncwarp();
             if (lane < n && ((keep >> lane) & 1u)) {
                 const int idx = write + __popc(keep & ((1u << lane) - 1u));
-                list.cj[idx] = cjv;
-                list.mask[idx] = m;
+                dst.cj[idx] = cjv;
+                dst.mask[idx] = m;
             }
             write += __popc(keep);
         }
         if (lane == 0) {
             const int len = write - item.y;
-            list.items[it].z = write;
-            atomicAdd(list.counters + CNT_PRUNED, len);
+            dst.items[it] = make_int4(item.x, item.y, write, item.w);
+            atomicAdd(dst.counters + CNT_PRUNED, len);
             if (ordered && len > kp.max_entries / 2)
-                list.order[atomicAdd(list.counters + CNT_ORD_LONG, 1)] = it;
+                dst.order[atomicAdd(dst.counters + CNT_ORD_LONG, 1)] = it;
             else if (ordered && len > 0)
-                list.order[list.item_cap - 1 - atomicAdd(list.counters + CNT_ORD_SHORT, 1)] = it;
+                dst.order[dst.item_cap - 1 - atomicAdd(dst.counters + CNT_ORD_SHORT, 1)] = it;
         }
     }
 }
@@ -486,7 +496,13 @@ cudaError_t launch_search(const PlanLaunch& p, cudaStream_t st) {
 
 cudaError_t launch_prune(const PlanLaunch& p, cudaStream_t st) {
     unsigned blocks = (unsigned)(p.num_sms * 8);
-    return launch_pdl(k_prune, blocks, PRUNE_WARPS * 32, 0, st, p.d_sys, p.list, p.kp);
+    return launch_pdl(k_prune, blocks, PRUNE_WARPS * 32, 0, st, p.d_sys, p.list, p.list, p.kp, -1.f);
+}
+
+cudaError_t launch_prune_into(const PlanLaunch& p, const ListDev& src, const ListDev& dst, float rl2_inner,
+                              cudaStream_t st) {
+    unsigned blocks = (unsigned)(p.num_sms * 8);
+    return launch_pdl(k_prune, blocks, PRUNE_WARPS * 32, 0, st, p.d_sys, src, dst, p.kp, rl2_inner);
 }
 
 }  // namespace nbgb

@@ -27,7 +27,7 @@ STATUS = {0: "NB_OK", 1: "NB_ERR_ARG", 2: "NB_ERR_BOX", 3: "NB_ERR_OOM", 4: "NB_
 # the exported functions declared in include/nb.h
 EXPORTS = ["nb_last_error", "nb_ctx_create", "nb_ctx_destroy", "nb_ctx_memory", "nb_sys_footprint",
            "nb_sys_create", "nb_sys_destroy", "nb_set_exclusions", "nb_grid_put", "nb_pairlist_build",
-           "nb_pairlist_info", "nb_forces", "nb_pairlist_export", "nb_batch_create",
+           "nb_pairlist_info", "nb_pairlist_prune", "nb_forces", "nb_pairlist_export", "nb_batch_create",
            "nb_batch_destroy", "nb_sys_set_coords", "nb_batch_submit", "nb_batch_poll",
            "nb_sys_results", "nb_ctx_set_timing", "nb_ctx_set_timing_stages", "nb_ctx_timing", "nb_eval_info",
            "nb_eval_noalloc", "nb_ctx_set_tuning", "nb_ctx_get_tuning", "nb_server_create",
@@ -65,7 +65,7 @@ class nb_request_stats(ctypes.Structure):
 class nb_list_info(ctypes.Structure):
     _fields_ = [("n_clusters", ctypes.c_longlong), ("n_items", ctypes.c_longlong),
                 ("n_entries", ctypes.c_longlong), ("n_entries_raw", ctypes.c_longlong),
-                ("n_slots", ctypes.c_longlong)]
+                ("n_slots", ctypes.c_longlong), ("n_entries_inner", ctypes.c_longlong)]
 
 
 _lib = None
@@ -100,6 +100,7 @@ def load(path: str | None = None):
         "nb_grid_put": ([_vp, _vp, _vp], _st),
         "nb_pairlist_build": ([_vp], _st),
         "nb_pairlist_info": ([_vp, ctypes.POINTER(nb_list_info)], _st),
+        "nb_pairlist_prune": ([_vp, ctypes.c_double], _st),
         "nb_forces": ([_vp, _vp, _vp, _vp, _vp, ctypes.c_uint], _st),
         "nb_pairlist_export": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong)], _st),
         "nb_batch_create": ([_vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp)], _st),
@@ -233,6 +234,10 @@ def nb_pairlist_info(sys) -> dict:
     info = nb_list_info()
     check(load().nb_pairlist_info(sys, ctypes.byref(info)))
     return {k: getattr(info, k) for k, _ in nb_list_info._fields_}
+
+
+def nb_pairlist_prune(sys, r_inner: float) -> None:
+    check(load().nb_pairlist_prune(sys, float(r_inner)))
 
 
 def nb_forces(sys, x_new=None, f=None, energy=None, virial=None, flags: int = 0) -> None:

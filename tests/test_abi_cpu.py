@@ -63,7 +63,7 @@ def test_params_struct_layout_matches_header(tmp_path):
         assert got[f"nb_params {name}"] == getattr(nb.nb_params, name).offset, name
     assert got["nb_tuning size"] == ctypes.sizeof(nb.nb_tuning)
     assert got["nb_request_stats size"] == ctypes.sizeof(nb.nb_request_stats)
-    assert got["nb_list_info size"] == ctypes.sizeof(nb.nb_list_info)
+    assert got["nb_list_info size"] == ctypes.sizeof(nb.nb_list_info) == 6 * 8
 
 
 def test_modifiers_are_validated(lib):

@@ -140,6 +140,54 @@ def test_stale_list_evaluations(ctx):
         nb.nb_sys_destroy(h)
 
 
+def test_dynamic_pruning(ctx):
+    """Outer list at rlist = 1.3 nm built once; pruned out of place to an inner
+    list at 1.1 nm every 5 evaluations while the atoms move (Gaussian, sigma
+    0.005 nm per evaluation); every checked evaluation matches the oracle,
+    interacting-pair count included."""
+    s = wb.mid_box(seed=2)
+    p = wb.Params(coul=wb.COUL_RF, rlist=1.3)
+    h = nb.nb_sys_create(ctx, p, s.n, s.box)
+    nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
+    rng = np.random.default_rng(123)
+    try:
+        with pytest.raises(nb.NbError) as ei:
+            nb.nb_pairlist_prune(h, 1.1)
+        assert ei.value.status == 8  # NB_ERR_STATE: no list yet
+        nb.nb_grid_put(h, s.xq(), s.type)
+        nb.nb_pairlist_build(h)
+        for bad in (0.9, 1.4):
+            with pytest.raises(nb.NbError) as ei:
+                nb.nb_pairlist_prune(h, bad)
+            assert ei.value.status == 1  # NB_ERR_ARG: outside [rc, rlist]
+        x_new = None
+        for ev in range(20):
+            if ev > 0:
+                s.x = (s.x.astype(np.float64) + rng.normal(0.0, 0.005, size=s.x.shape)).astype(np.float32)
+                x_new = np.ascontiguousarray(s.x)
+            if ev % 5 == 0:
+                if x_new is not None:
+                    nb.nb_forces(h, x_new, None, None, None, 0)  # coordinates of this evaluation
+                nb.nb_pairlist_prune(h, 1.1)
+                info = nb.nb_pairlist_info(h)
+                assert info["n_entries_inner"] < info["n_entries"]
+            if ev in (0, 4, 9, 14, 19):
+                f = np.zeros((s.n, 3), dtype=np.float32)
+                e = np.zeros(2)
+                v = np.zeros(9)
+                nb.nb_forces(h, x_new, f, e, v, nb.NB_F_ENERGY | nb.NB_F_VIRIAL)
+                _check(s, p, f, e, v)
+                assert nb.nb_eval_info(h)["n_pairs"] == oracle.energy_virial(s, p)["npairs"]
+            else:
+                nb.nb_forces(h, x_new, None, None, None, 0)
+        nb.nb_grid_put(h, s.xq(), s.type)
+        nb.nb_pairlist_build(h)  # a new outer list discards the inner one
+        info = nb.nb_pairlist_info(h)
+        assert info["n_entries_inner"] == info["n_entries"]
+    finally:
+        nb.nb_sys_destroy(h)
+
+
 def test_single_molecule_has_no_interactions(ctx):
     s = wb.water_box(1, 3.0, seed=5)
     f, e, v, _ = gpu_eval(ctx, s, wb.params_rf())
