@@ -530,6 +530,98 @@ def _batch_eval(nb, b, flags, timeout_us=60_000_000):
     return False
 
 
+def run_dynamic(args, n_evals: int = 100, r_outer: float = 1.5) -> dict:
+    """24,000-atom box, LJ + RF, 100 evaluations with Gaussian moves (sigma
+    0.005 nm each), energies and virial on every 10th, the same frames two ways:
+    standard: grid put + search + prune at rlist = 1.1 nm every 10 evaluations;
+    dynamic:  grid put + search + prune at r_outer once, then an out-of-place
+              prune to 1.1 nm every 10 evaluations (nb_pairlist_prune).
+    Both give the same interacting pairs (the counts of the energy evaluations
+    are compared)."""
+    import torch
+
+    from paper_1506_00716_gb300 import autotune, nb
+    from paper_1506_00716_gb300 import build as nbbuild
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    nbbuild.build()
+    stream = torch.cuda.Stream(device=dev)
+    s = wb.mid_box(seed=2)
+    rng = np.random.default_rng(7)
+    frames = [s.x.astype(np.float64)]
+    for _ in range(n_evals - 1):
+        frames.append(frames[-1] + rng.normal(0.0, SIGMA, size=s.x.shape))
+    frames = [torch.from_numpy(np.ascontiguousarray(f.astype(np.float32))).to(dev) for f in frames]
+    xq = torch.from_numpy(np.ascontiguousarray(s.xq())).to(dev)
+    ty = torch.from_numpy(np.ascontiguousarray(s.type)).to(dev)
+    f = torch.empty((s.n, 3), dtype=torch.float32, device=dev)
+    e = torch.empty(2, dtype=torch.float64, device=dev)
+    v = torch.empty(9, dtype=torch.float64, device=dev)
+    flags = nb.NB_F_ENERGY | nb.NB_F_VIRIAL
+    out = {}
+    for mode, rl in (("standard", 1.1), ("dynamic", r_outer)):
+        p = wb.Params(coul=wb.COUL_RF, rlist=rl)
+        ctx = nb.nb_ctx_create(0, stream.cuda_stream, 0)
+        autotune.apply(ctx, "rf", s.n, gpu=torch.cuda.get_device_name(dev))
+        h = nb.nb_sys_create(ctx, p, s.n, s.box)
+        nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
+        xq_k = xq.clone()
+
+        def run(count_pairs=False):
+            pairs = []
+            for k in range(n_evals):
+                fl = flags if k % 10 == 9 else 0
+                if mode == "standard" and k % 10 == 0:
+                    xq_k[:, :3] = frames[k]
+                    nb.nb_grid_put(h, xq_k, ty)
+                    nb.nb_pairlist_build(h)
+                    nb.nb_forces(h, None, f, e, v, fl)
+                elif mode == "dynamic" and k == 0:
+                    nb.nb_grid_put(h, xq, ty)
+                    nb.nb_pairlist_build(h)
+                    nb.nb_pairlist_prune(h, 1.1)
+                    nb.nb_forces(h, None, f, e, v, fl)
+                elif mode == "dynamic" and k % 10 == 0:
+                    nb.nb_forces(h, frames[k], f, e, v, fl)
+                    nb.nb_pairlist_prune(h, 1.1)  # for the next evaluations
+                else:
+                    nb.nb_forces(h, frames[k], f, e, v, fl)
+                if count_pairs and fl:
+                    pairs.append(nb.nb_eval_info(h)["n_pairs"])
+            return pairs
+
+        with torch.cuda.stream(stream):
+            pairs = run(count_pairs=True)
+            for _ in range(2):
+                run()
+            stream.synchronize()
+            reps = 5
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                run()
+            b.record(stream)
+            stream.synchronize()
+        ms = a.elapsed_time(b) / reps
+        info = nb.nb_pairlist_info(h)
+        out[mode] = {"ms_per_100_evals": round(ms, 4), "energy_eval_pairs": pairs,
+                     "entries_outer": info["n_entries"], "entries_inner": info["n_entries_inner"]}
+        nb.nb_sys_destroy(h)
+        nb.nb_ctx_destroy(ctx)
+    same = out["standard"]["energy_eval_pairs"] == out["dynamic"]["energy_eval_pairs"]
+    pairs_mean = float(np.mean(out["standard"]["energy_eval_pairs"]))
+    return {"workload": "24,000-atom box, LJ + RF, 100 evaluations, Gaussian moves sigma 0.005 nm, energies "
+                        f"and virial every 10th; standard: rebuild at rlist 1.1 every 10; dynamic: build at "
+                        f"{r_outer} once, prune to 1.1 every 10",
+            "standard": out["standard"], "dynamic": out["dynamic"], "same_interacting_pairs": same,
+            "standard_pairs_per_s": pairs_mean * n_evals / (out["standard"]["ms_per_100_evals"] * 1e-3),
+            "dynamic_pairs_per_s": pairs_mean * n_evals / (out["dynamic"]["ms_per_100_evals"] * 1e-3),
+            "dynamic_over_standard": out["standard"]["ms_per_100_evals"] / out["dynamic"]["ms_per_100_evals"],
+            "timing": "CUDA events around 5 repetitions of the 100 evaluations (no L2 flush)"}
+
+
 def run_ensemble(args) -> dict:
     """64 independent boxes (1,000-32,000 waters, log-uniform), LJ + RF: one
     batched submission (one launch per stage, CUDA graph) against 64 plain
@@ -711,7 +803,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 3M-atom summary object")
-    ap.add_argument("--workload", default="mid", choices=["mid", "large", "ensemble", "serve"])
+    ap.add_argument("--workload", default="mid", choices=["mid", "large", "ensemble", "serve", "dynamic"])
     ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and serving summaries")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -723,6 +815,9 @@ def main():
         return
     if args.workload == "serve" and args.impl == "ours":
         print(json.dumps(run_serve(args)))
+        return
+    if args.workload == "dynamic" and args.impl == "ours":
+        print(json.dumps(run_dynamic(args)))
         return
     if args.impl == "reference":
         out = run_reference(args)
@@ -742,6 +837,7 @@ def main():
         if world == 1 and not args.no_extra:
             out["ensemble"] = run_ensemble(argparse.Namespace(steps=5, warmup=3))
             out["serving"] = run_serve(argparse.Namespace(steps=1, warmup=1))
+            out["dynamic_pruning"] = run_dynamic(argparse.Namespace(steps=1, warmup=1))
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out))
