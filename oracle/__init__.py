@@ -85,11 +85,19 @@ def _i(a):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
 
 
+def _box6(sys):
+    """(ax, by, cz, bx, cx, cy): the box and the off-diagonal components of a
+    triclinic box (zeros for a rectangular one)."""
+    skew = getattr(sys, "skew", None)
+    skew = np.zeros(3) if skew is None else np.asarray(skew, dtype=np.float64)
+    return _d(np.concatenate([np.asarray(sys.box, dtype=np.float64), skew]))
+
+
 def _common(sys, params):
     x, xp = _d(sys.x.astype(np.float64))
     q, qp = _d(sys.q.astype(np.float64))
     t, tp = _i(sys.type)
-    b, bp = _d(sys.box)
+    b, bp = _box6(sys)
     c6, c6p = _d(np.asarray(params.c6, dtype=np.float64))
     c12, c12p = _d(np.asarray(params.c12, dtype=np.float64))
     ei, eip = _i(sys.excl_index)
@@ -138,7 +146,7 @@ def pairs(sys, r_cut: float) -> np.ndarray:
     """Sorted int64 keys i * n + j of all non-excluded pairs i < j with r < r_cut."""
     lib = _load()
     x, xp = _d(sys.x.astype(np.float64))
-    b, bp = _d(sys.box)
+    b, bp = _box6(sys)
     ei, eip = _i(sys.excl_index)
     ea, eap = _i(sys.excl_atoms)
     counts = np.zeros(sys.n, dtype=np.int64)

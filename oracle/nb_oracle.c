@@ -13,7 +13,8 @@
  * known to be zero, so the method reaches the same sum):
  *
  *   for every unordered atom pair (i, j), i < j, that is not excluded:
- *     d   = x_i - x_j, reduced to the minimum image of the rectangular box
+ *     d   = x_i - x_j, reduced to the minimum image of the periodic box
+ *           (rectangular, or triclinic with rows a, b, c; see pair_image)
  *     r^2 = |d|^2;  the pair contributes only if r^2 < rc^2 (strict)
  *     Lennard-Jones  V = c12 / r^12 - c6 / r^6
  *                    F/r = (12 c12 / r^12 - 6 c6 / r^6) / r^2
@@ -64,6 +65,50 @@
 #define OR_MOD_RF_EXCL 4
 
 static double min_image(double d, double L) { return d - L * round(d / L); }
+
+/*
+ * Minimum image of d = x_i - x_j.  box = (ax, by, cz, bx, cx, cy): the rows
+ * a = (ax, 0, 0), b = (bx, by, 0), c = (cx, cy, cz) of the periodic lattice.
+ * A rectangular box (bx = cx = cy = 0) reduces each component; a triclinic
+ * one is reduced by c, b, a in turn and then the shortest of the 27
+ * neighbouring images is taken (brute force).
+ */
+static void pair_image(const double *box, double dx, double dy, double dz, double *ox, double *oy,
+                       double *oz) {
+    const double ax = box[0], by = box[1], cz = box[2], bx = box[3], cx = box[4], cy = box[5];
+    if (bx == 0.0 && cx == 0.0 && cy == 0.0) {
+        *ox = min_image(dx, ax);
+        *oy = min_image(dy, by);
+        *oz = min_image(dz, cz);
+        return;
+    }
+    double k = round(dz / cz);
+    dx -= k * cx;
+    dy -= k * cy;
+    dz -= k * cz;
+    k = round(dy / by);
+    dx -= k * bx;
+    dy -= k * by;
+    dx -= round(dx / ax) * ax;
+    double best = dx * dx + dy * dy + dz * dz, bxo = dx, byo = dy, bzo = dz;
+    for (int i = -1; i <= 1; ++i)
+        for (int j = -1; j <= 1; ++j)
+            for (int l = -1; l <= 1; ++l) {
+                double ex = dx + i * ax + j * bx + l * cx;
+                double ey = dy + j * by + l * cy;
+                double ez = dz + l * cz;
+                double r2 = ex * ex + ey * ey + ez * ez;
+                if (r2 < best) {
+                    best = r2;
+                    bxo = ex;
+                    byo = ey;
+                    bzo = ez;
+                }
+            }
+    *ox = bxo;
+    *oy = byo;
+    *oz = bzo;
+}
 
 static int excluded(int i, int j, const int *ei, const int *ea) {
     if (!ei) return 0;
@@ -164,9 +209,9 @@ int or_energy_virial(int n, const double *x, const double *q, const int *type, c
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : elj, ec, e12, e6, rf_lj, rf_c, vxx, vxy, vxz, vyy, vyz, vzz, np)
     for (int i = 0; i < n; ++i) {
         for (int j = i + 1; j < n; ++j) {
-            double dx = min_image(x[3 * i + 0] - x[3 * j + 0], box[0]);
-            double dy = min_image(x[3 * i + 1] - x[3 * j + 1], box[1]);
-            double dz = min_image(x[3 * i + 2] - x[3 * j + 2], box[2]);
+            double dx, dy, dz;
+            pair_image(box, x[3 * i + 0] - x[3 * j + 0], x[3 * i + 1] - x[3 * j + 1],
+                       x[3 * i + 2] - x[3 * j + 2], &dx, &dy, &dz);
             double r2 = dx * dx + dy * dy + dz * dz;
             if (!(r2 < s.rc2)) continue;
             double fr;
@@ -226,9 +271,9 @@ int or_forces(int n, const double *x, const double *q, const int *type, const do
         double fx = 0, fy = 0, fz = 0;
         for (int j = 0; j < n; ++j) {
             if (j == i) continue;
-            double dx = min_image(x[3 * i + 0] - x[3 * j + 0], box[0]);
-            double dy = min_image(x[3 * i + 1] - x[3 * j + 1], box[1]);
-            double dz = min_image(x[3 * i + 2] - x[3 * j + 2], box[2]);
+            double dx, dy, dz;
+            pair_image(box, x[3 * i + 0] - x[3 * j + 0], x[3 * i + 1] - x[3 * j + 1],
+                       x[3 * i + 2] - x[3 * j + 2], &dx, &dy, &dz);
             double r2 = dx * dx + dy * dy + dz * dz;
             if (!(r2 < s.rc2)) continue;
             double fr;
@@ -267,9 +312,9 @@ long long or_pairs(int n, const double *x, const double *box, double r_cut, cons
         for (int i = 0; i < n; ++i) {
             long long c = 0;
             for (int j = i + 1; j < n; ++j) {
-                double dx = min_image(x[3 * i + 0] - x[3 * j + 0], box[0]);
-                double dy = min_image(x[3 * i + 1] - x[3 * j + 1], box[1]);
-                double dz = min_image(x[3 * i + 2] - x[3 * j + 2], box[2]);
+                double dx, dy, dz;
+                pair_image(box, x[3 * i + 0] - x[3 * j + 0], x[3 * i + 1] - x[3 * j + 1],
+                           x[3 * i + 2] - x[3 * j + 2], &dx, &dy, &dz);
                 if (!(dx * dx + dy * dy + dz * dz < rc2)) continue;
                 if (excluded(i, j, excl_index, excl_atoms)) continue;
                 ++c;
@@ -288,9 +333,9 @@ long long or_pairs(int n, const double *x, const double *box, double r_cut, cons
     for (int i = 0; i < n; ++i) {
         long long w = start[i];
         for (int j = i + 1; j < n; ++j) {
-            double dx = min_image(x[3 * i + 0] - x[3 * j + 0], box[0]);
-            double dy = min_image(x[3 * i + 1] - x[3 * j + 1], box[1]);
-            double dz = min_image(x[3 * i + 2] - x[3 * j + 2], box[2]);
+            double dx, dy, dz;
+            pair_image(box, x[3 * i + 0] - x[3 * j + 0], x[3 * i + 1] - x[3 * j + 1],
+                       x[3 * i + 2] - x[3 * j + 2], &dx, &dy, &dz);
             if (!(dx * dx + dy * dy + dz * dz < rc2)) continue;
             if (excluded(i, j, excl_index, excl_atoms)) continue;
             pairs[2 * w + 0] = i;

@@ -74,6 +74,11 @@ class System:
     excl_atoms: np.ndarray  # int32 [nnz], the excluded partners (both directions)
     n_mol: int
     seed: int
+    # off-diagonal box components (bx, cx, cy) of a triclinic box with rows
+    # a = (ax, 0, 0), b = (bx, by, 0), c = (cx, cy, cz), box = (ax, by, cz);
+    # zero for a rectangular box.  Coordinates then lie in the rectangle
+    # [0, ax) x [0, by) x [0, cz), a unit cell of the same lattice.
+    skew: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(3))
 
     @property
     def n(self) -> int:
@@ -133,6 +138,31 @@ def wrap32(x: np.ndarray, L: float) -> np.ndarray:
     return y
 
 
+def wrap_triclinic32(x: np.ndarray, box: np.ndarray, skew: np.ndarray) -> np.ndarray:
+    """Wrap float64 coordinates into the unit cell [0, ax) x [0, by) x [0, cz) of
+    the lattice a = (ax,0,0), b = (bx,by,0), c = (cx,cy,cz) (z by c first, then
+    y by b, then x by a) and round to float32, keeping every value below its
+    edge."""
+    ax, by, cz = (float(v) for v in box)
+    bx, cx, cy = (float(v) for v in skew)
+    y = np.array(x, dtype=np.float64)
+    k = np.floor(y[:, 2] / cz)
+    y[:, 0] -= k * cx
+    y[:, 1] -= k * cy
+    y[:, 2] -= k * cz
+    j = np.floor(y[:, 1] / by)
+    y[:, 0] -= j * bx
+    y[:, 1] -= j * by
+    y[:, 0] -= np.floor(y[:, 0] / ax) * ax
+    out = y.astype(np.float32)
+    for d, edge in enumerate((ax, by, cz)):
+        e = np.float32(edge)
+        col = out[:, d]
+        col[col >= e] = np.nextafter(e, np.float32(0.0))
+        col[col < 0] = np.float32(0.0)
+    return out
+
+
 def water_box(n_mol: int, L: float | None = None, seed: int = 1) -> System:
     """A jittered-lattice water box of n_mol molecules (recipe in the module doc)."""
     if L is None:
@@ -173,6 +203,54 @@ def water_box(n_mol: int, L: float | None = None, seed: int = 1) -> System:
     box = np.array([L, L, L], dtype=np.float64)
     return System(x=x, q=q, type=typ, box=box, excl_index=excl_index,
                   excl_atoms=excl_atoms, n_mol=n_mol, seed=seed)
+
+
+def _waters_at(o: np.ndarray, rng: np.random.Generator):
+    """Atoms (O, H, H per molecule) of water molecules with O at o [m, 3] in
+    random orientations, and their charges, types and exclusions."""
+    n_mol = o.shape[0]
+    half = math.radians(ANGLE_HOH_DEG) / 2.0
+    local = np.array([[R_OH * math.sin(half), 0.0, R_OH * math.cos(half)],
+                      [-R_OH * math.sin(half), 0.0, R_OH * math.cos(half)]])
+    rot = _random_rotations(rng, n_mol)
+    h = np.einsum("mij,kj->mki", rot, local)
+    pos = np.empty((n_mol, 3, 3))
+    pos[:, 0] = o
+    pos[:, 1] = o + h[:, 0]
+    pos[:, 2] = o + h[:, 1]
+    n = 3 * n_mol
+    q = np.tile(np.array([Q_O, Q_H, Q_H], dtype=np.float32), n_mol)
+    typ = np.tile(np.array([0, 1, 1], dtype=np.int32), n_mol)
+    excl_index = np.arange(0, 2 * n + 1, 2, dtype=np.int32)
+    base = np.repeat(np.arange(n_mol, dtype=np.int32) * 3, 3)
+    within = np.tile(np.array([[1, 2], [0, 2], [0, 1]], dtype=np.int32), (n_mol, 1))
+    excl_atoms = (base[:, None] + within).reshape(-1).astype(np.int32)
+    return pos.reshape(-1, 3), q, typ, excl_index, excl_atoms
+
+
+def rhombic_dodecahedron_box(n_mol: int, seed: int = 1) -> System:
+    """Water in a rhombic dodecahedron (its xy-square form: a = (d, 0, 0),
+    b = (0, d, 0), c = (d/2, d/2, d sqrt(2)/2)) at the standard density, with
+    about n_mol molecules.  O sits on a jittered lattice of n x n x nz sites in
+    the rectangle [0, d) x [0, d) x [0, cz), n even, so that c carries every
+    site onto a site: the lattice continues across every face of the cell."""
+    spacing = (1.0 / DENSITY_MOL) ** (1.0 / 3.0)
+    d = (n_mol / DENSITY_MOL / (math.sqrt(2.0) / 2.0)) ** (1.0 / 3.0)
+    n = max(2, 2 * int(round(d / spacing / 2.0)))
+    d = f32(n * spacing)
+    cz = f32(d * math.sqrt(2.0) / 2.0)
+    nz = max(1, int(round(cz / spacing)))
+    s_xy, s_z = d / n, cz / nz
+    rng = np.random.default_rng(seed)
+    i, j, k = np.meshgrid(np.arange(n), np.arange(n), np.arange(nz), indexing="ij")
+    o = np.stack([(i.ravel() + 0.5) * s_xy, (j.ravel() + 0.5) * s_xy, (k.ravel() + 0.5) * s_z], axis=1)
+    o = o + rng.uniform(-JITTER, JITTER, size=o.shape)
+    pos, q, typ, ei, ea = _waters_at(o, rng)
+    box = np.array([d, d, cz], dtype=np.float64)
+    skew = np.array([0.0, d / 2.0, d / 2.0], dtype=np.float64)
+    x = wrap_triclinic32(pos, box, skew)
+    return System(x=x, q=q, type=typ, box=box, excl_index=ei, excl_atoms=ea, n_mol=o.shape[0], seed=seed,
+                  skew=skew)
 
 
 def perturb(sys: System, rng: np.random.Generator, sigma: float = 0.005) -> np.ndarray:

@@ -395,3 +395,92 @@ def test_pair_count_matches_density_estimate():
     rho = sys.n / float(sys.box[0]) ** 3
     est = sys.n * rho * 4.0 / 3.0 * math.pi / 2.0
     assert abs(n_pairs - est) / est < 0.02
+
+
+# ------------------------------------------------------------ triclinic boxes
+
+def _lattice_images(sys, r_cut, reach=2):
+    """All non-excluded pairs i<j with some image under the lattice rows
+    a = (ax,0,0), b = (bx,by,0), c = (cx,cy,cz) closer than r_cut, by brute
+    force over |i|, |j|, |k| <= reach."""
+    x = sys.x.astype(np.float64)
+    ax, by, cz = sys.box
+    bx, cx, cy = sys.skew
+    a, b, c = np.array([ax, 0, 0]), np.array([bx, by, 0]), np.array([cx, cy, cz])
+    n = sys.n
+    excl = set()
+    for i in range(n):
+        for k in range(sys.excl_index[i], sys.excl_index[i + 1]):
+            j = int(sys.excl_atoms[k])
+            excl.add((min(i, j), max(i, j)))
+    best = np.full((n, n), np.inf)
+    rng = range(-reach, reach + 1)
+    for i in rng:
+        for j in rng:
+            for k in rng:
+                d = x[:, None, :] - x[None, :, :] + i * a + j * b + k * c
+                best = np.minimum(best, (d * d).sum(-1))
+    ii, jj = np.nonzero(np.triu(best < r_cut * r_cut, k=1))
+    keys = [i * n + j for i, j in zip(ii.tolist(), jj.tolist()) if (i, j) not in excl]
+    return np.array(sorted(keys), dtype=np.int64)
+
+
+def test_triclinic_pair_set_matches_lattice_enumeration():
+    sys = wb.rhombic_dodecahedron_box(120, seed=31)
+    assert sys.skew[1] > 0 and sys.skew[2] > 0
+    for r_cut in (1.0, 1.1):
+        assert np.array_equal(oracle.pairs(sys, r_cut), _lattice_images(sys, r_cut))
+
+
+@pytest.mark.parametrize("coul", [wb.COUL_RF, wb.COUL_EWALD])
+def test_rectangular_lattice_in_triclinic_form(coul):
+    """The rectangular lattice written with other rows (b' = a + b,
+    c' = a + b + c) is the same lattice: the triclinic reduction must give
+    the rectangular results."""
+    sys = wb.small_box(seed=32)
+    p = wb.Params(coul=coul)
+    L = float(sys.box[0])
+    ev0, f0 = oracle.energy_virial(sys, p), oracle.forces(sys, p)
+    for skew in ([L, 0.0, 0.0], [0.0, L, L], [L, L, L]):
+        tri = wb.System(**{**sys.__dict__, "skew": np.array(skew)})
+        ev1, f1 = oracle.energy_virial(tri, p), oracle.forces(tri, p)
+        assert ev1["npairs"] == ev0["npairs"]
+        for k in ("e_lj", "e_coul"):
+            assert ev1[k] == pytest.approx(ev0[k], rel=1e-12)
+        assert np.abs(f1 - f0).max() <= 1e-10 * np.abs(f0).max()
+        assert np.abs(ev1["virial"] - ev0["virial"]).max() <= 1e-10 * np.abs(ev0["virial"]).max()
+
+
+@pytest.mark.parametrize("coul", [wb.COUL_RF, wb.COUL_EWALD])
+def test_triclinic_translation_newton_and_gradient(coul):
+    sys = wb.rhombic_dodecahedron_box(600, seed=33)
+    sys.x = sys.x.astype(np.float64)
+    p = wb.Params(coul=coul)
+    ev0, f0, pr0 = oracle.energy_virial(sys, p), oracle.forces(sys, p), oracle.pairs(sys, p.rc)
+    assert np.abs(f0.sum(0)).max() <= 1e-9 * np.abs(f0).sum()
+    # translation (wrapped back into the cell with the lattice rows)
+    moved = wb.System(**{**sys.__dict__})
+    moved.x = wb.wrap_triclinic32(sys.x + np.array([1.37, -0.81, 2.9]), sys.box, sys.skew).astype(np.float64)
+    shifted_back = moved.x - sys.x
+    # the moved coordinates differ from x + t by lattice vectors and float32 rounding
+    assert np.abs(shifted_back).max() > 0
+    ev1 = oracle.energy_virial(moved, p)
+    assert ev1["e_lj"] + ev1["e_coul"] == pytest.approx(ev0["e_lj"] + ev0["e_coul"], rel=1e-5)
+    # forces are minus the energy gradient
+    rng = np.random.default_rng(3)
+    h = 1e-6
+    checked = 0
+    for a in rng.choice(sys.n, size=6, replace=False):
+        for d in range(3):
+            xp, xm = sys.x.copy(), sys.x.copy()
+            xp[a, d] += h
+            xm[a, d] -= h
+            sp = wb.System(**{**sys.__dict__}); sp.x = xp
+            sm = wb.System(**{**sys.__dict__}); sm.x = xm
+            ep, npp = _etot(sp, p)
+            em, nm = _etot(sm, p)
+            if npp != nm:
+                continue
+            assert -(ep - em) / (2 * h) == pytest.approx(f0[a, d], rel=2e-6, abs=2e-4)
+            checked += 1
+    assert checked >= 12
