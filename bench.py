@@ -530,6 +530,76 @@ def _batch_eval(nb, b, flags, timeout_us=60_000_000):
     return False
 
 
+def run_box_shapes(args, n_evals: int = 100) -> dict:
+    """The same loop on a rectangular and a triclinic box of about 24,000 atoms:
+    LJ + RF, 100 evaluations with Gaussian moves (sigma 0.005 nm), grid put +
+    search + prune every 10th, energies and virial every 10th."""
+    import torch
+
+    from paper_1506_00716_gb300 import autotune, nb
+    from paper_1506_00716_gb300 import build as nbbuild
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    nbbuild.build()
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    for name, s in (("rectangular", wb.mid_box(seed=2)), ("rhombic_dodecahedron", wb.rhombic_dodecahedron_box(8000, 6))):
+        rng = np.random.default_rng(8)
+        frames = [s.x.astype(np.float64)]
+        for _ in range(n_evals - 1):
+            frames.append(frames[-1] + rng.normal(0.0, SIGMA, size=s.x.shape))
+        frames = [torch.from_numpy(np.ascontiguousarray(f.astype(np.float32))).to(dev) for f in frames]
+        xq = torch.from_numpy(np.ascontiguousarray(s.xq())).to(dev)
+        ty = torch.from_numpy(np.ascontiguousarray(s.type)).to(dev)
+        f = torch.empty((s.n, 3), dtype=torch.float32, device=dev)
+        e = torch.empty(2, dtype=torch.float64, device=dev)
+        v = torch.empty(9, dtype=torch.float64, device=dev)
+        p = wb.params_rf()
+        ctx = nb.nb_ctx_create(0, stream.cuda_stream, 0)
+        autotune.apply(ctx, "rf", s.n, gpu=torch.cuda.get_device_name(dev))
+        h = nb.nb_sys_create(ctx, p, s.n, s.box, s.skew)
+        nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
+
+        def run(count=False):
+            pairs = 0
+            for k in range(n_evals):
+                fl = nb.NB_F_ENERGY | nb.NB_F_VIRIAL if (count or k % 10 == 9) else 0
+                if k % 10 == 0:
+                    xq[:, :3] = frames[k]
+                    nb.nb_grid_put(h, xq, ty)
+                    nb.nb_pairlist_build(h)
+                    nb.nb_forces(h, None, f, e, v, fl)
+                else:
+                    nb.nb_forces(h, frames[k], f, e, v, fl)
+                if count:
+                    pairs += nb.nb_eval_info(h)["n_pairs"]
+            return pairs
+
+        with torch.cuda.stream(stream):
+            pairs = run(count=True)
+            run()
+            stream.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(5):
+                run()
+            b.record(stream)
+            stream.synchronize()
+        ms = a.elapsed_time(b) / 5
+        info = nb.nb_pairlist_info(h)
+        out[name] = {"atoms": s.n, "box": [round(float(x), 4) for x in s.box],
+                     "skew": [round(float(x), 4) for x in s.skew], "ms_per_100_evals": round(ms, 4),
+                     "pairs_per_s": pairs / (ms * 1e-3), "list_entries": info["n_entries"]}
+        nb.nb_sys_destroy(h)
+        nb.nb_ctx_destroy(ctx)
+    return {"workload": "LJ + RF, 100 evaluations with Gaussian moves (sigma 0.005 nm), list rebuilt every "
+                        "10th, energies and virial every 10th; rectangular 24,000-atom box vs rhombic "
+                        "dodecahedron (xy-square form) of 23,232 atoms", **out,
+            "timing": "CUDA events around 5 repetitions of the 100 evaluations (no L2 flush)"}
+
+
 def run_dynamic(args, n_evals: int = 100, r_outer: float = 1.5) -> dict:
     """24,000-atom box, LJ + RF, 100 evaluations with Gaussian moves (sigma
     0.005 nm each), energies and virial on every 10th, the same frames two ways:
@@ -803,7 +873,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 3M-atom summary object")
-    ap.add_argument("--workload", default="mid", choices=["mid", "large", "ensemble", "serve", "dynamic"])
+    ap.add_argument("--workload", default="mid",
+                    choices=["mid", "large", "ensemble", "serve", "dynamic", "shapes"])
     ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and serving summaries")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -818,6 +889,9 @@ def main():
         return
     if args.workload == "dynamic" and args.impl == "ours":
         print(json.dumps(run_dynamic(args)))
+        return
+    if args.workload == "shapes" and args.impl == "ours":
+        print(json.dumps(run_box_shapes(args)))
         return
     if args.impl == "reference":
         out = run_reference(args)
@@ -838,6 +912,7 @@ def main():
             out["ensemble"] = run_ensemble(argparse.Namespace(steps=5, warmup=3))
             out["serving"] = run_serve(argparse.Namespace(steps=1, warmup=1))
             out["dynamic_pruning"] = run_dynamic(argparse.Namespace(steps=1, warmup=1))
+            out["box_shapes"] = run_box_shapes(argparse.Namespace(steps=1, warmup=1))
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out))

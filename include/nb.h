@@ -197,6 +197,18 @@ nb_status nb_sys_footprint(const nb_params *params, int natoms, const double box
  */
 nb_status nb_sys_create(nb_ctx *ctx, const nb_params *params, int natoms, const double box[3],
                         nb_sys **out);
+/*
+ * The same for a triclinic box.  box[9] holds the rows a = (ax, 0, 0),
+ * b = (bx, by, 0), c = (cx, cy, cz) of the periodic lattice.  Restrictions
+ * (NB_ERR_BOX otherwise): |bx| + |cx| <= ax/2, |cy| <= by/2; rlist <= ax/2,
+ * by/2 and < cz; every lattice vector at least 2 rlist long.  These admit
+ * the rectangular boxes and, among others, the rhombic dodecahedron in its
+ * xy-square form (a = (d,0,0), b = (0,d,0), c = (d/2, d/2, d sqrt(2)/2)).
+ * Coordinates are wrapped into the cell [0, ax) x [0, by) x [0, cz) (z by
+ * c, then y by b, then x by a); pairs interact through their minimum image.
+ */
+nb_status nb_sys_create_box(nb_ctx *ctx, const nb_params *params, int natoms, const double box[9],
+                            nb_sys **out);
 nb_status nb_sys_destroy(nb_sys *sys);
 
 /*

@@ -831,14 +831,9 @@ nb_status nb_sys_footprint(const nb_params* params, int natoms, const double box
     return NB_OK;
 }
 
-nb_status nb_sys_create(nb_ctx* ctx, const nb_params* params, int natoms, const double box[3], nb_sys** out) {
-    if (!ctx || !out) return fail(NB_ERR_ARG, "ctx / out is NULL");
-    *out = nullptr;
-    nb_status s = check_params(params);
-    if (s != NB_OK) return s;
-    if (natoms <= 0) return fail(NB_ERR_ARG, "natoms must be > 0");
-    s = check_box(params, box);
-    if (s != NB_OK) return s;
+static nb_status sys_create(nb_ctx* ctx, const nb_params* params, int natoms, const double box[3],
+                            const double skew[3], nb_sys** out) {
+    nb_status s;
     nb_sys* y = new nb_sys();
     y->ctx = ctx;
     y->p = *params;
@@ -857,7 +852,10 @@ nb_status nb_sys_create(nb_ctx* ctx, const nb_params* params, int natoms, const 
     sys_layout(natoms, y->geo, nt, &y->h, (char*)y->block);
     y->d_lj = sys_lj_ptr(y);
     SysDev& h = y->h;
-    for (int d = 0; d < 3; ++d) h.L[d] = (float)box[d];
+    for (int d = 0; d < 3; ++d) {
+        h.L[d] = (float)box[d];
+        h.T[d] = (float)skew[d];
+    }
     list_radii(params->rlist, box, &h);
     h.cw[0] = y->geo.cw[0];
     h.cw[1] = y->geo.cw[1];
@@ -885,6 +883,52 @@ nb_status nb_sys_create(nb_ctx* ctx, const nb_params* params, int natoms, const 
     }
     *out = y;
     return NB_OK;
+}
+
+nb_status nb_sys_create(nb_ctx* ctx, const nb_params* params, int natoms, const double box[3], nb_sys** out) {
+    if (!ctx || !out) return fail(NB_ERR_ARG, "ctx / out is NULL");
+    *out = nullptr;
+    nb_status s = check_params(params);
+    if (s != NB_OK) return s;
+    if (natoms <= 0) return fail(NB_ERR_ARG, "natoms must be > 0");
+    s = check_box(params, box);
+    if (s != NB_OK) return s;
+    const double zero[3] = {0.0, 0.0, 0.0};
+    return sys_create(ctx, params, natoms, box, zero, out);
+}
+
+nb_status nb_sys_create_box(nb_ctx* ctx, const nb_params* params, int natoms, const double m[9], nb_sys** out) {
+    if (!ctx || !out || !m) return fail(NB_ERR_ARG, "ctx / box / out is NULL");
+    *out = nullptr;
+    nb_status s = check_params(params);
+    if (s != NB_OK) return s;
+    if (natoms <= 0) return fail(NB_ERR_ARG, "natoms must be > 0");
+    // the float32 box the device uses
+    const double ax = (float)m[0], bx = (float)m[3], by = (float)m[4], cx = (float)m[6], cy = (float)m[7],
+                 cz = (float)m[8];
+    for (int k = 0; k < 9; ++k)
+        if (!std::isfinite(m[k])) return fail(NB_ERR_ARG, "box components must be finite");
+    if (m[1] != 0.0 || m[2] != 0.0 || m[5] != 0.0)
+        return fail(NB_ERR_BOX, "box rows must be a = (ax,0,0), b = (bx,by,0), c = (cx,cy,cz)");
+    if (!(ax > 0 && by > 0 && cz > 0)) return fail(NB_ERR_BOX, "ax, by and cz must be positive");
+    if (std::fabs(bx) + std::fabs(cx) > 0.5 * ax * (1.0 + 1e-6) || std::fabs(cy) > 0.5 * by * (1.0 + 1e-6))
+        return fail(NB_ERR_BOX, "box too skewed: need |bx| + |cx| <= ax/2 and |cy| <= by/2");
+    const double rl = params->rlist;
+    if (rl > 0.5 * ax || rl > 0.5 * by || !(rl < cz))
+        return fail(NB_ERR_BOX, "box too small for rlist: need rlist <= ax/2, by/2 and < cz");
+    // a pair inside rlist must have one image only: every lattice vector at
+    // least 2 rlist long
+    double shortest = 1e300;
+    for (int i = -1; i <= 1; ++i)
+        for (int j = -1; j <= 1; ++j)
+            for (int k = -1; k <= 1; ++k) {
+                if (!i && !j && !k) continue;
+                const double vx = i * ax + j * bx + k * cx, vy = j * by + k * cy, vz = k * cz;
+                shortest = std::min(shortest, std::sqrt(vx * vx + vy * vy + vz * vz));
+            }
+    if (shortest < 2.0 * rl) return fail(NB_ERR_BOX, "a lattice vector is shorter than 2 * rlist");
+    const double box[3] = {m[0], m[4], m[8]}, skew[3] = {m[3], m[6], m[7]};
+    return sys_create(ctx, params, natoms, box, skew, out);
 }
 
 nb_status nb_sys_destroy(nb_sys* sys) {

@@ -67,11 +67,27 @@ struct ShiftedI {
     float xh, yh, zh, xl, yl, zl;
 };
 
-__device__ __forceinline__ ShiftedI shift_i(float4 xi, int sh, float Lx, float Ly, float Lz) {
+// x + sum of the terms t_k carried as hi + lo: each addition error-free, the
+// low parts summed (exact when at most one term is nonzero).
+__device__ __forceinline__ void sum3(float x, float t0, float t1, float t2, float& h, float& l) {
+    float e0, e1, e2;
+    two_sum(x, t0, h, e0);
+    two_sum(h, t1, h, e1);
+    two_sum(h, t2, h, e2);
+    l = e0 + (e1 + e2);
+}
+
+// x_i + S for the item's periodic shift S = sx a + sy b + sz c (box rows a =
+// (Lx,0,0), b = (Tbx,Ly,0), c = (Tcx,Tcy,Lz)); every product is exact, so
+// the rectangular case is exact and the triclinic one within a rounding of
+// the low part.
+__device__ __forceinline__ ShiftedI shift_i(float4 xi, int sh, float Lx, float Ly, float Lz, float Tbx,
+                                            float Tcx, float Tcy) {
+    const float sx = (float)(sh / 9 - 1), sy = (float)((sh / 3) % 3 - 1), sz = (float)(sh % 3 - 1);
     ShiftedI s;
-    two_sum(xi.x, (float)(sh / 9 - 1) * Lx, s.xh, s.xl);
-    two_sum(xi.y, (float)((sh / 3) % 3 - 1) * Ly, s.yh, s.yl);
-    two_sum(xi.z, (float)(sh % 3 - 1) * Lz, s.zh, s.zl);
+    sum3(xi.x, sx * Lx, sy * Tbx, sz * Tcx, s.xh, s.xl);
+    sum3(xi.y, sy * Ly, sz * Tcy, 0.f, s.yh, s.yl);
+    two_sum(xi.z, sz * Lz, s.zh, s.zl);
     return s;
 }
 

@@ -316,7 +316,7 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     int cur_sys = -1;
     const float4* xq_s = nullptr;
     const int* type_s = nullptr;
-    float Lx = 0.f, Ly = 0.f, Lz = 0.f;
+    float Lx = 0.f, Ly = 0.f, Lz = 0.f, Tbx = 0.f, Tcx = 0.f, Tcy = 0.f;
     double dec = 0.0, d12 = 0.0, d6 = 0.0;
     long long np = 0;
 
@@ -336,11 +336,14 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             Lx = sys[sid].L[0];
             Ly = sys[sid].L[1];
             Lz = sys[sid].L[2];
+            Tbx = sys[sid].T[0];
+            Tcx = sys[sid].T[1];
+            Tcy = sys[sid].T[2];
         }
         const int ci = item.x, jb = item.y, je = item.z;
         if (jb >= je) continue;
         const float4 xi4 = xq_s[ci * CL + i];
-        const ShiftedI xs = shift_i(xi4, sh, Lx, Ly, Lz);
+        const ShiftedI xs = shift_i(xi4, sh, Lx, Ly, Lz, Tbx, Tcx, Tcy);
         __syncwarp();
         if (g == 0) {
             IRec r;

@@ -38,6 +38,18 @@ __device__ __forceinline__ float wrap1(float x, float L, int& k) {
     return w + 0.0f;      // turns -0 into +0
 }
 
+// Wrap a point into the cell [0, ax) x [0, by) x [0, cz) of the lattice a =
+// (ax,0,0), b = (bx,by,0), c = (cx,cy,cz): z by c first, then y by b, then x
+// by a (for a rectangular box, each coordinate by its own edge).  Returns the
+// multiples with wrapped = x - kx a - ky b - kz c.
+__device__ __forceinline__ void wrap_point(const SysDev& d, float4 v, float& x, float& y, float& z, int& kx,
+                                           int& ky, int& kz) {
+    z = wrap1(v.z, d.L[2], kz);
+    const float fz = (float)kz;
+    y = wrap1(fmaf(-fz, d.T[2], v.y), d.L[1], ky);
+    x = wrap1(fmaf(-(float)ky, d.T[0], fmaf(-fz, d.T[1], v.x)), d.L[0], kx);
+}
+
 __device__ __forceinline__ int pack_wrap(int kx, int ky, int kz) {
     kx = max(-127, min(127, kx));
     ky = max(-127, min(127, ky));
@@ -66,9 +78,8 @@ __global__ void k_bin(const SysDev* __restrict__ sys, const int* __restrict__ at
     int a = t - atom_off[s];
     float4 v = d.xq_in[a];
     int kx, ky, kz;
-    float x = wrap1(v.x, d.L[0], kx);
-    float y = wrap1(v.y, d.L[1], ky);
-    (void)wrap1(v.z, d.L[2], kz);
+    float x, y, z;
+    wrap_point(d, v, x, y, z, kx, ky, kz);
     int cx = max(0, min(d.ncx - 1, (int)(x * d.icw[0])));  // max(): NaN input
     int cy = max(0, min(d.ncy - 1, (int)(y * d.icw[1])));
     int col = cx * d.ncy + cy;
@@ -183,9 +194,8 @@ __global__ void __launch_bounds__(256) k_col_sort(const SysDev* __restrict__ sys
             int a = (int)(keys[k] & 0xffffffffull);
             float4 v = d.xq_in[a];
             int kx, ky, kz;
-            float x = wrap1(v.x, d.L[0], kx);
-            float y = wrap1(v.y, d.L[1], ky);
-            float z = wrap1(v.z, d.L[2], kz);
+            float x, y, z;
+            wrap_point(d, v, x, y, z, kx, ky, kz);
             d.xq_s[slot] = make_float4(x, y, z, v.w);
             d.type_s[slot] = d.type_in[a];
             d.perm[slot] = a;

@@ -37,7 +37,9 @@ enum {
 // the system (nb_sys).  "slot" arrays have clcap * CL elements in the sorted
 // (grid) order; "atom" arrays have natoms elements in the caller's order.
 struct SysDev {
-    float L[3];          // box edges
+    float L[3];          // box: ax, by, cz (the edges of a rectangular box)
+    float T[3];          // off-diagonal components bx, cx, cy of a triclinic box
+                         // (rows a = (ax,0,0), b = (bx,by,0), c = (cx,cy,cz)); 0 otherwise
     float cw[2];         // column widths in x, y
     float icw[2];        // 1 / column width
     int ncx, ncy, ncol;  // grid columns
@@ -180,6 +182,13 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, si
 // Shift index <-> vector.
 __host__ __device__ inline int shift_index(int sx, int sy, int sz) {
     return (sx + 1) * 9 + (sy + 1) * 3 + (sz + 1);
+}
+
+// The lattice vector sx a + sy b + sz c of shift index sh (float32; every
+// product is exact, the sums round only in a triclinic box).
+__device__ __forceinline__ float3 shift_vec(int sh, const float (&L)[3], const float (&T)[3]) {
+    const float sx = (float)(sh / 9 - 1), sy = (float)((sh / 3) % 3 - 1), sz = (float)(sh % 3 - 1);
+    return make_float3(fmaf(sz, T[1], fmaf(sy, T[0], sx * L[0])), fmaf(sz, T[2], sy * L[1]), sz * L[2]);
 }
 
 // Host helpers of nb_api.cu shared with the allocation-free entry point.

@@ -165,7 +165,7 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     const float4* xq_s = nullptr;
     const int* type_s = nullptr;
     float4* f_s = nullptr;
-    float Lx = 0.f, Ly = 0.f, Lz = 0.f;
+    float Lx = 0.f, Ly = 0.f, Lz = 0.f, Tbx = 0.f, Tcx = 0.f, Tcy = 0.f;
 
     for (;;) {
         int it = 0;
@@ -190,12 +190,15 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             Lx = sys[sid].L[0];
             Ly = sys[sid].L[1];
             Lz = sys[sid].L[2];
+            Tbx = sys[sid].T[0];
+            Tcx = sys[sid].T[1];
+            Tcy = sys[sid].T[2];
         }
         const int ci = item.x, jb = item.y, je = item.z;
         if (jb >= je) continue;
         const bool shifted = sh != SHIFT_ZERO;
         const float4 xi4 = xq_s[ci * CL + i];
-        const ShiftedI xs = shift_i(xi4, sh, Lx, Ly, Lz);
+        const ShiftedI xs = shift_i(xi4, sh, Lx, Ly, Lz, Tbx, Tcx, Tcy);
         const float qi = xi4.w * kp.fq;
         const int tirow = type_s[ci * CL + i] * nt;
 
@@ -340,9 +343,10 @@ __global__ void k_prepare(const SysDev* __restrict__ sys, const int* __restrict_
     int ky = (int)(signed char)((wk >> 8) & 0xff);
     int kz = (int)(signed char)((wk >> 16) & 0xff);
     const float* xn = x_ext ? x_ext : d.x_new;
+    // minus the lattice vector the last grid put removed: kx a + ky b + kz c
     float4 v = d.xq_s[slot];
-    v.x = xn[3 * a + 0] - (float)kx * d.L[0];
-    v.y = xn[3 * a + 1] - (float)ky * d.L[1];
+    v.x = xn[3 * a + 0] - (float)kx * d.L[0] - (float)ky * d.T[0] - (float)kz * d.T[1];
+    v.y = xn[3 * a + 1] - (float)ky * d.L[1] - (float)kz * d.T[2];
     v.z = xn[3 * a + 2] - (float)kz * d.L[2];
     d.xq_s[slot] = v;
 }

@@ -176,7 +176,7 @@ __device__ void flush(SearchWarpSmem& sm, int nbuf, int nruns, int ci, int sid, 
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(SEARCH_WARPS * 32)
+__global__ void __launch_bounds__(SEARCH_WARPS * 32, 7)
 k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys, int tot_clcap,
          ListDev list, KParams kp) {
     pdl_wait();
@@ -233,19 +233,28 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
     const bool ex_overflow = sm.n_ex > EXCL_BUF;
 
     int nbuf = 0, nruns = 0;
-    for (int sx = -1; sx <= 1; ++sx) {
-        if (sx == 1 && !(lo_i.x < rl)) continue;
-        if (sx == -1 && !(hi_i.x > d.L[0] - rl)) continue;
+    // images of the i-cluster: S = sx a + sy b + sz c; an image is visited when
+    // its bounding box comes within the list radius of the cell [0, ax) x
+    // [0, by) x [0, cz), which holds every atom (the box restrictions keep all
+    // such images within |s| <= 1)
+    // (z first: the gap of each coordinate is known once its shift terms are)
+    const float rle2 = (rl + eps) * (rl + eps);
+    for (int sz = -1; sz <= 1; ++sz) {
+        const float Sz = sz * d.L[2];
+        const float lz = lo_i.z + Sz, hz = hi_i.z + Sz;
+        const float gz = gap(lz, hz, 0.f, d.L[2]);
+        if (gz * gz >= rle2) continue;
         for (int sy = -1; sy <= 1; ++sy) {
-            if (sy == 1 && !(lo_i.y < rl)) continue;
-            if (sy == -1 && !(hi_i.y > d.L[1] - rl)) continue;
-            for (int sz = -1; sz <= 1; ++sz) {
-                if (sz == 1 && !(lo_i.z < rl)) continue;
-                if (sz == -1 && !(hi_i.z > d.L[2] - rl)) continue;
+            const float Sy = fmaf((float)sz, d.T[2], sy * d.L[1]);
+            const float ly = lo_i.y + Sy, hy = hi_i.y + Sy;
+            const float gy = gap(ly, hy, 0.f, d.L[1]);
+            if (gy * gy + gz * gz >= rle2) continue;
+            for (int sx = -1; sx <= 1; ++sx) {
+                const float Sx = fmaf((float)sz, d.T[1], fmaf((float)sy, d.T[0], sx * d.L[0]));
+                const float lx = lo_i.x + Sx, hx = hi_i.x + Sx;
+                const float gx = gap(lx, hx, 0.f, d.L[0]);
+                if (gx * gx + gy * gy + gz * gz >= rle2) continue;
                 const int shift = shift_index(sx, sy, sz);
-                const float Sx = sx * d.L[0], Sy = sy * d.L[1], Sz = sz * d.L[2];
-                const float lx = lo_i.x + Sx, ly = lo_i.y + Sy, lz = lo_i.z + Sz;
-                const float hx = hi_i.x + Sx, hy = hi_i.y + Sy, hz = hi_i.z + Sz;
                 const int cx0 = max(0, (int)floorf((lx - rl) * d.icw[0]) - 1);
                 const int cx1 = min(d.ncx - 1, (int)floorf((hx + rl) * d.icw[0]) + 1);
                 const int cy0 = max(0, (int)floorf((ly - rl) * d.icw[1]) - 1);
@@ -402,7 +411,8 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
         const SysDev& d = sys[item.w >> 5];
         const float rl2 = inner ? rl2_inner : d.rl2_prune;
         const int sh = item.w & 31;
-        const float Sx = (sh / 9 - 1) * d.L[0], Sy = ((sh / 3) % 3 - 1) * d.L[1], Sz = (sh % 3 - 1) * d.L[2];
+        const float3 S = shift_vec(sh, d.L, d.T);
+        const float Sx = S.x, Sy = S.y, Sz = S.z;
         float3 xi[CL];
 #pragma unroll
         for (int k = 0; k < CL; ++k) {

@@ -26,7 +26,8 @@ STATUS = {0: "NB_OK", 1: "NB_ERR_ARG", 2: "NB_ERR_BOX", 3: "NB_ERR_OOM", 4: "NB_
 
 # the exported functions declared in include/nb.h
 EXPORTS = ["nb_last_error", "nb_ctx_create", "nb_ctx_destroy", "nb_ctx_memory", "nb_sys_footprint",
-           "nb_sys_create", "nb_sys_destroy", "nb_set_exclusions", "nb_grid_put", "nb_pairlist_build",
+           "nb_sys_create", "nb_sys_create_box", "nb_sys_destroy", "nb_set_exclusions", "nb_grid_put",
+           "nb_pairlist_build",
            "nb_pairlist_info", "nb_pairlist_prune", "nb_forces", "nb_pairlist_export", "nb_batch_create",
            "nb_batch_destroy", "nb_sys_set_coords", "nb_batch_submit", "nb_batch_poll",
            "nb_sys_results", "nb_ctx_set_timing", "nb_ctx_set_timing_stages", "nb_ctx_timing", "nb_eval_info",
@@ -95,6 +96,8 @@ def load(path: str | None = None):
                               ctypes.POINTER(ctypes.c_size_t)], _st),
         "nb_sys_create": ([_vp, ctypes.POINTER(nb_params), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(_vp)], _st),
+        "nb_sys_create_box": ([_vp, ctypes.POINTER(nb_params), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(_vp)], _st),
         "nb_sys_destroy": ([_vp], _st),
         "nb_set_exclusions": ([_vp, _vp, _vp], _st),
         "nb_grid_put": ([_vp, _vp, _vp], _st),
@@ -199,11 +202,19 @@ def nb_sys_footprint(params, natoms: int, box) -> int:
     return out.value
 
 
-def nb_sys_create(ctx, params, natoms: int, box) -> int:
+def nb_sys_create(ctx, params, natoms: int, box, skew=None) -> int:
+    """A system in a rectangular box (box = edges), or in a triclinic one when
+    skew = (bx, cx, cy) is given and nonzero (box = (ax, by, cz))."""
     ps, keep = make_params(params)
-    b = (ctypes.c_double * 3)(*[float(v) for v in box])
     out = _vp()
-    check(load().nb_sys_create(ctx, ctypes.byref(ps), natoms, b, ctypes.byref(out)))
+    if skew is not None and any(float(v) != 0.0 for v in skew):
+        ax, by, cz = (float(v) for v in box)
+        bx, cx, cy = (float(v) for v in skew)
+        m = (ctypes.c_double * 9)(ax, 0.0, 0.0, bx, by, 0.0, cx, cy, cz)
+        check(load().nb_sys_create_box(ctx, ctypes.byref(ps), natoms, m, ctypes.byref(out)))
+    else:
+        b = (ctypes.c_double * 3)(*[float(v) for v in box])
+        check(load().nb_sys_create(ctx, ctypes.byref(ps), natoms, b, ctypes.byref(out)))
     del keep
     return out.value
 

@@ -11,7 +11,7 @@ from paper_1506_00716_gb300 import nb
 
 def gpu_eval(ctx, sys, params, flags=nb.NB_F_ENERGY | nb.NB_F_VIRIAL, keep=False):
     """Grid put, list build and one evaluation; returns (f, energy, virial, handle-or-None)."""
-    h = nb.nb_sys_create(ctx, params, sys.n, sys.box)
+    h = nb.nb_sys_create(ctx, params, sys.n, sys.box, getattr(sys, "skew", None))
     nb.nb_set_exclusions(h, sys.excl_index, sys.excl_atoms)
     nb.nb_grid_put(h, np.ascontiguousarray(sys.xq()), np.ascontiguousarray(sys.type))
     nb.nb_pairlist_build(h)
@@ -65,7 +65,9 @@ def expand_pairs(sys, perm, items, cj, mask, r_cut, chunk=20000):
         b = perm[cj[e[er]] * 8 + j]
         ok = (a >= 0) & (b >= 0)
         a, b, sh = a[ok], b[ok], sh[ok]
-        S = np.stack([sh // 9 - 1, (sh // 3) % 3 - 1, sh % 3 - 1], axis=1) * L
+        sx, sy, sz = sh // 9 - 1, (sh // 3) % 3 - 1, sh % 3 - 1
+        bx, cx, cy = getattr(sys, "skew", np.zeros(3))
+        S = np.stack([sx * L[0] + sy * bx + sz * cx, sy * L[1] + sz * cy, sz * L[2]], axis=1)
         d = x[a] + S - x[b]
         r2 = (d * d).sum(1)
         w = r2 < r_cut * r_cut

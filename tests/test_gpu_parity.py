@@ -38,10 +38,12 @@ def ctx():
 BOXES = {
     "small": lambda: wb.small_box(seed=1),
     "mid": lambda: wb.mid_box(seed=2),
+    # triclinic: a rhombic dodecahedron of 700 waters (d = 3.11 nm)
+    "rd_small": lambda: wb.rhombic_dodecahedron_box(648, seed=5),
 }
 
 
-@pytest.mark.parametrize("name", ["small", "mid"])
+@pytest.mark.parametrize("name", ["small", "mid", "rd_small"])
 def test_pairlist_covers_oracle_pairs_exactly(ctx, name):
     s = BOXES[name]()
     p = wb.params_rf()
@@ -78,7 +80,7 @@ def _check(s, p, f, e, v, f_tol=F_TOL, e_tol=E_TOL, v_tol=V_TOL):
     return errs
 
 
-@pytest.mark.parametrize("name", ["small", "mid"])
+@pytest.mark.parametrize("name", ["small", "mid", "rd_small"])
 @pytest.mark.parametrize("coul", [wb.COUL_RF, wb.COUL_EWALD])
 def test_forces_energies_virial(ctx, name, coul):
     s = BOXES[name]()
@@ -186,6 +188,52 @@ def test_dynamic_pruning(ctx):
         assert info["n_entries_inner"] == info["n_entries"]
     finally:
         nb.nb_sys_destroy(h)
+
+
+def test_triclinic_mid_box_sampled_forces_and_stale_moves(ctx):
+    """Rhombic dodecahedron of 7,744 waters (23,232 atoms), LJ + RF: forces of
+    sampled atoms against the oracle's per-atom loop, before and after moves
+    that carry atoms across the skewed faces (coordinates not re-wrapped), and
+    the net force."""
+    s = wb.rhombic_dodecahedron_box(8000, seed=6)
+    p = wb.params_rf()
+    h = nb.nb_sys_create(ctx, p, s.n, s.box, s.skew)
+    nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
+    rng = np.random.default_rng(61)
+    sel = np.sort(rng.choice(s.n, size=256, replace=False)).astype(np.int32)
+    try:
+        nb.nb_grid_put(h, s.xq(), s.type)
+        nb.nb_pairlist_build(h)
+        x_new = None
+        for ev in range(6):
+            if ev > 0:
+                s.x = (s.x.astype(np.float64) + rng.normal(0.0, 0.01, size=s.x.shape)).astype(np.float32)
+                x_new = np.ascontiguousarray(s.x)
+            f = np.zeros((s.n, 3), dtype=np.float32)
+            nb.nb_forces(h, x_new, f, None, None, 0)
+            if ev in (0, 5):
+                assert rel_rms(f[sel], oracle.forces(s, p, sel)) <= F_TOL
+                rms = np.sqrt((f.astype(np.float64) ** 2).mean())
+                assert np.linalg.norm(f.astype(np.float64).sum(0)) <= 1e-4 * np.sqrt(s.n) * rms
+    finally:
+        nb.nb_sys_destroy(h)
+
+
+def test_triclinic_box_validation(ctx):
+    p = wb.params_rf()
+    d = 3.2
+    rd = [d, 0, 0, 0, d, 0, d / 2, d / 2, d * 0.70710678]
+    box3, skew = (rd[0], rd[4], rd[8]), (rd[3], rd[6], rd[7])
+    h = nb.nb_sys_create(ctx, p, 100, box3, skew)  # a rhombic dodecahedron is admitted
+    nb.nb_sys_destroy(h)
+    bad = [((d, d, 3.0), (d * 0.3, d * 0.3, 0.0)),   # |bx| + |cx| > ax/2
+           ((d, d, 3.0), (0.0, 0.0, d * 0.6)),       # |cy| > by/2
+           ((2.0, d, 3.0), (0.0, 0.5, 0.0)),         # rlist > ax/2
+           ((d, d, 1.05), (0.0, 0.2, 0.2))]          # rlist >= cz
+    for box, sk in bad:
+        with pytest.raises(nb.NbError) as ei:
+            nb.nb_sys_create(ctx, p, 100, box, sk)
+        assert ei.value.status == 2  # NB_ERR_BOX
 
 
 def test_single_molecule_has_no_interactions(ctx):
