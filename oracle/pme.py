@@ -1,0 +1,206 @@
+"""Long-range (reciprocal-space) Ewald electrostatics for the oracle.
+
+TEST INFRASTRUCTURE ONLY: the tests are the only callers.  The CUDA library
+neither imports nor calls anything here, and nothing here is shared with it.
+
+The paper runs the long-range part of the electrostatics with particle-mesh
+Ewald (PME) next to the short-range pair kernel (the multi-level parallelism
+figure and the long-range discussion of the introduction) without stating its
+equations.  The reading taken here is the smooth PME of the standard
+literature, for a rectangular box of edges L and Gaussian splitting
+parameter beta (the same beta as the real-space erfc term):
+
+  reciprocal energy (exact Ewald sum, `ewald_reciprocal_direct`):
+    E_rec = f / (2 pi V) sum_{m != 0} exp(-pi^2 m^2 / beta^2) / m^2 |S(m)|^2,
+    S(m) = sum_j q_j exp(2 pi i m . r_j),  m = (k1/L1, k2/L2, k3/L3);
+  PME (`pme`): the structure factor from charges spread on a K1 x K2 x K3
+    grid with cardinal B-splines M_p of order p,
+      Q(n) = sum_j q_j prod_d M_p(u_jd - n_d),  u_jd = K_d x_jd / L_d (periodic),
+    E_rec ~ 1/2 sum_m B(m) C(m) |DFT(Q)(m)|^2 with C(m) the summand above
+    without |S|^2 (C(0) = 0) and B(m) = prod_d |b_d(m_d)|^2 the B-spline
+    moduli, |b(k)|^-2 = |sum_{j=0}^{p-2} M_p(j + 1) exp(2 pi i k j / K)|^2;
+    forces F_j = -dE_rec/dr_j through the splines' derivatives;
+  self energy   E_self = -f beta / sqrt(pi) sum_j q_j^2;
+  excluded pairs (inside a molecule; the reciprocal sum includes them):
+    E_excl = -f sum_{excluded i<j} q_i q_j erf(beta r) / r, with its forces;
+  virial (Xi = -1/2 sum r (x) F convention of the short-range part):
+    Xi_rec = -1/2 sum_m E_m (delta - 2 (1 + pi^2 m^2 / beta^2) m m / m^2),
+    E_m the energy of wave vector m.
+
+Everything is float64; the DFT is numpy's (a library primitive).  Pins in
+tests/test_pme_oracle.py: the Madelung constant of rock salt (real space +
+exact reciprocal sum + self term), two molecules far from their images
+against plain Coulomb (which needs the excluded-pair term), the homogeneity
+identity trace(virial) = -E/2 of the full Ewald sum, every virial component
+against the energy of a deformed (sheared) box, convergence of PME to the
+exact sum as the grid refines and the order rises, PME forces and virial
+against finite differences of the PME energy, and B-spline identities.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def _wrap_positions(sys) -> np.ndarray:
+    x = sys.x.astype(np.float64)
+    L = np.asarray(sys.box, dtype=np.float64)
+    return x - np.floor(x / L) * L
+
+
+def bspline(x: np.ndarray, p: int) -> np.ndarray:
+    """Cardinal B-spline M_p(x) (support (0, p)) by the recursion
+    M_n(x) = x/(n-1) M_{n-1}(x) + (n-x)/(n-1) M_{n-1}(x-1), M_2(x) = 1 - |x - 1|."""
+    x = np.asarray(x, dtype=np.float64)
+    if p == 2:
+        return np.where((x >= 0) & (x <= 2), 1.0 - np.abs(x - 1.0), 0.0)
+    return x / (p - 1) * bspline(x, p - 1) + (p - x) / (p - 1) * bspline(x - 1.0, p - 1)
+
+
+def bspline_deriv(x: np.ndarray, p: int) -> np.ndarray:
+    """dM_p/dx = M_{p-1}(x) - M_{p-1}(x - 1)."""
+    return bspline(x, p - 1) - bspline(np.asarray(x) - 1.0, p - 1)
+
+
+def bspline_moduli(K: int, p: int) -> np.ndarray:
+    """|b(k)|^2 for k = 0..K-1."""
+    j = np.arange(p - 1)
+    w = bspline(j + 1.0, p)
+    k = np.arange(K)[:, None]
+    den = (w[None, :] * np.exp(2j * np.pi * k * j[None, :] / K)).sum(1)
+    return 1.0 / np.abs(den) ** 2
+
+
+def _freq(K: int, L: float) -> np.ndarray:
+    """Wave numbers m = k'/L with k' the signed frequency of index k."""
+    k = np.arange(K)
+    return np.where(k <= K // 2, k, k - K) / L
+
+
+def pme(sys, params, grid=(32, 32, 32), order: int = 4) -> dict:
+    """Reciprocal energy, forces [n, 3] and virial (3x3) by smooth PME."""
+    x = _wrap_positions(sys)
+    q = sys.q.astype(np.float64)
+    L = np.asarray(sys.box, dtype=np.float64)
+    K = np.asarray(grid, dtype=np.int64)
+    f = params.fcoul / params.eps_r
+    beta = params.beta
+    p = order
+    n = x.shape[0]
+    u = x * (K / L)                        # fractional grid coordinates
+    base = np.floor(u).astype(np.int64)
+    frac = u - base
+    j = np.arange(p)
+    # grid point base - j carries weight M_p(frac + j)
+    w = np.stack([bspline(frac[:, d, None] + j[None, :], p) for d in range(3)], axis=1)      # [n, 3, p]
+    dw = np.stack([bspline_deriv(frac[:, d, None] + j[None, :], p) for d in range(3)], axis=1)
+    idx = np.stack([np.mod(base[:, d, None] - j[None, :], K[d]) for d in range(3)], axis=1)  # [n, 3, p]
+    Q = np.zeros(tuple(K))
+    for a in range(p):
+        for b in range(p):
+            for c in range(p):
+                np.add.at(Q, (idx[:, 0, a], idx[:, 1, b], idx[:, 2, c]), q * w[:, 0, a] * w[:, 1, b] * w[:, 2, c])
+    F = np.fft.fftn(Q)
+    mx, my, mz = np.meshgrid(_freq(K[0], L[0]), _freq(K[1], L[1]), _freq(K[2], L[2]), indexing="ij")
+    m2 = mx * mx + my * my + mz * mz
+    V = float(np.prod(L))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        C = np.where(m2 > 0, f * np.exp(-np.pi ** 2 * m2 / beta ** 2) / (np.pi * V * m2), 0.0)
+    B = (bspline_moduli(K[0], p)[:, None, None] * bspline_moduli(K[1], p)[None, :, None]
+         * bspline_moduli(K[2], p)[None, None, :])
+    G = B * C
+    Em = 0.5 * G * np.abs(F) ** 2
+    energy = float(Em.sum())
+    with np.errstate(divide="ignore", invalid="ignore"):
+        s = np.where(m2 > 0, 2.0 * (1.0 + np.pi ** 2 * m2 / beta ** 2) / m2, 0.0)
+    mv = (mx, my, mz)
+    W = np.zeros((3, 3))
+    for a in range(3):
+        for b in range(3):
+            W[a, b] = float((Em * ((1.0 if a == b else 0.0) - s * mv[a] * mv[b])).sum())
+    virial = -0.5 * W
+    phi = np.prod(K) * np.real(np.fft.ifftn(G * F))   # dE/dQ(n)
+    forces = np.zeros((n, 3))
+    scale = K / L
+    for a in range(p):
+        for b in range(p):
+            for c in range(p):
+                ph = phi[idx[:, 0, a], idx[:, 1, b], idx[:, 2, c]]
+                forces[:, 0] -= q * ph * dw[:, 0, a] * w[:, 1, b] * w[:, 2, c] * scale[0]
+                forces[:, 1] -= q * ph * w[:, 0, a] * dw[:, 1, b] * w[:, 2, c] * scale[1]
+                forces[:, 2] -= q * ph * w[:, 0, a] * w[:, 1, b] * dw[:, 2, c] * scale[2]
+    return {"energy": energy, "forces": forces, "virial": virial}
+
+
+def ewald_reciprocal_direct(sys, params, kmax: int) -> dict:
+    """The exact Ewald reciprocal sum over |k_d| <= kmax (m = k / L)."""
+    x = _wrap_positions(sys)
+    q = sys.q.astype(np.float64)
+    L = np.asarray(sys.box, dtype=np.float64)
+    f = params.fcoul / params.eps_r
+    beta = params.beta
+    V = float(np.prod(L))
+    k = np.arange(-kmax, kmax + 1)
+    kx, ky, kz = np.meshgrid(k, k, k, indexing="ij")
+    keep = (kx != 0) | (ky != 0) | (kz != 0)
+    m = np.stack([kx[keep] / L[0], ky[keep] / L[1], kz[keep] / L[2]], axis=1)   # [M, 3]
+    m2 = (m * m).sum(1)
+    c = f * np.exp(-np.pi ** 2 * m2 / beta ** 2) / (np.pi * V * m2)           # [M]
+    energy = 0.0
+    forces = np.zeros_like(x)
+    W = np.zeros((3, 3))
+    s = 2.0 * (1.0 + np.pi ** 2 * m2 / beta ** 2) / m2
+    for lo in range(0, m.shape[0], 512):
+        mm = m[lo:lo + 512]
+        arg = 2.0 * np.pi * (x @ mm.T)                                       # [n, b]
+        cs, sn = np.cos(arg), np.sin(arg)
+        Sr, Si = q @ cs, q @ sn                                              # [b]
+        cc = c[lo:lo + 512]
+        Em = 0.5 * cc * (Sr * Sr + Si * Si)
+        energy += float(Em.sum())
+        # dE/dr_j = sum_m c q_j 2 pi m (-sin Sr + cos Si)
+        g = q[:, None] * (-sn * Sr[None, :] + cs * Si[None, :]) * (2.0 * np.pi) * cc[None, :]
+        forces -= g @ mm
+        ss = s[lo:lo + 512]
+        for a in range(3):
+            for b in range(3):
+                W[a, b] += float((Em * ((1.0 if a == b else 0.0) - ss * mm[:, a] * mm[:, b])).sum())
+    return {"energy": energy, "forces": forces, "virial": -0.5 * W}
+
+
+def ewald_self(sys, params) -> float:
+    """-f beta / sqrt(pi) sum q^2."""
+    q = sys.q.astype(np.float64)
+    return float(-params.fcoul / params.eps_r * params.beta / math.sqrt(math.pi) * (q * q).sum())
+
+
+def ewald_exclusions(sys, params) -> dict:
+    """Energy, forces and virial of -f q_i q_j erf(beta r) / r over the excluded
+    pairs (each unordered pair once; minimum image of the rectangular box)."""
+    x = sys.x.astype(np.float64)
+    q = sys.q.astype(np.float64)
+    L = np.asarray(sys.box, dtype=np.float64)
+    f = params.fcoul / params.eps_r
+    beta = params.beta
+    energy = 0.0
+    forces = np.zeros_like(x)
+    virial = np.zeros((3, 3))
+    for i in range(sys.n):
+        for k in range(sys.excl_index[i], sys.excl_index[i + 1]):
+            j = int(sys.excl_atoms[k])
+            if j <= i:
+                continue
+            d = x[i] - x[j]
+            d -= L * np.round(d / L)
+            r = float(np.sqrt(d @ d))
+            qq = f * q[i] * q[j]
+            energy -= qq * math.erf(beta * r) / r
+            # V = -qq erf(br)/r; dV/dr = -qq (2b/sqrt(pi) exp(-b^2 r^2) / r - erf(br)/r^2)
+            dvdr = -qq * (2.0 * beta / math.sqrt(math.pi) * math.exp(-beta * beta * r * r) / r
+                          - math.erf(beta * r) / (r * r))
+            fi = -dvdr * d / r
+            forces[i] += fi
+            forces[j] -= fi
+            virial -= 0.5 * np.outer(d, fi)
+    return {"energy": energy, "forces": forces, "virial": virial}
