@@ -78,8 +78,14 @@ def _freq(K: int, L: float) -> np.ndarray:
     return np.where(k <= K // 2, k, k - K) / L
 
 
-def pme(sys, params, grid=(32, 32, 32), order: int = 4) -> dict:
-    """Reciprocal energy, forces [n, 3] and virial (3x3) by smooth PME."""
+def pme(sys, params, grid=(32, 32, 32), order: int = 4, sel=None) -> dict:
+    """Reciprocal energy, forces [n, 3] (of the atoms sel only, if given) and
+    virial (3x3) by smooth PME.
+
+    Even orders only: for odd p the modulus sum vanishes at k = K/2 (even K),
+    where |b|^2 has a pole."""
+    if order % 2:
+        raise ValueError("PME order must be even")
     x = _wrap_positions(sys)
     q = sys.q.astype(np.float64)
     L = np.asarray(sys.box, dtype=np.float64)
@@ -87,7 +93,6 @@ def pme(sys, params, grid=(32, 32, 32), order: int = 4) -> dict:
     f = params.fcoul / params.eps_r
     beta = params.beta
     p = order
-    n = x.shape[0]
     u = x * (K / L)                        # fractional grid coordinates
     base = np.floor(u).astype(np.int64)
     frac = u - base
@@ -96,11 +101,13 @@ def pme(sys, params, grid=(32, 32, 32), order: int = 4) -> dict:
     w = np.stack([bspline(frac[:, d, None] + j[None, :], p) for d in range(3)], axis=1)      # [n, 3, p]
     dw = np.stack([bspline_deriv(frac[:, d, None] + j[None, :], p) for d in range(3)], axis=1)
     idx = np.stack([np.mod(base[:, d, None] - j[None, :], K[d]) for d in range(3)], axis=1)  # [n, 3, p]
-    Q = np.zeros(tuple(K))
+    Q = np.zeros(int(np.prod(K)))
     for a in range(p):
         for b in range(p):
             for c in range(p):
-                np.add.at(Q, (idx[:, 0, a], idx[:, 1, b], idx[:, 2, c]), q * w[:, 0, a] * w[:, 1, b] * w[:, 2, c])
+                flat = (idx[:, 0, a] * K[1] + idx[:, 1, b]) * K[2] + idx[:, 2, c]
+                Q += np.bincount(flat, weights=q * w[:, 0, a] * w[:, 1, b] * w[:, 2, c], minlength=Q.size)
+    Q = Q.reshape(tuple(K))
     F = np.fft.fftn(Q)
     mx, my, mz = np.meshgrid(_freq(K[0], L[0]), _freq(K[1], L[1]), _freq(K[2], L[2]), indexing="ij")
     m2 = mx * mx + my * my + mz * mz
@@ -121,7 +128,10 @@ def pme(sys, params, grid=(32, 32, 32), order: int = 4) -> dict:
             W[a, b] = float((Em * ((1.0 if a == b else 0.0) - s * mv[a] * mv[b])).sum())
     virial = -0.5 * W
     phi = np.prod(K) * np.real(np.fft.ifftn(G * F))   # dE/dQ(n)
-    forces = np.zeros((n, 3))
+    if sel is not None:
+        sel = np.asarray(sel)
+        q, w, dw, idx = q[sel], w[sel], dw[sel], idx[sel]
+    forces = np.zeros((q.shape[0], 3))
     scale = K / L
     for a in range(p):
         for b in range(p):
@@ -183,24 +193,24 @@ def ewald_exclusions(sys, params) -> dict:
     L = np.asarray(sys.box, dtype=np.float64)
     f = params.fcoul / params.eps_r
     beta = params.beta
-    energy = 0.0
+    counts = np.diff(np.asarray(sys.excl_index, dtype=np.int64))
+    i = np.repeat(np.arange(sys.n), counts)
+    j = np.asarray(sys.excl_atoms, dtype=np.int64)[: i.shape[0]]
+    # each unordered pair once, whether the list names it under one atom or both
+    pairs = np.unique(np.stack([np.minimum(i, j), np.maximum(i, j)], axis=1)[i != j], axis=0)
+    i, j = pairs[:, 0], pairs[:, 1]
+    d = x[i] - x[j]
+    d -= L * np.round(d / L)
+    r = np.sqrt((d * d).sum(1))
+    qq = f * q[i] * q[j]
+    erf_br = np.array([math.erf(v) for v in beta * r])
+    energy = float(-(qq * erf_br / r).sum())
+    # V = -qq erf(br)/r; dV/dr = -qq (2b/sqrt(pi) exp(-b^2 r^2) / r - erf(br)/r^2); F_i = -dV/dr d / r
+    dvdr = -qq * (2.0 * beta / math.sqrt(math.pi) * np.exp(-beta * beta * r * r) / r - erf_br / (r * r))
+    fi = -(dvdr / r)[:, None] * d
     forces = np.zeros_like(x)
-    virial = np.zeros((3, 3))
-    for i in range(sys.n):
-        for k in range(sys.excl_index[i], sys.excl_index[i + 1]):
-            j = int(sys.excl_atoms[k])
-            if j <= i:
-                continue
-            d = x[i] - x[j]
-            d -= L * np.round(d / L)
-            r = float(np.sqrt(d @ d))
-            qq = f * q[i] * q[j]
-            energy -= qq * math.erf(beta * r) / r
-            # V = -qq erf(br)/r; dV/dr = -qq (2b/sqrt(pi) exp(-b^2 r^2) / r - erf(br)/r^2)
-            dvdr = -qq * (2.0 * beta / math.sqrt(math.pi) * math.exp(-beta * beta * r * r) / r
-                          - math.erf(beta * r) / (r * r))
-            fi = -dvdr * d / r
-            forces[i] += fi
-            forces[j] -= fi
-            virial -= 0.5 * np.outer(d, fi)
+    for c in range(3):
+        forces[:, c] = np.bincount(i, weights=fi[:, c], minlength=sys.n) - \
+            np.bincount(j, weights=fi[:, c], minlength=sys.n)
+    virial = -0.5 * np.einsum("pa,pb->ab", d, fi)
     return {"energy": energy, "forces": forces, "virial": virial}

@@ -264,7 +264,7 @@ def test_pme_converges_to_exact_reciprocal_sum():
 def test_pme_forces_are_minus_energy_gradient():
     sys = _small_neutral_box(seed=22)
     p = wb.Params(coul=wb.COUL_EWALD, beta=3.12)
-    r = opme.pme(sys, p, grid=(14, 14, 14), order=5)
+    r = opme.pme(sys, p, grid=(14, 14, 14), order=6)
     h = 1e-6
     rng = np.random.default_rng(1)
     for a in rng.choice(sys.n, size=5, replace=False):
@@ -273,7 +273,7 @@ def test_pme_forces_are_minus_energy_gradient():
             for sgn in (+1, -1):
                 s2 = _system(sys.x.copy(), sys.q, sys.box)
                 s2.x[a, d] += sgn * h
-                es.append(opme.pme(s2, p, grid=(14, 14, 14), order=5)["energy"])
+                es.append(opme.pme(s2, p, grid=(14, 14, 14), order=6)["energy"])
             fd = -(es[0] - es[1]) / (2 * h)
             assert fd == pytest.approx(r["forces"][a, d], rel=1e-6, abs=1e-5)
     # the PME virial along each axis against scaling the box and the atoms
@@ -283,7 +283,7 @@ def test_pme_forces_are_minus_energy_gradient():
             scale = np.ones(3)
             scale[a] += sgn * h
             s2 = _system(sys.x * scale, sys.q, sys.box * scale)
-            es.append(opme.pme(s2, p, grid=(14, 14, 14), order=5)["energy"])
+            es.append(opme.pme(s2, p, grid=(14, 14, 14), order=6)["energy"])
         dE = (es[0] - es[1]) / (2 * h)
         # the mesh charges depend on fractional coordinates only, so the PME
         # virial is the exact derivative of the PME energy
