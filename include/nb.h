@@ -63,7 +63,8 @@ enum { NB_COUL_RF = 0, NB_COUL_EWALD = 1 };
 /* Flags of nb_forces, nb_batch_submit. */
 enum {
     NB_F_ENERGY = 1u,  /* compute E_LJ and E_Coulomb */
-    NB_F_VIRIAL = 2u   /* compute the 3x3 virial */
+    NB_F_VIRIAL = 2u,  /* compute the 3x3 virial */
+    NB_F_PME = 4u      /* nb_forces only: add the long-range part (nb_pme_init) */
 };
 
 /*
@@ -136,7 +137,8 @@ enum {
     NB_STAGE_FORCES = 5,  /* the cluster-pair force kernel */
     NB_STAGE_FINAL = 6,   /* unsort + FP64 energy/virial finalisation */
     NB_STAGE_ENERGY = 7,  /* the double-float energy kernel (NB_F_ENERGY) */
-    NB_NSTAGE = 8
+    NB_STAGE_PME = 8,     /* the long-range part: spread, mesh FFT + solve, gather */
+    NB_NSTAGE = 9
 };
 
 /*
@@ -424,6 +426,65 @@ nb_status nb_eval_noalloc(const nb_params *params, int natoms, const double box[
                           const int *excl_index, const int *excl_atoms, const float *xq,
                           const int *type, float *f, double *energy, double *virial,
                           unsigned flags, void *cuda_stream);
+
+/*
+ * Long-range electrostatics by smooth particle-mesh Ewald (the paper runs
+ * PME next to the short-range kernel for the part of the Ewald sum beyond
+ * rc: Sections 1 and 2).  With NB_COUL_EWALD, the short-range kernel
+ * computes the real-space term f qi qj erfc(beta r) / r of non-excluded
+ * pairs inside rc; the long-range part adds
+ *   E_rec   the reciprocal sum, f / (2 pi V) sum_{m != 0} exp(-pi^2 m^2 /
+ *           beta^2) / m^2 |S(m)|^2 with S(m) = sum_j q_j exp(2 pi i m.x_j),
+ *           evaluated by spreading the charges with cardinal B-splines of
+ *           order p onto a K_x x K_y x K_z mesh, a 3D FFT, multiplication by
+ *           the influence function (with the B-spline moduli) and the
+ *           inverse FFT; forces by interpolating the potential mesh with the
+ *           splines' derivatives (they are the exact gradient of this E_rec)
+ *   E_self  -f beta / sqrt(pi) sum_j q_j^2
+ *   E_excl  -f sum over excluded pairs (each once, minimum image, any
+ *           distance) of q_i q_j erf(beta r) / r, with its forces
+ * and the virial of E_rec (Xi_rec = -1/2 sum_m E_m (delta - 2 (1 + pi^2 m^2
+ * / beta^2) m m / m^2)) and of E_excl, all with f = fcoul / eps_r.  The
+ * total electrostatic energy is then the Ewald sum with conducting
+ * boundary conditions.
+ *
+ * nb_pme_init: enable the long-range part for an NB_COUL_EWALD system with
+ * a rectangular box (nb_sys_create), or change its mesh; allocates the mesh
+ * (4 K_x K_y K_z + 8 K_x K_y (K_z / 2 + 1) bytes, counted against the
+ * budget).
+ *   grid[3]  mesh points along x, y, z: each 8..1024, a product of the
+ *            primes 2, 3 and 5 only, with K_d >= 2 p
+ *   order    B-spline order p: 4 (cubic, the usual choice), 6 or 8.  Odd
+ *            orders are not offered: their B-spline modulus has a pole at
+ *            k = K/2 for even K.
+ * NB_ERR_ARG for a bad mesh or order or a non-Ewald system, NB_ERR_BOX for
+ * a triclinic system.
+ */
+typedef struct {
+    int grid[3];
+    int order;
+} nb_pme_params;
+nb_status nb_pme_init(nb_sys *sys, const nb_pme_params *pme);
+
+/*
+ * The long-range part alone, for the coordinates of the last nb_grid_put,
+ * or for x_new (as nb_forces: continuous with the last nb_grid_put).
+ *   f       natoms * 3 floats (host or device), the long-range force on
+ *           each atom in the caller's order (overwritten); NULL allowed
+ *   energy  3 doubles (host or device): E_rec, E_self, E_excl; NULL allowed
+ *   virial  9 doubles (host or device): Xi_rec + Xi_excl; NULL allowed
+ *   flags   NB_F_ENERGY | NB_F_VIRIAL
+ * Needs nb_pme_init and a pair list (nb_pairlist_build: the atoms are taken
+ * in the grid's sorted order).  Mesh, transforms and forces are float32
+ * (fractional mesh coordinates float64); energies, virial and the
+ * excluded-pair terms float64.
+ *
+ * nb_forces with NB_F_PME adds the long-range part to the short-range
+ * result: the forces are the sum, E_Coulomb = real space + E_rec + E_self +
+ * E_excl, the virial the sum.
+ */
+nb_status nb_pme_forces(nb_sys *sys, const float *x_new, float *f, double *energy, double *virial,
+                        unsigned flags);
 
 #ifdef __cplusplus
 }

@@ -590,7 +590,9 @@ nb_status plan_build_list(Plan* pl) {
     return fail(NB_ERR_CAPACITY, "pair list did not fit after growing its buffers");
 }
 
-nb_status plan_eval(Plan* pl, unsigned flags, bool coords, const PlanLaunch* ext) {
+// One evaluation of a plan.  With pme (single-system plans), the long-range
+// part runs after the short-range kernels (flags may carry NB_F_PME).
+nb_status plan_eval(Plan* pl, unsigned flags, bool coords, const PlanLaunch* ext, const PmeHost* pme = nullptr) {
     cudaStream_t st = pl->ctx->stream;
     PlanLaunch p = launch_of(pl);
     if (ext) {
@@ -610,6 +612,10 @@ nb_status plan_eval(Plan* pl, unsigned flags, bool coords, const PlanLaunch* ext
     if (flags & NB_F_ENERGY) {
         StageScope sc(pl->ctx, NB_STAGE_ENERGY);
         NB_CK(launch_energy(p, st));
+    }
+    if (pme && (flags & NB_F_PME)) {
+        StageScope sc(pl->ctx, NB_STAGE_PME);
+        NB_CK(launch_pme(p, pme->dev, pl->systems[0]->h.acc, flags, st));
     }
     {
         StageScope sc(pl->ctx, NB_STAGE_FINAL);
@@ -717,6 +723,50 @@ KParams api_kparams(const nb_params& p, const double box[3], float2* lj) {
 void api_list_estimate(const nb_params& p, int natoms, const double box[3], int clcap, long long* items,
                        long long* entries) {
     list_estimate(p, natoms, box, clcap, 32, items, entries);
+}
+
+// ------------------------------------------------------------- PME (host)
+
+// Stockham stages of a length-n transform: radix 4 while possible, then 2,
+// 3 and 5.  False if n has another prime factor or needs too many stages.
+bool fft_radices(int n, FftAxis* ax) {
+    ax->n = n;
+    ax->nst = 0;
+    const int order[4] = {4, 2, 3, 5};
+    for (int r : order) {
+        while (n % r == 0) {
+            if (ax->nst == FFT_MAX_STAGES) return false;
+            ax->rad[ax->nst++] = r;
+            n /= r;
+        }
+    }
+    return n == 1;
+}
+
+// Cardinal B-spline M_p at the integers 0..p-1 (float64), by the recursion
+// M_k(x) = (x M_{k-1}(x) + (k - x) M_{k-1}(x - 1)) / (k - 1) from M_2.
+std::vector<double> bspline_at_integers(int p) {
+    std::vector<double> m(p, 0.0);
+    m[1] = 1.0;  // M_2(1) = 1, M_2(0) = 0
+    for (int k = 3; k <= p; ++k)
+        for (int j = k - 1; j >= 1; --j) m[j] = (j * m[j] + (k - j) * m[j - 1]) / (k - 1);
+    return m;
+}
+
+// |b(k)|^2 = 1 / |sum_{j=0}^{p-2} M_p(j + 1) exp(2 pi i k j / K)|^2, k = 0..K-1.
+std::vector<double> bspline_moduli(int K, int p) {
+    const std::vector<double> m = bspline_at_integers(p);
+    std::vector<double> out(K);
+    for (int k = 0; k < K; ++k) {
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j <= p - 2; ++j) {
+            const double a = 2.0 * M_PI * (double)k * j / K;
+            re += m[j + 1] * std::cos(a);
+            im += m[j + 1] * std::sin(a);
+        }
+        out[k] = 1.0 / (re * re + im * im);
+    }
+    return out;
 }
 
 }  // namespace nbgb
@@ -935,6 +985,10 @@ nb_status nb_sys_destroy(nb_sys* sys) {
     if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
     nb_ctx* ctx = sys->ctx;
     plan_destroy(sys->plan);
+    if (sys->pme) {
+        dev_free(ctx, sys->pme->block, sys->pme->bytes);
+        delete sys->pme;
+    }
     if (sys->d_excl) dev_free(ctx, sys->d_excl, sys->excl_bytes);
     dev_free(ctx, sys->block, sys->bytes);
     delete sys;
@@ -1067,7 +1121,8 @@ nb_status nb_pairlist_export(nb_sys* sys, int* perm, int* items, int* cj, unsign
 
 nb_status nb_forces(nb_sys* sys, const float* x_new, float* f, double* energy, double* virial, unsigned flags) {
     if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
-    if (flags & ~(unsigned)(NB_F_ENERGY | NB_F_VIRIAL)) return fail(NB_ERR_ARG, "unknown flag bits");
+    if (flags & ~(unsigned)(NB_F_ENERGY | NB_F_VIRIAL | NB_F_PME)) return fail(NB_ERR_ARG, "unknown flag bits");
+    if ((flags & NB_F_PME) && !sys->pme) return fail(NB_ERR_STATE, "NB_F_PME needs nb_pme_init");
     if ((flags & NB_F_ENERGY) && !energy) return fail(NB_ERR_ARG, "NB_F_ENERGY needs energy");
     if ((flags & NB_F_VIRIAL) && !virial) return fail(NB_ERR_ARG, "NB_F_VIRIAL needs virial");
     if (!sys->listed) return fail(NB_ERR_STATE, "nb_forces needs a pair list (nb_pairlist_build)");
@@ -1084,7 +1139,7 @@ nb_status nb_forces(nb_sys* sys, const float* x_new, float* f, double* energy, d
         StageScope sc(sys->ctx, NB_STAGE_COORD);
         NB_CK(cudaMemcpyAsync(sys->h.x_new, x_new, 12 * (size_t)sys->natoms, cudaMemcpyHostToDevice, st));
     }
-    nb_status s = plan_eval(pl, flags, x_new != nullptr, &ext);
+    nb_status s = plan_eval(pl, flags, x_new != nullptr, &ext, sys->pme);
     if (s != NB_OK) return s;
     bool need_sync = false;
     s = copy_out(sys, ext.f_ext ? nullptr : f, ext.e_ext ? nullptr : energy, ext.v_ext ? nullptr : virial,
@@ -1237,6 +1292,137 @@ nb_status nb_batch_poll(nb_batch* batch, unsigned long long ticket, long long ti
         NB_CK(cudaStreamSynchronize(batch->ctx->stream));
         return fail(NB_ERR_CAPACITY, "batch pair list outgrew its buffer; buffers grown, submit again");
     }
+    return NB_OK;
+}
+
+// ---------------------------------------------------------------- PME
+
+nb_status nb_pme_init(nb_sys* sys, const nb_pme_params* pp) {
+    if (!sys || !pp) return fail(NB_ERR_ARG, "sys / pme is NULL");
+    if (sys->p.coul != NB_COUL_EWALD) return fail(NB_ERR_ARG, "the long-range part needs NB_COUL_EWALD");
+    if (sys->h.T[0] != 0.f || sys->h.T[1] != 0.f || sys->h.T[2] != 0.f)
+        return fail(NB_ERR_BOX, "the long-range part supports rectangular boxes only");
+    const int p = pp->order;
+    if (p != 4 && p != 6 && p != 8) return fail(NB_ERR_ARG, "PME order must be 4, 6 or 8");
+    FftAxis ax[3];
+    for (int d = 0; d < 3; ++d) {
+        const int K = pp->grid[d];
+        if (K < 8 || K > 1024 || K < 2 * p || !fft_radices(K, &ax[d]))
+            return fail(NB_ERR_ARG, "each PME mesh size must be in 8..1024, >= 2 * order, with prime factors 2, 3, 5");
+    }
+    if ((size_t)pme_smem_need(pp->grid) > 227 * 1024) return fail(NB_ERR_ARG, "PME mesh too large");
+    const int K0 = pp->grid[0], K1 = pp->grid[1], K2 = pp->grid[2], Kzh = K2 / 2 + 1;
+    // one block: tables, twiddles, spectrum, mesh
+    size_t off = 0;
+    size_t o_tab[3], o_tw[3];
+    for (int d = 0; d < 3; ++d) {
+        o_tab[d] = off;
+        off = align256(off + 8 * (size_t)pp->grid[d]);
+        o_tw[d] = off;
+        off = align256(off + 8 * (size_t)pp->grid[d]);
+    }
+    const size_t o_S = off;
+    off = align256(off + 8 * (size_t)K0 * K1 * Kzh);
+    const size_t o_Q = off;
+    off = align256(off + 4 * (size_t)K0 * K1 * K2);
+    PmeHost* ph = new PmeHost();
+    nb_status s = dev_alloc(sys->ctx, &ph->block, off);
+    if (s != NB_OK) {
+        delete ph;
+        return s;
+    }
+    ph->bytes = off;
+    char* base = (char*)ph->block;
+    PmeDev& pm = ph->dev;
+    const double f = sys->p.fcoul / sys->p.eps_r, beta = sys->p.ewald_beta;
+    const double V = sys->box[0] * sys->box[1] * sys->box[2];
+    std::vector<float2> host(off / 8, make_float2(0.f, 0.f));
+    for (int d = 0; d < 3; ++d) {
+        const int K = pp->grid[d];
+        pm.K[d] = K;
+        pm.kl[d] = K / sys->box[d];
+        pm.ax[d] = ax[d];
+        pm.ax[d].tw = (const float2*)(base + o_tw[d]);
+        pm.tab[d] = (const float2*)(base + o_tab[d]);
+        const std::vector<double> bm = bspline_moduli(K, p);
+        for (int k = 0; k < K; ++k) {
+            const double m = (k <= K / 2 ? k : k - K) / sys->box[d];
+            host[o_tab[d] / 8 + k] = make_float2((float)m, (float)(bm[k] * std::exp(-M_PI * M_PI * m * m / (beta * beta))));
+            const double a = -2.0 * M_PI * (double)k / K;
+            host[o_tw[d] / 8 + k] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    }
+    pm.Kzh = Kzh;
+    pm.order = p;
+    pm.S = (float2*)(base + o_S);
+    pm.Q = (float*)(base + o_Q);
+    pm.cpre = (float)(f / (M_PI * V));
+    pm.pi2_b2 = (float)(M_PI * M_PI / (beta * beta));
+    pm.self_pre = -f * beta / std::sqrt(M_PI);
+    pm.beta = beta;
+    pm.fq = f;
+    cudaStream_t st = sys->ctx->stream;
+    // tables only (the mesh and spectrum are written by every evaluation)
+    cudaError_t e = cudaMemcpyAsync(base, host.data(), o_S, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = pme_prepare_kernels(pm);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        dev_free(sys->ctx, ph->block, ph->bytes);
+        delete ph;
+        return cuda_fail(e, "nb_pme_init");
+    }
+    if (sys->pme) {
+        dev_free(sys->ctx, sys->pme->block, sys->pme->bytes);
+        delete sys->pme;
+    }
+    sys->pme = ph;
+    return NB_OK;
+}
+
+nb_status nb_pme_forces(nb_sys* sys, const float* x_new, float* f, double* energy, double* virial,
+                        unsigned flags) {
+    if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
+    if (flags & ~(unsigned)(NB_F_ENERGY | NB_F_VIRIAL)) return fail(NB_ERR_ARG, "unknown flag bits");
+    if ((flags & NB_F_ENERGY) && !energy) return fail(NB_ERR_ARG, "NB_F_ENERGY needs energy");
+    if ((flags & NB_F_VIRIAL) && !virial) return fail(NB_ERR_ARG, "NB_F_VIRIAL needs virial");
+    if (!sys->pme) return fail(NB_ERR_STATE, "nb_pme_forces needs nb_pme_init");
+    if (!sys->listed) return fail(NB_ERR_STATE, "nb_pme_forces needs a pair list (nb_pairlist_build)");
+    Plan* pl = sys->plan;
+    cudaStream_t st = sys->ctx->stream;
+    PlanLaunch p = launch_of(pl);
+    if (x_new && is_device_ptr(x_new)) p.x_ext = x_new;
+    if (f && is_device_ptr(f)) p.f_ext = f;
+    if (virial && is_device_ptr(virial)) p.v_ext = virial;
+    if (x_new && !p.x_ext) {
+        StageScope sc(sys->ctx, NB_STAGE_COORD);
+        NB_CK(cudaMemcpyAsync(sys->h.x_new, x_new, 12 * (size_t)sys->natoms, cudaMemcpyHostToDevice, st));
+    }
+    {
+        StageScope sc(sys->ctx, NB_STAGE_ZERO);
+        NB_CK(launch_prepare(p, x_new != nullptr, st));
+    }
+    {
+        StageScope sc(sys->ctx, NB_STAGE_PME);
+        NB_CK(launch_pme(p, sys->pme->dev, sys->h.acc, flags, st));
+    }
+    {
+        StageScope sc(sys->ctx, NB_STAGE_FINAL);
+        NB_CK(launch_finalize(p, flags, st));
+    }
+    bool host = false;
+    if (f && !p.f_ext) {
+        NB_CK(cudaMemcpyAsync(f, sys->h.f_out, 12 * (size_t)sys->natoms, cudaMemcpyDefault, st));
+        host = true;
+    }
+    if (energy && (flags & NB_F_ENERGY)) {
+        NB_CK(cudaMemcpyAsync(energy, sys->h.res + 12, 24, cudaMemcpyDefault, st));
+        host = host || !is_device_ptr(energy);
+    }
+    if (virial && (flags & NB_F_VIRIAL) && !p.v_ext) {
+        NB_CK(cudaMemcpyAsync(virial, sys->h.res + 2, 72, cudaMemcpyDefault, st));
+        host = true;
+    }
+    if (host) NB_CK(cudaStreamSynchronize(st));
     return NB_OK;
 }
 

@@ -45,6 +45,14 @@ struct nb_ctx {
     long long launches[NB_NSTAGE] = {0};
 };
 
+// Long-range (PME) state of a system: the device view and the one
+// allocation holding its mesh, spectrum and tables.
+struct PmeHost {
+    nbgb::PmeDev dev{};
+    void* block = nullptr;
+    size_t bytes = 0;
+};
+
 struct nb_sys {
     nb_ctx* ctx = nullptr;
     nb_params p{};
@@ -59,6 +67,7 @@ struct nb_sys {
     size_t excl_bytes = 0;
     float2* d_lj = nullptr;
     Plan* plan = nullptr;    // standalone plan (lazy)
+    PmeHost* pme = nullptr;  // nb_pme_init
     bool has_coords = false;
     bool gridded = false;
     bool listed = false;

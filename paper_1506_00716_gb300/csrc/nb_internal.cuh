@@ -76,10 +76,14 @@ struct SysDev {
     float rl2_prune;     // its square, used by the prune
 };
 
-// Accumulator layout of SysDev::acc.
+// Accumulator layout of SysDev::acc.  The virial slots hold sum (F/r) d (x) d,
+// i.e. -2 Xi; the last three are the long-range (PME) energy parts.
 enum { ACC_E12 = 0, ACC_E6 = 1, ACC_EC = 2, ACC_VXX = 3, ACC_VYY = 4, ACC_VZZ = 5,
-       ACC_VXY = 6, ACC_VXZ = 7, ACC_VYZ = 8, ACC_NPAIR = 9, ACC_ECLO = 10, NACC = 11 };
-constexpr int NRES = 12;  // SysDev::res: E_LJ, E_C, virial[9], interacting pairs
+       ACC_VXY = 6, ACC_VXZ = 7, ACC_VYZ = 8, ACC_NPAIR = 9, ACC_ECLO = 10,
+       ACC_EREC = 11, ACC_ESELF = 12, ACC_EEXCL = 13, NACC = 14 };
+// SysDev::res: E_LJ, E_C (every Coulomb part), virial[9], interacting pairs,
+// then the long-range parts E_rec, E_self, E_excl
+constexpr int NRES = 15;
 
 // Per-plan (one system, or one batch of systems) cluster-pair list.
 struct ListDev {
@@ -130,6 +134,38 @@ struct KParams {
     int force_min_blocks;  // force-kernel launch-bounds variant: 1, 2 or 3
     const float2* lj;    // [ntypes^2] (6 c6, 12 c12), force kernel
     const float2* lje;   // [ntypes^2] (c6, c12), energy kernel
+};
+
+// ---------------------------------------------------- long-range part (PME)
+// One axis of the mesh FFT: a Stockham transform of length n in `nst`
+// stages of radix 2, 3, 4 or 5.
+constexpr int FFT_MAX_STAGES = 16;
+struct FftAxis {
+    int n;
+    int nst;
+    int rad[FFT_MAX_STAGES];
+    const float2* tw;  // [n] exp(-2 pi i j / n), rounded from float64
+};
+
+// Smooth particle-mesh Ewald state of one rectangular system (device
+// pointers owned by the system).  Mesh layout: x slowest, z fastest; the
+// spectrum keeps kz = 0..K[2]/2 of the real-to-complex transform.
+struct PmeDev {
+    int K[3];
+    int Kzh;           // K[2] / 2 + 1
+    int order;         // B-spline order p (4, 6 or 8)
+    double kl[3];      // K_d / L_d: mesh units per nm
+    float* Q;          // [K0 K1 K2] charges spread on the mesh, then the potential
+    float2* S;         // [K0 K1 Kzh] half spectrum
+    FftAxis ax[3];
+    // per mesh index k of axis d: (m_d, |b_d(k)|^2 exp(-pi^2 m_d^2 / beta^2)),
+    // m_d = k' / L_d with k' the signed frequency
+    const float2* tab[3];
+    float cpre;        // f / (pi V)
+    float pi2_b2;      // pi^2 / beta^2
+    double self_pre;   // -f beta / sqrt(pi)
+    double beta;       // splitting parameter (excluded-pair correction)
+    double fq;         // f = fcoul / eps_r
 };
 
 // Host-side view of a plan, used to size launches.
@@ -220,5 +256,15 @@ cudaError_t launch_finalize(const PlanLaunch& p, unsigned flags, cudaStream_t st
 // Reaction-field correction of excluded pairs (NB_MOD_RF_EXCL; nothing
 // otherwise): after the force and energy kernels, before the finalisation.
 cudaError_t launch_excl_corr(const PlanLaunch& p, unsigned flags, cudaStream_t st);
+// Long-range part of a single-system plan (spread, mesh FFT and solve, gather,
+// excluded-pair correction): adds its forces to the sorted force buffer and
+// its energies and virial to the accumulators.  After the force kernels,
+// before the finalisation.
+// acc: the system's accumulators (SysDev::acc).
+cudaError_t launch_pme(const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags, cudaStream_t st);
+// Raise the dynamic shared-memory limit of the mesh-FFT kernels to what the
+// mesh of pm needs; pme_smem_need gives that amount for a mesh K.
+cudaError_t pme_prepare_kernels(const PmeDev& pm);
+size_t pme_smem_need(const int K[3]);
 
 }  // namespace nbgb

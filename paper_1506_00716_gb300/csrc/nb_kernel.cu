@@ -365,7 +365,7 @@ __global__ void k_finish(const SysDev* __restrict__ sys, const int* __restrict__
         const double* a = d.acc;
         double* r = d.res;
         r[0] = a[ACC_E12] - a[ACC_E6];
-        r[1] = a[ACC_EC] + a[ACC_ECLO];
+        r[1] = a[ACC_EC] + a[ACC_ECLO] + (a[ACC_EREC] + a[ACC_ESELF] + a[ACC_EEXCL]);
         r[2] = -0.5 * a[ACC_VXX];
         r[3] = -0.5 * a[ACC_VXY];
         r[4] = -0.5 * a[ACC_VXZ];
@@ -376,6 +376,9 @@ __global__ void k_finish(const SysDev* __restrict__ sys, const int* __restrict__
         r[9] = -0.5 * a[ACC_VYZ];
         r[10] = -0.5 * a[ACC_VZZ];
         r[11] = a[ACC_NPAIR];
+        r[12] = a[ACC_EREC];
+        r[13] = a[ACC_ESELF];
+        r[14] = a[ACC_EEXCL];
         if (e_ext) {
             e_ext[0] = r[0];
             e_ext[1] = r[1];

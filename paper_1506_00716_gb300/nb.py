@@ -19,6 +19,7 @@ NB_COUL_RF = 0
 NB_COUL_EWALD = 1
 NB_F_ENERGY = 1
 NB_F_VIRIAL = 2
+NB_F_PME = 4
 
 STATUS = {0: "NB_OK", 1: "NB_ERR_ARG", 2: "NB_ERR_BOX", 3: "NB_ERR_OOM", 4: "NB_ERR_BUDGET",
           5: "NB_ERR_CUDA", 6: "NB_ERR_NOT_READY", 7: "NB_ERR_TIMEOUT", 8: "NB_ERR_STATE",
@@ -32,12 +33,12 @@ EXPORTS = ["nb_last_error", "nb_ctx_create", "nb_ctx_destroy", "nb_ctx_memory", 
            "nb_batch_destroy", "nb_sys_set_coords", "nb_batch_submit", "nb_batch_poll",
            "nb_sys_results", "nb_ctx_set_timing", "nb_ctx_set_timing_stages", "nb_ctx_timing", "nb_eval_info",
            "nb_eval_noalloc", "nb_ctx_set_tuning", "nb_ctx_get_tuning", "nb_server_create",
-           "nb_server_destroy", "nb_server_submit", "nb_server_wait"]
-NB_NSTAGE = 8
+           "nb_server_destroy", "nb_server_submit", "nb_server_wait", "nb_pme_init", "nb_pme_forces"]
+NB_NSTAGE = 9
 NB_MOD_LJ_SHIFT = 1
 NB_MOD_EWALD_SHIFT = 2
 NB_MOD_RF_EXCL = 4
-STAGES = ["grid", "search", "prune", "coord", "zero", "forces", "final", "energy"]
+STAGES = ["grid", "search", "prune", "coord", "zero", "forces", "final", "energy", "pme"]
 
 
 class NbError(RuntimeError):
@@ -52,6 +53,10 @@ class nb_params(ctypes.Structure):
                 ("ewald_beta", ctypes.c_double), ("fcoul", ctypes.c_double),
                 ("ntypes", ctypes.c_int), ("c6", ctypes.POINTER(ctypes.c_float)),
                 ("c12", ctypes.POINTER(ctypes.c_float)), ("modifiers", ctypes.c_uint)]
+
+
+class nb_pme_params(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int * 3), ("order", ctypes.c_int)]
 
 
 class nb_tuning(ctypes.Structure):
@@ -105,6 +110,8 @@ def load(path: str | None = None):
         "nb_pairlist_info": ([_vp, ctypes.POINTER(nb_list_info)], _st),
         "nb_pairlist_prune": ([_vp, ctypes.c_double], _st),
         "nb_forces": ([_vp, _vp, _vp, _vp, _vp, ctypes.c_uint], _st),
+        "nb_pme_init": ([_vp, ctypes.POINTER(nb_pme_params)], _st),
+        "nb_pme_forces": ([_vp, _vp, _vp, _vp, _vp, ctypes.c_uint], _st),
         "nb_pairlist_export": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong)], _st),
         "nb_batch_create": ([_vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp)], _st),
         "nb_batch_destroy": ([_vp], _st),
@@ -253,6 +260,17 @@ def nb_pairlist_prune(sys, r_inner: float) -> None:
 
 def nb_forces(sys, x_new=None, f=None, energy=None, virial=None, flags: int = 0) -> None:
     check(load().nb_forces(sys, ptr(x_new), ptr(f), ptr(energy), ptr(virial), flags))
+
+
+def nb_pme_init(sys, grid, order: int = 4) -> None:
+    """Enable the long-range (PME) part: grid = (Kx, Ky, Kz), B-spline order."""
+    pp = nb_pme_params((ctypes.c_int * 3)(*[int(k) for k in grid]), int(order))
+    check(load().nb_pme_init(sys, ctypes.byref(pp)))
+
+
+def nb_pme_forces(sys, x_new=None, f=None, energy=None, virial=None, flags: int = 0) -> None:
+    """Long-range part alone: energy = (E_rec, E_self, E_excl)."""
+    check(load().nb_pme_forces(sys, ptr(x_new), ptr(f), ptr(energy), ptr(virial), flags))
 
 
 def nb_pairlist_export(sys, perm=None, items=None, cj=None, mask=None) -> int:

@@ -53,6 +53,8 @@ def test_params_struct_layout_matches_header(tmp_path):
         '  printf("nb_tuning size %zu\\n", sizeof(nb_tuning));\n'
         '  printf("nb_request_stats size %zu\\n", sizeof(nb_request_stats));\n'
         '  printf("nb_list_info size %zu\\n", sizeof(nb_list_info));\n'
+        '  printf("nb_pme_params size %zu\\n", sizeof(nb_pme_params));\n'
+        "  F(nb_pme_params, grid); F(nb_pme_params, order);\n"
         "  return 0;\n}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -64,6 +66,8 @@ def test_params_struct_layout_matches_header(tmp_path):
     assert got["nb_tuning size"] == ctypes.sizeof(nb.nb_tuning)
     assert got["nb_request_stats size"] == ctypes.sizeof(nb.nb_request_stats)
     assert got["nb_list_info size"] == ctypes.sizeof(nb.nb_list_info) == 6 * 8
+    assert got["nb_pme_params size"] == ctypes.sizeof(nb.nb_pme_params) == 16
+    assert got["nb_pme_params order"] == nb.nb_pme_params.order.offset
 
 
 def test_modifiers_are_validated(lib):
