@@ -50,7 +50,7 @@ INST_PER_SLOT = {("rf", False): 26, ("rf", True): 32, ("ewald", False): 43, ("ew
 FLOPS_PER_SLOT = {("rf", False): 30, ("rf", True): 42, ("ewald", False): 56, ("ewald", True): 68}
 # kernels launched per timed stage (nb_ctx_timing)
 KERNELS_PER_STAGE = {"grid": 6, "search": 1, "prune": 1, "coord": 0, "zero": 1, "forces": 1, "final": 1,
-                     "energy": 1}
+                     "energy": 1, "pme_spread": 1, "pme_fft": 5, "pme_gather": 2}
 FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
 
 
@@ -518,6 +518,111 @@ def run_large(args) -> dict:
     }
 
 
+PME_GRID = (256, 256, 256)  # 0.121 nm spacing on the 31 nm box
+PME_ORDER = 4
+
+
+def run_pme(args) -> dict:
+    """Long-range part (smooth PME) on the 3,000,000-atom Ewald box, mesh 256^3
+    (0.121 nm), cubic B-splines: a step is one nb_pme_forces evaluation
+    (mesh clear, spreading, FFT + solve + inverse FFT, gathering, excluded
+    pairs, unsort) on a built list; also the combined short- plus long-range
+    nb_forces(NB_F_PME) evaluation."""
+    import torch
+
+    from paper_1506_00716_gb300 import build as nbbuild
+    from paper_1506_00716_gb300 import nb
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    nbbuild.build()
+    stream = torch.cuda.Stream(device=dev)
+    s = wb.large_box(seed=3)
+    p = wb.params_ewald()
+    ctx = nb.nb_ctx_create(0, stream.cuda_stream, 0)
+    from paper_1506_00716_gb300 import autotune
+
+    autotune.apply(ctx, "ewald", s.n, gpu=torch.cuda.get_device_name(dev))
+    h = nb.nb_sys_create(ctx, p, s.n, s.box)
+    nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
+    nb.nb_pme_init(h, PME_GRID, PME_ORDER)
+    xq = torch.from_numpy(s.xq()).to(dev)
+    ty = torch.from_numpy(s.type).to(dev)
+    f = torch.empty((s.n, 3), dtype=torch.float32, device=dev)
+    e = torch.empty(3, dtype=torch.float64, device=dev)
+    e2 = torch.empty(2, dtype=torch.float64, device=dev)
+    v = torch.empty(9, dtype=torch.float64, device=dev)
+    ev = nb.NB_F_ENERGY | nb.NB_F_VIRIAL
+    with torch.cuda.stream(stream):
+        nb.nb_grid_put(h, xq, ty)
+        nb.nb_pairlist_build(h)
+        for _ in range(args.warmup):
+            nb.nb_pme_forces(h, None, f, None, None, 0)
+        stream.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            t0.record(stream)
+            for _ in range(args.steps):
+                nb.nb_pme_forces(h, None, f, None, None, 0)
+            t1.record(stream)
+            stream.synchronize()
+            wall = t0.elapsed_time(t1) / args.steps
+            nb.nb_pme_forces(h, None, f, e, v, ev)
+            t0.record(stream)
+            for _ in range(args.steps):
+                nb.nb_forces(h, None, f, e2, v, nb.NB_F_PME)
+            t1.record(stream)
+            stream.synchronize()
+            combined = t0.elapsed_time(t1) / args.steps
+            t0.record(stream)
+            for _ in range(args.steps):
+                nb.nb_forces(h, None, f, None, None, 0)
+            t1.record(stream)
+            stream.synchronize()
+            short = t0.elapsed_time(t1) / args.steps
+        # per-stage times: a separate pass with stage events (they cost a little)
+        nb.nb_ctx_timing(ctx, reset=True)
+        nb.nb_ctx_set_timing(ctx, True)
+        for _ in range(args.steps):
+            nb.nb_pme_forces(h, None, f, None, None, 0)
+        stream.synchronize()
+        nb.nb_ctx_set_timing(ctx, False)
+        stage = nb.nb_ctx_timing(ctx, reset=True)
+    energies = e.cpu().tolist()
+    nb.nb_sys_destroy(h)
+    nb.nb_ctx_destroy(ctx)
+    per = {k: stage[k][0] / max(stage[k][1], 1) for k in ("pme_spread", "pme_fft", "pme_gather", "zero", "final")}
+    nmesh = PME_GRID[0] * PME_GRID[1] * PME_GRID[2]
+    nspec = PME_GRID[0] * PME_GRID[1] * (PME_GRID[2] // 2 + 1)
+    # algorithmic bytes of the five FFT passes: z forward reads the real mesh
+    # and writes the half spectrum, y, x (+ solve + inverse) and y each read and
+    # write the spectrum once, z inverse reads it and writes the real mesh
+    fft_bytes = 2 * (4 * nmesh + 8 * nspec) + 3 * (2 * 8 * nspec)
+    peaks, kind = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = fft_bytes / (per["pme_fft"] * 1e-3) / 1e9
+    spread_atomics = s.n * PME_ORDER ** 3
+    return {
+        "metric": "long-range (PME) evaluations/s", "value": 1e3 / wall, "unit": "evals/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "water box, 3,000,000 atoms, L=31.0 nm, smooth PME, mesh 256^3 (0.121 nm), "
+                               "order 4, beta=3.12 nm^-1; step = nb_pme_forces (forces only) on a built list",
+                   "atoms": s.n, "mesh": list(PME_GRID), "order": PME_ORDER},
+        "atoms_per_s": s.n / (wall * 1e-3),
+        "stage_ms": {k: round(v_, 4) for k, v_ in per.items()},
+        "combined_ms": combined, "short_range_ms": short,
+        "energies": {"E_rec": energies[0], "E_self": energies[1], "E_excl": energies[2]},
+        "fft_roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "traffic": None,
+                         "kernels": "k_fft_z_r2c, k_fft_strided x2, k_fft_x_solve, k_fft_z_c2r",
+                         "algorithmic_bytes": fft_bytes, "peak_kind": kind},
+        "spread": {"atomics_per_eval": spread_atomics,
+                   "atomics_per_s": spread_atomics / (per["pme_spread"] * 1e-3)},
+        "clocks": clk.summary(),
+    }
+
+
 def _batch_eval(nb, b, flags, timeout_us=60_000_000):
     """Submit a batch and wait; a list that outgrew its buffer (the library
     grows it and says so) is submitted once more."""
@@ -874,7 +979,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 3M-atom summary object")
     ap.add_argument("--workload", default="mid",
-                    choices=["mid", "large", "ensemble", "serve", "dynamic", "shapes"])
+                    choices=["mid", "large", "ensemble", "serve", "dynamic", "shapes", "pme"])
     ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and serving summaries")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -892,6 +997,9 @@ def main():
         return
     if args.workload == "shapes" and args.impl == "ours":
         print(json.dumps(run_box_shapes(args)))
+        return
+    if args.workload == "pme" and args.impl == "ours":
+        print(json.dumps(run_pme(args)))
         return
     if args.impl == "reference":
         out = run_reference(args)

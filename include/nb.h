@@ -137,8 +137,10 @@ enum {
     NB_STAGE_FORCES = 5,  /* the cluster-pair force kernel */
     NB_STAGE_FINAL = 6,   /* unsort + FP64 energy/virial finalisation */
     NB_STAGE_ENERGY = 7,  /* the double-float energy kernel (NB_F_ENERGY) */
-    NB_STAGE_PME = 8,     /* the long-range part: spread, mesh FFT + solve, gather */
-    NB_NSTAGE = 9
+    NB_STAGE_PME_SPREAD = 8,  /* long-range part: mesh clear + charge spreading */
+    NB_STAGE_PME_FFT = 9,     /* long-range part: forward FFT, solve, inverse FFT */
+    NB_STAGE_PME_GATHER = 10, /* long-range part: force gathering + excluded pairs */
+    NB_NSTAGE = 11
 };
 
 /*

@@ -590,6 +590,24 @@ nb_status plan_build_list(Plan* pl) {
     return fail(NB_ERR_CAPACITY, "pair list did not fit after growing its buffers");
 }
 
+// The long-range launches of one evaluation, each group a timing stage.
+nb_status pme_record(nb_ctx* ctx, const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags,
+                     cudaStream_t st) {
+    {
+        StageScope sc(ctx, NB_STAGE_PME_SPREAD);
+        NB_CK(launch_pme_spread(p, pm, acc, flags, st));
+    }
+    {
+        StageScope sc(ctx, NB_STAGE_PME_FFT);
+        NB_CK(launch_pme_fft(p, pm, acc, flags, st));
+    }
+    {
+        StageScope sc(ctx, NB_STAGE_PME_GATHER);
+        NB_CK(launch_pme_gather(p, pm, acc, flags, st));
+    }
+    return NB_OK;
+}
+
 // One evaluation of a plan.  With pme (single-system plans), the long-range
 // part runs after the short-range kernels (flags may carry NB_F_PME).
 nb_status plan_eval(Plan* pl, unsigned flags, bool coords, const PlanLaunch* ext, const PmeHost* pme = nullptr) {
@@ -614,8 +632,8 @@ nb_status plan_eval(Plan* pl, unsigned flags, bool coords, const PlanLaunch* ext
         NB_CK(launch_energy(p, st));
     }
     if (pme && (flags & NB_F_PME)) {
-        StageScope sc(pl->ctx, NB_STAGE_PME);
-        NB_CK(launch_pme(p, pme->dev, pl->systems[0]->h.acc, flags, st));
+        nb_status s = pme_record(pl->ctx, p, pme->dev, pl->systems[0]->h.acc, flags, st);
+        if (s != NB_OK) return s;
     }
     {
         StageScope sc(pl->ctx, NB_STAGE_FINAL);
@@ -1361,6 +1379,15 @@ nb_status nb_pme_init(nb_sys* sys, const nb_pme_params* pp) {
     pm.self_pre = -f * beta / std::sqrt(M_PI);
     pm.beta = beta;
     pm.fq = f;
+    auto split = [](double v, float& h, float& l) {
+        h = (float)v;
+        l = (float)(v - (double)h);
+    };
+    for (int d = 0; d < 3; ++d) split(pm.kl[d], pm.kl_h[d], pm.kl_l[d]);
+    split(f, pm.fq_h, pm.fq_l);
+    split(2.0 * beta / std::sqrt(M_PI), pm.ke_h, pm.ke_l);
+    split(4.0 / 3.0 * beta * beta * beta / std::sqrt(M_PI), pm.kf_h, pm.kf_l);
+    pm.beta2 = (float)(beta * beta);
     cudaStream_t st = sys->ctx->stream;
     // tables only (the mesh and spectrum are written by every evaluation)
     cudaError_t e = cudaMemcpyAsync(base, host.data(), o_S, cudaMemcpyHostToDevice, st);
@@ -1401,10 +1428,8 @@ nb_status nb_pme_forces(nb_sys* sys, const float* x_new, float* f, double* energ
         StageScope sc(sys->ctx, NB_STAGE_ZERO);
         NB_CK(launch_prepare(p, x_new != nullptr, st));
     }
-    {
-        StageScope sc(sys->ctx, NB_STAGE_PME);
-        NB_CK(launch_pme(p, sys->pme->dev, sys->h.acc, flags, st));
-    }
+    nb_status s = pme_record(sys->ctx, p, sys->pme->dev, sys->h.acc, flags, st);
+    if (s != NB_OK) return s;
     {
         StageScope sc(sys->ctx, NB_STAGE_FINAL);
         NB_CK(launch_finalize(p, flags, st));

@@ -155,6 +155,7 @@ struct PmeDev {
     int Kzh;           // K[2] / 2 + 1
     int order;         // B-spline order p (4, 6 or 8)
     double kl[3];      // K_d / L_d: mesh units per nm
+    float kl_h[3], kl_l[3];  // the same as an unevaluated float sum hi + lo
     float* Q;          // [K0 K1 K2] charges spread on the mesh, then the potential
     float2* S;         // [K0 K1 Kzh] half spectrum
     FftAxis ax[3];
@@ -166,6 +167,9 @@ struct PmeDev {
     double self_pre;   // -f beta / sqrt(pi)
     double beta;       // splitting parameter (excluded-pair correction)
     double fq;         // f = fcoul / eps_r
+    // excluded-pair constants as hi + lo: f, 2 beta / sqrt(pi), 4 beta^3 / (3 sqrt(pi))
+    float fq_h, fq_l, ke_h, ke_l, kf_h, kf_l;
+    float beta2;       // beta^2
 };
 
 // Host-side view of a plan, used to size launches.
@@ -260,8 +264,14 @@ cudaError_t launch_excl_corr(const PlanLaunch& p, unsigned flags, cudaStream_t s
 // excluded-pair correction): adds its forces to the sorted force buffer and
 // its energies and virial to the accumulators.  After the force kernels,
 // before the finalisation.
-// acc: the system's accumulators (SysDev::acc).
-cudaError_t launch_pme(const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags, cudaStream_t st);
+// acc: the system's accumulators (SysDev::acc).  Three launch groups, in
+// this order: mesh clear and spreading; FFT, solve and inverse FFT; gathering
+// and the excluded-pair correction.
+cudaError_t launch_pme_spread(const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags,
+                              cudaStream_t st);
+cudaError_t launch_pme_fft(const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags, cudaStream_t st);
+cudaError_t launch_pme_gather(const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags,
+                              cudaStream_t st);
 // Raise the dynamic shared-memory limit of the mesh-FFT kernels to what the
 // mesh of pm needs; pme_smem_need gives that amount for a mesh K.
 cudaError_t pme_prepare_kernels(const PmeDev& pm);

@@ -103,27 +103,51 @@ __device__ __forceinline__ void dft5(float2* v) {
     v[3] = csub(r2, i2);
 }
 
+// (q, r) = divmod(f, d) while f advances by a fixed stride: one division at
+// the start, then additions only (the index loops below would otherwise
+// spend most of their issue slots on integer division).
+struct DivWalk {
+    int q, r, dq, dr, d;
+    __device__ __forceinline__ DivWalk(int f0, int stride, int d_) : d(d_) {
+        q = f0 / d;
+        r = f0 - q * d;
+        dq = stride / d;
+        dr = stride - dq * d;
+    }
+    __device__ __forceinline__ void next() {
+        q += dq;
+        r += dr;
+        if (r >= d) {
+            r -= d;
+            ++q;
+        }
+    }
+};
+
 // One Stockham stage of radix R over nl lines (line stride ls) from src to dst.
 template <int R, bool INV>
 __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, float2* __restrict__ dst, int ls,
                                                int nl, int n, int ns, const float2* __restrict__ tw) {
     const int m = n / R;
     const int step = n / (ns * R);
+    // idx = line * m + j, k = j mod ns (m is a multiple of ns, so k only moves
+    // with j's own increments)
+    DivWalk w(threadIdx.x, blockDim.x, m);
+    int k = w.r % ns;
+    const int dk = w.dr % ns;
     for (int idx = threadIdx.x; idx < nl * m; idx += blockDim.x) {
-        const int line = idx / m;
-        const int j = idx - line * m;
+        const int line = w.q, j = w.r;
         const float2* s = src + line * ls;
         float2* d = dst + line * ls;
-        const int k = j % ns;
         float2 v[R];
 #pragma unroll
         for (int t = 0; t < R; ++t) v[t] = s[j + t * m];
         if (ns > 1) {
 #pragma unroll
             for (int t = 1; t < R; ++t) {
-                float2 w = __ldg(tw + t * k * step);
-                if (INV) w.y = -w.y;
-                v[t] = cmul(v[t], w);
+                float2 tf = __ldg(tw + t * k * step);
+                if (INV) tf.y = -tf.y;
+                v[t] = cmul(v[t], tf);
             }
         }
         if (R == 2) dft2<INV>(v);
@@ -133,6 +157,9 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
         const int o = (j - k) * R + k;
 #pragma unroll
         for (int t = 0; t < R; ++t) d[o + t * ns] = v[t];
+        w.next();
+        k += dk;
+        if (k >= ns) k -= ns;
     }
 }
 
@@ -158,7 +185,7 @@ __device__ float2* fft_lines(float2* a, float2* b, int ls, int nl, const FftAxis
 
 // Lines per block of the strided passes and real-line pairs per block of the
 // z pass.
-__host__ __device__ inline int tile_lines(int n) { return n <= 512 ? 16 : 8; }
+__host__ __device__ inline int tile_lines(int n) { return n <= 256 ? 8 : 4; }
 __host__ __device__ inline int z_pairs(int n) { return n >= 2048 ? 1 : (2048 / n > 16 ? 16 : 2048 / n); }
 
 // Forward z pass: real lines (K0 K1 of length n = K2) of Q to half spectra
@@ -177,15 +204,17 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(PmeDev pm, long long 
     const int np = (nlb + 1) >> 1;
     const float* __restrict__ q = pm.Q + line0 * n;
     float* af = reinterpret_cast<float*>(a);
-    for (int f = threadIdx.x; f < 2 * np * n; f += blockDim.x) {
-        const int l = f / n, e = f - l * n;
+    DivWalk wle(threadIdx.x, blockDim.x, n);
+    for (int f = threadIdx.x; f < 2 * np * n; f += blockDim.x, wle.next()) {
+        const int l = wle.q, e = wle.r;
         af[2 * ((l >> 1) * ls + e) + (l & 1)] = l < nlb ? q[f] : 0.f;
     }
     __syncthreads();
     const float2* z = fft_lines<false>(a, b, ls, np, ax);
     float2* __restrict__ out = pm.S + line0 * nh;
-    for (int f = threadIdx.x; f < nlb * nh; f += blockDim.x) {
-        const int l = f / nh, k = f - l * nh;
+    DivWalk wlk(threadIdx.x, blockDim.x, nh);
+    for (int f = threadIdx.x; f < nlb * nh; f += blockDim.x, wlk.next()) {
+        const int l = wlk.q, k = wlk.r;
         const float2* zp = z + (l >> 1) * ls;
         const float2 zk = zp[k], zm = zp[k == 0 ? 0 : n - k];
         out[f] = (l & 1) ? make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x))
@@ -208,8 +237,9 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(PmeDev pm, long long 
     const int nlb = (int)min((long long)2 * ppb, nlines - line0);
     const int np = (nlb + 1) >> 1;
     const float2* __restrict__ in = pm.S + line0 * nh;
-    for (int f = threadIdx.x; f < np * nh; f += blockDim.x) {
-        const int p = f / nh, k = f - p * nh;
+    DivWalk wpk(threadIdx.x, blockDim.x, nh);
+    for (int f = threadIdx.x; f < np * nh; f += blockDim.x, wpk.next()) {
+        const int p = wpk.q, k = wpk.r;
         const float2 A = in[(2 * p) * nh + k];
         const float2 B = 2 * p + 1 < nlb ? in[(2 * p + 1) * nh + k] : make_float2(0.f, 0.f);
         a[p * ls + k] = make_float2(A.x - B.y, A.y + B.x);
@@ -218,8 +248,9 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(PmeDev pm, long long 
     __syncthreads();
     const float2* z = fft_lines<true>(a, b, ls, np, ax);
     float* __restrict__ q = pm.Q + line0 * n;
-    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x) {
-        const int l = f / n, e = f - l * n;
+    DivWalk wle(threadIdx.x, blockDim.x, n);
+    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wle.next()) {
+        const int l = wle.q, e = wle.r;
         const float2 v = z[(l >> 1) * ls + e];
         q[f] = (l & 1) ? v.y : v.x;
     }
@@ -241,14 +272,16 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_strided(PmeDev pm, int axis
     const int i0 = blockIdx.x * tb;
     const int nlb = min(tb, n_inner - i0);
     float2* base = data + blockIdx.y * os + i0;
-    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x) {
-        const int e = f / nlb, l = f - e * nlb;
+    DivWalk wel(threadIdx.x, blockDim.x, nlb);
+    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wel.next()) {
+        const int e = wel.q, l = wel.r;
         a[l * ls + e] = base[e * es + l];
     }
     __syncthreads();
     const float2* z = fft_lines<INV>(a, b, ls, nlb, ax);
-    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x) {
-        const int e = f / nlb, l = f - e * nlb;
+    DivWalk wel2(threadIdx.x, blockDim.x, nlb);
+    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wel2.next()) {
+        const int e = wel2.q, l = wel2.r;
         base[e * es + l] = z[l * ls + e];
     }
 }
@@ -291,34 +324,44 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_x_solve(PmeDev pm, double* 
     const int i0 = blockIdx.x * tb;
     const int nlb = min(tb, n_inner - i0);
     float2* base = pm.S + i0;
-    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x) {
-        const int e = f / nlb, l = f - e * nlb;
+    DivWalk wel(threadIdx.x, blockDim.x, nlb);
+    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wel.next()) {
+        const int e = wel.q, l = wel.r;
         a[l * ls + e] = base[e * es + l];
+    }
+    // per line: (m_y, m_z, m_y^2 + m_z^2, B_y E_y B_z E_z), and the weight of
+    // the line's kz plane (1/2 on kz = 0 and K2/2, which hold their own mirrors)
+    __shared__ float4 s_line[8];
+    __shared__ float s_wz[8];
+    if (threadIdx.x < nlb) {
+        const int i = i0 + threadIdx.x;
+        const int ky = i / pm.Kzh, kz = i - ky * pm.Kzh;
+        const float2 ty = __ldg(pm.tab[1] + ky), tz = __ldg(pm.tab[2] + kz);
+        s_line[threadIdx.x] = make_float4(ty.x, tz.x, ty.x * ty.x + tz.x * tz.x, ty.y * tz.y);
+        s_wz[threadIdx.x] = (kz == 0 || 2 * kz == pm.K[2]) ? 0.5f : 1.f;
     }
     __syncthreads();
     float2* z = fft_lines<false>(a, b, ls, nlb, ax);
     float2* other = z == a ? b : a;
     double ev[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    const int kz_mid = (pm.K[2] & 1) ? -1 : pm.K[2] / 2;
-    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x) {
-        const int l = f / n, kx = f - l * n;
-        const int i = i0 + l;
-        const int ky = i / pm.Kzh, kz = i - ky * pm.Kzh;
-        const float2 tx = __ldg(pm.tab[0] + kx), ty = __ldg(pm.tab[1] + ky), tz = __ldg(pm.tab[2] + kz);
-        const float m2 = tx.x * tx.x + ty.x * ty.x + tz.x * tz.x;
-        const float g = m2 > 0.f ? pm.cpre * (tx.y * ty.y * tz.y) / m2 : 0.f;
+    DivWalk wlkx(threadIdx.x, blockDim.x, n);
+    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wlkx.next()) {
+        const int l = wlkx.q, kx = wlkx.r;
+        const float2 tx = __ldg(pm.tab[0] + kx);
+        const float4 ln = s_line[l];
+        const float m2 = tx.x * tx.x + ln.z;
+        const float g = m2 > 0.f ? pm.cpre * (tx.y * ln.w) / m2 : 0.f;
         float2 v = z[l * ls + kx];
         if (EV && m2 > 0.f) {
-            const float wz = (kz == 0 || kz == kz_mid) ? 0.5f : 1.f;  // 1/2 of the mirrored pair
-            const double em = (double)(wz * g * (v.x * v.x + v.y * v.y));
+            const double em = (double)(s_wz[l] * g * (v.x * v.x + v.y * v.y));
             const float s = 2.f * (1.f + pm.pi2_b2 * m2) / m2;
             ev[0] += em;
             ev[1] += em * (double)(1.f - s * tx.x * tx.x);
-            ev[2] += em * (double)(1.f - s * ty.x * ty.x);
-            ev[3] += em * (double)(1.f - s * tz.x * tz.x);
-            ev[4] += em * (double)(-s * tx.x * ty.x);
-            ev[5] += em * (double)(-s * tx.x * tz.x);
-            ev[6] += em * (double)(-s * ty.x * tz.x);
+            ev[2] += em * (double)(1.f - s * ln.x * ln.x);
+            ev[3] += em * (double)(1.f - s * ln.y * ln.y);
+            ev[4] += em * (double)(-s * tx.x * ln.x);
+            ev[5] += em * (double)(-s * tx.x * ln.y);
+            ev[6] += em * (double)(-s * ln.x * ln.y);
         }
         v.x *= g;
         v.y *= g;
@@ -326,8 +369,9 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_x_solve(PmeDev pm, double* 
     }
     __syncthreads();
     z = fft_lines<true>(z, other, ls, nlb, ax);
-    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x) {
-        const int e = f / nlb, l = f - e * nlb;
+    DivWalk wel2(threadIdx.x, blockDim.x, nlb);
+    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wel2.next()) {
+        const int e = wel2.q, l = wel2.r;
         base[e * es + l] = z[l * ls + e];
     }
     if (EV) {
@@ -369,12 +413,25 @@ __device__ __forceinline__ void bspline_weights(float w, float (&th)[P], float (
     }
 }
 
-// Mesh index and offset of one coordinate: u = x K / L in float64.
-__device__ __forceinline__ void mesh_coord(float x, double kl, int K, int& base, float& w) {
-    const double u = (double)x * kl;
-    const double fl = floor(u);
-    w = (float)(u - fl);
-    int b = (int)fl % K;
+// Mesh index and offset of one coordinate, u = x K / L, to float64 accuracy
+// on the float32 pipes (the float64 pipe of sm_103a is narrow): K / L =
+// klh + kll, x klh = ph + pe exactly, u = ph + (pe + x kll); ph - floor(ph)
+// is exact, so the offset w is u's fractional part rounded once.
+__device__ __forceinline__ void mesh_coord(float x, float klh, float kll, int K, int& base, float& w) {
+    float ph, pe;
+    two_prod(x, klh, ph, pe);
+    const float pl = fmaf(x, kll, pe);
+    float fl = floorf(ph);
+    float fr = (ph - fl) + pl;
+    if (fr < 0.f) {
+        fr += 1.f;
+        fl -= 1.f;
+    } else if (fr >= 1.f) {
+        fr -= 1.f;
+        fl += 1.f;
+    }
+    w = fr;
+    const int b = (int)fl % K;
     base = b < 0 ? b + K : b;
 }
 
@@ -382,6 +439,48 @@ __device__ __forceinline__ int wrap_down(int i, int K) { return i < 0 ? i + K : 
 
 // Lanes per atom of the spread and gather kernels.
 __host__ __device__ constexpr int pme_lanes(int P) { return P <= 4 ? 4 : 8; }
+
+// Spline weights of the block's atoms, computed once per (atom, dimension)
+// by one thread each and kept in shared memory for the P lanes of the atom
+// (which would otherwise each recompute all three).  Atoms are the block's
+// APB consecutive sorted slots; fillers and uncharged atoms get q = 0.
+template <int P, bool DERIV>
+struct SplineTile {
+    static constexpr int APB = PME_THREADS / pme_lanes(P);
+    float w[APB][3][P];
+    float dw[DERIV ? APB : 1][3][P];
+    int base[APB][3];
+    float q[APB];
+};
+
+template <int P, bool DERIV>
+__device__ __forceinline__ void spline_tile(const SysDev& d, const PmeDev& pm, int slot0, int nslots,
+                                            SplineTile<P, DERIV>& st) {
+    constexpr int APB = SplineTile<P, DERIV>::APB;
+    for (int t = threadIdx.x; t < APB * 3; t += blockDim.x) {
+        const int at = t / 3, dim = t - 3 * at;
+        const int slot = slot0 + at;
+        float4 xq = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (slot < nslots && d.perm[slot] >= 0) xq = d.xq_s[slot];
+        const float x = dim == 0 ? xq.x : (dim == 1 ? xq.y : xq.z);
+        const float klh = dim == 0 ? pm.kl_h[0] : (dim == 1 ? pm.kl_h[1] : pm.kl_h[2]);
+        const float kll = dim == 0 ? pm.kl_l[0] : (dim == 1 ? pm.kl_l[1] : pm.kl_l[2]);
+        const int K = dim == 0 ? pm.K[0] : (dim == 1 ? pm.K[1] : pm.K[2]);
+        int b;
+        float w;
+        mesh_coord(x, klh, kll, K, b, w);
+        float th[P], dth[P];
+        bspline_weights<P, DERIV>(w, th, dth);
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            st.w[at][dim][j] = th[j];
+            if (DERIV) st.dw[at][dim][j] = dth[j];
+        }
+        st.base[at][dim] = b;
+        if (dim == 0) st.q[at] = xq.w;
+    }
+    __syncthreads();
+}
 
 // Spread: lane c of an atom's group adds q th_x[a] th_y[b] th_z[c] to the
 // mesh point (base_x - a, base_y - b, base_z - c) for all a, b.  With ENER
@@ -392,41 +491,30 @@ __global__ void __launch_bounds__(PME_THREADS) k_pme_spread(const SysDev* __rest
     pdl_wait();
     pdl_trigger();
     constexpr int LPA = pme_lanes(P);
+    constexpr int APB = SplineTile<P, false>::APB;
+    __shared__ SplineTile<P, false> st;
     const SysDev& d = sys[0];
     const int nslots = d.col_cl0[d.ncol] * CL;
-    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int slot = (int)(gt / LPA), c = (int)(gt % LPA);
-    float4 xq = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (slot < nslots && d.perm[slot] >= 0) xq = d.xq_s[slot];
-    if (xq.w != 0.f && c < P) {
-        int bx, by, bz;
-        float wx, wy, wz;
-        mesh_coord(xq.x, pm.kl[0], pm.K[0], bx, wx);
-        mesh_coord(xq.y, pm.kl[1], pm.K[1], by, wy);
-        mesh_coord(xq.z, pm.kl[2], pm.K[2], bz, wz);
-        float tx[P], ty[P], tz[P], dummy[P];
-        bspline_weights<P, false>(wx, tx, dummy);
-        bspline_weights<P, false>(wy, ty, dummy);
-        bspline_weights<P, false>(wz, tz, dummy);
-        float thz = tz[0];
-#pragma unroll
-        for (int j = 1; j < P; ++j)
-            if (c == j) thz = tz[j];
-        const long long iz = wrap_down(bz - c, pm.K[2]);
-        const float qz = xq.w * thz;
+    spline_tile<P, false>(d, pm, blockIdx.x * APB, nslots, st);
+    const int at = threadIdx.x / LPA, c = threadIdx.x % LPA;
+    const float q = st.q[at];
+    if (q != 0.f && c < P) {
+        const int bx = st.base[at][0], by = st.base[at][1];
+        const long long iz = wrap_down(st.base[at][2] - c, pm.K[2]);
+        const float qz = q * st.w[at][2][c];
 #pragma unroll
         for (int a = 0; a < P; ++a) {
             const long long ix = wrap_down(bx - a, pm.K[0]);
-            const float qa = qz * tx[a];
+            const float qa = qz * st.w[at][0][a];
 #pragma unroll
             for (int b = 0; b < P; ++b) {
                 const long long iy = wrap_down(by - b, pm.K[1]);
-                atomicAdd(pm.Q + (ix * pm.K[1] + iy) * pm.K[2] + iz, qa * ty[b]);
+                atomicAdd(pm.Q + (ix * pm.K[1] + iy) * pm.K[2] + iz, qa * st.w[at][1][b]);
             }
         }
     }
     if (ENER) {
-        double q2[1] = {c == 0 ? (double)xq.w * (double)xq.w * pm.self_pre : 0.0};
+        double q2[1] = {c == 0 ? (double)q * (double)q * pm.self_pre : 0.0};
         const int slot_e[1] = {ACC_ESELF};
         block_add<1>(q2, acc, slot_e);
     }
@@ -439,31 +527,17 @@ __global__ void __launch_bounds__(PME_THREADS) k_pme_gather(const SysDev* __rest
     pdl_wait();
     pdl_trigger();
     constexpr int LPA = pme_lanes(P);
+    constexpr int APB = SplineTile<P, true>::APB;
+    __shared__ SplineTile<P, true> st;
     const SysDev& d = sys[0];
     const int nslots = d.col_cl0[d.ncol] * CL;
-    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int slot = (int)(gt / LPA), c = (int)(gt % LPA);
-    float4 xq = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (slot < nslots && d.perm[slot] >= 0) xq = d.xq_s[slot];
+    spline_tile<P, true>(d, pm, blockIdx.x * APB, nslots, st);
+    const int at = threadIdx.x / LPA, c = threadIdx.x % LPA;
+    const float q = st.q[at];
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    if (xq.w != 0.f && c < P) {
-        int bx, by, bz;
-        float wx, wy, wz;
-        mesh_coord(xq.x, pm.kl[0], pm.K[0], bx, wx);
-        mesh_coord(xq.y, pm.kl[1], pm.K[1], by, wy);
-        mesh_coord(xq.z, pm.kl[2], pm.K[2], bz, wz);
-        float tx[P], ty[P], tz[P], dx[P], dy[P], dz[P];
-        bspline_weights<P, true>(wx, tx, dx);
-        bspline_weights<P, true>(wy, ty, dy);
-        bspline_weights<P, true>(wz, tz, dz);
-        float thz = tz[0], dthz = dz[0];
-#pragma unroll
-        for (int j = 1; j < P; ++j)
-            if (c == j) {
-                thz = tz[j];
-                dthz = dz[j];
-            }
-        const long long iz = wrap_down(bz - c, pm.K[2]);
+    if (q != 0.f && c < P) {
+        const int bx = st.base[at][0], by = st.base[at][1];
+        const long long iz = wrap_down(st.base[at][2] - c, pm.K[2]);
         float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
         for (int a = 0; a < P; ++a) {
@@ -473,16 +547,16 @@ __global__ void __launch_bounds__(PME_THREADS) k_pme_gather(const SysDev* __rest
             for (int b = 0; b < P; ++b) {
                 const long long iy = wrap_down(by - b, pm.K[1]);
                 const float ph = __ldg(pm.Q + (ix * pm.K[1] + iy) * pm.K[2] + iz);
-                rx = fmaf(ty[b], ph, rx);
-                ry = fmaf(dy[b], ph, ry);
+                rx = fmaf(st.w[at][1][b], ph, rx);
+                ry = fmaf(st.dw[at][1][b], ph, ry);
             }
-            sx = fmaf(dx[a], rx, sx);  // sum dth_x th_y phi
-            sy = fmaf(tx[a], ry, sy);  // sum th_x dth_y phi
-            sz = fmaf(tx[a], rx, sz);  // sum th_x th_y phi
+            sx = fmaf(st.dw[at][0][a], rx, sx);  // sum dth_x th_y phi
+            sy = fmaf(st.w[at][0][a], ry, sy);   // sum th_x dth_y phi
+            sz = fmaf(st.w[at][0][a], rx, sz);   // sum th_x th_y phi
         }
-        fx = -xq.w * (float)pm.kl[0] * thz * sx;
-        fy = -xq.w * (float)pm.kl[1] * thz * sy;
-        fz = -xq.w * (float)pm.kl[2] * dthz * sz;
+        fx = -q * pm.kl_h[0] * st.w[at][2][c] * sx;
+        fy = -q * pm.kl_h[1] * st.w[at][2][c] * sy;
+        fz = -q * pm.kl_h[2] * st.dw[at][2][c] * sz;
     }
 #pragma unroll
     for (int off = LPA / 2; off > 0; off >>= 1) {
@@ -490,14 +564,67 @@ __global__ void __launch_bounds__(PME_THREADS) k_pme_gather(const SysDev* __rest
         fy += __shfl_xor_sync(FULL, fy, off);
         fz += __shfl_xor_sync(FULL, fz, off);
     }
-    if (c == 0 && xq.w != 0.f) atomicAdd(d.f_s + slot, make_float4(fx, fy, fz, 0.f));
+    if (c == 0 && q != 0.f) atomicAdd(d.f_s + blockIdx.x * APB + at, make_float4(fx, fy, fz, 0.f));
 }
 
 // Excluded-pair correction of the reciprocal sum: every excluded pair
 // (i, j), each unordered pair once, minimum image of the rectangular box,
-// V = -f qi qj erf(beta r) / r, F_i = (F/r) d, d = x_i - x_j,
-// F/r = f qi qj (2 beta / sqrt(pi) exp(-beta^2 r^2) - erf(beta r) / r) / r^2,
-// in float64.  One thread per atom.
+// V = -f qi qj erf(x) / r, x = beta r, F_i = (F/r) d, d = x_i - x_j,
+// F/r = -f qi qj (erf(x) - 2 x / sqrt(pi) exp(-x^2)) / r^3.
+//
+// The pairs are bonded neighbours (x well below 1 in water), where both
+// expressions cancel badly in floating point, and their forces are large
+// (~5000 kJ/mol/nm) next to the total long-range force (~60), which the
+// reciprocal force cancels down to: the pair terms need about 30 bits.
+// With y = x^2 the Taylor series of erf and exp give, without cancellation,
+//   erf(x) / r = 2 beta / sqrt(pi) (1 + e(y)),
+//     e(y) = sum_{n>=1} (-1)^n y^n / (n! (2n + 1)),
+//   F/r = -f qi qj 4 beta^3 / (3 sqrt(pi)) (1 + h(y)),
+//     h(y) = sum_{n>=1} (-1)^n (3 / 2) 2 (n + 1) / ((n + 1)! (2n + 3)) y^n,
+// whose small corrections e, h are summed in float32 (absolute error
+// ~5e-8 for y < 1, ~2e-9 at the bond lengths of water).  The rest is
+// double-float arithmetic on the float32 pipes: the exact difference d as
+// hi + lo, the prefactors as hi + lo, the force components to ~2^-44.
+// Pairs with y >= 1 (exclusions across more than 1 / beta, rare) take the
+// float64 library erf and exp.  One thread per atom.
+__device__ __forceinline__ float excl_series_e(float y) {
+    float t = (float)(-1.0 / 76204800.0);          // n = 10 ... 1, Horner in y
+    t = fmaf(t, y, (float)(1.0 / 6894720.0));
+    t = fmaf(t, y, (float)(-1.0 / 685440.0));
+    t = fmaf(t, y, (float)(1.0 / 75600.0));
+    t = fmaf(t, y, (float)(-1.0 / 9360.0));
+    t = fmaf(t, y, (float)(1.0 / 1320.0));
+    t = fmaf(t, y, (float)(-1.0 / 216.0));
+    t = fmaf(t, y, (float)(1.0 / 42.0));
+    t = fmaf(t, y, (float)(-1.0 / 10.0));
+    t = fmaf(t, y, (float)(1.0 / 3.0));
+    return -y * t;  // -y/3 + y^2/10 - ...
+}
+__device__ __forceinline__ float excl_series_h(float y) {
+    // coefficients (3/2) 2(n+1) / ((n+1)! (2n+3)), n = 1..12
+    float t = (float)(1.0 / 4311014400.0);                        // n = 12
+    t = fmaf(t, y, (float)(-1.0 / 332640000.0));                  // n = 11
+    t = fmaf(t, y, (float)(1.0 / 27820800.0));                    // n = 10
+    t = fmaf(t, y, (float)(-1.0 / 2540160.0));                    // n = 9
+    t = fmaf(t, y, (float)(1.0 / 255360.0));                      // n = 8
+    t = fmaf(t, y, (float)(-1.0 / 28560.0));                      // n = 7
+    t = fmaf(t, y, (float)(1.0 / 3600.0));                        // n = 6
+    t = fmaf(t, y, (float)(-1.0 / 520.0));                        // n = 5
+    t = fmaf(t, y, (float)(1.0 / 88.0));                          // n = 4
+    t = fmaf(t, y, (float)(-1.0 / 18.0));                         // n = 3
+    t = fmaf(t, y, (float)(3.0 / 14.0));                          // n = 2
+    t = fmaf(t, y, (float)(-0.6));                                // n = 1
+    return y * t;
+}
+
+// a + b for double-floats (hi, lo), renormalised
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& sh, float& sl) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e += al + bl;
+    fast_two_sum(s, e, sh, sl);
+}
+
 template <bool ENER, bool VIR>
 __global__ void __launch_bounds__(PME_THREADS) k_excl_ewald(const SysDev* __restrict__ sys, PmeDev pm,
                                                             double* __restrict__ acc) {
@@ -505,55 +632,96 @@ __global__ void __launch_bounds__(PME_THREADS) k_excl_ewald(const SysDev* __rest
     pdl_trigger();
     const SysDev& d = sys[0];
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    double e = 0.0;
-    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    float eh = 0.f, el = 0.f;  // energy of this thread's pairs, hi + lo
+    double e_far = 0.0;
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (a < d.natoms && d.excl_index) {
         const int sa = d.iperm[a];
         const float4 xa = d.xq_s[sa];
-        const double Lx = d.L[0], Ly = d.L[1], Lz = d.L[2];
-        const double b2sp = 2.0 * pm.beta * 0.564189583547756287;  // 2 beta / sqrt(pi)
-        float fx = 0.f, fy = 0.f, fz = 0.f;
+        const float L[3] = {d.L[0], d.L[1], d.L[2]};
+        const float iL[3] = {1.f / d.L[0], 1.f / d.L[1], 1.f / d.L[2]};
+        float fh[3] = {0.f, 0.f, 0.f}, fl[3] = {0.f, 0.f, 0.f};
         for (int k = d.excl_index[a]; k < d.excl_index[a + 1]; ++k) {
             const int b = d.excl_atoms[k];
             if (b <= a) continue;
             const int sb = d.iperm[b];
             const float4 xb = d.xq_s[sb];
             if (xa.w == 0.f || xb.w == 0.f) continue;
-            double dx = (double)xa.x - (double)xb.x, dy = (double)xa.y - (double)xb.y,
-                   dz = (double)xa.z - (double)xb.z;
-            dx -= Lx * rint(dx / Lx);
-            dy -= Ly * rint(dy / Ly);
-            dz -= Lz * rint(dz / Lz);
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            const double r = sqrt(r2);
-            const double qq = pm.fq * (double)xa.w * (double)xb.w;
-            const double ef = erf(pm.beta * r);
-            const double fr = qq * (b2sp * exp(-pm.beta * pm.beta * r2) - ef / r) / r2;
-            if (ENER) e -= qq * ef / r;
-            if (VIR) {
-                v[0] += fr * dx * dx;
-                v[1] += fr * dy * dy;
-                v[2] += fr * dz * dz;
-                v[3] += fr * dx * dy;
-                v[4] += fr * dx * dz;
-                v[5] += fr * dy * dz;
+            // d = x_a - x_b - s L exactly as hi + lo
+            const float xav[3] = {xa.x, xa.y, xa.z}, xbv[3] = {xb.x, xb.y, xb.z};
+            float dh[3], dl[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                two_sum(xav[c], -xbv[c], dh[c], dl[c]);
+                const float sh = rintf(dh[c] * iL[c]);
+                if (sh != 0.f) {
+                    float t, e;
+                    two_sum(dh[c], -sh * L[c], t, e);
+                    fast_two_sum(t, e + dl[c], dh[c], dl[c]);
+                }
             }
-            const float gx = (float)(fr * dx), gy = (float)(fr * dy), gz = (float)(fr * dz);
-            fx += gx;
-            fy += gy;
-            fz += gz;
-            atomicAdd(d.f_s + sb, make_float4(-gx, -gy, -gz, 0.f));
+            const float r2 = dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2];
+            const float y = pm.beta2 * r2;
+            // f qi qj as hi + lo
+            float qh, ql, fqh, fql;
+            two_prod(xa.w, xb.w, qh, ql);
+            dd_mul(pm.fq_h, pm.fq_l, qh, ql, fqh, fql);
+            float frh, frl;  // F/r
+            if (y < 1.f) {
+                float oh, ol;
+                two_sum(1.f, excl_series_h(y), oh, ol);
+                float th, tl;
+                dd_mul(pm.kf_h, pm.kf_l, oh, ol, th, tl);
+                dd_mul(fqh, fql, th, tl, frh, frl);
+                frh = -frh;
+                frl = -frl;
+                if (ENER) {
+                    two_sum(1.f, excl_series_e(y), oh, ol);
+                    dd_mul(pm.ke_h, pm.ke_l, oh, ol, th, tl);
+                    float ph, pl;
+                    dd_mul(fqh, fql, th, tl, ph, pl);
+                    df_add(eh, el, -ph, -pl, eh, el);
+                }
+            } else {
+                const double r2d = (double)dh[0] * dh[0] + (double)dh[1] * dh[1] + (double)dh[2] * dh[2];
+                const double r = sqrt(r2d);
+                const double qq = (double)fqh + (double)fql;
+                const double ef = erf(pm.beta * r);
+                const double fr = qq * ((double)pm.ke_h * exp(-pm.beta * pm.beta * r2d) - ef / r) / r2d;
+                frh = (float)fr;
+                frl = (float)(fr - (double)frh);
+                if (ENER) e_far -= qq * ef / r;
+            }
+            float gh[3], gl[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dd_mul(frh, frl, dh[c], dl[c], gh[c], gl[c]);
+                df_add(fh[c], fl[c], gh[c], gl[c], fh[c], fl[c]);
+            }
+            if (VIR) {
+                v[0] += frh * dh[0] * dh[0];
+                v[1] += frh * dh[1] * dh[1];
+                v[2] += frh * dh[2] * dh[2];
+                v[3] += frh * dh[0] * dh[1];
+                v[4] += frh * dh[0] * dh[2];
+                v[5] += frh * dh[1] * dh[2];
+            }
+            atomicAdd(d.f_s + sb, make_float4(-(gh[0] + gl[0]), -(gh[1] + gl[1]), -(gh[2] + gl[2]), 0.f));
         }
-        if (fx != 0.f || fy != 0.f || fz != 0.f) atomicAdd(d.f_s + sa, make_float4(fx, fy, fz, 0.f));
+        const float ox = fh[0] + fl[0], oy = fh[1] + fl[1], oz = fh[2] + fl[2];
+        if (ox != 0.f || oy != 0.f || oz != 0.f) atomicAdd(d.f_s + sa, make_float4(ox, oy, oz, 0.f));
     }
     if (ENER) {
-        double ee[1] = {e};
+        double ee[1] = {(double)eh + (double)el + e_far};
         const int slot_e[1] = {ACC_EEXCL};
         block_add<1>(ee, acc, slot_e);
     }
     if (VIR) {
+        double vv[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) vv[c] = (double)v[c];
         const int slot_v[6] = {ACC_VXX, ACC_VYY, ACC_VZZ, ACC_VXY, ACC_VXZ, ACC_VYZ};
-        block_add<6>(v, acc, slot_v);
+        block_add<6>(vv, acc, slot_v);
     }
 }
 
@@ -561,52 +729,28 @@ size_t strided_smem(int n) { return 2 * (size_t)tile_lines(n) * (n + 1) * sizeof
 size_t z_smem(int n) { return 2 * (size_t)z_pairs(n) * (n + 1) * sizeof(float2); }
 
 template <int P>
-cudaError_t launch_pme_p(const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags, cudaStream_t st) {
-    const bool en = flags & NB_F_ENERGY, vi = flags & NB_F_VIRIAL;
-    const SysDev* sys = p.d_sys;
-    cudaError_t e;
+cudaError_t launch_spread_p(const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags, cudaStream_t st) {
     const size_t nq = (size_t)pm.K[0] * pm.K[1] * pm.K[2];
-    e = cudaMemsetAsync(pm.Q, 0, sizeof(float) * nq, st);
+    cudaError_t e = cudaMemsetAsync(pm.Q, 0, sizeof(float) * nq, st);
     if (e != cudaSuccess) return e;
-    const long long threads = (long long)p.tot_clcap * CL * pme_lanes(P);
-    const unsigned ablocks = (unsigned)((threads + PME_THREADS - 1) / PME_THREADS);
-    e = en ? launch_pdl(k_pme_spread<P, true>, ablocks, PME_THREADS, 0, st, sys, pm, acc)
-           : launch_pdl(k_pme_spread<P, false>, ablocks, PME_THREADS, 0, st, sys, pm, acc);
+    constexpr int APB = PME_THREADS / pme_lanes(P);
+    const unsigned blocks = (unsigned)(((long long)p.tot_clcap * CL + APB - 1) / APB);
+    return (flags & NB_F_ENERGY) ? launch_pdl(k_pme_spread<P, true>, blocks, PME_THREADS, 0, st, p.d_sys, pm, acc)
+                                 : launch_pdl(k_pme_spread<P, false>, blocks, PME_THREADS, 0, st, p.d_sys, pm, acc);
+}
+
+template <int P>
+cudaError_t launch_gather_p(const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags, cudaStream_t st) {
+    constexpr int APB = PME_THREADS / pme_lanes(P);
+    const unsigned blocks = (unsigned)(((long long)p.tot_clcap * CL + APB - 1) / APB);
+    cudaError_t e = launch_pdl(k_pme_gather<P>, blocks, PME_THREADS, 0, st, p.d_sys, pm);
     if (e != cudaSuccess) return e;
-    const long long zlines = (long long)pm.K[0] * pm.K[1];
-    const unsigned zblocks = (unsigned)((zlines + 2 * z_pairs(pm.K[2]) - 1) / (2 * z_pairs(pm.K[2])));
-    e = launch_pdl(k_fft_z_r2c, zblocks, FFT_THREADS, z_smem(pm.K[2]), st, pm, zlines);
-    if (e != cudaSuccess) return e;
-    const int ty = tile_lines(pm.K[1]);
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3((pm.Kzh + ty - 1) / ty, pm.K[0]);
-    cfg.blockDim = dim3(FFT_THREADS);
-    cfg.dynamicSmemBytes = strided_smem(pm.K[1]);
-    cfg.stream = st;
-    const long long es_y = pm.Kzh, os_y = (long long)pm.K[1] * pm.Kzh;
-    e = cudaLaunchKernelEx(&cfg, k_fft_strided<false>, pm, 1, pm.S, pm.Kzh, es_y, os_y);
-    if (e != cudaSuccess) return e;
-    const int tx = tile_lines(pm.K[0]);
-    const unsigned xblocks = (unsigned)(((long long)pm.K[1] * pm.Kzh + tx - 1) / tx);
-    e = (en || vi) ? launch_pdl(k_fft_x_solve<true>, xblocks, FFT_THREADS, strided_smem(pm.K[0]), st, pm, acc)
-                   : launch_pdl(k_fft_x_solve<false>, xblocks, FFT_THREADS, strided_smem(pm.K[0]), st, pm, acc);
-    if (e != cudaSuccess) return e;
-    e = cudaLaunchKernelEx(&cfg, k_fft_strided<true>, pm, 1, pm.S, pm.Kzh, es_y, os_y);
-    if (e != cudaSuccess) return e;
-    e = launch_pdl(k_fft_z_c2r, zblocks, FFT_THREADS, z_smem(pm.K[2]), st, pm, zlines);
-    if (e != cudaSuccess) return e;
-    e = launch_pdl(k_pme_gather<P>, ablocks, PME_THREADS, 0, st, sys, pm);
-    if (e != cudaSuccess) return e;
+    const bool en = flags & NB_F_ENERGY, vi = flags & NB_F_VIRIAL;
     const unsigned eblocks = (unsigned)((p.tot_atoms + PME_THREADS - 1) / PME_THREADS);
-    if (en && vi) return launch_pdl(k_excl_ewald<true, true>, eblocks, PME_THREADS, 0, st, sys, pm, acc);
-    if (en) return launch_pdl(k_excl_ewald<true, false>, eblocks, PME_THREADS, 0, st, sys, pm, acc);
-    if (vi) return launch_pdl(k_excl_ewald<false, true>, eblocks, PME_THREADS, 0, st, sys, pm, acc);
-    return launch_pdl(k_excl_ewald<false, false>, eblocks, PME_THREADS, 0, st, sys, pm, acc);
+    if (en && vi) return launch_pdl(k_excl_ewald<true, true>, eblocks, PME_THREADS, 0, st, p.d_sys, pm, acc);
+    if (en) return launch_pdl(k_excl_ewald<true, false>, eblocks, PME_THREADS, 0, st, p.d_sys, pm, acc);
+    if (vi) return launch_pdl(k_excl_ewald<false, true>, eblocks, PME_THREADS, 0, st, p.d_sys, pm, acc);
+    return launch_pdl(k_excl_ewald<false, false>, eblocks, PME_THREADS, 0, st, p.d_sys, pm, acc);
 }
 
 template <typename K>
@@ -641,12 +785,54 @@ size_t pme_smem_need(const int K[3]) {
     return m;
 }
 
-cudaError_t launch_pme(const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags, cudaStream_t st) {
+cudaError_t launch_pme_spread(const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags,
+                              cudaStream_t st) {
     switch (pm.order) {
-        case 4: return launch_pme_p<4>(p, pm, acc, flags, st);
-        case 6: return launch_pme_p<6>(p, pm, acc, flags, st);
-        default: return launch_pme_p<8>(p, pm, acc, flags, st);
+        case 4: return launch_spread_p<4>(p, pm, acc, flags, st);
+        case 6: return launch_spread_p<6>(p, pm, acc, flags, st);
+        default: return launch_spread_p<8>(p, pm, acc, flags, st);
     }
+}
+
+cudaError_t launch_pme_gather(const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags,
+                              cudaStream_t st) {
+    switch (pm.order) {
+        case 4: return launch_gather_p<4>(p, pm, acc, flags, st);
+        case 6: return launch_gather_p<6>(p, pm, acc, flags, st);
+        default: return launch_gather_p<8>(p, pm, acc, flags, st);
+    }
+}
+
+cudaError_t launch_pme_fft(const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags, cudaStream_t st) {
+    (void)p;
+    const bool ev = flags & (NB_F_ENERGY | NB_F_VIRIAL);
+    const long long zlines = (long long)pm.K[0] * pm.K[1];
+    const unsigned zblocks = (unsigned)((zlines + 2 * z_pairs(pm.K[2]) - 1) / (2 * z_pairs(pm.K[2])));
+    cudaError_t e = launch_pdl(k_fft_z_r2c, zblocks, FFT_THREADS, z_smem(pm.K[2]), st, pm, zlines);
+    if (e != cudaSuccess) return e;
+    // y pass: a 2D grid (z tiles, x planes)
+    const int ty = tile_lines(pm.K[1]);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((pm.Kzh + ty - 1) / ty, pm.K[0]);
+    cfg.blockDim = dim3(FFT_THREADS);
+    cfg.dynamicSmemBytes = strided_smem(pm.K[1]);
+    cfg.stream = st;
+    const long long es_y = pm.Kzh, os_y = (long long)pm.K[1] * pm.Kzh;
+    e = cudaLaunchKernelEx(&cfg, k_fft_strided<false>, pm, 1, pm.S, pm.Kzh, es_y, os_y);
+    if (e != cudaSuccess) return e;
+    const int tx = tile_lines(pm.K[0]);
+    const unsigned xblocks = (unsigned)(((long long)pm.K[1] * pm.Kzh + tx - 1) / tx);
+    e = ev ? launch_pdl(k_fft_x_solve<true>, xblocks, FFT_THREADS, strided_smem(pm.K[0]), st, pm, acc)
+           : launch_pdl(k_fft_x_solve<false>, xblocks, FFT_THREADS, strided_smem(pm.K[0]), st, pm, acc);
+    if (e != cudaSuccess) return e;
+    e = cudaLaunchKernelEx(&cfg, k_fft_strided<true>, pm, 1, pm.S, pm.Kzh, es_y, os_y);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_fft_z_c2r, zblocks, FFT_THREADS, z_smem(pm.K[2]), st, pm, zlines);
 }
 
 }  // namespace nbgb

@@ -34,11 +34,12 @@ EXPORTS = ["nb_last_error", "nb_ctx_create", "nb_ctx_destroy", "nb_ctx_memory", 
            "nb_sys_results", "nb_ctx_set_timing", "nb_ctx_set_timing_stages", "nb_ctx_timing", "nb_eval_info",
            "nb_eval_noalloc", "nb_ctx_set_tuning", "nb_ctx_get_tuning", "nb_server_create",
            "nb_server_destroy", "nb_server_submit", "nb_server_wait", "nb_pme_init", "nb_pme_forces"]
-NB_NSTAGE = 9
+NB_NSTAGE = 11
 NB_MOD_LJ_SHIFT = 1
 NB_MOD_EWALD_SHIFT = 2
 NB_MOD_RF_EXCL = 4
-STAGES = ["grid", "search", "prune", "coord", "zero", "forces", "final", "energy", "pme"]
+STAGES = ["grid", "search", "prune", "coord", "zero", "forces", "final", "energy", "pme_spread", "pme_fft",
+          "pme_gather"]
 
 
 class NbError(RuntimeError):

@@ -97,6 +97,27 @@ def test_long_range_matches_oracle(ctx, name, grid, order):
     _check(f, e, v, *_oracle_lr(s, p, grid, order))
 
 
+def test_far_excluded_pairs(ctx):
+    """Exclusions between atoms of different molecules at any distance up to
+    half the box (beta r >= 1 takes the float64 library erf in the kernel,
+    beta r < 1 the series), listed under one atom only."""
+    s = BOXES["small"]()
+    p = wb.params_ewald()
+    n_mol = s.n // 3
+    extra = {3 * m: 3 * ((m * 7 + 5) % n_mol) + 1 for m in range(0, n_mol, 4)}
+    lists = [list(s.excl_atoms[s.excl_index[i]:s.excl_index[i + 1]]) for i in range(s.n)]
+    for a, b in extra.items():
+        if b != a and b not in lists[a]:
+            lists[a].append(b)
+    idx = np.zeros(s.n + 1, dtype=np.int32)
+    idx[1:] = np.cumsum([len(x) for x in lists])
+    at = np.array([b for x in lists for b in x], dtype=np.int32)
+    s2 = wb.System(**{**s.__dict__})
+    s2.excl_index, s2.excl_atoms = idx, at
+    f, e, v = _gpu_lr(ctx, s2, p, (24, 24, 24), 4)
+    _check(f, e, v, *_oracle_lr(s2, p, (24, 24, 24), 4))
+
+
 def test_forces_only_flags(ctx):
     s = BOXES["small"]()
     p = wb.params_ewald()
