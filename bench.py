@@ -11,7 +11,7 @@ Metric: useful non-bonded pair interactions per second (atom pairs inside
 rc, not excluded, counted by the kernel) over the whole step.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
-                    [--workload mid|large]
+                    [--workload mid|large|ensemble|serve|dynamic|shapes|pme]
 
 --impl reference times the FP64 oracle (the CPU baseline) on the same
 workload.  Under torchrun (N > 1) every rank evaluates an independent replica
@@ -1021,6 +1021,10 @@ def main():
             out["serving"] = run_serve(argparse.Namespace(steps=1, warmup=1))
             out["dynamic_pruning"] = run_dynamic(argparse.Namespace(steps=1, warmup=1))
             out["box_shapes"] = run_box_shapes(argparse.Namespace(steps=1, warmup=1))
+            lr = run_pme(argparse.Namespace(steps=20, warmup=3))
+            out["long_range"] = {k: lr[k] for k in ("config", "value", "unit", "ms_per_step", "atoms_per_s",
+                                                    "stage_ms", "combined_ms", "short_range_ms", "fft_roofline",
+                                                    "spread")}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out))

@@ -745,12 +745,12 @@ void api_list_estimate(const nb_params& p, int natoms, const double box[3], int 
 
 // ------------------------------------------------------------- PME (host)
 
-// Stockham stages of a length-n transform: radix 4 while possible, then 2,
-// 3 and 5.  False if n has another prime factor or needs too many stages.
+// Stockham stages of a length-n transform: radix 16 while possible, then 4,
+// 2, 3 and 5.  False if n has another prime factor or needs too many stages.
 bool fft_radices(int n, FftAxis* ax) {
     ax->n = n;
     ax->nst = 0;
-    const int order[4] = {4, 2, 3, 5};
+    const int order[5] = {16, 4, 2, 3, 5};
     for (int r : order) {
         while (n % r == 0) {
             if (ax->nst == FFT_MAX_STAGES) return false;

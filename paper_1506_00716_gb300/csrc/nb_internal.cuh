@@ -138,12 +138,12 @@ struct KParams {
 
 // ---------------------------------------------------- long-range part (PME)
 // One axis of the mesh FFT: a Stockham transform of length n in `nst`
-// stages of radix 2, 3, 4 or 5.
+// stages of radix 16, 4, 2, 3 or 5.
 constexpr int FFT_MAX_STAGES = 16;
 struct FftAxis {
     int n;
     int nst;
-    int rad[FFT_MAX_STAGES];
+    int rad[FFT_MAX_STAGES];  // radix of each stage
     const float2* tw;  // [n] exp(-2 pi i j / n), rounded from float64
 };
 

@@ -103,6 +103,45 @@ __device__ __forceinline__ void dft5(float2* v) {
     v[3] = csub(r2, i2);
 }
 
+// 16-point DFT as 4 x 4: DFT4 over n1 of x[4 n1 + n2], twiddle w16^(n2 k1),
+// DFT4 over n2; output k = k1 + 4 k2.  The constants are cos and sin of
+// multiples of pi / 8.
+template <bool INV>
+__device__ __forceinline__ float2 tw16(float2 v, float c, float s) {
+    // v * exp(-+ i theta) with c = cos theta, s = sin theta
+    return INV ? make_float2(v.x * c - v.y * s, v.x * s + v.y * c) : make_float2(v.x * c + v.y * s, v.y * c - v.x * s);
+}
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* v) {
+    constexpr float C1 = 0.923879532511286756f;  // cos(pi / 8)
+    constexpr float S1 = 0.382683432365089772f;  // sin(pi / 8)
+    constexpr float R2 = 0.707106781186547524f;  // cos(pi / 4)
+    float2 a[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        float2 t[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+        dft4<INV>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) a[n2][k1] = t[k1];
+    }
+    a[1][1] = tw16<INV>(a[1][1], C1, S1);    // w^1
+    a[1][2] = tw16<INV>(a[1][2], R2, R2);    // w^2
+    a[1][3] = tw16<INV>(a[1][3], S1, C1);    // w^3
+    a[2][1] = tw16<INV>(a[2][1], R2, R2);    // w^2
+    a[2][2] = mul_mi<INV>(a[2][2]);          // w^4
+    a[2][3] = tw16<INV>(a[2][3], -R2, R2);   // w^6
+    a[3][1] = tw16<INV>(a[3][1], S1, C1);    // w^3
+    a[3][2] = tw16<INV>(a[3][2], -R2, R2);   // w^6
+    a[3][3] = tw16<INV>(a[3][3], -C1, -S1);  // w^9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+        dft4<INV>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+    }
+}
+
 // (q, r) = divmod(f, d) while f advances by a fixed stride: one division at
 // the start, then additions only (the index loops below would otherwise
 // spend most of their issue slots on integer division).
@@ -124,6 +163,12 @@ struct DivWalk {
     }
 };
 
+// Element e of a line sits at pad16(e): one padding slot every 16 elements,
+// so that the stride-R accesses of the first stages spread over the banks.
+__host__ __device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
+// Line stride in float2 (odd, so that lines start on different banks).
+__host__ __device__ __forceinline__ int line_stride(int n) { return (pad16(n) + 1) | 1; }
+
 // One Stockham stage of radix R over nl lines (line stride ls) from src to dst.
 template <int R, bool INV>
 __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, float2* __restrict__ dst, int ls,
@@ -141,7 +186,7 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
         float2* d = dst + line * ls;
         float2 v[R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) v[t] = s[j + t * m];
+        for (int t = 0; t < R; ++t) v[t] = s[pad16(j + t * m)];
         if (ns > 1) {
 #pragma unroll
             for (int t = 1; t < R; ++t) {
@@ -154,9 +199,10 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
         if (R == 3) dft3<INV>(v);
         if (R == 4) dft4<INV>(v);
         if (R == 5) dft5<INV>(v);
+        if (R == 16) dft16<INV>(v);
         const int o = (j - k) * R + k;
 #pragma unroll
-        for (int t = 0; t < R; ++t) d[o + t * ns] = v[t];
+        for (int t = 0; t < R; ++t) d[pad16(o + t * ns)] = v[t];
         w.next();
         k += dk;
         if (k >= ns) k -= ns;
@@ -170,7 +216,8 @@ __device__ float2* fft_lines(float2* a, float2* b, int ls, int nl, const FftAxis
     int ns = 1;
     for (int s = 0; s < ax.nst; ++s) {
         const int r = ax.rad[s];
-        if (r == 4) stockham_stage<4, INV>(a, b, ls, nl, ax.n, ns, ax.tw);
+        if (r == 16) stockham_stage<16, INV>(a, b, ls, nl, ax.n, ns, ax.tw);
+        else if (r == 4) stockham_stage<4, INV>(a, b, ls, nl, ax.n, ns, ax.tw);
         else if (r == 2) stockham_stage<2, INV>(a, b, ls, nl, ax.n, ns, ax.tw);
         else if (r == 3) stockham_stage<3, INV>(a, b, ls, nl, ax.n, ns, ax.tw);
         else stockham_stage<5, INV>(a, b, ls, nl, ax.n, ns, ax.tw);
@@ -185,18 +232,18 @@ __device__ float2* fft_lines(float2* a, float2* b, int ls, int nl, const FftAxis
 
 // Lines per block of the strided passes and real-line pairs per block of the
 // z pass.
-__host__ __device__ inline int tile_lines(int n) { return n <= 256 ? 8 : 4; }
-__host__ __device__ inline int z_pairs(int n) { return n >= 2048 ? 1 : (2048 / n > 16 ? 16 : 2048 / n); }
+__host__ __device__ inline int tile_lines(int n) { return n <= 256 ? 16 : (n <= 512 ? 8 : 4); }
+__host__ __device__ inline int z_pairs(int n) { return n >= 4096 ? 1 : (4096 / n > 16 ? 16 : 4096 / n); }
 
 // Forward z pass: real lines (K0 K1 of length n = K2) of Q to half spectra
 // in S, two lines per complex transform, z = a + i b, then
 // A(k) = (Z(k) + conj Z(-k)) / 2, B(k) = (Z(k) - conj Z(-k)) / (2 i).
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(PmeDev pm, long long nlines) {
+__global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_z_r2c(PmeDev pm, long long nlines) {
     extern __shared__ float2 sm[];
     pdl_wait();
     pdl_trigger();
     const FftAxis& ax = pm.ax[2];
-    const int n = ax.n, ls = n + 1, nh = pm.Kzh, ppb = z_pairs(n);
+    const int n = ax.n, ls = line_stride(n), nh = pm.Kzh, ppb = z_pairs(n);
     float2* a = sm;
     float2* b = sm + ppb * ls;
     const long long line0 = (long long)blockIdx.x * 2 * ppb;
@@ -207,7 +254,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(PmeDev pm, long long 
     DivWalk wle(threadIdx.x, blockDim.x, n);
     for (int f = threadIdx.x; f < 2 * np * n; f += blockDim.x, wle.next()) {
         const int l = wle.q, e = wle.r;
-        af[2 * ((l >> 1) * ls + e) + (l & 1)] = l < nlb ? q[f] : 0.f;
+        af[2 * ((l >> 1) * ls + pad16(e)) + (l & 1)] = l < nlb ? q[f] : 0.f;
     }
     __syncthreads();
     const float2* z = fft_lines<false>(a, b, ls, np, ax);
@@ -216,7 +263,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(PmeDev pm, long long 
     for (int f = threadIdx.x; f < nlb * nh; f += blockDim.x, wlk.next()) {
         const int l = wlk.q, k = wlk.r;
         const float2* zp = z + (l >> 1) * ls;
-        const float2 zk = zp[k], zm = zp[k == 0 ? 0 : n - k];
+        const float2 zk = zp[pad16(k)], zm = zp[pad16(k == 0 ? 0 : n - k)];
         out[f] = (l & 1) ? make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x))
                          : make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
     }
@@ -225,12 +272,12 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(PmeDev pm, long long 
 // Inverse z pass: half spectra of S back to real lines of Q, two per complex
 // transform: Z(k) = A(k) + i B(k) over the full range, the upper half from
 // the Hermitian symmetry A(n - k) = conj A(k).
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(PmeDev pm, long long nlines) {
+__global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_z_c2r(PmeDev pm, long long nlines) {
     extern __shared__ float2 sm[];
     pdl_wait();
     pdl_trigger();
     const FftAxis& ax = pm.ax[2];
-    const int n = ax.n, ls = n + 1, nh = pm.Kzh, ppb = z_pairs(n);
+    const int n = ax.n, ls = line_stride(n), nh = pm.Kzh, ppb = z_pairs(n);
     float2* a = sm;
     float2* b = sm + ppb * ls;
     const long long line0 = (long long)blockIdx.x * 2 * ppb;
@@ -242,8 +289,8 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(PmeDev pm, long long 
         const int p = wpk.q, k = wpk.r;
         const float2 A = in[(2 * p) * nh + k];
         const float2 B = 2 * p + 1 < nlb ? in[(2 * p + 1) * nh + k] : make_float2(0.f, 0.f);
-        a[p * ls + k] = make_float2(A.x - B.y, A.y + B.x);
-        if (k > 0 && n - k >= nh) a[p * ls + n - k] = make_float2(A.x + B.y, B.x - A.y);
+        a[p * ls + pad16(k)] = make_float2(A.x - B.y, A.y + B.x);
+        if (k > 0 && n - k >= nh) a[p * ls + pad16(n - k)] = make_float2(A.x + B.y, B.x - A.y);
     }
     __syncthreads();
     const float2* z = fft_lines<true>(a, b, ls, np, ax);
@@ -251,7 +298,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(PmeDev pm, long long 
     DivWalk wle(threadIdx.x, blockDim.x, n);
     for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wle.next()) {
         const int l = wle.q, e = wle.r;
-        const float2 v = z[(l >> 1) * ls + e];
+        const float2 v = z[(l >> 1) * ls + pad16(e)];
         q[f] = (l & 1) ? v.y : v.x;
     }
 }
@@ -260,13 +307,13 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(PmeDev pm, long long 
 // data[o * os + e * es + i], i in [0, n_inner); a block takes tile_lines(n)
 // consecutive i, so that each row of its tile is one contiguous segment.
 template <bool INV>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_strided(PmeDev pm, int axis, float2* __restrict__ data,
+__global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_strided(PmeDev pm, int axis, float2* __restrict__ data,
                                                              int n_inner, long long es, long long os) {
     extern __shared__ float2 sm[];
     pdl_wait();
     pdl_trigger();
     const FftAxis& ax = pm.ax[axis];
-    const int n = ax.n, ls = n + 1, tb = tile_lines(n);
+    const int n = ax.n, ls = line_stride(n), tb = tile_lines(n);
     float2* a = sm;
     float2* b = sm + tb * ls;
     const int i0 = blockIdx.x * tb;
@@ -275,14 +322,14 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_strided(PmeDev pm, int axis
     DivWalk wel(threadIdx.x, blockDim.x, nlb);
     for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wel.next()) {
         const int e = wel.q, l = wel.r;
-        a[l * ls + e] = base[e * es + l];
+        a[l * ls + pad16(e)] = base[e * es + l];
     }
     __syncthreads();
     const float2* z = fft_lines<INV>(a, b, ls, nlb, ax);
     DivWalk wel2(threadIdx.x, blockDim.x, nlb);
     for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wel2.next()) {
         const int e = wel2.q, l = wel2.r;
-        base[e * es + l] = z[l * ls + e];
+        base[e * es + l] = z[l * ls + pad16(e)];
     }
 }
 
@@ -311,12 +358,12 @@ __device__ __forceinline__ void block_add(double (&v)[NV], double* __restrict__ 
 // of each wave vector, kz in (0, K2/2) counted twice for its mirror image),
 // inverse transform, store.
 template <bool EV>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_x_solve(PmeDev pm, double* __restrict__ acc) {
+__global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_x_solve(PmeDev pm, double* __restrict__ acc) {
     extern __shared__ float2 sm[];
     pdl_wait();
     pdl_trigger();
     const FftAxis& ax = pm.ax[0];
-    const int n = ax.n, ls = n + 1, tb = tile_lines(n);
+    const int n = ax.n, ls = line_stride(n), tb = tile_lines(n);
     const int n_inner = pm.K[1] * pm.Kzh;
     const long long es = n_inner;
     float2* a = sm;
@@ -327,12 +374,12 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_x_solve(PmeDev pm, double* 
     DivWalk wel(threadIdx.x, blockDim.x, nlb);
     for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wel.next()) {
         const int e = wel.q, l = wel.r;
-        a[l * ls + e] = base[e * es + l];
+        a[l * ls + pad16(e)] = base[e * es + l];
     }
     // per line: (m_y, m_z, m_y^2 + m_z^2, B_y E_y B_z E_z), and the weight of
     // the line's kz plane (1/2 on kz = 0 and K2/2, which hold their own mirrors)
-    __shared__ float4 s_line[8];
-    __shared__ float s_wz[8];
+    __shared__ float4 s_line[16];
+    __shared__ float s_wz[16];
     if (threadIdx.x < nlb) {
         const int i = i0 + threadIdx.x;
         const int ky = i / pm.Kzh, kz = i - ky * pm.Kzh;
@@ -351,7 +398,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_x_solve(PmeDev pm, double* 
         const float4 ln = s_line[l];
         const float m2 = tx.x * tx.x + ln.z;
         const float g = m2 > 0.f ? pm.cpre * (tx.y * ln.w) / m2 : 0.f;
-        float2 v = z[l * ls + kx];
+        float2 v = z[l * ls + pad16(kx)];
         if (EV && m2 > 0.f) {
             const double em = (double)(s_wz[l] * g * (v.x * v.x + v.y * v.y));
             const float s = 2.f * (1.f + pm.pi2_b2 * m2) / m2;
@@ -365,14 +412,14 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_x_solve(PmeDev pm, double* 
         }
         v.x *= g;
         v.y *= g;
-        z[l * ls + kx] = v;
+        z[l * ls + pad16(kx)] = v;
     }
     __syncthreads();
     z = fft_lines<true>(z, other, ls, nlb, ax);
     DivWalk wel2(threadIdx.x, blockDim.x, nlb);
     for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wel2.next()) {
         const int e = wel2.q, l = wel2.r;
-        base[e * es + l] = z[l * ls + e];
+        base[e * es + l] = z[l * ls + pad16(e)];
     }
     if (EV) {
         // em is the energy of wave vector m together with its mirror -m, which
@@ -725,8 +772,8 @@ __global__ void __launch_bounds__(PME_THREADS) k_excl_ewald(const SysDev* __rest
     }
 }
 
-size_t strided_smem(int n) { return 2 * (size_t)tile_lines(n) * (n + 1) * sizeof(float2); }
-size_t z_smem(int n) { return 2 * (size_t)z_pairs(n) * (n + 1) * sizeof(float2); }
+size_t strided_smem(int n) { return 2 * (size_t)tile_lines(n) * line_stride(n) * sizeof(float2); }
+size_t z_smem(int n) { return 2 * (size_t)z_pairs(n) * line_stride(n) * sizeof(float2); }
 
 template <int P>
 cudaError_t launch_spread_p(const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags, cudaStream_t st) {

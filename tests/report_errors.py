@@ -8,7 +8,9 @@ Per workload it evaluates through the C ABI and prints RMS(dF)/RMS(F), the
 relative errors of E_LJ and E_C, the largest virial component error relative to
 the virial's Frobenius norm, and whether the interacting-pair count equals the
 oracle's.  The 3M-atom box gets forces of 192 sampled atoms (the oracle's
-per-atom loop); the ensemble goes through the batched path.
+per-atom loop); the ensemble goes through the batched path.  A second table
+gives the long-range (PME) part against oracle/pme.py, the virial error
+relative to the sum of the reciprocal and excluded-pair virials' norms.
 """
 import os
 import sys
@@ -137,6 +139,51 @@ def main():
         nb.nb_sys_destroy(h)
     nb.nb_ctx_destroy(ctx)
     print("\n".join(rows))
+    print()
+    print("\n".join(pme_rows(gpu)))
+
+
+def pme_rows(gpu):
+    """The long-range part (nb_pme_forces) against oracle/pme.py."""
+    from oracle import pme as opme
+
+    rows = ["| workload | mesh, order | RMS(dF)/RMS(F) | E_rec rel | E_self rel | E_excl rel | virial / scale |",
+            "|---|---|---:|---:|---:|---:|---:|"]
+    ctx = nb.nb_ctx_create(0, None, 0)
+    p = wb.params_ewald()
+    cases = [("small (1,944 atoms)", wb.small_box(seed=1), (24, 24, 24), 4, None),
+             ("small (1,944 atoms)", wb.small_box(seed=1), (25, 27, 45), 6, None),
+             ("small (1,944 atoms)", wb.small_box(seed=1), (32, 30, 20), 8, None),
+             ("mid (24,000 atoms)", wb.mid_box(seed=2), (54, 50, 60), 4, None),
+             ("mid (24,000 atoms)", wb.mid_box(seed=2), (64, 64, 64), 6, None),
+             ("large (3,000,000 atoms), 192 sampled forces", wb.large_box(seed=3), (256, 256, 256), 4, 192)]
+    for name, s, grid, order, nsel in cases:
+        h = nb.nb_sys_create(ctx, p, s.n, s.box)
+        try:
+            nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
+            nb.nb_grid_put(h, s.xq(), s.type)
+            nb.nb_pairlist_build(h)
+            nb.nb_pme_init(h, grid, order)
+            f = np.zeros((s.n, 3), dtype=np.float32)
+            e = np.zeros(3)
+            v = np.zeros(9)
+            nb.nb_pme_forces(h, None, f, e, v, FLAGS)
+        finally:
+            nb.nb_sys_destroy(h)
+        sel = None if nsel is None else np.sort(np.random.default_rng(31).choice(s.n, size=nsel, replace=False))
+        rec = opme.pme(s, p, grid=grid, order=order, sel=sel)
+        ex = opme.ewald_exclusions(s, p)
+        rf = rec["forces"] + (ex["forces"] if sel is None else ex["forces"][sel])
+        fg = f if sel is None else f[sel]
+        re = [rec["energy"], opme.ewald_self(s, p), ex["energy"]]
+        rv = rec["virial"] + ex["virial"]
+        scale = np.linalg.norm(rec["virial"]) + np.linalg.norm(ex["virial"])
+        rows.append(f"| {name} | {grid[0]}x{grid[1]}x{grid[2]}, {order} | {rel_rms(fg, rf):.2e} | "
+                    + " | ".join(f"{abs(e[k] - re[k]) / abs(re[k]):.2e}" for k in range(3))
+                    + f" | {np.abs(v.reshape(3, 3) - rv).max() / scale:.2e} |")
+        print(rows[-1], flush=True)
+    nb.nb_ctx_destroy(ctx)
+    return rows
 
 
 if __name__ == "__main__":
