@@ -17,23 +17,27 @@
 //   gather   F_j = -q_j sum_n phi(n) grad_j [M_p M_p M_p]
 //   self     E_self = -f beta / sqrt(pi) sum q^2
 //   excluded E_excl = -f sum_excluded q_i q_j erf(beta r) / r with its forces
-//            (the reciprocal sum includes those pairs; float64)
+//            (the reciprocal sum includes those pairs; double-float)
 //
 // Design for sm_103a.  The mesh is small next to the atom data (a 256^3 mesh
-// of float32 is 67 MB), so every FFT pass is one read and one write of the
-// mesh through shared memory: a block loads a tile of whole lines (16 lines
-// side by side for the strided y and x passes, so that each row of the tile
-// is a 128-byte segment), transforms them with a Stockham autosort FFT of
-// radix 4, 2, 3 and 5 stages in shared memory (line stride n + 1 to avoid
-// bank conflicts), and writes them back.  The z pass packs two real lines
-// into one complex transform and separates them afterwards.  The x pass
-// holds complete x lines of the spectrum, so the solve is fused into it
-// between the forward and the inverse transform: the spectrum is never
-// written in the forward direction.  Spreading and gathering use P lanes per
-// atom (P = spline order, one z index each), so the P atomics of one (x, y)
-// row of an atom hit adjacent words; the atoms come in the grid's spatial
-// order, which keeps the mesh rows they touch in L2.  Fractional mesh
-// coordinates are formed in float64 (a float32 product of x and K/L would
+// of float32 is 67 MB, mostly L2-resident), so every FFT pass reads and
+// writes the mesh once: a block takes a tile of whole lines (16 lines side
+// by side for the strided y and x passes, so that each row of the tile is a
+// 128-byte segment) and transforms them with a Stockham autosort FFT of
+// radix 16 (4 x 4 in registers), 4, 2, 3 and 5 stages.  The first stage
+// reads global memory and the last writes it, so a 256-point line makes one
+// round trip through shared memory (lines padded by one slot every 16
+// elements against bank conflicts).  The z pass packs two real lines into
+// one complex transform and separates them afterwards.  The x pass holds
+// complete x lines of the spectrum, so the solve is fused into it between
+// the forward and the inverse transform: the spectrum is never written in
+// the forward direction.  Spreading and gathering compute each atom's
+// splines once into shared memory and use P lanes per atom (P = spline
+// order, one z index each), so the P atomics of one (x, y) row of an atom hit
+// adjacent words; the atoms come in the grid's spatial order, which keeps
+// the mesh rows they touch in L2.  Nothing on the per-atom or per-point paths
+// uses the (narrow) float64 pipe: fractional mesh coordinates are formed in
+// double-float on the float32 pipes (a float32 product of x and K/L would
 // move an atom by up to 1e-5 mesh units at L = 30 nm), the splines, mesh and
 // transforms are float32, energies and virial are summed in float64.
 #include "nb_device.cuh"
@@ -169,24 +173,55 @@ __host__ __device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
 // Line stride in float2 (odd, so that lines start on different banks).
 __host__ __device__ __forceinline__ int line_stride(int n) { return (pad16(n) + 1) | 1; }
 
-// One Stockham stage of radix R over nl lines (line stride ls) from src to dst.
-template <int R, bool INV>
-__device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, float2* __restrict__ dst, int ls,
-                                               int nl, int n, int ns, const float2* __restrict__ tw) {
+// Where a stage reads and writes element e of line l: shared memory (line
+// major, padded), a strided tile of the spectrum (element e of line l at
+// base[e * es + l], lines side by side), or pairs of real z lines (line p of
+// the transform is z = a + i b of the real lines 2p and 2p + 1).
+struct SmemAcc {
+    float2* p;
+    int ls;
+    __device__ __forceinline__ float2 ld(int l, int e) const { return p[l * ls + pad16(e)]; }
+    __device__ __forceinline__ void st(int l, int e, float2 v) const { p[l * ls + pad16(e)] = v; }
+};
+struct StridedAcc {
+    float2* base;
+    long long es;
+    __device__ __forceinline__ float2 ld(int l, int e) const { return base[e * es + l]; }
+    __device__ __forceinline__ void st(int l, int e, float2 v) const { base[e * es + l] = v; }
+};
+struct RealPairAcc {
+    float* q;  // first real line of the block
+    int n;     // line length
+    int nlb;   // real lines of the block
+    __device__ __forceinline__ float2 ld(int p, int e) const {
+        const float a = q[(long long)(2 * p) * n + e];
+        const float b = 2 * p + 1 < nlb ? q[(long long)(2 * p + 1) * n + e] : 0.f;
+        return make_float2(a, b);
+    }
+    __device__ __forceinline__ void st(int p, int e, float2 v) const {
+        q[(long long)(2 * p) * n + e] = v.x;
+        if (2 * p + 1 < nlb) q[(long long)(2 * p + 1) * n + e] = v.y;
+    }
+};
+
+// One Stockham stage of radix R over nl lines, from src to dst (which must
+// not be the same buffer).  LF: consecutive threads take consecutive lines
+// (for tiles whose lines lie side by side in global memory), else
+// consecutive butterflies of a line (lines contiguous in global memory).
+template <int R, bool INV, bool LF, class Src, class Dst>
+__device__ __forceinline__ void stockham_stage(const Src& src, const Dst& dst, int nl, int n, int ns,
+                                               const float2* __restrict__ tw) {
     const int m = n / R;
     const int step = n / (ns * R);
-    // idx = line * m + j, k = j mod ns (m is a multiple of ns, so k only moves
-    // with j's own increments)
-    DivWalk w(threadIdx.x, blockDim.x, m);
-    int k = w.r % ns;
-    const int dk = w.dr % ns;
-    for (int idx = threadIdx.x; idx < nl * m; idx += blockDim.x) {
-        const int line = w.q, j = w.r;
-        const float2* s = src + line * ls;
-        float2* d = dst + line * ls;
+    const bool ns_pow2 = (ns & (ns - 1)) == 0;
+    DivWalk w(threadIdx.x, blockDim.x, LF ? nl : m);
+    for (int idx = threadIdx.x; idx < nl * m; idx += blockDim.x, w.next()) {
+        const int line = LF ? w.r : w.q;
+        const int j = LF ? w.q : w.r;
+        const int k = ns_pow2 ? (j & (ns - 1)) : j % ns;
         float2 v[R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) v[t] = s[pad16(j + t * m)];
+        for (int t = 0; t < R; ++t) v[t] = src.ld(line, j + t * m);
         if (ns > 1) {
 #pragma unroll
             for (int t = 1; t < R; ++t) {
@@ -202,32 +237,57 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
         if (R == 16) dft16<INV>(v);
         const int o = (j - k) * R + k;
 #pragma unroll
-        for (int t = 0; t < R; ++t) d[pad16(o + t * ns)] = v[t];
-        w.next();
-        k += dk;
-        if (k >= ns) k -= ns;
+        for (int t = 0; t < R; ++t) dst.st(line, o + t * ns, v[t]);
     }
 }
 
-// Transform nl lines held in a (stride ls); b is scratch of the same size.
-// Returns the buffer that holds the result.  Every thread of the block calls it.
-template <bool INV>
-__device__ float2* fft_lines(float2* a, float2* b, int ls, int nl, const FftAxis& ax) {
-    int ns = 1;
-    for (int s = 0; s < ax.nst; ++s) {
-        const int r = ax.rad[s];
-        if (r == 16) stockham_stage<16, INV>(a, b, ls, nl, ax.n, ns, ax.tw);
-        else if (r == 4) stockham_stage<4, INV>(a, b, ls, nl, ax.n, ns, ax.tw);
-        else if (r == 2) stockham_stage<2, INV>(a, b, ls, nl, ax.n, ns, ax.tw);
-        else if (r == 3) stockham_stage<3, INV>(a, b, ls, nl, ax.n, ns, ax.tw);
-        else stockham_stage<5, INV>(a, b, ls, nl, ax.n, ns, ax.tw);
+template <bool INV, bool LF, class Src, class Dst>
+__device__ __forceinline__ void stage_r(int r, const Src& src, const Dst& dst, int nl, int n, int ns,
+                                        const float2* tw) {
+    if (r == 16) stockham_stage<16, INV, LF>(src, dst, nl, n, ns, tw);
+    else if (r == 4) stockham_stage<4, INV, LF>(src, dst, nl, n, ns, tw);
+    else if (r == 2) stockham_stage<2, INV, LF>(src, dst, nl, n, ns, tw);
+    else if (r == 3) stockham_stage<3, INV, LF>(src, dst, nl, n, ns, tw);
+    else stockham_stage<5, INV, LF>(src, dst, nl, n, ns, tw);
+}
+
+// Transform nl lines from src to dst through the shared-memory buffers a and
+// b (stride ls): the first stage reads src, the last writes dst, the stages
+// between run in shared memory, so a two-stage transform (n = 256 = 16 x 16)
+// makes one shared-memory round trip per element.  src and dst may be the
+// same global lines (the first stage has read everything before the last
+// writes: a barrier separates every stage).  The first stage writes a, so src
+// must not be a; with more than two stages the stages in between alternate
+// between a and b, and dst must not be the buffer the last stage reads (a
+// after an even number of stages in between, else b).  Every thread of the
+// block calls it.
+template <bool INV, bool LF, class Src, class Dst>
+__device__ void fft_run(const Src& src, const Dst& dst, float2* a, float2* b, int ls, int nl, const FftAxis& ax) {
+    if (ax.nst == 1) {
+        // one stage: through a, so that src and dst may be the same lines
+        stage_r<INV, LF>(ax.rad[0], src, SmemAcc{a, ls}, nl, ax.n, 1, ax.tw);
+        __syncthreads();
+        DivWalk w(threadIdx.x, blockDim.x, LF ? nl : ax.n);
+        for (int idx = threadIdx.x; idx < nl * ax.n; idx += blockDim.x, w.next()) {
+            const int line = LF ? w.r : w.q, e = LF ? w.q : w.r;
+            dst.st(line, e, a[line * ls + pad16(e)]);
+        }
+        __syncthreads();
+        return;
+    }
+    stage_r<INV, LF>(ax.rad[0], src, SmemAcc{a, ls}, nl, ax.n, 1, ax.tw);
+    __syncthreads();
+    int ns = ax.rad[0];
+    for (int s = 1; s < ax.nst - 1; ++s) {
+        stage_r<INV, LF>(ax.rad[s], SmemAcc{a, ls}, SmemAcc{b, ls}, nl, ax.n, ns, ax.tw);
         __syncthreads();
         float2* t = a;
         a = b;
         b = t;
-        ns *= r;
+        ns *= ax.rad[s];
     }
-    return a;
+    stage_r<INV, LF>(ax.rad[ax.nst - 1], SmemAcc{a, ls}, dst, nl, ax.n, ns, ax.tw);
+    __syncthreads();
 }
 
 // Lines per block of the strided passes and real-line pairs per block of the
@@ -238,6 +298,7 @@ __host__ __device__ inline int z_pairs(int n) { return n >= 4096 ? 1 : (4096 / n
 // Forward z pass: real lines (K0 K1 of length n = K2) of Q to half spectra
 // in S, two lines per complex transform, z = a + i b, then
 // A(k) = (Z(k) + conj Z(-k)) / 2, B(k) = (Z(k) - conj Z(-k)) / (2 i).
+// The transform lands in shared memory (buffer c); the separation writes S.
 __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_z_r2c(PmeDev pm, long long nlines) {
     extern __shared__ float2 sm[];
     pdl_wait();
@@ -249,20 +310,16 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_z_r2c(PmeDev pm, long lo
     const long long line0 = (long long)blockIdx.x * 2 * ppb;
     const int nlb = (int)min((long long)2 * ppb, nlines - line0);
     const int np = (nlb + 1) >> 1;
-    const float* __restrict__ q = pm.Q + line0 * n;
-    float* af = reinterpret_cast<float*>(a);
-    DivWalk wle(threadIdx.x, blockDim.x, n);
-    for (int f = threadIdx.x; f < 2 * np * n; f += blockDim.x, wle.next()) {
-        const int l = wle.q, e = wle.r;
-        af[2 * ((l >> 1) * ls + pad16(e)) + (l & 1)] = l < nlb ? q[f] : 0.f;
-    }
-    __syncthreads();
-    const float2* z = fft_lines<false>(a, b, ls, np, ax);
+    // the result must not land in the buffer the last stage reads: with an
+    // even stage count the stages end in a, so the result goes to b, and
+    // vice versa
+    float2* c = (ax.nst & 1) ? a : b;
+    fft_run<false, false>(RealPairAcc{pm.Q + line0 * n, n, nlb}, SmemAcc{c, ls}, a, b, ls, np, ax);
     float2* __restrict__ out = pm.S + line0 * nh;
     DivWalk wlk(threadIdx.x, blockDim.x, nh);
     for (int f = threadIdx.x; f < nlb * nh; f += blockDim.x, wlk.next()) {
         const int l = wlk.q, k = wlk.r;
-        const float2* zp = z + (l >> 1) * ls;
+        const float2* zp = c + (l >> 1) * ls;
         const float2 zk = zp[pad16(k)], zm = zp[pad16(k == 0 ? 0 : n - k)];
         out[f] = (l & 1) ? make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x))
                          : make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
@@ -271,7 +328,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_z_r2c(PmeDev pm, long lo
 
 // Inverse z pass: half spectra of S back to real lines of Q, two per complex
 // transform: Z(k) = A(k) + i B(k) over the full range, the upper half from
-// the Hermitian symmetry A(n - k) = conj A(k).
+// the Hermitian symmetry A(n - k) = conj A(k), built in shared memory; the
+// transform's last stage writes the real lines.
 __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_z_c2r(PmeDev pm, long long nlines) {
     extern __shared__ float2 sm[];
     pdl_wait();
@@ -283,29 +341,26 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_z_c2r(PmeDev pm, long lo
     const long long line0 = (long long)blockIdx.x * 2 * ppb;
     const int nlb = (int)min((long long)2 * ppb, nlines - line0);
     const int np = (nlb + 1) >> 1;
+    // the Hermitian fill goes to the buffer the first stage does not write
+    float2* c = b;
     const float2* __restrict__ in = pm.S + line0 * nh;
     DivWalk wpk(threadIdx.x, blockDim.x, nh);
     for (int f = threadIdx.x; f < np * nh; f += blockDim.x, wpk.next()) {
         const int p = wpk.q, k = wpk.r;
         const float2 A = in[(2 * p) * nh + k];
         const float2 B = 2 * p + 1 < nlb ? in[(2 * p + 1) * nh + k] : make_float2(0.f, 0.f);
-        a[p * ls + pad16(k)] = make_float2(A.x - B.y, A.y + B.x);
-        if (k > 0 && n - k >= nh) a[p * ls + pad16(n - k)] = make_float2(A.x + B.y, B.x - A.y);
+        c[p * ls + pad16(k)] = make_float2(A.x - B.y, A.y + B.x);
+        if (k > 0 && n - k >= nh) c[p * ls + pad16(n - k)] = make_float2(A.x + B.y, B.x - A.y);
     }
     __syncthreads();
-    const float2* z = fft_lines<true>(a, b, ls, np, ax);
-    float* __restrict__ q = pm.Q + line0 * n;
-    DivWalk wle(threadIdx.x, blockDim.x, n);
-    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wle.next()) {
-        const int l = wle.q, e = wle.r;
-        const float2 v = z[(l >> 1) * ls + pad16(e)];
-        q[f] = (l & 1) ? v.y : v.x;
-    }
+    // the first stage reads c = b and writes a; b is free after it
+    fft_run<true, false>(SmemAcc{c, ls}, RealPairAcc{pm.Q + line0 * n, n, nlb}, a, b, ls, np, ax);
 }
 
 // Strided complex pass: for each outer index o, lines of n = ax.n elements at
 // data[o * os + e * es + i], i in [0, n_inner); a block takes tile_lines(n)
-// consecutive i, so that each row of its tile is one contiguous segment.
+// consecutive i, so that each row of its tile is one contiguous segment.  The
+// first stage reads global memory, the last writes it back in place.
 template <bool INV>
 __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_strided(PmeDev pm, int axis, float2* __restrict__ data,
                                                              int n_inner, long long es, long long os) {
@@ -314,23 +369,10 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_strided(PmeDev pm, int a
     pdl_trigger();
     const FftAxis& ax = pm.ax[axis];
     const int n = ax.n, ls = line_stride(n), tb = tile_lines(n);
-    float2* a = sm;
-    float2* b = sm + tb * ls;
     const int i0 = blockIdx.x * tb;
     const int nlb = min(tb, n_inner - i0);
-    float2* base = data + blockIdx.y * os + i0;
-    DivWalk wel(threadIdx.x, blockDim.x, nlb);
-    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wel.next()) {
-        const int e = wel.q, l = wel.r;
-        a[l * ls + pad16(e)] = base[e * es + l];
-    }
-    __syncthreads();
-    const float2* z = fft_lines<INV>(a, b, ls, nlb, ax);
-    DivWalk wel2(threadIdx.x, blockDim.x, nlb);
-    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wel2.next()) {
-        const int e = wel2.q, l = wel2.r;
-        base[e * es + l] = z[l * ls + pad16(e)];
-    }
+    const StridedAcc g{data + blockIdx.y * os + i0, es};
+    fft_run<INV, true>(g, g, sm, sm + tb * ls, ls, nlb, ax);
 }
 
 // Sum of NV doubles over the block, added to dst[slot[c]] by one thread.
@@ -365,31 +407,30 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_x_solve(PmeDev pm, doubl
     const FftAxis& ax = pm.ax[0];
     const int n = ax.n, ls = line_stride(n), tb = tile_lines(n);
     const int n_inner = pm.K[1] * pm.Kzh;
-    const long long es = n_inner;
     float2* a = sm;
     float2* b = sm + tb * ls;
     const int i0 = blockIdx.x * tb;
     const int nlb = min(tb, n_inner - i0);
-    float2* base = pm.S + i0;
-    DivWalk wel(threadIdx.x, blockDim.x, nlb);
-    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wel.next()) {
-        const int e = wel.q, l = wel.r;
-        a[l * ls + pad16(e)] = base[e * es + l];
-    }
+    const StridedAcc spec{pm.S + i0, n_inner};
     // per line: (m_y, m_z, m_y^2 + m_z^2, B_y E_y B_z E_z), and the weight of
     // the line's kz plane (1/2 on kz = 0 and K2/2, which hold their own mirrors)
+    // Also whether the line's ky is the Nyquist index K1/2 (even K1).
     __shared__ float4 s_line[16];
     __shared__ float s_wz[16];
+    __shared__ bool s_nyq[16];
     if (threadIdx.x < nlb) {
         const int i = i0 + threadIdx.x;
         const int ky = i / pm.Kzh, kz = i - ky * pm.Kzh;
         const float2 ty = __ldg(pm.tab[1] + ky), tz = __ldg(pm.tab[2] + kz);
         s_line[threadIdx.x] = make_float4(ty.x, tz.x, ty.x * ty.x + tz.x * tz.x, ty.y * tz.y);
         s_wz[threadIdx.x] = (kz == 0 || 2 * kz == pm.K[2]) ? 0.5f : 1.f;
+        s_nyq[threadIdx.x] = 2 * ky == pm.K[1];
     }
-    __syncthreads();
-    float2* z = fft_lines<false>(a, b, ls, nlb, ax);
+    // forward transform from the spectrum into shared memory (buffer z, the
+    // one the last stage does not read), solve there, inverse back
+    float2* z = (ax.nst & 1) ? a : b;
     float2* other = z == a ? b : a;
+    fft_run<false, true>(spec, SmemAcc{z, ls}, a, b, ls, nlb, ax);
     double ev[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     DivWalk wlkx(threadIdx.x, blockDim.x, n);
     for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wlkx.next()) {
@@ -400,27 +441,32 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_x_solve(PmeDev pm, doubl
         const float g = m2 > 0.f ? pm.cpre * (tx.y * ln.w) / m2 : 0.f;
         float2 v = z[l * ls + pad16(kx)];
         if (EV && m2 > 0.f) {
-            const double em = (double)(s_wz[l] * g * (v.x * v.x + v.y * v.y));
+            const float wz = s_wz[l];
+            const double em = (double)(wz * g * (v.x * v.x + v.y * v.y));
             const float s = 2.f * (1.f + pm.pi2_b2 * m2) / m2;
+            // The Nyquist index K/2 stands for +K/2 in every wave vector, so
+            // the unstored mirror of a point with kz inside (0, K2/2) has -m
+            // except in a Nyquist component, where it keeps the sign: its
+            // off-diagonal products m_a m_b then cancel the stored point's
+            // where exactly one of a, b is a Nyquist component.
+            const bool inner = wz == 1.f, nx = 2 * kx == n, ny = s_nyq[l];
+            const float cxy = (inner && nx != ny) ? 0.f : 1.f;
+            const float cxz = (inner && nx) ? 0.f : 1.f;
+            const float cyz = (inner && ny) ? 0.f : 1.f;
             ev[0] += em;
             ev[1] += em * (double)(1.f - s * tx.x * tx.x);
             ev[2] += em * (double)(1.f - s * ln.x * ln.x);
             ev[3] += em * (double)(1.f - s * ln.y * ln.y);
-            ev[4] += em * (double)(-s * tx.x * ln.x);
-            ev[5] += em * (double)(-s * tx.x * ln.y);
-            ev[6] += em * (double)(-s * ln.x * ln.y);
+            ev[4] += em * (double)(-cxy * s * tx.x * ln.x);
+            ev[5] += em * (double)(-cxz * s * tx.x * ln.y);
+            ev[6] += em * (double)(-cyz * s * ln.x * ln.y);
         }
         v.x *= g;
         v.y *= g;
         z[l * ls + pad16(kx)] = v;
     }
     __syncthreads();
-    z = fft_lines<true>(z, other, ls, nlb, ax);
-    DivWalk wel2(threadIdx.x, blockDim.x, nlb);
-    for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wel2.next()) {
-        const int e = wel2.q, l = wel2.r;
-        base[e * es + l] = z[l * ls + pad16(e)];
-    }
+    fft_run<true, true>(SmemAcc{z, ls}, spec, other, z, ls, nlb, ax);
     if (EV) {
         // em is the energy of wave vector m together with its mirror -m, which
         // the half spectrum does not hold (of m alone on the planes kz = 0
@@ -531,7 +577,12 @@ __device__ __forceinline__ void spline_tile(const SysDev& d, const PmeDev& pm, i
 
 // Spread: lane c of an atom's group adds q th_x[a] th_y[b] th_z[c] to the
 // mesh point (base_x - a, base_y - b, base_z - c) for all a, b.  With ENER
-// also the self energy -f beta / sqrt(pi) sum q^2.
+// also the self energy -f beta / sqrt(pi) sum q^2.  The P lanes of an atom
+// hit P adjacent words of one mesh row, so each warp instruction's atomics
+// reach the L2 as few sector operations.  (Summing a block's contributions
+// in a shared-memory window first, and adding the window with vector
+// atomics, was 1.8x slower: the block's atoms are close together, and their
+// shared-memory atomics collide.)
 template <int P, bool ENER>
 __global__ void __launch_bounds__(PME_THREADS) k_pme_spread(const SysDev* __restrict__ sys, PmeDev pm,
                                                             double* __restrict__ acc) {
@@ -568,7 +619,10 @@ __global__ void __launch_bounds__(PME_THREADS) k_pme_spread(const SysDev* __rest
 }
 
 // Gather: the force on each atom from the potential mesh, the P lanes of its
-// group summing over their z index and reducing by shuffles.
+// group summing over their z index and reducing by shuffles.  The mesh is
+// read directly: neighbouring atoms of a block share most mesh lines in L1.
+// (Copying the block's box of mesh points into shared memory first was 2x
+// slower: the copy loads every point of the box from L2 once per block.)
 template <int P>
 __global__ void __launch_bounds__(PME_THREADS) k_pme_gather(const SysDev* __restrict__ sys, PmeDev pm) {
     pdl_wait();

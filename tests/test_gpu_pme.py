@@ -8,9 +8,10 @@ Frobenius norms of its parts.  The reciprocal and excluded-pair virials
 cancel in part (their sum is about a third of the reciprocal one in water),
 and each part carries the error of its own arithmetic (the float32 mesh and
 transforms: a few 1e-7 of the reciprocal virial's norm), so the bound of the
-sum is the sum of the parts' bounds.  Meshes cover every radix of the transform (4, 2, 3, 5),
-odd mesh sizes (an odd z length and an odd number of z lines), ragged
-transform tiles and all three spline orders.
+sum is the sum of the parts' bounds.  Meshes cover every radix of the
+transform (16, 4, 2, 3, 5), one-stage and many-stage transforms, odd mesh
+sizes (an odd z length and an odd number of z lines), ragged transform tiles
+and all three spline orders.
 """
 import numpy as np
 import pytest
@@ -87,6 +88,7 @@ def _check(f, e, v, rf, re, rv, vscale):
     ("small", (24, 24, 24), 4),      # radices 4, 2, 3
     ("small", (25, 27, 45), 6),      # 5, 3 only; odd z length, odd number of z lines
     ("small", (32, 30, 20), 8),      # mixed per axis, order 8
+    ("small", (16, 8, 16), 4),       # single-stage transforms (16) on x and z, 4 x 2 on y
     ("mid", (54, 50, 60), 4),        # 2 3 3 3 / 2 5 5 / 4 3 5
     ("mid", (64, 64, 64), 6),
 ])
