@@ -580,9 +580,8 @@ __device__ __forceinline__ void spline_tile(const SysDev& d, const PmeDev& pm, i
 // also the self energy -f beta / sqrt(pi) sum q^2.  The P lanes of an atom
 // hit P adjacent words of one mesh row, so each warp instruction's atomics
 // reach the L2 as few sector operations.  (Summing a block's contributions
-// in a shared-memory window first, and adding the window with vector
-// atomics, was 1.8x slower: the block's atoms are close together, and their
-// shared-memory atomics collide.)
+// in a shared-memory window first and adding the window with vector atomics
+// was 1.8x slower, with four lanes per atom or with a warp per atom.)
 template <int P, bool ENER>
 __global__ void __launch_bounds__(PME_THREADS) k_pme_spread(const SysDev* __restrict__ sys, PmeDev pm,
                                                             double* __restrict__ acc) {
