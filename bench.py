@@ -320,8 +320,9 @@ def job_throughput(pairs_per_step: int, steps: int, world: int, max_ms: float) -
     return pairs_per_step * steps * world / (max_ms * 1e-3)
 
 
-def _traffic_per_launch(key: str):
-    """DRAM bytes per launch from the committed ncu summary, if its kernel source still matches."""
+def _traffic_per_launch(key: str, source: str = "nb_kernel.cu"):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source
+    (csrc/<source>) still matches the one the counters were taken on."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -330,7 +331,7 @@ def _traffic_per_launch(key: str):
         return None
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_1506_00716_gb300", "csrc", "nb_kernel.cu")
+    src = os.path.join(ROOT, "paper_1506_00716_gb300", "csrc", source)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     return rec.get("bytes") if rec.get("source_sha") == sha else None
 
@@ -500,6 +501,13 @@ def run_large(args) -> dict:
     roofline = _fp32_roofline(torch, dev, "ewald", f_n - 1, 1, info["n_slots"], avg, "k_forces<Ewald>",
                               _traffic_per_launch("forces_ewald_large"))
     grid_bytes = s.n * (20 + 24 + 8 + 8) + info["n_clusters"] * 32
+    # algorithmic bytes of the build: the search reads the bounding boxes once
+    # and writes the raw list (4-byte j-cluster + 8-byte mask per entry) and
+    # the work items; the prune reads the raw list and the sorted coordinates
+    # once and writes the kept entries and the items
+    slots = info["n_clusters"] * 8
+    search_bytes = info["n_clusters"] * 32 + info["n_entries_raw"] * 12 + info["n_items"] * 16
+    prune_bytes = info["n_entries_raw"] * 12 + slots * 16 + info["n_entries"] * 12 + 2 * info["n_items"] * 16
     return {
         "metric": METRIC, "value": n_pairs / (avg * 1e-3), "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": avg, "higher_is_better": True,
@@ -513,6 +521,11 @@ def run_large(args) -> dict:
         "roofline": roofline,
         "build_ms": {"grid": stage["grid"][0], "search": stage["search"][0], "prune": stage["prune"][0]},
         "grid_put_gbs": grid_bytes / (stage["grid"][0] * 1e-3) / 1e9,
+        "build_gbs": {"grid": round(grid_bytes / (stage["grid"][0] * 1e-3) / 1e9, 1),
+                      "search": round(search_bytes / (stage["search"][0] * 1e-3) / 1e9, 1),
+                      "prune": round(prune_bytes / (stage["prune"][0] * 1e-3) / 1e9, 1),
+                      "bytes": {"grid": grid_bytes, "search": search_bytes, "prune": prune_bytes},
+                      "peak_gbs": float(_peaks()[0].get("hbm_gbs", 6800.0))},
         "energy_eval_ms": stage["energy"][0] / max(stage["energy"][1], 1),
         "clocks": clk.summary(),
     }
@@ -614,7 +627,8 @@ def run_pme(args) -> dict:
         "combined_ms": combined, "short_range_ms": short,
         "energies": {"E_rec": energies[0], "E_self": energies[1], "E_excl": energies[2]},
         "fft_roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                         "frac": round(achieved / hbm, 4), "traffic": None,
+                         "frac": round(achieved / hbm, 4),
+                         "traffic": _traffic_per_launch("fft_pme_large", "nb_pme.cu"),
                          "kernels": "k_fft_z_r2c, k_fft_strided x2, k_fft_x_solve, k_fft_z_c2r",
                          "algorithmic_bytes": fft_bytes, "peak_kind": kind},
         "spread": {"atomics_per_eval": spread_atomics,
@@ -1015,6 +1029,7 @@ def main():
                                 "unit": UNIT, "ms_per_eval": lg["ms_per_step"],
                                 "computed_pairs_per_s": lg["config"]["computed_pairs_per_s"],
                                 "roofline": lg["roofline"], "build_ms": lg["build_ms"],
+                                "build_gbs": lg["build_gbs"],
                                 "energy_eval_ms": lg["energy_eval_ms"], "tuning": lg["config"]["tuning"]}
         if world == 1 and not args.no_extra:
             out["ensemble"] = run_ensemble(argparse.Namespace(steps=5, warmup=3))
