@@ -196,6 +196,30 @@ def test_device_buffers(ctx):
     assert np.allclose(vd.cpu().numpy(), vh, rtol=0, atol=V_TOL * np.abs(vh).max())
 
 
+def test_reinit_mesh_and_memory_accounting(ctx):
+    """A second nb_pme_init replaces the mesh (new size and order take effect);
+    the budget accounting returns to its start when the system is destroyed."""
+    s = BOXES["small"]()
+    p = wb.params_ewald()
+    used0, _ = nb.nb_ctx_memory(ctx)
+    h = _system(ctx, s, p, (24, 24, 24), 4)
+    used1, _ = nb.nb_ctx_memory(ctx)
+    try:
+        nb.nb_pme_init(h, (32, 30, 20), 6)
+        used2, _ = nb.nb_ctx_memory(ctx)
+        # the mesh grows from 24^3 to 32 x 30 x 20 (real + half spectrum)
+        assert used2 > used1
+        f = np.zeros((s.n, 3), dtype=np.float32)
+        e = np.zeros(3)
+        v = np.zeros(9)
+        nb.nb_pme_forces(h, None, f, e, v, EV)
+    finally:
+        nb.nb_sys_destroy(h)
+    _check(f, e, v.reshape(3, 3), *_oracle_lr(s, p, (32, 30, 20), 6))
+    used3, _ = nb.nb_ctx_memory(ctx)
+    assert used3 == used0
+
+
 def test_validation(ctx):
     s = BOXES["small"]()
     p = wb.params_ewald()
