@@ -190,6 +190,14 @@ nb_status nb_ctx_set_timing_stages(nb_ctx *ctx, unsigned stage_mask);
 nb_status nb_ctx_timing(nb_ctx *ctx, double *ms, long long *launches, int reset);
 /* Device bytes currently held by the context's systems and batches. */
 nb_status nb_ctx_memory(nb_ctx *ctx, size_t *bytes_in_use, size_t *budget);
+/*
+ * Test hook (fault injection on the host): the next `count` device
+ * allocations of this context fail as an out-of-memory would, with
+ * NB_ERR_OOM and nothing allocated, so that callers can test their recovery
+ * without exhausting the GPU.  count = 0 clears it.  Every call that
+ * allocates leaves the context and its systems usable after such a failure.
+ */
+nb_status nb_ctx_inject_alloc_failures(nb_ctx *ctx, int count);
 /* Device bytes nb_sys_create would reserve for a system of natoms atoms. */
 nb_status nb_sys_footprint(const nb_params *params, int natoms, const double box[3], size_t *bytes);
 

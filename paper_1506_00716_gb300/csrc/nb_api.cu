@@ -168,14 +168,14 @@ nb_status excl_symmetrise(int n, const int* excl_index, const int* excl_atoms, s
 }
 
 nb_status sys_upload_exclusions(nb_sys* sys, const int* idx, const int* at) {
-    if (sys->d_excl) dev_free(sys->ctx, sys->d_excl, sys->excl_bytes);
-    sys->d_excl = nullptr;
     const size_t nidx = (size_t)sys->natoms + 1;
     const size_t nat = (size_t)idx[sys->natoms];
     size_t bytes = 4 * (nidx + std::max<size_t>(1, nat));
+    // the new buffer first: if it cannot be had, the old exclusions stay
     void* p = nullptr;
     nb_status s = dev_alloc(sys->ctx, &p, bytes);
     if (s != NB_OK) return s;
+    if (sys->d_excl) dev_free(sys->ctx, sys->d_excl, sys->excl_bytes);
     sys->d_excl = (int*)p;
     sys->excl_bytes = bytes;
     NB_CK(cudaMemcpyAsync(sys->d_excl, idx, 4 * nidx, cudaMemcpyHostToDevice, sys->ctx->stream));
@@ -228,6 +228,11 @@ nb_status ctx_reserve(nb_ctx* ctx, size_t bytes) {
 }
 
 nb_status dev_alloc(nb_ctx* ctx, void** ptr, size_t bytes) {
+    if (ctx->fail_allocs > 0) {
+        --ctx->fail_allocs;
+        *ptr = nullptr;
+        return fail(NB_ERR_OOM, "device allocation failed (injected)");
+    }
     nb_status s = ctx_reserve(ctx, bytes);
     if (s != NB_OK) return s;
     cudaError_t e = cudaMallocAsync(ptr, bytes, ctx->stream);
@@ -420,8 +425,10 @@ void plan_drop_graphs(Plan* pl) {
     }
 }
 
+// The list buffers of the plan, at the given capacities.  The new block is
+// allocated before the old one is freed, so that a failure (budget or device
+// memory) leaves the plan with its old, still valid list.
 nb_status plan_alloc_list(Plan* pl, long long items, long long entries) {
-    plan_free_list(pl);
     items = std::min<long long>(items, (1ll << 31) - 1);
     entries = std::min<long long>(entries, (1ll << 31) - 1);
     size_t bytes = align256(16 * (size_t)items) + align256(4 * (size_t)items) + align256(4 * (size_t)entries) +
@@ -429,6 +436,7 @@ nb_status plan_alloc_list(Plan* pl, long long items, long long entries) {
     void* blk = nullptr;
     nb_status s = dev_alloc(pl->ctx, &blk, bytes);
     if (s != NB_OK) return s;
+    plan_free_list(pl);
     char* b = (char*)blk;
     pl->list.items = (int4*)b;
     b += align256(16 * (size_t)items);
@@ -884,6 +892,12 @@ nb_status nb_ctx_memory(nb_ctx* ctx, size_t* bytes_in_use, size_t* budget) {
     if (!ctx) return fail(NB_ERR_ARG, "ctx is NULL");
     if (bytes_in_use) *bytes_in_use = ctx->in_use;
     if (budget) *budget = ctx->budget;
+    return NB_OK;
+}
+
+nb_status nb_ctx_inject_alloc_failures(nb_ctx* ctx, int count) {
+    if (!ctx || count < 0) return fail(NB_ERR_ARG, "ctx is NULL or count < 0");
+    ctx->fail_allocs = count;
     return NB_OK;
 }
 

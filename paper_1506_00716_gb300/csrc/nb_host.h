@@ -30,6 +30,7 @@ struct nb_ctx {
     cudaStream_t stream = nullptr;
     size_t budget = 0;
     size_t in_use = 0;
+    int fail_allocs = 0;  // nb_ctx_inject_alloc_failures
     int num_sms = 0;
     unsigned timing = 0;  // mask of timed stages (1 << NB_STAGE_*)
     bool capturing = false;

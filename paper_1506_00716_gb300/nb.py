@@ -33,7 +33,8 @@ EXPORTS = ["nb_last_error", "nb_ctx_create", "nb_ctx_destroy", "nb_ctx_memory", 
            "nb_batch_destroy", "nb_sys_set_coords", "nb_batch_submit", "nb_batch_poll",
            "nb_sys_results", "nb_ctx_set_timing", "nb_ctx_set_timing_stages", "nb_ctx_timing", "nb_eval_info",
            "nb_eval_noalloc", "nb_ctx_set_tuning", "nb_ctx_get_tuning", "nb_server_create",
-           "nb_server_destroy", "nb_server_submit", "nb_server_wait", "nb_pme_init", "nb_pme_forces"]
+           "nb_server_destroy", "nb_server_submit", "nb_server_wait", "nb_pme_init", "nb_pme_forces",
+           "nb_ctx_inject_alloc_failures"]
 NB_NSTAGE = 11
 NB_MOD_LJ_SHIFT = 1
 NB_MOD_EWALD_SHIFT = 2
@@ -98,6 +99,7 @@ def load(path: str | None = None):
         "nb_ctx_create": ([ctypes.c_int, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)], _st),
         "nb_ctx_destroy": ([_vp], _st),
         "nb_ctx_memory": ([_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)], _st),
+        "nb_ctx_inject_alloc_failures": ([_vp, ctypes.c_int], _st),
         "nb_sys_footprint": ([ctypes.POINTER(nb_params), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_size_t)], _st),
         "nb_sys_create": ([_vp, ctypes.POINTER(nb_params), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -199,6 +201,11 @@ def nb_ctx_memory(ctx) -> tuple[int, int]:
     a, b = ctypes.c_size_t(), ctypes.c_size_t()
     check(load().nb_ctx_memory(ctx, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def nb_ctx_inject_alloc_failures(ctx, count: int) -> None:
+    """Test hook: the next `count` device allocations of ctx fail with NB_ERR_OOM."""
+    check(load().nb_ctx_inject_alloc_failures(ctx, count))
 
 
 def nb_sys_footprint(params, natoms: int, box) -> int:
