@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_z_c2r(PmeDev pm, long lo
 // consecutive i, so that each row of its tile is one contiguous segment.  The
 // first stage reads global memory, the last writes it back in place.
 template <bool INV>
-__global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_strided(PmeDev pm, int axis, float2* __restrict__ data,
+__global__ void __launch_bounds__(FFT_THREADS, 4) k_fft_strided(PmeDev pm, int axis, float2* __restrict__ data,
                                                              int n_inner, long long es, long long os) {
     extern __shared__ float2 sm[];
     pdl_wait();
@@ -826,6 +826,9 @@ __global__ void __launch_bounds__(PME_THREADS) k_excl_ewald(const SysDev* __rest
 }
 
 size_t strided_smem(int n) { return 2 * (size_t)tile_lines(n) * line_stride(n) * sizeof(float2); }
+// The strided pass of an axis with at most two stages uses one buffer only
+// (global -> shared -> global).
+size_t strided_pass_smem(const FftAxis& ax) { return (ax.nst <= 2 ? 1 : 2) * (size_t)tile_lines(ax.n) * line_stride(ax.n) * sizeof(float2); }
 size_t z_smem(int n) { return 2 * (size_t)z_pairs(n) * line_stride(n) * sizeof(float2); }
 
 template <int P>
@@ -920,7 +923,7 @@ cudaError_t launch_pme_fft(const PlanLaunch& p, const PmeDev& pm, double* acc, u
     cfg.numAttrs = 1;
     cfg.gridDim = dim3((pm.Kzh + ty - 1) / ty, pm.K[0]);
     cfg.blockDim = dim3(FFT_THREADS);
-    cfg.dynamicSmemBytes = strided_smem(pm.K[1]);
+    cfg.dynamicSmemBytes = strided_pass_smem(pm.ax[1]);
     cfg.stream = st;
     const long long es_y = pm.Kzh, os_y = (long long)pm.K[1] * pm.Kzh;
     e = cudaLaunchKernelEx(&cfg, k_fft_strided<false>, pm, 1, pm.S, pm.Kzh, es_y, os_y);
