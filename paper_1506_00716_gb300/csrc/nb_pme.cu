@@ -290,6 +290,89 @@ __device__ void fft_run(const Src& src, const Dst& dst, float2* a, float2* b, in
     __syncthreads();
 }
 
+// Single-buffer variant, for transforms where every stage has at most one
+// butterfly per thread (nl * n / R <= blockDim; 256-point lines of 16 side
+// by side, for instance): each stage reads its inputs into registers, waits
+// for the whole block, and writes its outputs in place, so one shared buffer
+// serves the whole transform and twice as many blocks fit an SM.
+template <int R, bool INV, bool LF, class Src, class Dst>
+__device__ __forceinline__ void stockham_stage_1(const Src& src, const Dst& dst, int nl, int n, int ns,
+                                                 const float2* __restrict__ tw) {
+    const int m = n / R;
+    const int step = n / (ns * R);
+    const int idx = threadIdx.x;
+    const bool act = idx < nl * m;
+    const int q = LF ? idx / nl : idx / m;
+    const int line = LF ? idx - q * nl : q;
+    const int j = LF ? q : idx - q * m;
+    const int k = (ns & (ns - 1)) == 0 ? (j & (ns - 1)) : j % ns;
+    float2 v[R];
+    if (act) {
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[t] = src.ld(line, j + t * m);
+        if (ns > 1) {
+#pragma unroll
+            for (int t = 1; t < R; ++t) {
+                float2 tf = __ldg(tw + t * k * step);
+                if (INV) tf.y = -tf.y;
+                v[t] = cmul(v[t], tf);
+            }
+        }
+        if (R == 2) dft2<INV>(v);
+        if (R == 3) dft3<INV>(v);
+        if (R == 4) dft4<INV>(v);
+        if (R == 5) dft5<INV>(v);
+        if (R == 16) dft16<INV>(v);
+    }
+    __syncthreads();
+    if (act) {
+        const int o = (j - k) * R + k;
+#pragma unroll
+        for (int t = 0; t < R; ++t) dst.st(line, o + t * ns, v[t]);
+    }
+}
+
+template <bool INV, bool LF, class Src, class Dst>
+__device__ __forceinline__ void stage1_r(int r, const Src& src, const Dst& dst, int nl, int n, int ns,
+                                         const float2* tw) {
+    if (r == 16) stockham_stage_1<16, INV, LF>(src, dst, nl, n, ns, tw);
+    else if (r == 4) stockham_stage_1<4, INV, LF>(src, dst, nl, n, ns, tw);
+    else if (r == 2) stockham_stage_1<2, INV, LF>(src, dst, nl, n, ns, tw);
+    else if (r == 3) stockham_stage_1<3, INV, LF>(src, dst, nl, n, ns, tw);
+    else stockham_stage_1<5, INV, LF>(src, dst, nl, n, ns, tw);
+}
+
+// The transform with one shared buffer a (stride ls): first stage from src,
+// stages in between in place in a, last stage to dst (which may be a, or the
+// global lines src came from).  Every thread of the block calls it.
+template <bool INV, bool LF, class Src, class Dst>
+__device__ void fft_run_1(const Src& src, const Dst& dst, float2* a, int ls, int nl, const FftAxis& ax) {
+    const SmemAcc sa{a, ls};
+    if (ax.nst == 1) {
+        stage1_r<INV, LF>(ax.rad[0], src, dst, nl, ax.n, 1, ax.tw);
+        __syncthreads();
+        return;
+    }
+    stage1_r<INV, LF>(ax.rad[0], src, sa, nl, ax.n, 1, ax.tw);
+    __syncthreads();
+    int ns = ax.rad[0];
+    for (int s = 1; s < ax.nst - 1; ++s) {
+        stage1_r<INV, LF>(ax.rad[s], sa, sa, nl, ax.n, ns, ax.tw);
+        __syncthreads();
+        ns *= ax.rad[s];
+    }
+    stage1_r<INV, LF>(ax.rad[ax.nst - 1], sa, dst, nl, ax.n, ns, ax.tw);
+    __syncthreads();
+}
+
+// Whether every stage of the axis has at most one butterfly per thread for
+// nl lines (then one shared buffer suffices).
+__host__ __device__ inline bool one_buffer(const FftAxis& ax, int nl) {
+    for (int s = 0; s < ax.nst; ++s)
+        if (nl * (ax.n / ax.rad[s]) > FFT_THREADS) return false;
+    return true;
+}
+
 // Lines per block of the strided passes and real-line pairs per block of the
 // z pass.
 __host__ __device__ inline int tile_lines(int n) { return n <= 256 ? 16 : (n <= 512 ? 8 : 4); }
@@ -299,7 +382,7 @@ __host__ __device__ inline int z_pairs(int n) { return n >= 4096 ? 1 : (4096 / n
 // in S, two lines per complex transform, z = a + i b, then
 // A(k) = (Z(k) + conj Z(-k)) / 2, B(k) = (Z(k) - conj Z(-k)) / (2 i).
 // The transform lands in shared memory (buffer c); the separation writes S.
-__global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_z_r2c(PmeDev pm, long long nlines) {
+__global__ void __launch_bounds__(FFT_THREADS, 4) k_fft_z_r2c(PmeDev pm, long long nlines) {
     extern __shared__ float2 sm[];
     pdl_wait();
     pdl_trigger();
@@ -310,11 +393,17 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_z_r2c(PmeDev pm, long lo
     const long long line0 = (long long)blockIdx.x * 2 * ppb;
     const int nlb = (int)min((long long)2 * ppb, nlines - line0);
     const int np = (nlb + 1) >> 1;
-    // the result must not land in the buffer the last stage reads: with an
-    // even stage count the stages end in a, so the result goes to b, and
-    // vice versa
-    float2* c = (ax.nst & 1) ? a : b;
-    fft_run<false, false>(RealPairAcc{pm.Q + line0 * n, n, nlb}, SmemAcc{c, ls}, a, b, ls, np, ax);
+    float2* c;
+    if (one_buffer(ax, ppb)) {
+        c = a;
+        fft_run_1<false, false>(RealPairAcc{pm.Q + line0 * n, n, nlb}, SmemAcc{a, ls}, a, ls, np, ax);
+    } else {
+        // the result must not land in the buffer the last stage reads: with an
+        // even stage count the stages end in a, so the result goes to b, and
+        // vice versa
+        c = (ax.nst & 1) ? a : b;
+        fft_run<false, false>(RealPairAcc{pm.Q + line0 * n, n, nlb}, SmemAcc{c, ls}, a, b, ls, np, ax);
+    }
     float2* __restrict__ out = pm.S + line0 * nh;
     DivWalk wlk(threadIdx.x, blockDim.x, nh);
     for (int f = threadIdx.x; f < nlb * nh; f += blockDim.x, wlk.next()) {
@@ -330,7 +419,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_z_r2c(PmeDev pm, long lo
 // transform: Z(k) = A(k) + i B(k) over the full range, the upper half from
 // the Hermitian symmetry A(n - k) = conj A(k), built in shared memory; the
 // transform's last stage writes the real lines.
-__global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_z_c2r(PmeDev pm, long long nlines) {
+__global__ void __launch_bounds__(FFT_THREADS, 4) k_fft_z_c2r(PmeDev pm, long long nlines) {
     extern __shared__ float2 sm[];
     pdl_wait();
     pdl_trigger();
@@ -342,7 +431,9 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_z_c2r(PmeDev pm, long lo
     const int nlb = (int)min((long long)2 * ppb, nlines - line0);
     const int np = (nlb + 1) >> 1;
     // the Hermitian fill goes to the buffer the first stage does not write
-    float2* c = b;
+    // (with one buffer, to that buffer: its first stage works in place)
+    const bool one = one_buffer(ax, ppb);
+    float2* c = one ? a : b;
     const float2* __restrict__ in = pm.S + line0 * nh;
     DivWalk wpk(threadIdx.x, blockDim.x, nh);
     for (int f = threadIdx.x; f < np * nh; f += blockDim.x, wpk.next()) {
@@ -353,8 +444,12 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_z_c2r(PmeDev pm, long lo
         if (k > 0 && n - k >= nh) c[p * ls + pad16(n - k)] = make_float2(A.x + B.y, B.x - A.y);
     }
     __syncthreads();
-    // the first stage reads c = b and writes a; b is free after it
-    fft_run<true, false>(SmemAcc{c, ls}, RealPairAcc{pm.Q + line0 * n, n, nlb}, a, b, ls, np, ax);
+    if (one) {
+        fft_run_1<true, false>(SmemAcc{a, ls}, RealPairAcc{pm.Q + line0 * n, n, nlb}, a, ls, np, ax);
+    } else {
+        // the first stage reads c = b and writes a; b is free after it
+        fft_run<true, false>(SmemAcc{c, ls}, RealPairAcc{pm.Q + line0 * n, n, nlb}, a, b, ls, np, ax);
+    }
 }
 
 // Strided complex pass: for each outer index o, lines of n = ax.n elements at
@@ -372,7 +467,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_fft_strided(PmeDev pm, int a
     const int i0 = blockIdx.x * tb;
     const int nlb = min(tb, n_inner - i0);
     const StridedAcc g{data + blockIdx.y * os + i0, es};
-    fft_run<INV, true>(g, g, sm, sm + tb * ls, ls, nlb, ax);
+    if (one_buffer(ax, tb)) fft_run_1<INV, true>(g, g, sm, ls, nlb, ax);
+    else fft_run<INV, true>(g, g, sm, sm + tb * ls, ls, nlb, ax);
 }
 
 // Sum of NV doubles over the block, added to dst[slot[c]] by one thread.
@@ -400,7 +496,7 @@ __device__ __forceinline__ void block_add(double (&v)[NV], double* __restrict__ 
 // of each wave vector, kz in (0, K2/2) counted twice for its mirror image),
 // inverse transform, store.
 template <bool EV>
-__global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_x_solve(PmeDev pm, double* __restrict__ acc) {
+__global__ void __launch_bounds__(FFT_THREADS, 4) k_fft_x_solve(PmeDev pm, double* __restrict__ acc) {
     extern __shared__ float2 sm[];
     pdl_wait();
     pdl_trigger();
@@ -428,9 +524,11 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_x_solve(PmeDev pm, doubl
     }
     // forward transform from the spectrum into shared memory (buffer z, the
     // one the last stage does not read), solve there, inverse back
-    float2* z = (ax.nst & 1) ? a : b;
+    const bool one = one_buffer(ax, tb);
+    float2* z = one ? a : ((ax.nst & 1) ? a : b);
     float2* other = z == a ? b : a;
-    fft_run<false, true>(spec, SmemAcc{z, ls}, a, b, ls, nlb, ax);
+    if (one) fft_run_1<false, true>(spec, SmemAcc{z, ls}, z, ls, nlb, ax);
+    else fft_run<false, true>(spec, SmemAcc{z, ls}, a, b, ls, nlb, ax);
     double ev[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     DivWalk wlkx(threadIdx.x, blockDim.x, n);
     for (int f = threadIdx.x; f < nlb * n; f += blockDim.x, wlkx.next()) {
@@ -466,7 +564,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft_x_solve(PmeDev pm, doubl
         z[l * ls + pad16(kx)] = v;
     }
     __syncthreads();
-    fft_run<true, true>(SmemAcc{z, ls}, spec, other, z, ls, nlb, ax);
+    if (one) fft_run_1<true, true>(SmemAcc{z, ls}, spec, z, ls, nlb, ax);
+    else fft_run<true, true>(SmemAcc{z, ls}, spec, other, z, ls, nlb, ax);
     if (EV) {
         // em is the energy of wave vector m together with its mirror -m, which
         // the half spectrum does not hold (of m alone on the planes kz = 0
@@ -825,11 +924,22 @@ __global__ void __launch_bounds__(PME_THREADS) k_excl_ewald(const SysDev* __rest
     }
 }
 
+// Upper bounds (two buffers), for the size check of a mesh.
 size_t strided_smem(int n) { return 2 * (size_t)tile_lines(n) * line_stride(n) * sizeof(float2); }
-// The strided pass of an axis with at most two stages uses one buffer only
-// (global -> shared -> global).
-size_t strided_pass_smem(const FftAxis& ax) { return (ax.nst <= 2 ? 1 : 2) * (size_t)tile_lines(ax.n) * line_stride(ax.n) * sizeof(float2); }
 size_t z_smem(int n) { return 2 * (size_t)z_pairs(n) * line_stride(n) * sizeof(float2); }
+// What each pass launches with: one buffer where every stage has at most one
+// butterfly per thread, and for the strided pass also with at most two
+// stages (global -> shared -> global); else two.
+size_t strided_pass_smem(const FftAxis& ax) {
+    const int nb = (one_buffer(ax, tile_lines(ax.n)) || ax.nst <= 2) ? 1 : 2;
+    return nb * (size_t)tile_lines(ax.n) * line_stride(ax.n) * sizeof(float2);
+}
+size_t x_pass_smem(const FftAxis& ax) {
+    return (one_buffer(ax, tile_lines(ax.n)) ? 1 : 2) * (size_t)tile_lines(ax.n) * line_stride(ax.n) * sizeof(float2);
+}
+size_t z_pass_smem(const FftAxis& ax) {
+    return (one_buffer(ax, z_pairs(ax.n)) ? 1 : 2) * (size_t)z_pairs(ax.n) * line_stride(ax.n) * sizeof(float2);
+}
 
 template <int P>
 cudaError_t launch_spread_p(const PlanLaunch& p, const PmeDev& pm, double* acc, unsigned flags, cudaStream_t st) {
@@ -911,7 +1021,7 @@ cudaError_t launch_pme_fft(const PlanLaunch& p, const PmeDev& pm, double* acc, u
     const bool ev = flags & (NB_F_ENERGY | NB_F_VIRIAL);
     const long long zlines = (long long)pm.K[0] * pm.K[1];
     const unsigned zblocks = (unsigned)((zlines + 2 * z_pairs(pm.K[2]) - 1) / (2 * z_pairs(pm.K[2])));
-    cudaError_t e = launch_pdl(k_fft_z_r2c, zblocks, FFT_THREADS, z_smem(pm.K[2]), st, pm, zlines);
+    cudaError_t e = launch_pdl(k_fft_z_r2c, zblocks, FFT_THREADS, z_pass_smem(pm.ax[2]), st, pm, zlines);
     if (e != cudaSuccess) return e;
     // y pass: a 2D grid (z tiles, x planes)
     const int ty = tile_lines(pm.K[1]);
@@ -930,12 +1040,12 @@ cudaError_t launch_pme_fft(const PlanLaunch& p, const PmeDev& pm, double* acc, u
     if (e != cudaSuccess) return e;
     const int tx = tile_lines(pm.K[0]);
     const unsigned xblocks = (unsigned)(((long long)pm.K[1] * pm.Kzh + tx - 1) / tx);
-    e = ev ? launch_pdl(k_fft_x_solve<true>, xblocks, FFT_THREADS, strided_smem(pm.K[0]), st, pm, acc)
-           : launch_pdl(k_fft_x_solve<false>, xblocks, FFT_THREADS, strided_smem(pm.K[0]), st, pm, acc);
+    e = ev ? launch_pdl(k_fft_x_solve<true>, xblocks, FFT_THREADS, x_pass_smem(pm.ax[0]), st, pm, acc)
+           : launch_pdl(k_fft_x_solve<false>, xblocks, FFT_THREADS, x_pass_smem(pm.ax[0]), st, pm, acc);
     if (e != cudaSuccess) return e;
     e = cudaLaunchKernelEx(&cfg, k_fft_strided<true>, pm, 1, pm.S, pm.Kzh, es_y, os_y);
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_fft_z_c2r, zblocks, FFT_THREADS, z_smem(pm.K[2]), st, pm, zlines);
+    return launch_pdl(k_fft_z_c2r, zblocks, FFT_THREADS, z_pass_smem(pm.ax[2]), st, pm, zlines);
 }
 
 }  // namespace nbgb
