@@ -15,10 +15,15 @@
  *     is pruned on the GPU and reused for many steps);
  *   - a cluster-pair kernel computes M x N interactions per list entry
  *     (nb_forces; Section 3.2).
+ * With Ewald electrostatics the long-range part (smooth particle-mesh Ewald,
+ * which the paper runs next to the pair kernel) is available too
+ * (nb_pme_init, nb_pme_forces, NB_F_PME).  Batches of systems and a serving
+ * engine evaluate many systems per launch (nb_batch_*, nb_server_*).
  * All work runs on one CUDA device; there is no CPU fallback.
  *
  * Units: nm, kJ/mol, elementary charge.  Boxes are rectangular (periodic in
- * x, y and z) and every edge must be at least 2 * rlist.
+ * x, y and z) or triclinic (nb_sys_create_box); every edge must be at least
+ * 2 * rlist.
  *
  * Conventions shared by every call:
  *   - Every call returns an nb_status; none aborts.  NB_OK is 0.  A failing
