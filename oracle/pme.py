@@ -1,7 +1,8 @@
 """Long-range (reciprocal-space) Ewald electrostatics for the oracle.
 
-TEST INFRASTRUCTURE ONLY: the tests are the only callers.  The CUDA library
-neither imports nor calls anything here, and nothing here is shared with it.
+TEST INFRASTRUCTURE ONLY: the tests and the smoke check are the only
+callers.  The CUDA library neither imports nor calls anything here, and
+nothing here is shared with it.
 
 The paper runs the long-range part of the electrostatics with particle-mesh
 Ewald (PME) next to the short-range pair kernel (the multi-level parallelism
