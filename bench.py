@@ -535,7 +535,7 @@ PME_GRID = (256, 256, 256)  # 0.121 nm spacing on the 31 nm box
 PME_ORDER = 4
 
 
-def run_pme(args) -> dict:
+def run_pme(args, grid=None, order=None) -> dict:
     """Long-range part (smooth PME) on the 3,000,000-atom Ewald box, mesh 256^3
     (0.121 nm), cubic B-splines: a step is one nb_pme_forces evaluation
     (mesh clear, spreading, FFT + solve + inverse FFT, gathering, excluded
@@ -556,9 +556,11 @@ def run_pme(args) -> dict:
     from paper_1506_00716_gb300 import autotune
 
     autotune.apply(ctx, "ewald", s.n, gpu=torch.cuda.get_device_name(dev))
+    grid = tuple(grid or getattr(args, "pme_mesh", None) or PME_GRID)
+    order = int(order or getattr(args, "pme_order", None) or PME_ORDER)
     h = nb.nb_sys_create(ctx, p, s.n, s.box)
     nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
-    nb.nb_pme_init(h, PME_GRID, PME_ORDER)
+    nb.nb_pme_init(h, grid, order)
     xq = torch.from_numpy(s.xq()).to(dev)
     ty = torch.from_numpy(s.type).to(dev)
     f = torch.empty((s.n, 3), dtype=torch.float32, device=dev)
@@ -605,8 +607,8 @@ def run_pme(args) -> dict:
     nb.nb_sys_destroy(h)
     nb.nb_ctx_destroy(ctx)
     per = {k: stage[k][0] / max(stage[k][1], 1) for k in ("pme_spread", "pme_fft", "pme_gather", "zero", "final")}
-    nmesh = PME_GRID[0] * PME_GRID[1] * PME_GRID[2]
-    nspec = PME_GRID[0] * PME_GRID[1] * (PME_GRID[2] // 2 + 1)
+    nmesh = grid[0] * grid[1] * grid[2]
+    nspec = grid[0] * grid[1] * (grid[2] // 2 + 1)
     # algorithmic bytes of the five FFT passes: z forward reads the real mesh
     # and writes the half spectrum, y, x (+ solve + inverse) and y each read and
     # write the spectrum once, z inverse reads it and writes the real mesh
@@ -614,21 +616,23 @@ def run_pme(args) -> dict:
     peaks, kind = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = fft_bytes / (per["pme_fft"] * 1e-3) / 1e9
-    spread_atomics = s.n * PME_ORDER ** 3
+    spread_atomics = s.n * order ** 3
     return {
         "metric": "long-range (PME) evaluations/s", "value": 1e3 / wall, "unit": "evals/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall, "higher_is_better": True,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "water box, 3,000,000 atoms, L=31.0 nm, smooth PME, mesh 256^3 (0.121 nm), "
-                               "order 4, beta=3.12 nm^-1; step = nb_pme_forces (forces only) on a built list",
-                   "atoms": s.n, "mesh": list(PME_GRID), "order": PME_ORDER},
+        "config": {"workload": f"water box, 3,000,000 atoms, L=31.0 nm, smooth PME, mesh "
+                               f"{grid[0]}x{grid[1]}x{grid[2]} ({31.0 / grid[0]:.3f} nm), order {order}, "
+                               "beta=3.12 nm^-1; step = nb_pme_forces (forces only) on a built list",
+                   "atoms": s.n, "mesh": list(grid), "order": order},
         "atoms_per_s": s.n / (wall * 1e-3),
         "stage_ms": {k: round(v_, 4) for k, v_ in per.items()},
         "combined_ms": combined, "short_range_ms": short,
         "energies": {"E_rec": energies[0], "E_self": energies[1], "E_excl": energies[2]},
         "fft_roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4),
-                         "traffic": _traffic_per_launch("fft_pme_large", "nb_pme.cu"),
+                         "traffic": (_traffic_per_launch("fft_pme_large", "nb_pme.cu")
+                                     if grid == PME_GRID else None),
                          "kernels": "k_fft_z_r2c, k_fft_strided x2, k_fft_x_solve, k_fft_z_c2r",
                          "algorithmic_bytes": fft_bytes, "peak_kind": kind},
         "spread": {"atomics_per_eval": spread_atomics,
@@ -995,6 +999,8 @@ def main():
     ap.add_argument("--workload", default="mid",
                     choices=["mid", "large", "ensemble", "serve", "dynamic", "shapes", "pme"])
     ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and serving summaries")
+    ap.add_argument("--pme-mesh", type=int, nargs=3, default=None, help="mesh of --workload pme (default 256 256 256)")
+    ap.add_argument("--pme-order", type=int, default=None, help="B-spline order of --workload pme (default 4)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "large" and args.impl == "ours":
