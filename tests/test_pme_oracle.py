@@ -288,3 +288,151 @@ def test_pme_forces_are_minus_energy_gradient():
         # the mesh charges depend on fractional coordinates only, so the PME
         # virial is the exact derivative of the PME energy
         assert dE == pytest.approx(2 * r["virial"][a, a], rel=1e-6, abs=1e-7 * abs(r["energy"]))
+
+
+# ------------------------------------------------------------ triclinic boxes
+
+def _tri_system(x, q, rows, excl=None):
+    rows = np.asarray(rows, dtype=np.float64)
+    assert rows[0, 1] == rows[0, 2] == rows[1, 2] == 0.0
+    s = _system(x, q, np.array([rows[0, 0], rows[1, 1], rows[2, 2]]), excl)
+    s.skew = np.array([rows[1, 0], rows[2, 0], rows[2, 1]])
+    return s
+
+
+def _real_space_lattice(sys, rows, p, r_cut, reach):
+    """Real-space Ewald sum over explicit lattice images n1 a + n2 b + n3 c."""
+    x = sys.x.astype(np.float64)
+    q = sys.q.astype(np.float64)
+    f = p.fcoul / p.eps_r
+    n = x.shape[0]
+    e = 0.0
+    d0 = x[:, None, :] - x[None, :, :]
+    for n1 in range(-reach, reach + 1):
+        for n2 in range(-reach, reach + 1):
+            for n3 in range(-reach, reach + 1):
+                S = n1 * rows[0] + n2 * rows[1] + n3 * rows[2]
+                r = np.sqrt(((d0 + S) ** 2).sum(-1))
+                use = r < r_cut
+                if n1 == n2 == n3 == 0:
+                    use &= ~np.eye(n, dtype=bool)
+                rr = np.where(use, r, 1.0)
+                e += 0.5 * np.where(use, f * q[:, None] * q[None, :] * erfc(p.beta * rr) / rr, 0.0).sum()
+    return e
+
+
+def _fcc_primitive(d):
+    """Rock salt as its two-ion primitive cell: the fcc vectors of cube edge
+    2d, rotated into the lower-triangular box form (rows a, b, c)."""
+    B0 = d * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+    Qm, _ = np.linalg.qr(B0.T)
+    rows = B0 @ Qm
+    if rows[0, 0] < 0:
+        rows[:, 0] *= -1
+        Qm[:, 0] *= -1
+    if rows[1, 1] < 0:
+        rows[:, 1] *= -1
+        Qm[:, 1] *= -1
+    if rows[2, 2] < 0:
+        rows[:, 2] *= -1
+        Qm[:, 2] *= -1
+    rows[np.abs(rows) < 1e-14] = 0.0
+    x = np.array([[0.05, 0.02, 0.03], [0.05 + d, 0.02, 0.03]]) @ Qm
+    return rows, x
+
+
+def test_madelung_constant_in_a_triclinic_cell():
+    d = 0.282
+    rows, x = _fcc_primitive(d)
+    sys = _tri_system(x, [1.0, -1.0], rows)
+    p = wb.Params(coul=wb.COUL_EWALD, beta=3.12)
+    e_real = _real_space_lattice(sys, rows, p, r_cut=2.0, reach=10)
+    e_rec = opme.ewald_reciprocal_direct(sys, p, kmax=8)["energy"]
+    e_self = opme.ewald_self(sys, p)
+    assert e_real + e_rec + e_self == pytest.approx(-MADELUNG_NACL * p.fcoul / d, rel=1e-10)
+
+
+def test_reciprocal_sum_depends_on_the_lattice_not_the_basis():
+    rng = np.random.default_rng(12)
+    L = 1.4
+    x = rng.uniform(0, L, size=(12, 3))
+    q = rng.normal(size=12)
+    q -= q.mean()
+    p = wb.Params(coul=wb.COUL_EWALD, beta=3.12)
+    cube = _system(x, q, L)
+    sheared = _tri_system(x, q, [[L, 0, 0], [L, L, 0], [L, L, L]])  # the same cubic lattice
+    e0 = opme.ewald_reciprocal_direct(cube, p, kmax=10)
+    e1 = opme.ewald_reciprocal_direct(sheared, p, kmax=24)
+    assert e1["energy"] == pytest.approx(e0["energy"], rel=1e-11)
+    assert np.allclose(e1["forces"], e0["forces"], rtol=0, atol=1e-9 * np.abs(e0["forces"]).max())
+    assert np.allclose(e1["virial"], e0["virial"], rtol=0, atol=1e-9 * np.abs(e0["virial"]).max())
+
+
+def _rd_small():
+    rd = wb.rhombic_dodecahedron_box(80, seed=9)
+    return rd
+
+
+def test_triclinic_pme_converges_to_the_exact_sum():
+    s = _rd_small()
+    p = wb.Params(coul=wb.COUL_EWALD, beta=3.12)
+    ref = opme.ewald_reciprocal_direct(s, p, kmax=12)
+    fref = np.sqrt((ref["forces"] ** 2).mean())
+    errs = []
+    for K, order in ((16, 4), (24, 6), (40, 8)):
+        r = opme.pme(s, p, grid=(K, K, K), order=order)
+        errs.append((abs(r["energy"] - ref["energy"]) / abs(ref["energy"]),
+                     np.sqrt(((r["forces"] - ref["forces"]) ** 2).mean()) / fref,
+                     np.abs(r["virial"] - ref["virial"]).max() / np.abs(ref["virial"]).max()))
+    errs = np.array(errs)
+    assert np.all(np.diff(errs[:, 1]) < 0), errs
+    assert errs[-1, 0] < 1e-7 and errs[-1, 1] < 1e-5 and errs[-1, 2] < 1e-5, errs
+
+
+def _tri_copy(s, x, rows):
+    return _tri_system(x, s.q, rows, (s.excl_index, s.excl_atoms))
+
+
+def test_triclinic_pme_forces_and_virial_are_energy_derivatives():
+    s = _rd_small()
+    p = wb.Params(coul=wb.COUL_EWALD, beta=3.12)
+    rows = opme._box_rows(s)
+    x = s.x.astype(np.float64)
+    grid = (14, 14, 12)
+    r = opme.pme(s, p, grid=grid, order=6)
+    h = 1e-6
+    rng = np.random.default_rng(4)
+    for a in rng.choice(s.n, size=4, replace=False):
+        for dcomp in range(3):
+            es = []
+            for sgn in (+1, -1):
+                x2 = x.copy()
+                x2[a, dcomp] += sgn * h
+                es.append(opme.pme(_tri_copy(s, x2, rows), p, grid=grid, order=6)["energy"])
+            assert -(es[0] - es[1]) / (2 * h) == pytest.approx(r["forces"][a, dcomp], rel=1e-6, abs=1e-5)
+    # x_a -> x_a + eps x_b for the atoms and the box rows, keeping the box
+    # lower-triangular (b >= a): 2 Xi_ab = dE/deps
+    for a, b in ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)):
+        es = []
+        for sgn in (+1, -1):
+            D = np.eye(3)
+            D[a, b] += sgn * h
+            es.append(opme.pme(_tri_copy(s, x @ D.T, rows @ D.T), p, grid=grid, order=6)["energy"])
+        dE = (es[0] - es[1]) / (2 * h)
+        assert dE == pytest.approx(2 * r["virial"][a, b], rel=1e-6, abs=1e-7 * abs(r["energy"]))
+
+
+def test_triclinic_exclusions_use_the_minimum_image():
+    s = _rd_small()
+    p = wb.Params(coul=wb.COUL_EWALD, beta=3.12)
+    ex = opme.ewald_exclusions(s, p)
+    # the same molecules, each moved whole into the cell: nothing changes
+    rows = opme._box_rows(s)
+    x = s.x.astype(np.float64).reshape(-1, 3, 3)
+    shift = np.array([1, -1, 0]) @ rows
+    x2 = x.copy()
+    x2[::2] += shift              # every other molecule by a lattice vector
+    x2[1::3, 1] += rows[2]        # and some single atoms by another
+    ex2 = opme.ewald_exclusions(_tri_copy(s, x2.reshape(-1, 3), rows), p)
+    assert ex2["energy"] == pytest.approx(ex["energy"], rel=1e-12)
+    assert np.allclose(ex2["forces"], ex["forces"], rtol=0, atol=1e-9 * np.abs(ex["forces"]).max())
