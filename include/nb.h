@@ -463,17 +463,21 @@ nb_status nb_eval_noalloc(const nb_params *params, int natoms, const double box[
  * total electrostatic energy is then the Ewald sum with conducting
  * boundary conditions.
  *
- * nb_pme_init: enable the long-range part for an NB_COUL_EWALD system with
- * a rectangular box (nb_sys_create), or change its mesh; allocates the mesh
- * (4 K_x K_y K_z + 8 K_x K_y (K_z / 2 + 1) bytes, counted against the
- * budget).
+ * nb_pme_init: enable the long-range part for an NB_COUL_EWALD system, in a
+ * rectangular (nb_sys_create) or triclinic (nb_sys_create_box) cell, or
+ * change its mesh; allocates the mesh (4 K_x K_y K_z + 8 K_x K_y (K_z / 2 +
+ * 1) bytes, counted against the budget).  In a triclinic cell with rows a,
+ * b, c the mesh coordinates are u = x B^-1 diag(K) and the wave vectors m =
+ * k B^-T (smooth PME in a general periodic cell), V = ax by cz; the
+ * excluded pairs take the image reached by reducing z by c, then y by b,
+ * then x by a, which is the minimum image for pairs closer than half the
+ * shortest cell height (the molecules' own exclusions).
  *   grid[3]  mesh points along x, y, z: each 8..1024, a product of the
  *            primes 2, 3 and 5 only, with K_d >= 2 p
  *   order    B-spline order p: 4 (cubic, the usual choice), 6 or 8.  Odd
  *            orders are not offered: their B-spline modulus has a pole at
  *            k = K/2 for even K.
- * NB_ERR_ARG for a bad mesh or order or a non-Ewald system, NB_ERR_BOX for
- * a triclinic system.
+ * NB_ERR_ARG for a bad mesh or order or a non-Ewald system.
  */
 typedef struct {
     int grid[3];
@@ -490,9 +494,10 @@ nb_status nb_pme_init(nb_sys *sys, const nb_pme_params *pme);
  *   virial  9 doubles (host or device): Xi_rec + Xi_excl; NULL allowed
  *   flags   NB_F_ENERGY | NB_F_VIRIAL
  * Needs nb_pme_init and a pair list (nb_pairlist_build: the atoms are taken
- * in the grid's sorted order).  Mesh, transforms and forces are float32
- * (fractional mesh coordinates float64); energies, virial and the
- * excluded-pair terms float64.
+ * in the grid's sorted order).  Mesh, transforms and forces are float32;
+ * the mesh coordinates and the excluded-pair terms are formed as unevaluated
+ * float sums (hi + lo, about 48 bits), energies and virial accumulated in
+ * float64.
  *
  * nb_forces with NB_F_PME adds the long-range part to the short-range
  * result: the forces are the sum, E_Coulomb = real space + E_rec + E_self +

@@ -1335,14 +1335,12 @@ nb_status nb_batch_poll(nb_batch* batch, unsigned long long ticket, long long ti
 nb_status nb_pme_init(nb_sys* sys, const nb_pme_params* pp) {
     if (!sys || !pp) return fail(NB_ERR_ARG, "sys / pme is NULL");
     if (sys->p.coul != NB_COUL_EWALD) return fail(NB_ERR_ARG, "the long-range part needs NB_COUL_EWALD");
-    if (sys->h.T[0] != 0.f || sys->h.T[1] != 0.f || sys->h.T[2] != 0.f)
-        return fail(NB_ERR_BOX, "the long-range part supports rectangular boxes only");
     const int p = pp->order;
     if (p != 4 && p != 6 && p != 8) return fail(NB_ERR_ARG, "PME order must be 4, 6 or 8");
-    FftAxis ax[3];
+    FftAxis axis[3];
     for (int d = 0; d < 3; ++d) {
         const int K = pp->grid[d];
-        if (K < 8 || K > 1024 || K < 2 * p || !fft_radices(K, &ax[d]))
+        if (K < 8 || K > 1024 || K < 2 * p || !fft_radices(K, &axis[d]))
             return fail(NB_ERR_ARG, "each PME mesh size must be in 8..1024, >= 2 * order, with prime factors 2, 3, 5");
     }
     if ((size_t)pme_smem_need(pp->grid) > 227 * 1024) return fail(NB_ERR_ARG, "PME mesh too large");
@@ -1370,23 +1368,36 @@ nb_status nb_pme_init(nb_sys* sys, const nb_pme_params* pp) {
     char* base = (char*)ph->block;
     PmeDev& pm = ph->dev;
     const double f = sys->p.fcoul / sys->p.eps_r, beta = sys->p.ewald_beta;
-    const double V = sys->box[0] * sys->box[1] * sys->box[2];
+    // the cell the device uses (float32 box rows a = (ax,0,0), b = (bx,by,0),
+    // c = (cx,cy,cz)) and its inverse R = B^-1, lower-triangular
+    const double ax = sys->h.L[0], by = sys->h.L[1], cz = sys->h.L[2];
+    const double bx = sys->h.T[0], cx = sys->h.T[1], cy = sys->h.T[2];
+    const bool tri = bx != 0.0 || cx != 0.0 || cy != 0.0;
+    const double R10 = -bx / (ax * by), R21 = -cy / (by * cz), R20 = (bx * cy - by * cx) / (ax * by * cz);
+    const double V = ax * by * cz;
     std::vector<float2> host(off / 8, make_float2(0.f, 0.f));
+    const double Ld[3] = {ax, by, cz};
     for (int d = 0; d < 3; ++d) {
         const int K = pp->grid[d];
         pm.K[d] = K;
-        pm.kl[d] = K / sys->box[d];
-        pm.ax[d] = ax[d];
+        pm.kl[d] = K / Ld[d];
+        pm.ax[d] = axis[d];
         pm.ax[d].tw = (const float2*)(base + o_tw[d]);
         pm.tab[d] = (const float2*)(base + o_tab[d]);
         const std::vector<double> bm = bspline_moduli(K, p);
         for (int k = 0; k < K; ++k) {
-            const double m = (k <= K / 2 ? k : k - K) / sys->box[d];
-            host[o_tab[d] / 8 + k] = make_float2((float)m, (float)(bm[k] * std::exp(-M_PI * M_PI * m * m / (beta * beta))));
+            const double ks = (k <= K / 2 ? k : k - K);
+            const double m = ks / Ld[d];
+            host[o_tab[d] / 8 + k] =
+                tri ? make_float2((float)ks, (float)bm[k])
+                    : make_float2((float)m, (float)(bm[k] * std::exp(-M_PI * M_PI * m * m / (beta * beta))));
             const double a = -2.0 * M_PI * (double)k / K;
             host[o_tw[d] / 8 + k] = make_float2((float)std::cos(a), (float)std::sin(a));
         }
     }
+    pm.tri = tri ? 1 : 0;
+    const double mo[3] = {R10 * pp->grid[0], R20 * pp->grid[0], R21 * pp->grid[1]};
+    const double rdg[3] = {1.0 / ax, 1.0 / by, 1.0 / cz}, ro[3] = {R10, R20, R21};
     pm.Kzh = Kzh;
     pm.order = p;
     pm.S = (float2*)(base + o_S);
@@ -1400,7 +1411,12 @@ nb_status nb_pme_init(nb_sys* sys, const nb_pme_params* pp) {
         h = (float)v;
         l = (float)(v - (double)h);
     };
-    for (int d = 0; d < 3; ++d) split(pm.kl[d], pm.kl_h[d], pm.kl_l[d]);
+    for (int d = 0; d < 3; ++d) {
+        split(pm.kl[d], pm.kl_h[d], pm.kl_l[d]);
+        split(mo[d], pm.mo_h[d], pm.mo_l[d]);
+        pm.rd[d] = (float)rdg[d];
+        pm.ro[d] = (float)ro[d];
+    }
     split(f, pm.fq_h, pm.fq_l);
     split(2.0 * beta / std::sqrt(M_PI), pm.ke_h, pm.ke_l);
     split(4.0 / 3.0 * beta * beta * beta / std::sqrt(M_PI), pm.kf_h, pm.kf_l);

@@ -156,11 +156,22 @@ struct PmeDev {
     int order;         // B-spline order p (4, 6 or 8)
     double kl[3];      // K_d / L_d: mesh units per nm
     float kl_h[3], kl_l[3];  // the same as an unevaluated float sum hi + lo
+    // Triclinic cell (box rows a = (ax,0,0), b = (bx,by,0), c = (cx,cy,cz)):
+    // the mesh coordinates are u = x M, M = B^-1 diag(K), lower-triangular
+    // with diagonal K_d / L_d (kl) and the off-diagonal entries M10, M20, M21
+    // here as hi + lo; wave vectors are m = k R^T with R = B^-1 (diagonal
+    // 1 / L_d, off-diagonal R10, R20, R21).  All off-diagonals are zero in a
+    // rectangular box.
+    int tri;
+    float mo_h[3], mo_l[3];  // M10, M20, M21
+    float rd[3], ro[3];      // R00, R11, R22 and R10, R20, R21
     float* Q;          // [K0 K1 K2] charges spread on the mesh, then the potential
     float2* S;         // [K0 K1 Kzh] half spectrum
     FftAxis ax[3];
-    // per mesh index k of axis d: (m_d, |b_d(k)|^2 exp(-pi^2 m_d^2 / beta^2)),
-    // m_d = k' / L_d with k' the signed frequency
+    // per mesh index k of axis d, with k' its signed frequency (k' = +K/2 at
+    // the index K/2 of an even mesh): rectangular cell, (m_d, |b_d(k)|^2
+    // exp(-pi^2 m_d^2 / beta^2)) with m_d = k' / L_d; triclinic cell, (k',
+    // |b_d(k)|^2), the exponential then taken per wave vector
     const float2* tab[3];
     float cpre;        // f / (pi V)
     float pi2_b2;      // pi^2 / beta^2

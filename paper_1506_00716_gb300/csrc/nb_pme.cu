@@ -491,6 +491,59 @@ __device__ __forceinline__ void block_add(double (&v)[NV], double* __restrict__ 
     }
 }
 
+// The solve at one stored point of a triclinic cell's half spectrum.  With k'
+// the signed indices, m = k R^T and G(k) = |b(k)|^2 f exp(-pi^2 m^2 / beta^2)
+// / (pi V m^2).  The point's mirror -k (indices mod K, a Nyquist index its
+// own mirror) has m' = k'' R^T, k''_d = k'_d at a Nyquist index and -k'_d
+// otherwise, and in a skewed cell G(mirror) may differ from G(k).  The
+// spectrum is multiplied by (G(k) + G(mirror)) / 2, which keeps it Hermitian
+// and gives the real part of the full inverse transform of G F.  Energy and
+// virial take the point with its own m and, inside (0, K2/2) in kz, its
+// unstored mirror with m'; a point on the planes kz = 0, K2/2 counts alone
+// (its mirror is stored too).
+template <bool EV>
+__device__ __forceinline__ void tri_solve(const PmeDev& pm, float2 tx, float4 ln, bool nx, bool ny, bool plane,
+                                          float2* __restrict__ z, double (&ev)[7]) {
+    const float k0 = tx.x, k1 = ln.x, k2 = ln.y;
+    const float bb = tx.y * ln.w;
+    const float j0 = nx ? k0 : -k0, j1 = ny ? k1 : -k1, j2 = plane ? k2 : -k2;
+    const float ma = k0 * pm.rd[0], mb = fmaf(k0, pm.ro[0], k1 * pm.rd[1]),
+                mc = fmaf(k0, pm.ro[1], fmaf(k1, pm.ro[2], k2 * pm.rd[2]));
+    const float na = j0 * pm.rd[0], nb = fmaf(j0, pm.ro[0], j1 * pm.rd[1]),
+                nc = fmaf(j0, pm.ro[1], fmaf(j1, pm.ro[2], j2 * pm.rd[2]));
+    const float m2 = ma * ma + mb * mb + mc * mc, n2 = na * na + nb * nb + nc * nc;
+    const float g1 = m2 > 0.f ? pm.cpre * bb * expf(-pm.pi2_b2 * m2) / m2 : 0.f;
+    const float g2 = n2 > 0.f ? pm.cpre * bb * expf(-pm.pi2_b2 * n2) / n2 : 0.f;
+    float2 v = *z;
+    if (EV && m2 > 0.f) {
+        const float f2 = v.x * v.x + v.y * v.y;
+        const double e1 = (double)(0.5f * g1 * f2);
+        const float s1 = 2.f * (1.f + pm.pi2_b2 * m2) / m2;
+        ev[0] += e1;
+        ev[1] += e1 * (double)(1.f - s1 * ma * ma);
+        ev[2] += e1 * (double)(1.f - s1 * mb * mb);
+        ev[3] += e1 * (double)(1.f - s1 * mc * mc);
+        ev[4] += e1 * (double)(-s1 * ma * mb);
+        ev[5] += e1 * (double)(-s1 * ma * mc);
+        ev[6] += e1 * (double)(-s1 * mb * mc);
+        if (!plane) {
+            const double e2 = (double)(0.5f * g2 * f2);
+            const float s2 = 2.f * (1.f + pm.pi2_b2 * n2) / n2;
+            ev[0] += e2;
+            ev[1] += e2 * (double)(1.f - s2 * na * na);
+            ev[2] += e2 * (double)(1.f - s2 * nb * nb);
+            ev[3] += e2 * (double)(1.f - s2 * nc * nc);
+            ev[4] += e2 * (double)(-s2 * na * nb);
+            ev[5] += e2 * (double)(-s2 * na * nc);
+            ev[6] += e2 * (double)(-s2 * nb * nc);
+        }
+    }
+    const float gb = 0.5f * (g1 + g2);
+    v.x *= gb;
+    v.y *= gb;
+    *z = v;
+}
+
 // x pass with the solve: complete x lines of the spectrum (i = ky * Kzh + kz),
 // forward transform, multiplication by G(m) (with EV, the energy and virial
 // of each wave vector, kz in (0, K2/2) counted twice for its mirror image),
@@ -514,11 +567,13 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_fft_x_solve(PmeDev pm, doubl
     __shared__ float4 s_line[16];
     __shared__ float s_wz[16];
     __shared__ bool s_nyq[16];
+    // (In a triclinic cell the tables hold signed frequencies, and the line
+    // record is (k_y', k_z', 0, |b_y|^2 |b_z|^2).)
     if (threadIdx.x < nlb) {
         const int i = i0 + threadIdx.x;
         const int ky = i / pm.Kzh, kz = i - ky * pm.Kzh;
         const float2 ty = __ldg(pm.tab[1] + ky), tz = __ldg(pm.tab[2] + kz);
-        s_line[threadIdx.x] = make_float4(ty.x, tz.x, ty.x * ty.x + tz.x * tz.x, ty.y * tz.y);
+        s_line[threadIdx.x] = make_float4(ty.x, tz.x, pm.tri ? 0.f : ty.x * ty.x + tz.x * tz.x, ty.y * tz.y);
         s_wz[threadIdx.x] = (kz == 0 || 2 * kz == pm.K[2]) ? 0.5f : 1.f;
         s_nyq[threadIdx.x] = 2 * ky == pm.K[1];
     }
@@ -535,6 +590,10 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_fft_x_solve(PmeDev pm, doubl
         const int l = wlkx.q, kx = wlkx.r;
         const float2 tx = __ldg(pm.tab[0] + kx);
         const float4 ln = s_line[l];
+        if (pm.tri) {
+            tri_solve<EV>(pm, tx, ln, 2 * kx == n, s_nyq[l], s_wz[l] != 1.f, z + l * ls + pad16(kx), ev);
+            continue;
+        }
         const float m2 = tx.x * tx.x + ln.z;
         const float g = m2 > 0.f ? pm.cpre * (tx.y * ln.w) / m2 : 0.f;
         float2 v = z[l * ls + pad16(kx)];
@@ -629,6 +688,49 @@ __device__ __forceinline__ void mesh_coord(float x, float klh, float kll, int K,
 
 __device__ __forceinline__ int wrap_down(int i, int K) { return i < 0 ? i + K : i; }
 
+// Mesh coordinate of dimension d in a triclinic cell, u_d = sum_a x_a M[a][d]
+// (M lower-triangular: u_0 = x M00 + y M10 + z M20, u_1 = y M11 + z M21,
+// u_2 = z M22), each product exact as hi + lo and the terms summed
+// error-free before the fractional part is taken (as mesh_coord does for one
+// term).
+__device__ __forceinline__ void mesh_coord_tri(const float4& xq, int d, const PmeDev& pm, int& base, float& w) {
+    const float xs[3] = {xq.x, xq.y, xq.z};
+    const float x0 = d == 0 ? xs[0] : (d == 1 ? xs[1] : xs[2]);
+    const float dh = d == 0 ? pm.kl_h[0] : (d == 1 ? pm.kl_h[1] : pm.kl_h[2]);
+    const float dl = d == 0 ? pm.kl_l[0] : (d == 1 ? pm.kl_l[1] : pm.kl_l[2]);
+    float uh, ue;
+    two_prod(x0, dh, uh, ue);
+    float ul = fmaf(x0, dl, ue);
+    // off-diagonal terms: d = 0 takes y M10 and z M20, d = 1 takes z M21
+    const int nt = d == 0 ? 2 : (d == 1 ? 1 : 0);
+    for (int t = 0; t < nt; ++t) {
+        const float xv = (d == 0 && t == 0) ? xs[1] : xs[2];
+        const int mi = d == 0 ? t : 2;
+        const float mh = mi == 0 ? pm.mo_h[0] : (mi == 1 ? pm.mo_h[1] : pm.mo_h[2]);
+        const float ml = mi == 0 ? pm.mo_l[0] : (mi == 1 ? pm.mo_l[1] : pm.mo_l[2]);
+        float ph, pe, sh, se;
+        two_prod(xv, mh, ph, pe);
+        two_sum(uh, ph, sh, se);
+        uh = sh;
+        ul += se + fmaf(xv, ml, pe);
+    }
+    float hi, lo;
+    fast_two_sum(uh, ul, hi, lo);
+    float fl = floorf(hi);
+    float fr = (hi - fl) + lo;
+    if (fr < 0.f) {
+        fr += 1.f;
+        fl -= 1.f;
+    } else if (fr >= 1.f) {
+        fr -= 1.f;
+        fl += 1.f;
+    }
+    w = fr;
+    const int K = d == 0 ? pm.K[0] : (d == 1 ? pm.K[1] : pm.K[2]);
+    const int b = (int)fl % K;
+    base = b < 0 ? b + K : b;
+}
+
 // Lanes per atom of the spread and gather kernels.
 __host__ __device__ constexpr int pme_lanes(int P) { return P <= 4 ? 4 : 8; }
 
@@ -660,7 +762,8 @@ __device__ __forceinline__ void spline_tile(const SysDev& d, const PmeDev& pm, i
         const int K = dim == 0 ? pm.K[0] : (dim == 1 ? pm.K[1] : pm.K[2]);
         int b;
         float w;
-        mesh_coord(x, klh, kll, K, b, w);
+        if (pm.tri) mesh_coord_tri(xq, dim, pm, b, w);
+        else mesh_coord(x, klh, kll, K, b, w);
         float th[P], dth[P];
         bspline_weights<P, DERIV>(w, th, dth);
 #pragma unroll
@@ -753,9 +856,12 @@ __global__ void __launch_bounds__(PME_THREADS) k_pme_gather(const SysDev* __rest
             sy = fmaf(st.w[at][0][a], ry, sy);   // sum th_x dth_y phi
             sz = fmaf(st.w[at][0][a], rx, sz);   // sum th_x th_y phi
         }
-        fx = -q * pm.kl_h[0] * st.w[at][2][c] * sx;
-        fy = -q * pm.kl_h[1] * st.w[at][2][c] * sy;
-        fz = -q * pm.kl_h[2] * st.dw[at][2][c] * sz;
+        // F = -q (dE/du) M^T with M lower-triangular (diagonal K_d / L_d,
+        // off-diagonals zero in a rectangular cell)
+        const float g0 = st.w[at][2][c] * sx, g1 = st.w[at][2][c] * sy, g2 = st.dw[at][2][c] * sz;
+        fx = -q * (pm.kl_h[0] * g0);
+        fy = -q * fmaf(pm.mo_h[0], g0, pm.kl_h[1] * g1);
+        fz = -q * fmaf(pm.mo_h[1], g0, fmaf(pm.mo_h[2], g1, pm.kl_h[2] * g2));
     }
 #pragma unroll
     for (int off = LPA / 2; off > 0; off >>= 1) {
@@ -816,6 +922,14 @@ __device__ __forceinline__ float excl_series_h(float y) {
     return y * t;
 }
 
+// (h, l) -= v for a double-float and a float v, error-free but for the
+// rounding of the low part
+__device__ __forceinline__ void sub_df(float& h, float& l, float v) {
+    float t, e;
+    two_sum(h, -v, t, e);
+    fast_two_sum(t, e + l, h, l);
+}
+
 // a + b for double-floats (hi, lo), renormalised
 __device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& sh, float& sl) {
     float s, e;
@@ -838,6 +952,7 @@ __global__ void __launch_bounds__(PME_THREADS) k_excl_ewald(const SysDev* __rest
         const int sa = d.iperm[a];
         const float4 xa = d.xq_s[sa];
         const float L[3] = {d.L[0], d.L[1], d.L[2]};
+        const float T[3] = {d.T[0], d.T[1], d.T[2]};  // bx, cx, cy
         const float iL[3] = {1.f / d.L[0], 1.f / d.L[1], 1.f / d.L[2]};
         float fh[3] = {0.f, 0.f, 0.f}, fl[3] = {0.f, 0.f, 0.f};
         for (int k = d.excl_index[a]; k < d.excl_index[a + 1]; ++k) {
@@ -846,19 +961,26 @@ __global__ void __launch_bounds__(PME_THREADS) k_excl_ewald(const SysDev* __rest
             const int sb = d.iperm[b];
             const float4 xb = d.xq_s[sb];
             if (xa.w == 0.f || xb.w == 0.f) continue;
-            // d = x_a - x_b - s L exactly as hi + lo
+            // d = x_a - x_b minus lattice vectors, exactly as hi + lo: z by c,
+            // then y by b, then x by a (the c and b rows carry the cell's
+            // off-diagonal components cx, cy, bx, zero in a rectangular box)
             const float xav[3] = {xa.x, xa.y, xa.z}, xbv[3] = {xb.x, xb.y, xb.z};
             float dh[3], dl[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                two_sum(xav[c], -xbv[c], dh[c], dl[c]);
-                const float sh = rintf(dh[c] * iL[c]);
-                if (sh != 0.f) {
-                    float t, e;
-                    two_sum(dh[c], -sh * L[c], t, e);
-                    fast_two_sum(t, e + dl[c], dh[c], dl[c]);
-                }
+            for (int c = 0; c < 3; ++c) two_sum(xav[c], -xbv[c], dh[c], dl[c]);
+            const float sz = rintf(dh[2] * iL[2]);
+            if (sz != 0.f) {
+                sub_df(dh[2], dl[2], sz * L[2]);
+                if (T[2] != 0.f) sub_df(dh[1], dl[1], sz * T[2]);
+                if (T[1] != 0.f) sub_df(dh[0], dl[0], sz * T[1]);
             }
+            const float sy = rintf(dh[1] * iL[1]);
+            if (sy != 0.f) {
+                sub_df(dh[1], dl[1], sy * L[1]);
+                if (T[0] != 0.f) sub_df(dh[0], dl[0], sy * T[0]);
+            }
+            const float sx = rintf(dh[0] * iL[0]);
+            if (sx != 0.f) sub_df(dh[0], dl[0], sx * L[0]);
             const float r2 = dh[0] * dh[0] + dh[1] * dh[1] + dh[2] * dh[2];
             const float y = pm.beta2 * r2;
             // f qi qj as hi + lo

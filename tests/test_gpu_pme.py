@@ -10,8 +10,8 @@ and each part carries the error of its own arithmetic (the float32 mesh and
 transforms: a few 1e-7 of the reciprocal virial's norm), so the bound of the
 sum is the sum of the parts' bounds.  Meshes cover every radix of the
 transform (16, 4, 2, 3, 5), one-stage and many-stage transforms, odd mesh
-sizes (an odd z length and an odd number of z lines), ragged transform tiles
-and all three spline orders.
+sizes (an odd z length and an odd number of z lines), ragged transform tiles,
+all three spline orders, and triclinic cells (rhombic dodecahedra).
 """
 import numpy as np
 import pytest
@@ -47,7 +47,7 @@ BOXES = {"small": lambda: wb.small_box(seed=1), "mid": lambda: wb.mid_box(seed=2
 
 
 def _system(ctx, s, p, grid, order):
-    h = nb.nb_sys_create(ctx, p, s.n, s.box)
+    h = nb.nb_sys_create(ctx, p, s.n, s.box, getattr(s, "skew", None))
     nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
     nb.nb_grid_put(h, np.ascontiguousarray(s.xq()), np.ascontiguousarray(s.type))
     nb.nb_pairlist_build(h)
@@ -118,6 +118,47 @@ def test_far_excluded_pairs(ctx):
     s2.excl_index, s2.excl_atoms = idx, at
     f, e, v = _gpu_lr(ctx, s2, p, (24, 24, 24), 4)
     _check(f, e, v, *_oracle_lr(s2, p, (24, 24, 24), 4))
+
+
+TRI = {"rd_small": lambda: wb.rhombic_dodecahedron_box(648, seed=5),    # 2,100 atoms, d = 3.11 nm
+       "rd_mid": lambda: wb.rhombic_dodecahedron_box(7744, seed=6)}    # 23,232 atoms, d = 6.83 nm
+
+
+@pytest.mark.parametrize("name,grid,order", [
+    ("rd_small", (24, 30, 18), 4),   # even meshes: Nyquist mirrors with their own G in the skewed cell
+    ("rd_small", (16, 20, 12), 6),   # coarse, so that those terms matter
+    ("rd_small", (25, 27, 15), 4),   # odd sizes: no Nyquist index
+    ("rd_mid", (60, 60, 40), 4),
+])
+def test_triclinic_long_range_matches_oracle(ctx, name, grid, order):
+    """Rhombic dodecahedra (box rows a = (d,0,0), b = (0,d,0),
+    c = (d/2, d/2, d sqrt(2)/2))."""
+    s = TRI[name]()
+    p = wb.params_ewald()
+    f, e, v = _gpu_lr(ctx, s, p, grid, order)
+    _check(f, e, v, *_oracle_lr(s, p, grid, order))
+
+
+def test_triclinic_combined_with_short_range(ctx):
+    s = TRI["rd_small"]()
+    p = wb.params_ewald()
+    grid = (24, 30, 18)
+    h = _system(ctx, s, p, grid, 4)
+    try:
+        f = np.zeros((s.n, 3), dtype=np.float32)
+        e = np.zeros(2)
+        v = np.zeros(9)
+        nb.nb_forces(h, None, f, e, v, EV | nb.NB_F_PME)
+    finally:
+        nb.nb_sys_destroy(h)
+    lf, le, lv, lscale = _oracle_lr(s, p, grid, 4)
+    ev = oracle.energy_virial(s, p)
+    rf = oracle.forces(s, p) + lf
+    assert rel_rms(f, rf) <= F_TOL, rel_rms(f, rf)
+    e_c = ev["e_coul"] + le.sum()
+    assert abs(e[1] - e_c) <= E_TOL * (abs(ev["e_coul"]) + np.abs(le).sum())
+    rv = ev["virial"] + lv
+    assert np.abs(v.reshape(3, 3) - rv).max() <= V_TOL * (np.linalg.norm(ev["virial"]) + lscale)
 
 
 def test_forces_only_flags(ctx):
@@ -248,14 +289,6 @@ def test_validation(ctx):
         assert ei.value.status == 1
     finally:
         nb.nb_sys_destroy(hr)
-    rd = wb.rhombic_dodecahedron_box(648, seed=5)
-    ht = nb.nb_sys_create(ctx, p, rd.n, rd.box, rd.skew)
-    try:
-        with pytest.raises(nb.NbError) as ei:
-            nb.nb_pme_init(ht, (24, 24, 24), 4)
-        assert ei.value.status == 2
-    finally:
-        nb.nb_sys_destroy(ht)
 
 
 def test_full_size_3M_atoms(ctx):
