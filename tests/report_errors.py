@@ -2,7 +2,8 @@
 
 Not a test: a report, run on a GPU machine after `__graft_entry__.build()`:
 
-    python tests/report_errors.py
+    python tests/report_errors.py          # both tables
+    python tests/report_errors.py --pme    # the long-range table only
 
 Per workload it evaluates through the C ABI and prints RMS(dF)/RMS(F), the
 relative errors of E_LJ and E_C, the largest virial component error relative to
@@ -156,9 +157,12 @@ def pme_rows(gpu):
              ("small (1,944 atoms)", wb.small_box(seed=1), (32, 30, 20), 8, None),
              ("mid (24,000 atoms)", wb.mid_box(seed=2), (54, 50, 60), 4, None),
              ("mid (24,000 atoms)", wb.mid_box(seed=2), (64, 64, 64), 6, None),
+             ("rhombic dodecahedron (2,100 atoms)", wb.rhombic_dodecahedron_box(648, seed=5), (24, 30, 18), 4, None),
+             ("rhombic dodecahedron (2,100 atoms)", wb.rhombic_dodecahedron_box(648, seed=5), (16, 20, 12), 6, None),
+             ("rhombic dodecahedron (23,232 atoms)", wb.rhombic_dodecahedron_box(7744, seed=6), (60, 60, 40), 4, None),
              ("large (3,000,000 atoms), 192 sampled forces", wb.large_box(seed=3), (256, 256, 256), 4, 192)]
     for name, s, grid, order, nsel in cases:
-        h = nb.nb_sys_create(ctx, p, s.n, s.box)
+        h = nb.nb_sys_create(ctx, p, s.n, s.box, getattr(s, "skew", None))
         try:
             nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
             nb.nb_grid_put(h, s.xq(), s.type)
@@ -187,4 +191,7 @@ def pme_rows(gpu):
 
 
 if __name__ == "__main__":
-    main()
+    if "--pme" in sys.argv[1:]:
+        print("\n".join(pme_rows(None)))
+    else:
+        main()
