@@ -42,11 +42,12 @@ METRIC = "nonbonded pair interactions/s"
 UNIT = "pairs/s"
 EVALS_PER_STEP = 10
 SIGMA = 0.005
-# FP32-pipe instructions (FADD, FMUL, FFMA: one each) per evaluated atom-pair
+# FP32 operations (FADD, FMUL, FFMA: one each; the paired FADD2, FMUL2, FFMA2
+# instructions the kernel issues count one per half) per evaluated atom-pair
 # slot in the force kernel's pair code, by (coulomb, virial), counted from the
 # source; and the same code's flops (FFMA = 2).  The FP32-pipe fraction is the
-# instruction rate over SMs x 128 FP32 lanes x SM clock.
-INST_PER_SLOT = {("rf", False): 26, ("rf", True): 32, ("ewald", False): 43, ("ewald", True): 49}
+# operation rate over SMs x 128 FP32 lanes x SM clock.
+OPS_PER_SLOT = {("rf", False): 26, ("rf", True): 32, ("ewald", False): 43, ("ewald", True): 49}
 FLOPS_PER_SLOT = {("rf", False): 30, ("rf", True): 42, ("ewald", False): 56, ("ewald", True): 68}
 # kernels launched per timed stage (nb_ctx_timing)
 KERNELS_PER_STAGE = {"grid": 6, "search": 1, "prune": 1, "coord": 0, "zero": 1, "forces": 1, "final": 1,
@@ -279,10 +280,10 @@ def run_ours(args) -> dict:
 
 
 def _fp32_roofline(torch, dev, coul, n_plain, n_vir, slots, avg_ms, kernel, traffic) -> dict:
-    """FP32-pipe roofline of the force kernel: FP32 instructions per slot x
+    """FP32-pipe roofline of the force kernel: FP32 operations per slot x
     slots per launch / launch time, against SMs x 128 lanes x SM clock."""
     n = n_plain + n_vir
-    ips = (n_plain * INST_PER_SLOT[(coul, False)] + n_vir * INST_PER_SLOT[(coul, True)]) / n
+    ips = (n_plain * OPS_PER_SLOT[(coul, False)] + n_vir * OPS_PER_SLOT[(coul, True)]) / n
     fps = (n_plain * FLOPS_PER_SLOT[(coul, False)] + n_vir * FLOPS_PER_SLOT[(coul, True)]) / n
     props = torch.cuda.get_device_properties(dev)
     peaks, peak_kind = _peaks()
@@ -290,12 +291,12 @@ def _fp32_roofline(torch, dev, coul, n_plain, n_vir, slots, avg_ms, kernel, traf
     peak = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e12
     achieved = ips * slots / (avg_ms * 1e-3) / 1e12
     return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-            "unit": "T FP32 inst/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "unit": "T FP32 ops/s", "frac": round(achieved / peak, 4), "traffic": traffic,
             "kernel": kernel,
             "peak_kind": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz "
                          f"({peak_kind} max SM clock)",
             "avg_launch_ms": round(avg_ms, 5), "slots_per_launch": slots,
-            "inst_per_slot": round(ips, 2), "flops_per_slot": round(fps, 2),
+            "fp32_ops_per_slot": round(ips, 2), "flops_per_slot": round(fps, 2),
             "achieved_tflops": round(fps * slots / (avg_ms * 1e-3) / 1e12, 3)}
 
 

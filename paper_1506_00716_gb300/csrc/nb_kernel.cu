@@ -6,11 +6,14 @@
 // in registers while the list entries stream past; every entry's j-cluster
 // (N = 8 atoms) is staged in shared memory and its M x N pairs are computed
 // without further global loads.  Warp mapping on sm_103a: lane = 8 g + i,
-// i = i-slot, g = one of four entries in flight.  Lane i visits the j-slots
-// in the order t XOR i (t = 0..7), so the eight j-force partial sums it
-// keeps are already arranged for a three-step transposed butterfly that
-// leaves the full force of j-slot i in lane i (21 shuffles per 64 pairs, no
-// selects).  j-forces then go to memory with one float4 atomic per atom and
+// i = i-slot, g = one of four entries in flight.  The pair arithmetic runs
+// on the paired float32 instructions (FADD2, FMUL2, FFMA2): a lane takes two
+// j-slots per step, 2m and 2m+1 with m = p XOR (i >> 1) at step p, as the
+// halves of float2 values, from a staging layout that keeps both halves of
+// every operand in one aligned register pair.  The visiting order makes the
+// lane's j-force partial sums line up for a three-step transposed butterfly
+// that leaves the full force of j-slot i in lane i (21 shuffles per 64
+// pairs).  j-forces then go to memory with one float4 atomic per atom and
 // entry; i-forces are reduced over the four groups at the end of the item.
 // A persistent grid pulls (i-cluster, shift) work items from a global
 // counter, so one launch covers every system of a batch.
@@ -91,40 +94,131 @@ __device__ __forceinline__ void pair_force(float dx, float dy, float dz, float r
     }
 }
 
-// The M x N = 8 x 8 pairs of one entry for one lane (i-slot i): slot t pairs
-// i with j-slot t XOR i.  With EXACT, pairs within the band around rc^2 are
-// left out and reported in `band` (bit t).
-template <int COUL, bool VIR, bool MASKED, bool SHIFTED, bool EXACT>
-__device__ __forceinline__ void pair_block(const float4* __restrict__ sj, int i, const ShiftedI& xs,
-                                           float qi, int tirow, const float2* __restrict__ s_lj,
-                                           unsigned row, const KParams& kp, const EwaldC& ew,
-                                           float& fix, float& fiy, float& fiz, float (&fj)[CL][3],
-                                           float (&v)[6], unsigned& band) {
+// Paired float32 arithmetic of sm_100 and later: one instruction applies the
+// operation to both halves of a float2, each half rounded exactly as the
+// scalar operation rounds it.  Two pairs per instruction halve the issue
+// slots of the pair arithmetic, which bounds this kernel.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 sa, sb, sr;\n\tmov.b64 sa, {%2, %3};\n\tmov.b64 sb, {%4, %5};\n\t"
+        "sub.rn.f32x2 sr, sa, sb;\n\tmov.b64 {%0, %1}, sr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// erfc(x) exp(x^2) from the force fit, for two arguments.
+__device__ __forceinline__ float2 erfcx_force2(float2 x) {
+    x.x = fminf(x.x, EF_XMAX);
+    x.y = fminf(x.y, EF_XMAX);
+    const float2 d = fma2(dup2(EF_P), x, dup2(1.f));
+    const float2 t = make_float2(rcp_sfu(d.x), rcp_sfu(d.y));
+    const float2 u = fma2(dup2(EF_UA), t, dup2(EF_UB));
+    float2 r = dup2(EF_FORCE[EF_NF - 1]);
 #pragma unroll
-    for (int t = 0; t < CL; ++t) {
-        const int js = t ^ i;
-        const float4 xj = sj[js];
-        const int tj = __float_as_int(sj[CL + js].x);
-        float dx = xs.xh - xj.x;
-        float dy = xs.yh - xj.y;
-        float dz = xs.zh - xj.z;
+    for (int k = EF_NF - 2; k >= 0; --k) r = fma2(r, u, dup2(EF_FORCE[k]));
+    return r;
+}
+
+// The i-atom of a lane, shifted, with every component duplicated into both
+// halves of a float2.
+struct IPair {
+    float2 xh, yh, zh, xl, yl, zl;
+};
+
+// Force of two pair slots (the halves): as pair_force, with the decisions
+// in0, in1 applied to F/r at the end (a slot that is out contributes
+// nothing, whatever its arithmetic gave).
+template <int COUL, bool VIR>
+__device__ __forceinline__ void pair_force2(float2 dx, float2 dy, float2 dz, float2 r2, bool in0, bool in1,
+                                            float2 qi, float2 qj, float2 c6, float2 c12, const KParams& kp,
+                                            const EwaldC& ew, float2 (&fi)[3], float2 (&fj)[3],
+                                            float2 (&v)[6]) {
+    const float2 rinv = make_float2(rsqrt_sfu(r2.x), rsqrt_sfu(r2.y));
+    const float2 qq = mul2(qi, qj);
+    const float2 rinv2 = mul2(rinv, rinv);
+    const float2 rinv6 = mul2(mul2(rinv2, rinv2), rinv2);
+    const float2 t6 = mul2(c6, rinv6);
+    const float2 t12 = mul2(mul2(c12, rinv6), rinv6);
+    float2 fr;  // F/r
+    if (COUL == NB_COUL_RF) {
+        const float2 fc = mul2(qq, fma2(rinv, rinv2, dup2(-kp.two_krf)));
+        fr = fma2(sub2(t12, t6), rinv2, fc);
+    } else {
+        const float2 r = mul2(r2, rinv);
+        const float2 arg = mul2(r2, dup2(ew.mb2_log2e));
+        const float2 ex = make_float2(ex2_sfu(arg.x), ex2_sfu(arg.y));
+        const float2 erfcv = mul2(erfcx_force2(mul2(dup2(ew.beta), r)), ex);
+        fr = mul2(sub2(add2(fma2(mul2(qq, dup2(ew.c2)), ex, mul2(mul2(qq, erfcv), rinv)), t12), t6), rinv2);
+    }
+    fr.x = in0 ? fr.x : 0.f;
+    fr.y = in1 ? fr.y : 0.f;
+    const float2 fx = mul2(fr, dx), fy = mul2(fr, dy), fz = mul2(fr, dz);
+    fi[0] = add2(fi[0], fx);
+    fi[1] = add2(fi[1], fy);
+    fi[2] = add2(fi[2], fz);
+    fj[0] = sub2(fj[0], fx);
+    fj[1] = sub2(fj[1], fy);
+    fj[2] = sub2(fj[2], fz);
+    if (VIR) {
+        v[0] = fma2(fx, dx, v[0]);
+        v[1] = fma2(fy, dy, v[1]);
+        v[2] = fma2(fz, dz, v[2]);
+        v[3] = fma2(fx, dy, v[3]);
+        v[4] = fma2(fx, dz, v[4]);
+        v[5] = fma2(fy, dz, v[5]);
+    }
+}
+
+// Shared-memory block of one staged j-cluster (floats): x and y of the slot
+// pairs (2m, 2m+1) as float4 (x_2m, x_2m+1, y_2m, y_2m+1) at 4m, z and q
+// likewise at 16 + 4m, the types as int2 at 32 + 2m.  Every operand of the
+// paired arithmetic then arrives as one aligned register pair.
+constexpr int JB_Z = 16, JB_T = 32, JB_SIZE = 40;
+
+// The M x N = 8 x 8 pairs of one entry for one lane (i-slot i), two at a
+// time: step p takes the j-slots 2m and 2m+1, m = p XOR (i >> 1), as the
+// two halves.  `row` holds the lane's mask bits in that order (bit 2p + c
+// for half c of step p).  With EXACT, pairs within the band around rc^2 are
+// left out and `band` is set; the caller decides them one by one.
+template <int COUL, bool VIR, bool MASKED, bool SHIFTED, bool EXACT>
+__device__ __forceinline__ void pair_block2(const float* __restrict__ sj, int h, const IPair& xs, float2 qi,
+                                            const float* __restrict__ c6row, const float* __restrict__ c12row,
+                                            unsigned row, const KParams& kp, const EwaldC& ew,
+                                            float2 (&fi)[3], float2 (&fj)[4][3], float2 (&v)[6], bool& band) {
+#pragma unroll
+    for (int p = 0; p < CL / 2; ++p) {
+        const int m = p ^ h;
+        const float4 a = *reinterpret_cast<const float4*>(sj + 4 * m);
+        const float4 b = *reinterpret_cast<const float4*>(sj + JB_Z + 4 * m);
+        const int2 tj = *reinterpret_cast<const int2*>(sj + JB_T + 2 * m);
+        float2 dx = sub2(xs.xh, make_float2(a.x, a.y));
+        float2 dy = sub2(xs.yh, make_float2(a.z, a.w));
+        float2 dz = sub2(xs.zh, make_float2(b.x, b.y));
         if (SHIFTED) {
-            dx += xs.xl;
-            dy += xs.yl;
-            dz += xs.zl;
+            dx = add2(dx, xs.xl);
+            dy = add2(dy, xs.yl);
+            dz = add2(dz, xs.zl);
         }
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        bool in = r2 < (EXACT ? kp.rc2_lo : kp.rc2);
-        bool maybe = false;
-        if (EXACT) maybe = !in && r2 < kp.rc2_hi;
+        const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+        const float lim = EXACT ? kp.rc2_lo : kp.rc2;
+        bool in0 = r2.x < lim, in1 = r2.y < lim;
+        bool b0 = true, b1 = true;
         if (MASKED) {
-            const bool bit = (row >> t) & 1u;
-            in = in && bit;
-            maybe = maybe && bit;
+            b0 = (row >> (2 * p)) & 1u;
+            b1 = (row >> (2 * p + 1)) & 1u;
+            in0 = in0 && b0;
+            in1 = in1 && b1;
         }
-        if (EXACT && maybe) band |= 1u << t;
-        pair_force<COUL, VIR>(dx, dy, dz, r2, in, qi, xj.w, s_lj[tirow + tj], kp, ew, fix, fiy, fiz,
-                              fj[t][0], fj[t][1], fj[t][2], v);
+        if (EXACT) band = band || (b0 && !in0 && r2.x < kp.rc2_hi) || (b1 && !in1 && r2.y < kp.rc2_hi);
+        const float2 c6 = make_float2(c6row[tj.x], c6row[tj.y]);
+        const float2 c12 = make_float2(c12row[tj.x], c12row[tj.y]);
+        pair_force2<COUL, VIR>(dx, dy, dz, r2, in0, in1, qi, make_float2(b.z, b.w), c6, c12, kp, ew, fi, fj[p],
+                               v);
     }
 }
 
@@ -134,8 +228,9 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     pdl_wait();
     pdl_trigger();
     constexpr bool EXACT = COUL == NB_COUL_RF;
-    extern __shared__ float2 s_lj[];
-    __shared__ __align__(16) float4 s_j[FW][4][2 * CL];
+    // (6 c6) and (12 c12) tables, each [ntypes^2]
+    extern __shared__ float s_ljt[];
+    __shared__ __align__(16) float s_j[FW][4][JB_SIZE];
     __shared__ double s_acc[FW][6];
     __shared__ float s_fix[FW][4][CL][3];
 
@@ -143,8 +238,15 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     const int i = lane & 7;
     const int g = lane >> 3;
     const int w = threadIdx.x >> 5;
+    const int h = i >> 1, odd = i & 1;
     const int nt = kp.ntypes;
-    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) s_lj[k] = kp.lj[k];
+    float* const s_c6 = s_ljt;
+    float* const s_c12 = s_ljt + nt * nt;
+    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) {
+        const float2 c = kp.lj[k];
+        s_c6[k] = c.x;
+        s_c12[k] = c.y;
+    }
     if (lane < 6) s_acc[w][lane] = 0.0;
     __syncthreads();
 
@@ -153,7 +255,10 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     ew.mb2_log2e = -kp.beta * kp.beta * 1.4426950408889634f;
     ew.c2 = 2.0f * kp.beta * 0.5641895835477563f;
 
-    float4* sjg = &s_j[w][g][0];
+    float* const sjg = &s_j[w][g][0];
+    // where lane i stages j-slot i: x and y at 4 (i >> 1) + (i & 1) (+ 2),
+    // z and q 16 floats further, the type at 32 + i
+    const int st = 4 * h + odd;
     // longest-first order for short lists, where the last items decide the
     // launch's length; cluster order otherwise (neighbouring items share
     // j-clusters in L1 and L2)
@@ -199,11 +304,14 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         const bool shifted = sh != SHIFT_ZERO;
         const float4 xi4 = xq_s[ci * CL + i];
         const ShiftedI xs = shift_i(xi4, sh, Lx, Ly, Lz, Tbx, Tcx, Tcy);
+        const IPair xp = {dup2(xs.xh), dup2(xs.yh), dup2(xs.zh), dup2(xs.xl), dup2(xs.yl), dup2(xs.zl)};
         const float qi = xi4.w * kp.fq;
         const int tirow = type_s[ci * CL + i] * nt;
+        const float* const c6row = s_c6 + tirow;
+        const float* const c12row = s_c12 + tirow;
 
-        float fix = 0.f, fiy = 0.f, fiz = 0.f;
-        float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float2 fi[3] = {dup2(0.f), dup2(0.f), dup2(0.f)};
+        float2 v[6] = {dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f)};
 
         int e = jb + g;
         bool act = e < je;
@@ -219,8 +327,11 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         }
         for (int base = jb; base < je; base += 4) {
             __syncwarp();
-            sjg[i] = pxq;
-            sjg[CL + i] = make_float4(__int_as_float(pty), 0.f, 0.f, 0.f);
+            sjg[st] = pxq.x;
+            sjg[st + 2] = pxq.y;
+            sjg[JB_Z + st] = pxq.z;
+            sjg[JB_Z + st + 2] = pxq.w;
+            reinterpret_cast<int*>(sjg)[JB_T + i] = pty;
             const int ccj = cjn;
             const bool cact = act;
             const unsigned long long cm = pm;
@@ -234,61 +345,90 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
                 pty = type_s[cjn * CL + i];
             }
             __syncwarp();
+            // the lane's mask row (bit t: j-slot t XOR i) in the order of the
+            // paired steps (bit 2p + c: j-slot 2 (p XOR (i >> 1)) + c), i.e.
+            // adjacent bits swapped on odd lanes
             const unsigned row = (unsigned)(cm >> (8 * i)) & 0xffu;
-            float fj[CL][3];
+            const unsigned rowp = odd ? (((row & 0x55u) << 1) | ((row >> 1) & 0x55u)) : row;
+            float2 fj[CL / 2][3];
 #pragma unroll
-            for (int t = 0; t < CL; ++t) fj[t][0] = fj[t][1] = fj[t][2] = 0.f;
-            unsigned band = 0;
+            for (int p = 0; p < CL / 2; ++p) fj[p][0] = fj[p][1] = fj[p][2] = dup2(0.f);
+            bool band = false;
             const bool full = __all_sync(FULL, row == 0xffu);
             if (full && !shifted)
-                pair_block<COUL, VIR, false, false, EXACT>(sjg, i, xs, qi, tirow, s_lj, row, kp, ew,
-                                                          fix, fiy, fiz, fj, v, band);
+                pair_block2<COUL, VIR, false, false, EXACT>(sjg, h, xp, dup2(qi), c6row, c12row, rowp, kp, ew,
+                                                           fi, fj, v, band);
             else if (full)
-                pair_block<COUL, VIR, false, true, EXACT>(sjg, i, xs, qi, tirow, s_lj, row, kp, ew,
-                                                         fix, fiy, fiz, fj, v, band);
+                pair_block2<COUL, VIR, false, true, EXACT>(sjg, h, xp, dup2(qi), c6row, c12row, rowp, kp, ew,
+                                                          fi, fj, v, band);
             else
-                pair_block<COUL, VIR, true, true, EXACT>(sjg, i, xs, qi, tirow, s_lj, row, kp, ew,
-                                                        fix, fiy, fiz, fj, v, band);
-            // transposed butterfly over the 8 lanes of the group
+                pair_block2<COUL, VIR, true, true, EXACT>(sjg, h, xp, dup2(qi), c6row, c12row, rowp, kp, ew,
+                                                         fi, fj, v, band);
+            // transposed butterfly over the 8 lanes of the group: half c of
+            // fj[p] holds j-slot 2 (p XOR (i >> 1)) + c, so the partners at
+            // XOR 4 and 2 hold the same slots in fj[p ^ 2] and fj[p ^ 1]; at
+            // XOR 1 each lane keeps its own slot's half and sends the other
 #pragma unroll
-            for (int t = 0; t < 4; ++t)
+            for (int p = 0; p < 2; ++p)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) fj[t][c] += __shfl_xor_sync(FULL, fj[t + 4][c], 4);
+                for (int c = 0; c < 3; ++c)
+                    fj[p][c] = add2(fj[p][c], make_float2(__shfl_xor_sync(FULL, fj[p + 2][c].x, 4),
+                                                          __shfl_xor_sync(FULL, fj[p + 2][c].y, 4)));
 #pragma unroll
-            for (int t = 0; t < 2; ++t)
+            for (int c = 0; c < 3; ++c)
+                fj[0][c] = add2(fj[0][c], make_float2(__shfl_xor_sync(FULL, fj[1][c].x, 2),
+                                                      __shfl_xor_sync(FULL, fj[1][c].y, 2)));
+            float fjt[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) fj[t][c] += __shfl_xor_sync(FULL, fj[t + 2][c], 2);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) fj[0][c] += __shfl_xor_sync(FULL, fj[1][c], 1);
-            if (EXACT && __any_sync(FULL, band != 0u)) {
-                // rare path: pairs within the band around rc, decided exactly
+            for (int c = 0; c < 3; ++c) {
+                const float keep = odd ? fj[0][c].y : fj[0][c].x;
+                const float send = odd ? fj[0][c].x : fj[0][c].y;
+                fjt[c] = keep + __shfl_xor_sync(FULL, send, 1);
+            }
+            if (EXACT && __any_sync(FULL, band)) {
+                // rare path: pairs within the band around rc, found again with
+                // the main pass's arithmetic and decided exactly
                 s_fix[w][g][i][0] = s_fix[w][g][i][1] = s_fix[w][g][i][2] = 0.f;
                 __syncwarp();
-                while (band) {
-                    const int t = __ffs(band) - 1;
-                    band &= band - 1;
-                    const int js = t ^ i;
-                    const float4 xj = sjg[js];
-                    if (!exact_inside(xs, xj, kp.rc2_d)) continue;
-                    const int tj = __float_as_int(sjg[CL + js].x);
-                    const float dx = (xs.xh - xj.x) + xs.xl;
-                    const float dy = (xs.yh - xj.y) + xs.yl;
-                    const float dz = (xs.zh - xj.z) + xs.zl;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    float gx = 0.f, gy = 0.f, gz = 0.f;
-                    pair_force<COUL, VIR>(dx, dy, dz, r2, true, qi, xj.w, s_lj[tirow + tj], kp, ew, fix,
-                                          fiy, fiz, gx, gy, gz, v);
-                    atomicAdd(&s_fix[w][g][js][0], gx);
-                    atomicAdd(&s_fix[w][g][js][1], gy);
-                    atomicAdd(&s_fix[w][g][js][2], gz);
+                if (band) {
+                    float fsx = 0.f, fsy = 0.f, fsz = 0.f;
+                    for (int t = 0; t < CL; ++t) {
+                        if (!((row >> t) & 1u)) continue;
+                        const int js = t ^ i;
+                        const int o = 4 * (js >> 1) + (js & 1);
+                        const float4 xj = make_float4(sjg[o], sjg[o + 2], sjg[JB_Z + o], sjg[JB_Z + o + 2]);
+                        const float dx = (xs.xh - xj.x) + xs.xl;
+                        const float dy = (xs.yh - xj.y) + xs.yl;
+                        const float dz = (xs.zh - xj.z) + xs.zl;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        if (r2 < kp.rc2_lo || !(r2 < kp.rc2_hi)) continue;
+                        if (!exact_inside(xs, xj, kp.rc2_d)) continue;
+                        const int tj = reinterpret_cast<const int*>(sjg)[JB_T + js];
+                        const float2 c = make_float2(c6row[tj], c12row[tj]);
+                        float gx = 0.f, gy = 0.f, gz = 0.f;
+                        float vs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                        pair_force<COUL, VIR>(dx, dy, dz, r2, true, qi, xj.w, c, kp, ew, fsx, fsy, fsz, gx, gy,
+                                              gz, vs);
+                        if (VIR) {
+#pragma unroll
+                            for (int k = 0; k < 6; ++k) v[k].x += vs[k];
+                        }
+                        atomicAdd(&s_fix[w][g][js][0], gx);
+                        atomicAdd(&s_fix[w][g][js][1], gy);
+                        atomicAdd(&s_fix[w][g][js][2], gz);
+                    }
+                    fi[0].x += fsx;
+                    fi[1].x += fsy;
+                    fi[2].x += fsz;
                 }
                 __syncwarp();
-                fj[0][0] += s_fix[w][g][i][0];
-                fj[0][1] += s_fix[w][g][i][1];
-                fj[0][2] += s_fix[w][g][i][2];
+                fjt[0] += s_fix[w][g][i][0];
+                fjt[1] += s_fix[w][g][i][1];
+                fjt[2] += s_fix[w][g][i][2];
             }
-            if (cact) atomicAdd(f_s + ccj * CL + i, make_float4(fj[0][0], fj[0][1], fj[0][2], 0.f));
+            if (cact) atomicAdd(f_s + ccj * CL + i, make_float4(fjt[0], fjt[1], fjt[2], 0.f));
         }
+        float fix = fi[0].x + fi[0].y, fiy = fi[1].x + fi[1].y, fiz = fi[2].x + fi[2].y;
         fix += __shfl_xor_sync(FULL, fix, 8);
         fiy += __shfl_xor_sync(FULL, fiy, 8);
         fiz += __shfl_xor_sync(FULL, fiz, 8);
@@ -297,14 +437,16 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         fiz += __shfl_xor_sync(FULL, fiz, 16);
         if (g == 0) atomicAdd(f_s + ci * CL + i, make_float4(fix, fiy, fiz, 0.f));
         if (VIR) {
+            float vt[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
+                vt[k] = v[k].x + v[k].y;
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], off);
+                for (int off = 16; off > 0; off >>= 1) vt[k] += __shfl_xor_sync(FULL, vt[k], off);
             }
             if (lane == 0) {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) s_acc[w][k] += (double)v[k];
+                for (int k = 0; k < 6; ++k) s_acc[w][k] += (double)vt[k];
             }
         }
     }
