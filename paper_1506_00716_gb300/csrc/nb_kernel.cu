@@ -35,6 +35,7 @@
 // of the float32 inputs, the same decision the float64 oracle takes.
 #include "erfc_fit.cuh"
 #include "nb_device.cuh"
+#include "nb_pair2.cuh"
 
 namespace nbgb {
 
@@ -93,23 +94,6 @@ __device__ __forceinline__ void pair_force(float dx, float dy, float dz, float r
         v[5] = fmaf(fy, dz, v[5]);
     }
 }
-
-// Paired float32 arithmetic of sm_100 and later: one instruction applies the
-// operation to both halves of a float2, each half rounded exactly as the
-// scalar operation rounds it.  Two pairs per instruction halve the issue
-// slots of the pair arithmetic, which bounds this kernel.
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-    float2 r;
-    asm("{\n\t.reg .b64 sa, sb, sr;\n\tmov.b64 sa, {%2, %3};\n\tmov.b64 sb, {%4, %5};\n\t"
-        "sub.rn.f32x2 sr, sa, sb;\n\tmov.b64 {%0, %1}, sr;\n\t}"
-        : "=f"(r.x), "=f"(r.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return r;
-}
-__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
 // erfc(x) exp(x^2) from the force fit, for two arguments.
 __device__ __forceinline__ float2 erfcx_force2(float2 x) {
