@@ -158,11 +158,17 @@ __device__ __forceinline__ void pair_force2(float2 dx, float2 dy, float2 dz, flo
     }
 }
 
-// Shared-memory block of one staged j-cluster (floats): x and y of the slot
-// pairs (2m, 2m+1) as float4 (x_2m, x_2m+1, y_2m, y_2m+1) at 4m, z and q
-// likewise at 16 + 4m, the types as int2 at 32 + 2m.  Every operand of the
-// paired arithmetic then arrives as one aligned register pair.
-constexpr int JB_Z = 16, JB_T = 32, JB_SIZE = 40;
+// Shared-memory block of one staged j-cluster (floats): a 12-float record
+// per slot pair (2m, 2m+1) at 12m, holding (x_2m, x_2m+1, y_2m, y_2m+1),
+// then (z_2m, z_2m+1, q_2m, q_2m+1), then the types as int2.  Every operand
+// of the paired arithmetic arrives as one aligned register pair, and a step
+// reads its record from one address.  The 48-byte stride keeps the four
+// records a group reads at once in distinct banks.
+constexpr int JB_REC = 12, JB_Z = 4, JB_T = 8, JB_SIZE = 4 * JB_REC;
+// The (12 c12) table starts this many floats after the (6 c6) table, a
+// constant, so that both entries of a type pair are addressed from one
+// register.
+constexpr int LJ_C12 = MAX_TYPES * MAX_TYPES;
 
 // The M x N = 8 x 8 pairs of one entry for one lane (i-slot i), two at a
 // time: step p takes the j-slots 2m and 2m+1, m = p XOR (i >> 1), as the
@@ -171,15 +177,14 @@ constexpr int JB_Z = 16, JB_T = 32, JB_SIZE = 40;
 // left out and `band` is set; the caller decides them one by one.
 template <int COUL, bool VIR, bool MASKED, bool SHIFTED, bool EXACT>
 __device__ __forceinline__ void pair_block2(const float* __restrict__ sj, int h, const IPair& xs, float2 qi,
-                                            const float* __restrict__ c6row, const float* __restrict__ c12row,
-                                            unsigned row, const KParams& kp, const EwaldC& ew,
+                                            const float* __restrict__ ljrow, unsigned row, const KParams& kp, const EwaldC& ew,
                                             float2 (&fi)[3], float2 (&fj)[4][3], float2 (&v)[6], bool& band) {
 #pragma unroll
     for (int p = 0; p < CL / 2; ++p) {
-        const int m = p ^ h;
-        const float4 a = *reinterpret_cast<const float4*>(sj + 4 * m);
-        const float4 b = *reinterpret_cast<const float4*>(sj + JB_Z + 4 * m);
-        const int2 tj = *reinterpret_cast<const int2*>(sj + JB_T + 2 * m);
+        const float* rec = sj + JB_REC * (p ^ h);
+        const float4 a = *reinterpret_cast<const float4*>(rec);
+        const float4 b = *reinterpret_cast<const float4*>(rec + JB_Z);
+        const int2 tj = *reinterpret_cast<const int2*>(rec + JB_T);
         float2 dx = sub2(xs.xh, make_float2(a.x, a.y));
         float2 dy = sub2(xs.yh, make_float2(a.z, a.w));
         float2 dz = sub2(xs.zh, make_float2(b.x, b.y));
@@ -199,8 +204,10 @@ __device__ __forceinline__ void pair_block2(const float* __restrict__ sj, int h,
             in1 = in1 && b1;
         }
         if (EXACT) band = band || (b0 && !in0 && r2.x < kp.rc2_hi) || (b1 && !in1 && r2.y < kp.rc2_hi);
-        const float2 c6 = make_float2(c6row[tj.x], c6row[tj.y]);
-        const float2 c12 = make_float2(c12row[tj.x], c12row[tj.y]);
+        const float* l0 = ljrow + tj.x;
+        const float* l1 = ljrow + tj.y;
+        const float2 c6 = make_float2(l0[0], l1[0]);
+        const float2 c12 = make_float2(l0[LJ_C12], l1[LJ_C12]);
         pair_force2<COUL, VIR>(dx, dy, dz, r2, in0, in1, qi, make_float2(b.z, b.w), c6, c12, kp, ew, fi, fj[p],
                                v);
     }
@@ -212,7 +219,7 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     pdl_wait();
     pdl_trigger();
     constexpr bool EXACT = COUL == NB_COUL_RF;
-    // (6 c6) and (12 c12) tables, each [ntypes^2]
+    // (6 c6) table [ntypes^2] at 0, (12 c12) table at LJ_C12
     extern __shared__ float s_ljt[];
     __shared__ __align__(16) float s_j[FW][4][JB_SIZE];
     __shared__ double s_acc[FW][6];
@@ -224,12 +231,10 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     const int w = threadIdx.x >> 5;
     const int h = i >> 1, odd = i & 1;
     const int nt = kp.ntypes;
-    float* const s_c6 = s_ljt;
-    float* const s_c12 = s_ljt + nt * nt;
     for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) {
         const float2 c = kp.lj[k];
-        s_c6[k] = c.x;
-        s_c12[k] = c.y;
+        s_ljt[k] = c.x;
+        s_ljt[LJ_C12 + k] = c.y;
     }
     if (lane < 6) s_acc[w][lane] = 0.0;
     __syncthreads();
@@ -240,9 +245,9 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     ew.c2 = 2.0f * kp.beta * 0.5641895835477563f;
 
     float* const sjg = &s_j[w][g][0];
-    // where lane i stages j-slot i: x and y at 4 (i >> 1) + (i & 1) (+ 2),
-    // z and q 16 floats further, the type at 32 + i
-    const int st = 4 * h + odd;
+    // where lane i stages j-slot i: x and y at 12 (i >> 1) + (i & 1) (+ 2),
+    // z and q 4 floats further, the type 8 floats further
+    const int st = JB_REC * h + odd;
     // longest-first order for short lists, where the last items decide the
     // launch's length; cluster order otherwise (neighbouring items share
     // j-clusters in L1 and L2)
@@ -291,8 +296,7 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         const IPair xp = {dup2(xs.xh), dup2(xs.yh), dup2(xs.zh), dup2(xs.xl), dup2(xs.yl), dup2(xs.zl)};
         const float qi = xi4.w * kp.fq;
         const int tirow = type_s[ci * CL + i] * nt;
-        const float* const c6row = s_c6 + tirow;
-        const float* const c12row = s_c12 + tirow;
+        const float* const ljrow = s_ljt + tirow;
 
         float2 fi[3] = {dup2(0.f), dup2(0.f), dup2(0.f)};
         float2 v[6] = {dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f)};
@@ -315,7 +319,7 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             sjg[st + 2] = pxq.y;
             sjg[JB_Z + st] = pxq.z;
             sjg[JB_Z + st + 2] = pxq.w;
-            reinterpret_cast<int*>(sjg)[JB_T + i] = pty;
+            reinterpret_cast<int*>(sjg)[JB_T + st] = pty;
             const int ccj = cjn;
             const bool cact = act;
             const unsigned long long cm = pm;
@@ -340,13 +344,13 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             bool band = false;
             const bool full = __all_sync(FULL, row == 0xffu);
             if (full && !shifted)
-                pair_block2<COUL, VIR, false, false, EXACT>(sjg, h, xp, dup2(qi), c6row, c12row, rowp, kp, ew,
+                pair_block2<COUL, VIR, false, false, EXACT>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
                                                            fi, fj, v, band);
             else if (full)
-                pair_block2<COUL, VIR, false, true, EXACT>(sjg, h, xp, dup2(qi), c6row, c12row, rowp, kp, ew,
+                pair_block2<COUL, VIR, false, true, EXACT>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
                                                           fi, fj, v, band);
             else
-                pair_block2<COUL, VIR, true, true, EXACT>(sjg, h, xp, dup2(qi), c6row, c12row, rowp, kp, ew,
+                pair_block2<COUL, VIR, true, true, EXACT>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
                                                          fi, fj, v, band);
             // transposed butterfly over the 8 lanes of the group: half c of
             // fj[p] holds j-slot 2 (p XOR (i >> 1)) + c, so the partners at
@@ -379,16 +383,16 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
                     for (int t = 0; t < CL; ++t) {
                         if (!((row >> t) & 1u)) continue;
                         const int js = t ^ i;
-                        const int o = 4 * (js >> 1) + (js & 1);
-                        const float4 xj = make_float4(sjg[o], sjg[o + 2], sjg[JB_Z + o], sjg[JB_Z + o + 2]);
+                        const int o = JB_REC * (js >> 1) + (js & 1);
+                        const float4 xj = make_float4(sjg[o], sjg[o + 2], sjg[o + JB_Z], sjg[o + JB_Z + 2]);
                         const float dx = (xs.xh - xj.x) + xs.xl;
                         const float dy = (xs.yh - xj.y) + xs.yl;
                         const float dz = (xs.zh - xj.z) + xs.zl;
                         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                         if (r2 < kp.rc2_lo || !(r2 < kp.rc2_hi)) continue;
                         if (!exact_inside(xs, xj, kp.rc2_d)) continue;
-                        const int tj = reinterpret_cast<const int*>(sjg)[JB_T + js];
-                        const float2 c = make_float2(c6row[tj], c12row[tj]);
+                        const int tj = reinterpret_cast<const int*>(sjg)[o + JB_T];
+                        const float2 c = make_float2(ljrow[tj], ljrow[LJ_C12 + tj]);
                         float gx = 0.f, gy = 0.f, gz = 0.f;
                         float vs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                         pair_force<COUL, VIR>(dx, dy, dz, r2, true, qi, xj.w, c, kp, ew, fsx, fsy, fsz, gx, gy,
@@ -529,7 +533,7 @@ __global__ void k_finish(const SysDev* __restrict__ sys, const int* __restrict__
 
 template <int COUL, bool VIR, int MINB>
 cudaError_t launch_forces_t(const PlanLaunch& p, cudaStream_t st) {
-    size_t smem = (size_t)p.kp.ntypes * p.kp.ntypes * sizeof(float2);
+    size_t smem = (size_t)(LJ_C12 + p.kp.ntypes * p.kp.ntypes) * sizeof(float);
     auto kern = k_forces<COUL, VIR, MINB>;
     int per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FW * 32, smem);

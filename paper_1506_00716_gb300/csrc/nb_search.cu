@@ -20,6 +20,7 @@
 // on the GPU and then reused): entries with no unmasked atom pair closer
 // than rlist are removed, compacting each work item's entries in place.
 #include "nb_internal.cuh"
+#include "nb_pair2.cuh"
 
 namespace nbgb {
 
@@ -413,11 +414,14 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
         const int sh = item.w & 31;
         const float3 S = shift_vec(sh, d.L, d.T);
         const float Sx = S.x, Sy = S.y, Sz = S.z;
-        float3 xi[CL];
+        // the i-atoms in pairs (2k, 2k+1), for the paired float32 arithmetic
+        float2 xi[CL / 2], yi[CL / 2], zi[CL / 2];
 #pragma unroll
-        for (int k = 0; k < CL; ++k) {
-            const float4 v = d.xq_s[item.x * CL + k];
-            xi[k] = make_float3(v.x + Sx, v.y + Sy, v.z + Sz);
+        for (int k = 0; k < CL / 2; ++k) {
+            const float4 v0 = d.xq_s[item.x * CL + 2 * k], v1 = d.xq_s[item.x * CL + 2 * k + 1];
+            xi[k] = make_float2(v0.x + Sx, v1.x + Sx);
+            yi[k] = make_float2(v0.y + Sy, v1.y + Sy);
+            zi[k] = make_float2(v0.z + Sz, v1.z + Sz);
         }
         int write = item.y;
         for (int base = item.y; base < item.z; base += 32) {
@@ -450,12 +454,15 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     // bit ii: i-atom ii lies within the list radius of this j-atom
+                    // (two i-atoms per paired instruction)
                     unsigned nb8 = 0;
+                    const float2 jx = dup2(xj[u].x), jy = dup2(xj[u].y), jz = dup2(xj[u].z);
 #pragma unroll
-                    for (int ii = 0; ii < CL; ++ii) {
-                        const float dx = xi[ii].x - xj[u].x, dy = xi[ii].y - xj[u].y, dz = xi[ii].z - xj[u].z;
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        nb8 |= (r2 < rl2 ? 1u : 0u) << ii;
+                    for (int k = 0; k < CL / 2; ++k) {
+                        const float2 dx = sub2(xi[k], jx), dy = sub2(yi[k], jy), dz = sub2(zi[k], jz);
+                        const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                        nb8 |= (r2.x < rl2 ? 1u : 0u) << (2 * k);
+                        nb8 |= (r2.y < rl2 ? 1u : 0u) << (2 * k + 1);
                     }
                     // the mask column of j-slot jj (bit ii = pair (ii, jj)), only
                     // when one of the four entries has a partial mask
