@@ -86,38 +86,32 @@ __device__ __forceinline__ float gap(float alo, float ahi, float blo, float bhi)
 
 // Partition point of a column's clusters [lo, hi): with TOP, the first
 // cluster whose top z is >= z; otherwise the first whose bottom z is > z.
-// The clusters of a column are z-sorted, so both keys ascend.  The search
-// starts at a guess (the column's atoms spread evenly over the box height,
-// which puts it within a cluster or two) and walks at most WALK steps; if the
-// answer is farther, it bisects the remaining range.
-constexpr int WALK = 3;
+// The clusters of a column are z-sorted, so both keys ascend.  The guess
+// (the column's atoms spread evenly over the box height) is usually within a
+// cluster or two of the answer, so the keys of the PROBE clusters around it
+// are loaded at once, independent loads in one round trip; an answer outside
+// that window is found by bisecting the rest.
+constexpr int PROBE = 6;  // clusters guess - 3 .. guess + 2
 
 template <bool TOP>
 __device__ __forceinline__ int window_bound(const float4* __restrict__ bb, int lo, int hi, float z, int guess) {
     auto before = [&](int m) {  // cluster m lies before the partition point
         return TOP ? bb[2 * m + 1].z < z : bb[2 * m].z <= z;
     };
-    int g = min(max(guess, lo), hi);
-    int steps = 0;
-    while (g > lo && !before(g - 1)) {
-        if (++steps > WALK) {
-            hi = g - 1;  // the answer is <= g - 1
-            g = -1;
-            break;
-        }
-        --g;
+    const int p0 = min(max(guess - PROBE / 2, lo), hi);  // first probed cluster
+    bool bf[PROBE];
+#pragma unroll
+    for (int k = 0; k < PROBE; ++k) bf[k] = p0 + k < hi ? before(p0 + k) : false;
+    if (p0 > lo && !bf[0]) {
+        // the answer lies in [lo, p0]
+        hi = p0;
+    } else {
+        int k = 0;
+#pragma unroll
+        for (int q = 0; q < PROBE; ++q) k += bf[q] ? 1 : 0;  // the keys ascend: bf is true, then false
+        if (k < PROBE || p0 + PROBE >= hi) return min(p0 + k, hi);
+        lo = p0 + PROBE;  // the answer lies in [p0 + PROBE, hi]
     }
-    if (g >= 0) {
-        while (g < hi && before(g)) {
-            if (++steps > WALK) {
-                lo = g + 1;  // the answer is >= g + 1
-                g = -1;
-                break;
-            }
-            ++g;
-        }
-    }
-    if (g >= 0) return g;
     while (lo < hi) {
         const int m = (lo + hi) >> 1;
         if (before(m)) lo = m + 1; else hi = m;
@@ -281,8 +275,10 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
                             // first cluster with top >= zmin, and first with
                             // bottom > zmax (tops and bottoms ascend along the
                             // column)
+                            // (independent of each other: clusters before a
+                            // have bottom <= top < zmin <= zmax)
                             const int a = window_bound<true>(d.bb, a0, b0, zmin, a0 + (int)(zmin * cl_per_z));
-                            const int u = window_bound<false>(d.bb, a, b0, zmax, a + (int)((zmax - zmin) * cl_per_z));
+                            const int u = window_bound<false>(d.bb, a0, b0, zmax, a0 + (int)(zmax * cl_per_z));
                             c0 = a;
                             cnt = u - a;
                         }
