@@ -287,6 +287,12 @@ nb_status nb_pairlist_prune(nb_sys *sys, double r_inner);
  *           row-major; NULL allowed.
  *   flags   NB_F_ENERGY | NB_F_VIRIAL; energy / virial must be non-NULL when
  *           their flag is set.
+ * Buffers: device memory and pinned host memory (cudaHostAlloc, registered
+ * or pinned tensors) are read and written by the kernels themselves, pinned
+ * host memory through its mapped device address (no separate copy; over
+ * NVLink-C2C on a Grace-Blackwell node); pageable host memory goes through
+ * the system's staging buffers.  With any host buffer the call returns after
+ * the stream has finished with it.
  * Forces and virial: float32 pair arithmetic and per-atom accumulation, the
  * virial summed over the system in float64.  Energies (NB_F_ENERGY, an extra
  * kernel): double-float pair arithmetic on the float32 pipes, summed in

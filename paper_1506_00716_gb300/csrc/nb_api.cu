@@ -62,6 +62,27 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The address at which kernels may read or write a caller's buffer directly:
+// device or managed memory as it is, pinned host memory through its mapped
+// device address (on a Grace-Blackwell node the kernels then reach host
+// memory over the coherent NVLink-C2C link, with no separate copy); nullptr
+// for pageable host memory, which goes through the staging buffers.  *host
+// is set when the address is host memory.
+void* direct_ptr(const void* p, bool* host) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return const_cast<void*>(p);
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        *host = true;
+        return a.devicePointer;
+    }
+    return nullptr;
+}
+
 
 
 Geometry make_geometry(int natoms, const double box[3]) {
@@ -1163,13 +1184,15 @@ nb_status nb_forces(nb_sys* sys, const float* x_new, float* f, double* energy, d
     if (!sys->listed) return fail(NB_ERR_STATE, "nb_forces needs a pair list (nb_pairlist_build)");
     Plan* pl = sys->plan;
     cudaStream_t st = sys->ctx->stream;
-    // device arrays of the caller are read and written by the kernels
-    // themselves; host arrays go through the system's staging buffers
+    // device and pinned host arrays of the caller are read and written by
+    // the kernels themselves; pageable host arrays go through the system's
+    // staging buffers
     PlanLaunch ext{};
-    if (x_new && is_device_ptr(x_new)) ext.x_ext = x_new;
-    if (f && is_device_ptr(f)) ext.f_ext = f;
-    if (energy && is_device_ptr(energy)) ext.e_ext = energy;
-    if (virial && is_device_ptr(virial)) ext.v_ext = virial;
+    bool direct_host = false;
+    ext.x_ext = static_cast<const float*>(direct_ptr(x_new, &direct_host));
+    ext.f_ext = static_cast<float*>(direct_ptr(f, &direct_host));
+    ext.e_ext = static_cast<double*>(direct_ptr(energy, &direct_host));
+    ext.v_ext = static_cast<double*>(direct_ptr(virial, &direct_host));
     if (x_new && !ext.x_ext) {
         StageScope sc(sys->ctx, NB_STAGE_COORD);
         NB_CK(cudaMemcpyAsync(sys->h.x_new, x_new, 12 * (size_t)sys->natoms, cudaMemcpyHostToDevice, st));
@@ -1180,7 +1203,9 @@ nb_status nb_forces(nb_sys* sys, const float* x_new, float* f, double* energy, d
     s = copy_out(sys, ext.f_ext ? nullptr : f, ext.e_ext ? nullptr : energy, ext.v_ext ? nullptr : virial,
                  flags, &need_sync);
     if (s != NB_OK) return s;
-    if (need_sync) NB_CK(cudaStreamSynchronize(st));
+    // host memory read or written by the kernels is done with when the call
+    // returns, as with the staged copies
+    if (need_sync || direct_host) NB_CK(cudaStreamSynchronize(st));
     return NB_OK;
 }
 

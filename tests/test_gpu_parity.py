@@ -142,6 +142,36 @@ def test_stale_list_evaluations(ctx):
         nb.nb_sys_destroy(h)
 
 
+@pytest.mark.parametrize("kind", ["pageable", "pinned", "device"])
+def test_caller_buffer_kinds(ctx, kind):
+    """nb_forces with new coordinates and all outputs in pageable host
+    memory (staged copies), pinned host memory (read and written by the
+    kernels through its mapped address) or device memory."""
+    torch = pytest.importorskip("torch")
+    s = wb.small_box(seed=1)
+    p = wb.params_rf()
+    rng = np.random.default_rng(7)
+    x1 = (s.x.astype(np.float64) + rng.normal(0.0, 0.005, size=s.x.shape)).astype(np.float32)
+    h = nb.nb_sys_create(ctx, p, s.n, s.box)
+    try:
+        nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
+        nb.nb_grid_put(h, s.xq(), s.type)
+        nb.nb_pairlist_build(h)
+        if kind == "pageable":
+            x, f, e, v = np.ascontiguousarray(x1), np.zeros((s.n, 3), np.float32), np.zeros(2), np.zeros(9)
+        else:
+            mk = (lambda a: torch.from_numpy(a).pin_memory()) if kind == "pinned" else (lambda a: torch.from_numpy(a).cuda())
+            x, f, e, v = mk(x1), mk(np.zeros((s.n, 3), np.float32)), mk(np.zeros(2)), mk(np.zeros(9))
+        nb.nb_forces(h, x, f, e, v, nb.NB_F_ENERGY | nb.NB_F_VIRIAL)
+        # the call has finished with host memory when it returns
+        if kind != "pageable":
+            f, e, v = (t.cpu().numpy() for t in (f, e, v))
+    finally:
+        nb.nb_sys_destroy(h)
+    s.x = x1
+    _check(s, p, f, e, v)
+
+
 def test_dynamic_pruning(ctx):
     """Outer list at rlist = 1.3 nm built once; pruned out of place to an inner
     list at 1.1 nm every 5 evaluations while the atoms move (Gaussian, sigma
