@@ -272,6 +272,28 @@ def test_single_molecule_has_no_interactions(ctx):
     assert np.all(f == 0) and np.all(e == 0) and np.all(v == 0)
 
 
+def test_a_single_atom_and_no_atoms(ctx):
+    """The degenerate sizes: one atom has no pairs at all (zero forces,
+    energies, virial and pair count); no atoms is refused."""
+    p = wb.params_ewald()
+    h = nb.nb_sys_create(ctx, p, 1, [3.0, 3.0, 3.0])
+    try:
+        nb.nb_set_exclusions(h, np.zeros(2, np.int32), np.zeros(0, np.int32))
+        nb.nb_grid_put(h, np.array([[1.0, 2.0, 0.5, -0.8]], np.float32), np.zeros(1, np.int32))
+        nb.nb_pairlist_build(h)
+        f = np.full((1, 3), 7.0, np.float32)
+        e = np.full(2, 7.0)
+        v = np.full(9, 7.0)
+        nb.nb_forces(h, None, f, e, v, nb.NB_F_ENERGY | nb.NB_F_VIRIAL)
+        assert np.all(f == 0) and np.all(e == 0) and np.all(v == 0)
+        assert nb.nb_eval_info(h)["n_pairs"] == 0
+    finally:
+        nb.nb_sys_destroy(h)
+    with pytest.raises(nb.NbError) as ei:
+        nb.nb_sys_create(ctx, p, 0, [3.0, 3.0, 3.0])
+    assert ei.value.status == 1
+
+
 def test_two_atoms_across_the_boundary(ctx):
     L = wb.f32(2.5)
     s = wb.System(x=np.array([[0.05, 1.0, 1.0], [L - 0.25, 1.0, 1.0]], dtype=np.float32),
