@@ -313,6 +313,12 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             pxq = xq_s[cjn * CL + i];
             pty = type_s[cjn * CL + i];
         }
+        // the list entries one step further ahead, so that the coordinate
+        // loads of the next step never wait on them
+        int e2 = jb + 4 + g;
+        bool act2 = e2 < je;
+        int cjn2 = act2 ? list.cj[e2] : 0;
+        unsigned long long pm2 = act2 ? list.mask[e2] : 0ull;
         for (int base = jb; base < je; base += 4) {
             __syncwarp();
             sjg[st] = pxq.x;
@@ -323,14 +329,20 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             const int ccj = cjn;
             const bool cact = act;
             const unsigned long long cm = pm;
-            e = base + 4 + g;
-            act = e < je;
-            pm = 0ull;
+            act = act2;
+            cjn = cjn2;
+            pm = pm2;
             if (act) {
-                cjn = list.cj[e];
-                pm = list.mask[e];
                 pxq = xq_s[cjn * CL + i];
                 pty = type_s[cjn * CL + i];
+            }
+            e2 = base + 8 + g;
+            act2 = e2 < je;
+            cjn2 = 0;
+            pm2 = 0ull;
+            if (act2) {
+                cjn2 = list.cj[e2];
+                pm2 = list.mask[e2];
             }
             __syncwarp();
             // the lane's mask row (bit t: j-slot t XOR i) in the order of the
