@@ -420,16 +420,27 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
             zi[k] = make_float2(v0.z + Sz, v1.z + Sz);
         }
         int write = item.y;
+        // each chunk's entries are loaded while the previous chunk is tested
+        int c_next = 0;
+        unsigned long long m_next = 0ull;
+        if (lane < item.z - item.y) {
+            c_next = src.cj[item.y + lane];
+            m_next = src.mask[item.y + lane];
+        }
         for (int base = item.y; base < item.z; base += 32) {
             const int n = min(32, item.z - base);
             int cjv = 0;
             unsigned long long m = 0ull;
             bool chk = false;
             if (lane < n) {
-                const int c = src.cj[base + lane];
+                const int c = c_next;
                 chk = inner || (c & PRUNE_CHECK) != 0;
                 cjv = c & ~PRUNE_CHECK;
-                m = src.mask[base + lane];
+                m = m_next;
+            }
+            if (base + 32 + lane < item.z) {
+                c_next = src.cj[base + 32 + lane];
+                m_next = src.mask[base + 32 + lane];
             }
             const unsigned chk_bal = __ballot_sync(FULL, chk);
             unsigned keep = __ballot_sync(FULL, lane < n && !chk);  // bit k: entry base + k is kept
