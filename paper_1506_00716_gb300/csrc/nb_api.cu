@@ -1,9 +1,10 @@
 // nb_api.cu -- the C ABI (include/nb.h): contexts, systems, plans, the
 // batch engine and the long-range (PME) set-up.  Host code only; every
 // arithmetic step of the method runs in the kernels of nb_grid.cu,
-// nb_search.cu, nb_kernel.cu, nb_energy.cu, nb_excl.cu and nb_pme.cu (the
-// host computes only per-mesh constant tables: twiddle factors, B-spline
-// moduli, the influence function's per-axis factors).
+// nb_search.cu, nb_kernel.cu, nb_energy.cu, nb_excl.cu and nb_pme.cu, with
+// the paired float32 helpers of nb_pair2.cuh (the host computes only
+// per-mesh constant tables: twiddle factors, B-spline moduli, the influence
+// function's per-axis factors).
 //
 // A "plan" is a set of systems evaluated by one sequence of launches: a
 // standalone system owns a plan of one, a batch owns a plan over all of its
