@@ -797,9 +797,42 @@ __global__ void __launch_bounds__(PME_THREADS) k_pme_spread(const SysDev* __rest
     spline_tile<P, false>(d, pm, blockIdx.x * APB, nslots, st);
     const int at = threadIdx.x / LPA, c = threadIdx.x % LPA;
     const float q = st.q[at];
-    if (q != 0.f && c < P) {
+    const int K2 = pm.K[2];
+    if (q != 0.f && (K2 & 1) == 0) {
+        // Even z extent: the atom's P z points, zl .. zl + P - 1 (mod K2),
+        // go out as 8-byte reductions of aligned pairs (2k, 2k + 1), which
+        // never straddle a mesh row; lane c takes the c-th pair from zl
+        // rounded down to even, and a pair half outside the atom's points
+        // adds zero.  About 40% fewer L2 atomic operations than one per point.
+        const int zl = wrap_down(st.base[at][2] - (P - 1), K2);
+        const int lo = zl & 1;
+        if (c < P / 2 + lo) {
+            const int bx = st.base[at][0], by = st.base[at][1];
+            const int d0 = 2 * c - lo;  // offset of the pair's first point from zl
+            // the point at offset d from zl has the weight of index P - 1 - d
+            const float w0 = d0 >= 0 ? st.w[at][2][P - 1 - d0] : 0.f;
+            const float w1 = d0 + 1 < P ? st.w[at][2][P - 2 - d0] : 0.f;
+            int iz0 = zl - lo + 2 * c;
+            if (iz0 >= K2) iz0 -= K2;
+            const long long iz = iz0;
+            const float2 qz = make_float2(q * w0, q * w1);
+#pragma unroll
+            for (int a = 0; a < P; ++a) {
+                const long long ix = wrap_down(bx - a, pm.K[0]);
+                const float wa = st.w[at][0][a];
+                const float2 qa = make_float2(qz.x * wa, qz.y * wa);
+#pragma unroll
+                for (int b = 0; b < P; ++b) {
+                    const long long iy = wrap_down(by - b, pm.K[1]);
+                    const float wb = st.w[at][1][b];
+                    atomicAdd(reinterpret_cast<float2*>(pm.Q + (ix * pm.K[1] + iy) * K2 + iz),
+                              make_float2(qa.x * wb, qa.y * wb));
+                }
+            }
+        }
+    } else if (q != 0.f && c < P) {
         const int bx = st.base[at][0], by = st.base[at][1];
-        const long long iz = wrap_down(st.base[at][2] - c, pm.K[2]);
+        const long long iz = wrap_down(st.base[at][2] - c, K2);
         const float qz = q * st.w[at][2][c];
 #pragma unroll
         for (int a = 0; a < P; ++a) {
@@ -808,7 +841,7 @@ __global__ void __launch_bounds__(PME_THREADS) k_pme_spread(const SysDev* __rest
 #pragma unroll
             for (int b = 0; b < P; ++b) {
                 const long long iy = wrap_down(by - b, pm.K[1]);
-                atomicAdd(pm.Q + (ix * pm.K[1] + iy) * pm.K[2] + iz, qa * st.w[at][1][b]);
+                atomicAdd(pm.Q + (ix * pm.K[1] + iy) * K2 + iz, qa * st.w[at][1][b]);
             }
         }
     }
