@@ -406,7 +406,9 @@ nb_status nb_server_submit(nb_server *srv, int natoms, const double box[3], cons
  * Wait up to timeout_us (< 0: no limit) for a ticket and copy its results
  * to host memory: f (natoms*3 floats), energy (2), virial (9), stats; any
  * may be NULL.  NB_ERR_TIMEOUT if not finished in time (the ticket stays
- * valid); each ticket's results can be collected once.
+ * valid); each ticket's results can be collected once.  One thread at a
+ * time may wait on a ticket: a second concurrent wait on the same ticket
+ * fails at once with NB_ERR_ARG.
  */
 nb_status nb_server_wait(nb_server *srv, unsigned long long ticket, long long timeout_us, float *f,
                          double *energy, double *virial, nb_request_stats *stats);
@@ -421,8 +423,8 @@ nb_status nb_server_wait(nb_server *srv, unsigned long long ticket, long long ti
  * One call runs grid put, pair search, prune, forces and (per flags)
  * energies and virial for one system of at most NB_NOALLOC_MAX_ATOMS atoms,
  * using as scratch a fixed device array of NB_NOALLOC_SCRATCH_BYTES that is
- * part of the library (every GPU that loads the library holds it until the
- * process exits).  It calls no cudaMalloc, cudaFree or allocating library
+ * part of the library (every GPU that loads it holds it until the process
+ * exits; see below for when it is loaded).  It calls no cudaMalloc, cudaFree or allocating library
  * routine.
  *   params, natoms, box  as nb_sys_create
  *   excl_index,          host CSR of exclusions (may both be NULL); unlike
@@ -434,9 +436,17 @@ nb_status nb_server_wait(nb_server *srv, unsigned long long ticket, long long ti
  *   cuda_stream          the stream to run on (NULL = legacy default stream);
  *                        the calling thread's current CUDA device is used
  * Returns NB_ERR_CAPACITY if natoms exceeds the maximum or the pair list
- * does not fit the scratch array.  Synchronises the stream before returning.
+ * does not fit the scratch array; the outputs are then left untouched (the
+ * overflow is detected after the search, before any force is evaluated).
+ * After any other error the contents of f, energy and virial are undefined.
+ * Synchronises the stream after the search and before returning.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress), so make the first call before any stream capture.
+ * Under lazy module loading (CUDA_MODULE_LOADING=LAZY, the default of recent
+ * CUDA releases) that lookup also loads the library's module holding the
+ * array, so the first call on each device is the one that reserves its
+ * NB_NOALLOC_SCRATCH_BYTES, and it fails with NB_ERR_CUDA (out of memory)
+ * if the device has no room left for it.
  * All calls share the scratch array: calls whose GPU work overlaps (other
  * streams or host threads on the same device) race and must be serialised
  * by the caller.

@@ -55,6 +55,9 @@ struct Request {
     std::string err;
     Clock::time_point t_submit, t_admit, t_done;
     bool done = false;
+    // a thread is inside nb_server_wait for this request (set and cleared
+    // under the server's mutex); a second waiter is refused
+    bool claimed = false;
 };
 
 // Growable pinned host buffer.
@@ -493,12 +496,17 @@ nb_status nb_server_wait(nb_server* s, unsigned long long ticket, long long time
     auto it = s->reqs.find(ticket);
     if (it == s->reqs.end()) return fail(NB_ERR_ARG, "unknown or already collected ticket");
     Request* r = it->second;
+    if (r->claimed) return fail(NB_ERR_ARG, "another thread is already waiting on this ticket");
+    r->claimed = true;
     auto ready = [&] { return r->done; };
-    if (timeout_us < 0)
+    if (timeout_us < 0) {
         s->cv_done.wait(lock, ready);
-    else if (!s->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), ready))
+    } else if (!s->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), ready)) {
+        r->claimed = false;
         return fail(NB_ERR_TIMEOUT, "request not finished within the timeout");
-    s->reqs.erase(it);
+    }
+    // by key: submissions during the wait may have rehashed the map
+    s->reqs.erase(ticket);
     lock.unlock();
     nb_status st = r->status;
     if (st == NB_OK) {

@@ -6,8 +6,12 @@
 // host process that only owns a stream).
 //
 // The scratch array below is part of this library's device image: every GPU
-// that loads the library reserves NB_NOALLOC_SCRATCH_BYTES for it until the
-// process exits.  Host code cannot use the array's name as a device address
+// that loads the library's device code reserves NB_NOALLOC_SCRATCH_BYTES for
+// it until the process exits.  Under lazy module loading (CUDA_MODULE_LOADING
+// = LAZY, the default of recent CUDA releases) that happens at the first
+// nb_eval_noalloc call on a device, whose cudaGetSymbolAddress loads this
+// file's module; that call can therefore fail with out-of-memory on a device
+// that is already full.  Host code cannot use the array's name as a device address
 // (in host code it names a host-side shadow), so its device address is
 // looked up once per device with cudaGetSymbolAddress and passed to the
 // kernels as a plain pointer.
@@ -80,18 +84,25 @@ extern "C" nb_status nb_eval_noalloc(const nb_params* params, int natoms, const 
     if ((flags & NB_F_VIRIAL) && !virial) return api_fail(NB_ERR_ARG, "NB_F_VIRIAL needs virial");
     int nnz = 0;
     if (excl_index) {
+        // the index array first (non-decreasing from 0), so that no partner
+        // range read below lies outside excl_atoms[0 .. nnz)
         if (excl_index[0] != 0) return api_fail(NB_ERR_ARG, "excl_index[0] must be 0");
-        for (int a = 0; a < natoms; ++a) {
+        for (int a = 0; a < natoms; ++a)
             if (excl_index[a + 1] < excl_index[a]) return api_fail(NB_ERR_ARG, "excl_index must be non-decreasing");
+        nnz = excl_index[natoms];
+        if (nnz > 0 && !excl_atoms) return api_fail(NB_ERR_ARG, "excl_atoms is NULL but excl_index lists partners");
+        // then every partner, before any partner's own range is read
+        for (int k = 0; k < nnz; ++k)
+            if (excl_atoms[k] < 0 || excl_atoms[k] >= natoms) return api_fail(NB_ERR_ARG, "bad exclusion partner");
+        for (int a = 0; a < natoms; ++a) {
             for (int k = excl_index[a]; k < excl_index[a + 1]; ++k) {
                 int b = excl_atoms[k];
-                if (b < 0 || b >= natoms || b == a) return api_fail(NB_ERR_ARG, "bad exclusion partner");
+                if (b == a) return api_fail(NB_ERR_ARG, "bad exclusion partner");
                 bool mirrored = false;
                 for (int m = excl_index[b]; m < excl_index[b + 1]; ++m) mirrored = mirrored || excl_atoms[m] == a;
                 if (!mirrored) return api_fail(NB_ERR_ARG, "exclusions must list every pair under both atoms");
             }
         }
-        nnz = excl_index[natoms];
     }
     const int nt = params->ntypes;
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -197,6 +208,14 @@ extern "C" nb_status nb_eval_noalloc(const nb_params* params, int natoms, const 
     }
     NA_CK(launch_grid_put(p, st));
     NA_CK(launch_search(p, st));
+    // the search reports a list that outgrew the scratch array; stop there,
+    // before anything is evaluated or written to the caller's outputs
+    int counters[CNT_N] = {0};
+    NA_CK(cudaMemcpyAsync(counters, d_counters, sizeof(counters), cudaMemcpyDeviceToHost, st));
+    NA_CK(cudaStreamSynchronize(st));
+    if (e != cudaSuccess) return api_fail(NB_ERR_CUDA, cudaGetErrorString(e));
+    if (counters[CNT_OVERFLOW] & 3)
+        return api_fail(NB_ERR_CAPACITY, "nb_eval_noalloc: the pair list outgrew the scratch array");
     NA_CK(launch_prune(p, st));
     NA_CK(launch_prepare(p, false, st));
     NA_CK(launch_forces(p, flags, st));
@@ -206,12 +225,8 @@ extern "C" nb_status nb_eval_noalloc(const nb_params* params, int natoms, const 
     if (f) NA_CK(cudaMemcpyAsync(f, h.f_out, 12 * (size_t)natoms, cudaMemcpyDefault, st));
     if (flags & NB_F_ENERGY) NA_CK(cudaMemcpyAsync(energy, h.res, 16, cudaMemcpyDefault, st));
     if (flags & NB_F_VIRIAL) NA_CK(cudaMemcpyAsync(virial, h.res + 2, 72, cudaMemcpyDefault, st));
-    int counters[CNT_N] = {0};
-    NA_CK(cudaMemcpyAsync(counters, d_counters, sizeof(counters), cudaMemcpyDeviceToHost, st));
     NA_CK(cudaStreamSynchronize(st));
 #undef NA_CK
     if (e != cudaSuccess) return api_fail(NB_ERR_CUDA, cudaGetErrorString(e));
-    if (counters[CNT_OVERFLOW] & 3)
-        return api_fail(NB_ERR_CAPACITY, "nb_eval_noalloc: the pair list outgrew the scratch array");
     return NB_OK;
 }
