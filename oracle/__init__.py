@@ -67,6 +67,8 @@ def _load():
     lib.or_forces.restype = ctypes.c_int
     lib.or_pairs.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ip, ip, lp, ip]
     lib.or_pairs.restype = ctypes.c_longlong
+    lib.or_pairs_rows.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ip, ip, ctypes.c_int, ip, lp, ip]
+    lib.or_pairs_rows.restype = ctypes.c_longlong
     lib.or_num_threads.argtypes = []
     lib.or_num_threads.restype = ctypes.c_int
     _lib = lib
@@ -161,6 +163,30 @@ def pairs(sys, r_cut: float) -> np.ndarray:
         raise RuntimeError("oracle pairs count mismatch")
     out = out[:total].astype(np.int64)
     return out[:, 0] * sys.n + out[:, 1]
+
+
+def pairs_of_rows(sys, r_cut: float, sel) -> np.ndarray:
+    """Sorted unique int64 keys min(i,j) * n + max(i,j) of every non-excluded pair
+    with r < r_cut that has at least one atom in `sel` (O(N) per selected atom)."""
+    lib = _load()
+    x, xp = _d(sys.x.astype(np.float64))
+    b, bp = _box6(sys)
+    ei, eip = _i(sys.excl_index)
+    ea, eap = _i(sys.excl_atoms)
+    s, sp = _i(np.asarray(sel))
+    nsel = int(s.shape[0])
+    counts = np.zeros(max(nsel, 1), dtype=np.int64)
+    cp = counts.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
+    total = lib.or_pairs_rows(sys.n, xp, bp, float(r_cut), eip, eap, nsel, sp, cp, None)
+    if total < 0:
+        raise RuntimeError("oracle pairs_of_rows failed")
+    out = np.zeros((max(total, 1), 2), dtype=np.int32)
+    got = lib.or_pairs_rows(sys.n, xp, bp, float(r_cut), eip, eap, nsel, sp, cp,
+                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if got != total:
+        raise RuntimeError("oracle pairs_of_rows count mismatch")
+    out = out[:total].astype(np.int64)
+    return np.unique(out[:, 0] * sys.n + out[:, 1])
 
 
 def num_threads() -> int:

@@ -347,6 +347,68 @@ long long or_pairs(int n, const double *x, const double *box, double r_cut, cons
     return total;
 }
 
+/*
+ * The interacting pairs of selected atoms: for each selected atom i =
+ * sel[k], every other atom j (either side of i), not excluded, with
+ * minimum-image r^2 < r_cut^2 (double precision), reported as the unordered
+ * pair (min(i, j), max(i, j)).  This is the row i of the plain definition
+ * above, so the union over all atoms is the set or_pairs gives; it costs
+ * O(N) per selected atom and so reaches boxes where the full O(N^2) set is
+ * out of reach.  counts: nsel entries.  If pairs != NULL it receives 2 ints
+ * per pair, ordered by k then j, and must hold the total of a previous
+ * count-only call.  Returns the total, or -1.  A pair of two selected atoms
+ * appears under both of them.
+ */
+long long or_pairs_rows(int n, const double *x, const double *box, double r_cut, const int *excl_index,
+                        const int *excl_atoms, int nsel, const int *sel, long long *counts, int *pairs) {
+    if (n < 0 || nsel < 0 || !counts || !sel) return -1;
+    for (int k = 0; k < nsel; ++k)
+        if (sel[k] < 0 || sel[k] >= n) return -1;
+    double rc2 = r_cut * r_cut;
+    if (!pairs) {
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int k = 0; k < nsel; ++k) {
+            int i = sel[k];
+            long long c = 0;
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                double dx, dy, dz;
+                pair_image(box, x[3 * i + 0] - x[3 * j + 0], x[3 * i + 1] - x[3 * j + 1],
+                           x[3 * i + 2] - x[3 * j + 2], &dx, &dy, &dz);
+                if (!(dx * dx + dy * dy + dz * dz < rc2)) continue;
+                if (excluded(i, j, excl_index, excl_atoms)) continue;
+                ++c;
+            }
+            counts[k] = c;
+        }
+    }
+    long long total = 0;
+    for (int k = 0; k < nsel; ++k) total += counts[k];
+    if (!pairs) return total;
+    long long *start = (long long *)malloc(sizeof(long long) * (size_t)(nsel + 1));
+    if (!start) return -1;
+    start[0] = 0;
+    for (int k = 0; k < nsel; ++k) start[k + 1] = start[k] + counts[k];
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int k = 0; k < nsel; ++k) {
+        int i = sel[k];
+        long long w = start[k];
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx, dy, dz;
+            pair_image(box, x[3 * i + 0] - x[3 * j + 0], x[3 * i + 1] - x[3 * j + 1],
+                       x[3 * i + 2] - x[3 * j + 2], &dx, &dy, &dz);
+            if (!(dx * dx + dy * dy + dz * dz < rc2)) continue;
+            if (excluded(i, j, excl_index, excl_atoms)) continue;
+            pairs[2 * w + 0] = i < j ? i : j;
+            pairs[2 * w + 1] = i < j ? j : i;
+            ++w;
+        }
+    }
+    free(start);
+    return total;
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -76,11 +76,17 @@ def main():
     e2 = float(np.abs(np.polynomial.polynomial.polyval(ff, a2) / np.exp2(ff) - 1.0).max())
     a2_hi = a2.astype(np.float32)
     a2_lo = (a2 - a2_hi.astype(np.float64)).astype(np.float32)
+    # the errors of the coefficients as stored: float32 (force fit), float32
+    # head + float32 tail (energy fit), each evaluated exactly in float64
+    af_st = af.astype(np.float32).astype(np.float64)
+    ae_st = ae_hi.astype(np.float64) + ae_lo.astype(np.float64)
     lines = [
         "// erfc_fit.cuh -- generated by fit_erfc.py; do not edit.",
         "// erfc(x) = exp(-x^2) R(u), t = 1/(1 + EF_P x), u = EF_UA t + EF_UB, x in [0, EF_XMAX].",
-        f"// force fit: degree {len(af) - 1}, max relative error {max_rel_error(af):.2e}",
-        f"// energy fit: degree {len(ae) - 1}, max relative error {max_rel_error(ae):.2e}",
+        f"// force fit: degree {len(af) - 1}, max relative error {max_rel_error(af):.2e}"
+        f" ({max_rel_error(af_st):.2e} with the float32 coefficients below)",
+        f"// energy fit: degree {len(ae) - 1}, max relative error {max_rel_error(ae):.2e}"
+        f" ({max_rel_error(ae_st):.2e} with the head + tail coefficients below)",
         "#pragma once",
         "namespace nbgb {",
         f"constexpr float EF_P = {fmt(P)};",

@@ -25,7 +25,7 @@
 //   RF:    F/r = f qi qj (r^-3 - 2 k_rf)
 //   Ewald: F/r = f qi qj (erfc(b r)/r + 2b/sqrt(pi) exp(-b^2 r^2)) / r^2
 // with erfc(x) = exp(-x^2) R(u) from the degree-8 least-squares fit of
-// erfc_fit.cuh (relative error 2e-8).  Optional virial
+// erfc_fit.cuh (relative error 1.3e-7 with its float32 coefficients).  Optional virial
 // Xi = -1/2 sum_pairs (F/r) d (x) d, summed per pair in float32 and across
 // items in float64.
 //

@@ -80,3 +80,56 @@ def expand_pairs(sys, perm, items, cj, mask, r_cut, chunk=20000):
 
 def rel_rms(f, ref):
     return float(np.sqrt(((f - ref) ** 2).mean()) / np.sqrt((ref ** 2).mean()))
+
+
+def expand_pairs_of_rows(sys, perm, items, cj, mask, r_cut, sel, chunk=200000):
+    """Atom pairs (min * n + max keys, unique, sorted) of the list that touch an
+    atom of `sel` and lie closer than r_cut under their entry's shift (float64
+    distance of the float32 inputs), and the number of (pair, shift)
+    occurrences among them (more than the unique keys = a pair listed twice).
+
+    Only the entries whose i- or j-cluster holds a selected atom are expanded,
+    so a list of tens of millions of entries stays within seconds."""
+    n = sys.n
+    x = sys.x.astype(np.float64)
+    L = sys.box
+    bx, cx, cy = getattr(sys, "skew", np.zeros(3))
+    sel = np.asarray(sel, dtype=np.int64)
+    is_sel = np.zeros(n, dtype=bool)
+    is_sel[sel] = True
+    ncl = perm.shape[0] // 8
+    slot_atom = perm.reshape(ncl, 8)
+    cl_sel = ((slot_atom >= 0) & is_sel[np.maximum(slot_atom, 0)]).any(1)
+    lens = (items[:, 2] - items[:, 1]).astype(np.int64)
+    total = int(lens.sum())
+    ent_item = np.repeat(np.arange(items.shape[0]), lens)
+    offs = np.cumsum(lens) - lens
+    ent_idx = np.arange(total, dtype=np.int64) - np.repeat(offs, lens) + np.repeat(items[:, 1].astype(np.int64), lens)
+    keep = cl_sel[items[ent_item, 0]] | cl_sel[cj[ent_idx]]
+    ent_item, ent_idx = ent_item[keep], ent_idx[keep]
+    bits = np.arange(64, dtype=np.uint64)
+    keys_all = []
+    count = 0
+    for s in range(0, ent_idx.shape[0], chunk):
+        e = ent_idx[s:s + chunk]
+        it = items[ent_item[s:s + chunk]]
+        on = ((mask[e][:, None] >> bits[None, :]) & np.uint64(1)).astype(bool)
+        er, bit = np.nonzero(on)
+        i = bit // 8
+        j = (bit % 8) ^ i
+        a = perm[it[er, 0] * 8 + i]
+        b = perm[cj[e[er]] * 8 + j]
+        sh = it[er, 3]
+        ok = (a >= 0) & (b >= 0)
+        a, b, sh = a[ok], b[ok], sh[ok]
+        ok = is_sel[a] | is_sel[b]
+        a, b, sh = a[ok], b[ok], sh[ok]
+        sx, sy, sz = sh // 9 - 1, (sh // 3) % 3 - 1, sh % 3 - 1
+        S = np.stack([sx * L[0] + sy * bx + sz * cx, sy * L[1] + sz * cy, sz * L[2]], axis=1)
+        d = x[a] + S - x[b]
+        w = (d * d).sum(1) < r_cut * r_cut
+        a, b = a[w], b[w]
+        count += a.shape[0]
+        keys_all.append(np.minimum(a, b).astype(np.int64) * n + np.maximum(a, b))
+    keys = np.unique(np.concatenate(keys_all)) if keys_all else np.zeros(0, dtype=np.int64)
+    return keys, count

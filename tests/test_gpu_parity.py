@@ -406,3 +406,38 @@ def test_budget_refuses_without_allocating(ctx):
         assert nb.nb_ctx_memory(c)[0] == 0
     finally:
         nb.nb_ctx_destroy(c)
+
+
+def test_device_erfc_two_atom_pairs(ctx):
+    """The kernels' erfc on the device, one atom pair at a time: two unit
+    charges without Lennard-Jones at distance r in (0.02, rc), Ewald real
+    space.  The energy kernel's double-float V = f erfc(beta r) / r against
+    the standard library's erfc at 2e-9 relative (its erfc is good to 1e-9,
+    see tests/test_erfc_fit_cpu.py), and the force kernel's float32
+    F = f (erfc(beta r)/r + 2 beta/sqrt(pi) exp(-beta^2 r^2)) / r against the
+    same formula at 2e-6 relative (SFU rsqrt, reciprocal and 2^x, the fit's
+    1.3e-7 and a few float32 roundings)."""
+    import math
+
+    p = wb.params_ewald()
+    p = dataclasses.replace(p, c6=np.zeros(4, dtype=np.float32), c12=np.zeros(4, dtype=np.float32))
+    L = 2.4
+    x0 = np.float32(0.7)
+    worst_e = worst_f = 0.0
+    for r_want in np.concatenate([np.geomspace(0.02, 0.2, 8), np.linspace(0.21, 0.999, 40)]):
+        x1 = np.float32(x0 + np.float32(r_want))
+        r = float(x1) - float(x0)  # exact: both coordinates are float32
+        xq = np.array([[x0, 1.2, 1.2, 1.0], [x1, 1.2, 1.2, 1.0]], dtype=np.float32)
+        s = wb.System(x=xq[:, :3].copy(), q=xq[:, 3].copy(), type=np.array([1, 1], dtype=np.int32),
+                      box=np.array([L, L, L]), excl_index=np.zeros(3, dtype=np.int32),
+                      excl_atoms=np.zeros(0, dtype=np.int32), n_mol=0, seed=0)
+        f, e, v, _ = gpu_eval(ctx, s, p)
+        br = p.beta * r
+        v_ref = p.fcoul * math.erfc(br) / r
+        f_ref = p.fcoul * (math.erfc(br) / r + 2.0 * p.beta / math.sqrt(math.pi) * math.exp(-br * br)) / r
+        # the force on atom 0 points away from atom 1 (repulsion), along -x
+        worst_e = max(worst_e, abs(e[1] - v_ref) / abs(v_ref))
+        worst_f = max(worst_f, abs(-float(f[0, 0]) - f_ref) / f_ref, abs(float(f[1, 0]) - f_ref) / f_ref)
+        assert e[0] == 0.0 and f[0, 1] == 0.0 and f[0, 2] == 0.0
+    assert worst_e <= 2e-9, worst_e
+    assert worst_f <= 2e-6, worst_f

@@ -432,6 +432,33 @@ def test_triclinic_pair_set_matches_lattice_enumeration():
         assert np.array_equal(oracle.pairs(sys, r_cut), _lattice_images(sys, r_cut))
 
 
+def _rows_of(keys, n, sel):
+    a, b = keys // n, keys % n
+    return keys[np.isin(a, sel) | np.isin(b, sel)]
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_pairs_of_rows_are_rows_of_the_27_image_enumeration(seed):
+    """The row-wise pair oracle (O(N) per selected atom, for boxes where the
+    whole set is out of reach) against the brute-force enumeration: every
+    pair touching a selected atom, and with all atoms selected the whole set."""
+    sys = wb.water_box(120, 2.3, seed=seed)
+    rng = np.random.default_rng(seed)
+    for r_cut in (1.0, 1.1):
+        ref = _pairs_27_images(sys, r_cut)
+        sel = np.sort(rng.choice(sys.n, size=37, replace=False)).astype(np.int32)
+        assert np.array_equal(oracle.pairs_of_rows(sys, r_cut, sel), _rows_of(ref, sys.n, sel))
+        allrows = oracle.pairs_of_rows(sys, r_cut, np.arange(sys.n, dtype=np.int32))
+        assert np.array_equal(allrows, ref)
+
+
+def test_triclinic_pairs_of_rows_match_lattice_enumeration():
+    sys = wb.rhombic_dodecahedron_box(120, seed=31)
+    ref = _lattice_images(sys, 1.0)
+    sel = np.arange(0, sys.n, 7, dtype=np.int32)
+    assert np.array_equal(oracle.pairs_of_rows(sys, 1.0, sel), _rows_of(ref, sys.n, sel))
+
+
 @pytest.mark.parametrize("coul", [wb.COUL_RF, wb.COUL_EWALD])
 def test_rectangular_lattice_in_triclinic_form(coul):
     """The rectangular lattice written with other rows (b' = a + b,
