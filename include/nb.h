@@ -159,10 +159,16 @@ enum {
  *   force_min_blocks  register budget of the force kernel, as the number of
  *                     256-thread blocks guaranteed resident per SM: 1 (up to
  *                     255 registers per thread), 2 (128) or 3 (85, default)
+ *   search_mode       cluster-pair search: 1 = one warp per i-cluster (lanes
+ *                     share its candidates), 2 = one thread per i-cluster
+ *                     (count, scan and write passes, no atomics), 0 = by
+ *                     size (default: a thread per cluster from about eight
+ *                     warps' worth of clusters per SM).  The list is the same.
  */
 typedef struct {
     int max_entries;
     int force_min_blocks;
+    int search_mode;
 } nb_tuning;
 
 /* Message of the calling thread's last failure ("" if none). */

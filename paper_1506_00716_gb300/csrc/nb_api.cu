@@ -565,6 +565,7 @@ PlanLaunch launch_of(const Plan* pl) {
     PlanLaunch p{};
     const_cast<Plan*>(pl)->kp.max_entries = pl->ctx->tuning.max_entries;
     const_cast<Plan*>(pl)->kp.force_min_blocks = pl->ctx->tuning.force_min_blocks;
+    const_cast<Plan*>(pl)->kp.search_mode = pl->ctx->tuning.search_mode;
     const_cast<Plan*>(pl)->kp.lpt_max_items = LPT_ITEMS_PER_WARP * LPT_WARPS_PER_SM * pl->ctx->num_sms;
     int n = (int)pl->systems.size();
     p.nsys = n;
@@ -866,6 +867,7 @@ nb_status nb_ctx_set_tuning(nb_ctx* ctx, const nb_tuning* t) {
     if (!ctx || !t) return fail(NB_ERR_ARG, "ctx / tuning is NULL");
     if (t->max_entries < 4 || t->max_entries > 4096) return fail(NB_ERR_ARG, "max_entries must be in 4..4096");
     if (t->force_min_blocks < 1 || t->force_min_blocks > 3) return fail(NB_ERR_ARG, "force_min_blocks must be 1, 2 or 3");
+    if (t->search_mode < 0 || t->search_mode > 2) return fail(NB_ERR_ARG, "search_mode must be 0, 1 or 2");
     ctx->tuning = *t;
     ctx->tuning_gen += 1;
     return NB_OK;

@@ -54,7 +54,8 @@ struct SysDev {
     int* col_cl0;        // [ncol + 1] first cluster of each column; [ncol] = #clusters
     int* atom_col;       // [natoms]
     int* atom_slot;      // [natoms] arrival slot inside the column (pre-sort)
-    unsigned long long* keys;  // [slots] (z key << 32 | atom) in column order
+    unsigned long long* keys;  // [slots] (z key << 32 | atom) in column order; after the
+                               // grid put, scratch of the thread-per-cluster search
     float4* xq_s;        // [slots] sorted x y z q (fillers: far away, q = 0)
     int* type_s;         // [slots]
     int* perm;           // [slots] original atom of each slot, -1 = filler
@@ -130,6 +131,7 @@ struct KParams {
     float ewc_h, ewc_l;  // erfc(beta rc) / rc as hi + lo (NB_MOD_EWALD_SHIFT)
     double fq_d, krf_d, crf_d;  // f / eps_r, k_rf, c_rf in float64 (NB_MOD_RF_EXCL)
     int max_entries;     // list entries per work item (items are split beyond)
+    int search_mode;     // 0: by size, 1: a warp per i-cluster, 2: a thread per i-cluster
     int lpt_max_items;   // item count up to which items run longest first
     int force_min_blocks;  // force-kernel launch-bounds variant: 1, 2 or 3
     const float2* lj;    // [ntypes^2] (6 c6, 12 c12), force kernel

@@ -268,19 +268,24 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
                         const float fx0 = cx * d.cw[0] - eps, fx1 = (cx + 1) * d.cw[0] + eps;
                         const float fy0 = cy * d.cw[1] - eps, fy1 = (cy + 1) * d.cw[1] + eps;
                         const float gx = gap(lx, hx, fx0, fx1), gy = gap(ly, hy, fy0, fy1);
-                        if (gx * gx + gy * gy < rl2) {
-                            const int col = cx * d.ncy + cy;
-                            const int a0 = d.col_cl0[col], b0 = d.col_cl0[col + 1];
+                        const int col = cx * d.ncy + cy;
+                        // the half list keeps cur > ci (cur == ci only for the
+                        // zero and "positive" shifts): columns numbered wholly
+                        // below ci hold no candidate
+                        const int lo_c = shift >= SHIFT_ZERO ? ci : ci + 1;
+                        const int b0 = d.col_cl0[col + 1];
+                        if (gx * gx + gy * gy < rl2 && b0 > lo_c) {
+                            const int a0 = d.col_cl0[col];
                             const float cl_per_z = (float)(b0 - a0) * izl;
                             // first cluster with top >= zmin, and first with
                             // bottom > zmax (tops and bottoms ascend along the
                             // column)
                             // (independent of each other: clusters before a
                             // have bottom <= top < zmin <= zmax)
-                            const int a = window_bound<true>(d.bb, a0, b0, zmin, a0 + (int)(zmin * cl_per_z));
+                            const int a = max(lo_c, window_bound<true>(d.bb, a0, b0, zmin, a0 + (int)(zmin * cl_per_z)));
                             const int u = window_bound<false>(d.bb, a0, b0, zmax, a0 + (int)(zmax * cl_per_z));
                             c0 = a;
-                            cnt = u - a;
+                            cnt = max(0, u - a);
                         }
                     }
                     int incl = cnt;
@@ -370,7 +375,306 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
     flush(sm, nbuf, nruns, ci, sid, list, lane, kp.max_entries);
 }
 
+// ------------------------------------------- search, one thread per cluster
+//
+// For systems with many clusters the search takes one thread per i-cluster.
+// It tests the same candidates with the same rule as k_search, but a thread
+// walks its cluster's images, columns and z-windows on its own, with no
+// coordination between lanes, and writes into a range of the list reserved
+// for its cluster, with no atomics.  Three launches:
+//   k_tsearch<false>  count, per cluster, the entries that pass the box test
+//                     and the work items they make (one per run of equal
+//                     shift, split into pieces of at most max_entries);
+//                     exclusive scan of both over the block
+//   k_tsearch_scan    exclusive scan of the block totals (one block), the
+//                     list's entry and item counts, capacity check
+//   k_tsearch<true>   the same walk again, writing each entry (mask, and
+//                     the PRUNE_CHECK mark of entries whose boxes are not
+//                     clearly inside the radius) and each item at the
+//                     cluster's offsets; the prune follows as for k_search.
+// The per-cluster offsets live in the grid put's sort-key buffer, which is
+// not used again until the next grid put: cluster c's first key slot holds
+// its (entries, items) offsets packed into 64 bits, and the second slot of a
+// block's first cluster holds the block's totals, then its offsets.
+constexpr int TS_BLOCK = 128;
+constexpr int TS_EXK = 16;  // exclusion partners of a cluster kept in registers
+
+__device__ __forceinline__ unsigned long long* ts_slot(const SysDev& d, int c, int k) {
+    return d.keys + (size_t)c * CL + k;
+}
+
+// Walk one i-cluster's candidates.  Counting: returns the entry and item
+// counts.  Writing: writes the entries from base_e and the items from
+// base_i.
+template <bool WRITE>
+__device__ void ts_cluster(const SysDev& d, int sid, int ci, int max_entries, const ListDev& list,
+                           const unsigned long long* s_colmask, unsigned long long s_diag, int base_e, int base_i,
+                           int& n_e, int& n_i) {
+    const float4 lo_i = d.bb[2 * ci];
+    const float4 hi_i = d.bb[2 * ci + 1];
+    const int nri = (int)lo_i.w;
+    const unsigned long long rmask_i = row_mask(nri);
+    const float rl = d.rl_search;
+    const float rl2 = rl * rl;
+    const float izl = 1.f / d.L[2];
+    const float rbb = fmaxf(0.f, rl - PRUNE_SURE_MARGIN);
+    const float rbb2 = rbb * rbb;
+    const float eps = 1e-5f * fmaxf(1.f, fmaxf(d.L[0], fmaxf(d.L[1], d.L[2])));
+
+    // exclusion partners (sorted slot << 3 | i-slot) of the cluster's atoms
+    int exs[TS_EXK];
+    int n_ex = 0;
+    unsigned long long xfilter = 0;
+    if (WRITE && d.excl_index != nullptr) {
+        for (int ii = 0; ii < nri; ++ii) {
+            const int a = d.perm[ci * CL + ii];
+            for (int e = d.excl_index[a]; e < d.excl_index[a + 1]; ++e) {
+                const int p = d.iperm[d.excl_atoms[e]];
+                xfilter |= 1ull << ((p >> 3) & 63);
+                if (n_ex < TS_EXK) exs[n_ex] = (p << 3) | ii;
+                ++n_ex;
+            }
+        }
+    }
+
+    int w_e = 0, w_i = 0;
+    // images of the i-cluster (as in k_search; z first)
+    const float rle2 = (rl + eps) * (rl + eps);
+    for (int sz = -1; sz <= 1; ++sz) {
+        const float Sz = sz * d.L[2];
+        const float lz = lo_i.z + Sz, hz = hi_i.z + Sz;
+        const float gz = gap(lz, hz, 0.f, d.L[2]);
+        if (gz * gz >= rle2) continue;
+        for (int sy = -1; sy <= 1; ++sy) {
+            const float Sy = fmaf((float)sz, d.T[2], sy * d.L[1]);
+            const float ly = lo_i.y + Sy, hy = hi_i.y + Sy;
+            const float gy = gap(ly, hy, 0.f, d.L[1]);
+            if (gy * gy + gz * gz >= rle2) continue;
+            for (int sx = -1; sx <= 1; ++sx) {
+                const float Sx = fmaf((float)sz, d.T[1], fmaf((float)sy, d.T[0], sx * d.L[0]));
+                const float lx = lo_i.x + Sx, hx = hi_i.x + Sx;
+                const float gx = gap(lx, hx, 0.f, d.L[0]);
+                if (gx * gx + gy * gy + gz * gz >= rle2) continue;
+                const int shift = shift_index(sx, sy, sz);
+                const int cx0 = max(0, (int)floorf((lx - rl) * d.icw[0]) - 1);
+                const int cx1 = min(d.ncx - 1, (int)floorf((hx + rl) * d.icw[0]) + 1);
+                const int cy0 = max(0, (int)floorf((ly - rl) * d.icw[1]) - 1);
+                const int cy1 = min(d.ncy - 1, (int)floorf((hy + rl) * d.icw[1]) + 1);
+                const float zmin = lz - rl, zmax = hz + rl;
+                const int run0 = w_e;
+                for (int cx = cx0; cx <= cx1; ++cx) {
+                    const float fx0 = cx * d.cw[0] - eps, fx1 = (cx + 1) * d.cw[0] + eps;
+                    const float gcx = gap(lx, hx, fx0, fx1);
+                    if (gcx * gcx >= rl2) continue;
+                    for (int cy = cy0; cy <= cy1; ++cy) {
+                        const float fy0 = cy * d.cw[1] - eps, fy1 = (cy + 1) * d.cw[1] + eps;
+                        const float gcy = gap(ly, hy, fy0, fy1);
+                        if (gcx * gcx + gcy * gcy >= rl2) continue;
+                        const int col = cx * d.ncy + cy;
+                        const int a0 = d.col_cl0[col], b0 = d.col_cl0[col + 1];
+                        // the half list keeps cur > ci (cur == ci only for the zero
+                        // and "positive" shifts): columns numbered wholly below ci
+                        // hold no candidate
+                        const int lo_c = shift >= SHIFT_ZERO ? ci : ci + 1;
+                        if (b0 <= lo_c) continue;
+                        const float cl_per_z = (float)(b0 - a0) * izl;
+                        const int a = max(lo_c, window_bound<true>(d.bb, a0, b0, zmin, a0 + (int)(zmin * cl_per_z)));
+                        const int u = window_bound<false>(d.bb, a0, b0, zmax, a0 + (int)(zmax * cl_per_z));
+                        // each candidate's box is loaded one step ahead
+                        float4 ln = make_float4(0.f, 0.f, 0.f, 0.f), hn = ln;
+                        if (a < u) {
+                            ln = d.bb[2 * a];
+                            hn = d.bb[2 * a + 1];
+                        }
+                        for (int cur = a; cur < u; ++cur) {
+                            const float4 lj = ln;
+                            const float4 hj = hn;
+                            if (cur + 1 < u) {
+                                ln = d.bb[2 * cur + 2];
+                                hn = d.bb[2 * cur + 3];
+                            }
+                            const float gjx = gap(lx, hx, lj.x, hj.x);
+                            const float gjy = gap(ly, hy, lj.y, hj.y);
+                            const float gjz = gap(lz, hz, lj.z, hj.z);
+                            const float g2 = gjx * gjx + gjy * gjy + gjz * gjz;
+                            if (!(g2 < rl2)) continue;
+                            if (WRITE) {
+                                unsigned long long m = (cur == ci && shift == SHIFT_ZERO) ? s_diag : ~0ull;
+                                m &= rmask_i & s_colmask[(int)lj.w];
+                                if ((xfilter >> (cur & 63)) & 1ull) {
+                                    if (n_ex <= TS_EXK) {
+                                        for (int q = 0; q < n_ex; ++q) {
+                                            const int p = exs[q] >> 3;
+                                            if ((p >> 3) == cur) m &= ~(1ull << rot_bit(exs[q] & 7, p & 7));
+                                        }
+                                    } else {
+                                        for (int ii = 0; ii < nri; ++ii) {
+                                            const int aa = d.perm[ci * CL + ii];
+                                            for (int e = d.excl_index[aa]; e < d.excl_index[aa + 1]; ++e) {
+                                                const int p = d.iperm[d.excl_atoms[e]];
+                                                if ((p >> 3) == cur) m &= ~(1ull << rot_bit(ii, p & 7));
+                                            }
+                                        }
+                                    }
+                                }
+                                list.cj[base_e + w_e] = g2 < rbb2 ? cur : (cur | PRUNE_CHECK);
+                                list.mask[base_e + w_e] = m;
+                            }
+                            ++w_e;
+                        }
+                    }
+                }
+                // the run of this shift as items of at most max_entries entries
+                const int len = w_e - run0;
+                if (len > 0) {
+                    if (WRITE) {
+                        const int w = (sid << 5) | shift;
+                        for (int x = 0; x < len; x += max_entries) {
+                            const int y = min(len, x + max_entries);
+                            list.items[base_i + w_i] = make_int4(ci, base_e + run0 + x, base_e + run0 + y, w);
+                            ++w_i;
+                        }
+                    } else {
+                        w_i += (len + max_entries - 1) / max_entries;
+                    }
+                }
+            }
+        }
+    }
+    n_e = w_e;
+    n_i = w_i;
+}
+
+// Exclusive scan of packed (entries << 32 | items) counts over a block of
+// TS_BLOCK threads; returns the thread's offset and sets *total.
+__device__ __forceinline__ unsigned long long ts_block_scan(unsigned long long v, unsigned long long* s_warp,
+                                                            unsigned long long* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long incl = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long t = __shfl_up_sync(FULL, incl, off);
+        if (lane >= off) incl += t;
+    }
+    if (lane == 31) s_warp[w] = incl;
+    __syncthreads();
+    unsigned long long before = 0, all = 0;
+    for (int k = 0; k < TS_BLOCK / 32; ++k) {
+        if (k < w) before += s_warp[k];
+        all += s_warp[k];
+    }
+    *total = all;
+    return before + incl - v;
+}
+
+template <bool WRITE>
+__global__ void __launch_bounds__(TS_BLOCK)
+k_tsearch(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys, int tot_clcap, ListDev list,
+          KParams kp) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ unsigned long long s_colmask[CL + 1];
+    __shared__ unsigned long long s_diag;
+    __shared__ unsigned long long s_warp[TS_BLOCK / 32];
+    if (threadIdx.x <= CL) s_colmask[threadIdx.x] = col_mask(threadIdx.x);
+    if (threadIdx.x == 32) s_diag = diag_mask();
+    __syncthreads();
+    const int gc = blockIdx.x * TS_BLOCK + threadIdx.x;
+    int sid = 0, ci = 0;
+    bool real = false;
+    if (gc < tot_clcap) {
+        sid = find_sys(cl_off, nsys, gc);
+        ci = gc - cl_off[sid];
+        real = ci < sys[sid].col_cl0[sys[sid].ncol];
+    }
+    const SysDev& d = sys[sid];
+    if (!WRITE) {
+        int n_e = 0, n_i = 0;
+        if (real) ts_cluster<false>(d, sid, ci, kp.max_entries, list, s_colmask, s_diag, 0, 0, n_e, n_i);
+        unsigned long long total = 0;
+        const unsigned long long off =
+            ts_block_scan(((unsigned long long)n_e << 32) | (unsigned)n_i, s_warp, &total);
+        if (gc < tot_clcap) *ts_slot(d, ci, 0) = off;
+        if (threadIdx.x == 0) *ts_slot(d, ci, 1) = total;  // the block's first cluster
+        return;
+    }
+    if (gc >= tot_clcap) return;
+    // offsets: the block's (in its first cluster) plus the cluster's own
+    const int g0 = blockIdx.x * TS_BLOCK;
+    const int s0 = find_sys(cl_off, nsys, g0);
+    const unsigned long long boff = *ts_slot(sys[s0], g0 - cl_off[s0], 1);
+    const unsigned long long off = boff + *ts_slot(d, ci, 0);
+    const int base_e = (int)(off >> 32), base_i = (int)(off & 0xffffffffull);
+    if (list.counters[CNT_OVERFLOW] & 3) {
+        // the list does not fit: write empty items into the reserved item
+        // slots below the capacity, so that no kernel reads stale items
+        if (!real) return;
+        int n_e = 0, n_i = 0;
+        ts_cluster<false>(d, sid, ci, kp.max_entries, list, s_colmask, s_diag, 0, 0, n_e, n_i);
+        for (int k = 0; k < n_i && base_i + k < list.item_cap; ++k)
+            list.items[base_i + k] = make_int4(ci, 0, 0, (sid << 5) | SHIFT_ZERO);
+        return;
+    }
+    if (!real) return;
+    int n_e = 0, n_i = 0;
+    ts_cluster<true>(d, sid, ci, kp.max_entries, list, s_colmask, s_diag, base_e, base_i, n_e, n_i);
+}
+
+// One block: exclusive scan of the block totals of k_tsearch<false>, in
+// place; the list's entry and item counts; overflow bits if they exceed the
+// capacities (the write pass then writes no entries).
+__global__ void __launch_bounds__(1024)
+k_tsearch_scan(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys, int tot_clcap,
+               ListDev list) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ unsigned long long s_warp[32];
+    __shared__ unsigned long long s_carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nblk = (tot_clcap + TS_BLOCK - 1) / TS_BLOCK;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nblk; base += 1024) {
+        const int b = base + threadIdx.x;
+        unsigned long long v = 0;
+        unsigned long long* slot = nullptr;
+        if (b < nblk) {
+            const int g0 = b * TS_BLOCK;
+            const int s0 = find_sys(cl_off, nsys, g0);
+            slot = ts_slot(sys[s0], g0 - cl_off[s0], 1);
+            v = *slot;
+        }
+        unsigned long long incl = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long t = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += t;
+        }
+        if (lane == 31) s_warp[w] = incl;
+        __syncthreads();
+        unsigned long long before = s_carry;
+        for (int k = 0; k < w; ++k) before += s_warp[k];
+        if (slot) *slot = before + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry = before + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long tot = s_carry;
+        const long long n_e = (long long)(tot >> 32), n_i = (long long)(tot & 0xffffffffull);
+        list.counters[CNT_ENTRIES] = (int)min(n_e, (long long)0x7fffffff);
+        list.counters[CNT_ITEMS] = (int)min(n_i, (long long)0x7fffffff);
+        int ov = 0;
+        if (n_i > list.item_cap) ov |= 1;
+        if (n_e > list.entry_cap) ov |= 2;
+        if (ov) atomicOr(list.counters + CNT_OVERFLOW, ov);
+    }
+}
+
 constexpr int PRUNE_WARPS = 8;
+// checks in flight per lane (16 per round of independent j-atom loads; eight
+// per lane, one round per chunk, needs more registers and ran slower)
+constexpr int PRUNE_U = 4;
 
 // Prune (Section 3.3): drop the entries of which no atom pair whose mask bit
 // is set lies within the list radius.  A warp takes one work item at a time.
@@ -447,11 +751,11 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
             const int nchk = __popc(chk_bal);
             if (chk) s_rank[w][__popc(chk_bal & ((1u << lane) - 1u))] = (unsigned char)lane;
             __syncwarp();
-            for (int q0 = 0; q0 < nchk; q0 += 16) {
-                float4 xj[4];
-                unsigned long long mq[4];
+            for (int q0 = 0; q0 < nchk; q0 += 4 * PRUNE_U) {
+                float4 xj[PRUNE_U];
+                unsigned long long mq[PRUNE_U];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < PRUNE_U; ++u) {
                     const int k = q0 + 4 * u + g;
                     const int src = k < nchk ? s_rank[w][k] : 0;
                     const int cjk = __shfl_sync(FULL, cjv, src);
@@ -459,7 +763,7 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
                     xj[u] = k < nchk ? d.xq_s[cjk * CL + jj] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < PRUNE_U; ++u) {
                     // bit ii: i-atom ii lies within the list radius of this j-atom
                     // (two i-atoms per paired instruction)
                     unsigned nb8 = 0;
@@ -511,8 +815,27 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
 
 }  // namespace
 
+// Clusters from which the search takes one thread per cluster (about eight
+// warps per SM); smaller systems take one warp per cluster.
+static bool thread_search(const PlanLaunch& p) {
+    if (p.kp.search_mode == 1) return false;
+    if (p.kp.search_mode == 2) return true;
+    return (long long)p.tot_clcap >= (long long)p.num_sms * 8 * 32;
+}
+
 cudaError_t launch_search(const PlanLaunch& p, cudaStream_t st) {
     if (p.tot_clcap <= 0) return cudaSuccess;
+    if (thread_search(p)) {
+        const unsigned blocks = (unsigned)((p.tot_clcap + TS_BLOCK - 1) / TS_BLOCK);
+        cudaError_t e = launch_pdl(k_tsearch<false>, blocks, TS_BLOCK, 0, st, p.d_sys, p.d_cl_off, p.nsys,
+                                   p.tot_clcap, p.list, p.kp);
+        if (e == cudaSuccess)
+            e = launch_pdl(k_tsearch_scan, 1u, 1024, 0, st, p.d_sys, p.d_cl_off, p.nsys, p.tot_clcap, p.list);
+        if (e == cudaSuccess)
+            e = launch_pdl(k_tsearch<true>, blocks, TS_BLOCK, 0, st, p.d_sys, p.d_cl_off, p.nsys, p.tot_clcap,
+                           p.list, p.kp);
+        return e;
+    }
     unsigned blocks = (unsigned)((p.tot_clcap + SEARCH_WARPS - 1) / SEARCH_WARPS);
     return launch_pdl(k_search, blocks, SEARCH_WARPS * 32, 0, st, p.d_sys, p.d_cl_off, p.nsys, p.tot_clcap, p.list,
                       p.kp);

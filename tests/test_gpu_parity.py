@@ -43,8 +43,18 @@ BOXES = {
 }
 
 
+@pytest.fixture(params=[1, 2], ids=["warp_search", "thread_search"])
+def search_mode(request, ctx):
+    """Both search kernels (a warp per i-cluster, a thread per i-cluster),
+    whatever the size would choose; the tuning is restored afterwards."""
+    old = nb.nb_ctx_get_tuning(ctx)
+    nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], request.param)
+    yield request.param
+    nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], old["search_mode"])
+
+
 @pytest.mark.parametrize("name", ["small", "mid", "rd_small"])
-def test_pairlist_covers_oracle_pairs_exactly(ctx, name):
+def test_pairlist_covers_oracle_pairs_exactly(ctx, name, search_mode):
     s = BOXES[name]()
     p = wb.params_rf()
     _, _, _, h = gpu_eval(ctx, s, p, flags=0, keep=True)
@@ -82,7 +92,7 @@ def _check(s, p, f, e, v, f_tol=F_TOL, e_tol=E_TOL, v_tol=V_TOL):
 
 @pytest.mark.parametrize("name", ["small", "mid", "rd_small"])
 @pytest.mark.parametrize("coul", [wb.COUL_RF, wb.COUL_EWALD])
-def test_forces_energies_virial(ctx, name, coul):
+def test_forces_energies_virial(ctx, name, coul, search_mode):
     s = BOXES[name]()
     p = wb.Params(coul=coul)
     f, e, v, _ = gpu_eval(ctx, s, p)
@@ -441,3 +451,32 @@ def test_device_erfc_two_atom_pairs(ctx):
         assert e[0] == 0.0 and f[0, 1] == 0.0 and f[0, 2] == 0.0
     assert worst_e <= 2e-9, worst_e
     assert worst_f <= 2e-6, worst_f
+
+
+def test_thread_search_grows_an_overflowing_list(ctx):
+    """The thread-per-cluster search sized for one item split, then run with
+    a finer one: its scan sees the list outgrow the buffers, writes no
+    entries, the build grows the buffers and searches again; the forces are
+    the oracle's."""
+    s = BOXES["small"]()
+    p = wb.params_rf()
+    old = nb.nb_ctx_get_tuning(ctx)
+    nb.nb_ctx_set_tuning(ctx, 4096, old["force_min_blocks"], 2)
+    h = nb.nb_sys_create(ctx, p, s.n, s.box)
+    try:
+        nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
+        nb.nb_grid_put(h, s.xq(), s.type)
+        nb.nb_pairlist_build(h)
+        nb.nb_ctx_set_tuning(ctx, 4, old["force_min_blocks"], 2)
+        nb.nb_grid_put(h, s.xq(), s.type)
+        nb.nb_pairlist_build(h)
+        info = nb.nb_pairlist_info(h)
+        f = np.zeros((s.n, 3), dtype=np.float32)
+        e = np.zeros(2)
+        v = np.zeros(9)
+        nb.nb_forces(h, None, f, e, v, nb.NB_F_ENERGY | nb.NB_F_VIRIAL)
+        _check(s, p, f, e, v)
+        assert info["n_items"] >= info["n_entries"] / 4
+    finally:
+        nb.nb_sys_destroy(h)
+        nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], old["search_mode"])
