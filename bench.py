@@ -253,14 +253,23 @@ def run_ours(args) -> dict:
     dev_ms = max_over_ranks(dev_ms, dev)
     value = job_throughput(pairs_per_step, args.steps, world, dev_ms)
 
-    # roofline of the force kernel (9 launches without and 1 with virial per
-    # step), from its events inside the timed region
+    # roofline of the force kernel, from its events inside the timed region:
+    # with the separate energy kernel (the default) the force stage holds all
+    # 10 launches of a step (9 without, 1 with virial); with the energies fused
+    # into the force kernel it holds the 9 force-only launches (the 10th, with
+    # energies and virial, is timed as the energy stage)
+    fused = nb.nb_ctx_get_tuning(ctx)["energy_mode"] == 1
     f_ms, f_n = timed["forces"]
     avg_ms = f_ms / max(f_n, 1)
     slots = info["n_slots"]
-    roofline = _fp32_roofline(torch, dev, wl.coul, EVALS_PER_STEP - 1, 1, slots, avg_ms,
-                              "k_forces<RF> (9 of 10 launches without, 1 with virial)",
-                              _traffic_per_launch("forces_rf_mid"))
+    if fused:
+        roofline = _fp32_roofline(torch, dev, wl.coul, f_n, 0, slots, avg_ms,
+                                  "k_forces<RF> (the 9 force-only launches of each step)",
+                                  _traffic_per_launch("forces_rf_mid"))
+    else:
+        roofline = _fp32_roofline(torch, dev, wl.coul, EVALS_PER_STEP - 1, 1, slots, avg_ms,
+                                  "k_forces<RF> (9 of 10 launches without, 1 with virial)",
+                                  _traffic_per_launch("forces_rf_mid"))
     launches = sum(n * KERNELS_PER_STAGE[name] for name, (_, n) in stage.items()) * args.steps // n_inst
 
     # end to end through the C ABI with host buffers
@@ -512,9 +521,14 @@ def run_large(args) -> dict:
     nb.nb_ctx_destroy(ctx)
     f_ms, f_n = stage["forces"]
     avg = f_ms / f_n
-    # the last launch carried the virial
-    roofline = _fp32_roofline(torch, dev, "ewald", f_n - 1, 1, info["n_slots"], avg, "k_forces<Ewald>",
-                              _traffic_per_launch("forces_ewald_large"))
+    # the last evaluation carried energies and virial: with the energies fused
+    # into the force kernel it is timed as the energy stage, otherwise it is
+    # the force stage's last launch (with virial) plus the energy kernel
+    fused = nb.nb_ctx_get_tuning(ctx)["energy_mode"] == 1
+    roofline = _fp32_roofline(torch, dev, "ewald", f_n if fused else f_n - 1, 0 if fused else 1, info["n_slots"],
+                              avg, "k_forces<Ewald>", _traffic_per_launch("forces_ewald_large"))
+    e_ms, e_n = stage["energy"]
+    energy_eval = e_ms / max(e_n, 1) if fused else avg + e_ms / max(e_n, 1)
     grid_bytes = s.n * (20 + 24 + 8 + 8) + info["n_clusters"] * 32
     # algorithmic bytes of the build: the search reads the bounding boxes once
     # and writes the raw list (4-byte j-cluster + 8-byte mask per entry) and
@@ -541,7 +555,9 @@ def run_large(args) -> dict:
                       "prune": round(prune_bytes / (stage["prune"][0] * 1e-3) / 1e9, 1),
                       "bytes": {"grid": grid_bytes, "search": search_bytes, "prune": prune_bytes},
                       "peak_gbs": float(_peaks()[0].get("hbm_gbs", 6800.0))},
-        "energy_eval_ms": stage["energy"][0] / max(stage["energy"][1], 1),
+        # one evaluation with energies and virial, forces included
+        "energy_eval_ms": energy_eval,
+        "energy_mode": "fused into the force kernel" if fused else "separate energy kernel",
         "clocks": clk.summary(),
     }
 
@@ -1030,6 +1046,7 @@ def _targets_digest(out: dict) -> dict:
                          "ops_per_slot": r["fp32_ops_per_slot"],
                          "computed_over_useful": round(lb["computed_pairs_per_s"] / lb["value"], 3),
                          "ms_forces": round(lb["ms_per_eval"], 3), "ms_energy_eval": round(lb["energy_eval_ms"], 3),
+                         "energy_eval_over_forces": round(lb["energy_eval_ms"] / lb["ms_per_eval"], 3),
                          "ms_build": {k: round(v, 3) for k, v in lb["build_ms"].items()}}
     en = out.get("ensemble")
     if en:
@@ -1094,7 +1111,8 @@ def main():
                                 "computed_pairs_per_s": lg["config"]["computed_pairs_per_s"],
                                 "roofline": lg["roofline"], "build_ms": lg["build_ms"],
                                 "build_gbs": lg["build_gbs"],
-                                "energy_eval_ms": lg["energy_eval_ms"], "tuning": lg["config"]["tuning"]}
+                                "energy_eval_ms": lg["energy_eval_ms"], "energy_mode": lg["energy_mode"],
+                                "tuning": lg["config"]["tuning"]}
         if world == 1 and not args.no_extra:
             out["ensemble"] = run_ensemble(argparse.Namespace(steps=5, warmup=3))
             out["serving"] = run_serve(argparse.Namespace(steps=1, warmup=1))

@@ -139,9 +139,11 @@ enum {
     NB_STAGE_PRUNE = 2,   /* list prune */
     NB_STAGE_COORD = 3,   /* staging copy of nb_forces(x_new) */
     NB_STAGE_ZERO = 4,    /* force-buffer clear + coordinate update */
-    NB_STAGE_FORCES = 5,  /* the cluster-pair force kernel */
+    NB_STAGE_FORCES = 5,  /* the cluster-pair force kernel (all evaluations; with
+                             nb_tuning.energy_mode = 1 those without energies) */
     NB_STAGE_FINAL = 6,   /* unsort + FP64 energy/virial finalisation */
-    NB_STAGE_ENERGY = 7,  /* the double-float energy kernel (NB_F_ENERGY) */
+    NB_STAGE_ENERGY = 7,  /* NB_F_ENERGY evaluations: the double-float energy kernel, or
+                             (energy_mode = 1) the force kernel with the energies fused in */
     NB_STAGE_PME_SPREAD = 8,  /* long-range part: mesh clear + charge spreading */
     NB_STAGE_PME_FFT = 9,     /* long-range part: forward FFT, solve, inverse FFT */
     NB_STAGE_PME_GATHER = 10, /* long-range part: force gathering + excluded pairs */
@@ -164,11 +166,16 @@ enum {
  *                     (count, scan and write passes, no atomics), 0 = by
  *                     size (default: a thread per cluster from about eight
  *                     warps' worth of clusters per SM).  The list is the same.
+ *   energy_mode       evaluations with NB_F_ENERGY: 0 = a separate energy
+ *                     kernel after the force kernel (default), 1 = the force
+ *                     kernel also evaluates the energies of the pairs it
+ *                     finds inside rc.  The results are the same.
  */
 typedef struct {
     int max_entries;
     int force_min_blocks;
     int search_mode;
+    int energy_mode;
 } nb_tuning;
 
 /* Message of the calling thread's last failure ("" if none). */

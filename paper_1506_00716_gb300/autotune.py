@@ -6,13 +6,20 @@ Tuned per (electrostatics, system size):
                     persistent force kernel balances well on small systems
                     (list-splitting threshold);
   force_min_blocks  force-kernel register budget / block residency (block
-                    shape): 1, 2 or 3 resident 256-thread blocks per SM.
-The cluster size is fixed at M = N = 8 by the warp layout of the kernels.
+                    shape): 1, 2 or 3 resident 256-thread blocks per SM;
+  search_mode       cluster-pair search: a warp per i-cluster (1) or a
+                    thread per i-cluster (2);
+  energy_mode       evaluations with energies: a separate double-float energy
+                    kernel (0) or the energies fused into the force kernel (1).
+The cluster size is fixed at M = N = 8 by the warp layout of the kernels
+(other geometries and why they are not built: the design notes).
 
-For every candidate the tuner builds the list and times one build (search +
-prune) plus EVALS force evaluations with the library's per-stage CUDA events,
-and keeps the fastest.  The result is a JSON table keyed by GPU name; lookup()
-picks the entry of the nearest size (in log atoms).
+For every (max_entries, force_min_blocks) candidate the tuner builds the list
+and times one build (search + prune) plus EVALS force evaluations with the
+library's per-stage CUDA events, and keeps the fastest; at that setting it
+times the build with each search kernel, and one evaluation with energies and
+virial with each energy path.  The result is a JSON table keyed by GPU name;
+lookup() picks the entry of the nearest size (in log atoms).
 
     python -m paper_1506_00716_gb300.autotune [--out FILE]
 """
@@ -32,7 +39,49 @@ DEFAULT_TABLE = os.path.join(HERE, "tuning.json")
 SIZES_MOL = [1000, 8000, 64000, 1_000_000]
 MAX_ENTRIES = [8, 16, 32, 64, 128]
 MIN_BLOCKS = [1, 2, 3]
+SEARCH_MODES = [1, 2]
+ENERGY_MODES = [0, 1]
 EVALS = 10
+
+
+def _time_build(ctx, h, s, me, mb, search_mode, reps: int = 3) -> float:
+    """Fastest list build (search + prune), ms."""
+    nb.nb_ctx_set_tuning(ctx, me, mb, search_mode)
+    nb.nb_grid_put(h, s.xq(), s.type)
+    nb.nb_pairlist_build(h)
+    best = None
+    for _ in range(reps):
+        nb.nb_ctx_timing(ctx, reset=True)
+        nb.nb_ctx_set_timing(ctx, True)
+        nb.nb_pairlist_build(h)
+        nb.nb_ctx_set_timing(ctx, False)
+        st = nb.nb_ctx_timing(ctx, reset=True)
+        t = st["search"][0] + st["prune"][0]
+        best = t if best is None else min(best, t)
+    return best
+
+
+def _time_energy_eval(ctx, h, s, me, mb, search_mode, energy_mode, reps: int = 3) -> float:
+    """Fastest evaluation with energies and virial (force + energy stages), ms."""
+    nb.nb_ctx_set_tuning(ctx, me, mb, search_mode, energy_mode)
+    nb.nb_grid_put(h, s.xq(), s.type)
+    nb.nb_pairlist_build(h)
+    flags = nb.NB_F_ENERGY | nb.NB_F_VIRIAL
+    import numpy as np
+
+    e = np.zeros(2)
+    v = np.zeros(9)
+    nb.nb_forces(h, None, None, e, v, flags)
+    best = None
+    for _ in range(reps):
+        nb.nb_ctx_timing(ctx, reset=True)
+        nb.nb_ctx_set_timing(ctx, True)
+        nb.nb_forces(h, None, None, e, v, flags)
+        nb.nb_ctx_set_timing(ctx, False)
+        st = nb.nb_ctx_timing(ctx, reset=True)
+        t = st["forces"][0] + st["energy"][0]
+        best = t if best is None else min(best, t)
+    return best
 
 
 def _time_config(ctx, h, s, max_entries, min_blocks, reps: int = 2) -> dict:
@@ -77,19 +126,26 @@ def tune(sizes=SIZES_MOL, device: int = 0, verbose: bool = True) -> dict:
                     for mb in MIN_BLOCKS:
                         r = _time_config(ctx, h, s, me, mb)
                         results.append({"max_entries": me, "force_min_blocks": mb, **r})
-                nb.nb_sys_destroy(h)
                 best = min(results, key=lambda r: r["total_ms"])
+                me, mb = best["max_entries"], best["force_min_blocks"]
+                build = {sm: _time_build(ctx, h, s, me, mb, sm) for sm in SEARCH_MODES}
+                search_mode = min(build, key=build.get)
+                energy = {em: _time_energy_eval(ctx, h, s, me, mb, search_mode, em) for em in ENERGY_MODES}
+                energy_mode = min(energy, key=energy.get)
+                nb.nb_sys_destroy(h)
                 default = next(r for r in results if r["max_entries"] == 32 and r["force_min_blocks"] == 3)
-                entries.append({"coul": coul, "atoms": s.n, "max_entries": best["max_entries"],
-                                "force_min_blocks": best["force_min_blocks"],
+                entries.append({"coul": coul, "atoms": s.n, "max_entries": me, "force_min_blocks": mb,
+                                "search_mode": search_mode, "energy_mode": energy_mode,
+                                "build_ms_by_search_mode": {str(k): round(v, 5) for k, v in build.items()},
+                                "energy_eval_ms_by_energy_mode": {str(k): round(v, 5) for k, v in energy.items()},
                                 "total_ms": round(best["total_ms"], 5),
                                 "default_total_ms": round(default["total_ms"], 5),
                                 "sweep": [{k: (round(v, 5) if isinstance(v, float) else v)
                                            for k, v in r.items()} for r in results]})
                 if verbose:
-                    print(f"{coul:5s} {s.n:8d} atoms: best max_entries={best['max_entries']} "
-                          f"min_blocks={best['force_min_blocks']} {best['total_ms']:.4f} ms "
-                          f"(default {default['total_ms']:.4f} ms)", flush=True)
+                    print(f"{coul:5s} {s.n:8d} atoms: best max_entries={me} min_blocks={mb} "
+                          f"{best['total_ms']:.4f} ms (default {default['total_ms']:.4f} ms); search {build}; "
+                          f"energy {energy}", flush=True)
     finally:
         nb.nb_ctx_destroy(ctx)
     return {"gpu": gpu, "evals_per_build": EVALS, "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
@@ -106,19 +162,20 @@ def load(path: str = DEFAULT_TABLE) -> dict | None:
 
 def lookup(table: dict | None, coul: str, natoms: int, gpu: str | None = None) -> dict:
     """Tuning for a system: the table entry of the same electrostatics and nearest size."""
-    default = {"max_entries": 32, "force_min_blocks": 3}
+    default = {"max_entries": 32, "force_min_blocks": 3, "search_mode": 0, "energy_mode": 0}
     if not table or (gpu is not None and table.get("gpu") != gpu):
         return default
     cands = [e for e in table.get("entries", []) if e["coul"] == coul]
     if not cands:
         return default
     e = min(cands, key=lambda e: abs(math.log(e["atoms"]) - math.log(max(natoms, 1))))
-    return {"max_entries": int(e["max_entries"]), "force_min_blocks": int(e["force_min_blocks"])}
+    return {"max_entries": int(e["max_entries"]), "force_min_blocks": int(e["force_min_blocks"]),
+            "search_mode": int(e.get("search_mode", 0)), "energy_mode": int(e.get("energy_mode", 0))}
 
 
 def apply(ctx, coul: str, natoms: int, table: dict | None = None, gpu: str | None = None) -> dict:
     t = lookup(table if table is not None else load(), coul, natoms, gpu)
-    nb.nb_ctx_set_tuning(ctx, t["max_entries"], t["force_min_blocks"])
+    nb.nb_ctx_set_tuning(ctx, t["max_entries"], t["force_min_blocks"], t["search_mode"], t["energy_mode"])
     return t
 
 

@@ -566,6 +566,7 @@ PlanLaunch launch_of(const Plan* pl) {
     const_cast<Plan*>(pl)->kp.max_entries = pl->ctx->tuning.max_entries;
     const_cast<Plan*>(pl)->kp.force_min_blocks = pl->ctx->tuning.force_min_blocks;
     const_cast<Plan*>(pl)->kp.search_mode = pl->ctx->tuning.search_mode;
+    const_cast<Plan*>(pl)->kp.energy_mode = pl->ctx->tuning.energy_mode;
     const_cast<Plan*>(pl)->kp.lpt_max_items = LPT_ITEMS_PER_WARP * LPT_WARPS_PER_SM * pl->ctx->num_sms;
     int n = (int)pl->systems.size();
     p.nsys = n;
@@ -657,13 +658,19 @@ nb_status plan_eval(Plan* pl, unsigned flags, bool coords, const PlanLaunch* ext
         StageScope sc(pl->ctx, NB_STAGE_ZERO);
         NB_CK(launch_prepare(p, coords, st));
     }
-    {
-        StageScope sc(pl->ctx, NB_STAGE_FORCES);
-        NB_CK(launch_forces(p, flags, st));
-    }
-    if (flags & NB_F_ENERGY) {
+    if ((flags & NB_F_ENERGY) && energy_fused(p)) {
+        // one kernel: forces and energies, timed as the energy stage
         StageScope sc(pl->ctx, NB_STAGE_ENERGY);
-        NB_CK(launch_energy(p, st));
+        NB_CK(launch_forces(p, flags, st));
+    } else {
+        {
+            StageScope sc(pl->ctx, NB_STAGE_FORCES);
+            NB_CK(launch_forces(p, flags, st));
+        }
+        if (flags & NB_F_ENERGY) {
+            StageScope sc(pl->ctx, NB_STAGE_ENERGY);
+            NB_CK(launch_energy(p, st));
+        }
     }
     if (pme && (flags & NB_F_PME)) {
         nb_status s = pme_record(pl->ctx, p, pme->dev, pl->systems[0]->h.acc, flags, st);
@@ -868,6 +875,7 @@ nb_status nb_ctx_set_tuning(nb_ctx* ctx, const nb_tuning* t) {
     if (t->max_entries < 4 || t->max_entries > 4096) return fail(NB_ERR_ARG, "max_entries must be in 4..4096");
     if (t->force_min_blocks < 1 || t->force_min_blocks > 3) return fail(NB_ERR_ARG, "force_min_blocks must be 1, 2 or 3");
     if (t->search_mode < 0 || t->search_mode > 2) return fail(NB_ERR_ARG, "search_mode must be 0, 1 or 2");
+    if (t->energy_mode < 0 || t->energy_mode > 1) return fail(NB_ERR_ARG, "energy_mode must be 0 or 1");
     ctx->tuning = *t;
     ctx->tuning_gen += 1;
     return NB_OK;
@@ -1267,13 +1275,19 @@ static nb_status batch_record(Plan* pl, unsigned flags) {
         StageScope sc(pl->ctx, NB_STAGE_ZERO);
         NB_CK(launch_prepare(p, false, st));
     }
-    {
-        StageScope sc(pl->ctx, NB_STAGE_FORCES);
-        NB_CK(launch_forces(p, flags, st));
-    }
-    if (flags & NB_F_ENERGY) {
+    if ((flags & NB_F_ENERGY) && energy_fused(p)) {
+        // one kernel: forces and energies, timed as the energy stage
         StageScope sc(pl->ctx, NB_STAGE_ENERGY);
-        NB_CK(launch_energy(p, st));
+        NB_CK(launch_forces(p, flags, st));
+    } else {
+        {
+            StageScope sc(pl->ctx, NB_STAGE_FORCES);
+            NB_CK(launch_forces(p, flags, st));
+        }
+        if (flags & NB_F_ENERGY) {
+            StageScope sc(pl->ctx, NB_STAGE_ENERGY);
+            NB_CK(launch_energy(p, st));
+        }
     }
     {
         StageScope sc(pl->ctx, NB_STAGE_FINAL);

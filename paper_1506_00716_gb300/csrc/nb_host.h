@@ -34,7 +34,7 @@ struct nb_ctx {
     int num_sms = 0;
     unsigned timing = 0;  // mask of timed stages (1 << NB_STAGE_*)
     bool capturing = false;
-    nb_tuning tuning{32, 3, 0};
+    nb_tuning tuning{32, 3, 0, 0};
     unsigned tuning_gen = 0;
     std::vector<TimedLaunch> pending;
     std::vector<cudaEvent_t> pool;

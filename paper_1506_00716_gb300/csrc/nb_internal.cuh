@@ -132,6 +132,7 @@ struct KParams {
     double fq_d, krf_d, crf_d;  // f / eps_r, k_rf, c_rf in float64 (NB_MOD_RF_EXCL)
     int max_entries;     // list entries per work item (items are split beyond)
     int search_mode;     // 0: by size, 1: a warp per i-cluster, 2: a thread per i-cluster
+    int energy_mode;     // 0: a separate energy kernel, 1: energies fused into the force kernel
     int lpt_max_items;   // item count up to which items run longest first
     int force_min_blocks;  // force-kernel launch-bounds variant: 1, 2 or 3
     const float2* lj;    // [ntypes^2] (6 c6, 12 c12), force kernel
@@ -267,7 +268,11 @@ cudaError_t launch_prune_into(const PlanLaunch& p, const ListDev& src, const Lis
 // Start of an evaluation: clear forces, accumulators and work counters; with
 // coords, also move the staged x_new into the sorted slots.
 cudaError_t launch_prepare(const PlanLaunch& p, bool coords, cudaStream_t st);
+// Forces (and, per flags, virial; with NB_F_ENERGY and energy_fused(p) also
+// the energies, in the same kernel).
 cudaError_t launch_forces(const PlanLaunch& p, unsigned flags, cudaStream_t st);
+bool energy_fused(const PlanLaunch& p);
+// The separate energy kernel (nothing when the energies are fused).
 cudaError_t launch_energy(const PlanLaunch& p, cudaStream_t st);
 cudaError_t launch_finalize(const PlanLaunch& p, unsigned flags, cudaStream_t st);
 // Reaction-field correction of excluded pairs (NB_MOD_RF_EXCL; nothing

@@ -33,9 +33,7 @@
 // rc), pairs whose float32 r^2 lies within a relative 2e-5 of rc^2 are left
 // out of the main pass and decided on a rare path from the float64 distance
 // of the float32 inputs, the same decision the float64 oracle takes.
-#include "erfc_fit.cuh"
-#include "nb_device.cuh"
-#include "nb_pair2.cuh"
+#include "nb_energy2.cuh"
 
 namespace nbgb {
 
@@ -167,18 +165,24 @@ __device__ __forceinline__ void pair_force2(float2 dx, float2 dy, float2 dz, flo
 constexpr int JB_REC = 12, JB_Z = 4, JB_T = 8, JB_SIZE = 4 * JB_REC;
 // The (12 c12) table starts this many floats after the (6 c6) table, a
 // constant, so that both entries of a type pair are addressed from one
-// register.
+// register; the energies' (c6, c12) table follows it (lj_e_offset).
 constexpr int LJ_C12 = MAX_TYPES * MAX_TYPES;
+__host__ __device__ __forceinline__ int lj_e_offset(int nt) { return (LJ_C12 + nt * nt + 1) & ~1; }
 
 // The M x N = 8 x 8 pairs of one entry for one lane (i-slot i), two at a
 // time: step p takes the j-slots 2m and 2m+1, m = p XOR (i >> 1), as the
 // two halves.  `row` holds the lane's mask bits in that order (bit 2p + c
 // for half c of step p).  With EXACT, pairs within the band around rc^2 are
 // left out and `band` is set; the caller decides them one by one.
-template <int COUL, bool VIR, bool MASKED, bool SHIFTED, bool EXACT>
+//
+// With ENER, the slots whose pair lies inside rc (or within the band around
+// it, decided exactly later) are also marked for the energies: bit 2p + c of
+// ebits for half c of step p, the same bit of mbits if it lies in the band.
+template <int COUL, bool VIR, bool MASKED, bool SHIFTED, bool EXACT, bool ENER>
 __device__ __forceinline__ void pair_block2(const float* __restrict__ sj, int h, const IPair& xs, float2 qi,
                                             const float* __restrict__ ljrow, unsigned row, const KParams& kp, const EwaldC& ew,
-                                            float2 (&fi)[3], float2 (&fj)[4][3], float2 (&v)[6], bool& band) {
+                                            float2 (&fi)[3], float2 (&fj)[4][3], float2 (&v)[6], bool& band,
+                                            unsigned& ebits, unsigned& mbits) {
 #pragma unroll
     for (int p = 0; p < CL / 2; ++p) {
         const float* rec = sj + JB_REC * (p ^ h);
@@ -204,6 +208,11 @@ __device__ __forceinline__ void pair_block2(const float* __restrict__ sj, int h,
             in1 = in1 && b1;
         }
         if (EXACT) band = band || (b0 && !in0 && r2.x < kp.rc2_hi) || (b1 && !in1 && r2.y < kp.rc2_hi);
+        if (ENER) {
+            const bool q0 = b0 && r2.x < kp.rc2_hi, q1 = b1 && r2.y < kp.rc2_hi;
+            ebits |= ((q0 ? 1u : 0u) | (q1 ? 2u : 0u)) << (2 * p);
+            mbits |= ((q0 && !(r2.x < kp.rc2_lo) ? 1u : 0u) | (q1 && !(r2.y < kp.rc2_lo) ? 2u : 0u)) << (2 * p);
+        }
         const float* l0 = ljrow + tj.x;
         const float* l1 = ljrow + tj.y;
         const float2 c6 = make_float2(l0[0], l1[0]);
@@ -213,17 +222,27 @@ __device__ __forceinline__ void pair_block2(const float* __restrict__ sj, int h,
     }
 }
 
-template <int COUL, bool VIR, int MINB>
+// With ENER (an evaluation with NB_F_ENERGY), the kernel also computes the
+// energies: the pairs that the force pass finds inside rc (or in the band
+// around it) go to a per-warp ring queue in shared memory as (j slot, i-slot,
+// band) records, and whenever 64 are queued the warp evaluates them in
+// double-float (nb_energy2.cuh, the energy kernel's arithmetic), two per lane;
+// the queue is emptied at the end of every work item.  The energy kernel's
+// second pass over the list (staging, screening) is saved.
+template <int COUL, bool VIR, int MINB, bool ENER, bool LJSH>
 __global__ void __launch_bounds__(FW * 32, MINB)
 k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     pdl_wait();
     pdl_trigger();
     constexpr bool EXACT = COUL == NB_COUL_RF;
-    // (6 c6) table [ntypes^2] at 0, (12 c12) table at LJ_C12
+    // (6 c6) table [ntypes^2] at 0, (12 c12) table at LJ_C12; with ENER the
+    // (c6, c12) table of the energies (float2) at lj_e_offset(ntypes)
     extern __shared__ float s_ljt[];
     __shared__ __align__(16) float s_j[FW][4][JB_SIZE];
     __shared__ double s_acc[FW][6];
     __shared__ float s_fix[FW][4][CL][3];
+    __shared__ int s_qm[ENER ? FW : 1][ENER ? QCAP : 1];
+    __shared__ IRec s_irec[ENER ? FW : 1][CL];
 
     const int lane = threadIdx.x & 31;
     const int i = lane & 7;
@@ -236,8 +255,15 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         s_ljt[k] = c.x;
         s_ljt[LJ_C12 + k] = c.y;
     }
+    float2* const s_lje = reinterpret_cast<float2*>(s_ljt + lj_e_offset(nt));
+    if (ENER)
+        for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) s_lje[k] = kp.lje[k];
     if (lane < 6) s_acc[w][lane] = 0.0;
     __syncthreads();
+    int* const qm = s_qm[ENER ? w : 0];
+    IRec* const irec = s_irec[ENER ? w : 0];
+    double dec = 0.0, d12 = 0.0, d6 = 0.0;
+    long long np = 0;
 
     EwaldC ew;
     ew.beta = kp.beta;
@@ -270,6 +296,7 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         const int sid = item.w >> 5;
         const int sh = item.w & 31;
         if (sid != cur_sys) {
+            if (ENER && cur_sys >= 0) flush_energy(sys, cur_sys, dec, d12, d6, np, lane);
             if (VIR && cur_sys >= 0) {
                 __syncwarp();
                 if (lane < 6 && s_acc[w][lane] != 0.0) atomicAdd(sys[cur_sys].acc + ACC_VXX + lane, s_acc[w][lane]);
@@ -297,6 +324,21 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         const float qi = xi4.w * kp.fq;
         const int tirow = type_s[ci * CL + i] * nt;
         const float* const ljrow = s_ljt + tirow;
+        float2 ch = dup2(0.f), cl = dup2(0.f), e12 = dup2(0.f), e12l = dup2(0.f), e6 = dup2(0.f),
+               e6l = dup2(0.f);
+        int npair = 0;
+        int head = 0, tail = 0;  // energy ring positions, identical in every lane
+        if (ENER) {
+            __syncwarp();
+            if (g == 0) {
+                IRec r;
+                r.xs = xs;
+                two_prod(kp.fq_h, xi4.w, r.qih, r.qil);
+                r.qil = fmaf(kp.fq_l, xi4.w, r.qil);
+                r.tirow = tirow;
+                irec[i] = r;
+            }
+        }
 
         float2 fi[3] = {dup2(0.f), dup2(0.f), dup2(0.f)};
         float2 v[6] = {dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f), dup2(0.f)};
@@ -354,16 +396,17 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
 #pragma unroll
             for (int p = 0; p < CL / 2; ++p) fj[p][0] = fj[p][1] = fj[p][2] = dup2(0.f);
             bool band = false;
+            unsigned ebits = 0u, mbits = 0u;
             const bool full = __all_sync(FULL, row == 0xffu);
             if (full && !shifted)
-                pair_block2<COUL, VIR, false, false, EXACT>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
-                                                           fi, fj, v, band);
+                pair_block2<COUL, VIR, false, false, EXACT, ENER>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
+                                                                 fi, fj, v, band, ebits, mbits);
             else if (full)
-                pair_block2<COUL, VIR, false, true, EXACT>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
-                                                          fi, fj, v, band);
+                pair_block2<COUL, VIR, false, true, EXACT, ENER>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
+                                                                fi, fj, v, band, ebits, mbits);
             else
-                pair_block2<COUL, VIR, true, true, EXACT>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
-                                                         fi, fj, v, band);
+                pair_block2<COUL, VIR, true, true, EXACT, ENER>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
+                                                               fi, fj, v, band, ebits, mbits);
             // transposed butterfly over the 8 lanes of the group: half c of
             // fj[p] holds j-slot 2 (p XOR (i >> 1)) + c, so the partners at
             // XOR 4 and 2 hold the same slots in fj[p ^ 2] and fj[p ^ 1]; at
@@ -427,6 +470,40 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
                 fjt[2] += s_fix[w][g][i][2];
             }
             if (cact) atomicAdd(f_s + ccj * CL + i, make_float4(fjt[0], fjt[1], fjt[2], 0.f));
+            if (ENER) {
+                // queue this entry's candidate pairs (bit 2p + c: j-slot
+                // 2 (p XOR (i >> 1)) + c), then evaluate them 64 at a time
+                const int cnt = __popc(ebits);
+                int incl = cnt;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int t = __shfl_up_sync(FULL, incl, off);
+                    if (lane >= off) incl += t;
+                }
+                const int tot = __shfl_sync(FULL, incl, 31);
+                int pos = tail + incl - cnt;
+                for (unsigned bits = ebits; bits != 0u; bits &= bits - 1u, ++pos) {
+                    const int t = __ffs(bits) - 1;
+                    const int js = ccj * CL + 2 * ((t >> 1) ^ h) + (t & 1);
+                    qm[pos & (QCAP - 1)] = (js << 4) | (i << 1) | (int)((mbits >> t) & 1u);
+                }
+                tail += tot;
+                __syncwarp();
+                while (tail - head >= 64) {
+                    drain2<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lje, kp, ch, cl, e12, e12l, e6, e6l,
+                                       npair, true, true);
+                    head += 64;
+                }
+            }
+        }
+        if (ENER) {
+            if (tail > head)
+                drain2<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lje, kp, ch, cl, e12, e12l, e6, e6l, npair,
+                                   lane < tail - head, lane + 32 < tail - head);
+            dec += ((double)ch.x + (double)cl.x) + ((double)ch.y + (double)cl.y);
+            d12 += ((double)e12.x + (double)e12l.x) + ((double)e12.y + (double)e12l.y);
+            d6 += ((double)e6.x + (double)e6l.x) + ((double)e6.y + (double)e6l.y);
+            if (lane == 0) np += npair;
         }
         float fix = fi[0].x + fi[0].y, fiy = fi[1].x + fi[1].y, fiz = fi[2].x + fi[2].y;
         fix += __shfl_xor_sync(FULL, fix, 8);
@@ -454,6 +531,7 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         __syncwarp();
         if (lane < 6 && s_acc[w][lane] != 0.0) atomicAdd(sys[cur_sys].acc + ACC_VXX + lane, s_acc[w][lane]);
     }
+    if (ENER && cur_sys >= 0) flush_energy(sys, cur_sys, dec, d12, d6, np, lane);
 }
 
 // Start of an evaluation: zero the sorted force buffers, the accumulators of
@@ -543,10 +621,17 @@ __global__ void k_finish(const SysDev* __restrict__ sys, const int* __restrict__
     }
 }
 
-template <int COUL, bool VIR, int MINB>
+template <int COUL, bool VIR, int MINB, bool ENER = false, bool LJSH = false>
 cudaError_t launch_forces_t(const PlanLaunch& p, cudaStream_t st) {
-    size_t smem = (size_t)(LJ_C12 + p.kp.ntypes * p.kp.ntypes) * sizeof(float);
-    auto kern = k_forces<COUL, VIR, MINB>;
+    const size_t nt2 = (size_t)p.kp.ntypes * p.kp.ntypes;
+    const size_t smem = ENER ? (lj_e_offset(p.kp.ntypes) + 2 * nt2) * sizeof(float) : (LJ_C12 + nt2) * sizeof(float);
+    auto kern = k_forces<COUL, VIR, MINB, ENER, LJSH>;
+    if (ENER) {
+        // the energy queue makes static + dynamic shared memory pass 48 KB
+        // for larger type tables: allow the dynamic part explicitly
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     int per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FW * 32, smem);
     if (err != cudaSuccess) return err;
@@ -576,8 +661,23 @@ cudaError_t launch_forces_v(const PlanLaunch& p, cudaStream_t st) {
     }
 }
 
+// The force kernel with the energies fused in (NB_F_ENERGY evaluations when
+// the tuning's energy_mode is 1): one register budget (2 blocks per SM).
+template <int COUL, bool VIR>
+cudaError_t launch_forces_e(const PlanLaunch& p, cudaStream_t st) {
+    if (p.kp.mods & NB_MOD_LJ_SHIFT) return launch_forces_t<COUL, VIR, 2, true, true>(p, st);
+    return launch_forces_t<COUL, VIR, 2, true, false>(p, st);
+}
+
+bool energy_fused(const PlanLaunch& p) { return p.kp.energy_mode == 1; }
+
 cudaError_t launch_forces(const PlanLaunch& p, unsigned flags, cudaStream_t st) {
     bool vi = flags & NB_F_VIRIAL;
+    if ((flags & NB_F_ENERGY) && energy_fused(p)) {
+        if (p.kp.coul == NB_COUL_RF)
+            return vi ? launch_forces_e<NB_COUL_RF, true>(p, st) : launch_forces_e<NB_COUL_RF, false>(p, st);
+        return vi ? launch_forces_e<NB_COUL_EWALD, true>(p, st) : launch_forces_e<NB_COUL_EWALD, false>(p, st);
+    }
     if (p.kp.coul == NB_COUL_RF)
         return vi ? launch_forces_v<NB_COUL_RF, true>(p, st) : launch_forces_v<NB_COUL_RF, false>(p, st);
     return vi ? launch_forces_v<NB_COUL_EWALD, true>(p, st) : launch_forces_v<NB_COUL_EWALD, false>(p, st);

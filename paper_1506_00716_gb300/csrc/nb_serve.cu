@@ -143,7 +143,7 @@ struct nb_server {
     Wave waves[2];
     nb_params p{};
     std::vector<float> c6, c12;
-    nb_tuning tuning{32, 3, 0};
+    nb_tuning tuning{32, 3, 0, 0};
     size_t budget = 0;
     int max_wave = 64;
     size_t in_use = 0;

@@ -62,7 +62,8 @@ class nb_pme_params(ctypes.Structure):
 
 
 class nb_tuning(ctypes.Structure):
-    _fields_ = [("max_entries", ctypes.c_int), ("force_min_blocks", ctypes.c_int), ("search_mode", ctypes.c_int)]
+    _fields_ = [("max_entries", ctypes.c_int), ("force_min_blocks", ctypes.c_int), ("search_mode", ctypes.c_int),
+                ("energy_mode", ctypes.c_int)]
 
 
 class nb_request_stats(ctypes.Structure):
@@ -366,15 +367,17 @@ def nb_eval_noalloc(params, natoms: int, box, excl_index, excl_atoms, xq, type_,
     del keep
 
 
-def nb_ctx_set_tuning(ctx, max_entries: int = 32, force_min_blocks: int = 3, search_mode: int = 0) -> None:
-    t = nb_tuning(int(max_entries), int(force_min_blocks), int(search_mode))
+def nb_ctx_set_tuning(ctx, max_entries: int = 32, force_min_blocks: int = 3, search_mode: int = 0,
+                      energy_mode: int = 0) -> None:
+    t = nb_tuning(int(max_entries), int(force_min_blocks), int(search_mode), int(energy_mode))
     check(load().nb_ctx_set_tuning(ctx, ctypes.byref(t)))
 
 
 def nb_ctx_get_tuning(ctx) -> dict:
     t = nb_tuning()
     check(load().nb_ctx_get_tuning(ctx, ctypes.byref(t)))
-    return {"max_entries": t.max_entries, "force_min_blocks": t.force_min_blocks, "search_mode": t.search_mode}
+    return {"max_entries": t.max_entries, "force_min_blocks": t.force_min_blocks, "search_mode": t.search_mode,
+            "energy_mode": t.energy_mode}
 
 
 def nb_server_create(ctx, params, budget: int = 0, max_wave: int = 64) -> int:

@@ -123,8 +123,9 @@ def test_batch_poll_times_out_while_the_stream_is_busy(torch_cuda):
         nb.nb_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("search_mode", [1, 2], ids=["warp_search", "thread_search"])
-def test_batch_recovers_from_a_list_overflow(torch_cuda, search_mode):
+@pytest.mark.parametrize("search_mode,energy_mode", [(1, 0), (2, 0), (2, 1)],
+                         ids=["warp_search", "thread_search", "thread_search+fused_energy"])
+def test_batch_recovers_from_a_list_overflow(torch_cuda, search_mode, energy_mode):
     """A list that outgrows its capacity reports NB_ERR_CAPACITY, leaves the
     device state sound, and the resubmitted batch is correct.
 
@@ -139,7 +140,7 @@ def test_batch_recovers_from_a_list_overflow(torch_cuda, search_mode):
     p = wb.params_rf()
     handles = []
     try:
-        nb.nb_ctx_set_tuning(ctx, 4096, 3, search_mode)
+        nb.nb_ctx_set_tuning(ctx, 4096, 3, search_mode, energy_mode)
         for s in systems:
             h = nb.nb_sys_create(ctx, p, s.n, s.box)
             nb.nb_set_exclusions(h, s.excl_index, s.excl_atoms)
@@ -147,7 +148,7 @@ def test_batch_recovers_from_a_list_overflow(torch_cuda, search_mode):
             handles.append(h)
         b = nb.nb_batch_create(ctx, handles)
         try:
-            nb.nb_ctx_set_tuning(ctx, 4, 3, search_mode)
+            nb.nb_ctx_set_tuning(ctx, 4, 3, search_mode, energy_mode)
             t = nb.nb_batch_submit(b, FLAGS)
             with pytest.raises(nb.NbError) as ei:
                 nb.nb_batch_poll(b, t, 10_000_000)

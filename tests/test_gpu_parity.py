@@ -43,14 +43,17 @@ BOXES = {
 }
 
 
-@pytest.fixture(params=[1, 2], ids=["warp_search", "thread_search"])
+@pytest.fixture(params=[(1, 0), (2, 0), (1, 1)],
+                ids=["warp_search+energy_kernel", "thread_search+energy_kernel", "warp_search+fused_energy"])
 def search_mode(request, ctx):
     """Both search kernels (a warp per i-cluster, a thread per i-cluster),
-    whatever the size would choose; the tuning is restored afterwards."""
+    whatever the size would choose, and both energy paths (fused into the
+    force kernel, or the separate energy kernel); the tuning is restored
+    afterwards."""
     old = nb.nb_ctx_get_tuning(ctx)
-    nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], request.param)
+    nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], *request.param)
     yield request.param
-    nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], old["search_mode"])
+    nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], old["search_mode"], old["energy_mode"])
 
 
 @pytest.mark.parametrize("name", ["small", "mid", "rd_small"])
@@ -351,7 +354,7 @@ MODIFIER_CASES = [
 
 @pytest.mark.parametrize("coul,mods", MODIFIER_CASES)
 @pytest.mark.parametrize("name", ["small", "mid"])
-def test_potential_modifiers(ctx, name, coul, mods):
+def test_potential_modifiers(ctx, name, coul, mods, search_mode):
     """Potential-shift and excluded-pair reaction-field variants against the
     oracle with the same modifiers, at the standard tolerances."""
     s = BOXES[name]()
@@ -479,4 +482,5 @@ def test_thread_search_grows_an_overflowing_list(ctx):
         assert info["n_items"] >= info["n_entries"] / 4
     finally:
         nb.nb_sys_destroy(h)
-        nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], old["search_mode"])
+        nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], old["search_mode"],
+                             old["energy_mode"])
