@@ -901,7 +901,7 @@ def run_ensemble(args) -> dict:
 
     def plain_pass():
         for h, (xq, ty), t in zip(hs, dev_in, plain_tuning):
-            nb.nb_ctx_set_tuning(ctx, t["max_entries"], t["force_min_blocks"])
+            nb.nb_ctx_set_tuning(ctx, t["max_entries"], t["force_min_blocks"], t["search_mode"], t["energy_mode"])
             nb.nb_grid_put(h, xq, ty)
             nb.nb_pairlist_build(h)
             nb.nb_forces(h, None, f, ed, vd, flags)
@@ -917,16 +917,58 @@ def run_ensemble(args) -> dict:
         t_plain = (time.perf_counter() - t0) / args.steps
         for h in hs:
             pairs += nb.nb_eval_info(h)["n_pairs"]
+        # per-stage device time of one plain pass (every stage bracketed by
+        # events: an instrumented pass after the timed ones)
+        nb.nb_ctx_timing(ctx, reset=True)
+        nb.nb_ctx_set_timing(ctx, True)
+        plain_pass()
+        stream.synchronize()
+        nb.nb_ctx_set_timing(ctx, False)
+        plain_stages = nb.nb_ctx_timing(ctx, reset=True)
     for h in hs:
         nb.nb_sys_destroy(h)
     nb.nb_ctx_destroy(ctx)
+    # per-stage device time of one batched evaluation: the same batch on a
+    # context on the legacy stream, which runs its launches directly (a
+    # captured graph cannot carry the stage events)
+    ctx2 = nb.nb_ctx_create(0, None, 0)
+    autotune.apply(ctx2, "rf", tot_atoms, table, gpu=gpu)
+    hs2 = []
+    for x, (xq, ty) in zip(systems, dev_in):
+        h = nb.nb_sys_create(ctx2, p, x.n, x.box)
+        nb.nb_set_exclusions(h, x.excl_index, x.excl_atoms)
+        nb.nb_sys_set_coords(h, xq, ty)
+        hs2.append(h)
+    b2 = nb.nb_batch_create(ctx2, hs2)
+    for _ in range(2):
+        assert _batch_eval(nb, b2, flags)
+    nb.nb_ctx_timing(ctx2, reset=True)
+    nb.nb_ctx_set_timing(ctx2, True)
+    assert _batch_eval(nb, b2, flags)
+    nb.nb_ctx_set_timing(ctx2, False)
+    batch_stages = nb.nb_ctx_timing(ctx2, reset=True)
+    nb.nb_batch_destroy(b2)
+    for h in hs2:
+        nb.nb_sys_destroy(h)
+    nb.nb_ctx_destroy(ctx2)
+
+    def table_of(st):
+        return {k: round(v[0], 4) for k, v in st.items() if v[1] > 0}
+
+    bst, pst = table_of(batch_stages), table_of(plain_stages)
     return {"workload": "64 water boxes, 1,000-32,000 waters (log-uniform, seed 4), "
                         f"{tot_atoms} atoms in total, LJ + RF, energies and virial",
             "batched_systems_per_s": len(systems) / t_batch, "plain_systems_per_s": len(systems) / t_plain,
             "batched_over_plain": t_plain / t_batch, "batched_pairs_per_s": pairs / t_batch,
             "batched_ms": 1e3 * t_batch, "plain_ms": 1e3 * t_plain, "tuning": tuning,
             "plain_tuning": "the tuner's entry for each system's own size",
-            "timing": "host wall clock per evaluation of all 64 systems (submit to completion)"}
+            "timing": "host wall clock per evaluation of all 64 systems (submit to completion)",
+            "stages_ms": {"batched": bst, "plain": pst,
+                          "batched_sum": round(sum(bst.values()), 4), "plain_sum": round(sum(pst.values()), 4),
+                          "plain_launches": {k: v[1] for k, v in plain_stages.items() if v[1] > 0},
+                          "note": "device time per stage of one evaluation of all 64 systems, every stage "
+                                  "bracketed by CUDA events (instrumented passes after the timed ones; the "
+                                  "batched one runs its launches directly instead of the graph)"}}
 
 
 def run_serve(args, n_req: int = 256) -> dict:
