@@ -45,13 +45,17 @@ SIGMA = 0.005
 # FP32 operations (FADD, FMUL, FFMA: one each; the paired FADD2, FMUL2, FFMA2
 # instructions the kernel issues count one per half) per evaluated atom-pair
 # slot in the force kernel's pair code, by (coulomb, virial), counted from the
-# source; and the same code's flops (FFMA = 2).  The FP32-pipe fraction is the
-# operation rate over SMs x 128 FP32 lanes x SM clock.
-OPS_PER_SLOT = {("rf", False): 26, ("rf", True): 32, ("ewald", False): 43, ("ewald", True): 49}
-FLOPS_PER_SLOT = {("rf", False): 30, ("rf", True): 42, ("ewald", False): 56, ("ewald", True): 68}
+# source; and the same code's flops (FFMA = 2).  The water boxes take the
+# Lennard-Jones weight path (one nonzero LJ parameter pair): against the type-
+# pair table it adds the weight product w_i w_j and one multiply by it per
+# slot (RF: 26 -> 28; Ewald: the multiply is fused into an FFMA that replaces
+# an FADD, 43 -> 44).  The FP32-pipe fraction is the operation rate over SMs x
+# 128 FP32 lanes x SM clock.
+OPS_PER_SLOT = {("rf", False): 28, ("rf", True): 34, ("ewald", False): 44, ("ewald", True): 50}
+FLOPS_PER_SLOT = {("rf", False): 32, ("rf", True): 44, ("ewald", False): 58, ("ewald", True): 70}
 # SHA-256 prefix of csrc/nb_kernel.cu when the two tables above were counted:
 # the line reports whether the timed kernel is still that source
-OPS_COUNTED_FOR = "e7c502c015cfe5ef"
+OPS_COUNTED_FOR = "2a9b9fb96b3e9560"
 # The algorithmic budget per computed slot of a forces-only evaluation, from
 # the operation list of the pair interaction (d 3, r^2 3, cut-off select 2-3,
 # 1/r^2 and 1/r^6 3, LJ 4-5, RF 3 or the Ewald erfc polynomial 8-12 and its

@@ -388,6 +388,32 @@ KParams make_kparams(const nb_sys* s) {
     k.force_min_blocks = 3;
     k.coul = p.coul;
     k.ntypes = p.ntypes;
+    {
+        // Lennard-Jones as weights (KParams::lj_weights): every nonzero entry
+        // is the same (c6, c12) and the nonzero entries are exactly the pairs
+        // of types in one set
+        const int nt = p.ntypes;
+        const float* c6 = s->c6.empty() ? p.c6 : s->c6.data();
+        const float* c12 = s->c12.empty() ? p.c12 : s->c12.data();
+        unsigned long long m = 0;
+        float C6 = 0.f, C12 = 0.f;
+        for (int t = 0; t < nt; ++t)
+            if (c6[t * nt + t] != 0.f || c12[t * nt + t] != 0.f) {
+                m |= 1ull << t;
+                C6 = c6[t * nt + t];
+                C12 = c12[t * nt + t];
+            }
+        bool ok = nt <= 64;
+        for (int i = 0; i < nt && ok; ++i)
+            for (int j = 0; j < nt && ok; ++j) {
+                const bool in = ((m >> i) & 1ull) && ((m >> j) & 1ull);
+                ok = in ? (c6[i * nt + j] == C6 && c12[i * nt + j] == C12) : (c6[i * nt + j] == 0.f && c12[i * nt + j] == 0.f);
+            }
+        k.lj_weights = ok ? 1 : 0;
+        k.ljw_mask = m;
+        k.c6w = 6.0f * C6;
+        k.c12w = 12.0f * C12;
+    }
     k.lj = s->d_lj;
     k.lje = s->d_lj + (size_t)p.ntypes * p.ntypes;
     return k;

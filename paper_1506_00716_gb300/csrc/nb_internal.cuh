@@ -135,6 +135,13 @@ struct KParams {
     int energy_mode;     // 0: a separate energy kernel, 1: energies fused into the force kernel
     int lpt_max_items;   // item count up to which items run longest first
     int force_min_blocks;  // force-kernel launch-bounds variant: 1, 2 or 3
+    // Lennard-Jones as weights: when the table has one nonzero parameter
+    // pair, c6_ij = C6 w_i w_j and c12_ij = C12 w_i w_j with w = 1 for the
+    // types in ljw_mask and 0 otherwise, exactly; the force kernel then takes
+    // w from the type instead of looking the pair up
+    int lj_weights;                 // 1: the table is of that form
+    unsigned long long ljw_mask;    // bit t: type t has w = 1
+    float c6w, c12w;                // 6 C6, 12 C12 (the force table's values)
     const float2* lj;    // [ntypes^2] (6 c6, 12 c12), force kernel
     const float2* lje;   // [ntypes^2] (c6, c12), energy kernel
 };

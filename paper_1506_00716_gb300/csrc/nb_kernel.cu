@@ -114,12 +114,15 @@ struct IPair {
 
 // Force of two pair slots (the halves): as pair_force, with the decisions
 // in0, in1 applied to F/r at the end (a slot that is out contributes
-// nothing, whatever its arithmetic gave).
-template <int COUL, bool VIR>
+// nothing, whatever its arithmetic gave).  With LJW the Lennard-Jones
+// parameters are the table's single pair (6 C6, 12 C12) and its term is
+// multiplied by the pair weight ww = w_i w_j (0 or 1), which reproduces the
+// table's values exactly.
+template <int COUL, bool VIR, bool LJW = false>
 __device__ __forceinline__ void pair_force2(float2 dx, float2 dy, float2 dz, float2 r2, bool in0, bool in1,
                                             float2 qi, float2 qj, float2 c6, float2 c12, const KParams& kp,
                                             const EwaldC& ew, float2 (&fi)[3], float2 (&fj)[3],
-                                            float2 (&v)[6]) {
+                                            float2 (&v)[6], float2 ww = make_float2(1.f, 1.f)) {
     const float2 rinv = make_float2(rsqrt_sfu(r2.x), rsqrt_sfu(r2.y));
     const float2 qq = mul2(qi, qj);
     const float2 rinv2 = mul2(rinv, rinv);
@@ -129,13 +132,17 @@ __device__ __forceinline__ void pair_force2(float2 dx, float2 dy, float2 dz, flo
     float2 fr;  // F/r
     if (COUL == NB_COUL_RF) {
         const float2 fc = mul2(qq, fma2(rinv, rinv2, dup2(-kp.two_krf)));
-        fr = fma2(sub2(t12, t6), rinv2, fc);
+        fr = fma2(LJW ? mul2(sub2(t12, t6), ww) : sub2(t12, t6), rinv2, fc);
     } else {
         const float2 r = mul2(r2, rinv);
         const float2 arg = mul2(r2, dup2(ew.mb2_log2e));
         const float2 ex = make_float2(ex2_sfu(arg.x), ex2_sfu(arg.y));
         const float2 erfcv = mul2(erfcx_force2(mul2(dup2(ew.beta), r)), ex);
-        fr = mul2(sub2(add2(fma2(mul2(qq, dup2(ew.c2)), ex, mul2(mul2(qq, erfcv), rinv)), t12), t6), rinv2);
+        const float2 coul = fma2(mul2(qq, dup2(ew.c2)), ex, mul2(mul2(qq, erfcv), rinv));
+        if (LJW)
+            fr = mul2(fma2(sub2(t12, t6), ww, coul), rinv2);
+        else
+            fr = mul2(sub2(add2(coul, t12), t6), rinv2);
     }
     fr.x = in0 ? fr.x : 0.f;
     fr.y = in1 ? fr.y : 0.f;
@@ -178,11 +185,14 @@ __host__ __device__ __forceinline__ int lj_e_offset(int nt) { return (LJ_C12 + n
 // With ENER, the slots whose pair lies inside rc (or within the band around
 // it, decided exactly later) are also marked for the energies: bit 2p + c of
 // ebits for half c of step p, the same bit of mbits if it lies in the band.
-template <int COUL, bool VIR, bool MASKED, bool SHIFTED, bool EXACT, bool ENER>
+//
+// With LJW the staged type slots hold the j-atoms' Lennard-Jones weights
+// (0.f or 1.f) and wi2 holds the i-atom's, in both halves.
+template <int COUL, bool VIR, bool MASKED, bool SHIFTED, bool EXACT, bool ENER, bool LJW>
 __device__ __forceinline__ void pair_block2(const float* __restrict__ sj, int h, const IPair& xs, float2 qi,
                                             const float* __restrict__ ljrow, unsigned row, const KParams& kp, const EwaldC& ew,
                                             float2 (&fi)[3], float2 (&fj)[4][3], float2 (&v)[6], bool& band,
-                                            unsigned& ebits, unsigned& mbits) {
+                                            unsigned& ebits, unsigned& mbits, float2 wi2) {
 #pragma unroll
     for (int p = 0; p < CL / 2; ++p) {
         const float* rec = sj + JB_REC * (p ^ h);
@@ -213,12 +223,18 @@ __device__ __forceinline__ void pair_block2(const float* __restrict__ sj, int h,
             ebits |= ((q0 ? 1u : 0u) | (q1 ? 2u : 0u)) << (2 * p);
             mbits |= ((q0 && !(r2.x < kp.rc2_lo) ? 1u : 0u) | (q1 && !(r2.y < kp.rc2_lo) ? 2u : 0u)) << (2 * p);
         }
-        const float* l0 = ljrow + tj.x;
-        const float* l1 = ljrow + tj.y;
-        const float2 c6 = make_float2(l0[0], l1[0]);
-        const float2 c12 = make_float2(l0[LJ_C12], l1[LJ_C12]);
-        pair_force2<COUL, VIR>(dx, dy, dz, r2, in0, in1, qi, make_float2(b.z, b.w), c6, c12, kp, ew, fi, fj[p],
-                               v);
+        if (LJW) {
+            const float2 ww = mul2(wi2, make_float2(__int_as_float(tj.x), __int_as_float(tj.y)));
+            pair_force2<COUL, VIR, true>(dx, dy, dz, r2, in0, in1, qi, make_float2(b.z, b.w), dup2(kp.c6w),
+                                         dup2(kp.c12w), kp, ew, fi, fj[p], v, ww);
+        } else {
+            const float* l0 = ljrow + tj.x;
+            const float* l1 = ljrow + tj.y;
+            const float2 c6 = make_float2(l0[0], l1[0]);
+            const float2 c12 = make_float2(l0[LJ_C12], l1[LJ_C12]);
+            pair_force2<COUL, VIR>(dx, dy, dz, r2, in0, in1, qi, make_float2(b.z, b.w), c6, c12, kp, ew, fi, fj[p],
+                                   v);
+        }
     }
 }
 
@@ -229,7 +245,10 @@ __device__ __forceinline__ void pair_block2(const float* __restrict__ sj, int h,
 // double-float (nb_energy2.cuh, the energy kernel's arithmetic), two per lane;
 // the queue is emptied at the end of every work item.  The energy kernel's
 // second pass over the list (staging, screening) is saved.
-template <int COUL, bool VIR, int MINB, bool ENER, bool LJSH>
+//
+// With LJW (KParams::lj_weights) the Lennard-Jones parameters come from the
+// atoms' weights instead of the type-pair table.
+template <int COUL, bool VIR, int MINB, bool ENER, bool LJSH, bool LJW = false>
 __global__ void __launch_bounds__(FW * 32, MINB)
 k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     pdl_wait();
@@ -322,8 +341,10 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         const ShiftedI xs = shift_i(xi4, sh, Lx, Ly, Lz, Tbx, Tcx, Tcy);
         const IPair xp = {dup2(xs.xh), dup2(xs.yh), dup2(xs.zh), dup2(xs.xl), dup2(xs.yl), dup2(xs.zl)};
         const float qi = xi4.w * kp.fq;
-        const int tirow = type_s[ci * CL + i] * nt;
+        const int ti = type_s[ci * CL + i];
+        const int tirow = ti * nt;
         const float* const ljrow = s_ljt + tirow;
+        const float wi = LJW ? (float)((kp.ljw_mask >> ti) & 1ull) : 0.f;
         float2 ch = dup2(0.f), cl = dup2(0.f), e12 = dup2(0.f), e12l = dup2(0.f), e6 = dup2(0.f),
                e6l = dup2(0.f);
         int npair = 0;
@@ -367,7 +388,7 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             sjg[st + 2] = pxq.y;
             sjg[JB_Z + st] = pxq.z;
             sjg[JB_Z + st + 2] = pxq.w;
-            reinterpret_cast<int*>(sjg)[JB_T + st] = pty;
+            reinterpret_cast<int*>(sjg)[JB_T + st] = LJW ? __float_as_int((float)((kp.ljw_mask >> pty) & 1ull)) : pty;
             const int ccj = cjn;
             const bool cact = act;
             const unsigned long long cm = pm;
@@ -399,14 +420,14 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             unsigned ebits = 0u, mbits = 0u;
             const bool full = __all_sync(FULL, row == 0xffu);
             if (full && !shifted)
-                pair_block2<COUL, VIR, false, false, EXACT, ENER>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
-                                                                 fi, fj, v, band, ebits, mbits);
+                pair_block2<COUL, VIR, false, false, EXACT, ENER, LJW>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
+                                                                      fi, fj, v, band, ebits, mbits, dup2(wi));
             else if (full)
-                pair_block2<COUL, VIR, false, true, EXACT, ENER>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
-                                                                fi, fj, v, band, ebits, mbits);
+                pair_block2<COUL, VIR, false, true, EXACT, ENER, LJW>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
+                                                                     fi, fj, v, band, ebits, mbits, dup2(wi));
             else
-                pair_block2<COUL, VIR, true, true, EXACT, ENER>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
-                                                               fi, fj, v, band, ebits, mbits);
+                pair_block2<COUL, VIR, true, true, EXACT, ENER, LJW>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
+                                                                    fi, fj, v, band, ebits, mbits, dup2(wi));
             // transposed butterfly over the 8 lanes of the group: half c of
             // fj[p] holds j-slot 2 (p XOR (i >> 1)) + c, so the partners at
             // XOR 4 and 2 hold the same slots in fj[p ^ 2] and fj[p ^ 1]; at
@@ -447,7 +468,9 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
                         if (r2 < kp.rc2_lo || !(r2 < kp.rc2_hi)) continue;
                         if (!exact_inside(xs, xj, kp.rc2_d)) continue;
                         const int tj = reinterpret_cast<const int*>(sjg)[o + JB_T];
-                        const float2 c = make_float2(ljrow[tj], ljrow[LJ_C12 + tj]);
+                        const float wij = LJW ? wi * __int_as_float(tj) : 0.f;
+                        const float2 c = LJW ? make_float2(kp.c6w * wij, kp.c12w * wij)
+                                             : make_float2(ljrow[tj], ljrow[LJ_C12 + tj]);
                         float gx = 0.f, gy = 0.f, gz = 0.f;
                         float vs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                         pair_force<COUL, VIR>(dx, dy, dz, r2, true, qi, xj.w, c, kp, ew, fsx, fsy, fsz, gx, gy,
@@ -621,11 +644,11 @@ __global__ void k_finish(const SysDev* __restrict__ sys, const int* __restrict__
     }
 }
 
-template <int COUL, bool VIR, int MINB, bool ENER = false, bool LJSH = false>
+template <int COUL, bool VIR, int MINB, bool ENER = false, bool LJSH = false, bool LJW = false>
 cudaError_t launch_forces_t(const PlanLaunch& p, cudaStream_t st) {
     const size_t nt2 = (size_t)p.kp.ntypes * p.kp.ntypes;
     const size_t smem = ENER ? (lj_e_offset(p.kp.ntypes) + 2 * nt2) * sizeof(float) : (LJ_C12 + nt2) * sizeof(float);
-    auto kern = k_forces<COUL, VIR, MINB, ENER, LJSH>;
+    auto kern = k_forces<COUL, VIR, MINB, ENER, LJSH, LJW>;
     if (ENER) {
         // the energy queue makes static + dynamic shared memory pass 48 KB
         // for larger type tables: allow the dynamic part explicitly
@@ -654,10 +677,13 @@ cudaError_t launch_prepare(const PlanLaunch& p, bool coords, cudaStream_t st) {
 
 template <int COUL, bool VIR>
 cudaError_t launch_forces_v(const PlanLaunch& p, cudaStream_t st) {
+    // Lennard-Jones by weights for the register budgets of 2 and 3 blocks per
+    // SM (the others take the table)
+    const bool w = p.kp.lj_weights != 0;
     switch (p.kp.force_min_blocks) {
         case 1: return launch_forces_t<COUL, VIR, 1>(p, st);
-        case 2: return launch_forces_t<COUL, VIR, 2>(p, st);
-        default: return launch_forces_t<COUL, VIR, 3>(p, st);
+        case 2: return w ? launch_forces_t<COUL, VIR, 2, false, false, true>(p, st) : launch_forces_t<COUL, VIR, 2>(p, st);
+        default: return w ? launch_forces_t<COUL, VIR, 3, false, false, true>(p, st) : launch_forces_t<COUL, VIR, 3>(p, st);
     }
 }
 

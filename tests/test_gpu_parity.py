@@ -484,3 +484,56 @@ def test_thread_search_grows_an_overflowing_list(ctx):
         nb.nb_sys_destroy(h)
         nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], old["search_mode"],
                              old["energy_mode"])
+
+
+def _three_type_box(seed):
+    """The 1,944-atom box with every third oxygen made type 2: a Lennard-Jones
+    table with three distinct nonzero parameter pairs (geometric mixing of
+    sigma-epsilon pairs), which the kernels must look up per type pair."""
+    s = wb.small_box(seed=seed)
+    t = s.type.copy()
+    o = np.nonzero(t == 0)[0]
+    t[o[::3]] = 2
+    s = dataclasses.replace(s, type=t)
+    sig = np.array([0.3166, 0.0, 0.34])
+    eps = np.array([0.650, 0.0, 0.45])
+    c6 = np.zeros(9, dtype=np.float32)
+    c12 = np.zeros(9, dtype=np.float32)
+    for a in range(3):
+        for b in range(3):
+            sg = 0.5 * (sig[a] + sig[b])
+            ep = np.sqrt(eps[a] * eps[b])
+            c6[3 * a + b] = 4 * ep * sg**6
+            c12[3 * a + b] = 4 * ep * sg**12
+    return s, c6, c12
+
+
+@pytest.mark.parametrize("coul", [wb.COUL_RF, wb.COUL_EWALD])
+def test_general_lennard_jones_table(ctx, coul):
+    """A type-pair table that is not one parameter pair: the force kernel's
+    table lookup, against the oracle."""
+    s, c6, c12 = _three_type_box(seed=1)
+    p = wb.Params(coul=coul, ntypes=3, c6=c6, c12=c12)
+    f, e, v, _ = gpu_eval(ctx, s, p)
+    _check(s, p, f, e, v)
+
+
+@pytest.mark.parametrize("coul", [wb.COUL_RF, wb.COUL_EWALD])
+def test_lennard_jones_weights_match_the_table(ctx, coul):
+    """Water (Lennard-Jones on oxygen only) takes the force kernel's weight
+    path; the same water with an unused third type whose own pair is nonzero
+    (so that the table is no longer one parameter pair) takes the table path.
+    The pair terms are the same floats (Ewald adds one term in another
+    order), so the forces agree to the rounding of their float atomic sums,
+    whose order differs from run to run."""
+    s = wb.small_box(seed=1)
+    p = wb.Params(coul=coul)
+    f1, e1, v1, _ = gpu_eval(ctx, s, p, flags=nb.NB_F_VIRIAL)
+    c6 = np.zeros(9, dtype=np.float32)
+    c12 = np.zeros(9, dtype=np.float32)
+    c6[0], c12[0] = p.c6[0], p.c12[0]
+    c6[8], c12[8] = 1e-3, 1e-6  # type 2: no atom has it
+    q = wb.Params(coul=coul, ntypes=3, c6=c6, c12=c12)
+    f2, e2, v2, _ = gpu_eval(ctx, s, q, flags=nb.NB_F_VIRIAL)
+    assert rel_rms(f1, f2) <= 1e-6
+    assert np.abs(v1 - v2).max() <= 1e-6 * np.linalg.norm(v1)
