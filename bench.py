@@ -49,19 +49,22 @@ SIGMA = 0.005
 # Lennard-Jones weight path (one nonzero LJ parameter pair): against the type-
 # pair table it adds the weight product w_i w_j and one multiply by it per
 # slot (RF: 26 -> 28; Ewald: the multiply is fused into an FFMA that replaces
-# an FADD, 43 -> 44).  The FP32-pipe fraction is the operation rate over SMs x
-# 128 FP32 lanes x SM clock.
-OPS_PER_SLOT = {("rf", False): 28, ("rf", True): 34, ("ewald", False): 44, ("ewald", True): 50}
-FLOPS_PER_SLOT = {("rf", False): 32, ("rf", True): 44, ("ewald", False): 58, ("ewald", True): 70}
+# an FADD, 34 -> 35).  The Ewald term is a cubic table of G(r): r, the
+# interval index (round-down FFMA, FADD), s, three FFMA, qq G / r.  The
+# FP32-pipe fraction is the operation rate over SMs x 128 FP32 lanes x SM
+# clock.
+OPS_PER_SLOT = {("rf", False): 28, ("rf", True): 34, ("ewald", False): 35, ("ewald", True): 41}
+FLOPS_PER_SLOT = {("rf", False): 32, ("rf", True): 44, ("ewald", False): 43, ("ewald", True): 55}
 # SHA-256 prefix of csrc/nb_kernel.cu when the two tables above were counted:
 # the line reports whether the timed kernel is still that source
-OPS_COUNTED_FOR = "2a9b9fb96b3e9560"
+OPS_COUNTED_FOR = "06a96200b0d088ec"
 # The algorithmic budget per computed slot of a forces-only evaluation, from
 # the operation list of the pair interaction (d 3, r^2 3, cut-off select 2-3,
-# 1/r^2 and 1/r^6 3, LJ 4-5, RF 3 or the Ewald erfc polynomial 8-12 and its
-# exponential, F/r combine 2, i- and j-force 6): the fraction is also given
+# 1/r^2 and 1/r^6 3, LJ 4-5, RF 3, or for Ewald r and G(r) by a table
+# (index, cubic: 6) up to an erfc polynomial with its exponential (12) and
+# qq G / r 2, F/r combine 2, i- and j-force 6): the fraction is also given
 # against these bounds, independent of how the source is written.
-ALGO_OPS_PER_SLOT = {"rf": (25, 28), "ewald": (33, 40)}
+ALGO_OPS_PER_SLOT = {"rf": (25, 28), "ewald": (31, 40)}
 # kernels launched per timed stage (nb_ctx_timing)
 KERNELS_PER_STAGE = {"grid": 6, "search": 1, "prune": 1, "coord": 0, "zero": 1, "forces": 1, "final": 1,
                      "energy": 1, "pme_spread": 1, "pme_fft": 5, "pme_gather": 2}

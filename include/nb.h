@@ -82,7 +82,7 @@ enum {
  *                 ((2 eps_rf + eps_r) rc^3), c_rf = 1/rc + k_rf rc^2
  *                 (eps_rf = 0 means infinity: k_rf = 1/(2 rc^3));
  *               NB_COUL_EWALD: Ewald real space, V = f qi qj / eps_r
- *                 erfc(beta r) / r
+ *                 erfc(beta r) / r (ewald_beta > 0, ewald_beta rc <= 10)
  *   fcoul       electric conversion factor f = 1/(4 pi eps_0), 138.935458
  *   ntypes      number of Lennard-Jones types, 1..64
  *   c6, c12     host arrays of ntypes*ntypes floats, row-major [ti*ntypes+tj],
@@ -333,6 +333,28 @@ nb_status nb_eval_info(nb_sys *sys, nb_eval_stats *stats);
  */
 nb_status nb_pairlist_export(nb_sys *sys, int *perm, int *items, int *cj,
                              unsigned long long *mask, long long *n_entries_total);
+
+/*
+ * Test hook (host only, no device work): the Ewald force table of the
+ * force kernel for splitting parameter beta (nm^-1) and cut-off rc (nm).
+ * With NB_COUL_EWALD the force kernel takes the real-space force factor as
+ * F/r = f qi qj G(r) / r^3, with G(r) = erfc(beta r) + 2 beta r / sqrt(pi)
+ * exp(-beta^2 r^2) (the derivative of the energy term of Section 3.2's
+ * pair interaction, see nb_params), from a cubic Hermite table of G on
+ * intervals of width h = 2^-n: interval k covers [k h, (k + 1) h) and holds
+ * (b0, b1, b2, b3), G(r) ~ b0 + b1 s + b2 s^2 + b3 s^3 with s = r / h - k.
+ * h is the largest power of two for which every interval's interpolation
+ * error bound (h^4 / 384 times the maximum of |d^4 G / dr^4| on it) is at
+ * most 1e-7 of G at the interval's far end (G decreases; G taken as at least
+ * 1e-7 there), and the intervals reach rc (1 + 1e-4).
+ *   coef          4 * max_intervals floats (host), or NULL for the size only
+ *   n_intervals   receives the number of intervals (at most 2048)
+ *   h             receives the interval width (nm); may be NULL
+ * NB_ERR_ARG unless beta > 0, rc > 0 and beta rc <= 10 (the limit of
+ * nb_sys_create for NB_COUL_EWALD), or if coef holds fewer intervals.
+ */
+nb_status nb_ewald_force_table(double beta, double rc, float *coef, int max_intervals, int *n_intervals,
+                               double *h);
 
 /*
  * Batched evaluation of many independent systems (the paper's ensemble

@@ -1,6 +1,5 @@
 // erfc_fit.cuh -- generated by fit_erfc.py; do not edit.
 // erfc(x) = exp(-x^2) R(u), t = 1/(1 + EF_P x), u = EF_UA t + EF_UB, x in [0, EF_XMAX].
-// force fit: degree 8, max relative error 2.00e-08 (1.34e-07 with the float32 coefficients below)
 // energy fit: degree 12, max relative error 4.41e-11 (4.41e-11 with the head + tail coefficients below)
 #pragma once
 namespace nbgb {
@@ -8,8 +7,6 @@ constexpr float EF_P = 0.4f;
 constexpr float EF_XMAX = 6.0f;
 constexpr float EF_UA = 2.8333333f;
 constexpr float EF_UB = -1.8333334f;
-constexpr int EF_NF = 9;
-__device__ constexpr float EF_FORCE[EF_NF] = {0.3454021f, 0.39277083f, 0.19105749f, 0.06116954f, 0.010361112f, -0.0003214845f, -0.00045302324f, -7.110746e-06f, 2.069298e-05f};
 constexpr int EF_NE = 13;
 __device__ constexpr float EF_EN_HI[EF_NE] = {0.3454021f, 0.39277083f, 0.19105737f, 0.06116964f, 0.0103621f, -0.00032189983f, -0.00045583156f, -6.419039e-06f, 2.3997538e-05f, -4.913019e-07f, -1.4358875e-06f, 1.203554e-07f, 6.9129975e-08f};
 __device__ constexpr float EF_EN_LO[EF_NE] = {-4.4934265e-09f, -5.7412146e-09f, -6.573779e-09f, -5.609882e-10f, -8.8758646e-11f, 4.9718953e-13f, -1.41651925e-11f, 1.4295954e-13f, 2.5595736e-13f, -1.0181217e-14f, -3.9859138e-14f, -2.4092192e-15f, 2.3144078e-15f};

@@ -1,5 +1,5 @@
 #!/usr/bin/env python3
-"""Fit the erfc approximations used by the Ewald kernels; writes erfc_fit.cuh.
+"""Fit the erfc approximation used by the Ewald energy kernel; writes erfc_fit.cuh.
 
 Form: erfc(x) = exp(-x^2) R(u), with t = 1 / (1 + P x) on x in [0, XMAX]
 and u = UA t + UB mapping t's range onto [-1, 1].  R is a polynomial in u
@@ -11,12 +11,12 @@ R stays smooth and close to 1, and the power-basis coefficients sum to
 about 1 in magnitude, so a float32 Horner evaluation adds only a few
 roundings.
 
-Two fits: degree 8 for the force kernel (max relative error ~2e-8) and
-degree 12 for the energy kernel (~4e-11), the latter with every
+The fit is of degree 12 (max relative error ~4e-11), with every
 coefficient split into a float32 head and a float32 tail so that the
-rounding of the coefficients does not bias the energy.  A third fit, of
+rounding of the coefficients does not bias the energy.  A second fit, of
 2^f on [-0.5, 0.5] (degree 10, head + tail), gives the energy kernel an
-exponential free of the SFU's approximation error.
+exponential free of the SFU's approximation error.  (The force kernel
+takes the Ewald force from a table built by the library at run time.)
 
 Run: python fit_erfc.py  (needs numpy and scipy; the output is committed)
 """
@@ -67,7 +67,6 @@ def fmt(v: float) -> str:
 
 
 def main():
-    af = fit(8)
     ae = fit(12)
     ae_hi = ae.astype(np.float32)
     ae_lo = (ae - ae_hi.astype(np.float64)).astype(np.float32)
@@ -76,15 +75,12 @@ def main():
     e2 = float(np.abs(np.polynomial.polynomial.polyval(ff, a2) / np.exp2(ff) - 1.0).max())
     a2_hi = a2.astype(np.float32)
     a2_lo = (a2 - a2_hi.astype(np.float64)).astype(np.float32)
-    # the errors of the coefficients as stored: float32 (force fit), float32
-    # head + float32 tail (energy fit), each evaluated exactly in float64
-    af_st = af.astype(np.float32).astype(np.float64)
+    # the error of the coefficients as stored (float32 head + float32 tail),
+    # evaluated exactly in float64
     ae_st = ae_hi.astype(np.float64) + ae_lo.astype(np.float64)
     lines = [
         "// erfc_fit.cuh -- generated by fit_erfc.py; do not edit.",
         "// erfc(x) = exp(-x^2) R(u), t = 1/(1 + EF_P x), u = EF_UA t + EF_UB, x in [0, EF_XMAX].",
-        f"// force fit: degree {len(af) - 1}, max relative error {max_rel_error(af):.2e}"
-        f" ({max_rel_error(af_st):.2e} with the float32 coefficients below)",
         f"// energy fit: degree {len(ae) - 1}, max relative error {max_rel_error(ae):.2e}"
         f" ({max_rel_error(ae_st):.2e} with the head + tail coefficients below)",
         "#pragma once",
@@ -93,8 +89,6 @@ def main():
         f"constexpr float EF_XMAX = {fmt(XMAX)};",
         f"constexpr float EF_UA = {fmt(UA)};",
         f"constexpr float EF_UB = {fmt(UB)};",
-        f"constexpr int EF_NF = {len(af)};",
-        "__device__ constexpr float EF_FORCE[EF_NF] = {" + ", ".join(fmt(v) for v in af) + "};",
         f"constexpr int EF_NE = {len(ae)};",
         "__device__ constexpr float EF_EN_HI[EF_NE] = {" + ", ".join(fmt(v) for v in ae_hi) + "};",
         "__device__ constexpr float EF_EN_LO[EF_NE] = {" + ", ".join(fmt(v) for v in ae_lo) + "};",
@@ -109,7 +103,7 @@ def main():
     with open(out, "w") as fh:
         fh.write("\n".join(lines))
     print(out)
-    print("\n".join(lines[2:4]))
+    print(lines[2])
 
 
 if __name__ == "__main__":

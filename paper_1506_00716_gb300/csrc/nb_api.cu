@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -304,7 +305,7 @@ size_t sys_layout(int natoms, const Geometry& g, int ntypes, SysDev* h, char* ba
     char* col_cl0 = take(4 * ((size_t)g.ncol + 1));
     char* acc = take(8 * NACC);
     char* res = take(8 * NRES);
-    char* lj = take(16 * (size_t)ntypes * ntypes);  // (6 c6, 12 c12) then (c6, c12)
+    char* lj = take(param_table_bytes(ntypes));  // (6 c6, 12 c12), (c6, c12), Ewald force table
     (void)lj;
     if (h) {
         h->xq_in = (float4*)xq_in;
@@ -331,7 +332,7 @@ size_t sys_layout(int natoms, const Geometry& g, int ntypes, SysDev* h, char* ba
 
 float2* sys_lj_ptr(nb_sys* s) {
     size_t total = sys_layout(s->natoms, s->geo, s->p.ntypes, nullptr, nullptr);
-    size_t lj = align256(16 * (size_t)s->p.ntypes * s->p.ntypes);
+    size_t lj = align256(param_table_bytes(s->p.ntypes));
     return (float2*)((char*)s->block + total - lj);
 }
 
@@ -343,6 +344,69 @@ void list_radii(double rlist, const double box[3], SysDev* h) {
     double rl = rlist + 1e-5 * (1.0 + maxL);
     h->rl_search = (float)rl;
     h->rl2_prune = (float)(rl * rl);
+}
+
+int ewald_force_table(double beta, double rc, float4* coef, float* invh) {
+    // the last table built is kept and handed out again while beta and rc
+    // stay the same: building one takes a few hundred microseconds
+    static std::mutex memo_mu;
+    static double memo_beta = -1.0, memo_rc = -1.0;
+    static int memo_n = 0;
+    static float memo_invh = 0.f;
+    static float4 memo[GT_MAX];
+    {
+        std::lock_guard<std::mutex> lk(memo_mu);
+        if (beta == memo_beta && rc == memo_rc) {
+            std::memcpy(coef, memo, sizeof(float4) * (size_t)memo_n);
+            *invh = memo_invh;
+            return memo_n;
+        }
+    }
+    const double isqpi = 0.5641895835477563;
+    // G(r) = erfc(x) + 2 x exp(-x^2) / sqrt(pi), x = beta r, decreasing in r;
+    // its x-derivatives are -4 x^2 exp(-x^2) / sqrt(pi), then -8 (x - x^3),
+    // -8 (1 - 5 x^2 + 2 x^4) and -8 (-12 x + 18 x^3 - 4 x^5), each times
+    // exp(-x^2) / sqrt(pi); the r-derivatives carry powers of beta
+    auto G = [&](double r) { const double x = beta * r; return std::erfc(x) + 2.0 * isqpi * x * std::exp(-x * x); };
+    auto dG = [&](double r) { const double x = beta * r; return -4.0 * isqpi * beta * x * x * std::exp(-x * x); };
+    auto d4G = [&](double r) {
+        const double x = beta * r;
+        const double x2 = x * x, b2 = beta * beta;
+        return std::fabs(8.0 * isqpi * x * (-12.0 + x2 * (18.0 - 4.0 * x2)) * std::exp(-x2)) * b2 * b2;
+    };
+    // relative to G at the interval's far end, G taken as at least 1e-7
+    // (where a pair's force factor is below 1e-7 of its value at contact:
+    // an absolute error of at most 1e-14 there)
+    const double tol = 1e-7;
+    const double rmax = rc * (1.0 + 1e-4);
+    for (int n = 0; n <= 30; ++n) {
+        const double h = std::ldexp(1.0, -n);
+        if (h > rmax) continue;
+        const int K = (int)std::ceil(rmax / h);
+        if (K > GT_MAX) return 0;
+        bool ok = true;
+        for (int k = 0; k < K && ok; ++k) {
+            double m4 = 0.0;
+            for (int q = 0; q <= 16; ++q) m4 = std::max(m4, d4G((k + q / 16.0) * h));
+            ok = h * h * h * h / 384.0 * m4 <= tol * std::max(G((k + 1) * h), 1e-7);
+        }
+        if (!ok) continue;
+        for (int k = 0; k < K; ++k) {
+            const double g0 = G(k * h), g1 = G((k + 1) * h);
+            const double d0 = h * dG(k * h), d1 = h * dG((k + 1) * h);
+            coef[k] = make_float4((float)g0, (float)d0, (float)(3.0 * (g1 - g0) - 2.0 * d0 - d1),
+                                  (float)(2.0 * (g0 - g1) + d0 + d1));
+        }
+        *invh = (float)(1.0 / h);
+        std::lock_guard<std::mutex> lk(memo_mu);
+        std::memcpy(memo, coef, sizeof(float4) * (size_t)K);
+        memo_n = K;
+        memo_invh = *invh;
+        memo_beta = beta;
+        memo_rc = rc;
+        return K;
+    }
+    return 0;
 }
 
 KParams make_kparams(const nb_sys* s) {
@@ -416,6 +480,13 @@ KParams make_kparams(const nb_sys* s) {
     }
     k.lj = s->d_lj;
     k.lje = s->d_lj + (size_t)p.ntypes * p.ntypes;
+    k.gtab = reinterpret_cast<const float4*>(s->d_lj + 2 * (size_t)p.ntypes * p.ntypes);
+    k.gt_n = 0;
+    k.gt_invh = 0.f;
+    if (p.coul == NB_COUL_EWALD) {
+        float4 tab[GT_MAX];
+        k.gt_n = ewald_force_table(p.ewald_beta, p.rc, tab, &k.gt_invh);
+    }
     return k;
 }
 
@@ -735,6 +806,8 @@ nb_status check_params(const nb_params* p) {
     if (p->coul != NB_COUL_RF && p->coul != NB_COUL_EWALD) return fail(NB_ERR_ARG, "unknown coul");
     if (!(p->eps_r > 0)) return fail(NB_ERR_ARG, "eps_r must be > 0");
     if (p->coul == NB_COUL_EWALD && !(p->ewald_beta > 0)) return fail(NB_ERR_ARG, "ewald_beta must be > 0");
+    if (p->coul == NB_COUL_EWALD && !(p->ewald_beta * p->rc <= 10.0))
+        return fail(NB_ERR_ARG, "ewald_beta * rc must be at most 10 (Ewald force table)");
     if (p->ntypes < 1 || p->ntypes > MAX_TYPES) return fail(NB_ERR_ARG, "ntypes must be in 1..64");
     if (!p->c6 || !p->c12) return fail(NB_ERR_ARG, "c6 / c12 are NULL");
     if (p->modifiers & ~(unsigned)(NB_MOD_LJ_SHIFT | NB_MOD_EWALD_SHIFT | NB_MOD_RF_EXCL))
@@ -1011,12 +1084,19 @@ static nb_status sys_create(nb_ctx* ctx, const nb_params* params, int natoms, co
     h.clcap = y->geo.clcap;
     h.excl_index = nullptr;
     h.excl_atoms = nullptr;
-    std::vector<float2> lj(2 * nt * nt);
+    // parameter tables: the Lennard-Jones pairs, then (Ewald) the force table
+    std::vector<float2> lj(2 * nt * nt + 2 * (size_t)GT_MAX);
     for (int k = 0; k < nt * nt; ++k) {
         lj[k] = make_float2(6.0f * y->c6[k], 12.0f * y->c12[k]);
         lj[nt * nt + k] = make_float2(y->c6[k], y->c12[k]);
     }
-    cudaError_t e = cudaMemcpyAsync(y->d_lj, lj.data(), 8 * lj.size(), cudaMemcpyHostToDevice, ctx->stream);
+    int gt_n = 0;
+    if (y->p.coul == NB_COUL_EWALD) {
+        float invh = 0.f;
+        gt_n = ewald_force_table(y->p.ewald_beta, y->p.rc, reinterpret_cast<float4*>(lj.data() + 2 * nt * nt), &invh);
+    }
+    cudaError_t e = cudaMemcpyAsync(y->d_lj, lj.data(), 8 * (2 * (size_t)nt * nt + 2 * (size_t)gt_n),
+                                    cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h.acc, 0, 8 * NACC, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h.res, 0, 8 * NRES, ctx->stream);
     if (e != cudaSuccess) {
@@ -1190,6 +1270,23 @@ nb_status nb_eval_info(nb_sys* sys, nb_eval_stats* stats) {
     NB_CK(cudaMemcpyAsync(&np, sys->h.res + 11, 8, cudaMemcpyDeviceToHost, sys->ctx->stream));
     NB_CK(cudaStreamSynchronize(sys->ctx->stream));
     stats->n_pairs = (long long)np;
+    return NB_OK;
+}
+
+nb_status nb_ewald_force_table(double beta, double rc, float* coef, int max_intervals, int* n_intervals,
+                               double* h) {
+    if (!(beta > 0) || !(rc > 0) || !(beta * rc <= 10.0)) return fail(NB_ERR_ARG, "need beta > 0, rc > 0, beta rc <= 10");
+    if (!n_intervals) return fail(NB_ERR_ARG, "n_intervals is NULL");
+    float4 tab[GT_MAX];
+    float invh = 0.f;
+    const int K = ewald_force_table(beta, rc, tab, &invh);
+    if (K <= 0) return fail(NB_ERR_ARG, "the table needs more intervals than it may hold");
+    *n_intervals = K;
+    if (h) *h = 1.0 / (double)invh;
+    if (coef) {
+        if (max_intervals < K) return fail(NB_ERR_ARG, "coef holds fewer intervals than the table");
+        std::memcpy(coef, tab, 16 * (size_t)K);
+    }
     return NB_OK;
 }
 

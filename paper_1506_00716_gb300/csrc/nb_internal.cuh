@@ -19,6 +19,7 @@ constexpr int NSHIFT = 27;         // periodic images (sx, sy, sz) in {-1,0,1}^3
 constexpr int SHIFT_ZERO = 13;     // index of the zero shift
 constexpr int SEARCH_BUF = 384;    // entries a search warp buffers before flushing
 constexpr int EXCL_BUF = 128;      // exclusion partners a search warp caches
+constexpr int GT_MAX = 2048;       // intervals of the Ewald force table, at most
 
 // Counter slots of a list (ListDev::counters).
 enum {
@@ -142,6 +143,12 @@ struct KParams {
     int lj_weights;                 // 1: the table is of that form
     unsigned long long ljw_mask;    // bit t: type t has w = 1
     float c6w, c12w;                // 6 C6, 12 C12 (the force table's values)
+    // Ewald force table (force kernel): cubic Hermite pieces of G(r) =
+    // erfc(beta r) + 2 beta r / sqrt(pi) exp(-beta^2 r^2) on intervals of
+    // width h = 1 / gt_invh, coefficients (b0, b1, b2, b3) of s = r / h - k
+    const float4* gtab;  // [gt_n]
+    int gt_n;            // intervals (0: reaction field)
+    float gt_invh;
     const float2* lj;    // [ntypes^2] (6 c6, 12 c12), force kernel
     const float2* lje;   // [ntypes^2] (c6, c12), energy kernel
 };
@@ -251,6 +258,19 @@ __device__ __forceinline__ float3 shift_vec(int sh, const float (&L)[3], const f
     const float sx = (float)(sh / 9 - 1), sy = (float)((sh / 3) % 3 - 1), sz = (float)(sh % 3 - 1);
     return make_float3(fmaf(sz, T[1], fmaf(sy, T[0], sx * L[0])), fmaf(sz, T[2], sy * L[1]), sz * L[2]);
 }
+
+// Bytes of a system's parameter tables: the Lennard-Jones tables ((6 c6, 12
+// c12) then (c6, c12), 16 per type pair) and the Ewald force table after them.
+inline size_t param_table_bytes(int ntypes) { return 16 * (size_t)ntypes * ntypes + 16 * (size_t)GT_MAX; }
+// The Ewald force table for splitting parameter beta and cut-off rc: writes
+// up to GT_MAX float4 coefficients, sets *invh, returns the number of
+// intervals (0 if it would need more than GT_MAX; never for beta rc <= 10).
+// Each interval k of width h = 2^-n covers [k h, (k + 1) h); its cubic in
+// s = r / h - k is the Hermite interpolant of G and dG/dr at both ends, with
+// h the largest power of two for which every interval's error bound
+// h^4 / 384 max|d^4 G / dr^4| is at most 1e-7 of G at its far end (G
+// decreases; G taken as at least 1e-7), and the intervals reach rc (1 + 1e-4).
+int ewald_force_table(double beta, double rc, float4* coef, float* invh);
 
 // Host helpers of nb_api.cu shared with the allocation-free entry point.
 nb_status api_fail(nb_status s, const char* msg);

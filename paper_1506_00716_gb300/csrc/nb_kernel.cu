@@ -24,8 +24,10 @@
 //   LJ:    F/r = (12 c12 r^-12 - 6 c6 r^-6) / r^2
 //   RF:    F/r = f qi qj (r^-3 - 2 k_rf)
 //   Ewald: F/r = f qi qj (erfc(b r)/r + 2b/sqrt(pi) exp(-b^2 r^2)) / r^2
-// with erfc(x) = exp(-x^2) R(u) from the degree-8 least-squares fit of
-// erfc_fit.cuh (relative error 1.3e-7 with its float32 coefficients).  Optional virial
+//              = f qi qj G(r) / r^3, G(r) = erfc(b r) + 2 b r / sqrt(pi)
+//                exp(-b^2 r^2), from a cubic Hermite table of G in shared
+//                memory (ewald_force_table: error at most 1e-7, absolute,
+//                with G between 0 and 1).  Optional virial
 // Xi = -1/2 sum_pairs (F/r) d (x) d, summed per pair in float32 and across
 // items in float64.
 //
@@ -42,19 +44,37 @@ namespace {
 constexpr unsigned FULL = FULL_MASK;
 constexpr int FW = 8;  // warps per block of the force kernel
 
+// The Ewald force table in shared memory (KParams::gtab).
 struct EwaldC {
-    float beta, mb2_log2e, c2;  // beta, -beta^2 log2(e), 2 beta / sqrt(pi)
+    const float4* tab;
+    float invh;
+    unsigned last;  // gt_n - 1
 };
 
-// erfc(x) exp(x^2) from the force fit.
-__device__ __forceinline__ float erfcx_force(float x) {
-    x = fminf(x, EF_XMAX);
-    const float t = rcp_sfu(fmaf(EF_P, x, 1.f));
-    const float u = fmaf(EF_UA, t, EF_UB);
-    float r = EF_FORCE[EF_NF - 1];
-#pragma unroll
-    for (int k = EF_NF - 2; k >= 0; --k) r = fmaf(r, u, EF_FORCE[k]);
-    return r;
+// 1.5 * 2^23: a float in [2^23, 2^24) holds an integer in its mantissa
+constexpr float GT_MAGIC = 12582912.f;
+
+// G(r) from the table: interval k = floor(r / h) by the magic constant and
+// a round-down fused multiply-add (no conversion instructions), clamped to
+// the table (far and masked slots give finite or NaN values that the cut-off
+// select discards), and its cubic in s = r / h - k, formed exactly (h is a
+// power of two, so r / h is exact, and so is its fractional part).
+__device__ __forceinline__ float ewald_g(float r, const EwaldC& ew) {
+    const float m = __fmaf_rd(r, ew.invh, GT_MAGIC);
+    const float s = fmaf(r, ew.invh, GT_MAGIC - m);
+    const unsigned k = min((unsigned)(__float_as_int(m) - __float_as_int(GT_MAGIC)), ew.last);
+    const float4 c = ew.tab[k];
+    return fmaf(fmaf(fmaf(c.w, s, c.z), s, c.y), s, c.x);
+}
+__device__ __forceinline__ float2 ewald_g2(float2 r, const EwaldC& ew) {
+    const float2 m = __ffma2_rd(r, dup2(ew.invh), dup2(GT_MAGIC));
+    const float2 s = fma2(r, dup2(ew.invh), sub2(dup2(GT_MAGIC), m));
+    const unsigned k0 = min((unsigned)(__float_as_int(m.x) - __float_as_int(GT_MAGIC)), ew.last);
+    const unsigned k1 = min((unsigned)(__float_as_int(m.y) - __float_as_int(GT_MAGIC)), ew.last);
+    const float4 c0 = ew.tab[k0], c1 = ew.tab[k1];
+    float2 g = fma2(make_float2(c0.w, c1.w), s, make_float2(c0.z, c1.z));
+    g = fma2(g, s, make_float2(c0.y, c1.y));
+    return fma2(g, s, make_float2(c0.x, c1.x));
 }
 
 // Force of one pair slot: d, r^2 and the decision `in` are given.
@@ -75,10 +95,8 @@ __device__ __forceinline__ void pair_force(float dx, float dy, float dz, float r
         const float fc = qq * fmaf(rinv, rinv2, -kp.two_krf);
         fr = fmaf(t12 - t6, rinv2, fc);
     } else {
-        const float r = r2 * rinv;
-        const float ex = ex2_sfu(r2 * ew.mb2_log2e);
-        const float erfcv = erfcx_force(ew.beta * r) * ex;
-        fr = (fmaf(qq * ew.c2, ex, qq * erfcv * rinv) + t12 - t6) * rinv2;
+        const float g = ewald_g(r2 * rinv, ew);
+        fr = (qq * g * rinv + t12 - t6) * rinv2;
     }
     const float fx = fr * dx, fy = fr * dy, fz = fr * dz;
     fix += fx; fiy += fy; fiz += fz;
@@ -91,19 +109,6 @@ __device__ __forceinline__ void pair_force(float dx, float dy, float dz, float r
         v[4] = fmaf(fx, dz, v[4]);
         v[5] = fmaf(fy, dz, v[5]);
     }
-}
-
-// erfc(x) exp(x^2) from the force fit, for two arguments.
-__device__ __forceinline__ float2 erfcx_force2(float2 x) {
-    x.x = fminf(x.x, EF_XMAX);
-    x.y = fminf(x.y, EF_XMAX);
-    const float2 d = fma2(dup2(EF_P), x, dup2(1.f));
-    const float2 t = make_float2(rcp_sfu(d.x), rcp_sfu(d.y));
-    const float2 u = fma2(dup2(EF_UA), t, dup2(EF_UB));
-    float2 r = dup2(EF_FORCE[EF_NF - 1]);
-#pragma unroll
-    for (int k = EF_NF - 2; k >= 0; --k) r = fma2(r, u, dup2(EF_FORCE[k]));
-    return r;
 }
 
 // The i-atom of a lane, shifted, with every component duplicated into both
@@ -134,11 +139,9 @@ __device__ __forceinline__ void pair_force2(float2 dx, float2 dy, float2 dz, flo
         const float2 fc = mul2(qq, fma2(rinv, rinv2, dup2(-kp.two_krf)));
         fr = fma2(LJW ? mul2(sub2(t12, t6), ww) : sub2(t12, t6), rinv2, fc);
     } else {
-        const float2 r = mul2(r2, rinv);
-        const float2 arg = mul2(r2, dup2(ew.mb2_log2e));
-        const float2 ex = make_float2(ex2_sfu(arg.x), ex2_sfu(arg.y));
-        const float2 erfcv = mul2(erfcx_force2(mul2(dup2(ew.beta), r)), ex);
-        const float2 coul = fma2(mul2(qq, dup2(ew.c2)), ex, mul2(mul2(qq, erfcv), rinv));
+        // f qi qj G(r) / r^3 = (qq G / r) / r^2
+        const float2 g = ewald_g2(mul2(r2, rinv), ew);
+        const float2 coul = mul2(mul2(qq, g), rinv);
         if (LJW)
             fr = mul2(fma2(sub2(t12, t6), ww, coul), rinv2);
         else
@@ -175,6 +178,8 @@ constexpr int JB_REC = 12, JB_Z = 4, JB_T = 8, JB_SIZE = 4 * JB_REC;
 // register; the energies' (c6, c12) table follows it (lj_e_offset).
 constexpr int LJ_C12 = MAX_TYPES * MAX_TYPES;
 __host__ __device__ __forceinline__ int lj_e_offset(int nt) { return (LJ_C12 + nt * nt + 1) & ~1; }
+// the Ewald force table (float4, 16-byte aligned) after both
+__host__ __device__ __forceinline__ int gt_offset(int nt) { return (lj_e_offset(nt) + 2 * nt * nt + 3) & ~3; }
 
 // The M x N = 8 x 8 pairs of one entry for one lane (i-slot i), two at a
 // time: step p takes the j-slots 2m and 2m+1, m = p XOR (i >> 1), as the
@@ -277,6 +282,9 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     float2* const s_lje = reinterpret_cast<float2*>(s_ljt + lj_e_offset(nt));
     if (ENER)
         for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) s_lje[k] = kp.lje[k];
+    if (COUL == NB_COUL_EWALD)
+        for (int k = threadIdx.x; k < kp.gt_n; k += blockDim.x)
+            reinterpret_cast<float4*>(s_ljt + gt_offset(nt))[k] = kp.gtab[k];
     if (lane < 6) s_acc[w][lane] = 0.0;
     __syncthreads();
     int* const qm = s_qm[ENER ? w : 0];
@@ -285,9 +293,9 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     long long np = 0;
 
     EwaldC ew;
-    ew.beta = kp.beta;
-    ew.mb2_log2e = -kp.beta * kp.beta * 1.4426950408889634f;
-    ew.c2 = 2.0f * kp.beta * 0.5641895835477563f;
+    ew.tab = reinterpret_cast<const float4*>(s_ljt + gt_offset(nt));
+    ew.invh = kp.gt_invh;
+    ew.last = (unsigned)max(kp.gt_n - 1, 0);
 
     float* const sjg = &s_j[w][g][0];
     // where lane i stages j-slot i: x and y at 12 (i >> 1) + (i & 1) (+ 2),
@@ -647,11 +655,14 @@ __global__ void k_finish(const SysDev* __restrict__ sys, const int* __restrict__
 template <int COUL, bool VIR, int MINB, bool ENER = false, bool LJSH = false, bool LJW = false>
 cudaError_t launch_forces_t(const PlanLaunch& p, cudaStream_t st) {
     const size_t nt2 = (size_t)p.kp.ntypes * p.kp.ntypes;
-    const size_t smem = ENER ? (lj_e_offset(p.kp.ntypes) + 2 * nt2) * sizeof(float) : (LJ_C12 + nt2) * sizeof(float);
+    // LJ tables (the energies' too with ENER), then the Ewald force table
+    const size_t smem = COUL == NB_COUL_EWALD ? (gt_offset(p.kp.ntypes) + 4 * (size_t)p.kp.gt_n) * sizeof(float)
+                        : ENER ? (lj_e_offset(p.kp.ntypes) + 2 * nt2) * sizeof(float)
+                               : (LJ_C12 + nt2) * sizeof(float);
     auto kern = k_forces<COUL, VIR, MINB, ENER, LJSH, LJW>;
-    if (ENER) {
-        // the energy queue makes static + dynamic shared memory pass 48 KB
-        // for larger type tables: allow the dynamic part explicitly
+    if (ENER || smem > 48 * 1024) {
+        // the energy queue (or a large Ewald table) makes static + dynamic
+        // shared memory pass 48 KB: allow the dynamic part explicitly
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }

@@ -126,7 +126,7 @@ extern "C" nb_status nb_eval_noalloc(const nb_params* params, int natoms, const 
     api_sys_layout(natoms, box, nt, &h, sys_base);
     api_list_radii(params->rlist, box, &h);
     off += up256(sys_bytes);
-    float2* d_lj = (float2*)(sys_base + sys_bytes - up256(16 * (size_t)nt * nt));
+    float2* d_lj = (float2*)(sys_base + sys_bytes - up256(param_table_bytes(nt)));
     float2* d_lje = d_lj + (size_t)nt * nt;
     float* d_c6 = (float*)(base + off);
     off += up256(4 * (size_t)nt * nt);
@@ -205,6 +205,18 @@ extern "C" nb_status nb_eval_noalloc(const nb_params* params, int natoms, const 
     if (e == cudaSuccess) {
         k_lj_tables<<<(nt * nt + 255) / 256, 256, 0, st>>>(d_c6, d_c12, nt * nt, d_lj, d_lje);
         e = cudaGetLastError();
+    }
+    // the Ewald force table, after the Lennard-Jones tables (built on the host,
+    // in a buffer on this call's stack)
+    float4 gtab[GT_MAX];
+    if (params->coul == NB_COUL_EWALD) {
+        float invh = 0.f;
+        const int gt_n = ewald_force_table(params->ewald_beta, params->rc, gtab, &invh);
+        if (gt_n > 0)
+            NA_CK(cudaMemcpyAsync((float4*)(d_lj + 2 * (size_t)nt * nt), gtab, 16 * (size_t)gt_n,
+                                  cudaMemcpyHostToDevice, st));
+        // the copy reads the stack buffer: let it finish before the buffer goes
+        NA_CK(cudaStreamSynchronize(st));
     }
     NA_CK(launch_grid_put(p, st));
     NA_CK(launch_search(p, st));

@@ -34,7 +34,7 @@ EXPORTS = ["nb_last_error", "nb_ctx_create", "nb_ctx_destroy", "nb_ctx_memory", 
            "nb_sys_results", "nb_ctx_set_timing", "nb_ctx_set_timing_stages", "nb_ctx_timing", "nb_eval_info",
            "nb_eval_noalloc", "nb_ctx_set_tuning", "nb_ctx_get_tuning", "nb_server_create",
            "nb_server_destroy", "nb_server_submit", "nb_server_wait", "nb_pme_init", "nb_pme_forces",
-           "nb_ctx_inject_alloc_failures"]
+           "nb_ctx_inject_alloc_failures", "nb_ewald_force_table"]
 NB_NSTAGE = 11
 NB_MOD_LJ_SHIFT = 1
 NB_MOD_EWALD_SHIFT = 2
@@ -117,6 +117,8 @@ def load(path: str | None = None):
         "nb_pme_init": ([_vp, ctypes.POINTER(nb_pme_params)], _st),
         "nb_pme_forces": ([_vp, _vp, _vp, _vp, _vp, ctypes.c_uint], _st),
         "nb_pairlist_export": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong)], _st),
+        "nb_ewald_force_table": ([ctypes.c_double, ctypes.c_double, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_double)], _st),
         "nb_batch_create": ([_vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp)], _st),
         "nb_batch_destroy": ([_vp], _st),
         "nb_sys_set_coords": ([_vp, _vp, _vp], _st),
@@ -280,6 +282,19 @@ def nb_pme_init(sys, grid, order: int = 4) -> None:
 def nb_pme_forces(sys, x_new=None, f=None, energy=None, virial=None, flags: int = 0) -> None:
     """Long-range part alone: energy = (E_rec, E_self, E_excl)."""
     check(load().nb_pme_forces(sys, ptr(x_new), ptr(f), ptr(energy), ptr(virial), flags))
+
+
+def nb_ewald_force_table(beta: float, rc: float):
+    """The force kernel's Ewald table: (float32 [K, 4] coefficients, h)."""
+    import numpy as np
+
+    n = ctypes.c_int()
+    h = ctypes.c_double()
+    check(load().nb_ewald_force_table(float(beta), float(rc), None, 0, ctypes.byref(n), ctypes.byref(h)))
+    coef = np.zeros((n.value, 4), dtype=np.float32)
+    check(load().nb_ewald_force_table(float(beta), float(rc), coef.ctypes.data_as(_vp), n.value, ctypes.byref(n),
+                                      ctypes.byref(h)))
+    return coef, h.value
 
 
 def nb_pairlist_export(sys, perm=None, items=None, cj=None, mask=None) -> int:

@@ -1,30 +1,28 @@
-"""Pins of the erfc and 2^f fits that the Ewald kernels evaluate.
+"""Pins of the erfc and 2^f fits that the Ewald energy kernel evaluates.
 
-The kernels take erfc(x) = exp(-x^2) R(u), t = 1 / (1 + P x), u = UA t + UB,
-with R a least-squares polynomial fitted by csrc/fit_erfc.py, and (energy
-kernel) 2^f on [-0.5, 0.5] as a fitted polynomial.  These tests read the
+The energy kernel takes erfc(x) = exp(-x^2) R(u), t = 1 / (1 + P x),
+u = UA t + UB, with R a least-squares polynomial fitted by csrc/fit_erfc.py,
+and 2^f on [-0.5, 0.5] as a fitted polynomial.  These tests read the
 coefficients exactly as csrc/erfc_fit.cuh stores them and check them against
-the standard library's erfc and 2^f (math.erfc, math.exp, math.ldexp; not
-scipy, which the fitter used):
+the standard library's erfc and 2^f (math.erfc, math.exp; not scipy, which
+the fitter used):
 
   * the fits with the stored coefficients, evaluated exactly in float64,
     meet the errors the header states;
-  * the force kernel's float32 evaluation (float32 Horner with fused
-    multiply-adds, exp(-x^2) = 2^(-x^2 log2 e)) stays within a few float32
-    roundings of erfc;
-  * the energy kernel's double-float evaluation (error-free two-sum and
-    two-product steps, compensated Horner for the head terms, exact range
-    reduction of 2^a) reaches erfc to 1e-9 relative (the fit's 4.4e-11 plus
-    the float32 tail terms of its two polynomials).
+  * the kernel's double-float evaluation (error-free two-sum and two-product
+    steps, compensated Horner for the head terms, exact range reduction of
+    2^a) reaches erfc to 1e-9 relative (the fit's 4.4e-11 plus the float32
+    tail terms of its two polynomials).
 
 The float32 arithmetic is emulated with numpy: a product of two float32
 values is exact in float64, so a fused multiply-add is formed in float64 and
 rounded once more to float32 (a double rounding that can move a result by
 one float32 ulp in rare cases; the bounds below leave room for it).  The
-SFU reciprocal and 2^x are replaced by correctly rounded values; the energy
-kernel refines its reciprocal by a residual step and uses no SFU 2^x, so its
-emulation is faithful.  These pins need no GPU; the same quantities are
-checked on the device through the library in tests/test_gpu_parity.py.
+kernel refines its SFU reciprocal by a residual step and uses no SFU 2^x, so
+the emulation is faithful.  The force kernel uses no erfc fit: its table of
+the force factor is pinned in tests/test_ewald_table_cpu.py.  These pins need
+no GPU; the same quantities are checked on the device through the library in
+tests/test_gpu_parity.py.
 """
 import math
 import os
@@ -49,7 +47,7 @@ def _header():
         return np.array([float(v.strip().rstrip("f")) for v in body.split(",")], dtype=np.float32)
 
     h = {n: scal(n) for n in ("EF_P", "EF_XMAX", "EF_UA", "EF_UB")}
-    for n in ("EF_FORCE", "EF_EN_HI", "EF_EN_LO", "EX2_HI", "EX2_LO"):
+    for n in ("EF_EN_HI", "EF_EN_LO", "EX2_HI", "EX2_LO"):
         h[n] = arr(n)
     h["stated"] = [float(v) for v in re.findall(r"\(([0-9.e+-]+) with the", src)]
     return h
@@ -84,22 +82,15 @@ X = np.linspace(0.0, float(H["EF_XMAX"]), 6001)
 # ------------------------------------------------------- the stored fits
 
 
-def test_header_states_the_stored_coefficients_errors():
-    assert len(H["stated"]) == 2  # force, energy
-
-
-def test_force_fit_with_stored_coefficients():
-    r = _horner64(H["EF_FORCE"].astype(np.float64), _mapping64(X))
-    err = np.abs(r / erfcx_ref(X) - 1.0).max()
-    assert err <= 1.05 * H["stated"][0], err
-    assert err < 2e-7  # a few float32 ulps: far below the force tolerance 1e-5
+def test_header_states_the_stored_coefficients_error():
+    assert len(H["stated"]) == 1  # energy
 
 
 def test_energy_fit_with_stored_coefficients():
     c = H["EF_EN_HI"].astype(np.float64) + H["EF_EN_LO"].astype(np.float64)
     r = _horner64(c, _mapping64(X))
     err = np.abs(r / erfcx_ref(X) - 1.0).max()
-    assert err <= 1.05 * H["stated"][1], err
+    assert err <= 1.05 * H["stated"][0], err
     assert err < 5e-11
 
 
@@ -111,10 +102,9 @@ def test_exp2_fit_with_stored_coefficients():
     assert err < 2e-15, err
 
 
-def test_fits_reduce_to_erfc_at_zero():
-    # erfc(0) = 1: R(u(0)) = 1 for both fits
+def test_fit_reduces_to_erfc_at_zero():
+    # erfc(0) = 1: R(u(0)) = 1
     u0 = _mapping64(np.array([0.0]))
-    assert abs(_horner64(H["EF_FORCE"].astype(np.float64), u0)[0] - 1.0) < 2e-7
     c = H["EF_EN_HI"].astype(np.float64) + H["EF_EN_LO"].astype(np.float64)
     assert abs(_horner64(c, u0)[0] - 1.0) < 5e-11
 
@@ -141,22 +131,6 @@ def two_prod(a, b):
 def split(v):
     hi = f32(v)
     return hi, f32(np.float64(v) - np.float64(hi))
-
-
-def erfc_force32(x):
-    """The force kernel's erfc: R(u) by float32 Horner, times 2^(-x^2 log2 e)."""
-    xc = np.minimum(f32(x), H["EF_XMAX"])
-    t = f32(1.0) / fma32(H["EF_P"], xc, f32(1.0))
-    u = fma32(H["EF_UA"], t, H["EF_UB"])
-    c = H["EF_FORCE"]
-    r = np.full_like(u, c[-1])
-    for k in range(len(c) - 2, -1, -1):
-        r = fma32(r, u, c[k])
-    # the kernel takes exp(-x^2) from the squared distance and the splitting
-    # parameter; here x^2 directly
-    a = f32(f32(f32(x) * f32(x)) * f32(-1.4426950408889634))
-    ex = f32(np.exp2(a.astype(np.float64)))
-    return f32(r * ex)
 
 
 def _horner_dd(hi, lo, k1, uh, ul, ph, pl):
@@ -206,22 +180,6 @@ def erfc_energy_dd(xh, xl, ah, al):
     ch, ce = two_prod(ph, qh)
     cl = f32(ce + fma32(ph, ql, f32(pl * qh)))
     return f32(ch * scale), f32(cl * scale)
-
-
-def test_force_kernel_float32_erfc():
-    x = X.astype(np.float32)
-    got = erfc_force32(x).astype(np.float64)
-    ref = erfc_ref(x.astype(np.float64))
-    err = np.abs(got / ref - 1.0)
-    # the fit (1.3e-7) and about ten float32 roundings of R (each 2^-24
-    # relative), plus the argument of the exponential: a = -x^2 log2(e) is
-    # formed with three roundings (x^2, the product, the float32 constant),
-    # an absolute error of up to 3 * 2^-24 |a| in a and so a relative error of
-    # 3 * 2^-24 |a| ln 2 = 3 * 2^-24 x^2 in 2^a.  At x = 6 (erfc = 2e-17) that
-    # is 6e-6 of a value that no longer matters next to the 1/r it multiplies.
-    bound = 1.4e-7 + 10 * 2.0**-24 + 3 * 2.0**-24 * x.astype(np.float64) ** 2
-    assert (err <= bound).all(), (err / bound).max()
-    assert err[x <= 2.0].max() < 8e-7, err[x <= 2.0].max()
 
 
 @pytest.mark.parametrize("lo,hi", [(0.0, 0.5), (0.5, 3.2), (3.2, 6.0)])
