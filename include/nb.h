@@ -319,14 +319,16 @@ nb_status nb_eval_info(nb_sys *sys, nb_eval_stats *stats);
 
 /*
  * Test hook: copy the current list to host memory.  Any output pointer may
- * be NULL.  Sizes come from nb_pairlist_info.
+ * be NULL.  Sizes come from nb_pairlist_info, except that of the entry
+ * arrays: a call with cj = mask = NULL returns it in n_entries_total.
  *   perm        n_clusters * 8 ints: original atom index of each sorted slot,
  *               -1 for fillers
  *   items       n_items * 4 ints: (i-cluster, first entry, end entry, shift)
  *               where shift = (sx+1)*9 + (sy+1)*3 + (sz+1), the i-cluster
  *               being displaced by (sx Lx, sy Ly, sz Lz)
  *   cj          n_entries_total ints, j-cluster of each entry (indices up to
- *               the largest item end)
+ *               the largest item end; entries outside every item's range
+ *               are gaps and hold no list data)
  *   mask        n_entries_total unsigned long long: bit 8*i + t set means the
  *               pair (i-slot i, j-slot t XOR i) may interact
  *   n_entries_total  receives the size of the entry arrays

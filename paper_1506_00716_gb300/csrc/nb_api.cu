@@ -114,7 +114,11 @@ void list_estimate(const nb_params& p, int natoms, const double box[3], int clca
     double per_cl = steiner * rho / CL / 2.0;
     double shift = 1.0;
     for (int d = 0; d < 3; ++d) shift *= 1.0 + 2.0 * std::min(1.0, (r + ext) / box[d]);
-    *entries = (long long)(clcap * (per_cl * 1.35 + 8.0) * std::max(1.0, shift / 4.0)) + 4096;
+    // the thread-per-cluster search gives every cluster a slab as large as
+    // the largest cluster's count: up to the whole neighbourhood (twice the
+    // half-list average) for the clusters whose periodic neighbours all
+    // have higher indices
+    *entries = (long long)(clcap * (per_cl * 2.6 + 16.0) * std::max(1.0, shift / 4.0)) + 4096;
     // one item per (cluster, shift) run, plus the splits of runs longer than
     // max_entries
     *items = (long long)(clcap * std::min(27.0, shift * 1.25)) + *entries / std::max(1, max_entries) + 256;
@@ -707,7 +711,7 @@ nb_status plan_build_list(Plan* pl) {
         int ov = pl->h_counters[CNT_OVERFLOW];
         if (ov & 3) {
             long long ni = std::max<long long>(pl->h_counters[CNT_ITEMS], pl->item_cap);
-            long long ne = std::max<long long>(pl->h_counters[CNT_ENTRIES], pl->entry_cap);
+            long long ne = std::max<long long>(entries_needed(pl->h_counters, pl->tot_clcap), pl->entry_cap);
             NB_CK(cudaMemsetAsync(pl->list.counters + CNT_OVERFLOW, 0, 4, st));
             nb_status s = plan_alloc_list(pl, ni + ni / 4 + 256, ne + ne / 4 + 4096);
             if (s != NB_OK) return s;
@@ -1299,10 +1303,19 @@ nb_status nb_pairlist_export(nb_sys* sys, int* perm, int* items, int* cj, unsign
     if (s != NB_OK) return s;
     Plan* pl = sys->plan;
     cudaStream_t st = sys->ctx->stream;
-    long long ne = std::min<long long>(info.n_entries_raw, pl->entry_cap);
+    // the entry arrays reach the largest item end (the thread-per-cluster
+    // search leaves gaps between the clusters' slabs)
+    const long long n_items = std::min<long long>(info.n_items, pl->item_cap);
+    std::vector<int4> it((size_t)std::max<long long>(n_items, 1));
+    if (n_items > 0)
+        NB_CK(cudaMemcpyAsync(it.data(), pl->list.items, 16 * (size_t)n_items, cudaMemcpyDeviceToHost, st));
+    NB_CK(cudaStreamSynchronize(st));
+    long long ne = 0;
+    for (long long k = 0; k < n_items; ++k) ne = std::max<long long>(ne, it[k].z);
+    ne = std::min<long long>(ne, pl->entry_cap);
     if (n_entries_total) *n_entries_total = ne;
     if (perm) NB_CK(cudaMemcpyAsync(perm, sys->h.perm, 4 * (size_t)info.n_clusters * CL, cudaMemcpyDefault, st));
-    if (items) NB_CK(cudaMemcpyAsync(items, pl->list.items, 16 * (size_t)info.n_items, cudaMemcpyDefault, st));
+    if (items && n_items > 0) std::memcpy(items, it.data(), 16 * (size_t)n_items);
     if (cj) NB_CK(cudaMemcpyAsync(cj, pl->list.cj, 4 * (size_t)ne, cudaMemcpyDefault, st));
     if (mask) NB_CK(cudaMemcpyAsync(mask, pl->list.mask, 8 * (size_t)ne, cudaMemcpyDefault, st));
     NB_CK(cudaStreamSynchronize(st));
@@ -1486,7 +1499,7 @@ nb_status nb_batch_poll(nb_batch* batch, unsigned long long ticket, long long ti
     int ov = pl->h_counters[CNT_OVERFLOW];
     if (ov & 3) {
         long long ni = std::max<long long>(pl->h_counters[CNT_ITEMS], pl->item_cap);
-        long long ne = std::max<long long>(pl->h_counters[CNT_ENTRIES], pl->entry_cap);
+        long long ne = std::max<long long>(entries_needed(pl->h_counters, pl->tot_clcap), pl->entry_cap);
         nb_status s = plan_alloc_list(pl, ni + ni / 4 + 256, ne + ne / 4 + 4096);
         if (s != NB_OK) return s;
         NB_CK(cudaStreamSynchronize(batch->ctx->stream));

@@ -31,8 +31,27 @@ enum {
     CNT_EWORK = 5,      // energy-kernel work counter
     CNT_ORD_LONG = 6,   // non-empty items the prune ordered first (long ones)
     CNT_ORD_SHORT = 7,  // non-empty items the prune ordered last (short ones)
-    CNT_N = 8
+    CNT_NEED = 8,       // thread-per-cluster search: most entries of one cluster
+    CNT_N = 9
 };
+
+// Entries per cluster slab of the thread-per-cluster search: the list's
+// entry capacity spread over the clusters, a multiple of 8.
+__host__ __device__ inline int slab_stride(long long entry_cap, long long tot_clcap) {
+    if (tot_clcap <= 0) return 0;
+    long long s = entry_cap / tot_clcap;
+    if (s > (1 << 24)) s = 1 << 24;
+    return (int)(s & ~7ll);
+}
+
+// The entry capacity a search's counters ask for: the entries written, and
+// (thread-per-cluster search) a slab as large as the largest cluster's
+// count for every cluster.
+inline long long entries_needed(const int* counters, long long tot_clcap) {
+    const long long slab = ((long long)counters[CNT_NEED] + 7) & ~7ll;
+    const long long a = counters[CNT_ENTRIES], b = slab * tot_clcap;
+    return a > b ? a : b;
+}
 
 // Per-system device descriptor.  Every pointer is a device pointer owned by
 // the system (nb_sys).  "slot" arrays have clcap * CL elements in the sorted
@@ -55,8 +74,7 @@ struct SysDev {
     int* col_cl0;        // [ncol + 1] first cluster of each column; [ncol] = #clusters
     int* atom_col;       // [natoms]
     int* atom_slot;      // [natoms] arrival slot inside the column (pre-sort)
-    unsigned long long* keys;  // [slots] (z key << 32 | atom) in column order; after the
-                               // grid put, scratch of the thread-per-cluster search
+    unsigned long long* keys;  // [slots] (z key << 32 | atom) in column order
     float4* xq_s;        // [slots] sorted x y z q (fillers: far away, q = 0)
     int* type_s;         // [slots]
     int* perm;           // [slots] original atom of each slot, -1 = filler

@@ -377,208 +377,50 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
 
 // ------------------------------------------- search, one thread per cluster
 //
-// For systems with many clusters the search takes one thread per i-cluster.
-// It tests the same candidates with the same rule as k_search, but a thread
-// walks its cluster's images, columns and z-windows on its own, with no
-// coordination between lanes, and writes into a range of the list reserved
-// for its cluster, with no atomics.  Three launches:
-//   k_tsearch<false>  count, per cluster, the entries that pass the box test
-//                     and the work items they make (one per run of equal
-//                     shift, split into pieces of at most max_entries);
-//                     exclusive scan of both over the block
-//   k_tsearch_scan    exclusive scan of the block totals (one block), the
-//                     list's entry and item counts, capacity check
-//   k_tsearch<true>   the same walk again, writing each entry (mask, and
-//                     the PRUNE_CHECK mark of entries whose boxes are not
-//                     clearly inside the radius) and each item at the
-//                     cluster's offsets; the prune follows as for k_search.
-// The per-cluster offsets live in the grid put's sort-key buffer, which is
-// not used again until the next grid put: cluster c's first key slot holds
-// its (entries, items) offsets packed into 64 bits, and the second slot of a
-// block's first cluster holds the block's totals, then its offsets.
+// For systems with many clusters the search takes one thread per i-cluster,
+// in one pass.  It tests the same candidates with the same rule as
+// k_search, but a thread walks its cluster's images, columns and z-windows
+// on its own, with no coordination between lanes, and writes the entries
+// into a slab of `ce` entries reserved for its cluster (cluster gc's
+// entries at gc * ce; ce is a multiple of 8).  The work items reference
+// ranges of those slabs, so the slabs need no compaction: the gaps between
+// clusters are never read.  Entries are collected four at a time and
+// written as one 16-byte (cluster indices) and one 32-byte (masks) store.
+// The threads of a warp walk the 27 images in step; after each image the
+// warp reserves the items of its runs with one atomic add and writes them.
+// A cluster with more than ce entries sets the entries' overflow bit and
+// reports its count (CNT_NEED, the maximum over clusters); its items are
+// clipped to its slab.
 constexpr int TS_BLOCK = 128;
-constexpr int TS_EXK = 16;  // exclusion partners of a cluster kept in registers
+constexpr int TS_XS = 16;  // exclusion partner clusters of an i-cluster kept in shared memory
 
-__device__ __forceinline__ unsigned long long* ts_slot(const SysDev& d, int c, int k) {
-    return d.keys + (size_t)c * CL + k;
+__device__ __forceinline__ void ts_store4(const ListDev& list, long long at, const int (&c)[4],
+                                          const unsigned long long (&m)[4]) {
+    *reinterpret_cast<int4*>(list.cj + at) = make_int4(c[0], c[1], c[2], c[3]);
+    ulonglong4_32a v;
+    v.x = m[0];
+    v.y = m[1];
+    v.z = m[2];
+    v.w = m[3];
+    *reinterpret_cast<ulonglong4_32a*>(list.mask + at) = v;
 }
 
-// Walk one i-cluster's candidates.  Counting: returns the entry and item
-// counts.  Writing: writes the entries from base_e and the items from
-// base_i.
-template <bool WRITE>
-__device__ void ts_cluster(const SysDev& d, int sid, int ci, int max_entries, const ListDev& list,
-                           const unsigned long long* s_colmask, unsigned long long s_diag, int base_e, int base_i,
-                           int& n_e, int& n_i) {
-    const float4 lo_i = d.bb[2 * ci];
-    const float4 hi_i = d.bb[2 * ci + 1];
-    const int nri = (int)lo_i.w;
-    const unsigned long long rmask_i = row_mask(nri);
-    const float rl = d.rl_search;
-    const float rl2 = rl * rl;
-    const float izl = 1.f / d.L[2];
-    const float rbb = fmaxf(0.f, rl - PRUNE_SURE_MARGIN);
-    const float rbb2 = rbb * rbb;
-    const float eps = 1e-5f * fmaxf(1.f, fmaxf(d.L[0], fmaxf(d.L[1], d.L[2])));
-
-    // exclusion partners (sorted slot << 3 | i-slot) of the cluster's atoms
-    int exs[TS_EXK];
-    int n_ex = 0;
-    unsigned long long xfilter = 0;
-    if (WRITE && d.excl_index != nullptr) {
-        for (int ii = 0; ii < nri; ++ii) {
-            const int a = d.perm[ci * CL + ii];
-            for (int e = d.excl_index[a]; e < d.excl_index[a + 1]; ++e) {
-                const int p = d.iperm[d.excl_atoms[e]];
-                xfilter |= 1ull << ((p >> 3) & 63);
-                if (n_ex < TS_EXK) exs[n_ex] = (p << 3) | ii;
-                ++n_ex;
-            }
-        }
-    }
-
-    int w_e = 0, w_i = 0;
-    // images of the i-cluster (as in k_search; z first)
-    const float rle2 = (rl + eps) * (rl + eps);
-    for (int sz = -1; sz <= 1; ++sz) {
-        const float Sz = sz * d.L[2];
-        const float lz = lo_i.z + Sz, hz = hi_i.z + Sz;
-        const float gz = gap(lz, hz, 0.f, d.L[2]);
-        if (gz * gz >= rle2) continue;
-        for (int sy = -1; sy <= 1; ++sy) {
-            const float Sy = fmaf((float)sz, d.T[2], sy * d.L[1]);
-            const float ly = lo_i.y + Sy, hy = hi_i.y + Sy;
-            const float gy = gap(ly, hy, 0.f, d.L[1]);
-            if (gy * gy + gz * gz >= rle2) continue;
-            for (int sx = -1; sx <= 1; ++sx) {
-                const float Sx = fmaf((float)sz, d.T[1], fmaf((float)sy, d.T[0], sx * d.L[0]));
-                const float lx = lo_i.x + Sx, hx = hi_i.x + Sx;
-                const float gx = gap(lx, hx, 0.f, d.L[0]);
-                if (gx * gx + gy * gy + gz * gz >= rle2) continue;
-                const int shift = shift_index(sx, sy, sz);
-                const int cx0 = max(0, (int)floorf((lx - rl) * d.icw[0]) - 1);
-                const int cx1 = min(d.ncx - 1, (int)floorf((hx + rl) * d.icw[0]) + 1);
-                const int cy0 = max(0, (int)floorf((ly - rl) * d.icw[1]) - 1);
-                const int cy1 = min(d.ncy - 1, (int)floorf((hy + rl) * d.icw[1]) + 1);
-                const float zmin = lz - rl, zmax = hz + rl;
-                const int run0 = w_e;
-                for (int cx = cx0; cx <= cx1; ++cx) {
-                    const float fx0 = cx * d.cw[0] - eps, fx1 = (cx + 1) * d.cw[0] + eps;
-                    const float gcx = gap(lx, hx, fx0, fx1);
-                    if (gcx * gcx >= rl2) continue;
-                    for (int cy = cy0; cy <= cy1; ++cy) {
-                        const float fy0 = cy * d.cw[1] - eps, fy1 = (cy + 1) * d.cw[1] + eps;
-                        const float gcy = gap(ly, hy, fy0, fy1);
-                        if (gcx * gcx + gcy * gcy >= rl2) continue;
-                        const int col = cx * d.ncy + cy;
-                        const int a0 = d.col_cl0[col], b0 = d.col_cl0[col + 1];
-                        // the half list keeps cur > ci (cur == ci only for the zero
-                        // and "positive" shifts): columns numbered wholly below ci
-                        // hold no candidate
-                        const int lo_c = shift >= SHIFT_ZERO ? ci : ci + 1;
-                        if (b0 <= lo_c) continue;
-                        const float cl_per_z = (float)(b0 - a0) * izl;
-                        const int a = max(lo_c, window_bound<true>(d.bb, a0, b0, zmin, a0 + (int)(zmin * cl_per_z)));
-                        const int u = window_bound<false>(d.bb, a0, b0, zmax, a0 + (int)(zmax * cl_per_z));
-                        // each candidate's box is loaded one step ahead
-                        float4 ln = make_float4(0.f, 0.f, 0.f, 0.f), hn = ln;
-                        if (a < u) {
-                            ln = d.bb[2 * a];
-                            hn = d.bb[2 * a + 1];
-                        }
-                        for (int cur = a; cur < u; ++cur) {
-                            const float4 lj = ln;
-                            const float4 hj = hn;
-                            if (cur + 1 < u) {
-                                ln = d.bb[2 * cur + 2];
-                                hn = d.bb[2 * cur + 3];
-                            }
-                            const float gjx = gap(lx, hx, lj.x, hj.x);
-                            const float gjy = gap(ly, hy, lj.y, hj.y);
-                            const float gjz = gap(lz, hz, lj.z, hj.z);
-                            const float g2 = gjx * gjx + gjy * gjy + gjz * gjz;
-                            if (!(g2 < rl2)) continue;
-                            if (WRITE) {
-                                unsigned long long m = (cur == ci && shift == SHIFT_ZERO) ? s_diag : ~0ull;
-                                m &= rmask_i & s_colmask[(int)lj.w];
-                                if ((xfilter >> (cur & 63)) & 1ull) {
-                                    if (n_ex <= TS_EXK) {
-                                        for (int q = 0; q < n_ex; ++q) {
-                                            const int p = exs[q] >> 3;
-                                            if ((p >> 3) == cur) m &= ~(1ull << rot_bit(exs[q] & 7, p & 7));
-                                        }
-                                    } else {
-                                        for (int ii = 0; ii < nri; ++ii) {
-                                            const int aa = d.perm[ci * CL + ii];
-                                            for (int e = d.excl_index[aa]; e < d.excl_index[aa + 1]; ++e) {
-                                                const int p = d.iperm[d.excl_atoms[e]];
-                                                if ((p >> 3) == cur) m &= ~(1ull << rot_bit(ii, p & 7));
-                                            }
-                                        }
-                                    }
-                                }
-                                list.cj[base_e + w_e] = g2 < rbb2 ? cur : (cur | PRUNE_CHECK);
-                                list.mask[base_e + w_e] = m;
-                            }
-                            ++w_e;
-                        }
-                    }
-                }
-                // the run of this shift as items of at most max_entries entries
-                const int len = w_e - run0;
-                if (len > 0) {
-                    if (WRITE) {
-                        const int w = (sid << 5) | shift;
-                        for (int x = 0; x < len; x += max_entries) {
-                            const int y = min(len, x + max_entries);
-                            list.items[base_i + w_i] = make_int4(ci, base_e + run0 + x, base_e + run0 + y, w);
-                            ++w_i;
-                        }
-                    } else {
-                        w_i += (len + max_entries - 1) / max_entries;
-                    }
-                }
-            }
-        }
-    }
-    n_e = w_e;
-    n_i = w_i;
-}
-
-// Exclusive scan of packed (entries << 32 | items) counts over a block of
-// TS_BLOCK threads; returns the thread's offset and sets *total.
-__device__ __forceinline__ unsigned long long ts_block_scan(unsigned long long v, unsigned long long* s_warp,
-                                                            unsigned long long* total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned long long incl = v;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const unsigned long long t = __shfl_up_sync(FULL, incl, off);
-        if (lane >= off) incl += t;
-    }
-    if (lane == 31) s_warp[w] = incl;
-    __syncthreads();
-    unsigned long long before = 0, all = 0;
-    for (int k = 0; k < TS_BLOCK / 32; ++k) {
-        if (k < w) before += s_warp[k];
-        all += s_warp[k];
-    }
-    *total = all;
-    return before + incl - v;
-}
-
-template <bool WRITE>
 __global__ void __launch_bounds__(TS_BLOCK)
-k_tsearch(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys, int tot_clcap, ListDev list,
-          KParams kp) {
+k_tsearch(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys, int tot_clcap, int ce,
+          ListDev list, KParams kp) {
     pdl_wait();
     pdl_trigger();
     __shared__ unsigned long long s_colmask[CL + 1];
     __shared__ unsigned long long s_diag;
-    __shared__ unsigned long long s_warp[TS_BLOCK / 32];
+    __shared__ unsigned long long s_xm[TS_XS][TS_BLOCK];
+    __shared__ int s_xc[TS_XS][TS_BLOCK];
     if (threadIdx.x <= CL) s_colmask[threadIdx.x] = col_mask(threadIdx.x);
     if (threadIdx.x == 32) s_diag = diag_mask();
     __syncthreads();
+    const int lane = threadIdx.x & 31;
+    // a warp whose clusters all lie past the end leaves as a whole (the warp
+    // collectives below need every lane)
+    if (blockIdx.x * TS_BLOCK + (threadIdx.x & ~31) >= tot_clcap) return;
     const int gc = blockIdx.x * TS_BLOCK + threadIdx.x;
     int sid = 0, ci = 0;
     bool real = false;
@@ -588,103 +430,202 @@ k_tsearch(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int ns
         real = ci < sys[sid].col_cl0[sys[sid].ncol];
     }
     const SysDev& d = sys[sid];
-    if (!WRITE) {
-        int n_e = 0, n_i = 0;
-        if (real) ts_cluster<false>(d, sid, ci, kp.max_entries, list, s_colmask, s_diag, 0, 0, n_e, n_i);
-        unsigned long long total = 0;
-        const unsigned long long off =
-            ts_block_scan(((unsigned long long)n_e << 32) | (unsigned)n_i, s_warp, &total);
-        if (gc < tot_clcap) *ts_slot(d, ci, 0) = off;
-        if (threadIdx.x == 0) *ts_slot(d, ci, 1) = total;  // the block's first cluster
-        return;
+    const int max_entries = kp.max_entries;
+    float4 lo_i = make_float4(0.f, 0.f, 0.f, 0.f), hi_i = lo_i;
+    if (real) {
+        lo_i = d.bb[2 * ci];
+        hi_i = d.bb[2 * ci + 1];
     }
-    if (gc >= tot_clcap) return;
-    // offsets: the block's (in its first cluster) plus the cluster's own
-    const int g0 = blockIdx.x * TS_BLOCK;
-    const int s0 = find_sys(cl_off, nsys, g0);
-    const unsigned long long boff = *ts_slot(sys[s0], g0 - cl_off[s0], 1);
-    const unsigned long long off = boff + *ts_slot(d, ci, 0);
-    const int base_e = (int)(off >> 32), base_i = (int)(off & 0xffffffffull);
-    if (list.counters[CNT_OVERFLOW] & 3) {
-        // the list does not fit: write empty items into the reserved item
-        // slots below the capacity, so that no kernel reads stale items
-        if (!real) return;
-        int n_e = 0, n_i = 0;
-        ts_cluster<false>(d, sid, ci, kp.max_entries, list, s_colmask, s_diag, 0, 0, n_e, n_i);
-        for (int k = 0; k < n_i && base_i + k < list.item_cap; ++k)
-            list.items[base_i + k] = make_int4(ci, 0, 0, (sid << 5) | SHIFT_ZERO);
-        return;
-    }
-    if (!real) return;
-    int n_e = 0, n_i = 0;
-    ts_cluster<true>(d, sid, ci, kp.max_entries, list, s_colmask, s_diag, base_e, base_i, n_e, n_i);
-}
+    const int nri = (int)lo_i.w;
+    const unsigned long long rmask_i = row_mask(nri);
+    const float rl = d.rl_search;
+    const float rl2 = rl * rl;
+    const float izl = 1.f / d.L[2];
+    const float rbb = fmaxf(0.f, rl - PRUNE_SURE_MARGIN);
+    const float rbb2 = rbb * rbb;
+    const float eps = 1e-5f * fmaxf(1.f, fmaxf(d.L[0], fmaxf(d.L[1], d.L[2])));
 
-// One block: exclusive scan of the block totals of k_tsearch<false>, in
-// place; the list's entry and item counts; overflow bits if they exceed the
-// capacities (the write pass then writes no entries).
-__global__ void __launch_bounds__(1024)
-k_tsearch_scan(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsys, int tot_clcap,
-               ListDev list) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ unsigned long long s_warp[32];
-    __shared__ unsigned long long s_carry;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nblk = (tot_clcap + TS_BLOCK - 1) / TS_BLOCK;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (int base = 0; base < nblk; base += 1024) {
-        const int b = base + threadIdx.x;
-        unsigned long long v = 0;
-        unsigned long long* slot = nullptr;
-        if (b < nblk) {
-            const int g0 = b * TS_BLOCK;
-            const int s0 = find_sys(cl_off, nsys, g0);
-            slot = ts_slot(sys[s0], g0 - cl_off[s0], 1);
-            v = *slot;
+    // the clusters holding exclusion partners of the cluster's atoms, each
+    // with the mask bits of its excluded pairs, in shared memory (TS_XS per
+    // thread); a 64-bit filter (bit c mod 64 of every partner cluster c)
+    // sends only the candidates that may be partners to the table.  More
+    // partner clusters than the table holds take the slow path through the
+    // exclusion lists for the candidates that hit the filter.
+    int n_xc = 0;
+    unsigned long long x_filter = 0ull;
+    bool x_slow = false;
+    if (real && d.excl_index != nullptr) {
+        for (int ii = 0; ii < nri; ++ii) {
+            const int a = d.perm[ci * CL + ii];
+            for (int e = d.excl_index[a]; e < d.excl_index[a + 1]; ++e) {
+                const int p = d.iperm[d.excl_atoms[e]];
+                const int c = p >> 3;
+                const unsigned long long bit = 1ull << rot_bit(ii, p & 7);
+                x_filter |= 1ull << (c & 63);
+                int k = 0;
+                while (k < n_xc && s_xc[k][threadIdx.x] != c) ++k;
+                if (k < n_xc) {
+                    s_xm[k][threadIdx.x] |= bit;
+                } else if (n_xc < TS_XS) {
+                    s_xc[n_xc][threadIdx.x] = c;
+                    s_xm[n_xc][threadIdx.x] = bit;
+                    ++n_xc;
+                } else {
+                    x_slow = true;
+                }
+            }
         }
-        unsigned long long incl = v;
+    }
+
+    const long long ebase = (long long)gc * ce;
+    int bc[4] = {0, 0, 0, 0};
+    unsigned long long bm[4] = {0ull, 0ull, 0ull, 0ull};
+    int w_e = 0;
+    const float rle2 = (rl + eps) * (rl + eps);
+    // images of the i-cluster (as in k_search; z first); every lane takes
+    // all 27 steps (one loop, not unrolled: its body is large)
+#pragma unroll 1
+    for (int img = 0; img < NSHIFT; ++img) {
+        const int sz = img / 9 - 1, sy = (img / 3) % 3 - 1, sx = img % 3 - 1;
+        const int run0 = w_e;
+        const int shift = shift_index(sx, sy, sz);
+        const float Sz = sz * d.L[2];
+        const float lz = lo_i.z + Sz, hz = hi_i.z + Sz;
+        const float gz = gap(lz, hz, 0.f, d.L[2]);
+        const float Sy = fmaf((float)sz, d.T[2], sy * d.L[1]);
+        const float ly = lo_i.y + Sy, hy = hi_i.y + Sy;
+        const float gy = gap(ly, hy, 0.f, d.L[1]);
+        const float Sx = fmaf((float)sz, d.T[1], fmaf((float)sy, d.T[0], sx * d.L[0]));
+        const float lx = lo_i.x + Sx, hx = hi_i.x + Sx;
+        const float gx = gap(lx, hx, 0.f, d.L[0]);
+        if (real && gx * gx + gy * gy + gz * gz < rle2) {
+            const int cx0 = max(0, (int)floorf((lx - rl) * d.icw[0]) - 1);
+            const int cx1 = min(d.ncx - 1, (int)floorf((hx + rl) * d.icw[0]) + 1);
+            const int cy0 = max(0, (int)floorf((ly - rl) * d.icw[1]) - 1);
+            const int cy1 = min(d.ncy - 1, (int)floorf((hy + rl) * d.icw[1]) + 1);
+            const float zmin = lz - rl, zmax = hz + rl;
+            // the half list keeps cur > ci (cur == ci only for the
+            // zero and "positive" shifts)
+            const int lo_c = shift >= SHIFT_ZERO ? ci : ci + 1;
+            for (int cx = cx0; cx <= cx1; ++cx) {
+                const float fx0 = cx * d.cw[0] - eps, fx1 = (cx + 1) * d.cw[0] + eps;
+                const float gcx = gap(lx, hx, fx0, fx1);
+                if (gcx * gcx >= rl2) continue;
+                for (int cy = cy0; cy <= cy1; ++cy) {
+                    const float fy0 = cy * d.cw[1] - eps, fy1 = (cy + 1) * d.cw[1] + eps;
+                    const float gcy = gap(ly, hy, fy0, fy1);
+                    if (gcx * gcx + gcy * gcy >= rl2) continue;
+                    const int col = cx * d.ncy + cy;
+                    const int a0 = d.col_cl0[col], b0 = d.col_cl0[col + 1];
+                    // columns numbered wholly below ci hold no candidate
+                    if (b0 <= lo_c) continue;
+                    const float cl_per_z = (float)(b0 - a0) * izl;
+                    const int a =
+                        max(lo_c, window_bound<true>(d.bb, a0, b0, zmin, a0 + (int)(zmin * cl_per_z)));
+                    const int u = window_bound<false>(d.bb, a0, b0, zmax, a0 + (int)(zmax * cl_per_z));
+                    // each candidate's box is loaded one step ahead
+                    float4 ln = make_float4(0.f, 0.f, 0.f, 0.f), hn = ln;
+                    if (a < u) {
+                        ln = d.bb[2 * a];
+                        hn = d.bb[2 * a + 1];
+                    }
+                    for (int cur = a; cur < u; ++cur) {
+                        const float4 lj = ln;
+                        const float4 hj = hn;
+                        if (cur + 1 < u) {
+                            ln = d.bb[2 * cur + 2];
+                            hn = d.bb[2 * cur + 3];
+                        }
+                        const float gjx = gap(lx, hx, lj.x, hj.x);
+                        const float gjy = gap(ly, hy, lj.y, hj.y);
+                        const float gjz = gap(lz, hz, lj.z, hj.z);
+                        const float g2 = gjx * gjx + gjy * gjy + gjz * gjz;
+                        if (!(g2 < rl2)) continue;
+                        unsigned long long m = (cur == ci && shift == SHIFT_ZERO) ? s_diag : ~0ull;
+                        m &= rmask_i & s_colmask[(int)lj.w];
+                        if ((x_filter >> (cur & 63)) & 1ull) {
+                            for (int k = 0; k < n_xc; ++k)
+                                if (s_xc[k][threadIdx.x] == cur) m &= ~s_xm[k][threadIdx.x];
+                        }
+                        if (x_slow && ((x_filter >> (cur & 63)) & 1ull)) {
+                            for (int ii = 0; ii < nri; ++ii) {
+                                const int aa = d.perm[ci * CL + ii];
+                                for (int e = d.excl_index[aa]; e < d.excl_index[aa + 1]; ++e) {
+                                    const int p = d.iperm[d.excl_atoms[e]];
+                                    if ((p >> 3) == cur) m &= ~(1ull << rot_bit(ii, p & 7));
+                                }
+                            }
+                        }
+                        // entries whose boxes are not clearly inside the
+                        // list radius get their atom pairs tested by the prune
+                        const int cv = g2 < rbb2 ? cur : (cur | PRUNE_CHECK);
+                        const int q = w_e & 3;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (k == q) {
+                                bc[k] = cv;
+                                bm[k] = m;
+                            }
+                        ++w_e;
+                        if (q == 3 && w_e <= ce) ts_store4(list, ebase + w_e - 4, bc, bm);
+                    }
+                }
+            }
+        }
+        // the run of this image as items of at most max_entries
+        // entries, clipped to the slab; one reservation per warp
+        const int r0 = min(run0, ce), r1 = min(w_e, ce);
+        const int n_it = r1 > r0 ? (r1 - r0 + max_entries - 1) / max_entries : 0;
+        int incl = n_it;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const unsigned long long t = __shfl_up_sync(FULL, incl, off);
+            const int t = __shfl_up_sync(FULL, incl, off);
             if (lane >= off) incl += t;
         }
-        if (lane == 31) s_warp[w] = incl;
-        __syncthreads();
-        unsigned long long before = s_carry;
-        for (int k = 0; k < w; ++k) before += s_warp[k];
-        if (slot) *slot = before + incl - v;
-        __syncthreads();
-        if (threadIdx.x == 1023) s_carry = before + incl;
-        __syncthreads();
+        const int wtot = __shfl_sync(FULL, incl, 31);
+        if (wtot > 0) {
+            int ib = 0;
+            if (lane == 31) {
+                ib = atomicAdd(list.counters + CNT_ITEMS, wtot);
+                if ((long long)ib + wtot > list.item_cap) atomicOr(list.counters + CNT_OVERFLOW, 1);
+            }
+            ib = __shfl_sync(FULL, ib, 31) + incl - n_it;
+            const int w = (sid << 5) | shift;
+            for (int x = r0; x < r1; x += max_entries, ++ib) {
+                if (ib >= list.item_cap) break;
+                list.items[ib] = make_int4(ci, (int)(ebase + x), (int)(ebase + min(r1, x + max_entries)), w);
+            }
+        }
     }
-    if (threadIdx.x == 0) {
-        const unsigned long long tot = s_carry;
-        const long long n_e = (long long)(tot >> 32), n_i = (long long)(tot & 0xffffffffull);
-        list.counters[CNT_ENTRIES] = (int)min(n_e, (long long)0x7fffffff);
-        list.counters[CNT_ITEMS] = (int)min(n_i, (long long)0x7fffffff);
-        int ov = 0;
-        if (n_i > list.item_cap) ov |= 1;
-        if (n_e > list.entry_cap) ov |= 2;
-        if (ov) atomicOr(list.counters + CNT_OVERFLOW, ov);
+    // the last partial group of four (the slab has room: ce is a multiple of 8)
+    if ((w_e & 3) != 0 && w_e < ce) ts_store4(list, ebase + (w_e & ~3), bc, bm);
+    // the list's entry count, and the largest count of a cluster
+    int tot = w_e;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) tot += __shfl_xor_sync(FULL, tot, off);
+    const int mx = __reduce_max_sync(FULL, (unsigned)w_e);
+    if (lane == 0) {
+        if (tot > 0) atomicAdd(list.counters + CNT_ENTRIES, tot);
+        atomicMax(list.counters + CNT_NEED, mx);
+        if (mx > ce) atomicOr(list.counters + CNT_OVERFLOW, 2);
     }
 }
 
 constexpr int PRUNE_WARPS = 8;
-// checks in flight per lane (16 per round of independent j-atom loads; eight
-// per lane, one round per chunk, needs more registers and ran slower)
-constexpr int PRUNE_U = 4;
+// checks in flight per lane (8 per round of independent j-atom loads).  On
+// the 3M-atom box, 2 at three blocks per SM ran faster than 4 at two blocks
+// (0.98 vs 1.05 ms) and than 4 at three blocks, which spills.
+constexpr int PRUNE_U = 2;
 
 // Prune (Section 3.3): drop the entries of which no atom pair whose mask bit
 // is set lies within the list radius.  A warp takes one work item at a time.
 // Per chunk of 32 entries, lane k loads entry k's j-cluster index and mask
 // (coalesced).  Entries the search marked as certain are kept as they are;
-// the others are tested 16 at a time, lane = 8 g + j holding j-atom j of four
-// of them (four independent coalesced loads in flight) against the eight
-// i-atoms of the item, which every lane keeps in registers.  Kept entries are
-// compacted in place, in order, without the mark; a write never passes the
-// entries still to be read.
+// the others are tested 4 * PRUNE_U at a time, lane = 8 g + j holding j-atom j
+// of PRUNE_U of them (independent coalesced loads in flight) against the
+// eight i-atoms of the item, which every lane keeps in registers.  Kept
+// entries are compacted in place, in order, without the mark; a write never
+// passes the entries still to be read.
 //
 // The same kernel prunes out of place (dst != src, the inner list of
 // nb_pairlist_prune): it then tests every entry against the radius rl2_inner
@@ -714,15 +655,27 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
         const int sh = item.w & 31;
         const float3 S = shift_vec(sh, d.L, d.T);
         const float Sx = S.x, Sy = S.y, Sz = S.z;
-        // the i-atoms in pairs (2k, 2k+1), for the paired float32 arithmetic
-        float2 xi[CL / 2], yi[CL / 2], zi[CL / 2];
+        // Distances relative to c, the shifted i-cluster's first atom: with
+        // a' = a - c for both atoms of a pair (the shift cancels on the i
+        // side), r^2 = |i'|^2 + |j'|^2 - 2 i'.j', so r^2 < rl2 becomes
+        // |i'|^2 - 2 i'.j' < rl2 - |j'|^2: three paired multiply-adds per
+        // two i-atoms.  The primed coordinates stay within a few nm, so the
+        // float32 rounding of the terms (~1e-6 nm^2) lies far inside the
+        // padding of the list radius.  Fillers, 10^6 nm away, stay far.
+        // The i-atoms in pairs (2k, 2k+1): -2 i' and |i'|^2.
+        const float4 c0 = d.xq_s[item.x * CL];
+        float2 ax[CL / 2], ay[CL / 2], az[CL / 2], a2[CL / 2];
 #pragma unroll
         for (int k = 0; k < CL / 2; ++k) {
             const float4 v0 = d.xq_s[item.x * CL + 2 * k], v1 = d.xq_s[item.x * CL + 2 * k + 1];
-            xi[k] = make_float2(v0.x + Sx, v1.x + Sx);
-            yi[k] = make_float2(v0.y + Sy, v1.y + Sy);
-            zi[k] = make_float2(v0.z + Sz, v1.z + Sz);
+            const float x0 = v0.x - c0.x, y0 = v0.y - c0.y, z0 = v0.z - c0.z;
+            const float x1 = v1.x - c0.x, y1 = v1.y - c0.y, z1 = v1.z - c0.z;
+            ax[k] = make_float2(-2.f * x0, -2.f * x1);
+            ay[k] = make_float2(-2.f * y0, -2.f * y1);
+            az[k] = make_float2(-2.f * z0, -2.f * z1);
+            a2[k] = make_float2(fmaf(x0, x0, fmaf(y0, y0, z0 * z0)), fmaf(x1, x1, fmaf(y1, y1, z1 * z1)));
         }
+        const float cx = c0.x + Sx, cy = c0.y + Sy, cz = c0.z + Sz;
         int write = item.y;
         // each chunk's entries are loaded while the previous chunk is tested
         int c_next = 0;
@@ -751,48 +704,56 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
             const int nchk = __popc(chk_bal);
             if (chk) s_rank[w][__popc(chk_bal & ((1u << lane) - 1u))] = (unsigned char)lane;
             __syncwarp();
+            // bit k of a lane's word: checked entry base + k has an unmasked
+            // pair within the radius (any lane of its group may set it)
+            unsigned found = 0u;
             for (int q0 = 0; q0 < nchk; q0 += 4 * PRUNE_U) {
                 float4 xj[PRUNE_U];
                 unsigned long long mq[PRUNE_U];
+                int rk[PRUNE_U];  // the entry's lane in the chunk, -1 past the checked ones
 #pragma unroll
                 for (int u = 0; u < PRUNE_U; ++u) {
                     const int k = q0 + 4 * u + g;
-                    const int src = k < nchk ? s_rank[w][k] : 0;
-                    const int cjk = __shfl_sync(FULL, cjv, src);
-                    mq[u] = __shfl_sync(FULL, m, src);
-                    xj[u] = k < nchk ? d.xq_s[cjk * CL + jj] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+                    rk[u] = k < nchk ? s_rank[w][k] : -1;
+                    const int cjk = __shfl_sync(FULL, cjv, max(rk[u], 0));
+                    mq[u] = __shfl_sync(FULL, m, max(rk[u], 0));
+                    xj[u] = rk[u] >= 0 ? d.xq_s[cjk * CL + jj] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
 #pragma unroll
                 for (int u = 0; u < PRUNE_U; ++u) {
-                    // bit ii: i-atom ii lies within the list radius of this j-atom
-                    // (two i-atoms per paired instruction)
-                    unsigned nb8 = 0;
-                    const float2 jx = dup2(xj[u].x), jy = dup2(xj[u].y), jz = dup2(xj[u].z);
-#pragma unroll
-                    for (int k = 0; k < CL / 2; ++k) {
-                        const float2 dx = sub2(xi[k], jx), dy = sub2(yi[k], jy), dz = sub2(zi[k], jz);
-                        const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-                        nb8 |= (r2.x < rl2 ? 1u : 0u) << (2 * k);
-                        nb8 |= (r2.y < rl2 ? 1u : 0u) << (2 * k + 1);
-                    }
-                    // the mask column of j-slot jj (bit ii = pair (ii, jj)), only
-                    // when one of the four entries has a partial mask
+                    // j-atom jj of the entry, relative to c
+                    const float jx = xj[u].x - cx, jy = xj[u].y - cy, jz = xj[u].z - cz;
+                    const float t = rl2 - fmaf(jx, jx, fmaf(jy, jy, jz * jz));
+                    const float2 jx2 = dup2(jx), jy2 = dup2(jy), jz2 = dup2(jz);
+                    bool near = false;
                     if (__any_sync(FULL, mq[u] != ~0ull)) {
+                        // one of the four entries has a partial mask: bit ii of
+                        // nb8 is i-atom ii within the radius, masked by the
+                        // entry's column of j-slot jj (bit ii = pair (ii, jj))
+                        unsigned nb8 = 0;
+#pragma unroll
+                        for (int k = 0; k < CL / 2; ++k) {
+                            const float2 q = fma2(ax[k], jx2, fma2(ay[k], jy2, fma2(az[k], jz2, a2[k])));
+                            nb8 |= (q.x < t ? 1u : 0u) << (2 * k);
+                            nb8 |= (q.y < t ? 1u : 0u) << (2 * k + 1);
+                        }
                         const unsigned lo = (unsigned)mq[u], hi = (unsigned)(mq[u] >> 32);
                         unsigned col = 0;
 #pragma unroll
                         for (int ii = 0; ii < CL; ++ii)
                             col |= (((ii < 4 ? lo : hi) >> (8 * (ii & 3) + (ii ^ jj))) & 1u) << ii;
-                        nb8 &= col;
-                    }
-                    const unsigned bal = __ballot_sync(FULL, nb8 != 0u);
+                        near = (nb8 & col) != 0u;
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int k = q0 + 4 * u + q;
-                        if (k < nchk && ((bal >> (8 * q)) & 0xffu) != 0u) keep |= 1u << s_rank[w][k];
+                        for (int k = 0; k < CL / 2; ++k) {
+                            const float2 q = fma2(ax[k], jx2, fma2(ay[k], jy2, fma2(az[k], jz2, a2[k])));
+                            near = near || q.x < t || q.y < t;
+                        }
                     }
+                    if (near && rk[u] >= 0) found |= 1u << rk[u];
                 }
             }
+            keep |= __reduce_or_sync(FULL, found);
             __syncwarp();
             if (lane < n && ((keep >> lane) & 1u)) {
                 const int idx = write + __popc(keep & ((1u << lane) - 1u));
@@ -827,14 +788,8 @@ cudaError_t launch_search(const PlanLaunch& p, cudaStream_t st) {
     if (p.tot_clcap <= 0) return cudaSuccess;
     if (thread_search(p)) {
         const unsigned blocks = (unsigned)((p.tot_clcap + TS_BLOCK - 1) / TS_BLOCK);
-        cudaError_t e = launch_pdl(k_tsearch<false>, blocks, TS_BLOCK, 0, st, p.d_sys, p.d_cl_off, p.nsys,
-                                   p.tot_clcap, p.list, p.kp);
-        if (e == cudaSuccess)
-            e = launch_pdl(k_tsearch_scan, 1u, 1024, 0, st, p.d_sys, p.d_cl_off, p.nsys, p.tot_clcap, p.list);
-        if (e == cudaSuccess)
-            e = launch_pdl(k_tsearch<true>, blocks, TS_BLOCK, 0, st, p.d_sys, p.d_cl_off, p.nsys, p.tot_clcap,
-                           p.list, p.kp);
-        return e;
+        return launch_pdl(k_tsearch, blocks, TS_BLOCK, 0, st, p.d_sys, p.d_cl_off, p.nsys, p.tot_clcap,
+                          slab_stride(p.list.entry_cap, p.tot_clcap), p.list, p.kp);
     }
     unsigned blocks = (unsigned)((p.tot_clcap + SEARCH_WARPS - 1) / SEARCH_WARPS);
     return launch_pdl(k_search, blocks, SEARCH_WARPS * 32, 0, st, p.d_sys, p.d_cl_off, p.nsys, p.tot_clcap, p.list,

@@ -280,7 +280,8 @@ void retire_wave(nb_server* s, int k) {
         // The list outgrew its estimate: the counters hold the sizes the
         // search wanted, so run the wave again with room for them.
         const double need = std::max((double)cnt[CNT_ITEMS] / std::max<long long>(1, w.plan->item_cap),
-                                     (double)cnt[CNT_ENTRIES] / std::max<long long>(1, w.plan->entry_cap));
+                                     (double)entries_needed(cnt, w.plan->tot_clcap) /
+                                         std::max<long long>(1, w.plan->entry_cap));
         const double boost = w.boost * 1.25 * std::max(1.0, need) * (w.attempts == 1 ? 1.0 : 2.0);
         plan_destroy(w.plan);
         w.plan = nullptr;

@@ -29,7 +29,7 @@ def export_list(h):
     info = nb.nb_pairlist_info(h)
     perm = np.zeros(info["n_clusters"] * 8, dtype=np.int32)
     items = np.zeros((max(info["n_items"], 1), 4), dtype=np.int32)
-    ne = info["n_entries_raw"]
+    ne = nb.nb_pairlist_export(h)  # the entry arrays' extent (the largest item end)
     cj = np.zeros(max(ne, 1), dtype=np.int32)
     mask = np.zeros(max(ne, 1), dtype=np.uint64)
     nb.nb_pairlist_export(h, perm, items, cj, mask)
