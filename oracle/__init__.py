@@ -63,6 +63,8 @@ def _load():
               ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, ip, ip, ctypes.c_int]
     lib.or_energy_virial.argtypes = common + [dp, lp]
     lib.or_energy_virial.restype = ctypes.c_int
+    lib.or_energy_virial_rows.argtypes = common + [ctypes.c_int, ctypes.c_int, dp, lp]
+    lib.or_energy_virial_rows.restype = ctypes.c_int
     lib.or_forces.argtypes = common + [ctypes.c_int, ip, dp]
     lib.or_forces.restype = ctypes.c_int
     lib.or_pairs.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ip, ip, lp, ip]
@@ -122,9 +124,34 @@ def energy_virial(sys, params) -> dict:
     if rc != 0:
         raise RuntimeError("oracle energy_virial failed")
     del keep
+    return _ev_dict(out, npairs.value)
+
+
+def energy_virial_rows(sys, params, i0: int, i1: int) -> tuple:
+    """The raw sums of energy_virial over the pairs (i, j), i0 <= i < i1, j > i:
+    (float64 [15] in the C layout, pair count).  Sums over consecutive row
+    ranges covering [0, n) add up to energy_virial's (see ev_from_sums)."""
+    lib = _load()
+    keep, args = _common(sys, params)
+    out = np.zeros(15, dtype=np.float64)
+    npairs = ctypes.c_longlong(0)
+    rc = lib.or_energy_virial_rows(*args, int(i0), int(i1), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   ctypes.byref(npairs))
+    if rc != 0:
+        raise RuntimeError("oracle energy_virial_rows failed")
+    del keep
+    return out, int(npairs.value)
+
+
+def ev_from_sums(out, npairs: int) -> dict:
+    """energy_virial's dictionary from summed raw sums of energy_virial_rows."""
+    return _ev_dict(np.asarray(out, dtype=np.float64), npairs)
+
+
+def _ev_dict(out, npairs: int) -> dict:
     return {"e_lj": out[0], "e_coul": out[1], "virial": out[2:11].reshape(3, 3).copy(),
             "e12": out[11], "e6": out[12], "rdotf_lj": out[13], "rdotf_coul": out[14],
-            "npairs": int(npairs.value)}
+            "npairs": int(npairs)}
 
 
 def forces(sys, params, sel=None) -> np.ndarray:

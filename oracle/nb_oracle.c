@@ -197,17 +197,35 @@ static double excl_rf_terms(const setup_t *s, double r2, double qq, double *v_c)
  * out[13] = sum over pairs of d.F (LJ part), out[14] = the same for Coulomb.
  * npairs[0] = number of interacting pairs.
  */
+int or_energy_virial_rows(int n, const double *x, const double *q, const int *type, const double *box,
+                          double rc, int coul, double eps_r, double eps_rf, double beta, double fcoul,
+                          int ntypes, const double *c6, const double *c12, const int *excl_index,
+                          const int *excl_atoms, int mods, int i0, int i1, double *out, long long *npairs);
+
 int or_energy_virial(int n, const double *x, const double *q, const int *type, const double *box,
                      double rc, int coul, double eps_r, double eps_rf, double beta, double fcoul,
                      int ntypes, const double *c6, const double *c12, const int *excl_index,
                      const int *excl_atoms, int mods, double *out, long long *npairs) {
-    if (n < 0 || !out) return 1;
+    return or_energy_virial_rows(n, x, q, type, box, rc, coul, eps_r, eps_rf, beta, fcoul, ntypes, c6, c12,
+                                 excl_index, excl_atoms, mods, 0, n, out, npairs);
+}
+
+/*
+ * The same sums restricted to the pairs (i, j) with i in [i0, i1), j > i:
+ * the sums over consecutive row ranges add up to those of all pairs (a
+ * long evaluation can be taken in pieces).
+ */
+int or_energy_virial_rows(int n, const double *x, const double *q, const int *type, const double *box,
+                          double rc, int coul, double eps_r, double eps_rf, double beta, double fcoul,
+                          int ntypes, const double *c6, const double *c12, const int *excl_index,
+                          const int *excl_atoms, int mods, int i0, int i1, double *out, long long *npairs) {
+    if (n < 0 || !out || i0 < 0 || i1 > n || i0 > i1) return 1;
     setup_t s = make_setup(rc, coul, eps_r, eps_rf, beta, fcoul, ntypes, c6, c12, mods);
     double elj = 0, ec = 0, e12 = 0, e6 = 0, rf_lj = 0, rf_c = 0;
     double vxx = 0, vxy = 0, vxz = 0, vyy = 0, vyz = 0, vzz = 0;
     long long np = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : elj, ec, e12, e6, rf_lj, rf_c, vxx, vxy, vxz, vyy, vyz, vzz, np)
-    for (int i = 0; i < n; ++i) {
+    for (int i = i0; i < i1; ++i) {
         for (int j = i + 1; j < n; ++j) {
             double dx, dy, dz;
             pair_image(box, x[3 * i + 0] - x[3 * j + 0], x[3 * i + 1] - x[3 * j + 1],

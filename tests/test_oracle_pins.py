@@ -511,3 +511,25 @@ def test_triclinic_translation_newton_and_gradient(coul):
             assert -(ep - em) / (2 * h) == pytest.approx(f0[a, d], rel=2e-6, abs=2e-4)
             checked += 1
     assert checked >= 12
+
+
+def test_energy_virial_row_ranges_add_up_to_all_pairs():
+    """The row-range sums (used to take the 3M-atom golden sums in pieces)
+    cover every pair once: consecutive ranges add up to the full sums."""
+    s = wb.small_box(seed=2)
+    p = wb.params_ewald()
+    full = oracle.energy_virial(s, p)
+    cuts = [0, 1, 100, s.n // 2, s.n - 1, s.n]
+    sums = np.zeros(15)
+    npairs = 0
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        out, k = oracle.energy_virial_rows(s, p, a, b)
+        sums += out
+        npairs += k
+    ev = oracle.ev_from_sums(sums, npairs)
+    assert ev["npairs"] == full["npairs"]
+    for key in ("e_lj", "e_coul", "e12", "e6"):
+        assert abs(ev[key] - full[key]) <= 1e-12 * abs(full[key])
+    assert np.allclose(ev["virial"], full["virial"], rtol=1e-12, atol=1e-9)
+    with pytest.raises(RuntimeError):
+        oracle.energy_virial_rows(s, p, 5, 3)
