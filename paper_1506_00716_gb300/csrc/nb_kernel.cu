@@ -44,11 +44,22 @@ namespace {
 constexpr unsigned FULL = FULL_MASK;
 constexpr int FW = 8;  // warps per block of the force kernel
 
-// The Ewald force table in shared memory (KParams::gtab).
+// The Ewald force table in shared memory (KParams::gtab), in R copies:
+// entry k of copy c at k R + c, lane l reading copy l mod R.  A 16-byte
+// load is served a quarter warp (eight lanes) at a time, so with R = 8 the
+// eight lanes read eight different bank quads wherever their entries lie
+// (one copy took 199 M bank conflicts per 3M-atom launch).  R is the
+// largest power of two up to 8 that keeps the copies within 40 KB.
+__host__ __device__ __forceinline__ int gt_log_rep(int n) {
+    int lr = 3;
+    while (lr > 0 && (long long)n * (16 << lr) > 40 * 1024) --lr;
+    return lr;
+}
 struct EwaldC {
-    const float4* tab;
+    const float4* tab;  // this lane's copy
     float invh;
     unsigned last;  // gt_n - 1
+    int lr;         // log2 R
 };
 
 // 1.5 * 2^23: a float in [2^23, 2^24) holds an integer in its mantissa
@@ -63,7 +74,7 @@ __device__ __forceinline__ float ewald_g(float r, const EwaldC& ew) {
     const float m = __fmaf_rd(r, ew.invh, GT_MAGIC);
     const float s = fmaf(r, ew.invh, GT_MAGIC - m);
     const unsigned k = min((unsigned)(__float_as_int(m) - __float_as_int(GT_MAGIC)), ew.last);
-    const float4 c = ew.tab[k];
+    const float4 c = ew.tab[k << ew.lr];
     return fmaf(fmaf(fmaf(c.w, s, c.z), s, c.y), s, c.x);
 }
 __device__ __forceinline__ float2 ewald_g2(float2 r, const EwaldC& ew) {
@@ -71,7 +82,7 @@ __device__ __forceinline__ float2 ewald_g2(float2 r, const EwaldC& ew) {
     const float2 s = fma2(r, dup2(ew.invh), sub2(dup2(GT_MAGIC), m));
     const unsigned k0 = min((unsigned)(__float_as_int(m.x) - __float_as_int(GT_MAGIC)), ew.last);
     const unsigned k1 = min((unsigned)(__float_as_int(m.y) - __float_as_int(GT_MAGIC)), ew.last);
-    const float4 c0 = ew.tab[k0], c1 = ew.tab[k1];
+    const float4 c0 = ew.tab[k0 << ew.lr], c1 = ew.tab[k1 << ew.lr];
     float2 g = fma2(make_float2(c0.w, c1.w), s, make_float2(c0.z, c1.z));
     g = fma2(g, s, make_float2(c0.y, c1.y));
     return fma2(g, s, make_float2(c0.x, c1.x));
@@ -282,9 +293,10 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     float2* const s_lje = reinterpret_cast<float2*>(s_ljt + lj_e_offset(nt));
     if (ENER)
         for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) s_lje[k] = kp.lje[k];
+    const int gt_lr = gt_log_rep(kp.gt_n);
     if (COUL == NB_COUL_EWALD)
-        for (int k = threadIdx.x; k < kp.gt_n; k += blockDim.x)
-            reinterpret_cast<float4*>(s_ljt + gt_offset(nt))[k] = kp.gtab[k];
+        for (int k = threadIdx.x; k < (kp.gt_n << gt_lr); k += blockDim.x)
+            reinterpret_cast<float4*>(s_ljt + gt_offset(nt))[k] = kp.gtab[k >> gt_lr];
     if (lane < 6) s_acc[w][lane] = 0.0;
     __syncthreads();
     int* const qm = s_qm[ENER ? w : 0];
@@ -293,9 +305,10 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     long long np = 0;
 
     EwaldC ew;
-    ew.tab = reinterpret_cast<const float4*>(s_ljt + gt_offset(nt));
+    ew.tab = reinterpret_cast<const float4*>(s_ljt + gt_offset(nt)) + (lane & ((1 << gt_lr) - 1));
     ew.invh = kp.gt_invh;
     ew.last = (unsigned)max(kp.gt_n - 1, 0);
+    ew.lr = gt_lr;
 
     float* const sjg = &s_j[w][g][0];
     // where lane i stages j-slot i: x and y at 12 (i >> 1) + (i & 1) (+ 2),
@@ -658,7 +671,7 @@ template <int COUL, bool VIR, int MINB, bool ENER = false, bool LJSH = false, bo
 cudaError_t launch_forces_t(const PlanLaunch& p, cudaStream_t st) {
     const size_t nt2 = (size_t)p.kp.ntypes * p.kp.ntypes;
     // LJ tables (the energies' too with ENER), then the Ewald force table
-    const size_t smem = COUL == NB_COUL_EWALD ? (gt_offset(p.kp.ntypes) + 4 * (size_t)p.kp.gt_n) * sizeof(float)
+    const size_t smem = COUL == NB_COUL_EWALD ? (gt_offset(p.kp.ntypes) + ((4 * (size_t)p.kp.gt_n) << gt_log_rep(p.kp.gt_n))) * sizeof(float)
                         : ENER ? (lj_e_offset(p.kp.ntypes) + 2 * nt2) * sizeof(float)
                                : (LJ_C12 + nt2) * sizeof(float);
     auto kern = k_forces<COUL, VIR, MINB, ENER, LJSH, LJW>;
