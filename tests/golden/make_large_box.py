@@ -7,7 +7,8 @@ Run once on the host (about three and a half hours on 8 cores):
 The O(N^2) sum is taken in 64 row ranges of about equal pair counts; the
 sums of finished ranges are kept in large_box_seed3.partial.json beside the
 output, so an interrupted run resumes where it stopped (and the file is
-removed at the end).
+removed at the end).  `--add-moments` adds the input moments (see
+input_moments) to an existing output without the O(N^2) work.
 
 It calls only the FP64 oracle (oracle/nb_oracle.c, the plain O(N^2)
 minimum-image pair sum) and the seeded input generator, on the box the
@@ -50,6 +51,28 @@ def input_digest(s) -> str:
               np.ascontiguousarray(s.excl_atoms, dtype=np.int32), np.asarray(s.box, dtype=np.float64)):
         h.update(a.tobytes())
     return h.hexdigest()
+
+
+def input_moments(s) -> list:
+    """Float64 sums of the float32 coordinates and of their squares, per axis,
+    and of the charges: a fingerprint of the atoms that a few last-bit
+    differences of the generator on another machine (fused multiply-adds,
+    libm) leave equal to about 1e-12, where the SHA-256 would change."""
+    x = np.asarray(s.x, dtype=np.float64)
+    return [float(v) for v in np.concatenate([x.sum(0), (x * x).sum(0), [np.asarray(s.q, np.float64).sum()]])]
+
+
+def add_moments():
+    """Add the input moments to an existing output (no O(N^2) work)."""
+    with open(OUT) as fh:
+        rec = json.load(fh)
+    s = wb.large_box(seed=rec["seed"])
+    if input_digest(s) != rec["input_sha256"]:
+        raise SystemExit("the generator made other atoms than the stored run")
+    rec["input_moments"] = input_moments(s)
+    with open(OUT, "w") as fh:
+        json.dump(rec, fh, indent=1)
+        fh.write("\n")
 
 
 def main():
@@ -102,6 +125,7 @@ def main():
         "params": {"rc": p.rc, "coul": "ewald", "beta": p.beta, "eps_r": p.eps_r, "fcoul": p.fcoul,
                    "c6_OO": float(p.c6[0]), "c12_OO": float(p.c12[0]), "modifiers": 0},
         "input_sha256": digest,
+        "input_moments": input_moments(s),
         "e_lj": float(ev["e_lj"]),
         "e_coul": float(ev["e_coul"]),
         "virial": [float(v) for v in ev["virial"].reshape(-1)],
@@ -120,4 +144,7 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    if sys.argv[1:] == ["--add-moments"]:
+        add_moments()
+    else:
+        main()
