@@ -523,7 +523,7 @@ nb_status plan_alloc_inner(Plan* pl) {
     plan_free_inner(pl);
     const size_t items = (size_t)pl->list.item_cap, entries = (size_t)pl->list.entry_cap;
     size_t bytes = align256(16 * items) + align256(4 * items) + align256(4 * entries) + align256(8 * entries) +
-                   align256(4 * CNT_N);
+                   align256(8 * entries) + align256(4 * CNT_N);
     void* blk = nullptr;
     nb_status s = dev_alloc(pl->ctx, &blk, bytes);
     if (s != NB_OK) return s;
@@ -535,6 +535,8 @@ nb_status plan_alloc_inner(Plan* pl) {
     pl->inner.cj = (int*)b;
     b += align256(4 * entries);
     pl->inner.mask = (unsigned long long*)b;
+    b += align256(8 * entries);
+    pl->inner.marks = (unsigned char*)b;
     b += align256(8 * entries);
     pl->inner.counters = (int*)b;
     pl->inner.item_cap = pl->list.item_cap;
@@ -558,7 +560,7 @@ nb_status plan_alloc_list(Plan* pl, long long items, long long entries) {
     items = std::min<long long>(items, (1ll << 31) - 1);
     entries = std::min<long long>(entries, (1ll << 31) - 1);
     size_t bytes = align256(16 * (size_t)items) + align256(4 * (size_t)items) + align256(4 * (size_t)entries) +
-                   align256(8 * (size_t)entries) + align256(4 * CNT_N);
+                   align256(8 * (size_t)entries) + align256(8 * (size_t)entries) + align256(4 * CNT_N);
     void* blk = nullptr;
     nb_status s = dev_alloc(pl->ctx, &blk, bytes);
     if (s != NB_OK) return s;
@@ -571,6 +573,8 @@ nb_status plan_alloc_list(Plan* pl, long long items, long long entries) {
     pl->list.cj = (int*)b;
     b += align256(4 * (size_t)entries);
     pl->list.mask = (unsigned long long*)b;
+    b += align256(8 * (size_t)entries);
+    pl->list.marks = (unsigned char*)b;
     b += align256(8 * (size_t)entries);
     pl->list.counters = (int*)b;
     pl->list.item_cap = (int)items;
@@ -836,7 +840,7 @@ nb_status check_box(const nb_params* p, const double box[3]) {
 size_t plan_bytes_estimate(const nb_params* p, int natoms, const double box[3], const Geometry& g) {
     long long it, en;
     list_estimate(*p, natoms, box, g.clcap, 8, &it, &en);
-    return align256(20 * (size_t)it) + align256(12 * (size_t)en) + 4096;
+    return align256(20 * (size_t)it) + align256(20 * (size_t)en) + 4096;
 }
 
 }  // namespace nbgb

@@ -42,7 +42,11 @@ namespace {
 constexpr unsigned FULL = FULL_MASK;
 constexpr int EW = 8;  // warps per block
 
-template <int COUL, bool LJSH>
+// With MK the force kernel of the same evaluation has marked, per entry and
+// i-row, the slots inside rc or in the band (ListDev::marks): the warp queues
+// them from those bits, without staging the j-clusters or computing any
+// distance (the screening is 41% of this kernel's time otherwise).
+template <int COUL, bool LJSH, bool MK>
 __global__ void __launch_bounds__(EW * 32, 3)
 k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     pdl_wait();
@@ -116,6 +120,45 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         int npair = 0;
         int head = 0, tail = 0;  // ring positions, identical in every lane
 
+        if (MK) {
+            const int h = i >> 1;
+            int e = jb + g;
+            unsigned pmk = 0u;
+            int pj = 0;
+            if (e < je) {
+                pmk = list.marks[(size_t)e * CL + i];
+                pj = list.cj[e] * CL;
+            }
+            for (int base = jb; base < je; base += 4) {
+                const unsigned mk = pmk;
+                const int cj0 = pj;
+                e = base + 4 + g;
+                pmk = 0u;
+                if (e < je) {
+                    pmk = list.marks[(size_t)e * CL + i];
+                    pj = list.cj[e] * CL;
+                }
+                // bit b: j-slot 2 ((b >> 1) XOR h) + (b & 1) is queued (the
+                // drain finds the band pairs from its own distances)
+#pragma unroll
+                for (int b = 0; b < CL; ++b) {
+                    const bool q = (mk >> b) & 1u;
+                    const unsigned bal = __ballot_sync(FULL, q);
+                    if (q) {
+                        const int js = 2 * ((b >> 1) ^ h) + (b & 1);
+                        const int pos = (tail + __popc(bal & ((1u << lane) - 1u))) & (QCAP - 1);
+                        qm[pos] = ((cj0 + js) << 4) | (i << 1);
+                    }
+                    tail += __popc(bal);
+                }
+                __syncwarp();
+                while (tail - head >= 64) {
+                    drain2<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e12l, e6, e6l,
+                                       npair, true, true);
+                    head += 64;
+                }
+            }
+        } else {
         int e = jb + g;
         bool act = e < je;
         unsigned long long pm = 0ull;
@@ -165,6 +208,7 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
                 head += 64;
             }
         }
+        }
         if (tail > head)
             drain2<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e12l, e6, e6l, npair,
                                lane < tail - head, lane + 32 < tail - head);
@@ -179,7 +223,7 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
 template <int COUL, bool LJSH>
 cudaError_t launch_energy_t(const PlanLaunch& p, cudaStream_t st) {
     size_t smem = (size_t)p.kp.ntypes * p.kp.ntypes * sizeof(float2);
-    auto kern = k_energy<COUL, LJSH>;
+    auto kern = energy_marks(p, NB_F_ENERGY) ? k_energy<COUL, LJSH, true> : k_energy<COUL, LJSH, false>;
     int per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, EW * 32, smem);
     if (err != cudaSuccess) return err;

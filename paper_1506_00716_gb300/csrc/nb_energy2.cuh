@@ -114,6 +114,11 @@ __device__ __forceinline__ void pair_energy2(const float4 xj0, const float4 xj1,
     two_sum2(s1, pz, r2h, e2);
     const float2 r2l = add2(add2(e1, e2), add2(ex, add2(ey, ez)));
 
+    // a pair in the band around rc (marked by the screening, or found here:
+    // the high part of the double-float r^2 is within 2^-24 of r^2, far
+    // inside the band) is decided exactly, in the oracle's arithmetic
+    maybe0 = maybe0 || !(r2h.x < kp.rc2_lo);
+    maybe1 = maybe1 || !(r2h.y < kp.rc2_lo);
     bool in0 = valid0, in1 = valid1;
     if (valid0 && maybe0) in0 = exact_inside(xs0, xj0, kp.rc2_d);
     if (valid1 && maybe1) in1 = exact_inside(xs1, xj1, kp.rc2_d);

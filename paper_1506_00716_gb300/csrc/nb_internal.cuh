@@ -110,6 +110,12 @@ struct ListDev {
     int4* items;         // (ci, first entry, end entry, sys << 5 | shift)
     int* cj;             // j-cluster per entry
     unsigned long long* mask;  // 8x8 interaction bits per entry (rotated layout)
+    // per entry and i-row (entry * 8 + i-slot), written by the force kernel of
+    // an evaluation with energies: the slots inside rc or in the band around
+    // it, bit 2p + c standing for j-slot 2 (p XOR (i >> 1)) + c; the energy
+    // kernel queues from them instead of computing every slot's distance
+    // again.  NULL: the energy kernel screens the slots itself.
+    unsigned char* marks;
     int* counters;       // [CNT_N]
     // evaluation order of the non-empty items, written by the prune: the
     // long items (more than max_entries / 2 entries) from the front, the
@@ -317,6 +323,10 @@ cudaError_t launch_prepare(const PlanLaunch& p, bool coords, cudaStream_t st);
 // the energies, in the same kernel).
 cudaError_t launch_forces(const PlanLaunch& p, unsigned flags, cudaStream_t st);
 bool energy_fused(const PlanLaunch& p);
+// Whether the force kernel of an evaluation with these flags writes the
+// list's marks and the energy kernel queues from them (separate energies,
+// a list with marks, a force register budget of 2 or 3 blocks per SM).
+bool energy_marks(const PlanLaunch& p, unsigned flags);
 // The separate energy kernel (nothing when the energies are fused).
 cudaError_t launch_energy(const PlanLaunch& p, cudaStream_t st);
 cudaError_t launch_finalize(const PlanLaunch& p, unsigned flags, cudaStream_t st);

@@ -264,7 +264,13 @@ __device__ __forceinline__ void pair_block2(const float* __restrict__ sj, int h,
 //
 // With LJW (KParams::lj_weights) the Lennard-Jones parameters come from the
 // atoms' weights instead of the type-pair table.
-template <int COUL, bool VIR, int MINB, bool ENER, bool LJSH, bool LJW = false>
+//
+// With MARK (an evaluation with energies on the separate energy kernel) the
+// kernel writes, per entry and i-row, the slots inside rc or in the band
+// around it (ListDev::marks), from the distances it has just computed, so
+// that the energy kernel needs no second distance pass (it finds the band
+// pairs among them from its own double-float distances).
+template <int COUL, bool VIR, int MINB, bool ENER, bool LJSH, bool LJW = false, bool MARK = false>
 __global__ void __launch_bounds__(FW * 32, MINB)
 k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     pdl_wait();
@@ -443,13 +449,13 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             unsigned ebits = 0u, mbits = 0u;
             const bool full = __all_sync(FULL, row == 0xffu);
             if (full && !shifted)
-                pair_block2<COUL, VIR, false, false, EXACT, ENER, LJW>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
+                pair_block2<COUL, VIR, false, false, EXACT, ENER || MARK, LJW>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
                                                                       fi, fj, v, band, ebits, mbits, dup2(wi));
             else if (full)
-                pair_block2<COUL, VIR, false, true, EXACT, ENER, LJW>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
+                pair_block2<COUL, VIR, false, true, EXACT, ENER || MARK, LJW>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
                                                                      fi, fj, v, band, ebits, mbits, dup2(wi));
             else
-                pair_block2<COUL, VIR, true, true, EXACT, ENER, LJW>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
+                pair_block2<COUL, VIR, true, true, EXACT, ENER || MARK, LJW>(sjg, h, xp, dup2(qi), ljrow, rowp, kp, ew,
                                                                     fi, fj, v, band, ebits, mbits, dup2(wi));
             // transposed butterfly over the 8 lanes of the group: half c of
             // fj[p] holds j-slot 2 (p XOR (i >> 1)) + c, so the partners at
@@ -516,6 +522,7 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
                 fjt[2] += s_fix[w][g][i][2];
             }
             if (cact) atomicAdd(f_s + ccj * CL + i, make_float4(fjt[0], fjt[1], fjt[2], 0.f));
+            if (MARK && cact) list.marks[(size_t)(base + g) * CL + i] = (unsigned char)ebits;
             if (ENER) {
                 // queue this entry's candidate pairs (bit 2p + c: j-slot
                 // 2 (p XOR (i >> 1)) + c), then evaluate them 64 at a time
@@ -667,14 +674,14 @@ __global__ void k_finish(const SysDev* __restrict__ sys, const int* __restrict__
     }
 }
 
-template <int COUL, bool VIR, int MINB, bool ENER = false, bool LJSH = false, bool LJW = false>
+template <int COUL, bool VIR, int MINB, bool ENER = false, bool LJSH = false, bool LJW = false, bool MARK = false>
 cudaError_t launch_forces_t(const PlanLaunch& p, cudaStream_t st) {
     const size_t nt2 = (size_t)p.kp.ntypes * p.kp.ntypes;
     // LJ tables (the energies' too with ENER), then the Ewald force table
     const size_t smem = COUL == NB_COUL_EWALD ? (gt_offset(p.kp.ntypes) + ((4 * (size_t)p.kp.gt_n) << gt_log_rep(p.kp.gt_n))) * sizeof(float)
                         : ENER ? (lj_e_offset(p.kp.ntypes) + 2 * nt2) * sizeof(float)
                                : (LJ_C12 + nt2) * sizeof(float);
-    auto kern = k_forces<COUL, VIR, MINB, ENER, LJSH, LJW>;
+    auto kern = k_forces<COUL, VIR, MINB, ENER, LJSH, LJW, MARK>;
     if (ENER || smem > 48 * 1024) {
         // the energy queue (or a large Ewald table) makes static + dynamic
         // shared memory pass 48 KB: allow the dynamic part explicitly
@@ -701,6 +708,17 @@ cudaError_t launch_prepare(const PlanLaunch& p, bool coords, cudaStream_t st) {
                       (const float*)nullptr);
 }
 
+// The force kernel writing the energy kernel's marks (2 or 3 blocks per SM).
+template <int COUL, bool VIR>
+cudaError_t launch_forces_m(const PlanLaunch& p, cudaStream_t st) {
+    const bool w = p.kp.lj_weights != 0;
+    if (p.kp.force_min_blocks == 2)
+        return w ? launch_forces_t<COUL, VIR, 2, false, false, true, true>(p, st)
+                 : launch_forces_t<COUL, VIR, 2, false, false, false, true>(p, st);
+    return w ? launch_forces_t<COUL, VIR, 3, false, false, true, true>(p, st)
+             : launch_forces_t<COUL, VIR, 3, false, false, false, true>(p, st);
+}
+
 template <int COUL, bool VIR>
 cudaError_t launch_forces_v(const PlanLaunch& p, cudaStream_t st) {
     // Lennard-Jones by weights for the register budgets of 2 and 3 blocks per
@@ -723,12 +741,21 @@ cudaError_t launch_forces_e(const PlanLaunch& p, cudaStream_t st) {
 
 bool energy_fused(const PlanLaunch& p) { return p.kp.energy_mode == 1; }
 
+bool energy_marks(const PlanLaunch& p, unsigned flags) {
+    return (flags & NB_F_ENERGY) && !energy_fused(p) && p.list.marks != nullptr && p.kp.force_min_blocks != 1;
+}
+
 cudaError_t launch_forces(const PlanLaunch& p, unsigned flags, cudaStream_t st) {
     bool vi = flags & NB_F_VIRIAL;
     if ((flags & NB_F_ENERGY) && energy_fused(p)) {
         if (p.kp.coul == NB_COUL_RF)
             return vi ? launch_forces_e<NB_COUL_RF, true>(p, st) : launch_forces_e<NB_COUL_RF, false>(p, st);
         return vi ? launch_forces_e<NB_COUL_EWALD, true>(p, st) : launch_forces_e<NB_COUL_EWALD, false>(p, st);
+    }
+    if (energy_marks(p, flags)) {
+        if (p.kp.coul == NB_COUL_RF)
+            return vi ? launch_forces_m<NB_COUL_RF, true>(p, st) : launch_forces_m<NB_COUL_RF, false>(p, st);
+        return vi ? launch_forces_m<NB_COUL_EWALD, true>(p, st) : launch_forces_m<NB_COUL_EWALD, false>(p, st);
     }
     if (p.kp.coul == NB_COUL_RF)
         return vi ? launch_forces_v<NB_COUL_RF, true>(p, st) : launch_forces_v<NB_COUL_RF, false>(p, st);
