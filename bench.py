@@ -1063,16 +1063,23 @@ def run_serve(args, n_req: int = 256) -> dict:
     # serial plain calls, one request after another
     e = np.zeros(2)
     v = np.zeros(9)
+
+    def serial(batch):
+        for r, (xq, ty) in batch:
+            autotune.apply(ctx, "ewald", r.n, table, gpu=gpu)
+            h = nb.nb_sys_create(ctx, p, r.n, r.box)
+            nb.nb_set_exclusions(h, r.excl_index, r.excl_atoms)
+            nb.nb_grid_put(h, xq, ty)
+            nb.nb_pairlist_build(h)
+            f = np.empty((r.n, 3), dtype=np.float32)
+            nb.nb_forces(h, None, f, e, v, flags)
+            nb.nb_sys_destroy(h)
+
+    # untimed, as the server's first burst: every kernel variant the serial
+    # calls take is loaded, and the allocation pool holds their sizes
+    serial(list(zip(reqs, inputs))[::8])
     t0 = time.perf_counter()
-    for r, (xq, ty) in zip(reqs, inputs):
-        autotune.apply(ctx, "ewald", r.n, table, gpu=gpu)
-        h = nb.nb_sys_create(ctx, p, r.n, r.box)
-        nb.nb_set_exclusions(h, r.excl_index, r.excl_atoms)
-        nb.nb_grid_put(h, xq, ty)
-        nb.nb_pairlist_build(h)
-        f = np.empty((r.n, 3), dtype=np.float32)
-        nb.nb_forces(h, None, f, e, v, flags)
-        nb.nb_sys_destroy(h)
+    serial(zip(reqs, inputs))
     t_serial = time.perf_counter() - t0
     nb.nb_ctx_destroy(ctx)
     lat_ms = np.array(lat) * 1e3
