@@ -1098,7 +1098,7 @@ def run_serve(args, n_req: int = 256) -> dict:
 
 
 def _targets_digest(out: dict) -> dict:
-    """The few numbers the benchmark spec's targets are stated on, rounded."""
+    """The few numbers the performance targets are stated on, rounded."""
     d = {"headline_24k": {"pairs_per_s": round(out["value"] / 1e9, 2), "unit": "G pairs/s",
                           "fp32_frac": out["roofline"]["frac"], "ms_per_step": round(out["ms_per_step"], 4)}}
     lb = out.get("large_box")
