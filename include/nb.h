@@ -170,12 +170,21 @@ enum {
  *                     kernel after the force kernel (default), 1 = the force
  *                     kernel also evaluates the energies of the pairs it
  *                     finds inside rc.  The results are the same.
+ *   jcluster          j-cluster size N of the list (Section 3.2's cluster
+ *                     geometry; the i-cluster size M is 8): 8 (or 0, the
+ *                     default) = 8 x 8 entries; 4 = the z-halves of the
+ *                     8-atom clusters as 4-atom j-clusters, those without a
+ *                     pair within the list radius dropped by the prune and
+ *                     the rest paired two per entry (fewer pair slots per
+ *                     interacting pair, more list entries per slot).  The
+ *                     interacting pairs and the results are the same.
  */
 typedef struct {
     int max_entries;
     int force_min_blocks;
     int search_mode;
     int energy_mode;
+    int jcluster;
 } nb_tuning;
 
 /* Message of the calling thread's last failure ("" if none). */
@@ -335,6 +344,19 @@ nb_status nb_eval_info(nb_sys *sys, nb_eval_stats *stats);
  */
 nb_status nb_pairlist_export(nb_sys *sys, int *perm, int *items, int *cj,
                              unsigned long long *mask, long long *n_entries_total);
+/*
+ * Test hook: as nb_pairlist_export, for either j-cluster geometry
+ * (nb_tuning.jcluster), with the j-atoms of each entry given by sorted slot
+ * instead of by j-cluster.  Section 3.2 sets the cluster sizes by the SIMD
+ * width of the hardware; with 4-atom j-clusters one entry holds two of them.
+ *   jslot   2 * n_entries_total ints: entry e's j-slots 0-3 are the sorted
+ *           slots jslot[2e] + 0..3 and its j-slots 4-7 the slots
+ *           jslot[2e + 1] + 0..3 (8 x 8 lists: 8 cj and 8 cj + 4)
+ * nb_pairlist_export itself refuses (NB_ERR_STATE) to write cj for a list of
+ * 4-atom j-clusters, which have no single j-cluster per entry.
+ */
+nb_status nb_pairlist_export_slots(nb_sys *sys, int *perm, int *items, int *jslot,
+                                   unsigned long long *mask, long long *n_entries_total);
 
 /*
  * Test hook (host only, no device work): the Ewald force table of the
@@ -357,6 +379,30 @@ nb_status nb_pairlist_export(nb_sys *sys, int *perm, int *items, int *cj,
  */
 nb_status nb_ewald_force_table(double beta, double rc, float *coef, int max_intervals, int *n_intervals,
                                double *h);
+
+/*
+ * Test hook (host only, no device work): the Ewald energy table of the
+ * energy kernels for splitting parameter beta (nm^-1) and cut-off rc (nm).
+ * With NB_COUL_EWALD the energy kernels take erfc(beta r) of the pair energy
+ * f qi qj erfc(beta r) / r (Section 3.2's pair interaction, see nb_params)
+ * from a table of quartics on intervals of width h = 2^-n: interval k covers
+ * [k h, (k + 1) h) and gives erfc(beta r) ~ a0 + a1 s + a2 s^2 + a3 s^3 +
+ * a4 s^4, s = r / h - k, the polynomial interpolating erfc(beta r) (float64)
+ * at the five Chebyshev points (1 - cos((2 j + 1) pi / 10)) / 2 of s.  h is
+ * the largest power of two for which the interpolation error bound
+ * 2 (h / 4)^5 max|d^5 erfc(beta r) / dr^5| / 5! is at most 1e-12 and
+ * max|a2| at most 1e-4, and the intervals reach rc (1 + 1e-4).  The kernels
+ * evaluate a0 + a1 s in double-float and the rest in float32.
+ *   coef          8 * max_intervals floats (host), or NULL for the size only:
+ *                 per interval (a0 hi, a0 lo, a1 hi, a1 lo, a2, a3, a4, 0),
+ *                 a0 = a0 hi + a0 lo and a1 = a1 hi + a1 lo as float sums
+ *   n_intervals   receives the number of intervals (at most 2048)
+ *   h             receives the interval width (nm); may be NULL
+ * NB_ERR_ARG unless beta > 0, rc > 0 and beta rc <= 10 (the limit of
+ * nb_sys_create for NB_COUL_EWALD), or if coef holds fewer intervals.
+ */
+nb_status nb_ewald_energy_table(double beta, double rc, float *coef, int max_intervals, int *n_intervals,
+                                double *h);
 
 /*
  * Batched evaluation of many independent systems (the paper's ensemble

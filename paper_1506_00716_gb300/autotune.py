@@ -10,14 +10,16 @@ Tuned per (electrostatics, system size):
   search_mode       cluster-pair search: a warp per i-cluster (1) or a
                     thread per i-cluster (2);
   energy_mode       evaluations with energies: a separate double-float energy
-                    kernel (0) or the energies fused into the force kernel (1).
-The cluster size is fixed at M = N = 8 by the warp layout of the kernels
-(other geometries and why they are not built: the design notes).
+                    kernel (0) or the energies fused into the force kernel (1);
+  jcluster          cluster geometry M x N (Section 3.2): 8 x 8, or 8 x 4 with
+                    the z-halves of the 8-atom clusters as j-clusters, two per
+                    list entry (fewer computed pair slots, more entries).
 
 For every (max_entries, force_min_blocks) candidate the tuner builds the list
 and times one build (search + prune) plus EVALS force evaluations with the
 library's per-stage CUDA events, and keeps the fastest; at that setting it
-times the build with each search kernel, and one evaluation with energies and
+times the same with each cluster geometry and keeps the faster, then times
+the build with each search kernel, and one evaluation with energies and
 virial with each energy path.  The result is a JSON table keyed by GPU name;
 lookup() picks the entry of the nearest size (in log atoms).
 
@@ -41,12 +43,13 @@ MAX_ENTRIES = [8, 16, 32, 64, 128]
 MIN_BLOCKS = [1, 2, 3]
 SEARCH_MODES = [1, 2]
 ENERGY_MODES = [0, 1]
+JCLUSTERS = [8, 4]
 EVALS = 10
 
 
-def _time_build(ctx, h, s, me, mb, search_mode, reps: int = 3) -> float:
+def _time_build(ctx, h, s, me, mb, search_mode, jc: int = 8, reps: int = 3) -> float:
     """Fastest list build (search + prune), ms."""
-    nb.nb_ctx_set_tuning(ctx, me, mb, search_mode)
+    nb.nb_ctx_set_tuning(ctx, me, mb, search_mode, 0, jc)
     nb.nb_grid_put(h, s.xq(), s.type)
     nb.nb_pairlist_build(h)
     best = None
@@ -61,9 +64,9 @@ def _time_build(ctx, h, s, me, mb, search_mode, reps: int = 3) -> float:
     return best
 
 
-def _time_energy_eval(ctx, h, s, me, mb, search_mode, energy_mode, reps: int = 3) -> float:
+def _time_energy_eval(ctx, h, s, me, mb, search_mode, energy_mode, jc: int = 8, reps: int = 3) -> float:
     """Fastest evaluation with energies and virial (force + energy stages), ms."""
-    nb.nb_ctx_set_tuning(ctx, me, mb, search_mode, energy_mode)
+    nb.nb_ctx_set_tuning(ctx, me, mb, search_mode, energy_mode, jc)
     nb.nb_grid_put(h, s.xq(), s.type)
     nb.nb_pairlist_build(h)
     flags = nb.NB_F_ENERGY | nb.NB_F_VIRIAL
@@ -84,8 +87,8 @@ def _time_energy_eval(ctx, h, s, me, mb, search_mode, energy_mode, reps: int = 3
     return best
 
 
-def _time_config(ctx, h, s, max_entries, min_blocks, reps: int = 2) -> dict:
-    nb.nb_ctx_set_tuning(ctx, max_entries, min_blocks)
+def _time_config(ctx, h, s, max_entries, min_blocks, jc: int = 8, reps: int = 2) -> dict:
+    nb.nb_ctx_set_tuning(ctx, max_entries, min_blocks, 0, 0, jc)
     xq, ty = s.xq(), s.type
     nb.nb_grid_put(h, xq, ty)
     nb.nb_pairlist_build(h)
@@ -102,7 +105,8 @@ def _time_config(ctx, h, s, max_entries, min_blocks, reps: int = 2) -> dict:
         st = nb.nb_ctx_timing(ctx, reset=True)
         total = st["search"][0] + st["prune"][0] + st["forces"][0] + st["zero"][0] + st["final"][0]
         rec = {"total_ms": total, "forces_ms": st["forces"][0] / EVALS,
-               "build_ms": st["search"][0] + st["prune"][0]}
+               "build_ms": st["search"][0] + st["prune"][0],
+               "slots": 64 * nb.nb_pairlist_info(h)["n_entries"]}
         if best is None or rec["total_ms"] < best["total_ms"]:
             best = rec
     return best
@@ -128,14 +132,21 @@ def tune(sizes=SIZES_MOL, device: int = 0, verbose: bool = True) -> dict:
                         results.append({"max_entries": me, "force_min_blocks": mb, **r})
                 best = min(results, key=lambda r: r["total_ms"])
                 me, mb = best["max_entries"], best["force_min_blocks"]
-                build = {sm: _time_build(ctx, h, s, me, mb, sm) for sm in SEARCH_MODES}
+                geo = {jc: (best if jc == 8 else _time_config(ctx, h, s, me, mb, jc)) for jc in JCLUSTERS}
+                jc = min(geo, key=lambda k: geo[k]["total_ms"])
+                best = geo[jc]
+                build = {sm: _time_build(ctx, h, s, me, mb, sm, jc) for sm in SEARCH_MODES}
                 search_mode = min(build, key=build.get)
-                energy = {em: _time_energy_eval(ctx, h, s, me, mb, search_mode, em) for em in ENERGY_MODES}
+                energy = {em: _time_energy_eval(ctx, h, s, me, mb, search_mode, em, jc) for em in ENERGY_MODES}
                 energy_mode = min(energy, key=energy.get)
                 nb.nb_sys_destroy(h)
                 default = next(r for r in results if r["max_entries"] == 32 and r["force_min_blocks"] == 3)
                 entries.append({"coul": coul, "atoms": s.n, "max_entries": me, "force_min_blocks": mb,
-                                "search_mode": search_mode, "energy_mode": energy_mode,
+                                "search_mode": search_mode, "energy_mode": energy_mode, "jcluster": jc,
+                                "by_jcluster": {str(k): {"total_ms": round(v["total_ms"], 5),
+                                                         "forces_ms": round(v["forces_ms"], 5),
+                                                         "build_ms": round(v["build_ms"], 5), "slots": v["slots"]}
+                                                for k, v in geo.items()},
                                 "build_ms_by_search_mode": {str(k): round(v, 5) for k, v in build.items()},
                                 "energy_eval_ms_by_energy_mode": {str(k): round(v, 5) for k, v in energy.items()},
                                 "total_ms": round(best["total_ms"], 5),
@@ -143,8 +154,9 @@ def tune(sizes=SIZES_MOL, device: int = 0, verbose: bool = True) -> dict:
                                 "sweep": [{k: (round(v, 5) if isinstance(v, float) else v)
                                            for k, v in r.items()} for r in results]})
                 if verbose:
-                    print(f"{coul:5s} {s.n:8d} atoms: best max_entries={me} min_blocks={mb} "
-                          f"{best['total_ms']:.4f} ms (default {default['total_ms']:.4f} ms); search {build}; "
+                    print(f"{coul:5s} {s.n:8d} atoms: best max_entries={me} min_blocks={mb} jcluster={jc} "
+                          f"{best['total_ms']:.4f} ms (default {default['total_ms']:.4f} ms); "
+                          f"geometry { {k: round(v['total_ms'], 4) for k, v in geo.items()} }; search {build}; "
                           f"energy {energy}", flush=True)
     finally:
         nb.nb_ctx_destroy(ctx)
@@ -162,7 +174,7 @@ def load(path: str = DEFAULT_TABLE) -> dict | None:
 
 def lookup(table: dict | None, coul: str, natoms: int, gpu: str | None = None) -> dict:
     """Tuning for a system: the table entry of the same electrostatics and nearest size."""
-    default = {"max_entries": 32, "force_min_blocks": 3, "search_mode": 0, "energy_mode": 0}
+    default = {"max_entries": 32, "force_min_blocks": 3, "search_mode": 0, "energy_mode": 0, "jcluster": 8}
     if not table or (gpu is not None and table.get("gpu") != gpu):
         return default
     cands = [e for e in table.get("entries", []) if e["coul"] == coul]
@@ -170,12 +182,14 @@ def lookup(table: dict | None, coul: str, natoms: int, gpu: str | None = None) -
         return default
     e = min(cands, key=lambda e: abs(math.log(e["atoms"]) - math.log(max(natoms, 1))))
     return {"max_entries": int(e["max_entries"]), "force_min_blocks": int(e["force_min_blocks"]),
-            "search_mode": int(e.get("search_mode", 0)), "energy_mode": int(e.get("energy_mode", 0))}
+            "search_mode": int(e.get("search_mode", 0)), "energy_mode": int(e.get("energy_mode", 0)),
+            "jcluster": int(e.get("jcluster", 8))}
 
 
 def apply(ctx, coul: str, natoms: int, table: dict | None = None, gpu: str | None = None) -> dict:
     t = lookup(table if table is not None else load(), coul, natoms, gpu)
-    nb.nb_ctx_set_tuning(ctx, t["max_entries"], t["force_min_blocks"], t["search_mode"], t["energy_mode"])
+    nb.nb_ctx_set_tuning(ctx, t["max_entries"], t["force_min_blocks"], t["search_mode"], t["energy_mode"],
+                         t["jcluster"])
     return t
 
 

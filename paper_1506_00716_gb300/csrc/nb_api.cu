@@ -413,6 +413,79 @@ int ewald_force_table(double beta, double rc, float4* coef, float* invh) {
     return 0;
 }
 
+int ewald_energy_table(double beta, double rc, float4* coef, float* invh) {
+    static std::mutex memo_mu;
+    static double memo_beta = -1.0, memo_rc = -1.0;
+    static int memo_n = 0;
+    static float memo_invh = 0.f;
+    static float4 memo[2 * ET_MAX];
+    {
+        std::lock_guard<std::mutex> lk(memo_mu);
+        if (beta == memo_beta && rc == memo_rc) {
+            std::memcpy(coef, memo, sizeof(float4) * (size_t)memo_n);
+            std::memcpy(coef + ET_MAX, memo + ET_MAX, sizeof(float4) * (size_t)memo_n);
+            *invh = memo_invh;
+            return memo_n;
+        }
+    }
+    // the largest |d^2 erfc / dx^2| = (4 / sqrt(pi)) max x exp(-x^2) =
+    // 2 sqrt(2 / (e pi)), and |d^5 erfc / dx^5| = (2 / sqrt(pi)) |H4(x)|
+    // exp(-x^2) <= 24 / sqrt(pi) (H4 the Hermite polynomial, largest at 0)
+    const double pi = 3.14159265358979323846;
+    const double m2 = 2.0 * std::sqrt(2.0 / (std::exp(1.0) * pi)), m5 = 24.0 / std::sqrt(pi);
+    const double rmax = rc * (1.0 + 1e-4);
+    for (int n = 0; n <= 30; ++n) {
+        const double h = std::ldexp(1.0, -n);
+        if (h > rmax) continue;
+        const double bh = beta * h;
+        if (0.5 * bh * bh * m2 > 1e-4) continue;
+        if (2.0 * std::pow(bh / 4.0, 5) * m5 / 120.0 > 1e-12) continue;
+        const int K = (int)std::ceil(rmax / h);
+        if (K > ET_MAX) return 0;
+        for (int k = 0; k < K; ++k) {
+            // interpolation at s_j = (1 - cos((2 j + 1) pi / 10)) / 2: the
+            // Vandermonde system in s, solved by Gaussian elimination with
+            // partial pivoting
+            double A[5][6];
+            for (int j = 0; j < 5; ++j) {
+                const double sj = 0.5 * (1.0 - std::cos((2 * j + 1) * pi / 10.0));
+                double pw = 1.0;
+                for (int c = 0; c < 5; ++c, pw *= sj) A[j][c] = pw;
+                A[j][5] = std::erfc(beta * h * (k + sj));
+            }
+            for (int c = 0; c < 5; ++c) {
+                int piv = c;
+                for (int r = c + 1; r < 5; ++r)
+                    if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+                for (int q = 0; q < 6; ++q) std::swap(A[c][q], A[piv][q]);
+                for (int r = c + 1; r < 5; ++r) {
+                    const double f = A[r][c] / A[c][c];
+                    for (int q = c; q < 6; ++q) A[r][q] -= f * A[c][q];
+                }
+            }
+            double a[5];
+            for (int c = 4; c >= 0; --c) {
+                double t = A[c][5];
+                for (int q = c + 1; q < 5; ++q) t -= A[c][q] * a[q];
+                a[c] = t / A[c][c];
+            }
+            const float a0h = (float)a[0], a1h = (float)a[1];
+            coef[k] = make_float4(a0h, (float)(a[0] - (double)a0h), a1h, (float)(a[1] - (double)a1h));
+            coef[ET_MAX + k] = make_float4((float)a[2], (float)a[3], (float)a[4], 0.f);
+        }
+        *invh = (float)(1.0 / h);
+        std::lock_guard<std::mutex> lk(memo_mu);
+        std::memcpy(memo, coef, sizeof(float4) * (size_t)K);
+        std::memcpy(memo + ET_MAX, coef + ET_MAX, sizeof(float4) * (size_t)K);
+        memo_n = K;
+        memo_invh = *invh;
+        memo_beta = beta;
+        memo_rc = rc;
+        return K;
+    }
+    return 0;
+}
+
 KParams make_kparams(const nb_sys* s) {
     KParams k{};
     const nb_params& p = s->p;
@@ -429,17 +502,12 @@ KParams make_kparams(const nb_sys* s) {
     k.beta = (float)p.ewald_beta;
     double crf = 1.0 / p.rc + krf * p.rc * p.rc;
     double fq = p.fcoul / p.eps_r;
-    double mb = -p.ewald_beta * p.ewald_beta * 1.4426950408889634;
     k.krf_h = (float)krf;
     k.krf_l = (float)(krf - (double)k.krf_h);
     k.crf_h = (float)crf;
     k.crf_l = (float)(crf - (double)k.crf_h);
     k.fq_h = (float)fq;
     k.fq_l = (float)(fq - (double)k.fq_h);
-    k.mb2l2e_h = (float)mb;
-    k.mb2l2e_l = (float)(mb - (double)k.mb2l2e_h);
-    k.beta_h = (float)p.ewald_beta;
-    k.beta_l = (float)(p.ewald_beta - (double)k.beta_h);
     k.mods = p.modifiers;
     const double irc6 = 1.0 / (p.rc * p.rc * p.rc * p.rc * p.rc * p.rc);
     k.irc6_h = (float)irc6;
@@ -487,9 +555,13 @@ KParams make_kparams(const nb_sys* s) {
     k.gtab = reinterpret_cast<const float4*>(s->d_lj + 2 * (size_t)p.ntypes * p.ntypes);
     k.gt_n = 0;
     k.gt_invh = 0.f;
+    k.etab = reinterpret_cast<const float4*>(s->d_lj + etab_offset2(p.ntypes));
+    k.et_n = 0;
+    k.et_invh = 0.f;
     if (p.coul == NB_COUL_EWALD) {
-        float4 tab[GT_MAX];
-        k.gt_n = ewald_force_table(p.ewald_beta, p.rc, tab, &k.gt_invh);
+        std::vector<float4> tab(2 * (size_t)std::max(GT_MAX, ET_MAX));
+        k.gt_n = ewald_force_table(p.ewald_beta, p.rc, tab.data(), &k.gt_invh);
+        k.et_n = ewald_energy_table(p.ewald_beta, p.rc, tab.data(), &k.et_invh);
     }
     return k;
 }
@@ -522,7 +594,7 @@ nb_status plan_alloc_inner(Plan* pl) {
         return NB_OK;
     plan_free_inner(pl);
     const size_t items = (size_t)pl->list.item_cap, entries = (size_t)pl->list.entry_cap;
-    size_t bytes = align256(16 * items) + align256(4 * items) + align256(4 * entries) + align256(8 * entries) +
+    size_t bytes = align256(16 * items) + align256(4 * items) + 2 * align256(4 * entries) + align256(8 * entries) +
                    align256(8 * entries) + align256(4 * CNT_N);
     void* blk = nullptr;
     nb_status s = dev_alloc(pl->ctx, &blk, bytes);
@@ -533,6 +605,8 @@ nb_status plan_alloc_inner(Plan* pl) {
     pl->inner.order = (int*)b;
     b += align256(4 * items);
     pl->inner.cj = (int*)b;
+    b += align256(4 * entries);
+    pl->inner.cjb = (int*)b;
     b += align256(4 * entries);
     pl->inner.mask = (unsigned long long*)b;
     b += align256(8 * entries);
@@ -559,7 +633,7 @@ void plan_drop_graphs(Plan* pl) {
 nb_status plan_alloc_list(Plan* pl, long long items, long long entries) {
     items = std::min<long long>(items, (1ll << 31) - 1);
     entries = std::min<long long>(entries, (1ll << 31) - 1);
-    size_t bytes = align256(16 * (size_t)items) + align256(4 * (size_t)items) + align256(4 * (size_t)entries) +
+    size_t bytes = align256(16 * (size_t)items) + align256(4 * (size_t)items) + 2 * align256(4 * (size_t)entries) +
                    align256(8 * (size_t)entries) + align256(8 * (size_t)entries) + align256(4 * CNT_N);
     void* blk = nullptr;
     nb_status s = dev_alloc(pl->ctx, &blk, bytes);
@@ -571,6 +645,8 @@ nb_status plan_alloc_list(Plan* pl, long long items, long long entries) {
     pl->list.order = (int*)b;
     b += align256(4 * (size_t)items);
     pl->list.cj = (int*)b;
+    b += align256(4 * (size_t)entries);
+    pl->list.cjb = (int*)b;
     b += align256(4 * (size_t)entries);
     pl->list.mask = (unsigned long long*)b;
     b += align256(8 * (size_t)entries);
@@ -698,10 +774,15 @@ nb_status stage_coords(nb_sys* s, const float* xq, const int* type) {
     return NB_OK;
 }
 
+// The j-cluster geometry of the list the next build writes (the context's
+// nb_tuning.jcluster); the evaluations of that list read it from the list.
+void plan_set_geometry(Plan* pl) { pl->list.jgeo = pl->ctx->tuning.jcluster == 4 ? 1 : 0; }
+
 // Search + prune with capacity growth.  Synchronises the stream.
 nb_status plan_build_list(Plan* pl) {
     cudaStream_t st = pl->ctx->stream;
     pl->use_inner = false;  // a new outer list supersedes any inner one
+    plan_set_geometry(pl);
     for (int attempt = 0; attempt < 4; ++attempt) {
         NB_CK(cudaMemsetAsync(pl->list.counters + CNT_ITEMS, 0, 4 * 2, st));
         NB_CK(cudaMemsetAsync(pl->list.counters + CNT_PRUNED, 0, 4 * (CNT_N - CNT_PRUNED), st));
@@ -983,6 +1064,8 @@ nb_status nb_ctx_set_tuning(nb_ctx* ctx, const nb_tuning* t) {
     if (t->force_min_blocks < 1 || t->force_min_blocks > 3) return fail(NB_ERR_ARG, "force_min_blocks must be 1, 2 or 3");
     if (t->search_mode < 0 || t->search_mode > 2) return fail(NB_ERR_ARG, "search_mode must be 0, 1 or 2");
     if (t->energy_mode < 0 || t->energy_mode > 1) return fail(NB_ERR_ARG, "energy_mode must be 0 or 1");
+    if (t->jcluster != 0 && t->jcluster != 8 && t->jcluster != 4)
+        return fail(NB_ERR_ARG, "jcluster must be 0, 8 or 4");
     ctx->tuning = *t;
     ctx->tuning_gen += 1;
     return NB_OK;
@@ -1093,7 +1176,7 @@ static nb_status sys_create(nb_ctx* ctx, const nb_params* params, int natoms, co
     h.excl_index = nullptr;
     h.excl_atoms = nullptr;
     // parameter tables: the Lennard-Jones pairs, then (Ewald) the force table
-    std::vector<float2> lj(2 * nt * nt + 2 * (size_t)GT_MAX);
+    std::vector<float2> lj(etab_offset2(nt) + 4 * (size_t)ET_MAX, make_float2(0.f, 0.f));
     for (int k = 0; k < nt * nt; ++k) {
         lj[k] = make_float2(6.0f * y->c6[k], 12.0f * y->c12[k]);
         lj[nt * nt + k] = make_float2(y->c6[k], y->c12[k]);
@@ -1102,9 +1185,13 @@ static nb_status sys_create(nb_ctx* ctx, const nb_params* params, int natoms, co
     if (y->p.coul == NB_COUL_EWALD) {
         float invh = 0.f;
         gt_n = ewald_force_table(y->p.ewald_beta, y->p.rc, reinterpret_cast<float4*>(lj.data() + 2 * nt * nt), &invh);
+        float einvh = 0.f;
+        ewald_energy_table(y->p.ewald_beta, y->p.rc, reinterpret_cast<float4*>(lj.data() + etab_offset2(nt)), &einvh);
     }
-    cudaError_t e = cudaMemcpyAsync(y->d_lj, lj.data(), 8 * (2 * (size_t)nt * nt + 2 * (size_t)gt_n),
-                                    cudaMemcpyHostToDevice, ctx->stream);
+    // the whole table block when there are Ewald tables, else the
+    // Lennard-Jones pairs only
+    const size_t n2 = gt_n > 0 ? lj.size() : 2 * (size_t)nt * nt;
+    cudaError_t e = cudaMemcpyAsync(y->d_lj, lj.data(), 8 * n2, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h.acc, 0, 8 * NACC, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h.res, 0, 8 * NRES, ctx->stream);
     if (e != cudaSuccess) {
@@ -1240,6 +1327,7 @@ nb_status nb_pairlist_prune(nb_sys* sys, double r_inner) {
     double maxL = std::max(sys->box[0], std::max(sys->box[1], sys->box[2]));
     double r = r_inner + 1e-5 * (1.0 + maxL);
     pl->use_inner = false;
+    pl->inner.jgeo = pl->list.jgeo;
     PlanLaunch p = launch_of(pl);
     {
         StageScope sc(sys->ctx, NB_STAGE_PRUNE);
@@ -1281,6 +1369,27 @@ nb_status nb_eval_info(nb_sys* sys, nb_eval_stats* stats) {
     return NB_OK;
 }
 
+nb_status nb_ewald_energy_table(double beta, double rc, float* coef, int max_intervals, int* n_intervals,
+                                double* h) {
+    if (!(beta > 0) || !(rc > 0) || !(beta * rc <= 10.0)) return fail(NB_ERR_ARG, "need beta > 0, rc > 0, beta rc <= 10");
+    if (!n_intervals) return fail(NB_ERR_ARG, "n_intervals is NULL");
+    std::vector<float4> tab(2 * (size_t)ET_MAX);
+    float invh = 0.f;
+    const int K = ewald_energy_table(beta, rc, tab.data(), &invh);
+    if (K <= 0) return fail(NB_ERR_ARG, "the table needs more intervals than it may hold");
+    *n_intervals = K;
+    if (h) *h = 1.0 / (double)invh;
+    if (coef) {
+        if (max_intervals < K) return fail(NB_ERR_ARG, "coef holds fewer intervals than the table");
+        for (int k = 0; k < K; ++k) {
+            const float4 a = tab[(size_t)k], b = tab[(size_t)ET_MAX + k];
+            const float row[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            std::memcpy(coef + 8 * (size_t)k, row, sizeof(row));
+        }
+    }
+    return NB_OK;
+}
+
 nb_status nb_ewald_force_table(double beta, double rc, float* coef, int max_intervals, int* n_intervals,
                                double* h) {
     if (!(beta > 0) || !(rc > 0) || !(beta * rc <= 10.0)) return fail(NB_ERR_ARG, "need beta > 0, rc > 0, beta rc <= 10");
@@ -1298,10 +1407,10 @@ nb_status nb_ewald_force_table(double beta, double rc, float* coef, int max_inte
     return NB_OK;
 }
 
-nb_status nb_pairlist_export(nb_sys* sys, int* perm, int* items, int* cj, unsigned long long* mask,
-                             long long* n_entries_total) {
-    if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
-    if (!sys->listed) return fail(NB_ERR_STATE, "no pair list");
+// The list's items and masks (and, for a list of the 8 x 8 geometry, its
+// j-clusters) in host or device arrays.
+static nb_status nb_pairlist_export_any(nb_sys* sys, int* perm, int* items, int* cj, unsigned long long* mask,
+                                        long long* n_entries_total) {
     nb_list_info info;
     nb_status s = nb_pairlist_info(sys, &info);
     if (s != NB_OK) return s;
@@ -1323,6 +1432,37 @@ nb_status nb_pairlist_export(nb_sys* sys, int* perm, int* items, int* cj, unsign
     if (cj) NB_CK(cudaMemcpyAsync(cj, pl->list.cj, 4 * (size_t)ne, cudaMemcpyDefault, st));
     if (mask) NB_CK(cudaMemcpyAsync(mask, pl->list.mask, 8 * (size_t)ne, cudaMemcpyDefault, st));
     NB_CK(cudaStreamSynchronize(st));
+    return NB_OK;
+}
+
+nb_status nb_pairlist_export(nb_sys* sys, int* perm, int* items, int* cj, unsigned long long* mask,
+                             long long* n_entries_total) {
+    if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
+    if (!sys->listed) return fail(NB_ERR_STATE, "no pair list");
+    if (cj && sys->plan->list.jgeo)
+        return fail(NB_ERR_STATE, "the list has 4-atom j-clusters: nb_pairlist_export_slots gives its j-atoms");
+    return nb_pairlist_export_any(sys, perm, items, cj, mask, n_entries_total);
+}
+
+nb_status nb_pairlist_export_slots(nb_sys* sys, int* perm, int* items, int* jslot, unsigned long long* mask,
+                                   long long* n_entries_total) {
+    if (!sys) return fail(NB_ERR_ARG, "sys is NULL");
+    if (!sys->listed) return fail(NB_ERR_STATE, "no pair list");
+    long long ne = 0;
+    nb_status s = nb_pairlist_export_any(sys, perm, items, nullptr, mask, &ne);
+    if (s != NB_OK) return s;
+    if (n_entries_total) *n_entries_total = ne;
+    if (!jslot || ne == 0) return NB_OK;
+    Plan* pl = sys->plan;
+    cudaStream_t st = sys->ctx->stream;
+    std::vector<int> a((size_t)ne), b(pl->list.jgeo ? (size_t)ne : 0);
+    NB_CK(cudaMemcpyAsync(a.data(), pl->list.cj, 4 * (size_t)ne, cudaMemcpyDeviceToHost, st));
+    if (pl->list.jgeo) NB_CK(cudaMemcpyAsync(b.data(), pl->list.cjb, 4 * (size_t)ne, cudaMemcpyDeviceToHost, st));
+    NB_CK(cudaStreamSynchronize(st));
+    for (long long e = 0; e < ne; ++e) {
+        jslot[2 * e] = pl->list.jgeo ? a[(size_t)e] : a[(size_t)e] * CL;
+        jslot[2 * e + 1] = pl->list.jgeo ? b[(size_t)e] + 4 : a[(size_t)e] * CL + 4;
+    }
     return NB_OK;
 }
 
@@ -1396,6 +1536,7 @@ nb_status nb_batch_destroy(nb_batch* batch) {
 
 static nb_status batch_record(Plan* pl, unsigned flags) {
     cudaStream_t st = pl->ctx->stream;
+    plan_set_geometry(pl);
     PlanLaunch p = launch_of(pl);
     // per-stage timing applies when the sequence runs directly (not captured)
     NB_CK(cudaMemsetAsync(pl->list.counters, 0, 4 * CNT_N, st));

@@ -11,11 +11,11 @@
 //   y = rsqrt(r^2_hi) and the residual h = 1 - r^2 y^2 computed with fused
 //   multiply-adds, and then
 //   RF:    V = f qi qj (1/r + k_rf r^2 - c_rf) fully in double-float;
-//   Ewald: V = f qi qj erfc(b r)/r with erfc(x) = exp(-x^2) R(u) from the
-//          degree-12 fit and exp(-x^2) = 2^a by exact range reduction and
-//          the degree-10 fit of 2^f (no SFU approximation); x = b r, t, u
-//          and the large head terms of both polynomials in double-float
-//          (compensated Horner), their small tails in float32;
+//   Ewald: V = f qi qj erfc(b r)/r, r = r^2 (1/r) in double-float and
+//          erfc(b r) from a table of quartics in s = r / h - k (interval
+//          width h = 2^-n, built on the host by ewald_energy_table): the
+//          constant and linear terms in double-float, the small rest in
+//          float32 (error at most about 1.3e-11, no SFU approximation);
 //   LJ:    c12 r^-12, c6 r^-6 in float32 from the accurate 1/r and the
 //          unscaled c6, c12 (pre-scaled 6 c6, 12 c12 would round).
 // With the potential-shift modifiers the LJ terms become c12 (r^-12 -
@@ -62,6 +62,18 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     const int w = threadIdx.x >> 5;
     const int nt = kp.ntypes;
     for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) s_lj[k] = kp.lje[k];
+    // the Ewald energy table after the Lennard-Jones pairs (16-byte aligned)
+    float4* const s_et = reinterpret_cast<float4*>(s_lj + ((nt * nt + 1) & ~1));
+    const int etn = COUL == NB_COUL_EWALD ? kp.et_n : 0;
+    for (int k = threadIdx.x; k < etn; k += blockDim.x) {
+        s_et[k] = kp.etab[k];
+        s_et[etn + k] = kp.etab[ET_MAX + k];
+    }
+    EwaldE et;
+    et.a = s_et;
+    et.b = s_et + etn;
+    et.invh = kp.et_invh;
+    et.last = (unsigned)max(etn - 1, 0);
     __syncthreads();
 
     float4* sjg = &s_j[w][g][0];
@@ -124,19 +136,19 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             const int h = i >> 1;
             int e = jb + g;
             unsigned pmk = 0u;
-            int pj = 0;
+            int pjl = 0, pjh = 0;
             if (e < je) {
                 pmk = list.marks[(size_t)e * CL + i];
-                pj = list.cj[e] * CL;
+                entry_slots(list, e, pjl, pjh);
             }
             for (int base = jb; base < je; base += 4) {
                 const unsigned mk = pmk;
-                const int cj0 = pj;
+                const int cjl0 = pjl, cjh0 = pjh;
                 e = base + 4 + g;
                 pmk = 0u;
                 if (e < je) {
                     pmk = list.marks[(size_t)e * CL + i];
-                    pj = list.cj[e] * CL;
+                    entry_slots(list, e, pjl, pjh);
                 }
                 // bit b: j-slot 2 ((b >> 1) XOR h) + (b & 1) is queued (the
                 // drain finds the band pairs from its own distances)
@@ -147,13 +159,13 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
                     if (q) {
                         const int js = 2 * ((b >> 1) ^ h) + (b & 1);
                         const int pos = (tail + __popc(bal & ((1u << lane) - 1u))) & (QCAP - 1);
-                        qm[pos] = ((cj0 + js) << 4) | (i << 1);
+                        qm[pos] = ((js + (js < 4 ? cjl0 : cjh0)) << 4) | (i << 1);
                     }
                     tail += __popc(bal);
                 }
                 __syncwarp();
                 while (tail - head >= 64) {
-                    drain2<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e12l, e6, e6l,
+                    drain2<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, et, ch, cl, e12, e12l, e6, e6l,
                                        npair, true, true);
                     head += 64;
                 }
@@ -162,25 +174,25 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         int e = jb + g;
         bool act = e < je;
         unsigned long long pm = 0ull;
-        int pj = 0;
+        int pjl = 0, pjh = 0;
         float4 pxq = make_float4(0.f, 0.f, 0.f, 0.f);
         if (act) {
-            pj = list.cj[e] * CL;
+            entry_slots(list, e, pjl, pjh);
             pm = list.mask[e];
-            pxq = xq_s[pj + i];
+            pxq = xq_s[i + (i < 4 ? pjl : pjh)];
         }
         for (int base = jb; base < je; base += 4) {
             __syncwarp();
             sjg[i] = pxq;
-            const int cj0 = pj;
+            const int cjl0 = pjl, cjh0 = pjh;
             const unsigned long long cm = pm;
             e = base + 4 + g;
             act = e < je;
             pm = 0ull;
             if (act) {
-                pj = list.cj[e] * CL;
+                entry_slots(list, e, pjl, pjh);
                 pm = list.mask[e];
-                pxq = xq_s[pj + i];
+                pxq = xq_s[i + (i < 4 ? pjl : pjh)];
             }
             __syncwarp();
             const unsigned row = (unsigned)(cm >> (8 * i)) & 0xffu;
@@ -197,20 +209,20 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
                 const unsigned bal = __ballot_sync(FULL, q);
                 if (q) {
                     const int pos = (tail + __popc(bal & ((1u << lane) - 1u))) & (QCAP - 1);
-                    qm[pos] = ((cj0 + js) << 4) | (i << 1) | (int)maybe;
+                    qm[pos] = ((js + (js < 4 ? cjl0 : cjh0)) << 4) | (i << 1) | (int)maybe;
                 }
                 tail += __popc(bal);
             }
             __syncwarp();
             while (tail - head >= 64) {
-                drain2<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e12l, e6, e6l,
+                drain2<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, et, ch, cl, e12, e12l, e6, e6l,
                                    npair, true, true);
                 head += 64;
             }
         }
         }
         if (tail > head)
-            drain2<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, ch, cl, e12, e12l, e6, e6l, npair,
+            drain2<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lj, kp, et, ch, cl, e12, e12l, e6, e6l, npair,
                                lane < tail - head, lane + 32 < tail - head);
         dec += ((double)ch.x + (double)cl.x) + ((double)ch.y + (double)cl.y);
         d12 += ((double)e12.x + (double)e12l.x) + ((double)e12.y + (double)e12l.y);
@@ -222,7 +234,9 @@ k_energy(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
 
 template <int COUL, bool LJSH>
 cudaError_t launch_energy_t(const PlanLaunch& p, cudaStream_t st) {
-    size_t smem = (size_t)p.kp.ntypes * p.kp.ntypes * sizeof(float2);
+    // Lennard-Jones pairs, then (Ewald) the energy table's two halves
+    const size_t nt2 = (size_t)p.kp.ntypes * p.kp.ntypes;
+    size_t smem = ((nt2 + 1) & ~(size_t)1) * sizeof(float2) + (COUL == NB_COUL_EWALD ? 32 * (size_t)p.kp.et_n : 0);
     auto kern = energy_marks(p, NB_F_ENERGY) ? k_energy<COUL, LJSH, true> : k_energy<COUL, LJSH, false>;
     int per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, EW * 32, smem);

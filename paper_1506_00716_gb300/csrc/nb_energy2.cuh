@@ -1,11 +1,10 @@
 // nb_energy2.cuh -- double-float pair energies, shared by the energy kernel
-// (k_energy) and the force kernel's fused energy variant: the compensated
-// erfc and 2^a, the energy of two queued pairs at a time (the halves of the
-// paired float32 instructions), and the drain of a warp's queue of pairs
-// inside (or near) the cut-off.  nb_energy.cu describes the arithmetic.
+// (k_energy) and the force kernel's fused energy variant: erfc from the
+// Ewald energy table, the energy of two queued pairs at a time (the halves
+// of the paired float32 instructions), and the drain of a warp's queue of
+// pairs inside (or near) the cut-off.  nb_energy.cu describes the arithmetic.
 #pragma once
 
-#include "erfc_fit.cuh"
 #include "nb_device.cuh"
 #include "nb_pair2.cuh"
 
@@ -15,69 +14,48 @@ namespace {
 
 constexpr unsigned EFULL = FULL_MASK;
 
-// Number of head coefficients evaluated in double-float; the tail terms are
-// small enough (|a_k u^k| <= 5e-4) for plain float32.
-constexpr int EF_HEAD = 5;   // erfc fit: k = 0..4
-constexpr int EX2_HEAD = 4;  // 2^f fit: k = 0..3
+// The Ewald energy table as the energy code reads it (KParams::etab): per
+// interval k, a[k] = (a0 hi, a0 lo, a1 hi, a1 lo) and b[k] = (a2, a3, a4, -)
+// of erfc(beta r) ~ a0 + a1 s + a2 s^2 + a3 s^3 + a4 s^4, s = r / h - k.
+struct EwaldE {
+    const float4* a;
+    const float4* b;
+    float invh;     // 1 / h (a power of two)
+    unsigned last;  // intervals - 1
+};
 
-// Horner steps over coefficients hi[k] + lo[k], k = k1 .. 0, in compensated
-// (double-float) arithmetic, p = p * u + c with p, u, c all hi + lo; for two
-// arguments (the halves).
-template <int K1>
-__device__ __forceinline__ void horner_dd2(const float* hi, const float* lo, float2 uh, float2 ul, float2& ph,
-                                           float2& pl) {
-#pragma unroll
-    for (int k = K1; k >= 0; --k) {
-        float2 m, me, sum, se;
-        two_prod2(ph, uh, m, me);
-        const float2 cross = fma2(ph, ul, mul2(pl, uh));
-        two_sum2(m, dup2(hi[k]), sum, se);
-        ph = sum;
-        pl = add2(add2(add2(me, se), cross), dup2(lo[k]));
-    }
-}
+// 1.5 * 2^23: a float in [2^23, 2^24) holds an integer in its mantissa
+constexpr float ET_MAGIC = 12582912.f;
 
-// erfc(x) in double-float for x = xh + xl >= 0, from the degree-12 fit and
-// the double-float exponential 2^a, a = ah + al = -x^2 log2(e) (given); for
-// two arguments (the halves).  Steps: d = 1 + P x; t = 1/d by a refined SFU
-// reciprocal; u = UA t + UB; R(u) with a float32 tail and a double-float
-// head; 2^a = 2^n 2^f with f = (ah - n) + al in [-0.5, 0.5] (ah - n exact);
-// erfc = R 2^a.
-__device__ __forceinline__ void erfc_dd2(float2 xh, float2 xl, float2 ah, float2 al, float2& eh, float2& el) {
-    const bool c0 = xh.x > EF_XMAX, c1 = xh.y > EF_XMAX;
-    xh = sel2(c0, c1, dup2(EF_XMAX), xh);
-    xl = sel2(c0, c1, dup2(0.f), xl);
-    float2 m, me, dh, de;
-    two_prod2(dup2(EF_P), xh, m, me);
-    two_sum2(dup2(1.f), m, dh, de);
-    const float2 dl = add2(de, fma2(dup2(EF_P), xl, me));
-    float2 th = make_float2(rcp_sfu(dh.x), rcp_sfu(dh.y));
-    th = mul2(th, fma2(neg2(dh), th, dup2(2.f)));
-    float2 r = fma2(neg2(dh), th, dup2(1.f));
-    r = fma2(neg2(dl), th, r);
-    const float2 tl = mul2(th, r);
-    float2 uh, ue, sh, se;
-    two_prod2(dup2(EF_UA), th, uh, ue);
-    two_sum2(uh, dup2(EF_UB), sh, se);
-    const float2 ul = add2(se, fma2(dup2(EF_UA), tl, ue));
-    uh = sh;
-    float2 ph = dup2(EF_EN_HI[EF_NE - 1]), pl = dup2(0.f);
-#pragma unroll
-    for (int k = EF_NE - 2; k >= EF_HEAD; --k) ph = fma2(ph, uh, dup2(EF_EN_HI[k]));
-    horner_dd2<EF_HEAD - 1>(EF_EN_HI, EF_EN_LO, uh, ul, ph, pl);
-    ah = make_float2(fmaxf(ah.x, -120.f), fmaxf(ah.y, -120.f));
-    const float2 n = make_float2(rintf(ah.x), rintf(ah.y));
-    const float2 fh = sub2(ah, n);
-    float2 qh = dup2(EX2_HI[EX2_N - 1]), ql = dup2(0.f);
-#pragma unroll
-    for (int k = EX2_N - 2; k >= EX2_HEAD; --k) qh = fma2(qh, fh, dup2(EX2_HI[k]));
-    horner_dd2<EX2_HEAD - 1>(EX2_HI, EX2_LO, fh, al, qh, ql);
-    const float2 scale = make_float2(__int_as_float(((int)n.x + 127) << 23), __int_as_float(((int)n.y + 127) << 23));
-    float2 ch, ce;
-    two_prod2(ph, qh, ch, ce);
-    const float2 cl = add2(ce, fma2(ph, ql, mul2(pl, qh)));
-    eh = mul2(ch, scale);
-    el = mul2(cl, scale);
+// erfc(beta r) in double-float for r = rh + rl >= 0, from the table; two
+// arguments (the halves).  Interval k = floor(rh / h) by a round-down fused
+// multiply-add onto 1.5 * 2^23 (clamped to the table: far and masked slots
+// give finite values that the caller discards), s = sh + sl with sh = rh / h
+// - k exact and sl = rl / h; then a0 + a1 s in double-float (the product of
+// the high parts error-free, the terms of sl and of the low parts to first
+// order) plus s^2 (a2 + s (a3 + s a4)) in float32, whose rounding (the
+// quadratic coefficient is at most 1e-4) stays below 1e-11.
+__device__ __forceinline__ void erfc_tab2(float2 rh, float2 rl, const EwaldE& et, float2& eh, float2& el) {
+    const float2 m = __ffma2_rd(rh, dup2(et.invh), dup2(ET_MAGIC));
+    const float2 sh = fma2(rh, dup2(et.invh), sub2(dup2(ET_MAGIC), m));
+    const float2 sl = mul2(rl, dup2(et.invh));
+    const unsigned k0 = min((unsigned)(__float_as_int(m.x) - __float_as_int(ET_MAGIC)), et.last);
+    const unsigned k1 = min((unsigned)(__float_as_int(m.y) - __float_as_int(ET_MAGIC)), et.last);
+    const float4 a0 = et.a[k0], a1 = et.a[k1];
+    const float4 b0 = et.b[k0], b1 = et.b[k1];
+    float2 t = fma2(make_float2(b0.z, b1.z), sh, make_float2(b0.y, b1.y));
+    t = fma2(t, sh, make_float2(b0.x, b1.x));
+    // s^2 t, to first order in sl: t sh (sh + 2 sl)
+    const float2 q = mul2(mul2(t, sh), fma2(dup2(2.f), sl, sh));
+    const float2 c1h = make_float2(a0.z, a1.z), c1l = make_float2(a0.w, a1.w);
+    float2 p, pe;
+    two_prod2(c1h, sh, p, pe);
+    const float2 low = fma2(c1h, sl, fma2(c1l, sh, pe));
+    float2 p2, e1, vh, e2;
+    two_sum2(p, q, p2, e1);
+    two_sum2(make_float2(a0.x, a1.x), p2, vh, e2);
+    const float2 vl = add2(add2(e1, e2), add2(low, make_float2(a0.y, a1.y)));
+    fast_two_sum2(vh, vl, eh, el);
 }
 
 // Energy of two queued pairs (the halves).  `valid`: the lane's half holds
@@ -95,7 +73,8 @@ template <int COUL, bool LJSH>
 __device__ __forceinline__ void pair_energy2(const float4 xj0, const float4 xj1, float2 c6, float2 c12,
                                              const IPair2& ip, const ShiftedI& xs0, const ShiftedI& xs1,
                                              bool valid0, bool valid1, bool maybe0, bool maybe1,
-                                             const KParams& kp, float2& ch, float2& cl, float2& e12,
+                                             const KParams& kp, const EwaldE& et, float2& ch, float2& cl,
+                                             float2& e12,
                                              float2& e12l, float2& e6, float2& e6l, int& npair) {
     float2 dxh, dxe, dyh, dye, dzh, dze;
     two_diff2(ip.xh, make_float2(xj0.x, xj1.x), dxh, dxe);
@@ -191,14 +170,8 @@ __device__ __forceinline__ void pair_energy2(const float4 xj0, const float4 xj1,
         float2 rh, re;
         two_prod2(r2h, y, rh, re);
         const float2 rl = add2(re, fma2(r2h, ril, mul2(r2l, y)));
-        float2 xh, xe;
-        two_prod2(dup2(kp.beta_h), rh, xh, xe);
-        const float2 xl = add2(xe, fma2(dup2(kp.beta_h), rl, mul2(dup2(kp.beta_l), rh)));
-        float2 ah, ae;
-        two_prod2(dup2(kp.mb2l2e_h), r2h, ah, ae);
-        const float2 al = fma2(dup2(kp.mb2l2e_h), r2l, fma2(dup2(kp.mb2l2e_l), r2h, ae));
         float2 eh, el;
-        erfc_dd2(xh, xl, ah, al, eh, el);
+        erfc_tab2(rh, rl, et, eh, el);
         float2 wh, we;
         two_prod2(eh, y, wh, we);
         float2 wl = add2(we, fma2(eh, ril, mul2(el, y)));
@@ -254,7 +227,8 @@ struct IRec {
 template <int COUL, bool LJSH>
 __device__ __forceinline__ void drain2(int k, const int* __restrict__ qm, const IRec* __restrict__ irec,
                                        const float4* __restrict__ xq_s, const int* __restrict__ type_s,
-                                       const float2* __restrict__ s_lj, const KParams& kp, float2& ch,
+                                       const float2* __restrict__ s_lj, const KParams& kp, const EwaldE& et,
+                                       float2& ch,
                                        float2& cl, float2& e12, float2& e12l, float2& e6, float2& e6l,
                                        int& npair, bool valid0, bool valid1) {
     const int m0 = valid0 ? qm[k & (QCAP - 1)] : 0;
@@ -278,7 +252,7 @@ __device__ __forceinline__ void drain2(int k, const int* __restrict__ qm, const 
     ip.qil = make_float2(r0.qil, r1.qil);
     const float2 l0 = s_lj[r0.tirow + tj0], l1 = s_lj[r1.tirow + tj1];
     pair_energy2<COUL, LJSH>(xj0, xj1, make_float2(l0.x, l1.x), make_float2(l0.y, l1.y), ip, r0.xs, r1.xs, valid0,
-                             valid1, m0 & 1, m1 & 1, kp, ch, cl, e12, e12l, e6, e6l, npair);
+                             valid1, m0 & 1, m1 & 1, kp, et, ch, cl, e12, e12l, e6, e6l, npair);
 }
 
 }  // namespace

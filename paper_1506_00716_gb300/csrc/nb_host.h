@@ -120,6 +120,9 @@ void dev_free(nb_ctx* ctx, void* ptr, size_t bytes);
 // boost scales the estimated list capacity (retries after an overflow)
 nb_status plan_create(nb_ctx* ctx, nb_sys* const* systems, int n, Plan** out, double boost = 1.0);
 void plan_destroy(Plan* pl);
+// Set the geometry of the list the next search and prune write (from the
+// context's tuning); call before launch_of of a build.
+void plan_set_geometry(Plan* pl);
 PlanLaunch launch_of(const Plan* pl);
 nb_status stage_coords(nb_sys* s, const float* xq, const int* type);
 // Symmetric, sorted, duplicate-free exclusion CSR from the caller's CSR

@@ -20,6 +20,7 @@ constexpr int SHIFT_ZERO = 13;     // index of the zero shift
 constexpr int SEARCH_BUF = 384;    // entries a search warp buffers before flushing
 constexpr int EXCL_BUF = 128;      // exclusion partners a search warp caches
 constexpr int GT_MAX = 2048;       // intervals of the Ewald force table, at most
+constexpr int ET_MAX = 2048;       // intervals of the Ewald energy table, at most
 
 // Counter slots of a list (ListDev::counters).
 enum {
@@ -108,7 +109,19 @@ constexpr int NRES = 15;
 // Per-plan (one system, or one batch of systems) cluster-pair list.
 struct ListDev {
     int4* items;         // (ci, first entry, end entry, sys << 5 | shift)
-    int* cj;             // j-cluster per entry
+    // j-atoms of an entry, by geometry (jgeo):
+    //   0 (M x N = 8 x 8): cj = the j-cluster; j-slot t is sorted slot 8 cj + t.
+    //   1 (8 x 4, two 4-atom j-clusters per entry): the j-clusters are the
+    //     halves (z-halves after the column sort) of the 8-atom clusters;
+    //     j-slots 0-3 are slots cj + t, j-slots 4-7 are slots cjb + t, i.e.
+    //     cj is the first slot of the first half and cjb + 4 that of the
+    //     second.  The prune writes this form, pairing the halves that keep
+    //     a pair within the list radius two by two in each item; an item's
+    //     odd last half is paired with itself under a zero mask.
+    // Search output (before the prune) is always of the first form.
+    int* cj;
+    int* cjb;            // [entry_cap] with jgeo = 1, else unused
+    int jgeo;
     unsigned long long* mask;  // 8x8 interaction bits per entry (rotated layout)
     // per entry and i-row (entry * 8 + i-slot), written by the force kernel of
     // an evaluation with energies: the slots inside rc or in the band around
@@ -132,6 +145,22 @@ struct ListDev {
 constexpr int LPT_ITEMS_PER_WARP = 4;
 constexpr int LPT_WARPS_PER_SM = 24;
 
+// Bits of j-slots 0-3 in the rotated mask layout (bit 8 i + (j XOR i) for
+// the pair of i-slot i and j-slot j): the low nibble of bytes 0-3 and the
+// high nibble of bytes 4-7.  j-slots 4-7 hold the complement.
+constexpr unsigned long long MASK_JLO = 0xF0F0F0F00F0F0F0Full;
+
+// First sorted slot of j-slots 0-3 (lo) and j-slots 4-7 minus 4 (hi) of
+// entry e: j-slot t lies at slot t + (t < 4 ? lo : hi).
+__device__ __forceinline__ void entry_slots(const ListDev& list, int e, int& lo, int& hi) {
+    if (list.jgeo) {
+        lo = list.cj[e];
+        hi = list.cjb[e];
+    } else {
+        lo = hi = list.cj[e] * 8;
+    }
+}
+
 // Item index of the k-th item in evaluation order (k < n_long + n_short).
 __device__ __forceinline__ int ordered_item(const ListDev& list, int k, int n_long) {
     return k < n_long ? list.order[k] : list.order[list.item_cap - 1 - (k - n_long)];
@@ -147,8 +176,6 @@ struct KParams {
     float beta;          // Ewald splitting parameter
     // double-float (hi + lo) constants of the energy kernel
     float krf_h, krf_l, crf_h, crf_l, fq_h, fq_l;
-    float mb2l2e_h, mb2l2e_l;  // -beta^2 log2(e)
-    float beta_h, beta_l;
     int coul;
     int ntypes;
     unsigned mods;       // NB_MOD_* potential modifiers
@@ -173,6 +200,13 @@ struct KParams {
     const float4* gtab;  // [gt_n]
     int gt_n;            // intervals (0: reaction field)
     float gt_invh;
+    // Ewald energy table (energy kernels): erfc(beta r) on intervals of
+    // width h = 1 / et_invh as quartics in s = r / h - k, interval k at
+    // etab[k] = (a0 hi, a0 lo, a1 hi, a1 lo) and etab[ET_MAX + k] =
+    // (a2, a3, a4, 0), the constant and linear coefficients as hi + lo
+    const float4* etab;  // [2 * ET_MAX]
+    int et_n;            // intervals (0: reaction field)
+    float et_invh;
     const float2* lj;    // [ntypes^2] (6 c6, 12 c12), force kernel
     const float2* lje;   // [ntypes^2] (c6, c12), energy kernel
 };
@@ -285,7 +319,12 @@ __device__ __forceinline__ float3 shift_vec(int sh, const float (&L)[3], const f
 
 // Bytes of a system's parameter tables: the Lennard-Jones tables ((6 c6, 12
 // c12) then (c6, c12), 16 per type pair) and the Ewald force table after them.
-inline size_t param_table_bytes(int ntypes) { return 16 * (size_t)ntypes * ntypes + 16 * (size_t)GT_MAX; }
+inline size_t param_table_bytes(int ntypes) {
+    return 16 * (size_t)ntypes * ntypes + 16 * (size_t)GT_MAX + 32 * (size_t)ET_MAX;
+}
+// Float2 offset of the Ewald energy table from the start of the parameter
+// tables (after both Lennard-Jones tables and the force table).
+inline size_t etab_offset2(int ntypes) { return 2 * (size_t)ntypes * ntypes + 2 * (size_t)GT_MAX; }
 // The Ewald force table for splitting parameter beta and cut-off rc: writes
 // up to GT_MAX float4 coefficients, sets *invh, returns the number of
 // intervals (0 if it would need more than GT_MAX; never for beta rc <= 10).
@@ -295,6 +334,17 @@ inline size_t param_table_bytes(int ntypes) { return 16 * (size_t)ntypes * ntype
 // h^4 / 384 max|d^4 G / dr^4| is at most 1e-7 of G at its far end (G
 // decreases; G taken as at least 1e-7), and the intervals reach rc (1 + 1e-4).
 int ewald_force_table(double beta, double rc, float4* coef, float* invh);
+// The Ewald energy table for beta and rc: writes 2 * ET_MAX float4 (the
+// KParams::etab layout; entries past the intervals are left as they are),
+// sets *invh, returns the number of intervals (0 if more than ET_MAX would
+// be needed; never for beta rc <= 10).  Interval k of width h = 2^-n covers
+// [k h, (k + 1) h); its quartic in s = r / h - k interpolates erfc(beta r)
+// at the five Chebyshev points of the interval, in float64.  h is the
+// largest power of two for which the interpolation error bound
+// 2 (h / 4)^5 max|d^5 erfc(beta r) / dr^5| / 5! is at most 1e-12 and the
+// quadratic coefficient, evaluated in float32, at most 1e-4 (so that its
+// float32 rounding is below 1e-11), with the intervals reaching rc (1 + 1e-4).
+int ewald_energy_table(double beta, double rc, float4* coef, float* invh);
 
 // Host helpers of nb_api.cu shared with the allocation-free entry point.
 nb_status api_fail(nb_status s, const char* msg);

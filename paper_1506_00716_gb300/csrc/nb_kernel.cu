@@ -310,6 +310,12 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     double dec = 0.0, d12 = 0.0, d6 = 0.0;
     long long np = 0;
 
+    // the energies' Ewald table (ENER), read through L1
+    EwaldE et;
+    et.a = kp.etab;
+    et.b = kp.etab + ET_MAX;
+    et.invh = kp.et_invh;
+    et.last = (unsigned)max(kp.et_n - 1, 0);
     EwaldC ew;
     ew.tab = reinterpret_cast<const float4*>(s_ljt + gt_offset(nt)) + (lane & ((1 << gt_lr) - 1));
     ew.invh = kp.gt_invh;
@@ -317,6 +323,11 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     ew.lr = gt_lr;
 
     float* const sjg = &s_j[w][g][0];
+    // the list's j-atoms of this lane's j-slot i: slot cjl[e] * jmul + i
+    // (ListDev: 8 x 8 entries name the j-cluster, 8 x 4 entries the first
+    // slot of each half, j-slots 4-7 offset by -4)
+    const int* const cjl = list.jgeo && i >= 4 ? list.cjb : list.cj;
+    const int jmul = list.jgeo ? 1 : CL;
     // where lane i stages j-slot i: x and y at 12 (i >> 1) + (i & 1) (+ 2),
     // z and q 4 floats further, the type 8 floats further
     const int st = JB_REC * h + odd;
@@ -400,16 +411,16 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         float4 pxq = make_float4(0.f, 0.f, 0.f, 0.f);
         int pty = 0;
         if (act) {
-            cjn = list.cj[e];
+            cjn = cjl[e];
             pm = list.mask[e];
-            pxq = xq_s[cjn * CL + i];
-            pty = type_s[cjn * CL + i];
+            pxq = xq_s[cjn * jmul + i];
+            pty = type_s[cjn * jmul + i];
         }
         // the list entries one step further ahead, so that the coordinate
         // loads of the next step never wait on them
         int e2 = jb + 4 + g;
         bool act2 = e2 < je;
-        int cjn2 = act2 ? list.cj[e2] : 0;
+        int cjn2 = act2 ? cjl[e2] : 0;
         unsigned long long pm2 = act2 ? list.mask[e2] : 0ull;
         for (int base = jb; base < je; base += 4) {
             __syncwarp();
@@ -425,15 +436,15 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
             cjn = cjn2;
             pm = pm2;
             if (act) {
-                pxq = xq_s[cjn * CL + i];
-                pty = type_s[cjn * CL + i];
+                pxq = xq_s[cjn * jmul + i];
+                pty = type_s[cjn * jmul + i];
             }
             e2 = base + 8 + g;
             act2 = e2 < je;
             cjn2 = 0;
             pm2 = 0ull;
             if (act2) {
-                cjn2 = list.cj[e2];
+                cjn2 = cjl[e2];
                 pm2 = list.mask[e2];
             }
             __syncwarp();
@@ -521,7 +532,7 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
                 fjt[1] += s_fix[w][g][i][1];
                 fjt[2] += s_fix[w][g][i][2];
             }
-            if (cact) atomicAdd(f_s + ccj * CL + i, make_float4(fjt[0], fjt[1], fjt[2], 0.f));
+            if (cact) atomicAdd(f_s + ccj * jmul + i, make_float4(fjt[0], fjt[1], fjt[2], 0.f));
             if (MARK && cact) list.marks[(size_t)(base + g) * CL + i] = (unsigned char)ebits;
             if (ENER) {
                 // queue this entry's candidate pairs (bit 2p + c: j-slot
@@ -535,15 +546,19 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
                 }
                 const int tot = __shfl_sync(FULL, incl, 31);
                 int pos = tail + incl - cnt;
+                // the slots of the entry's j-slots 0-3 and 4-7 (minus 4), from
+                // the group's lanes 0 and 4
+                const int jlo = __shfl_sync(FULL, ccj, 8 * g) * jmul, jhi = __shfl_sync(FULL, ccj, 8 * g + 4) * jmul;
                 for (unsigned bits = ebits; bits != 0u; bits &= bits - 1u, ++pos) {
                     const int t = __ffs(bits) - 1;
-                    const int js = ccj * CL + 2 * ((t >> 1) ^ h) + (t & 1);
+                    const int jt = 2 * ((t >> 1) ^ h) + (t & 1);
+                    const int js = jt + (jt < 4 ? jlo : jhi);
                     qm[pos & (QCAP - 1)] = (js << 4) | (i << 1) | (int)((mbits >> t) & 1u);
                 }
                 tail += tot;
                 __syncwarp();
                 while (tail - head >= 64) {
-                    drain2<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lje, kp, ch, cl, e12, e12l, e6, e6l,
+                    drain2<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lje, kp, et, ch, cl, e12, e12l, e6, e6l,
                                        npair, true, true);
                     head += 64;
                 }
@@ -551,7 +566,7 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
         }
         if (ENER) {
             if (tail > head)
-                drain2<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lje, kp, ch, cl, e12, e12l, e6, e6l, npair,
+                drain2<COUL, LJSH>(head + lane, qm, irec, xq_s, type_s, s_lje, kp, et, ch, cl, e12, e12l, e6, e6l, npair,
                                    lane < tail - head, lane + 32 < tail - head);
             dec += ((double)ch.x + (double)cl.x) + ((double)ch.y + (double)cl.y);
             d12 += ((double)e12.x + (double)e12l.x) + ((double)e12.y + (double)e12l.y);

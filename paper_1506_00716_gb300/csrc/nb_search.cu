@@ -619,7 +619,7 @@ constexpr int PRUNE_U = 2;
 
 // Prune (Section 3.3): drop the entries of which no atom pair whose mask bit
 // is set lies within the list radius.  A warp takes one work item at a time.
-// Per chunk of 32 entries, lane k loads entry k's j-cluster index and mask
+// Per chunk of 32 entries, lane k loads entry k's j-atoms' slots and mask
 // (coalesced).  Entries the search marked as certain are kept as they are;
 // the others are tested 4 * PRUNE_U at a time, lane = 8 g + j holding j-atom j
 // of PRUNE_U of them (independent coalesced loads in flight) against the
@@ -627,15 +627,35 @@ constexpr int PRUNE_U = 2;
 // entries are compacted in place, in order, without the mark; a write never
 // passes the entries still to be read.
 //
+// With POUT (a list of the 8 x 4 geometry, ListDev::jgeo) every entry is
+// tested, per 4-atom half of its j-atoms; the halves with a pair within the
+// radius are packed two by two into the entries of the item (each half's
+// mask bits moved to its new side), and an odd last half is paired with
+// itself under a zero mask.  PIN: the source entries are of that packed
+// form already (the inner list of such a list).
+//
 // The same kernel prunes out of place (dst != src, the inner list of
 // nb_pairlist_prune): it then tests every entry against the radius rl2_inner
 // and writes the kept entries to the same positions of dst, with dst's items,
 // counters and order.
+constexpr int PRUNE_UNITS = 2 * 32 + 1;  // halves of one chunk, plus one carried over
+
+// The mask bits of a half moved from j-slots 4 s + t to 4 s' + t (s != s'):
+// the nibbles of every byte swap.
+__device__ __forceinline__ unsigned long long half_to_side(unsigned long long m, int from, int to) {
+    return from == to ? m : (((m >> 4) & 0x0F0F0F0F0F0F0F0Full) | ((m << 4) & 0xF0F0F0F0F0F0F0F0ull));
+}
+
+template <bool PIN, bool POUT>
 __global__ void __launch_bounds__(PRUNE_WARPS * 32, 3)
 k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, float rl2_inner) {
     pdl_wait();
     pdl_trigger();
     __shared__ unsigned char s_rank[PRUNE_WARPS][32];
+    // POUT: the kept halves of a chunk (first slot, mask bits, side), in order
+    __shared__ int s_ub[POUT ? PRUNE_WARPS : 1][POUT ? PRUNE_UNITS : 1];
+    __shared__ unsigned long long s_um[POUT ? PRUNE_WARPS : 1][POUT ? PRUNE_UNITS : 1];
+    __shared__ unsigned char s_us[POUT ? PRUNE_WARPS : 1][POUT ? PRUNE_UNITS : 1];
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int jj = lane & 7;
@@ -676,27 +696,38 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
             a2[k] = make_float2(fmaf(x0, x0, fmaf(y0, y0, z0 * z0)), fmaf(x1, x1, fmaf(y1, y1, z1 * z1)));
         }
         const float cx = c0.x + Sx, cy = c0.y + Sy, cz = c0.z + Sz;
+        // POUT after a search: the shifted i-cluster box and the radii of the
+        // half-box decisions
         int write = item.y;
+        int carry = 0;  // POUT: a half waiting for its partner (unit 0 of s_u*)
         // each chunk's entries are loaded while the previous chunk is tested
-        int c_next = 0;
+        int c_next = 0, b_next = 0;
         unsigned long long m_next = 0ull;
         if (lane < item.z - item.y) {
             c_next = src.cj[item.y + lane];
+            if (PIN) b_next = src.cjb[item.y + lane];
             m_next = src.mask[item.y + lane];
         }
         for (int base = item.y; base < item.z; base += 32) {
             const int n = min(32, item.z - base);
-            int cjv = 0;
+            int cjv = 0, lo = 0, hi = 0;
             unsigned long long m = 0ull;
             bool chk = false;
             if (lane < n) {
                 const int c = c_next;
-                chk = inner || (c & PRUNE_CHECK) != 0;
+                chk = POUT || inner || (c & PRUNE_CHECK) != 0;
                 cjv = c & ~PRUNE_CHECK;
+                if (PIN) {
+                    lo = cjv;
+                    hi = b_next;
+                } else {
+                    lo = hi = cjv * CL;
+                }
                 m = m_next;
             }
             if (base + 32 + lane < item.z) {
                 c_next = src.cj[base + 32 + lane];
+                if (PIN) b_next = src.cjb[base + 32 + lane];
                 m_next = src.mask[base + 32 + lane];
             }
             const unsigned chk_bal = __ballot_sync(FULL, chk);
@@ -705,8 +736,10 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
             if (chk) s_rank[w][__popc(chk_bal & ((1u << lane) - 1u))] = (unsigned char)lane;
             __syncwarp();
             // bit k of a lane's word: checked entry base + k has an unmasked
-            // pair within the radius (any lane of its group may set it)
+            // pair within the radius (any lane of its group may set it); with
+            // POUT bits 2k and 2k + 1 of found2 stand for its two halves
             unsigned found = 0u;
+            unsigned long long found2 = 0ull;
             for (int q0 = 0; q0 < nchk; q0 += 4 * PRUNE_U) {
                 float4 xj[PRUNE_U];
                 unsigned long long mq[PRUNE_U];
@@ -715,9 +748,10 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
                 for (int u = 0; u < PRUNE_U; ++u) {
                     const int k = q0 + 4 * u + g;
                     rk[u] = k < nchk ? s_rank[w][k] : -1;
-                    const int cjk = __shfl_sync(FULL, cjv, max(rk[u], 0));
+                    const int lok = __shfl_sync(FULL, lo, max(rk[u], 0));
+                    const int hik = __shfl_sync(FULL, hi, max(rk[u], 0));
                     mq[u] = __shfl_sync(FULL, m, max(rk[u], 0));
-                    xj[u] = rk[u] >= 0 ? d.xq_s[cjk * CL + jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    xj[u] = rk[u] >= 0 ? d.xq_s[jj + (jj < 4 ? lok : hik)] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
 #pragma unroll
                 for (int u = 0; u < PRUNE_U; ++u) {
@@ -737,11 +771,11 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
                             nb8 |= (q.x < t ? 1u : 0u) << (2 * k);
                             nb8 |= (q.y < t ? 1u : 0u) << (2 * k + 1);
                         }
-                        const unsigned lo = (unsigned)mq[u], hi = (unsigned)(mq[u] >> 32);
+                        const unsigned lo32 = (unsigned)mq[u], hi32 = (unsigned)(mq[u] >> 32);
                         unsigned col = 0;
 #pragma unroll
                         for (int ii = 0; ii < CL; ++ii)
-                            col |= (((ii < 4 ? lo : hi) >> (8 * (ii & 3) + (ii ^ jj))) & 1u) << ii;
+                            col |= (((ii < 4 ? lo32 : hi32) >> (8 * (ii & 3) + (ii ^ jj))) & 1u) << ii;
                         near = (nb8 & col) != 0u;
                     } else {
 #pragma unroll
@@ -750,17 +784,72 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
                             near = near || q.x < t || q.y < t;
                         }
                     }
-                    if (near && rk[u] >= 0) found |= 1u << rk[u];
+                    if (near && rk[u] >= 0) {
+                        if (POUT)
+                            found2 |= 1ull << (2 * rk[u] + (jj >> 2));
+                        else
+                            found |= 1u << rk[u];
+                    }
                 }
             }
-            keep |= __reduce_or_sync(FULL, found);
-            __syncwarp();
-            if (lane < n && ((keep >> lane) & 1u)) {
-                const int idx = write + __popc(keep & ((1u << lane) - 1u));
-                dst.cj[idx] = cjv;
-                dst.mask[idx] = m;
+            if (!POUT) {
+                keep |= __reduce_or_sync(FULL, found);
+                __syncwarp();
+                if (lane < n && ((keep >> lane) & 1u)) {
+                    const int idx = write + __popc(keep & ((1u << lane) - 1u));
+                    dst.cj[idx] = cjv;
+                    dst.mask[idx] = m;
+                }
+                write += __popc(keep);
+            } else {
+                const unsigned f_lo = __reduce_or_sync(FULL, (unsigned)found2);
+                const unsigned f_hi = __reduce_or_sync(FULL, (unsigned)(found2 >> 32));
+                const unsigned long long f = ((unsigned long long)f_hi << 32) | f_lo;
+                const bool k0 = lane < n && ((f >> (2 * lane)) & 1ull);
+                const bool k1 = lane < n && ((f >> (2 * lane + 1)) & 1ull);
+                const unsigned b0 = __ballot_sync(FULL, k0), b1 = __ballot_sync(FULL, k1);
+                const unsigned lt = (1u << lane) - 1u;
+                int q = carry + __popc(b0 & lt) + __popc(b1 & lt);
+                if (k0) {
+                    s_ub[w][q] = lo;
+                    s_um[w][q] = m & MASK_JLO;
+                    s_us[w][q] = 0;
+                    ++q;
+                }
+                if (k1) {
+                    s_ub[w][q] = hi + 4;
+                    s_um[w][q] = m & ~MASK_JLO;
+                    s_us[w][q] = 1;
+                }
+                const int units = carry + __popc(b0) + __popc(b1);
+                const int npk = units >> 1;  // at most 32
+                __syncwarp();
+                if (lane < npk) {
+                    const int a = 2 * lane, b = 2 * lane + 1;
+                    dst.cj[write + lane] = s_ub[w][a];
+                    dst.cjb[write + lane] = s_ub[w][b] - 4;
+                    dst.mask[write + lane] =
+                        half_to_side(s_um[w][a], s_us[w][a], 0) | half_to_side(s_um[w][b], s_us[w][b], 1);
+                }
+                write += npk;
+                carry = units & 1;
+                __syncwarp();
+                if (carry && lane == 0) {
+                    s_ub[w][0] = s_ub[w][units - 1];
+                    s_um[w][0] = s_um[w][units - 1];
+                    s_us[w][0] = s_us[w][units - 1];
+                }
+                __syncwarp();
             }
-            write += __popc(keep);
+        }
+        if (POUT && carry) {
+            // the item's odd last half, paired with itself under a zero mask
+            if (lane == 0) {
+                dst.cj[write] = s_ub[w][0];
+                dst.cjb[write] = s_ub[w][0] - 4;
+                dst.mask[write] = half_to_side(s_um[w][0], s_us[w][0], 0);
+            }
+            ++write;
         }
         if (lane == 0) {
             const int len = write - item.y;
@@ -771,6 +860,7 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
             else if (ordered && len > 0)
                 dst.order[dst.item_cap - 1 - atomicAdd(dst.counters + CNT_ORD_SHORT, 1)] = it;
         }
+        __syncwarp();
     }
 }
 
@@ -796,15 +886,23 @@ cudaError_t launch_search(const PlanLaunch& p, cudaStream_t st) {
                       p.kp);
 }
 
+// The prune of a list just searched (always of the 8 x 8 form) into the
+// list's own geometry, in place.
 cudaError_t launch_prune(const PlanLaunch& p, cudaStream_t st) {
     unsigned blocks = (unsigned)(p.num_sms * 8);
-    return launch_pdl(k_prune, blocks, PRUNE_WARPS * 32, 0, st, p.d_sys, p.list, p.list, p.kp, -1.f);
+    if (p.list.jgeo)
+        return launch_pdl(k_prune<false, true>, blocks, PRUNE_WARPS * 32, 0, st, p.d_sys, p.list, p.list, p.kp, -1.f);
+    return launch_pdl(k_prune<false, false>, blocks, PRUNE_WARPS * 32, 0, st, p.d_sys, p.list, p.list, p.kp, -1.f);
 }
 
+// The prune of a pruned list into another (dst takes src's geometry).
 cudaError_t launch_prune_into(const PlanLaunch& p, const ListDev& src, const ListDev& dst, float rl2_inner,
                               cudaStream_t st) {
     unsigned blocks = (unsigned)(p.num_sms * 8);
-    return launch_pdl(k_prune, blocks, PRUNE_WARPS * 32, 0, st, p.d_sys, src, dst, p.kp, rl2_inner);
+    if (src.jgeo != dst.jgeo) return cudaErrorInvalidValue;
+    if (src.jgeo)
+        return launch_pdl(k_prune<true, true>, blocks, PRUNE_WARPS * 32, 0, st, p.d_sys, src, dst, p.kp, rl2_inner);
+    return launch_pdl(k_prune<false, false>, blocks, PRUNE_WARPS * 32, 0, st, p.d_sys, src, dst, p.kp, rl2_inner);
 }
 
 }  // namespace nbgb

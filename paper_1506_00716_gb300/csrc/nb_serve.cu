@@ -240,6 +240,7 @@ nb_status run_wave(nb_server* s, int k, double boost) {
     }
     ++w.attempts;
     w.boost = boost;
+    plan_set_geometry(w.plan);
     PlanLaunch pl = launch_of(w.plan);
     cudaError_t e = cudaMemsetAsync(w.plan->list.counters, 0, 4 * CNT_N, st);
     if (e == cudaSuccess) e = launch_grid_put(pl, st);

@@ -209,12 +209,20 @@ extern "C" nb_status nb_eval_noalloc(const nb_params* params, int natoms, const 
     // the Ewald force table, after the Lennard-Jones tables (built on the host,
     // in a buffer on this call's stack)
     float4 gtab[GT_MAX];
+    float4 etab[2 * ET_MAX];
     if (params->coul == NB_COUL_EWALD) {
         float invh = 0.f;
         const int gt_n = ewald_force_table(params->ewald_beta, params->rc, gtab, &invh);
         if (gt_n > 0)
             NA_CK(cudaMemcpyAsync((float4*)(d_lj + 2 * (size_t)nt * nt), gtab, 16 * (size_t)gt_n,
                                   cudaMemcpyHostToDevice, st));
+        // the energy table after it (the KParams::etab layout)
+        const int et_n = ewald_energy_table(params->ewald_beta, params->rc, etab, &invh);
+        if (et_n > 0) {
+            float4* d_et = (float4*)(d_lj + etab_offset2(nt));
+            NA_CK(cudaMemcpyAsync(d_et, etab, 16 * (size_t)et_n, cudaMemcpyHostToDevice, st));
+            NA_CK(cudaMemcpyAsync(d_et + ET_MAX, etab + ET_MAX, 16 * (size_t)et_n, cudaMemcpyHostToDevice, st));
+        }
         // the copy reads the stack buffer: let it finish before the buffer goes
         NA_CK(cudaStreamSynchronize(st));
     }

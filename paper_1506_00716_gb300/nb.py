@@ -29,12 +29,13 @@ STATUS = {0: "NB_OK", 1: "NB_ERR_ARG", 2: "NB_ERR_BOX", 3: "NB_ERR_OOM", 4: "NB_
 EXPORTS = ["nb_last_error", "nb_ctx_create", "nb_ctx_destroy", "nb_ctx_memory", "nb_sys_footprint",
            "nb_sys_create", "nb_sys_create_box", "nb_sys_destroy", "nb_set_exclusions", "nb_grid_put",
            "nb_pairlist_build",
-           "nb_pairlist_info", "nb_pairlist_prune", "nb_forces", "nb_pairlist_export", "nb_batch_create",
+           "nb_pairlist_info", "nb_pairlist_prune", "nb_forces", "nb_pairlist_export", "nb_pairlist_export_slots",
+           "nb_batch_create",
            "nb_batch_destroy", "nb_sys_set_coords", "nb_batch_submit", "nb_batch_poll",
            "nb_sys_results", "nb_ctx_set_timing", "nb_ctx_set_timing_stages", "nb_ctx_timing", "nb_eval_info",
            "nb_eval_noalloc", "nb_ctx_set_tuning", "nb_ctx_get_tuning", "nb_server_create",
            "nb_server_destroy", "nb_server_submit", "nb_server_wait", "nb_pme_init", "nb_pme_forces",
-           "nb_ctx_inject_alloc_failures", "nb_ewald_force_table"]
+           "nb_ctx_inject_alloc_failures", "nb_ewald_force_table", "nb_ewald_energy_table"]
 NB_NSTAGE = 11
 NB_MOD_LJ_SHIFT = 1
 NB_MOD_EWALD_SHIFT = 2
@@ -63,7 +64,7 @@ class nb_pme_params(ctypes.Structure):
 
 class nb_tuning(ctypes.Structure):
     _fields_ = [("max_entries", ctypes.c_int), ("force_min_blocks", ctypes.c_int), ("search_mode", ctypes.c_int),
-                ("energy_mode", ctypes.c_int)]
+                ("energy_mode", ctypes.c_int), ("jcluster", ctypes.c_int)]
 
 
 class nb_request_stats(ctypes.Structure):
@@ -117,6 +118,9 @@ def load(path: str | None = None):
         "nb_pme_init": ([_vp, ctypes.POINTER(nb_pme_params)], _st),
         "nb_pme_forces": ([_vp, _vp, _vp, _vp, _vp, ctypes.c_uint], _st),
         "nb_pairlist_export": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong)], _st),
+        "nb_pairlist_export_slots": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong)], _st),
+        "nb_ewald_energy_table": ([ctypes.c_double, ctypes.c_double, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_double)], _st),
         "nb_ewald_force_table": ([ctypes.c_double, ctypes.c_double, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_double)], _st),
         "nb_batch_create": ([_vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp)], _st),
@@ -284,6 +288,19 @@ def nb_pme_forces(sys, x_new=None, f=None, energy=None, virial=None, flags: int 
     check(load().nb_pme_forces(sys, ptr(x_new), ptr(f), ptr(energy), ptr(virial), flags))
 
 
+def nb_ewald_energy_table(beta: float, rc: float):
+    """The energy kernels' Ewald table: (float32 [K, 8] coefficients, h)."""
+    import numpy as np
+
+    n = ctypes.c_int()
+    h = ctypes.c_double()
+    check(load().nb_ewald_energy_table(float(beta), float(rc), None, 0, ctypes.byref(n), ctypes.byref(h)))
+    coef = np.zeros((n.value, 8), dtype=np.float32)
+    check(load().nb_ewald_energy_table(float(beta), float(rc), coef.ctypes.data_as(_vp), n.value, ctypes.byref(n),
+                                       ctypes.byref(h)))
+    return coef, h.value
+
+
 def nb_ewald_force_table(beta: float, rc: float):
     """The force kernel's Ewald table: (float32 [K, 4] coefficients, h)."""
     import numpy as np
@@ -300,6 +317,12 @@ def nb_ewald_force_table(beta: float, rc: float):
 def nb_pairlist_export(sys, perm=None, items=None, cj=None, mask=None) -> int:
     n = ctypes.c_longlong()
     check(load().nb_pairlist_export(sys, ptr(perm), ptr(items), ptr(cj), ptr(mask), ctypes.byref(n)))
+    return n.value
+
+
+def nb_pairlist_export_slots(sys, perm=None, items=None, jslot=None, mask=None) -> int:
+    n = ctypes.c_longlong()
+    check(load().nb_pairlist_export_slots(sys, ptr(perm), ptr(items), ptr(jslot), ptr(mask), ctypes.byref(n)))
     return n.value
 
 
@@ -383,8 +406,8 @@ def nb_eval_noalloc(params, natoms: int, box, excl_index, excl_atoms, xq, type_,
 
 
 def nb_ctx_set_tuning(ctx, max_entries: int = 32, force_min_blocks: int = 3, search_mode: int = 0,
-                      energy_mode: int = 0) -> None:
-    t = nb_tuning(int(max_entries), int(force_min_blocks), int(search_mode), int(energy_mode))
+                      energy_mode: int = 0, jcluster: int = 8) -> None:
+    t = nb_tuning(int(max_entries), int(force_min_blocks), int(search_mode), int(energy_mode), int(jcluster))
     check(load().nb_ctx_set_tuning(ctx, ctypes.byref(t)))
 
 
@@ -392,7 +415,7 @@ def nb_ctx_get_tuning(ctx) -> dict:
     t = nb_tuning()
     check(load().nb_ctx_get_tuning(ctx, ctypes.byref(t)))
     return {"max_entries": t.max_entries, "force_min_blocks": t.force_min_blocks, "search_mode": t.search_mode,
-            "energy_mode": t.energy_mode}
+            "energy_mode": t.energy_mode, "jcluster": t.jcluster or 8}
 
 
 def nb_server_create(ctx, params, budget: int = 0, max_wave: int = 64) -> int:

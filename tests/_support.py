@@ -1,8 +1,9 @@
 """Test helpers: run the CUDA path through the C ABI and expand its pair list.
 
 Test infrastructure; the expansion reads the list exactly as the kernels do
-(bit 8*i + t of an entry's mask = pair (i-slot i, j-slot t XOR i), the
-i-cluster displaced by the item's periodic shift).
+(bit 8*i + t of an entry's mask = pair (i-slot i, j-slot t XOR i), j-slot j
+at sorted slot jslot[e, j // 4] + j % 4, the i-cluster displaced by the
+item's periodic shift), for either j-cluster geometry.
 """
 import numpy as np
 
@@ -29,14 +30,14 @@ def export_list(h):
     info = nb.nb_pairlist_info(h)
     perm = np.zeros(info["n_clusters"] * 8, dtype=np.int32)
     items = np.zeros((max(info["n_items"], 1), 4), dtype=np.int32)
-    ne = nb.nb_pairlist_export(h)  # the entry arrays' extent (the largest item end)
-    cj = np.zeros(max(ne, 1), dtype=np.int32)
+    ne = nb.nb_pairlist_export_slots(h)  # the entry arrays' extent (the largest item end)
+    jslot = np.zeros((max(ne, 1), 2), dtype=np.int32)
     mask = np.zeros(max(ne, 1), dtype=np.uint64)
-    nb.nb_pairlist_export(h, perm, items, cj, mask)
-    return info, perm, items[: info["n_items"]], cj, mask
+    nb.nb_pairlist_export_slots(h, perm, items, jslot, mask)
+    return info, perm, items[: info["n_items"]], jslot, mask
 
 
-def expand_pairs(sys, perm, items, cj, mask, r_cut, chunk=20000):
+def expand_pairs(sys, perm, items, jslot, mask, r_cut, chunk=20000):
     """Atom pairs (i<j keys) of the list whose distance under the entry's shift is < r_cut
     (float64), plus the number of such (pair, shift) occurrences (duplicates > 0 = double count)."""
     n = sys.n
@@ -62,7 +63,7 @@ def expand_pairs(sys, perm, items, cj, mask, r_cut, chunk=20000):
         ci = it[er, 0]
         sh = it[er, 3]
         a = perm[ci * 8 + i]
-        b = perm[cj[e[er]] * 8 + j]
+        b = perm[jslot[e[er], j // 4] + j % 4]
         ok = (a >= 0) & (b >= 0)
         a, b, sh = a[ok], b[ok], sh[ok]
         sx, sy, sz = sh // 9 - 1, (sh // 3) % 3 - 1, sh % 3 - 1
@@ -82,7 +83,7 @@ def rel_rms(f, ref):
     return float(np.sqrt(((f - ref) ** 2).mean()) / np.sqrt((ref ** 2).mean()))
 
 
-def expand_pairs_of_rows(sys, perm, items, cj, mask, r_cut, sel, chunk=200000):
+def expand_pairs_of_rows(sys, perm, items, jslot, mask, r_cut, sel, chunk=200000):
     """Atom pairs (min * n + max keys, unique, sorted) of the list that touch an
     atom of `sel` and lie closer than r_cut under their entry's shift (float64
     distance of the float32 inputs), and the number of (pair, shift)
@@ -105,7 +106,7 @@ def expand_pairs_of_rows(sys, perm, items, cj, mask, r_cut, sel, chunk=200000):
     ent_item = np.repeat(np.arange(items.shape[0]), lens)
     offs = np.cumsum(lens) - lens
     ent_idx = np.arange(total, dtype=np.int64) - np.repeat(offs, lens) + np.repeat(items[:, 1].astype(np.int64), lens)
-    keep = cl_sel[items[ent_item, 0]] | cl_sel[cj[ent_idx]]
+    keep = cl_sel[items[ent_item, 0]] | cl_sel[jslot[ent_idx, 0] // 8] | cl_sel[jslot[ent_idx, 1] // 8]
     ent_item, ent_idx = ent_item[keep], ent_idx[keep]
     bits = np.arange(64, dtype=np.uint64)
     keys_all = []
@@ -118,7 +119,7 @@ def expand_pairs_of_rows(sys, perm, items, cj, mask, r_cut, sel, chunk=200000):
         i = bit // 8
         j = (bit % 8) ^ i
         a = perm[it[er, 0] * 8 + i]
-        b = perm[cj[e[er]] * 8 + j]
+        b = perm[jslot[e[er], j // 4] + j % 4]
         sh = it[er, 3]
         ok = (a >= 0) & (b >= 0)
         a, b, sh = a[ok], b[ok], sh[ok]

@@ -64,12 +64,14 @@ def _run_batch(ctx, systems, params, submits=2):
     return out
 
 
-@pytest.mark.parametrize("use_stream", [True, False])
+@pytest.mark.parametrize("use_stream,jcluster", [(True, 8), (False, 8), (True, 4)],
+                         ids=["graph", "direct", "graph+8x4"])
 @pytest.mark.parametrize("coul", [wb.COUL_RF, wb.COUL_EWALD])
-def test_batch_matches_plain_and_oracle(torch_cuda, use_stream, coul):
+def test_batch_matches_plain_and_oracle(torch_cuda, use_stream, jcluster, coul):
     torch = torch_cuda
     stream = torch.cuda.Stream() if use_stream else None
     ctx = nb.nb_ctx_create(0, stream, 0)
+    nb.nb_ctx_set_tuning(ctx, 32, 3, 0, 0, jcluster)
     try:
         systems = _systems()
         p = wb.Params(coul=coul)

@@ -113,7 +113,7 @@ def test_large_box_against_the_oracle(torch_cuda):
             v = np.zeros(9)
             nb.nb_forces(h, None, f, e, v, FLAGS)
             npairs = nb.nb_eval_info(h)["n_pairs"]
-            info, perm, items, cj, mask = export_list(h)
+            info, perm, items, jslot, mask = export_list(h)
         finally:
             nb.nb_sys_destroy(h)
     finally:
@@ -127,12 +127,12 @@ def test_large_box_against_the_oracle(torch_cuda):
 
     rng = np.random.default_rng(31)
     sel = np.sort(rng.choice(s.n, size=10_000, replace=False)).astype(np.int32)
-    got, occurrences = expand_pairs_of_rows(s, perm, items, cj, mask, p.rc, sel)
+    got, occurrences = expand_pairs_of_rows(s, perm, items, jslot, mask, p.rc, sel)
     ref = oracle.pairs_of_rows(s, p.rc, sel)
     assert occurrences == got.shape[0]  # no atom pair listed twice
     assert np.array_equal(got, ref)
     sub = sel[:2000]
-    inside, _ = expand_pairs_of_rows(s, perm, items, cj, mask, p.rlist, sub)
+    inside, _ = expand_pairs_of_rows(s, perm, items, jslot, mask, p.rlist, sub)
     assert np.isin(oracle.pairs_of_rows(s, p.rlist, sub), inside).all()
 
     assert rel_rms(f[sel], oracle.forces(s, p, sel)) <= F_TOL

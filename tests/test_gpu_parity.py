@@ -43,17 +43,24 @@ BOXES = {
 }
 
 
-@pytest.fixture(params=[(1, 0), (2, 0), (1, 1)],
-                ids=["warp_search+energy_kernel", "thread_search+energy_kernel", "warp_search+fused_energy"])
+@pytest.fixture(params=[(1, 0, 8, None), (2, 0, 8, None), (1, 1, 8, None),
+                        (1, 0, 4, None), (2, 0, 4, None), (1, 1, 4, None), (2, 0, 4, 1)],
+                ids=["warp_search+energy_kernel", "thread_search+energy_kernel", "warp_search+fused_energy",
+                     "8x4+warp_search+energy_kernel", "8x4+thread_search+energy_kernel",
+                     "8x4+warp_search+fused_energy", "8x4+thread_search+screening_energy_kernel"])
 def search_mode(request, ctx):
     """Both search kernels (a warp per i-cluster, a thread per i-cluster),
-    whatever the size would choose, and both energy paths (fused into the
-    force kernel, or the separate energy kernel); the tuning is restored
-    afterwards."""
+    whatever the size would choose, both energy paths (fused into the force
+    kernel, or the separate energy kernel, queuing from the force kernel's
+    marks or, at the register budget of one block per SM, screening the
+    slots itself) and both cluster geometries (8 x 8, 8 x 4); the tuning is
+    restored afterwards."""
     old = nb.nb_ctx_get_tuning(ctx)
-    nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], *request.param)
+    sm, em, jc, mb = request.param
+    nb.nb_ctx_set_tuning(ctx, old["max_entries"], mb or old["force_min_blocks"], sm, em, jc)
     yield request.param
-    nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], old["search_mode"], old["energy_mode"])
+    nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], old["search_mode"], old["energy_mode"],
+                         old["jcluster"])
 
 
 @pytest.mark.parametrize("name", ["small", "mid", "rd_small"])
@@ -62,15 +69,15 @@ def test_pairlist_covers_oracle_pairs_exactly(ctx, name, search_mode):
     p = wb.params_rf()
     _, _, _, h = gpu_eval(ctx, s, p, flags=0, keep=True)
     try:
-        info, perm, items, cj, mask = export_list(h)
+        info, perm, items, jslot, mask = export_list(h)
     finally:
         nb.nb_sys_destroy(h)
     assert sorted(perm[perm >= 0].tolist()) == list(range(s.n))
-    got, occurrences = expand_pairs(s, perm, items, cj, mask, p.rc)
+    got, occurrences = expand_pairs(s, perm, items, jslot, mask, p.rc)
     ref = oracle.pairs(s, p.rc)
     assert occurrences == got.shape[0], "a pair appears twice inside rc (double counting)"
     assert np.array_equal(got, ref)
-    got_l, _ = expand_pairs(s, perm, items, cj, mask, p.rlist)
+    got_l, _ = expand_pairs(s, perm, items, jslot, mask, p.rlist)
     ref_l = oracle.pairs(s, p.rlist)
     assert np.isin(ref_l, got_l).all(), "a pair inside rlist is missing from the list"
     assert info["n_entries"] <= info["n_entries_raw"]
@@ -127,8 +134,10 @@ def test_flag_variants_give_the_same_forces(ctx, flags):
         assert np.allclose(v, v_all, rtol=1e-9, atol=1e-9)
 
 
-def test_stale_list_evaluations(ctx):
-    """24,000-atom box: list rebuilt every 10 evaluations, Gaussian moves between."""
+@pytest.mark.parametrize("geometry", [8, 4], indirect=True, ids=["8x8", "8x4"])
+def test_stale_list_evaluations(ctx, geometry):
+    """24,000-atom box: list rebuilt every 10 evaluations, Gaussian moves
+    between; both cluster geometries."""
     s = wb.mid_box(seed=2)
     p = wb.params_rf()
     h = nb.nb_sys_create(ctx, p, s.n, s.box)
@@ -185,11 +194,24 @@ def test_caller_buffer_kinds(ctx, kind):
     _check(s, p, f, e, v)
 
 
-def test_dynamic_pruning(ctx):
+@pytest.fixture
+def geometry(request, ctx):
+    """The context's j-cluster size set to the test's parameter, restored after."""
+    old = nb.nb_ctx_get_tuning(ctx)
+    nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], old["search_mode"], old["energy_mode"],
+                         request.param)
+    yield request.param
+    nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], old["search_mode"], old["energy_mode"],
+                         old["jcluster"])
+
+
+@pytest.mark.parametrize("geometry", [8, 4], indirect=True, ids=["8x8", "8x4"])
+def test_dynamic_pruning(ctx, geometry):
     """Outer list at rlist = 1.3 nm built once; pruned out of place to an inner
     list at 1.1 nm every 5 evaluations while the atoms move (Gaussian, sigma
     0.005 nm per evaluation); every checked evaluation matches the oracle,
-    interacting-pair count included."""
+    interacting-pair count included.  Both cluster geometries (the inner
+    list of an 8 x 4 list re-pairs the halves it keeps)."""
     s = wb.mid_box(seed=2)
     p = wb.Params(coul=wb.COUL_RF, rlist=1.3)
     h = nb.nb_sys_create(ctx, p, s.n, s.box)
