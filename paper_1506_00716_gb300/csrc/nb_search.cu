@@ -68,6 +68,10 @@ constexpr int MAX_RUNS = 32;
 // masked-out work.  The others carry PRUNE_CHECK in their cluster index
 // until the prune has tested them.
 constexpr float PRUNE_SURE_MARGIN = 0.3f;
+// The margin for lists of 4-atom j-clusters (ListDev::jgeo): the prune keeps
+// both halves of a certain entry, so only the closest pairs of clusters
+// skip the per-half test.
+constexpr float PRUNE_SURE_MARGIN4 = 0.6f;
 constexpr int PRUNE_CHECK = 1 << 30;
 
 struct SearchWarpSmem {
@@ -200,7 +204,7 @@ k_search(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int nsy
     const float rl = d.rl_search;
     const float rl2 = rl * rl;
     const float izl = 1.f / d.L[2];
-    const float rbb = fmaxf(0.f, rl - PRUNE_SURE_MARGIN);
+    const float rbb = fmaxf(0.f, rl - (list.jgeo ? PRUNE_SURE_MARGIN4 : PRUNE_SURE_MARGIN));
     const float rbb2 = rbb * rbb;
     const float eps = 1e-5f * fmaxf(1.f, fmaxf(d.L[0], fmaxf(d.L[1], d.L[2])));
 
@@ -441,7 +445,7 @@ k_tsearch(const SysDev* __restrict__ sys, const int* __restrict__ cl_off, int ns
     const float rl = d.rl_search;
     const float rl2 = rl * rl;
     const float izl = 1.f / d.L[2];
-    const float rbb = fmaxf(0.f, rl - PRUNE_SURE_MARGIN);
+    const float rbb = fmaxf(0.f, rl - (list.jgeo ? PRUNE_SURE_MARGIN4 : PRUNE_SURE_MARGIN));
     const float rbb2 = rbb * rbb;
     const float eps = 1e-5f * fmaxf(1.f, fmaxf(d.L[0], fmaxf(d.L[1], d.L[2])));
 
@@ -627,11 +631,12 @@ constexpr int PRUNE_U = 2;
 // entries are compacted in place, in order, without the mark; a write never
 // passes the entries still to be read.
 //
-// With POUT (a list of the 8 x 4 geometry, ListDev::jgeo) every entry is
-// tested, per 4-atom half of its j-atoms; the halves with a pair within the
-// radius are packed two by two into the entries of the item (each half's
-// mask bits moved to its new side), and an odd last half is paired with
-// itself under a zero mask.  PIN: the source entries are of that packed
+// With POUT (a list of the 8 x 4 geometry, ListDev::jgeo) the entries are
+// kept per 4-atom half of their j-atoms: a tested entry keeps the halves with
+// a pair within the radius, a certain one the halves with an unmasked pair.
+// The kept halves are packed two by two into the entries of the item (each
+// half's mask bits moved to its new side), and an odd last half is paired
+// with itself under a zero mask.  PIN: the source entries are of that packed
 // form already (the inner list of such a list).
 //
 // The same kernel prunes out of place (dst != src, the inner list of
@@ -715,7 +720,7 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
             bool chk = false;
             if (lane < n) {
                 const int c = c_next;
-                chk = POUT || inner || (c & PRUNE_CHECK) != 0;
+                chk = inner || (c & PRUNE_CHECK) != 0;
                 cjv = c & ~PRUNE_CHECK;
                 if (PIN) {
                     lo = cjv;
@@ -805,8 +810,10 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
                 const unsigned f_lo = __reduce_or_sync(FULL, (unsigned)found2);
                 const unsigned f_hi = __reduce_or_sync(FULL, (unsigned)(found2 >> 32));
                 const unsigned long long f = ((unsigned long long)f_hi << 32) | f_lo;
-                const bool k0 = lane < n && ((f >> (2 * lane)) & 1ull);
-                const bool k1 = lane < n && ((f >> (2 * lane + 1)) & 1ull);
+                // an entry the search marked as certain keeps both halves
+                // that have an unmasked pair
+                const bool k0 = lane < n && (chk ? ((f >> (2 * lane)) & 1ull) != 0ull : (m & MASK_JLO) != 0ull);
+                const bool k1 = lane < n && (chk ? ((f >> (2 * lane + 1)) & 1ull) != 0ull : (m & ~MASK_JLO) != 0ull);
                 const unsigned b0 = __ballot_sync(FULL, k0), b1 = __ballot_sync(FULL, k1);
                 const unsigned lt = (1u << lane) - 1u;
                 int q = carry + __popc(b0 & lt) + __popc(b1 & lt);
