@@ -160,7 +160,10 @@ enum {
  *                     4..4096 (default 32)
  *   force_min_blocks  register budget of the force kernel, as the number of
  *                     256-thread blocks guaranteed resident per SM: 1 (up to
- *                     255 registers per thread), 2 (128) or 3 (85, default)
+ *                     255 registers per thread), 2 (128) or 3 (80, default);
+ *                     or 4: two 320-thread blocks per SM (96 registers, 20
+ *                     warps per SM).  Evaluations with energies fused into the
+ *                     force kernel (energy_mode 1) take budget 2.
  *   search_mode       cluster-pair search: 1 = one warp per i-cluster (lanes
  *                     share its candidates), 2 = one thread per i-cluster
  *                     (count, scan and write passes, no atomics), 0 = by

@@ -6,7 +6,8 @@ Tuned per (electrostatics, system size):
                     persistent force kernel balances well on small systems
                     (list-splitting threshold);
   force_min_blocks  force-kernel register budget / block residency (block
-                    shape): 1, 2 or 3 resident 256-thread blocks per SM;
+                    shape): 1, 2 or 3 resident 256-thread blocks per SM, or
+                    4: two 320-thread blocks (96 registers);
   search_mode       cluster-pair search: a warp per i-cluster (1) or a
                     thread per i-cluster (2);
   energy_mode       evaluations with energies: a separate double-float energy
@@ -40,7 +41,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_TABLE = os.path.join(HERE, "tuning.json")
 SIZES_MOL = [1000, 8000, 64000, 1_000_000]
 MAX_ENTRIES = [8, 16, 32, 64, 128]
-MIN_BLOCKS = [1, 2, 3]
+MIN_BLOCKS = [1, 2, 3, 4]
 SEARCH_MODES = [1, 2]
 ENERGY_MODES = [0, 1]
 JCLUSTERS = [8, 4]

@@ -1061,7 +1061,8 @@ nb_status nb_ctx_destroy(nb_ctx* ctx) {
 nb_status nb_ctx_set_tuning(nb_ctx* ctx, const nb_tuning* t) {
     if (!ctx || !t) return fail(NB_ERR_ARG, "ctx / tuning is NULL");
     if (t->max_entries < 4 || t->max_entries > 4096) return fail(NB_ERR_ARG, "max_entries must be in 4..4096");
-    if (t->force_min_blocks < 1 || t->force_min_blocks > 3) return fail(NB_ERR_ARG, "force_min_blocks must be 1, 2 or 3");
+    if (t->force_min_blocks < 1 || t->force_min_blocks > 4)
+        return fail(NB_ERR_ARG, "force_min_blocks must be 1, 2, 3 or 4");
     if (t->search_mode < 0 || t->search_mode > 2) return fail(NB_ERR_ARG, "search_mode must be 0, 1 or 2");
     if (t->energy_mode < 0 || t->energy_mode > 1) return fail(NB_ERR_ARG, "energy_mode must be 0 or 1");
     if (t->jcluster != 0 && t->jcluster != 8 && t->jcluster != 4)

@@ -186,7 +186,7 @@ struct KParams {
     int search_mode;     // 0: by size, 1: a warp per i-cluster, 2: a thread per i-cluster
     int energy_mode;     // 0: a separate energy kernel, 1: energies fused into the force kernel
     int lpt_max_items;   // item count up to which items run longest first
-    int force_min_blocks;  // force-kernel launch-bounds variant: 1, 2 or 3
+    int force_min_blocks;  // force-kernel launch-bounds variant: 1, 2, 3 or 4 (nb_tuning)
     // Lennard-Jones as weights: when the table has one nonzero parameter
     // pair, c6_ij = C6 w_i w_j and c12_ij = C12 w_i w_j with w = 1 for the
     // types in ljw_mask and 0 otherwise, exactly; the force kernel then takes

@@ -42,7 +42,11 @@ namespace nbgb {
 namespace {
 
 constexpr unsigned FULL = FULL_MASK;
-constexpr int FW = 8;  // warps per block of the force kernel
+constexpr int FW = 8;  // warps per block of the force kernel (the default shape)
+// The shape of the 96-register budget (force_min_blocks = 4): two blocks of 10
+// warps per SM.  The register file is split between the four SM
+// sub-partitions, so 20 warps (5 per sub-partition) is the most that fits at
+// 96 registers a thread: 16384 / (5 * 32) = 102.
 
 // The Ewald force table in shared memory (KParams::gtab), in R copies:
 // entry k of copy c at k R + c, lane l reading copy l mod R.  A 16-byte
@@ -270,8 +274,8 @@ __device__ __forceinline__ void pair_block2(const float* __restrict__ sj, int h,
 // around it (ListDev::marks), from the distances it has just computed, so
 // that the energy kernel needs no second distance pass (it finds the band
 // pairs among them from its own double-float distances).
-template <int COUL, bool VIR, int MINB, bool ENER, bool LJSH, bool LJW = false, bool MARK = false>
-__global__ void __launch_bounds__(FW * 32, MINB)
+template <int COUL, bool VIR, int MINB, bool ENER, bool LJSH, bool LJW = false, bool MARK = false, int FWT = FW>
+__global__ void __launch_bounds__(FWT * 32, MINB)
 k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     pdl_wait();
     pdl_trigger();
@@ -279,11 +283,11 @@ k_forces(const SysDev* __restrict__ sys, ListDev list, KParams kp) {
     // (6 c6) table [ntypes^2] at 0, (12 c12) table at LJ_C12; with ENER the
     // (c6, c12) table of the energies (float2) at lj_e_offset(ntypes)
     extern __shared__ float s_ljt[];
-    __shared__ __align__(16) float s_j[FW][4][JB_SIZE];
-    __shared__ double s_acc[FW][6];
-    __shared__ float s_fix[FW][4][CL][3];
-    __shared__ int s_qm[ENER ? FW : 1][ENER ? QCAP : 1];
-    __shared__ IRec s_irec[ENER ? FW : 1][CL];
+    __shared__ __align__(16) float s_j[FWT][4][JB_SIZE];
+    __shared__ double s_acc[FWT][6];
+    __shared__ float s_fix[FWT][4][CL][3];
+    __shared__ int s_qm[ENER ? FWT : 1][ENER ? QCAP : 1];
+    __shared__ IRec s_irec[ENER ? FWT : 1][CL];
 
     const int lane = threadIdx.x & 31;
     const int i = lane & 7;
@@ -689,14 +693,15 @@ __global__ void k_finish(const SysDev* __restrict__ sys, const int* __restrict__
     }
 }
 
-template <int COUL, bool VIR, int MINB, bool ENER = false, bool LJSH = false, bool LJW = false, bool MARK = false>
+template <int COUL, bool VIR, int MINB, bool ENER = false, bool LJSH = false, bool LJW = false, bool MARK = false,
+          int FWT = FW>
 cudaError_t launch_forces_t(const PlanLaunch& p, cudaStream_t st) {
     const size_t nt2 = (size_t)p.kp.ntypes * p.kp.ntypes;
     // LJ tables (the energies' too with ENER), then the Ewald force table
     const size_t smem = COUL == NB_COUL_EWALD ? (gt_offset(p.kp.ntypes) + ((4 * (size_t)p.kp.gt_n) << gt_log_rep(p.kp.gt_n))) * sizeof(float)
                         : ENER ? (lj_e_offset(p.kp.ntypes) + 2 * nt2) * sizeof(float)
                                : (LJ_C12 + nt2) * sizeof(float);
-    auto kern = k_forces<COUL, VIR, MINB, ENER, LJSH, LJW, MARK>;
+    auto kern = k_forces<COUL, VIR, MINB, ENER, LJSH, LJW, MARK, FWT>;
     if (ENER || smem > 48 * 1024) {
         // the energy queue (or a large Ewald table) makes static + dynamic
         // shared memory pass 48 KB: allow the dynamic part explicitly
@@ -704,10 +709,10 @@ cudaError_t launch_forces_t(const PlanLaunch& p, cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     int per_sm = 0;
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FW * 32, smem);
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FWT * 32, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) per_sm = 1;
-    return launch_pdl(kern, (unsigned)(p.num_sms * per_sm), FW * 32, smem, st, p.d_sys, p.list, p.kp);
+    return launch_pdl(kern, (unsigned)(p.num_sms * per_sm), FWT * 32, smem, st, p.d_sys, p.list, p.kp);
 }
 
 }  // namespace
@@ -723,10 +728,14 @@ cudaError_t launch_prepare(const PlanLaunch& p, bool coords, cudaStream_t st) {
                       (const float*)nullptr);
 }
 
-// The force kernel writing the energy kernel's marks (2 or 3 blocks per SM).
+// The force kernel writing the energy kernel's marks (register budgets 2, 3
+// and 4: two or three blocks of 8 warps, two of 10).
 template <int COUL, bool VIR>
 cudaError_t launch_forces_m(const PlanLaunch& p, cudaStream_t st) {
     const bool w = p.kp.lj_weights != 0;
+    if (p.kp.force_min_blocks == 4)
+        return w ? launch_forces_t<COUL, VIR, 2, false, false, true, true, 10>(p, st)
+                 : launch_forces_t<COUL, VIR, 2, false, false, false, true, 10>(p, st);
     if (p.kp.force_min_blocks == 2)
         return w ? launch_forces_t<COUL, VIR, 2, false, false, true, true>(p, st)
                  : launch_forces_t<COUL, VIR, 2, false, false, false, true>(p, st);
@@ -742,6 +751,9 @@ cudaError_t launch_forces_v(const PlanLaunch& p, cudaStream_t st) {
     switch (p.kp.force_min_blocks) {
         case 1: return launch_forces_t<COUL, VIR, 1>(p, st);
         case 2: return w ? launch_forces_t<COUL, VIR, 2, false, false, true>(p, st) : launch_forces_t<COUL, VIR, 2>(p, st);
+        case 4:
+            return w ? launch_forces_t<COUL, VIR, 2, false, false, true, false, 10>(p, st)
+                     : launch_forces_t<COUL, VIR, 2, false, false, false, false, 10>(p, st);
         default: return w ? launch_forces_t<COUL, VIR, 3, false, false, true>(p, st) : launch_forces_t<COUL, VIR, 3>(p, st);
     }
 }

@@ -44,17 +44,18 @@ BOXES = {
 
 
 @pytest.fixture(params=[(1, 0, 8, None), (2, 0, 8, None), (1, 1, 8, None),
-                        (1, 0, 4, None), (2, 0, 4, None), (1, 1, 4, None), (2, 0, 4, 1)],
+                        (1, 0, 4, None), (2, 0, 4, None), (1, 1, 4, None), (2, 0, 4, 1), (1, 0, 4, 4)],
                 ids=["warp_search+energy_kernel", "thread_search+energy_kernel", "warp_search+fused_energy",
                      "8x4+warp_search+energy_kernel", "8x4+thread_search+energy_kernel",
-                     "8x4+warp_search+fused_energy", "8x4+thread_search+screening_energy_kernel"])
+                     "8x4+warp_search+fused_energy", "8x4+thread_search+screening_energy_kernel",
+                     "8x4+warp_search+energy_kernel+96_registers"])
 def search_mode(request, ctx):
     """Both search kernels (a warp per i-cluster, a thread per i-cluster),
     whatever the size would choose, both energy paths (fused into the force
     kernel, or the separate energy kernel, queuing from the force kernel's
     marks or, at the register budget of one block per SM, screening the
-    slots itself) and both cluster geometries (8 x 8, 8 x 4); the tuning is
-    restored afterwards."""
+    slots itself) and both cluster geometries (8 x 8, 8 x 4), and the force
+    kernel's register budgets; the tuning is restored afterwards."""
     old = nb.nb_ctx_get_tuning(ctx)
     sm, em, jc, mb = request.param
     nb.nb_ctx_set_tuning(ctx, old["max_entries"], mb or old["force_min_blocks"], sm, em, jc)
