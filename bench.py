@@ -57,7 +57,7 @@ OPS_PER_SLOT = {("rf", False): 28, ("rf", True): 34, ("ewald", False): 35, ("ewa
 FLOPS_PER_SLOT = {("rf", False): 32, ("rf", True): 44, ("ewald", False): 43, ("ewald", True): 55}
 # SHA-256 prefix of csrc/nb_kernel.cu when the two tables above were counted:
 # the line reports whether the timed kernel is still that source
-OPS_COUNTED_FOR = "ddda8871d4dd411b"
+OPS_COUNTED_FOR = "99e0cd2c282c1b74"
 # The algorithmic budget per computed slot of a forces-only evaluation, from
 # the operation list of the pair interaction (d 3, r^2 3, cut-off select 2-3,
 # 1/r^2 and 1/r^6 3, LJ 4-5, RF 3, or for Ewald r and G(r) by a table
