@@ -43,9 +43,19 @@ def _wait(srv, s, t, timeout=-1):
     return f, e, v, st
 
 
-def test_same_result_alone_and_in_the_mix(ctx):
+@pytest.mark.parametrize("jcluster", [8, 4], ids=["8x8", "8x4"])
+def test_same_result_alone_and_in_the_mix(ctx, jcluster):
+    """Both cluster geometries (the server takes the context's tuning when it
+    is created)."""
     p = wb.params_ewald()
-    srv = nb.nb_server_create(ctx, p, 0, 64)
+    old = nb.nb_ctx_get_tuning(ctx)
+    nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], old["search_mode"], old["energy_mode"],
+                         jcluster)
+    try:
+        srv = nb.nb_server_create(ctx, p, 0, 64)
+    finally:
+        nb.nb_ctx_set_tuning(ctx, old["max_entries"], old["force_min_blocks"], old["search_mode"],
+                             old["energy_mode"], old["jcluster"])
     try:
         target = wb.water_box(1500, None, seed=71)
         f0, e0, v0, st0 = _wait(srv, target, _submit(srv, target))
