@@ -1182,17 +1182,22 @@ static nb_status sys_create(nb_ctx* ctx, const nb_params* params, int natoms, co
         lj[k] = make_float2(6.0f * y->c6[k], 12.0f * y->c12[k]);
         lj[nt * nt + k] = make_float2(y->c6[k], y->c12[k]);
     }
-    int gt_n = 0;
+    int gt_n = 0, et_n = 0;
     if (y->p.coul == NB_COUL_EWALD) {
         float invh = 0.f;
         gt_n = ewald_force_table(y->p.ewald_beta, y->p.rc, reinterpret_cast<float4*>(lj.data() + 2 * nt * nt), &invh);
         float einvh = 0.f;
-        ewald_energy_table(y->p.ewald_beta, y->p.rc, reinterpret_cast<float4*>(lj.data() + etab_offset2(nt)), &einvh);
+        et_n = ewald_energy_table(y->p.ewald_beta, y->p.rc, reinterpret_cast<float4*>(lj.data() + etab_offset2(nt)),
+                                  &einvh);
     }
-    // the whole table block when there are Ewald tables, else the
-    // Lennard-Jones pairs only
-    const size_t n2 = gt_n > 0 ? lj.size() : 2 * (size_t)nt * nt;
-    cudaError_t e = cudaMemcpyAsync(y->d_lj, lj.data(), 8 * n2, cudaMemcpyHostToDevice, ctx->stream);
+    // the filled parts only: the Lennard-Jones pairs with the force table
+    // after them, then the energy table's two halves
+    cudaError_t e = cudaMemcpyAsync(y->d_lj, lj.data(), 8 * (2 * (size_t)nt * nt + 2 * (size_t)gt_n),
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    for (int half = 0; half < 2 && et_n > 0 && e == cudaSuccess; ++half) {
+        const size_t off = etab_offset2(nt) + 2 * (size_t)ET_MAX * half;
+        e = cudaMemcpyAsync(y->d_lj + off, lj.data() + off, 16 * (size_t)et_n, cudaMemcpyHostToDevice, ctx->stream);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(h.acc, 0, 8 * NACC, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h.res, 0, 8 * NRES, ctx->stream);
     if (e != cudaSuccess) {
