@@ -9,9 +9,10 @@
 
 namespace nbgb {
 
-// Cluster size: every i- and j-cluster holds exactly CL atom slots
-// (Section 3.2: "clusters, each containing exactly M particles"; here
-// M = N = 8 so that one 8-lane group of a warp covers one cluster).
+// Cluster size: every i- and j-cluster holds exactly CL atom slots (Section
+// 3.2 groups the atoms into clusters of a fixed size M); here M = N = 8 so
+// that one 8-lane group of a warp covers one cluster, and the 8 x 4 geometry
+// (ListDev::jgeo) takes the two 4-slot halves of a cluster as j-clusters.
 constexpr int CL = 8;
 constexpr int MAX_TYPES = 64;
 constexpr int COL_MAX = 4096;      // atoms per column sorted in shared memory

@@ -8,8 +8,10 @@ Not a test: a report, run on a GPU machine after `__graft_entry__.build()`:
 Per workload it evaluates through the C ABI and prints RMS(dF)/RMS(F), the
 relative errors of E_LJ and E_C, the largest virial component error relative to
 the virial's Frobenius norm, and whether the interacting-pair count equals the
-oracle's.  The 3M-atom box gets forces of 192 sampled atoms (the oracle's
-per-atom loop); the ensemble goes through the batched path.  A second table
+oracle's.  The 3M-atom box gets forces of 10^4 sampled atoms (the oracle's
+per-atom loop) and its energies, virial and pair count against the oracle's
+O(N^2) sums stored in tests/golden/large_box_seed3.json; the ensemble goes
+through the batched path.  A second table
 gives the long-range (PME) part against oracle/pme.py, the virial error
 relative to the sum of the reciprocal and excluded-pair virials' norms.
 """

@@ -448,11 +448,12 @@ def test_device_erfc_two_atom_pairs(ctx):
     """The kernels' erfc on the device, one atom pair at a time: two unit
     charges without Lennard-Jones at distance r in (0.02, rc), Ewald real
     space.  The energy kernel's double-float V = f erfc(beta r) / r against
-    the standard library's erfc at 2e-9 relative (its erfc is good to 1e-9,
-    see tests/test_erfc_fit_cpu.py), and the force kernel's float32
-    F = f (erfc(beta r)/r + 2 beta/sqrt(pi) exp(-beta^2 r^2)) / r against the
-    same formula at 2e-6 relative (SFU rsqrt, reciprocal and 2^x, the fit's
-    1.3e-7 and a few float32 roundings)."""
+    the standard library's erfc at 2e-9 relative (its erfc, from the energy
+    table, is good to 3e-11 absolute, see tests/test_ewald_energy_table_cpu.py),
+    and the force kernel's float32 F = f (erfc(beta r)/r + 2 beta/sqrt(pi)
+    exp(-beta^2 r^2)) / r against the same formula at 2e-6 relative (SFU rsqrt,
+    the force table's 1e-7, see tests/test_ewald_table_cpu.py, and a few float32
+    roundings)."""
     import math
 
     p = wb.params_ewald()
