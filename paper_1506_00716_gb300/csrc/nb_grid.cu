@@ -71,20 +71,35 @@ __global__ void k_bin(const SysDev* __restrict__ sys, const int* __restrict__ at
                       int tot_atoms) {
     pdl_wait();
     pdl_trigger();
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tot_atoms) return;
-    int s = find_sys(atom_off, nsys, t);
-    const SysDev& d = sys[s];
-    int a = t - atom_off[s];
-    float4 v = d.xq_in[a];
-    int kx, ky, kz;
-    float x, y, z;
-    wrap_point(d, v, x, y, z, kx, ky, kz);
-    int cx = max(0, min(d.ncx - 1, (int)(x * d.icw[0])));  // max(): NaN input
-    int cy = max(0, min(d.ncy - 1, (int)(y * d.icw[1])));
-    int col = cx * d.ncy + cy;
-    d.atom_col[a] = col;
-    d.atom_slot[a] = atomicAdd(d.col_count + col, 1);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = t < tot_atoms;
+    int* cc = nullptr;  // the atom's column counter
+    int* slot = nullptr;
+    if (ok) {
+        const int s = find_sys(atom_off, nsys, t);
+        const SysDev& d = sys[s];
+        const int a = t - atom_off[s];
+        float4 v = d.xq_in[a];
+        int kx, ky, kz;
+        float x, y, z;
+        wrap_point(d, v, x, y, z, kx, ky, kz);
+        int cx = max(0, min(d.ncx - 1, (int)(x * d.icw[0])));  // max(): NaN input
+        int cy = max(0, min(d.ncy - 1, (int)(y * d.icw[1])));
+        int col = cx * d.ncy + cy;
+        d.atom_col[a] = col;
+        cc = d.col_count + col;
+        slot = d.atom_slot + a;
+    }
+    // one atomic per column and warp: consecutive atoms (a molecule, a run of
+    // neighbours) mostly share a column, and the lanes of a column take
+    // consecutive arrival slots from it (the z sort orders them anyway)
+    const int lane = threadIdx.x & 31;
+    const unsigned grp = __match_any_sync(0xffffffffu, (unsigned long long)cc);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (ok && lane == leader) base = atomicAdd(cc, __popc(grp));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (ok) *slot = base + __popc(grp & ((1u << lane) - 1u));
 }
 
 // One block per system: exclusive prefix over clusters per column.
