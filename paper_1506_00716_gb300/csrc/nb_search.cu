@@ -814,6 +814,10 @@ k_prune(const SysDev* __restrict__ sys, ListDev src, ListDev dst, KParams kp, fl
                 // that have an unmasked pair
                 const bool k0 = lane < n && (chk ? ((f >> (2 * lane)) & 1ull) != 0ull : (m & MASK_JLO) != 0ull);
                 const bool k1 = lane < n && (chk ? ((f >> (2 * lane + 1)) & 1ull) != 0ull : (m & ~MASK_JLO) != 0ull);
+                // the chunk's kept halves go to shared memory in list order,
+                // after a half left over from the previous chunk (unit 0);
+                // lane k then writes packed entry k from units 2k and 2k + 1,
+                // and an odd last unit waits for the next chunk
                 const unsigned b0 = __ballot_sync(FULL, k0), b1 = __ballot_sync(FULL, k1);
                 const unsigned lt = (1u << lane) - 1u;
                 int q = carry + __popc(b0 & lt) + __popc(b1 & lt);
