@@ -109,3 +109,14 @@ def test_footprint_grows_with_atoms(lib):
     small = nb.nb_sys_footprint(p, 24000, [6.21] * 3)
     large = nb.nb_sys_footprint(p, 3_000_000, [31.0] * 3)
     assert 100 * small < large < 200 * small
+
+
+def test_null_handles_are_refused_without_device_work(lib):
+    """The list exports and the tuning calls refuse a NULL handle with
+    NB_ERR_ARG before touching the device (here, where there is none)."""
+    n = ctypes.c_longlong()
+    assert lib.nb_pairlist_export(None, None, None, None, None, ctypes.byref(n)) == 1
+    assert lib.nb_pairlist_export_slots(None, None, None, None, None, ctypes.byref(n)) == 1
+    t = nb.nb_tuning(32, 3, 0, 0, 4)
+    assert lib.nb_ctx_set_tuning(None, ctypes.byref(t)) == 1
+    assert lib.nb_ctx_get_tuning(None, ctypes.byref(t)) == 1
